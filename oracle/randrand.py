@@ -1,0 +1,429 @@
+"""ORACLE (test infrastructure only) -- plain FP64 RandRAND on the CPU.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  It shares no code with the CUDA
+library: it is a slow, direct transcription of the method in float64 numpy,
+written so that each step can be checked against the paper by eye.
+
+What it computes (paper: Balabanov, Derezinski, Mahoney et al., "RandRAND",
+arXiv 2509.19747):
+
+* the shifted system (A + mu I) x = b, A symmetric PSD (Sec. 1, eq:initsys);
+* the test matrix Omega = X^T (q = 0 in eq:testmatrix), Gaussian or sparse
+  sign (Sec. 2), drawn by ``oracle.philox``;
+* the basis Y_mu = A_mu Omega and its orthogonalisation A_mu Omega = Q R
+  (Sec. 4.1 eq:Rdef) by Householder QR (library ``numpy.linalg.qr``), or
+  the randomised Q-less preconditioned Cholesky QR (Sec. 4.2, Alg. 3);
+* the projector Pi u = Q Q^T u and A_mu^-1 Pi u = Omega R^-1 Q^T u
+  (Sec. 4.1 eq:projector; Sec. 1.1 eq:invAPi);
+* C-RandRAND: P = I - Q Q^T + tau Q G Q^T with G = R^-T (Omega^T A_mu Omega)
+  R^-1 (Sec. 4.1 eq:g_randrand_explicit) in the SPD-preserving form
+  G = (R_M R^-1)^T (R_M R^-1), R_M^T R_M = Omega^T A_mu Omega (remark after
+  Alg. 7); tau = rho |E| / lambda_max(Pi A_mu Pi~) (Sec. 3.2
+  eq:c_randrand_tau) with rho from eq:optimal_rho, F = 1/mu;
+* R-RandRAND: CG on B y = r, B = (I - Pi) A_mu (I - Pi) + tau Pi (Sec. 3.1
+  eq:APdef2), recovery x = Omega R^-1 Q^T (tau y - A_mu (I - Pi) y) +
+  (I - Pi) y (eq:APdef3), tau = |E| (Alg. 4 step 2);
+* |E| and lambda_max by power iterations (Alg. 4 step 2, Alg. 7 step 3);
+* PCG / CG with restarts after each residual reduction by eta = 1e-2
+  (Sec. 7 experimental setup; Alg. 4 step 9, Alg. 7 step 10), the restart
+  residual b - A_mu x recomputed in float64;
+* the exact solution x* = A_mu^-1 b by a dense Cholesky solve.
+
+Readings where the paper is silent: 20 power iterations from seeded start
+vectors, estimate = |w_20| (norm of the last image of a unit vector); the
+inner stop max(eta |r_0|, 0.5 rtol |b|); R = R_chol R_sk as the product
+order in Alg. 3 (the only order with R^T R = Y_mu^T Y_mu); l_sk = 4k and
+gamma_sk = 8 for Theta.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import philox
+
+VARIANT_C = "C"
+VARIANT_R = "R"
+
+
+# ==========================================================================
+# Operators: u -> A u (Sec. 1: access to A through matvecs only)
+# ==========================================================================
+class DenseOp:
+    def __init__(self, A: np.ndarray):
+        self.A = np.asarray(A, dtype=np.float64)
+        self.n = self.A.shape[0]
+
+    def matmat(self, V: np.ndarray) -> np.ndarray:
+        return self.A @ V
+
+    def dense(self) -> np.ndarray:
+        return self.A
+
+
+class CsrOp:
+    def __init__(self, rowptr, colidx, vals, n: int):
+        import scipy.sparse as sp
+        self.n = int(n)
+        self.M = sp.csr_matrix((np.asarray(vals, dtype=np.float64),
+                                np.asarray(colidx), np.asarray(rowptr)), shape=(n, n))
+
+    def matmat(self, V: np.ndarray) -> np.ndarray:
+        return self.M @ V
+
+    def dense(self) -> np.ndarray:
+        return self.M.toarray()
+
+
+class GaussKernelOp:
+    """K_ij = exp(-|x_i - x_j|^2 / (2 h^2)) evaluated in float64 from the
+    given (float32) coordinates, never stored whole (Sec. 7.2.2 eq:kernel,
+    with the kernel matrix itself as A)."""
+
+    def __init__(self, points: np.ndarray, bandwidth: float = 1.0, block: int = 2048):
+        self.X = np.asarray(points, dtype=np.float64)
+        self.n = self.X.shape[0]
+        self.h = float(bandwidth)
+        self.block = block
+
+    def rows(self, lo: int, hi: int) -> np.ndarray:
+        diff2 = ((self.X[lo:hi, None, :] - self.X[None, :, :]) ** 2).sum(-1) \
+            if (hi - lo) * self.n * self.X.shape[1] <= 4_000_000 else None
+        if diff2 is None:
+            xi = self.X[lo:hi]
+            diff2 = np.zeros((hi - lo, self.n))
+            for c in range(self.X.shape[1]):
+                diff2 += (xi[:, c:c + 1] - self.X[None, :, c]) ** 2
+        return np.exp(-diff2 / (2.0 * self.h * self.h))
+
+    def matmat(self, V: np.ndarray) -> np.ndarray:
+        V = np.asarray(V, dtype=np.float64)
+        out = np.empty((self.n,) + V.shape[1:])
+        for lo in range(0, self.n, self.block):
+            hi = min(self.n, lo + self.block)
+            out[lo:hi] = self.rows(lo, hi) @ V
+        return out
+
+    def dense(self) -> np.ndarray:
+        return self.rows(0, self.n)
+
+
+def shifted(op, mu: float):
+    """u -> A_mu u = A u + mu u (Sec. 1)."""
+    return lambda V: op.matmat(V) + mu * V
+
+
+# ==========================================================================
+# Small helpers
+# ==========================================================================
+def householder_qr(Y: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Economic QR with diag(R) > 0 (makes Q, R unique for full column rank)."""
+    Q, R = np.linalg.qr(Y)
+    s = np.sign(np.diag(R))
+    s[s == 0] = 1.0
+    return Q * s, R * s[:, None]
+
+
+def chol_upper(M: np.ndarray) -> np.ndarray:
+    """Upper-triangular R with R^T R = M (raises LinAlgError if not SPD)."""
+    return np.linalg.cholesky(M).T
+
+
+def chol_upper_jitter(M: np.ndarray) -> tuple[np.ndarray, float]:
+    """Cholesky with the jitter ladder of App. C: on failure add alpha I with
+    alpha the smallest of 1e-14 |M|, ..., 1e-1 |M| that succeeds."""
+    try:
+        return chol_upper(M), 0.0
+    except np.linalg.LinAlgError:
+        pass
+    nrm = np.linalg.norm(M, 2)
+    for e in range(-14, 0):
+        alpha = 10.0 ** e * nrm
+        try:
+            return chol_upper(M + alpha * np.eye(M.shape[0])), alpha
+        except np.linalg.LinAlgError:
+            continue
+    raise np.linalg.LinAlgError("matrix not SPD even with the jitter ladder")
+
+
+def solve_upper(R: np.ndarray, B: np.ndarray) -> np.ndarray:
+    import scipy.linalg as sl
+    return sl.solve_triangular(R, B, lower=False)
+
+
+def right_solve_upper(Y: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """Y R^-1 for upper-triangular R."""
+    import scipy.linalg as sl
+    return sl.solve_triangular(R, Y.T, trans="T", lower=False).T
+
+
+# ==========================================================================
+# Build: Alg. 7 steps 1-4 (C) / Alg. 4 steps 1-2 (R)
+# ==========================================================================
+@dataclasses.dataclass
+class Build:
+    op: object
+    mu: float
+    k: int
+    variant: str
+    Omega: np.ndarray        # n x k test matrix
+    Ymu: np.ndarray          # A_mu Omega
+    Q: np.ndarray            # orthonormal basis of range(A_mu Omega)
+    R: np.ndarray            # A_mu Omega = Q R
+    G: np.ndarray | None     # C-RandRAND core matrix
+    normE: float
+    lam_max: float
+    tau: float
+    rho: float
+    jitter: float = 0.0
+
+    # --- projector and preconditioner applications (Sec. 4.1 eq:projector)
+    def Pi(self, V):
+        return self.Q @ (self.Q.T @ V)
+
+    def Ainv_Pi(self, V):
+        """A_mu^-1 Pi V = Omega R^-1 Q^T V (eq:projector with eq:invAPi)."""
+        return self.Omega @ solve_upper(self.R, self.Q.T @ V)
+
+    def apply_P(self, V):
+        """C-RandRAND: P V = V - Q Q^T V + tau Q G Q^T V (eq:g_randrand_explicit)."""
+        t = self.Q.T @ V
+        return V - self.Q @ t + self.tau * (self.Q @ (self.G @ t))
+
+    def apply_B(self, V):
+        """R-RandRAND operator B = (I - Pi) A_mu (I - Pi) + tau Pi (eq:APdef2)."""
+        Amu = shifted(self.op, self.mu)
+        U = V - self.Pi(V)
+        W = Amu(U)
+        return W - self.Pi(W) + self.tau * self.Pi(V)
+
+    def recover_R(self, Yv):
+        """x = Omega R^-1 Q^T (tau y - A_mu (I - Pi) y) + (I - Pi) y (eq:APdef3)."""
+        Amu = shifted(self.op, self.mu)
+        U = Yv - self.Pi(Yv)
+        return self.Ainv_Pi(self.tau * Yv - Amu(U)) + U
+
+
+def make_omega(n: int, k: int, sketch: str, seed: int, gamma: int = 8,
+               precision: str = "fp64") -> np.ndarray:
+    """Test matrix Omega = X^T (eq:testmatrix with q = 0), rounded to the
+    working precision of the sketch (float64, float32 or bfloat16)."""
+    if sketch == "gaussian":
+        Om = philox.gaussian_omega(n, k, seed)
+    elif sketch == "sparse_sign":
+        Om = philox.sparse_sign_omega_dense(n, k, gamma, seed)
+    else:
+        raise ValueError(sketch)
+    if precision == "bf16":
+        Om = philox.round_bf16(Om)
+    elif precision == "fp32":
+        Om = philox.round_f32(Om)
+    return Om
+
+
+def power_iteration(apply, v0: np.ndarray, iters: int) -> float:
+    """|w_iters| where v_0 = v0/|v0|, w_i = apply(v_{i-1}), v_i = w_i/|w_i|."""
+    v = v0 / np.linalg.norm(v0)
+    lam = 0.0
+    for _ in range(iters):
+        w = apply(v)
+        lam = float(np.linalg.norm(w))
+        if lam == 0.0:
+            return 0.0
+        v = w / lam
+    return lam
+
+
+def orthogonalize_householder(Ymu):
+    return householder_qr(Ymu)
+
+
+def fast_q_less_precond_chol_qr(Ymu: np.ndarray, Theta: np.ndarray) -> np.ndarray:
+    """Alg. 3: S = Theta A_mu Omega; R_sk = qr(S); G = R_sk^-T Y^T Y R_sk^-1
+    formed as W^T W with W = Y R_sk^-1; R_chol = chol(G); R = R_chol R_sk."""
+    S = Theta @ Ymu
+    _, Rsk = householder_qr(S)
+    W = right_solve_upper(Ymu, Rsk)
+    Rchol = chol_upper(W.T @ W)
+    return Rchol @ Rsk
+
+
+def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
+          variant: str = VARIANT_C, omega: np.ndarray | None = None,
+          omega_precision: str = "fp64", orth: str = "householder",
+          gamma: int = 8, l_sk: int | None = None, gamma_sk: int = 8,
+          power_iters: int = 20, rho: float | None = None,
+          tau: float | None = None) -> Build:
+    n = op.n
+    if not (1 <= k <= n):
+        raise ValueError("need 1 <= k <= n")
+    Om = make_omega(n, k, sketch, seed, gamma, omega_precision) if omega is None \
+        else np.asarray(omega, dtype=np.float64)
+    # Alg. 7 step 1 / Alg. 4 step 1: Y_mu = A Omega + mu Omega
+    Ymu = op.matmat(Om) + mu * Om
+    if orth == "householder":
+        Q, R = orthogonalize_householder(Ymu)
+    elif orth == "qless":
+        Theta = philox.theta_dense(l_sk or 4 * k, n, gamma_sk, seed)
+        R = fast_q_less_precond_chol_qr(Ymu, Theta)
+        Q = right_solve_upper(Ymu, R)       # Q u = A_mu Omega R^-1 u (eq:implicit)
+    else:
+        raise ValueError(orth)
+
+    b = Build(op=op, mu=mu, k=k, variant=variant, Omega=Om, Ymu=Ymu, Q=Q, R=R,
+              G=None, normE=0.0, lam_max=0.0, tau=0.0, rho=0.0)
+    Amu = shifted(op, mu)
+
+    # |E|, E = (I - Pi) A_mu (I - Pi): Alg. 4 step 2 / Alg. 7 step 3
+    def E_apply(v):
+        u = v - b.Pi(v)
+        w = Amu(u)
+        return w - b.Pi(w)
+    b.normE = power_iteration(E_apply, philox.power_start(n, 0, seed), power_iters)
+    # For k < n, interlacing gives |E| >= lambda_min(A_mu) >= mu (the
+    # eigenvalues of E on the complement of range(Y_mu) are not below those
+    # of A_mu).  Clamping the estimate at mu changes nothing then, and keeps
+    # tau > 0 in the degenerate case k = n, where E = 0 up to rounding.
+    nE = max(b.normE, mu)
+
+    if variant == VARIANT_C:
+        # Alg. 7 step 2 with the SPD-preserving form of G
+        M = Om.T @ Ymu
+        M = 0.5 * (M + M.T)
+        RM, b.jitter = chol_upper_jitter(M)
+        T = right_solve_upper(RM, R)        # R_M R^-1
+        b.G = T.T @ T
+        # lambda_max(Pi A_mu Pi~), Pi~ = Q G Q^T: Alg. 7 step 3
+        b.lam_max = power_iteration(lambda v: b.Pi(Amu(b.Q @ (b.G @ (b.Q.T @ v)))),
+                                    philox.power_start(n, 1, seed), power_iters)
+        if tau is not None:
+            b.tau = float(tau)
+            b.rho = b.tau * b.lam_max / nE
+        else:
+            if rho is None or rho <= 0:
+                # eq:optimal_rho with F = 1/mu; rho = 0.5 a priori when mu = 0
+                b.rho = math.sqrt(mu * b.lam_max / nE) if mu > 0 else 0.5
+            else:
+                b.rho = float(rho)
+            b.tau = b.rho * nE / b.lam_max           # eq:c_randrand_tau
+            if b.tau <= 0.0:                         # mu = 0 and k = n
+                b.tau = 1.0 / b.lam_max
+    elif variant == VARIANT_R:
+        b.rho = 1.0
+        b.tau = nE if tau is None else float(tau)        # Alg. 4 step 2
+        if b.tau <= 0.0:                                  # mu = 0 and k = n
+            b.tau = 1.0
+    else:
+        raise ValueError(variant)
+    return b
+
+
+# ==========================================================================
+# Solve: Alg. 7 steps 5-11 (PCG) / Alg. 4 steps 3-9 (CG on B) with restarts
+# ==========================================================================
+@dataclasses.dataclass
+class SolveInfo:
+    inner_iters: int = 0
+    outer_iters: int = 0
+    rel_residual: float = math.inf
+    converged: bool = False
+    history: list = dataclasses.field(default_factory=list)
+
+
+def pcg(Aop, b, Pop, stop: float, maxit: int):
+    """Textbook preconditioned CG (Saad, Iterative Methods, Alg. 9.1), x0 = 0.
+    Stops when the recursive residual norm is <= stop or after maxit steps."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    it = 0
+    if np.linalg.norm(r) <= stop:
+        return x, it
+    z = Pop(r)
+    p = z.copy()
+    rz = float(r @ z)
+    while it < maxit:
+        w = Aop(p)
+        alpha = rz / float(p @ w)
+        x += alpha * p
+        r -= alpha * w
+        it += 1
+        if np.linalg.norm(r) <= stop:
+            break
+        z = Pop(r)
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it
+
+
+def solve(b_: Build, B: np.ndarray, rtol: float, maxit: int = 20000,
+          eta: float = 1e-2, x0: np.ndarray | None = None,
+          fixed_inner: int | None = None):
+    """Solve A_mu X = B column by column.  Returns (X, [SolveInfo]).
+
+    Outer loop = the paper's restarting (Alg. 7 step 10 / Alg. 4 step 9):
+    r = b - A_mu x in float64; stop when |r| <= rtol |b| or when the inner
+    iterations reach maxit; otherwise run PCG (C) or CG on B (R) to the inner
+    target max(eta |r|, 0.5 rtol |b|) and add the correction to x.
+
+    fixed_inner: if set, run exactly that many inner iterations once (no
+    restart), for iteration-level comparisons.
+    """
+    Amu = shifted(b_.op, b_.mu)
+    B = np.asarray(B, dtype=np.float64)
+    one = B.ndim == 1
+    B2 = B[:, None] if one else B
+    X = np.zeros_like(B2) if x0 is None else np.array(x0, dtype=np.float64).reshape(B2.shape)
+    infos = []
+    for c in range(B2.shape[1]):
+        bc = B2[:, c]
+        x = X[:, c]
+        info = SolveInfo()
+        nb = float(np.linalg.norm(bc))
+        if nb == 0.0:
+            x[:] = 0.0
+            info.rel_residual = 0.0
+            info.converged = True
+            infos.append(info)
+            continue
+        while True:
+            r = bc - Amu(x)
+            rel = float(np.linalg.norm(r)) / nb
+            info.history.append(rel)
+            info.rel_residual = rel
+            if fixed_inner is None and rel <= rtol:
+                info.converged = True
+                break
+            if fixed_inner is not None and info.outer_iters == 1:
+                break
+            budget = maxit - info.inner_iters if fixed_inner is None else fixed_inner
+            if budget <= 0:
+                break
+            stop = max(eta * rel * nb, 0.5 * rtol * nb) if fixed_inner is None else 0.0
+            if b_.variant == VARIANT_C:
+                e, it = pcg(Amu, r, b_.apply_P, stop, budget)
+            else:
+                y, it = pcg(b_.apply_B, r, lambda v: v, stop, budget)
+                e = b_.recover_R(y)
+            x += e
+            info.inner_iters += it
+            info.outer_iters += 1
+        infos.append(info)
+    return (X[:, 0] if one else X), infos
+
+
+def exact_solve(op, mu: float, B: np.ndarray) -> np.ndarray:
+    """x* = (A + mu I)^-1 b by a dense Cholesky solve (library routine)."""
+    import scipy.linalg as sl
+    A = op.dense() + mu * np.eye(op.n)
+    return sl.cho_solve(sl.cho_factor(A, lower=True), B)
+
+
+def true_rel_residual(op, mu: float, X: np.ndarray, B: np.ndarray) -> np.ndarray:
+    R = np.asarray(B) - shifted(op, mu)(np.asarray(X))
+    R = R.reshape(R.shape[0], -1)
+    Bn = np.asarray(B).reshape(R.shape)
+    return np.linalg.norm(R, axis=0) / np.linalg.norm(Bn, axis=0)

@@ -1,0 +1,422 @@
+"""Pins of the float64 oracle to facts fixed by the paper and by mathematics.
+
+None of these re-types an oracle formula: each checks the oracle against an
+independent computation (dense inverse, dense eigenvalues, a closed-form
+spectrum, a textbook routine, brute force) or an invariant the paper proves.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import philox
+from oracle import randrand as O
+from workloads import generators as W
+
+
+# --------------------------------------------------------------------------
+# fixtures
+# --------------------------------------------------------------------------
+def small_dense(n=160, power=2.0, seed=11):
+    P = W.dense_power_spectrum(n, seed=seed, power=power)
+    return P, O.DenseOp(P.A)
+
+
+def dense_inv(op, mu):
+    return np.linalg.inv(op.dense() + mu * np.eye(op.n))
+
+
+def sym_sqrt(M):
+    w, V = np.linalg.eigh(0.5 * (M + M.T))
+    return (V * np.sqrt(np.maximum(w, 0))) @ V.T
+
+
+# --------------------------------------------------------------------------
+# Philox streams: statistics and structure (the paper fixes no generator)
+# --------------------------------------------------------------------------
+def test_philox_uniform_statistics():
+    n = 1 << 18
+    ctr = np.zeros((n // 4, 4), dtype=np.uint64)
+    ctr[:, 0] = np.arange(n // 4)
+    w = philox.philox4x32_10(ctr, philox.seed_key(12345)).ravel()
+    u = philox.uniform24(w)
+    assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / n)
+    assert abs(u.var() - 1 / 12) < 5e-3 / 12 * 4
+    # every bit of the 32-bit words is balanced
+    bits = (w[:, None] >> np.arange(32, dtype=np.uint32)) & 1
+    frac = bits.mean(axis=0)
+    assert np.all(np.abs(frac - 0.5) < 5 * 0.5 / math.sqrt(n))
+    # chi-square of the top byte over 256 bins
+    hist = np.bincount((w >> 24).astype(np.int64), minlength=256)
+    exp = n / 256
+    chi2 = ((hist - exp) ** 2 / exp).sum()
+    assert chi2 < 255 + 6 * math.sqrt(2 * 255)
+
+
+def test_philox_avalanche_and_key_dependence():
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2**32, size=(2048, 4), dtype=np.uint64)
+    key = (0x1234, 0x5678)
+    base = philox.philox4x32_10(ctr, key)
+    for word in range(4):
+        for bit in (0, 13, 31):
+            c2 = ctr.copy()
+            c2[:, word] ^= np.uint64(1 << bit)
+            diff = philox.philox4x32_10(c2, key) ^ base
+            flips = np.unpackbits(diff.view(np.uint8)).mean()
+            assert abs(flips - 0.5) < 0.02
+    other = philox.philox4x32_10(ctr, (0x1235, 0x5678)) ^ base
+    assert abs(np.unpackbits(other.view(np.uint8)).mean() - 0.5) < 0.02
+
+
+def test_gaussian_omega_moments():
+    n, k = 4000, 64
+    Om = philox.gaussian_omega(n, k, seed=77)
+    z = Om.ravel() * math.sqrt(k)            # entries N(0, 1/k) (Sec. 2)
+    N = z.size
+    assert abs(z.mean()) < 5 / math.sqrt(N)
+    assert abs(z.var() - 1) < 5 * math.sqrt(2 / N)
+    kurt = (z ** 4).mean() / z.var() ** 2
+    assert abs(kurt - 3) < 5 * math.sqrt(24 / N)
+    # columns nearly orthogonal with norm^2 ~ n/k
+    G = Om.T @ Om
+    assert np.allclose(np.diag(G), n / k, rtol=0.15)
+    # independent counters -> distinct seeds give different matrices
+    assert not np.allclose(Om, philox.gaussian_omega(n, k, seed=78))
+
+
+def test_sparse_sign_structure():
+    n, k, gamma = 3000, 40, 8
+    cols, sgn = philox.sparse_sign_pattern(n, k, gamma, seed=5, stream=philox.STREAM_OMEGA)
+    assert cols.min() >= 0 and cols.max() < k
+    for r in range(n):
+        assert len(set(cols[r].tolist())) == gamma      # distinct per row
+    assert set(np.unique(sgn)) == {-1, 1}
+    assert abs(sgn.mean()) < 5 / math.sqrt(sgn.size)
+    # column choice uniform: chi-square over k bins
+    hist = np.bincount(cols.ravel(), minlength=k)
+    exp = n * gamma / k
+    chi2 = ((hist - exp) ** 2 / exp).sum()
+    assert chi2 < (k - 1) + 6 * math.sqrt(2 * (k - 1))
+    Om = philox.sparse_sign_omega_dense(n, k, gamma, seed=5)
+    assert np.allclose(np.abs(Om[Om != 0]), 1 / math.sqrt(gamma))
+    assert np.all((Om != 0).sum(axis=1) == gamma)
+    Th = philox.theta_dense(32, 500, 8, seed=5)
+    assert np.all((Th != 0).sum(axis=0) == 8)
+
+
+def test_bf16_rounding_brute_force():
+    # brute force: the nearest bfloat16 (ties to even) among all candidates
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(2000) * 10.0 ** rng.integers(-3, 3, 2000)
+    r = philox.round_bf16(x)
+    x32 = x.astype(np.float32).astype(np.float64)
+    for xi, ri in zip(x32, r):
+        u = np.array([xi], dtype=np.float32).view(np.uint32)[0] & 0xFFFF0000
+        lo = np.array([u], dtype=np.uint32).view(np.float32)[0].astype(np.float64)
+        hi = np.array([u + 0x10000], dtype=np.uint32).view(np.float32)[0].astype(np.float64)
+        cands = sorted([lo, hi], key=lambda c: (abs(c - xi),
+                                                int(np.array([c], np.float32).view(np.uint32)[0] >> 16) & 1))
+        assert ri == cands[0]
+
+
+# --------------------------------------------------------------------------
+# Input generators
+# --------------------------------------------------------------------------
+def test_dense_generator_closed_form_spectrum():
+    P = W.dense_power_spectrum(300, seed=1)
+    ev = np.linalg.eigvalsh(P.A)[::-1]
+    assert np.max(np.abs(ev - np.arange(1, 301) ** -2.0)) < 1e-13
+    assert np.allclose(P.U.T @ P.U, np.eye(300), atol=1e-13)
+
+
+def test_kernel_operator_brute_force():
+    X = W.mixture_points(60, seed=3)
+    op = O.GaussKernelOp(X, bandwidth=1.3)
+    K = op.dense()
+    for i, j in [(0, 0), (0, 5), (17, 42), (59, 1)]:
+        d2 = sum((float(X[i, c]) - float(X[j, c])) ** 2 for c in range(X.shape[1]))
+        assert K[i, j] == pytest.approx(math.exp(-d2 / (2 * 1.3 ** 2)), rel=1e-14)
+    assert np.allclose(K, K.T) and np.allclose(np.diag(K), 1.0)
+    v = np.random.default_rng(0).standard_normal((60, 3))
+    assert np.allclose(op.matmat(v), K @ v, rtol=1e-13, atol=1e-13)
+
+
+def test_csr_generator_properties():
+    C = W.diffusion_csr(side=24, seed=9, corr_len=4.0)
+    assert C.nnz == 5 * C.n - 4 * 24
+    D = C.to_dense()
+    assert np.allclose(D, D.T)
+    assert np.all(D.sum(axis=1) > -1e-5)              # weak diagonal dominance
+    assert np.linalg.eigvalsh(D).min() > 0             # SPD with Dirichlet boundary
+    op = O.CsrOp(C.rowptr, C.colidx, C.vals, C.n)
+    v = np.random.default_rng(1).standard_normal(C.n)
+    assert np.allclose(op.matmat(v), D @ v)
+
+
+# --------------------------------------------------------------------------
+# Projector, basis and the identity A_mu^-1 Pi = Omega (A_mu Omega)^+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("sketch", ["gaussian", "sparse_sign"])
+def test_projector_is_orthogonal_projector_onto_range(sketch):
+    P, op = small_dense()
+    k, mu = 20, 1e-3
+    bd = O.build(op, mu, k, sketch, seed=3)
+    Pi = bd.Pi(np.eye(op.n))
+    assert np.linalg.norm(Pi @ Pi - Pi, 2) <= 1e-12          # idempotent
+    assert np.linalg.norm(Pi - Pi.T, 2) <= 1e-12             # symmetric
+    assert abs(np.trace(Pi) - k) < 1e-10                     # rank k
+    Ymu = op.A @ bd.Omega + mu * bd.Omega                    # independent A_mu Omega
+    assert np.linalg.norm(Ymu - Pi @ Ymu) <= 1e-12 * np.linalg.norm(Ymu)
+    assert np.linalg.norm(bd.Q @ bd.R - Ymu) <= 1e-13 * np.linalg.norm(Ymu)
+    assert np.all(np.diag(bd.R) > 0)
+
+
+def test_invAPi_identity_against_dense_inverse():
+    # Sec. 1.1 eq:invAPi: A_mu^-1 Pi = Omega (A_mu Omega)^+, used through
+    # Omega R^-1 Q^T (eq:projector)
+    P, op = small_dense()
+    mu = 1e-2
+    bd = O.build(op, mu, 15, "gaussian", seed=4)
+    lhs = dense_inv(op, mu) @ bd.Pi(np.eye(op.n))
+    rhs = bd.Ainv_Pi(np.eye(op.n))
+    assert np.linalg.norm(lhs - rhs, 2) <= 1e-10 * np.linalg.norm(lhs, 2)
+    pinv = bd.Omega @ np.linalg.pinv(op.A @ bd.Omega + mu * bd.Omega)
+    assert np.linalg.norm(pinv - rhs, 2) <= 1e-9 * np.linalg.norm(lhs, 2)
+
+
+def test_core_matrix_G_equals_QT_Ainv_Q():
+    # G = R^-T (Omega^T A_mu Omega) R^-1 (eq:g_randrand_explicit) equals
+    # Q^T A_mu^-1 Q by eq:invAPi; the oracle forms G as (R_M R^-1)^T (R_M R^-1)
+    P, op = small_dense()
+    mu = 1e-2
+    bd = O.build(op, mu, 25, "gaussian", seed=5)
+    ref = bd.Q.T @ dense_inv(op, mu) @ bd.Q
+    assert np.linalg.norm(bd.G - ref, 2) <= 1e-9 * np.linalg.norm(ref, 2)
+    assert np.linalg.eigvalsh(bd.G).min() > 0
+
+
+# --------------------------------------------------------------------------
+# Special cases with closed-form spectra
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("variant", ["C", "R"])
+def test_exact_eigenvector_deflation_spectrum(variant):
+    # Omega = U_k (exact top-k eigenvectors): Pi = U_k U_k^T and both the
+    # R-RandRAND operator B (eq:APdef2) and the C-RandRAND P A_mu have
+    # spectrum {tau (k times)} U {lambda_i + mu, i > k}
+    P, op = small_dense(n=120)
+    k, mu = 10, 1e-3
+    bd = O.build(op, mu, k, omega=P.U[:, :k], variant=variant)
+    I = np.eye(op.n)
+    if variant == "C":
+        M = bd.apply_P(I) @ (op.A + mu * I)
+    else:
+        M = bd.apply_B(I)
+    ev = np.sort(np.linalg.eigvals(M).real)
+    expect = np.sort(np.concatenate([np.full(k, bd.tau), P.lam[k:] + mu]))
+    assert np.allclose(ev, expect, rtol=1e-9, atol=1e-12)
+    if variant == "C":
+        # Pi A_mu Pi~ = Pi on range(Q): lambda_max = 1 exactly
+        assert bd.lam_max == pytest.approx(1.0, rel=1e-10)
+        # eq:optimal_rho with F = 1/mu: tau = sqrt(mu |E| / lambda_max)
+        assert bd.tau == pytest.approx(math.sqrt(mu * bd.normE / bd.lam_max), rel=1e-14)
+    # |E| = lambda_{k+1} + mu is approached from below by the power iteration
+    assert bd.normE <= (P.lam[k] + mu) * (1 + 1e-12)
+    assert bd.normE >= 0.5 * (P.lam[k] + mu)
+
+
+@pytest.mark.parametrize("variant", ["C", "R"])
+def test_full_sketch_converges_in_one_iteration(variant):
+    # k = n: Pi = I, P = tau A_mu^-1 (C) and B = tau I (R): one CG step
+    P, op = small_dense(n=40)
+    bd = O.build(op, 1e-2, 40, "gaussian", seed=6, variant=variant)
+    b = W.gaussian_rhs(40, 1, 6)[:, 0]
+    x, info = O.solve(bd, b, rtol=1e-10, fixed_inner=1)
+    assert O.true_rel_residual(op, 1e-2, x, b)[0] < 1e-9
+
+
+def test_c_randrand_eigenvalue_bracket():
+    # Prop. thm:cnd_bound2 eq:c_randrand_eigenvalues:
+    # (|F| + 1/tau)^-1 <= lambda_i(P^1/2 A_mu P^1/2) <= (1 + rho) |E|,
+    # rho = tau lambda_max(Pi A_mu Pi A_mu^-1 Pi) / |E|; all from dense algebra
+    P, op = small_dense(n=150, power=1.5)
+    mu = 1e-3
+    bd = O.build(op, mu, 12, "gaussian", seed=7)
+    I = np.eye(op.n)
+    Amu = op.A + mu * I
+    Pi = bd.Pi(I)
+    E = (I - Pi) @ Amu @ (I - Pi)
+    F = (I - Pi) @ np.linalg.inv(Amu) @ (I - Pi)
+    nE, nF = np.linalg.norm(E, 2), np.linalg.norm(F, 2)
+    lmax = np.max(np.linalg.eigvals(Pi @ Amu @ Pi @ np.linalg.inv(Amu) @ Pi).real)
+    rho = bd.tau * lmax / nE
+    Pm = bd.apply_P(I)
+    S = sym_sqrt(Pm)
+    ev = np.linalg.eigvalsh(S @ Amu @ S)
+    assert ev.min() >= (nF + 1 / bd.tau) ** -1 * (1 - 1e-9)
+    assert ev.max() <= (1 + rho) * nE * (1 + 1e-9)
+    # power-iteration estimates: |E| (symmetric E) from below; lambda_max of
+    # the product of two SPD factors (not normal: the norm ratio may overshoot)
+    assert bd.normE <= nE * (1 + 1e-12) and bd.normE >= 0.8 * nE
+    assert abs(bd.lam_max - lmax) <= 0.05 * lmax
+    # Prop. thm:cnd_bound2_ext eq:c_randrand_eigenvalues2_ext
+    Ainv = np.linalg.inv(Amu)
+    N = Pi @ Ainv @ Pi
+    w, V = np.linalg.eigh(0.5 * (N + N.T))
+    keep = w > 1e-12 * w.max()
+    Nh = (V[:, keep] * np.sqrt(w[keep])) @ V[:, keep].T
+    Nmh = (V[:, keep] / np.sqrt(w[keep])) @ V[:, keep].T
+    C1 = (I - Pi) @ Ainv @ Pi @ Nmh
+    C2 = (I - Pi) @ Amu @ Pi @ Nh
+    lmin = np.linalg.eigvalsh(Amu).min()
+    lo = (max(1 / lmin, 1 / bd.tau) + bd.tau ** -0.5 * np.linalg.norm(C1 + C1.T, 2)) ** -1
+    hi = max(nE, lmax) + bd.tau ** 0.5 * np.linalg.norm(C2 + C2.T, 2)
+    assert ev.min() >= lo * (1 - 1e-9) and ev.max() <= hi * (1 + 1e-9)
+
+
+def test_r_randrand_condition_bound():
+    # Prop. thm:cnd_bound eq:cnd_bound: for lambda_min <= tau <= |E| the
+    # spectrum of B lies in [lambda_min(A_mu), |E|] (rho = 1)
+    P, op = small_dense(n=150, power=1.5)
+    mu = 1e-3
+    bd = O.build(op, mu, 12, "gaussian", seed=8, variant="R")
+    I = np.eye(op.n)
+    Amu = op.A + mu * I
+    Pi = bd.Pi(I)
+    nE = np.linalg.norm((I - Pi) @ Amu @ (I - Pi), 2)
+    lmin = np.linalg.eigvalsh(Amu).min()
+    assert lmin <= bd.tau <= nE * (1 + 1e-12)
+    ev = np.linalg.eigvalsh(0.5 * (bd.apply_B(I) + bd.apply_B(I).T))
+    assert ev.min() >= min(bd.tau, lmin) * (1 - 1e-9)
+    assert ev.max() <= max(bd.tau, nE) * (1 + 1e-9)
+    # B P^-1 = A_mu (the recovery is exact): x = P y solves A_mu x = B y
+    y = np.random.default_rng(0).standard_normal(op.n)
+    assert np.allclose(Amu @ bd.recover_R(y), bd.apply_B(y[:, None])[:, 0], rtol=1e-9, atol=1e-12)
+
+
+def test_iteration_count_within_convergence_bound():
+    # Prop. thm:conv_bound: |y - y_t|_B <= 2 exp(-2t/T) |y - y_0|_B with
+    # T = (|E| / (lambda_n + mu))^1/2.  Since |r_t| / |r_0| <= cond(B)^1/2
+    # times the B-norm ratio and cond(B) <= T^2 here, reaching |r_t| <= u |r_0|
+    # takes at most t = ceil(T/2 (log(2T) + log(1/u))) CG steps (exact |E|).
+    P, op = small_dense(n=200, power=2.0)
+    mu, u = 1e-4, 1e-8
+    bd = O.build(op, mu, 20, "gaussian", seed=9, variant="R")
+    I = np.eye(op.n)
+    Pi = bd.Pi(I)
+    nE = np.linalg.norm((I - Pi) @ (op.A + mu * I) @ (I - Pi), 2)
+    T = math.sqrt(nE / (P.lam[-1] + mu))
+    b = W.gaussian_rhs(op.n, 1, 9)[:, 0]
+    y, it = O.pcg(bd.apply_B, b, lambda v: v, u * np.linalg.norm(b), 10 * op.n)
+    assert it <= math.ceil(T / 2 * (math.log(2 * T) + math.log(1 / u)))
+    assert it > 0
+
+
+# --------------------------------------------------------------------------
+# Solutions against the dense Cholesky solve
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("variant", ["C", "R"])
+@pytest.mark.parametrize("sketch", ["gaussian", "sparse_sign"])
+def test_solution_matches_dense_cholesky(variant, sketch):
+    P, op = small_dense(n=300)
+    mu, rtol = 1e-4, 1e-10
+    bd = O.build(op, mu, 30, sketch, seed=10, variant=variant)
+    B = W.gaussian_rhs(op.n, 3, 10)
+    X, infos = O.solve(bd, B, rtol)
+    Xs = O.exact_solve(op, mu, B)
+    cond = (1 + mu) / (P.lam[-1] + mu)
+    assert all(i.converged for i in infos)
+    assert np.all(O.true_rel_residual(op, mu, X, B) <= rtol)
+    err = np.linalg.norm(X - Xs, axis=0) / np.linalg.norm(Xs, axis=0)
+    assert np.all(err <= cond * rtol)
+
+
+def test_kernel_system_solution():
+    X = W.mixture_points(400, seed=12)
+    op = O.GaussKernelOp(X)
+    mu = 1e-3
+    bd = O.build(op, mu, 40, "gaussian", seed=12)
+    B = W.gaussian_rhs(400, 2, 12)
+    Xs = O.exact_solve(op, mu, B)
+    Xo, infos = O.solve(bd, B, 1e-10)
+    assert np.allclose(Xo, Xs, rtol=0, atol=1e-7 * np.abs(Xs).max())
+
+
+# --------------------------------------------------------------------------
+# Alg. 3 (randomised Q-less preconditioned Cholesky QR)
+# --------------------------------------------------------------------------
+def test_qless_R_matches_householder():
+    P, op = small_dense(n=400, power=1.0)
+    mu, k = 1e-6, 30
+    Om = O.make_omega(op.n, k, "sparse_sign", 13)
+    Ymu = op.A @ Om + mu * Om
+    Th = philox.theta_dense(4 * k, op.n, 8, 13)
+    R3 = O.fast_q_less_precond_chol_qr(Ymu, Th)
+    _, Rh = O.householder_qr(Ymu)
+    c = np.linalg.cond(Ymu)
+    assert np.linalg.norm(R3 - Rh) <= 1e3 * c * 1e-16 * np.linalg.norm(Rh)
+    # orthogonality of Q = Y R^-1 scales with u cond (Sec. 4.2), not u cond^2
+    Q = O.right_solve_upper(Ymu, R3)
+    assert np.linalg.norm(Q.T @ Q - np.eye(k), 2) <= 1e3 * c * 1e-16
+    # the embedding makes W = Y R_sk^-1 well conditioned (eq:epsilon_embedding)
+    _, Rsk = O.householder_qr(Th @ Ymu)
+    assert np.linalg.cond(O.right_solve_upper(Ymu, Rsk)) < 10
+
+
+# --------------------------------------------------------------------------
+# Lemma thm:apriori_gen00: expected projection error with l = 2k+2
+# --------------------------------------------------------------------------
+@pytest.mark.slow
+def test_gaussian_range_approximation_expectation():
+    n, kk = 256, 8
+    l = 2 * kk + 2
+    P = W.dense_power_spectrum(n, seed=21, power=1.0)
+    mu = 1e-3
+    Amu = P.A + mu * np.eye(n)
+    sig = P.lam + mu
+    sr = (sig[kk - 1:] ** 2).sum() / sig[kk - 1] ** 2
+    bound = (2 + math.sqrt(2) * math.e * math.sqrt(sr / kk)) * sig[kk - 1]
+    errs = []
+    for s in range(40):
+        Om = philox.gaussian_omega(n, l, seed=1000 + s)
+        Q, _ = np.linalg.qr(Amu @ Om)
+        errs.append(np.linalg.norm(Amu - Q @ (Q.T @ Amu), 2))
+    assert np.mean(errs) <= bound
+
+
+# --------------------------------------------------------------------------
+# Planted mistakes: each pin above must catch a plausible slip in the oracle
+# --------------------------------------------------------------------------
+def test_pins_catch_planted_mistakes(monkeypatch):
+    P, op = small_dense(n=80)
+    mu, k = 1e-3, 8
+    I = np.eye(op.n)
+
+    def spectrum_ok(bd):
+        M = bd.apply_P(I) @ (op.A + mu * I)
+        ev = np.sort(np.linalg.eigvals(M).real)
+        expect = np.sort(np.concatenate([np.full(k, bd.tau), P.lam[k:] + mu]))
+        return np.allclose(ev, expect, rtol=1e-9, atol=1e-12)
+
+    good = O.build(op, mu, k, omega=P.U[:, :k])
+    assert spectrum_ok(good)
+
+    # (1) dropped "- Q Q^T V" term in P
+    monkeypatch.setattr(O.Build, "apply_P",
+                        lambda self, V: V + self.tau * (self.Q @ (self.G @ (self.Q.T @ V))))
+    assert not spectrum_ok(good)
+    monkeypatch.undo()
+
+    # (2) transposed R in A_mu^-1 Pi
+    bd = O.build(op, mu, k, "gaussian", seed=1)
+    lhs = dense_inv(op, mu) @ bd.Pi(I)
+    monkeypatch.setattr(O.Build, "Ainv_Pi",
+                        lambda self, V: self.Omega @ O.solve_upper(self.R.T.copy(), self.Q.T @ V))
+    assert np.linalg.norm(lhs - bd.Ainv_Pi(I), 2) > 1e-6 * np.linalg.norm(lhs, 2)
+    monkeypatch.undo()
+
+    # (3) wrong sign of the shift in the basis
+    orig = O.shifted
+    bad = O.build(op, -mu, k, "gaussian", seed=1)
+    assert np.linalg.norm((op.A + mu * I) @ bad.Omega - bad.Q @ bad.R) > 1e-8
+    assert orig is O.shifted
