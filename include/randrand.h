@@ -1,0 +1,273 @@
+/*
+ * randrand.h -- C ABI of the GB300 RandRAND-PCG library.
+ *
+ * RandRAND (Randomized RANge Deflation; arXiv 2509.19747) preconditions a
+ * Krylov solver for the shifted system
+ *
+ *     (A + mu I) x = b,   A symmetric positive semidefinite, mu >= 0
+ *                                              (Sec. 1, eq:initsys)
+ *
+ * by orthogonal projection onto range(A_mu Omega), A_mu = A + mu I, where
+ * Omega is a random n x k test matrix (Sec. 1.1 eq:testmatrix, q = 0).
+ * The library builds the preconditioner once per (A, mu, k, seed) and then
+ * solves for any number of right-hand sides.  Every floating-point step
+ * runs in this library's own CUDA kernels on the GPU; there is no host
+ * fallback.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named "device" must point to GPU global memory of the
+ *     current device; the caller allocates and owns that memory.  The
+ *     library allocates no device memory: all scratch lives in the
+ *     caller-provided workspace (randrand_workspace_bytes).
+ *   - All GPU work is enqueued on the stream given to randrand_build
+ *     (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *   - Every function returns an rr_status and never aborts.  Arguments are
+ *     validated on the host before any launch; on an error return nothing
+ *     has been written to caller buffers unless stated otherwise.
+ *   - Matrices are row-major unless stated otherwise; right-hand sides and
+ *     solutions are column-major (column j starts at ptr + j * ld).
+ */
+#ifndef RANDRAND_H
+#define RANDRAND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rr_status;
+enum {
+  RR_OK = 0,
+  RR_ERR_INVALID_ARG = 1,   /* a size, pointer, option or value is invalid */
+  RR_ERR_WORKSPACE = 2,     /* workspace smaller than randrand_workspace_bytes */
+  RR_ERR_NOT_SPD = 3,       /* a k x k Gram / core matrix is not positive definite */
+  RR_ERR_BREAKDOWN = 4,     /* p^T A_mu p <= 0 or a non-finite Krylov scalar */
+  RR_ERR_MAXIT = 5,         /* iteration budget reached before rtol; x holds the last iterate */
+  RR_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  RR_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+  RR_ERR_UNSUPPORTED = 8    /* the combination of options is not implemented */
+};
+
+/* Operator kinds: A is only accessed through u -> A u (Sec. 1) */
+enum {
+  RR_OP_DENSE = 0,          /* explicit n x n symmetric matrix */
+  RR_OP_CSR = 1,            /* sparse symmetric matrix, CSR, int32 indices */
+  RR_OP_GAUSS_KERNEL = 2    /* K_ij = exp(-|x_i - x_j|^2 / (2 h^2)), generated on the fly */
+};
+
+/* Test matrices Omega = X^T (Sec. 2) */
+enum {
+  RR_SKETCH_GAUSSIAN = 0,   /* entries N(0, 1/k) */
+  RR_SKETCH_SPARSE_SIGN = 1 /* gamma entries +-1/sqrt(gamma) per row of Omega */
+};
+
+/* Arithmetic of the path */
+enum {
+  RR_PREC_FP64 = 0,         /* everything in float64 */
+  RR_PREC_FP32 = 1,         /* float32 sketch, iterations and restart residual ("plain form") */
+  RR_PREC_MIXED = 2         /* bf16 sketch with fp32 accumulation, fp32 iterations,
+                               float64-accurate restart residual (iterative refinement) */
+};
+
+/* Preconditioner variants */
+enum {
+  RR_VARIANT_C = 0,         /* C-RandRAND PCG (Sec. 3.2, Alg. 7) */
+  RR_VARIANT_R = 1          /* R-RandRAND CG on B y = b, x = P y (Sec. 3.1, Alg. 4) */
+};
+
+/* Orthogonalisation of Y_mu = A_mu Omega */
+enum {
+  RR_ORTH_CHOLQR2 = 0,      /* Cholesky QR applied twice (Sec. 4.2 Alg. 2 as first pass) */
+  RR_ORTH_RAND_CHOLQR = 1   /* Alg. 3 (sketch-preconditioned Cholesky QR) + one CholQR pass */
+};
+
+/*
+ * Operator description.  Borrowed: every pointer must stay valid and
+ * unchanged until randrand_free of each handle built from it.
+ *   kind = RR_OP_DENSE:   dense (device) n x n row-major with leading
+ *                         dimension ld >= n, element type dtype
+ *                         (0 = float64, 1 = float32); must be symmetric.
+ *   kind = RR_OP_CSR:     rowptr (device, n+1 int32), colidx (device, nnz
+ *                         int32, sorted per row), vals (device, nnz, dtype);
+ *                         the matrix must be symmetric.
+ *   kind = RR_OP_GAUSS_KERNEL: points (device, n x dim float32 row-major),
+ *                         bandwidth h > 0; A = K is never stored.
+ */
+typedef struct {
+  int32_t kind;
+  int32_t dtype;
+  int64_t n;
+  const void* dense;
+  int64_t ld;
+  const int32_t* rowptr;
+  const int32_t* colidx;
+  const void* vals;
+  int64_t nnz;
+  const float* points;
+  int32_t dim;
+  int32_t pad_;
+  double bandwidth;
+} rr_operator;
+
+typedef struct {
+  int32_t variant;       /* RR_VARIANT_*                          default C      */
+  int32_t precision;     /* RR_PREC_*                             default FP64   */
+  int32_t orth;          /* RR_ORTH_*                             default CHOLQR2 */
+  int32_t gamma;         /* nonzeros per row of a sparse-sign Omega, default 8  */
+  int32_t l_sk;          /* rows of Theta for RAND_CHOLQR (0 -> 4k)             */
+  int32_t gamma_sk;      /* nonzeros per column of Theta, default 8             */
+  int32_t power_iters;   /* power iterations per estimate, default 20           */
+  int32_t max_rhs;       /* right-hand sides a solve may pass (1..8), default 1 */
+  int32_t profile;       /* 1: time the hot kernels with CUDA events (rr_profile) */
+  int32_t pad_;
+  double rho;            /* C variant: <= 0 -> eq:optimal_rho with F = 1/mu     */
+  double restart_eta;    /* restart after this residual reduction, default 1e-2 */
+} rr_build_opts;
+
+typedef struct {
+  int32_t inner_iters;   /* Krylov iterations, summed over restarts           */
+  int32_t outer_iters;   /* restarts (= refinement steps)                     */
+  int32_t matvecs;       /* products with A_mu in the solve                    */
+  rr_status status;      /* RR_OK, RR_ERR_MAXIT or RR_ERR_BREAKDOWN            */
+  double rel_residual;   /* |b - A_mu x| / |b|, evaluated by the restart residual */
+  double tau;            /* preconditioner coefficient                         */
+  double normE;          /* power-iteration estimate of |(I-Pi) A_mu (I-Pi)|   */
+  double lam_max;        /* estimate of lambda_max(Pi A_mu Pi~) (C variant)    */
+} rr_solve_info;
+
+/* Per-kernel device time of a profiled handle (opts.profile = 1), summed
+ * over its build and solves: launches and milliseconds measured with CUDA
+ * events recorded on the handle stream around each launch. */
+enum {
+  RR_PROF_SKETCH = 0,     /* Y_mu = A_mu Omega                                   */
+  RR_PROF_MATVEC = 1,     /* A_mu p in the Krylov iterations (working precision) */
+  RR_PROF_RESIDUAL = 2,   /* A_mu x of the restart residual                      */
+  RR_PROF_POWER = 3,      /* A_mu u in the power iterations                      */
+  RR_PROF_COUNT = 8
+};
+typedef struct {
+  int32_t launches[RR_PROF_COUNT];
+  double ms[RR_PROF_COUNT];
+} rr_profile;
+
+typedef struct rr_handle rr_handle;
+
+/* Fill *o with the defaults listed in rr_build_opts. */
+void rr_build_opts_default(rr_build_opts* o);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* randrand_status_str(rr_status s);
+
+/*
+ * Device bytes the handle needs for (A, k, opts): the test matrix, the basis
+ * Q (and Y_mu while building), the k x k factors, the power-iteration and
+ * Krylov state for opts->max_rhs columns and all reduction scratch.
+ * Host only; touches no device memory.  Errors: RR_ERR_INVALID_ARG.
+ */
+rr_status randrand_workspace_bytes(const rr_operator* A, int32_t k,
+                                   const rr_build_opts* opts, size_t* bytes);
+
+/*
+ * Build the RandRAND preconditioner: Alg. 7 steps 1-4 (variant C) or Alg. 4
+ * steps 1-2 (variant R), with the basis-explicit representation of Sec. 4.1.
+ *   A          operator (see rr_operator); borrowed.
+ *   mu         shift, >= 0 and finite.
+ *   k          sketch dimension l of the paper, 1 <= k <= n.
+ *   sketch     RR_SKETCH_GAUSSIAN or RR_SKETCH_SPARSE_SIGN.
+ *   seed       64-bit key of the counter-based generator that draws Omega,
+ *              Theta and the power-iteration start vectors.
+ *   opts       NULL for defaults.
+ *   workspace  device buffer of ws_bytes >= randrand_workspace_bytes(),
+ *              256-byte aligned; owned by the caller, used exclusively by
+ *              the handle until randrand_free.
+ *   stream     cudaStream_t (as void*) for all work of this handle.
+ *   out        receives a host-allocated handle (free with randrand_free).
+ * Synchronises the stream once at the end (to read the tau estimates).
+ * Errors: RR_ERR_INVALID_ARG, RR_ERR_WORKSPACE, RR_ERR_NOT_SPD (Y_mu
+ * numerically rank deficient even after a shifted Cholesky retry),
+ * RR_ERR_UNSUPPORTED, RR_ERR_CUDA.  On error *out is NULL.
+ */
+rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t sketch,
+                         uint64_t seed, const rr_build_opts* opts, void* workspace,
+                         size_t ws_bytes, void* stream, rr_handle** out);
+
+/*
+ * Solve A_mu X = B with the handle's preconditioner: PCG (variant C,
+ * Alg. 7 steps 5-11) or CG on B y = r with recovery x = P y (variant R,
+ * Alg. 4 steps 3-9), restarted after each residual reduction by
+ * restart_eta (Sec. 7 setup).  Each restart recomputes r = b - A_mu x
+ * (float64-accurate for RR_PREC_FP64 and RR_PREC_MIXED).
+ *   b       device, n x nrhs float64, column-major, leading dimension ldb >= n.
+ *   x       device, n x nrhs float64, column-major, ldx >= n.  On entry the
+ *           initial guess if x_is_guess != 0 (else ignored); on exit the
+ *           solution, also for RR_ERR_MAXIT.
+ *   nrhs    1 <= nrhs <= opts.max_rhs of the build.
+ *   rtol    stop when |b - A_mu x| <= rtol |b| for every column.
+ *   maxit   budget of Krylov iterations per column (summed over restarts).
+ *   info    host array of nrhs entries (may be NULL).
+ * Synchronises the stream.  Returns RR_OK when every column met rtol,
+ * otherwise the worst per-column status.  Errors: RR_ERR_INVALID_ARG,
+ * RR_ERR_CUDA.
+ */
+rr_status randrand_solve(rr_handle* h, const double* b, int32_t nrhs, int64_t ldb,
+                         double* x, int64_t ldx, int32_t x_is_guess, double rtol,
+                         int32_t maxit, rr_solve_info* info);
+
+/*
+ * Same as randrand_solve with host buffers (pageable or pinned): b is
+ * copied to the device and x back inside the call.  b, x column-major
+ * n x nrhs float64 with leading dimensions ldb, ldx.
+ */
+rr_status randrand_solve_host(rr_handle* h, const double* b_host, int32_t nrhs,
+                              int64_t ldb, double* x_host, int64_t ldx, double rtol,
+                              int32_t maxit, rr_solve_info* info);
+
+/* Release a handle (host memory only; the workspace stays the caller's).
+ * NULL is accepted.  Never fails.  Synchronises the handle's stream. */
+void randrand_free(rr_handle* h);
+
+/*
+ * Test and inspection hooks (used by the parity tests): copy device-resident
+ * build products into caller device buffers, enqueued on the handle stream.
+ *   what = 0: Omega  (n x k row-major, float64)
+ *          1: Q      (n x k row-major, float64)
+ *          2: R      (k x k row-major, float64, upper triangular)
+ *          3: G      (k x k row-major, float64; C variant core matrix)
+ *          4: Y_mu   (n x k row-major, float64; A_mu Omega before
+ *                     orthogonalisation, kept only when opts were built
+ *                     with max_rhs >= 1 and the build is done)
+ *   dst   device buffer of float64 of the stated size.
+ * Errors: RR_ERR_INVALID_ARG, RR_ERR_CUDA.
+ */
+rr_status randrand_export(rr_handle* h, int32_t what, double* dst);
+
+/* Profile of a handle built with opts.profile = 1 (zeros otherwise).
+ * Synchronises the handle stream.  Errors: RR_ERR_INVALID_ARG, RR_ERR_CUDA. */
+rr_status randrand_profile(rr_handle* h, rr_profile* out);
+
+/* Scalars of a handle: tau, |E| estimate, lambda_max estimate. */
+rr_status randrand_scalars(const rr_handle* h, double* tau, double* normE, double* lam_max);
+
+/*
+ * Apply the preconditioner (variant C: z = P r, P = I + Q (tau G - I) Q^T,
+ * the footnote form of Sec. 7.3) or the operator B of variant R
+ * (z = (I-Pi) A_mu (I-Pi) r + tau Pi r, eq:APdef2) to m <= max_rhs columns.
+ *   r, z  device, n x m float64 column-major with leading dimension ld.
+ * Enqueued on the handle stream; does not synchronise.
+ */
+rr_status randrand_apply(rr_handle* h, const double* r, double* z, int32_t m, int64_t ld);
+
+/*
+ * Product with the shifted operator, w = (A + mu I) v, float64 accurate
+ * (the restart residual's arithmetic).  v, w device n x m float64
+ * column-major, leading dimension ld; m <= max_rhs.
+ */
+rr_status randrand_matvec(rr_handle* h, const double* v, double* w, int32_t m, int64_t ld);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RANDRAND_H */

@@ -1,0 +1,356 @@
+"""Python binding of the GB300 RandRAND-PCG library (include/randrand.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``lib/librandrand.so``.  PyTorch provides device memory and streams; the
+binding passes raw pointers through the C ABI.  The functions named
+``randrand_*`` / ``rr_*`` mirror the C entry points one to one; ``Operator``
+and ``Handle`` are small conveniences on top of them.
+
+Importing this package loads the compiled library and raises if it is missing:
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import lib_path
+
+__all__ = [
+    "RR_OK", "RR_ERR_INVALID_ARG", "RR_ERR_WORKSPACE", "RR_ERR_NOT_SPD", "RR_ERR_BREAKDOWN",
+    "RR_ERR_MAXIT", "RR_ERR_TIMEOUT", "RR_ERR_CUDA", "RR_ERR_UNSUPPORTED",
+    "RR_OP_DENSE", "RR_OP_CSR", "RR_OP_GAUSS_KERNEL", "RR_SKETCH_GAUSSIAN",
+    "RR_SKETCH_SPARSE_SIGN", "RR_PREC_FP64", "RR_PREC_FP32", "RR_PREC_MIXED", "RR_VARIANT_C",
+    "RR_VARIANT_R", "rr_operator", "rr_build_opts", "rr_solve_info", "rr_profile", "RandRandError",
+    "load_library", "Operator", "Handle",
+]
+
+RR_OK, RR_ERR_INVALID_ARG, RR_ERR_WORKSPACE, RR_ERR_NOT_SPD, RR_ERR_BREAKDOWN = 0, 1, 2, 3, 4
+RR_ERR_MAXIT, RR_ERR_TIMEOUT, RR_ERR_CUDA, RR_ERR_UNSUPPORTED = 5, 6, 7, 8
+RR_OP_DENSE, RR_OP_CSR, RR_OP_GAUSS_KERNEL = 0, 1, 2
+RR_SKETCH_GAUSSIAN, RR_SKETCH_SPARSE_SIGN = 0, 1
+RR_PREC_FP64, RR_PREC_FP32, RR_PREC_MIXED = 0, 1, 2
+RR_VARIANT_C, RR_VARIANT_R = 0, 1
+RR_ORTH_CHOLQR2, RR_ORTH_RAND_CHOLQR = 0, 1
+
+SKETCHES = {"gaussian": RR_SKETCH_GAUSSIAN, "sparse_sign": RR_SKETCH_SPARSE_SIGN}
+PRECISIONS = {"fp64": RR_PREC_FP64, "fp32": RR_PREC_FP32, "mixed": RR_PREC_MIXED}
+VARIANTS = {"C": RR_VARIANT_C, "R": RR_VARIANT_R}
+
+
+class rr_operator(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("n", ctypes.c_int64),
+        ("dense", ctypes.c_void_p), ("ld", ctypes.c_int64),
+        ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("vals", ctypes.c_void_p),
+        ("nnz", ctypes.c_int64), ("points", ctypes.c_void_p), ("dim", ctypes.c_int32),
+        ("pad_", ctypes.c_int32), ("bandwidth", ctypes.c_double),
+    ]
+
+
+class rr_build_opts(ctypes.Structure):
+    _fields_ = [
+        ("variant", ctypes.c_int32), ("precision", ctypes.c_int32), ("orth", ctypes.c_int32),
+        ("gamma", ctypes.c_int32), ("l_sk", ctypes.c_int32), ("gamma_sk", ctypes.c_int32),
+        ("power_iters", ctypes.c_int32), ("max_rhs", ctypes.c_int32), ("profile", ctypes.c_int32),
+        ("pad_", ctypes.c_int32), ("rho", ctypes.c_double), ("restart_eta", ctypes.c_double),
+    ]
+
+
+RR_PROF_SKETCH, RR_PROF_MATVEC, RR_PROF_RESIDUAL, RR_PROF_POWER, RR_PROF_COUNT = 0, 1, 2, 3, 8
+
+
+class rr_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int32 * RR_PROF_COUNT), ("ms", ctypes.c_double * RR_PROF_COUNT)]
+
+
+class rr_solve_info(ctypes.Structure):
+    _fields_ = [
+        ("inner_iters", ctypes.c_int32), ("outer_iters", ctypes.c_int32),
+        ("matvecs", ctypes.c_int32), ("status", ctypes.c_int32),
+        ("rel_residual", ctypes.c_double), ("tau", ctypes.c_double),
+        ("normE", ctypes.c_double), ("lam_max", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class RandRandError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {randrand_status_str(status)} (status {status})")
+
+
+_LIB = None
+
+# (name, restype, argtypes) of every exported entry point
+_SIGNATURES = [
+    ("rr_build_opts_default", None, [ctypes.POINTER(rr_build_opts)]),
+    ("randrand_status_str", ctypes.c_char_p, [ctypes.c_int32]),
+    ("randrand_workspace_bytes", ctypes.c_int32,
+     [ctypes.POINTER(rr_operator), ctypes.c_int32, ctypes.POINTER(rr_build_opts),
+      ctypes.POINTER(ctypes.c_size_t)]),
+    ("randrand_build", ctypes.c_int32,
+     [ctypes.POINTER(rr_operator), ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+      ctypes.c_uint64, ctypes.POINTER(rr_build_opts), ctypes.c_void_p, ctypes.c_size_t,
+      ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("randrand_solve", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+      ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+      ctypes.POINTER(rr_solve_info)]),
+    ("randrand_solve_host", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+      ctypes.c_int64, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(rr_solve_info)]),
+    ("randrand_free", None, [ctypes.c_void_p]),
+    ("randrand_export", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    ("randrand_scalars", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+      ctypes.POINTER(ctypes.c_double)]),
+    ("randrand_apply", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
+    ("randrand_profile", ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rr_profile)]),
+    ("randrand_matvec", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
+]
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load librandrand.so (built in-tree by build.py); raises if it is missing."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or lib_path()
+    if not os.path.exists(p):
+        raise RuntimeError(
+            f"{p} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(p)
+    for name, res, args in _SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+def _lib() -> ctypes.CDLL:
+    return load_library()
+
+
+# ------------------------------------------------------------ C entry points
+def rr_build_opts_default() -> rr_build_opts:
+    o = rr_build_opts()
+    _lib().rr_build_opts_default(ctypes.byref(o))
+    return o
+
+
+def randrand_status_str(s: int) -> str:
+    return _lib().randrand_status_str(int(s)).decode()
+
+
+def randrand_workspace_bytes(op: rr_operator, k: int, opts: rr_build_opts) -> int:
+    out = ctypes.c_size_t(0)
+    s = _lib().randrand_workspace_bytes(ctypes.byref(op), int(k), ctypes.byref(opts), ctypes.byref(out))
+    if s != RR_OK:
+        raise RandRandError(s, "randrand_workspace_bytes")
+    return int(out.value)
+
+
+def randrand_build(op, mu, k, sketch, seed, opts, workspace_ptr, ws_bytes, stream_ptr):
+    h = ctypes.c_void_p(None)
+    s = _lib().randrand_build(ctypes.byref(op), float(mu), int(k), int(sketch),
+                              int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(opts),
+                              ctypes.c_void_p(workspace_ptr), int(ws_bytes),
+                              ctypes.c_void_p(stream_ptr), ctypes.byref(h))
+    if s != RR_OK:
+        raise RandRandError(s, "randrand_build")
+    return h
+
+
+def randrand_solve(h, b_ptr, nrhs, ldb, x_ptr, ldx, x_is_guess, rtol, maxit):
+    infos = (rr_solve_info * nrhs)()
+    s = _lib().randrand_solve(h, ctypes.c_void_p(b_ptr), int(nrhs), int(ldb), ctypes.c_void_p(x_ptr),
+                              int(ldx), int(x_is_guess), float(rtol), int(maxit), infos)
+    if s not in (RR_OK, RR_ERR_MAXIT, RR_ERR_BREAKDOWN):
+        raise RandRandError(s, "randrand_solve")
+    return s, [i.as_dict() for i in infos]
+
+
+def randrand_solve_host(h, b_host_ptr, nrhs, ldb, x_host_ptr, ldx, rtol, maxit):
+    infos = (rr_solve_info * nrhs)()
+    s = _lib().randrand_solve_host(h, ctypes.c_void_p(b_host_ptr), int(nrhs), int(ldb),
+                                   ctypes.c_void_p(x_host_ptr), int(ldx), float(rtol), int(maxit),
+                                   infos)
+    if s not in (RR_OK, RR_ERR_MAXIT, RR_ERR_BREAKDOWN):
+        raise RandRandError(s, "randrand_solve_host")
+    return s, [i.as_dict() for i in infos]
+
+
+def randrand_free(h) -> None:
+    _lib().randrand_free(h)
+
+
+def randrand_export(h, what: int, dst_ptr: int) -> None:
+    s = _lib().randrand_export(h, int(what), ctypes.c_void_p(dst_ptr))
+    if s != RR_OK:
+        raise RandRandError(s, "randrand_export")
+
+
+def randrand_scalars(h) -> tuple[float, float, float]:
+    t, e, l = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    s = _lib().randrand_scalars(h, ctypes.byref(t), ctypes.byref(e), ctypes.byref(l))
+    if s != RR_OK:
+        raise RandRandError(s, "randrand_scalars")
+    return t.value, e.value, l.value
+
+
+def randrand_apply(h, r_ptr, z_ptr, m, ld) -> None:
+    s = _lib().randrand_apply(h, ctypes.c_void_p(r_ptr), ctypes.c_void_p(z_ptr), int(m), int(ld))
+    if s != RR_OK:
+        raise RandRandError(s, "randrand_apply")
+
+
+def randrand_profile(h) -> dict:
+    p = rr_profile()
+    s = _lib().randrand_profile(h, ctypes.byref(p))
+    if s != RR_OK:
+        raise RandRandError(s, "randrand_profile")
+    names = ("sketch", "matvec", "residual", "power")
+    return {nm: (int(p.launches[i]), float(p.ms[i])) for i, nm in enumerate(names)}
+
+
+def randrand_matvec(h, v_ptr, w_ptr, m, ld) -> None:
+    s = _lib().randrand_matvec(h, ctypes.c_void_p(v_ptr), ctypes.c_void_p(w_ptr), int(m), int(ld))
+    if s != RR_OK:
+        raise RandRandError(s, "randrand_matvec")
+
+
+# ------------------------------------------------------------- conveniences
+class Operator:
+    """Device-resident operator description.  Holds references to the torch
+    tensors so that the borrowed pointers stay valid."""
+
+    def __init__(self, op: rr_operator, keep: list):
+        self.c = op
+        self._keep = keep
+        self.n = int(op.n)
+
+    @staticmethod
+    def dense(A) -> "Operator":
+        import torch
+        assert A.is_cuda and A.dim() == 2 and A.shape[0] == A.shape[1] and A.is_contiguous()
+        dtype = {torch.float64: 0, torch.float32: 1}[A.dtype]
+        op = rr_operator(kind=RR_OP_DENSE, dtype=dtype, n=A.shape[0], dense=A.data_ptr(), ld=A.shape[1])
+        return Operator(op, [A])
+
+    @staticmethod
+    def csr(rowptr, colidx, vals) -> "Operator":
+        import torch
+        assert rowptr.dtype == torch.int32 and colidx.dtype == torch.int32
+        dtype = {torch.float64: 0, torch.float32: 1}[vals.dtype]
+        op = rr_operator(kind=RR_OP_CSR, dtype=dtype, n=rowptr.numel() - 1, rowptr=rowptr.data_ptr(),
+                         colidx=colidx.data_ptr(), vals=vals.data_ptr(), nnz=colidx.numel())
+        return Operator(op, [rowptr, colidx, vals])
+
+    @staticmethod
+    def gauss_kernel(points, bandwidth: float = 1.0) -> "Operator":
+        import torch
+        assert points.is_cuda and points.dtype == torch.float32 and points.is_contiguous()
+        op = rr_operator(kind=RR_OP_GAUSS_KERNEL, dtype=1, n=points.shape[0], points=points.data_ptr(),
+                         dim=points.shape[1], bandwidth=float(bandwidth))
+        return Operator(op, [points])
+
+
+class Handle:
+    """A built RandRAND preconditioner (randrand_build) and its workspace."""
+
+    def __init__(self, op: Operator, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
+                 variant: str = "C", precision: str = "fp64", max_rhs: int = 1,
+                 power_iters: int = 20, rho: float = 0.0, restart_eta: float = 1e-2,
+                 gamma: int = 8, profile: bool = False, stream=None):
+        import torch
+        self.op = op
+        self.n = op.n
+        self.k = k
+        o = rr_build_opts_default()
+        o.variant = VARIANTS[variant]
+        o.precision = PRECISIONS[precision]
+        o.max_rhs = max_rhs
+        o.power_iters = power_iters
+        o.rho = rho
+        o.restart_eta = restart_eta
+        o.gamma = gamma
+        o.profile = 1 if profile else 0
+        self.opts = o
+        self.ws_bytes = randrand_workspace_bytes(op.c, k, o)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = randrand_build(op.c, mu, k, SKETCHES[sketch], seed, o, self.ws.data_ptr(),
+                                self.ws_bytes, self.stream.cuda_stream)
+
+    def solve(self, b, rtol: float, maxit: int = 20000, x0=None):
+        """b: (n,) or (n, m) float64 CUDA tensor.  Returns (x, status, infos)."""
+        import torch
+        one = b.dim() == 1
+        B = b.reshape(self.n, -1)
+        m = B.shape[1]
+        Bc = B.t().contiguous()                      # column-major n x m
+        Xc = torch.zeros_like(Bc) if x0 is None else x0.reshape(self.n, -1).t().contiguous()
+        s, infos = randrand_solve(self.h, Bc.data_ptr(), m, self.n, Xc.data_ptr(), self.n,
+                                  0 if x0 is None else 1, rtol, maxit)
+        X = Xc.t()
+        return (X[:, 0] if one else X), s, infos
+
+    def solve_host(self, b_host, x_host, rtol: float, maxit: int = 20000):
+        """b_host, x_host: (m, n) C-contiguous float64 host tensors (= column-major n x m)."""
+        m = b_host.shape[0]
+        return randrand_solve_host(self.h, b_host.data_ptr(), m, self.n, x_host.data_ptr(), self.n,
+                                   rtol, maxit)
+
+    def export(self, what: str):
+        import torch
+        code = {"omega": 0, "Q": 1, "R": 2, "G": 3}[what]
+        shape = (self.n, self.k) if code < 2 else (self.k, self.k)
+        out = torch.empty(shape, dtype=torch.float64, device="cuda")
+        randrand_export(self.h, code, out.data_ptr())
+        self.stream.synchronize()
+        return out
+
+    def scalars(self):
+        return randrand_scalars(self.h)
+
+    def profile(self) -> dict:
+        return randrand_profile(self.h)
+
+    def apply(self, r):
+        import torch
+        R = r.reshape(self.n, -1)
+        Rc = R.t().contiguous()
+        Zc = torch.empty_like(Rc)
+        randrand_apply(self.h, Rc.data_ptr(), Zc.data_ptr(), Rc.shape[0], self.n)
+        self.stream.synchronize()
+        return Zc.t().reshape(r.shape)
+
+    def matvec(self, v):
+        import torch
+        V = v.reshape(self.n, -1)
+        Vc = V.t().contiguous()
+        Wc = torch.empty_like(Vc)
+        randrand_matvec(self.h, Vc.data_ptr(), Wc.data_ptr(), Vc.shape[0], self.n)
+        self.stream.synchronize()
+        return Wc.t().reshape(v.shape)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            randrand_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+load_library()

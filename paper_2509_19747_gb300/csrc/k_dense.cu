@@ -1,0 +1,491 @@
+// Dense building blocks of the basis construction (Sec. 4.1: A_mu Omega = Q R,
+// G = R^-T (Omega^T A_mu Omega) R^-1): tiled GEMM, split-row Gram products
+// with float64 accumulation, and the k x k float64 Cholesky / triangular
+// inverse used by Cholesky QR (Alg. 2 as the first pass of CholeskyQR2).
+//
+// GB300 note: float64 runs at ~1/64 of the float32 rate on this part, so the
+// k x k float64 kernels spread their work over many CTAs (column-parallel
+// triangular inverse, tile-parallel trailing updates) instead of one CTA.
+#include <cmath>
+
+#include "rr_common.cuh"
+
+namespace rr {
+
+// ======================================================================
+// Tiled GEMM  C = alpha A B + beta D   (row-major; D may alias nothing or B)
+// Optional triangular skipping: a_upper (A_ip = 0 for p < i) and b_upper
+// (B_pj = 0 for p > j) restrict the K range of each tile.
+// ======================================================================
+template <typename T, int BM>
+__global__ void __launch_bounds__(256) k_gemm_nn(int64_t M, int64_t N, int64_t K, T alpha,
+                                                 const T* __restrict__ A, int64_t lda,
+                                                 const T* __restrict__ B, int64_t ldb, T beta,
+                                                 const T* __restrict__ D, int64_t ldd,
+                                                 T* __restrict__ C, int64_t ldc, int a_upper,
+                                                 int b_upper) {
+  constexpr int BK = 16;
+  constexpr int TM = BM / 16;  // outputs per thread per dimension
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BM + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BM;
+  int64_t kbeg = 0, kend = K;
+  if (a_upper) kbeg = m0;                                   // A_ip = 0 for p < i >= m0
+  if (b_upper) kend = (n0 + BM < K) ? (n0 + BM) : K;        // B_pj = 0 for p > j
+  T acc[TM][TM];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TM; ++b) acc[a][b] = (T)0;
+
+  for (int64_t k0 = (kbeg / BK) * BK; k0 < kend; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += 256) {
+      const int r = e / BK, c = e % BK;            // A tile: BM rows x BK cols
+      const int64_t gi = m0 + r, gk = k0 + c;
+      As[c][r] = (gi < M && gk < K && gk >= kbeg && gk < kend) ? A[gi * lda + gk] : (T)0;
+      const int r2 = e / BM, c2 = e % BM;          // B tile: BK rows x BM cols
+      const int64_t gk2 = k0 + r2, gj = n0 + c2;
+      Bs[r2][c2] = (gk2 < K && gj < N && gk2 >= kbeg && gk2 < kend) ? B[gk2 * ldb + gj] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], b[TM];
+#pragma unroll
+      for (int t = 0; t < TM; ++t) {
+        a[t] = As[kk][ty * TM + t];
+        b[t] = Bs[kk][tx * TM + t];
+      }
+#pragma unroll
+      for (int x = 0; x < TM; ++x)
+#pragma unroll
+        for (int y = 0; y < TM; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < TM; ++x) {
+    const int64_t gi = m0 + ty * TM + x;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int y = 0; y < TM; ++y) {
+      const int64_t gj = n0 + tx * TM + y;
+      if (gj >= N) continue;
+      T v = alpha * acc[x][y];
+      if (D) v = fma(beta, D[gi * ldd + gj], v);
+      C[gi * ldc + gj] = v;
+    }
+  }
+}
+
+template <typename T>
+static void gemm_launch(int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t lda,
+                        const T* B, int64_t ldb, double beta, const T* D, int64_t ldd, T* C,
+                        int64_t ldc, int a_upper, int b_upper, cudaStream_t st) {
+  const int64_t tiles64 = cdiv(M, 64) * cdiv(N, 64);
+  if (tiles64 >= 2 * 152) {
+    dim3 grid((unsigned)cdiv(N, 64), (unsigned)cdiv(M, 64));
+    k_gemm_nn<T, 64><<<grid, 256, 0, st>>>(M, N, K, (T)alpha, A, lda, B, ldb, (T)beta, D, ldd,
+                                           C, ldc, a_upper, b_upper);
+  } else {
+    dim3 grid((unsigned)cdiv(N, 32), (unsigned)cdiv(M, 32));
+    k_gemm_nn<T, 32><<<grid, 256, 0, st>>>(M, N, K, (T)alpha, A, lda, B, ldb, (T)beta, D, ldd,
+                                           C, ldc, a_upper, b_upper);
+  }
+}
+
+template <typename T>
+void gemm_nn(int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t lda,
+             const T* B, int64_t ldb, double beta, const T* D, int64_t ldd, T* C,
+             int64_t ldc, cudaStream_t st) {
+  gemm_launch<T>(M, N, K, alpha, A, lda, B, ldb, beta, D, ldd, C, ldc, 0, 0, st);
+}
+
+// upper-triangular x upper-triangular (k x k float64), C = A B
+void gemm_upper_upper(int k, const double* A, const double* B, double* C, cudaStream_t st) {
+  gemm_launch<double>(k, k, k, 1.0, A, k, B, k, 0.0, nullptr, 0, C, k, 1, 1, st);
+}
+
+// ======================================================================
+// Split-row Gram  part[s] = A[rows_s]^T B[rows_s]  (float64 partials)
+// Float inputs: products and sums in float over blocks of kFold rows, then
+// folded into float64 accumulators.
+// ======================================================================
+template <typename T>
+struct GramAcc;
+template <>
+struct GramAcc<double> {
+  static constexpr int kFold = 1 << 30;
+};
+template <>
+struct GramAcc<float> {
+  static constexpr int kFold = 256;
+};
+
+template <typename T, int BM>
+__global__ void __launch_bounds__(256) k_gram_partial(const T* __restrict__ A, int64_t lda,
+                                                      const T* __restrict__ B, int64_t ldb,
+                                                      int64_t nrows, int k1, int k2,
+                                                      int symmetric, int64_t rows_per_split,
+                                                      int tri_limit, double* __restrict__ part) {
+  constexpr int BK = 16;
+  constexpr int TM = BM / 16;
+  const int ti = blockIdx.y, tj = blockIdx.x, s = blockIdx.z;
+  if (symmetric && ti > tj) return;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BM + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int i0 = ti * BM, j0 = tj * BM;
+  int64_t r0 = (int64_t)s * rows_per_split;
+  int64_t r1 = r0 + rows_per_split;
+  if (r1 > nrows) r1 = nrows;
+  if (tri_limit) {  // A and B upper triangular (k x k): rows r <= min(i, j) only
+    const int64_t lim = (int64_t)((i0 + BM < j0 + BM) ? i0 + BM : j0 + BM);
+    if (r1 > lim) r1 = lim;
+  }
+  double accd[TM][TM];
+  T acc[TM][TM];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TM; ++b) {
+      accd[a][b] = 0.0;
+      acc[a][b] = (T)0;
+    }
+  int folded = 0;
+  for (int64_t rb = r0; rb < r1; rb += BK) {
+    for (int e = tid; e < BM * BK; e += 256) {
+      const int r = e / BM, c = e % BM;
+      const int64_t gr = rb + r;
+      const bool okr = gr < r1;
+      As[r][c] = (okr && i0 + c < k1) ? A[gr * lda + i0 + c] : (T)0;
+      Bs[r][c] = (okr && j0 + c < k2) ? B[gr * ldb + j0 + c] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], b[TM];
+#pragma unroll
+      for (int t = 0; t < TM; ++t) {
+        a[t] = As[kk][ty * TM + t];
+        b[t] = Bs[kk][tx * TM + t];
+      }
+#pragma unroll
+      for (int x = 0; x < TM; ++x)
+#pragma unroll
+        for (int y = 0; y < TM; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+    }
+    __syncthreads();
+    folded += BK;
+    if (folded >= GramAcc<T>::kFold) {
+#pragma unroll
+      for (int x = 0; x < TM; ++x)
+#pragma unroll
+        for (int y = 0; y < TM; ++y) {
+          accd[x][y] += (double)acc[x][y];
+          acc[x][y] = (T)0;
+        }
+      folded = 0;
+    }
+  }
+  double* out = part + (int64_t)s * k1 * k2;
+#pragma unroll
+  for (int x = 0; x < TM; ++x) {
+    const int gi = i0 + ty * TM + x;
+    if (gi >= k1) continue;
+#pragma unroll
+    for (int y = 0; y < TM; ++y) {
+      const int gj = j0 + tx * TM + y;
+      if (gj >= k2) continue;
+      out[(int64_t)gi * k2 + gj] = accd[x][y] + (double)acc[x][y];
+    }
+  }
+}
+
+int gram_nsplit(int64_t nrows, int k1, int k2) {
+  const int64_t tiles = cdiv(k1, 32) * cdiv(k2, 32);
+  int64_t ns = cdiv(4 * 152, tiles);
+  const int64_t maxs = cdiv(nrows, 64);  // at least 64 rows per split
+  if (ns > maxs) ns = maxs;
+  if (ns < 1) ns = 1;
+  if (ns > 64) ns = 64;
+  return (int)ns;
+}
+
+template <typename T>
+static void gram_launch(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t nrows, int k1,
+                        int k2, bool symmetric, int nsplit, int tri_limit, double* part,
+                        cudaStream_t st) {
+  const int64_t rps = cdiv(cdiv(nrows, nsplit), 16) * 16;
+  dim3 grid((unsigned)cdiv(k2, 32), (unsigned)cdiv(k1, 32), (unsigned)nsplit);
+  k_gram_partial<T, 32><<<grid, 256, 0, st>>>(A, lda, B, ldb, nrows, k1, k2, symmetric ? 1 : 0,
+                                              rps, tri_limit, part);
+}
+
+template <typename T>
+void gram_partial(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t nrows, int k1,
+                  int k2, bool symmetric, int nsplit, double* part, cudaStream_t st) {
+  gram_launch<T>(A, lda, B, ldb, nrows, k1, k2, symmetric, nsplit, 0, part, st);
+}
+
+__global__ void k_reduce_gram(const double* __restrict__ part, int nsplit, int k1, int k2,
+                              int symmetric, int symmetrize, double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)k1 * k2) return;
+  const int i = (int)(e / k2), j = (int)(e % k2);
+  const int64_t src = (symmetric && i > j) ? ((int64_t)j * k2 + i) : e;
+  double acc = 0.0;
+  for (int s = 0; s < nsplit; ++s) acc += part[(int64_t)s * k1 * k2 + src];
+  if (symmetrize) {
+    const int64_t tr = (int64_t)j * k2 + i;
+    double acc2 = 0.0;
+    for (int s = 0; s < nsplit; ++s) acc2 += part[(int64_t)s * k1 * k2 + tr];
+    acc = 0.5 * (acc + acc2);
+  }
+  out[e] = acc;
+}
+
+void reduce_gram(const double* part, int nsplit, int k1, int k2, bool symmetric, bool symmetrize,
+                 double* out, cudaStream_t st) {
+  const int64_t total = (int64_t)k1 * k2;
+  k_reduce_gram<<<(unsigned)cdiv(total, 256), 256, 0, st>>>(part, nsplit, k1, k2,
+                                                             symmetric ? 1 : 0,
+                                                             symmetrize ? 1 : 0, out);
+}
+
+void gram_upper(const double* Tm, int k, double* part, double* out, cudaStream_t st) {
+  gram_launch<double>(Tm, k, Tm, k, k, k, k, true, 1, 1, part, st);
+  reduce_gram(part, 1, k, k, true, false, out, st);
+}
+
+// ======================================================================
+// Blocked upper Cholesky  A = R^T R  (k x k float64, row-major, in place)
+// ======================================================================
+constexpr int kNb = 32;
+
+// Factor the diagonal block A[j0:j0+jb, j0:j0+jb] and write its inverse to
+// winv (jb x jb, row-major, upper).
+__global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int k, int j0,
+                                                    double* __restrict__ winv,
+                                                    int* __restrict__ status) {
+  __shared__ double S[kNb][kNb + 1];
+  __shared__ double Wi[kNb][kNb + 1];
+  const int jb = (k - j0 < kNb) ? (k - j0) : kNb;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < jb * jb; e += blockDim.x) {
+    const int r = e / jb, c = e % jb;
+    S[r][c] = A[(int64_t)(j0 + r) * k + j0 + c];
+  }
+  __syncthreads();
+  for (int p = 0; p < jb; ++p) {
+    // pivot
+    const double app = S[p][p];
+    const bool bad = !(app > 0.0) || !isfinite(app);
+    const double d = bad ? 1.0 : sqrt(app);
+    __syncthreads();
+    if (tid == 0) {
+      if (bad) atomicCAS(status, 0, j0 + p + 1);
+      S[p][p] = d;
+    }
+    for (int q = p + 1 + tid; q < jb; q += blockDim.x) S[p][q] /= d;
+    __syncthreads();
+    // trailing update of the upper part: S[i][q] -= S[p][i] S[p][q], p < i <= q
+    const int rem = jb - p - 1;
+    for (int e = tid; e < rem * rem; e += blockDim.x) {
+      const int i = p + 1 + e / rem, q = p + 1 + e % rem;
+      if (q >= i) S[i][q] -= S[p][i] * S[p][q];
+    }
+    __syncthreads();
+  }
+  // inverse of the upper factor: column-oriented back substitution, one
+  // thread per column c of Wi (jb <= 32)
+  if (tid < jb) {
+    const int c = tid;
+    for (int r = 0; r < jb; ++r) Wi[r][c] = 0.0;
+    for (int r = c; r >= 0; --r) {
+      double s = (r == c) ? 1.0 : 0.0;
+      for (int q = r + 1; q <= c; ++q) s -= S[r][q] * Wi[q][c];
+      Wi[r][c] = s / S[r][r];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < jb * jb; e += blockDim.x) {
+    const int r = e / jb, c = e % jb;
+    A[(int64_t)(j0 + r) * k + j0 + c] = (c >= r) ? S[r][c] : 0.0;
+    winv[r * kNb + c] = (c >= r) ? Wi[r][c] : 0.0;
+  }
+}
+
+// R12 = R11^-T A12 for the panel rows j0..j0+jb, columns >= j0+jb; one CTA
+// per 32 columns.  (R11^-T)[p][q] = winv[q][p], nonzero for q <= p.
+__global__ void __launch_bounds__(256) k_potrf_trsm(double* __restrict__ A, int k, int j0,
+                                                    const double* __restrict__ winv) {
+  __shared__ double W[kNb][kNb + 1];
+  __shared__ double X[kNb][33];
+  const int jb = (k - j0 < kNb) ? (k - j0) : kNb;
+  const int c0 = j0 + jb + blockIdx.x * 32;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kNb * kNb; e += blockDim.x) W[e / kNb][e % kNb] = winv[e];
+  for (int e = tid; e < jb * 32; e += blockDim.x) {
+    const int r = e / 32, c = e % 32;
+    X[r][c] = (c0 + c < k) ? A[(int64_t)(j0 + r) * k + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < jb * 32; e += blockDim.x) {
+    const int p = e / 32, c = e % 32;
+    double s = 0.0;
+    for (int q = 0; q <= p; ++q) s += W[q][p] * X[q][c];
+    if (c0 + c < k) A[(int64_t)(j0 + p) * k + c0 + c] = s;
+  }
+}
+
+// A22 -= R12^T R12 on the upper part (rows/cols >= j1 = j0 + jb), 32 x 32 tiles
+__global__ void __launch_bounds__(256) k_potrf_syrk(double* __restrict__ A, int k, int j0) {
+  const int jb = (k - j0 < kNb) ? (k - j0) : kNb;
+  const int j1 = j0 + jb;
+  const int ti = blockIdx.y, tj = blockIdx.x;
+  if (ti > tj) return;
+  __shared__ double Pi[kNb][33];
+  __shared__ double Pj[kNb][33];
+  const int i0 = j1 + ti * 32, jj0 = j1 + tj * 32;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < jb * 32; e += blockDim.x) {
+    const int p = e / 32, c = e % 32;
+    Pi[p][c] = (i0 + c < k) ? A[(int64_t)(j0 + p) * k + i0 + c] : 0.0;
+    Pj[p][c] = (jj0 + c < k) ? A[(int64_t)(j0 + p) * k + jj0 + c] : 0.0;
+  }
+  __syncthreads();
+  const int tx = tid % 16, ty = tid / 16;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int p = 0; p < jb; ++p) {
+    const double a0 = Pi[p][ty * 2], a1 = Pi[p][ty * 2 + 1];
+    const double b0 = Pj[p][tx * 2], b1 = Pj[p][tx * 2 + 1];
+    acc[0][0] = fma(a0, b0, acc[0][0]);
+    acc[0][1] = fma(a0, b1, acc[0][1]);
+    acc[1][0] = fma(a1, b0, acc[1][0]);
+    acc[1][1] = fma(a1, b1, acc[1][1]);
+  }
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int y = 0; y < 2; ++y) {
+      const int gi = i0 + ty * 2 + x, gj = jj0 + tx * 2 + y;
+      if (gi < k && gj < k && gj >= gi) A[(int64_t)gi * k + gj] -= acc[x][y];
+    }
+}
+
+__global__ void k_zero_lower(double* A, int k) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)k * k) return;
+  const int i = (int)(e / k), j = (int)(e % k);
+  if (j < i) A[e] = 0.0;
+}
+
+void potrf_upper(double* A, int k, double* work, int* status, cudaStream_t st) {
+  for (int j0 = 0; j0 < k; j0 += kNb) {
+    const int jb = (k - j0 < kNb) ? (k - j0) : kNb;
+    k_potrf_diag<<<1, 256, 0, st>>>(A, k, j0, work, status);
+    const int rest = k - j0 - jb;
+    if (rest <= 0) break;
+    k_potrf_trsm<<<(unsigned)cdiv(rest, 32), 256, 0, st>>>(A, k, j0, work);
+    const unsigned t = (unsigned)cdiv(rest, 32);
+    k_potrf_syrk<<<dim3(t, t), 256, 0, st>>>(A, k, j0);
+  }
+  k_zero_lower<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(A, k);
+}
+
+// ======================================================================
+// Upper-triangular inverse, column-parallel back substitution.
+// Rt = R^T (row p of Rt = column p of R, contiguous).
+// ======================================================================
+__global__ void __launch_bounds__(128) k_trtri_cols(const double* __restrict__ Rt, int k,
+                                                    double* __restrict__ Rinv) {
+  extern __shared__ double b[];  // k entries
+  const int j = blockIdx.x;      // column of Rinv
+  const int tid = threadIdx.x;
+  for (int i = tid; i < k; i += blockDim.x) b[i] = (i == j) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int p = j; p >= 0; --p) {
+    const double xp = b[p] / Rt[(int64_t)p * k + p];
+    __syncthreads();
+    if (tid == 0) b[p] = xp;
+    // b[i] -= R[i][p] x_p for i < p; R[i][p] = Rt[p][i]
+    const double* rowp = Rt + (int64_t)p * k;
+    for (int i = tid; i < p; i += blockDim.x) b[i] -= rowp[i] * xp;
+    __syncthreads();
+  }
+  for (int i = tid; i < k; i += blockDim.x) Rinv[(int64_t)i * k + j] = (i <= j) ? b[i] : 0.0;
+}
+
+__global__ void k_transpose(const double* __restrict__ in, double* __restrict__ out, int k) {
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int r = by + y, c = bx + threadIdx.x;
+    if (r < k && c < k) tile[y][threadIdx.x] = in[(int64_t)r * k + c];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int r = bx + y, c = by + threadIdx.x;
+    if (r < k && c < k) out[(int64_t)r * k + c] = tile[threadIdx.x][y];
+  }
+}
+
+void transpose_kxk(const double* in, double* out, int k, cudaStream_t st) {
+  dim3 grid((unsigned)cdiv(k, 32), (unsigned)cdiv(k, 32));
+  k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, out, k);
+}
+
+void trtri_upper_with(const double* R, int k, double* Rt, double* Rinv, cudaStream_t st) {
+  transpose_kxk(R, Rt, k, st);
+  k_trtri_cols<<<(unsigned)k, 128, (size_t)k * sizeof(double), st>>>(Rt, k, Rinv);
+}
+
+// ======================================================================
+// Small helpers
+// ======================================================================
+__global__ void k_add_diag(double* A, int k, double alpha) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) A[(int64_t)i * k + i] += alpha;
+}
+void add_diag(double* A, int k, double alpha, cudaStream_t st) {
+  k_add_diag<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(A, k, alpha);
+}
+
+__global__ void k_form_H(const double* __restrict__ G, double tau, double* __restrict__ H, int k) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)k * k) return;
+  const int i = (int)(e / k), j = (int)(e % k);
+  H[e] = tau * G[e] - (i == j ? 1.0 : 0.0);
+}
+void form_H(const double* G, double tau, double* H, int k, cudaStream_t st) {
+  k_form_H<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(G, tau, H, k);
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_convert(const Tin* __restrict__ in, Tout* __restrict__ out, int64_t count) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) out[e] = (Tout)in[e];
+}
+template <typename Tin, typename Tout>
+void convert(const Tin* in, Tout* out, int64_t count, cudaStream_t st) {
+  k_convert<Tin, Tout><<<(unsigned)cdiv(count, 256), 256, 0, st>>>(in, out, count);
+}
+
+template void gemm_nn<float>(int64_t, int64_t, int64_t, double, const float*, int64_t,
+                             const float*, int64_t, double, const float*, int64_t, float*,
+                             int64_t, cudaStream_t);
+template void gemm_nn<double>(int64_t, int64_t, int64_t, double, const double*, int64_t,
+                              const double*, int64_t, double, const double*, int64_t, double*,
+                              int64_t, cudaStream_t);
+template void gram_partial<float>(const float*, int64_t, const float*, int64_t, int64_t, int, int,
+                                  bool, int, double*, cudaStream_t);
+template void gram_partial<double>(const double*, int64_t, const double*, int64_t, int64_t, int,
+                                   int, bool, int, double*, cudaStream_t);
+template void convert<double, float>(const double*, float*, int64_t, cudaStream_t);
+template void convert<float, double>(const float*, double*, int64_t, cudaStream_t);
+template void convert<double, double>(const double*, double*, int64_t, cudaStream_t);
+
+}  // namespace rr

@@ -1,0 +1,626 @@
+// Krylov iteration kernels: the deflation projector pieces (t = Q^T v over
+// row slabs, out = a v + Q t), the float64 scalar reductions (alpha, beta,
+// residual norms) and the fused vector updates of PCG (Alg. 7 with
+// P = I + Q (tau G - I) Q^T, the footnote form of Sec. 7.3) and of CG on the
+// R-RandRAND operator B = (I - Pi) A_mu (I - Pi) + tau Pi (eq:APdef2).
+//
+// Cross-block reductions use the "last block finishes" pattern: every CTA
+// writes its partial, fences, and takes a ticket; the CTA that draws the
+// last ticket sums the partials in block order (deterministic) and updates
+// the per-column Krylov scalars.  No CTA ever waits for another.
+#include <cmath>
+
+#include "rr_common.cuh"
+#include "rr_krylov.cuh"
+
+namespace rr {
+
+// ------------------------------------------------------------- helpers
+__device__ __forceinline__ bool last_block(unsigned* counter) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned prev = atomicAdd(counter, 1u);
+    s_last = (prev == total - 1);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+  return s_last;
+}
+
+// Block-wide sum of per-thread values v[0..mp) into sh[0..mp) (thread 0 holds them).
+template <int NT>
+__device__ __forceinline__ void block_sum_cols(double* v, int mp, double* sh /*[NT/32][8]*/) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (c >= mp) break;
+    double x = v[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[wid * 8 + c] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < mp; ++c) {
+      double s = 0.0;
+      for (int w = 0; w < NT / 32; ++w) s += sh[w * 8 + c];
+      v[c] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// sum over blocks of part[b][c] in block order, by thread 0 of the last block
+__device__ __forceinline__ double sum_parts(const double* part, int nb, int mp, int c) {
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(int64_t)b * mp + c];
+  return s;
+}
+
+__device__ __forceinline__ bool any_active(const ColState* cs, int mp) {
+  bool a = false;
+  for (int c = 0; c < mp; ++c) a |= (cs[c].active != 0);
+  return a;
+}
+
+int qt_rows_per_slab(int64_t n) {
+  int64_t rps = cdiv(n, kSmSlabs);
+  if (rps < 16) rps = 16;
+  if (rps > 512) rps = 512;
+  return (int)rps;
+}
+int qt_nslab(int64_t n) { return (int)cdiv(n, qt_rows_per_slab(n)); }
+
+constexpr int kNT = 256;
+static unsigned grid_rows(int64_t n, int rows_per_thread_block) {
+  int64_t b = cdiv(n, rows_per_thread_block);
+  if (b > 8 * 152) b = 8 * 152;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+// ============================================================ Q^T V slabs
+// part[slab][j][c] = sum_{i in slab} Q[i][j] V[i][c]
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_qt_partial(const T* __restrict__ Q, const T* __restrict__ V,
+                                                    int64_t n, int k, int mp, int rps,
+                                                    double* __restrict__ part,
+                                                    const ColState* __restrict__ cs_gate) {
+  if (cs_gate && !any_active(cs_gate, mp)) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* Vs = reinterpret_cast<T*>(smem_raw);  // rps x mp
+  const int64_t r0 = (int64_t)blockIdx.x * rps;
+  const int cnt = (int)((n - r0 < rps) ? (n - r0) : rps);
+  for (int e = threadIdx.x; e < cnt * mp; e += kNT) Vs[e] = V[r0 * mp + e];
+  __syncthreads();
+  double* out = part + (int64_t)blockIdx.x * k * mp;
+  for (int j = threadIdx.x; j < k; j += kNT) {
+    T acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = (T)0;
+    const T* q = Q + r0 * k + j;
+    for (int i = 0; i < cnt; ++i) {
+      const T qij = q[(int64_t)i * k];
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (c < mp) acc[c] = fma(qij, Vs[i * mp + c], acc[c]);
+    }
+    for (int c = 0; c < mp; ++c) out[(int64_t)j * mp + c] = (double)acc[c];
+  }
+}
+
+template <typename T>
+void qt_partial(const T* Q, const T* V, int64_t n, int k, int mp, int nslab, double* part,
+                cudaStream_t st) {
+  const int rps = qt_rows_per_slab(n);
+  k_qt_partial<T><<<(unsigned)nslab, kNT, (size_t)rps * mp * sizeof(T), st>>>(Q, V, n, k, mp, rps,
+                                                                             part, nullptr);
+}
+
+template <typename T>
+void qt_partial_gated(const T* Q, const T* V, int64_t n, int k, int mp, double* part,
+                      const ColState* cs, cudaStream_t st) {
+  const int rps = qt_rows_per_slab(n);
+  const int nslab = qt_nslab(n);
+  k_qt_partial<T><<<(unsigned)nslab, kNT, (size_t)rps * mp * sizeof(T), st>>>(Q, V, n, k, mp, rps,
+                                                                             part, cs);
+}
+
+__global__ void k_reduce_slabs(const double* __restrict__ part, int nslab, int len,
+                               double* __restrict__ out, const ColState* __restrict__ cs_gate,
+                               int mp) {
+  if (cs_gate && !any_active(cs_gate, mp)) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= len) return;
+  double s = 0.0;
+  for (int b = 0; b < nslab; ++b) s += part[(int64_t)b * len + e];
+  out[e] = s;
+}
+
+void reduce_slabs(const double* part, int nslab, int len, double* out, cudaStream_t st) {
+  k_reduce_slabs<<<(unsigned)cdiv(len, 256), 256, 0, st>>>(part, nslab, len, out, nullptr, 1);
+}
+void reduce_slabs_gated(const double* part, int nslab, int len, double* out, const ColState* cs,
+                        int mp, cudaStream_t st) {
+  k_reduce_slabs<<<(unsigned)cdiv(len, 256), 256, 0, st>>>(part, nslab, len, out, cs, mp);
+}
+
+// ============================================== small k x k column transforms
+// out[:,c] = ca[c] t[:,c] + cb[c] (M t)[:,c]     (M k x k float64, may be null)
+__global__ void k_kxk_apply(const double* __restrict__ M, const double* __restrict__ t, int k,
+                            int mp, Coefs8 ca, Coefs8 cb, double* __restrict__ out) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= k) return;
+  double acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+  if (M) {
+    const double* m = M + (int64_t)row * k;
+    for (int j = lane; j < k; j += 32) {
+      const double mj = m[j];
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (c < mp) acc[c] = fma(mj, t[(int64_t)j * mp + c], acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (c >= mp) break;
+    double v = acc[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) out[(int64_t)row * mp + c] = ca.v[c] * t[(int64_t)row * mp + c] + cb.v[c] * v;
+  }
+}
+
+void kxk_apply(const double* M, const double* t, int k, int mp, Coefs8 ca, Coefs8 cb,
+               double* out, cudaStream_t st) {
+  k_kxk_apply<<<(unsigned)cdiv(k, 8), 256, 0, st>>>(M, t, k, mp, ca, cb, out);
+}
+
+// ======================================================= out = a X + Q t
+// One warp per row; t (k x mp) staged in shared memory in the working type.
+// Optional fused dot: dot[c] = sum_i D[i][c] out[i][c] -> last block writes
+// per-column results according to `mode`.
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_qcomb(const T* __restrict__ Q, int64_t n, int k, int mp,
+                                               const double* __restrict__ t, Coefs8 a,
+                                               const T* __restrict__ X, T* __restrict__ out,
+                                               const T* __restrict__ D, int mode,
+                                               double* __restrict__ part,
+                                               unsigned* __restrict__ counter,
+                                               ColState* __restrict__ cs, int gated) {
+  if (gated && !any_active(cs, mp)) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* ts = reinterpret_cast<T*>(smem_raw);  // k x mp
+  __shared__ double red[kNT / 32 * 8];
+  for (int e = threadIdx.x; e < k * mp; e += kNT) ts[e] = (T)t[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (kNT / 32);
+  double dacc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) dacc[c] = 0.0;
+  for (int64_t row = (int64_t)blockIdx.x * (kNT / 32) + (threadIdx.x >> 5); row < n;
+       row += warps_total) {
+    T acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = (T)0;
+    const T* q = Q + row * k;
+    for (int j = lane; j < k; j += 32) {
+      const T qj = q[j];
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (c < mp) acc[c] = fma(qj, ts[j * mp + c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c >= mp) break;
+      T v = acc[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      acc[c] = v;
+    }
+    if (lane < mp) {
+      T v = (T)0;
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (c == lane) v = acc[c];
+      const int64_t idx = row * mp + lane;
+      const T o = (X ? (T)a.v[lane] * X[idx] : (T)0) + v;
+      out[idx] = o;
+      if (D) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c == lane) dacc[c] += (double)D[idx] * (double)o;
+      }
+    }
+  }
+  if (mode == kModeNone) return;
+  // lanes hold their own column's partial in dacc[lane]; gather to warp lane 0
+  double v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = dacc[c];
+  block_sum_cols<kNT>(v, mp, red);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < mp; ++c) part[(int64_t)blockIdx.x * mp + c] = v[c];
+  if (!last_block(counter)) return;
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < mp; ++c) {
+      const double s = sum_parts(part, gridDim.x, mp, c);
+      ColState& st = cs[c];
+      if (mode == kModeRhoInit) {          // rho = r^T z (C) / r^T r (R)
+        st.rho = s;
+        if (st.active && !(s > 0.0 && isfinite(s))) {
+          if (s == 0.0) st.active = 0;      // r = 0 already
+          else { st.status = RR_ERR_BREAKDOWN; st.active = 0; }
+        }
+      } else if (mode == kModeBeta) {      // beta = rho_new / rho, rho = rho_new
+        if (st.active) {
+          if (!(s > 0.0 && isfinite(s))) { st.status = RR_ERR_BREAKDOWN; st.active = 0; st.beta = 0.0; }
+          else { st.beta = s / st.rho; st.rho = s; }
+        }
+      } else if (mode == kModeAlpha) {     // alpha = rho / (p^T A p)
+        st.pw = s;
+        if (st.active) {
+          if (!(s > 0.0 && isfinite(s))) { st.status = RR_ERR_BREAKDOWN; st.active = 0; st.alpha = 0.0; }
+          else st.alpha = st.rho / s;
+        } else {
+          st.alpha = 0.0;
+        }
+      } else if (mode == kModeNorm) {      // lam = |out|
+        st.lam = sqrt(s);
+      }
+    }
+  }
+}
+
+template <typename T>
+void qcomb(const T* Q, int64_t n, int k, int mp, const double* t, Coefs8 a, const T* X, T* out,
+           const T* D, int mode, double* part, unsigned* counter, ColState* cs, bool gated,
+           cudaStream_t st) {
+  const unsigned blocks = grid_rows(n, kNT / 32 * 4);
+  const size_t smem = (size_t)k * mp * sizeof(T);
+  auto kern = k_qcomb<T>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<blocks, kNT, smem, st>>>(Q, n, k, mp, t, a, X, out, D, mode, part, counter, cs,
+                                  gated ? 1 : 0);
+}
+
+// ==================================================== column dot products
+// dot[c] = sum_i X[i][c] Y[i][c]; last block applies `mode` (alpha/beta/rho/norm)
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_dot_cols(const T* __restrict__ X, const T* __restrict__ Y,
+                                                  int64_t n, int mp, int mode,
+                                                  double* __restrict__ part,
+                                                  unsigned* __restrict__ counter,
+                                                  ColState* __restrict__ cs, int gated,
+                                                  double* __restrict__ out_raw) {
+  if (gated && !any_active(cs, mp)) return;
+  __shared__ double red[kNT / 32 * 8];
+  double v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * kNT;
+  for (int64_t i = (int64_t)blockIdx.x * kNT + threadIdx.x; i < n; i += stride) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (c < mp) v[c] += (double)X[i * mp + c] * (double)Y[i * mp + c];
+  }
+  block_sum_cols<kNT>(v, mp, red);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < mp; ++c) part[(int64_t)blockIdx.x * mp + c] = v[c];
+  if (!last_block(counter)) return;
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < mp; ++c) {
+      const double s = sum_parts(part, gridDim.x, mp, c);
+      if (out_raw) out_raw[c] = s;
+      if (!cs) continue;
+      ColState& st = cs[c];
+      if (mode == kModeAlpha) {
+        st.pw = s;
+        if (st.active) {
+          if (!(s > 0.0 && isfinite(s))) { st.status = RR_ERR_BREAKDOWN; st.active = 0; st.alpha = 0.0; }
+          else st.alpha = st.rho / s;
+        } else {
+          st.alpha = 0.0;
+        }
+      } else if (mode == kModeRhoInit) {
+        st.rho = s;
+        st.rr = s;
+        if (st.active && !(s > 0.0 && isfinite(s))) {
+          if (s == 0.0) st.active = 0;
+          else { st.status = RR_ERR_BREAKDOWN; st.active = 0; }
+        }
+      } else if (mode == kModeNorm) {
+        st.lam = sqrt(s);
+      }
+    }
+  }
+}
+
+template <typename T>
+void dot_cols(const T* X, const T* Y, int64_t n, int mp, int mode, double* part,
+              unsigned* counter, ColState* cs, bool gated, double* out_raw, cudaStream_t st) {
+  const unsigned blocks = grid_rows(n, kNT * 4);
+  k_dot_cols<T><<<blocks, kNT, 0, st>>>(X, Y, n, mp, mode, part, counter, cs, gated ? 1 : 0,
+                                        out_raw);
+}
+
+// ===================================== C variant: e += a p, r -= a w, rr
+// Fused with the Q^T r slab partials.  Last block: convergence check.
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_update_qt(T* __restrict__ E, T* __restrict__ R,
+                                                   const T* __restrict__ P,
+                                                   const T* __restrict__ W,
+                                                   const T* __restrict__ Q, int64_t n, int k,
+                                                   int mp, int rps, double* __restrict__ tpart,
+                                                   double* __restrict__ part,
+                                                   unsigned* __restrict__ counter,
+                                                   ColState* __restrict__ cs) {
+  if (!any_active(cs, mp)) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* Rs = reinterpret_cast<T*>(smem_raw);  // rps x mp
+  __shared__ double red[kNT / 32 * 8];
+  __shared__ T al[8];
+  if (threadIdx.x < 8) al[threadIdx.x] = (threadIdx.x < mp && cs[threadIdx.x].active) ? (T)cs[threadIdx.x].alpha : (T)0;
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * rps;
+  const int cnt = (int)((n - r0 < rps) ? (n - r0) : rps);
+  double v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = 0.0;
+  for (int e = threadIdx.x; e < cnt * mp; e += kNT) {
+    const int64_t g = r0 * mp + e;
+    const int c = e % mp;
+    const T a = al[c];
+    E[g] = fma(a, P[g], E[g]);
+    const T r = fma(-a, W[g], R[g]);
+    R[g] = r;
+    Rs[e] = r;
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc)
+      if (cc == c) v[cc] += (double)r * (double)r;
+  }
+  __syncthreads();
+  if (tpart) {
+    double* out = tpart + (int64_t)blockIdx.x * k * mp;
+    for (int j = threadIdx.x; j < k; j += kNT) {
+      T acc[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[c] = (T)0;
+      const T* q = Q + r0 * k + j;
+      for (int i = 0; i < cnt; ++i) {
+        const T qij = q[(int64_t)i * k];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c < mp) acc[c] = fma(qij, Rs[i * mp + c], acc[c]);
+      }
+      for (int c = 0; c < mp; ++c) out[(int64_t)j * mp + c] = (double)acc[c];
+    }
+  }
+  block_sum_cols<kNT>(v, mp, red);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < mp; ++c) part[(int64_t)blockIdx.x * mp + c] = v[c];
+  if (!last_block(counter)) return;
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < mp; ++c) {
+      ColState& st = cs[c];
+      const double s = sum_parts(part, gridDim.x, mp, c);
+      st.rr = s;
+      if (!st.active) continue;
+      st.iters += 1;
+      if (!isfinite(s)) { st.status = RR_ERR_BREAKDOWN; st.active = 0; }
+      else if (s <= st.stop2 || st.iters >= st.budget) st.active = 0;
+    }
+  }
+}
+
+template <typename T>
+void update_qt(T* E, T* R, const T* P, const T* W, const T* Q, int64_t n, int k, int mp,
+               double* tpart, double* part, unsigned* counter, ColState* cs, cudaStream_t st) {
+  const int rps = qt_rows_per_slab(n);
+  const int nslab = qt_nslab(n);
+  k_update_qt<T><<<(unsigned)nslab, kNT, (size_t)rps * mp * sizeof(T), st>>>(
+      E, R, P, W, Q, n, k, mp, rps, tpart, part, counter, cs);
+}
+
+// ========================== R variant: y += a p, r -= a q, rho = r^T r, beta
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_update_cg(T* __restrict__ Yv, T* __restrict__ R,
+                                                   const T* __restrict__ P,
+                                                   const T* __restrict__ Bp, int64_t n, int mp,
+                                                   double* __restrict__ part,
+                                                   unsigned* __restrict__ counter,
+                                                   ColState* __restrict__ cs) {
+  if (!any_active(cs, mp)) return;
+  __shared__ double red[kNT / 32 * 8];
+  __shared__ T al[8];
+  if (threadIdx.x < 8) al[threadIdx.x] = (threadIdx.x < mp && cs[threadIdx.x].active) ? (T)cs[threadIdx.x].alpha : (T)0;
+  __syncthreads();
+  double v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = 0.0;
+  const int64_t total = n * mp;
+  const int64_t stride = (int64_t)gridDim.x * kNT;
+  for (int64_t g = (int64_t)blockIdx.x * kNT + threadIdx.x; g < total; g += stride) {
+    const int c = (int)(g % mp);
+    const T a = al[c];
+    Yv[g] = fma(a, P[g], Yv[g]);
+    const T r = fma(-a, Bp[g], R[g]);
+    R[g] = r;
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc)
+      if (cc == c) v[cc] += (double)r * (double)r;
+  }
+  block_sum_cols<kNT>(v, mp, red);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < mp; ++c) part[(int64_t)blockIdx.x * mp + c] = v[c];
+  if (!last_block(counter)) return;
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < mp; ++c) {
+      ColState& st = cs[c];
+      const double s = sum_parts(part, gridDim.x, mp, c);
+      st.rr = s;
+      if (!st.active) continue;
+      st.iters += 1;
+      if (!isfinite(s)) { st.status = RR_ERR_BREAKDOWN; st.active = 0; continue; }
+      st.beta = (st.rho > 0.0) ? s / st.rho : 0.0;
+      st.rho = s;
+      if (s <= st.stop2 || st.iters >= st.budget) st.active = 0;
+    }
+  }
+}
+
+template <typename T>
+void update_cg(T* Yv, T* R, const T* P, const T* Bp, int64_t n, int mp, double* part,
+               unsigned* counter, ColState* cs, cudaStream_t st) {
+  const unsigned blocks = grid_rows(n * mp, kNT * 4);
+  k_update_cg<T><<<blocks, kNT, 0, st>>>(Yv, R, P, Bp, n, mp, part, counter, cs);
+}
+
+// ========================================= p = z + beta p  (active columns)
+template <typename T>
+__global__ void k_p_update(T* __restrict__ P, const T* __restrict__ Z, int64_t n, int mp,
+                           const ColState* __restrict__ cs, int init) {
+  if (!init && !any_active(cs, mp)) return;
+  __shared__ T be[8];
+  __shared__ int ac[8];
+  if (threadIdx.x < 8) {
+    be[threadIdx.x] = (threadIdx.x < mp) ? (T)cs[threadIdx.x].beta : (T)0;
+    ac[threadIdx.x] = (threadIdx.x < mp) ? cs[threadIdx.x].active : 0;
+  }
+  __syncthreads();
+  const int64_t total = n * mp;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const int c = (int)(g % mp);
+    if (init) P[g] = Z[g];
+    else if (ac[c]) P[g] = fma(be[c], P[g], Z[g]);
+  }
+}
+
+template <typename T>
+void p_update(T* P, const T* Z, int64_t n, int mp, const ColState* cs, bool init,
+              cudaStream_t st) {
+  const unsigned blocks = grid_rows(n * mp, 256 * 4);
+  k_p_update<T><<<blocks, 256, 0, st>>>(P, Z, n, mp, cs, init ? 1 : 0);
+}
+
+// ============================================================ elementwise
+// out = a X + b Y (per column coefficients), any of X, Y may be null
+template <typename TX, typename TY, typename TO>
+__global__ void k_axpby(const TX* __restrict__ X, Coefs8 a, const TY* __restrict__ Y, Coefs8 b,
+                        TO* __restrict__ out, int64_t n, int mp) {
+  const int64_t total = n * mp;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const int c = (int)(g % mp);
+    double v = 0.0;
+    if (X) v += a.v[c] * (double)X[g];
+    if (Y) v += b.v[c] * (double)Y[g];
+    out[g] = (TO)v;
+  }
+}
+
+template <typename TX, typename TY, typename TO>
+void axpby(const TX* X, Coefs8 a, const TY* Y, Coefs8 b, TO* out, int64_t n, int mp,
+           cudaStream_t st) {
+  const unsigned blocks = grid_rows(n * mp, 256 * 4);
+  k_axpby<TX, TY, TO><<<blocks, 256, 0, st>>>(X, a, Y, b, out, n, mp);
+}
+
+// out = X / lam[c] (lam from ColState; zero columns stay zero)
+template <typename T>
+__global__ void k_scale_cols(const T* __restrict__ X, T* __restrict__ out, int64_t n, int mp,
+                             const ColState* __restrict__ cs) {
+  const int64_t total = n * mp;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const int c = (int)(g % mp);
+    const double l = cs[c].lam;
+    out[g] = (l > 0.0) ? (T)((double)X[g] / l) : (T)0;
+  }
+}
+
+template <typename T>
+void scale_cols(const T* X, T* out, int64_t n, int mp, const ColState* cs, cudaStream_t st) {
+  k_scale_cols<T><<<grid_rows(n * mp, 256 * 4), 256, 0, st>>>(X, out, n, mp, cs);
+}
+
+// column-major (ld) <-> interleaved n x mp
+__global__ void k_gather_cols(const double* __restrict__ B, int64_t ld, int m, int64_t n, int mp,
+                              double* __restrict__ out) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * mp) return;
+  const int64_t i = g / mp;
+  const int c = (int)(g % mp);
+  out[g] = (c < m) ? B[(int64_t)c * ld + i] : 0.0;
+}
+__global__ void k_scatter_cols(const double* __restrict__ X, int64_t n, int mp, int m,
+                               double* __restrict__ out, int64_t ld) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * mp) return;
+  const int64_t i = g / mp;
+  const int c = (int)(g % mp);
+  if (c < m) out[(int64_t)c * ld + i] = X[g];
+}
+void gather_cols(const double* B, int64_t ld, int m, int64_t n, int mp, double* out,
+                 cudaStream_t st) {
+  k_gather_cols<<<(unsigned)cdiv(n * mp, 256), 256, 0, st>>>(B, ld, m, n, mp, out);
+}
+void scatter_cols(const double* X, int64_t n, int mp, int m, double* out, int64_t ld,
+                  cudaStream_t st) {
+  k_scatter_cols<<<(unsigned)cdiv(n * mp, 256), 256, 0, st>>>(X, n, mp, m, out, ld);
+}
+
+// restart: set per-column stop thresholds, budgets and activity
+__global__ void k_restart_init(ColState* cs, int mp, RestartParams p) {
+  const int c = threadIdx.x;
+  if (c >= mp) return;
+  ColState& s = cs[c];
+  s.stop2 = p.stop2[c];
+  s.budget = p.budget[c];
+  s.active = p.active[c];
+  s.iters = 0;
+  s.alpha = 0.0;
+  s.beta = 0.0;
+  s.rho = 0.0;
+  s.status = RR_OK;
+}
+void restart_init(ColState* cs, int mp, const RestartParams& p, cudaStream_t st) {
+  k_restart_init<<<1, 32, 0, st>>>(cs, mp, p);
+}
+
+// ------------------------------------------------------------ instances
+#define RR_INST(T)                                                                               \
+  template void qt_partial<T>(const T*, const T*, int64_t, int, int, int, double*, cudaStream_t); \
+  template void qt_partial_gated<T>(const T*, const T*, int64_t, int, int, double*,               \
+                                    const ColState*, cudaStream_t);                               \
+  template void qcomb<T>(const T*, int64_t, int, int, const double*, Coefs8, const T*, T*,       \
+                         const T*, int, double*, unsigned*, ColState*, bool, cudaStream_t);      \
+  template void dot_cols<T>(const T*, const T*, int64_t, int, int, double*, unsigned*,           \
+                            ColState*, bool, double*, cudaStream_t);                             \
+  template void update_qt<T>(T*, T*, const T*, const T*, const T*, int64_t, int, int, double*,   \
+                             double*, unsigned*, ColState*, cudaStream_t);                       \
+  template void update_cg<T>(T*, T*, const T*, const T*, int64_t, int, double*, unsigned*,       \
+                             ColState*, cudaStream_t);                                           \
+  template void p_update<T>(T*, const T*, int64_t, int, const ColState*, bool, cudaStream_t);    \
+  template void scale_cols<T>(const T*, T*, int64_t, int, const ColState*, cudaStream_t);
+
+RR_INST(float)
+RR_INST(double)
+template void axpby<double, double, double>(const double*, Coefs8, const double*, Coefs8, double*, int64_t, int, cudaStream_t);
+template void axpby<double, float, double>(const double*, Coefs8, const float*, Coefs8, double*, int64_t, int, cudaStream_t);
+template void axpby<double, double, float>(const double*, Coefs8, const double*, Coefs8, float*, int64_t, int, cudaStream_t);
+template void axpby<float, float, float>(const float*, Coefs8, const float*, Coefs8, float*, int64_t, int, cudaStream_t);
+template void axpby<double, float, float>(const double*, Coefs8, const float*, Coefs8, float*, int64_t, int, cudaStream_t);
+
+}  // namespace rr

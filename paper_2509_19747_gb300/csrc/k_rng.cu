@@ -1,0 +1,108 @@
+// Random test matrices drawn from the seeded Philox streams (Sec. 2 test
+// matrices; stream layout in philox.cuh).
+#include "philox.cuh"
+#include "rr_common.cuh"
+
+namespace rr {
+
+template <typename T>
+__global__ void k_gaussian_omega(T* __restrict__ Om, __nv_bfloat16* __restrict__ Ob, int64_t n,
+                                 int k, uint64_t seed, int round_bf16) {
+  const int q4 = (k + 3) >> 2;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * q4) return;
+  const int64_t i = g / q4;
+  const int q = (int)(g - i * q4);
+  const U32x4 w = philox_draw(seed, (uint32_t)i, (uint32_t)q, kStreamOmega);
+  T z[4];
+  box_muller4(w, z);
+  const T scale = (T)(1.0 / sqrt((double)k));
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int j = 4 * q + t;
+    if (j >= k) break;
+    T v = z[t] * scale;
+    if (round_bf16) {
+      const __nv_bfloat16 b = __float2bfloat16_rn((float)v);
+      v = (T)__bfloat162float(b);
+      if (Ob) Ob[i * k + j] = b;
+    }
+    Om[i * k + j] = v;
+  }
+}
+
+template <typename T>
+void gen_gaussian_omega(T* Om, __nv_bfloat16* Om_bf16, int64_t n, int k, uint64_t seed,
+                        bool round_bf16, cudaStream_t st) {
+  const int64_t total = n * ((k + 3) / 4);
+  k_gaussian_omega<T><<<(unsigned)cdiv(total, 256), 256, 0, st>>>(Om, Om_bf16, n, k, seed,
+                                                                   round_bf16 ? 1 : 0);
+}
+
+__global__ void k_sparse_sign(int32_t* __restrict__ cols, int8_t* __restrict__ sgn,
+                              int64_t nlines, int ncols, int gamma, uint64_t seed,
+                              uint32_t stream_id) {
+  const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (line >= nlines) return;
+  int32_t c[kMaxGamma];
+  int8_t s[kMaxGamma];
+  sparse_sign_line(seed, stream_id, (uint32_t)line, (uint32_t)ncols, gamma, c, s);
+  for (int t = 0; t < gamma; ++t) {
+    cols[line * gamma + t] = c[t];
+    sgn[line * gamma + t] = s[t];
+  }
+}
+
+void gen_sparse_sign(int32_t* cols, int8_t* sgn, int64_t nlines, int ncols, int gamma,
+                     uint64_t seed, uint32_t stream_id, cudaStream_t st) {
+  k_sparse_sign<<<(unsigned)cdiv(nlines, 128), 128, 0, st>>>(cols, sgn, nlines, ncols, gamma,
+                                                              seed, stream_id);
+}
+
+template <typename T>
+__global__ void k_sparse_to_dense(T* __restrict__ Om, const int32_t* __restrict__ cols,
+                                  const int8_t* __restrict__ sgn, int64_t n, int k, int gamma,
+                                  T val) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T* row = Om + i * k;
+  for (int j = 0; j < k; ++j) row[j] = (T)0;
+  for (int t = 0; t < gamma; ++t) row[cols[i * gamma + t]] = sgn[i * gamma + t] > 0 ? val : -val;
+}
+
+template <typename T>
+void sparse_to_dense_omega(T* Om, const int32_t* cols, const int8_t* sgn, int64_t n, int k,
+                           int gamma, cudaStream_t st) {
+  const T val = (T)(1.0 / sqrt((double)gamma));
+  k_sparse_to_dense<T><<<(unsigned)cdiv(n, 128), 128, 0, st>>>(Om, cols, sgn, n, k, gamma, val);
+}
+
+template <typename T>
+__global__ void k_power_start(T* __restrict__ V, int64_t n, int mp, int col, int which,
+                              uint64_t seed) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const U32x4 w = philox_draw(seed, (uint32_t)i, 0u, kStreamPower);
+  double z[4];
+  box_muller4(w, z);
+  V[i * mp + col] = (T)z[which];
+}
+
+template <typename T>
+void gen_power_start(T* V, int64_t n, int mp, int col, int which, uint64_t seed,
+                     cudaStream_t st) {
+  k_power_start<T><<<(unsigned)cdiv(n, 256), 256, 0, st>>>(V, n, mp, col, which, seed);
+}
+
+template void gen_gaussian_omega<float>(float*, __nv_bfloat16*, int64_t, int, uint64_t, bool,
+                                        cudaStream_t);
+template void gen_gaussian_omega<double>(double*, __nv_bfloat16*, int64_t, int, uint64_t, bool,
+                                         cudaStream_t);
+template void sparse_to_dense_omega<float>(float*, const int32_t*, const int8_t*, int64_t, int,
+                                           int, cudaStream_t);
+template void sparse_to_dense_omega<double>(double*, const int32_t*, const int8_t*, int64_t,
+                                            int, int, cudaStream_t);
+template void gen_power_start<float>(float*, int64_t, int, int, int, uint64_t, cudaStream_t);
+template void gen_power_start<double>(double*, int64_t, int, int, int, uint64_t, cudaStream_t);
+
+}  // namespace rr

@@ -1,0 +1,1013 @@
+// C ABI of the library and the host-side orchestration of RandRAND:
+//   build  = Alg. 7 steps 1-4 (C-RandRAND) / Alg. 4 steps 1-2 (R-RandRAND)
+//   solve  = Alg. 7 steps 5-11 / Alg. 4 steps 3-9 with restarts (Sec. 7 setup)
+// All arithmetic runs in the kernels of this library on the handle's stream;
+// the host only sequences launches and reads a few scalars (residual norms,
+// iteration counters, the power-iteration estimates that fix tau).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rr_common.cuh"
+#include "rr_krylov.cuh"
+
+using namespace rr;
+
+namespace {
+
+constexpr int kKK = 12;           // k x k float64 work matrices
+constexpr int kMaxGammaHost = 16; // sparse-sign nonzeros per row, at most
+constexpr int kChunk = 8;         // Krylov iterations per captured graph
+constexpr int kMaxRestarts = 400;
+
+enum Region {
+  R_OM, R_OMB, R_SSC, R_SSS, R_Y, R_Q, R_KK, R_KKT, R_GPART, R_CHOLW, R_STATUS, R_XS, R_CN,
+  R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT, R_CS, R_NORMS, R_NREG
+};
+
+struct Layout {
+  size_t off[R_NREG];
+  size_t size[R_NREG];
+  size_t total;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int pad_mp(int m) {
+  int mp = 2;
+  while (mp < m) mp <<= 1;
+  return mp;
+}
+
+bool uses_f64(const rr_build_opts& o) { return o.precision == RR_PREC_FP64; }
+
+Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
+  Layout L;
+  memset(&L, 0, sizeof(L));
+  const size_t n = (size_t)A.n, kk = (size_t)k;
+  const size_t ts = uses_f64(o) ? 8 : 4;
+  const int mp = pad_mp(o.max_rhs);
+  OpDev od;
+  memset(&od, 0, sizeof(od));
+  od.kind = A.kind;
+  od.n = A.n;
+  const int gs_max = std::max(gram_nsplit(A.n, k, k), 1);
+  L.size[R_OM] = n * kk * ts;
+  L.size[R_OMB] = (o.precision == RR_PREC_MIXED) ? n * kk * 2 : 0;
+  L.size[R_SSC] = n * (size_t)o.gamma * 4;
+  L.size[R_SSS] = n * (size_t)o.gamma;
+  L.size[R_Y] = n * kk * ts;
+  L.size[R_Q] = n * kk * ts;
+  L.size[R_KK] = (size_t)kKK * kk * kk * 8;
+  L.size[R_KKT] = kk * kk * ts;
+  L.size[R_GPART] = (size_t)gs_max * kk * kk * 8;
+  L.size[R_CHOLW] = 32 * 32 * 8;
+  L.size[R_STATUS] = 64;
+  L.size[R_XS] = (A.kind == RR_OP_GAUSS_KERNEL) ? n * (size_t)A.dim * 4 : 0;
+  L.size[R_CN] = (A.kind == RR_OP_GAUSS_KERNEL) ? n * 4 : 0;
+  L.size[R_MVS] = op_matvec_scratch_elems(od, mp) * 8;
+  L.size[R_VT] = 7 * n * (size_t)mp * ts;
+  L.size[R_V64] = 4 * n * (size_t)mp * 8;
+  L.size[R_STAGE] = 2 * n * (size_t)mp * 8;
+  L.size[R_TPART] = (size_t)qt_nslab(A.n) * kk * (size_t)mp * 8;
+  L.size[R_TVEC] = 3 * kk * (size_t)mp * 8;
+  L.size[R_RPART] = (size_t)kMaxReduceBlocks * 8 * 8;
+  L.size[R_CNT] = 64 * 4;
+  L.size[R_CS] = 8 * sizeof(ColState);
+  L.size[R_NORMS] = 64 * 8;
+  size_t off = 0;
+  for (int r = 0; r < R_NREG; ++r) {
+    L.off[r] = off;
+    off += align256(L.size[r]);
+  }
+  L.total = off;
+  return L;
+}
+
+rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
+  if (!A) return RR_ERR_INVALID_ARG;
+  if (A->n < 1 || A->n > (int64_t)INT32_MAX) return RR_ERR_INVALID_ARG;
+  if (k < 1 || (int64_t)k > A->n) return RR_ERR_INVALID_ARG;
+  if (o.max_rhs < 1 || o.max_rhs > 8) return RR_ERR_INVALID_ARG;
+  if (o.variant != RR_VARIANT_C && o.variant != RR_VARIANT_R) return RR_ERR_INVALID_ARG;
+  if (o.precision < RR_PREC_FP64 || o.precision > RR_PREC_MIXED) return RR_ERR_INVALID_ARG;
+  if (o.orth != RR_ORTH_CHOLQR2) return RR_ERR_UNSUPPORTED;
+  if (o.gamma < 1 || o.gamma > kMaxGammaHost || o.gamma > k) return RR_ERR_INVALID_ARG;
+  if (o.power_iters < 1 || o.power_iters > 1000) return RR_ERR_INVALID_ARG;
+  if (!(o.restart_eta > 0.0 && o.restart_eta < 1.0)) return RR_ERR_INVALID_ARG;
+  switch (A->kind) {
+    case RR_OP_DENSE:
+      if (!A->dense || A->ld < A->n || (A->dtype != 0 && A->dtype != 1)) return RR_ERR_INVALID_ARG;
+      // the sketch GEMM runs in the working type: float64 storage for FP64
+      if ((A->dtype == 0) != uses_f64(o)) return RR_ERR_UNSUPPORTED;
+      break;
+    case RR_OP_CSR:
+      if (!A->rowptr || !A->colidx || !A->vals || A->nnz < 0 || (A->dtype != 0 && A->dtype != 1))
+        return RR_ERR_INVALID_ARG;
+      break;
+    case RR_OP_GAUSS_KERNEL:
+      if (!A->points || A->dim < 1 || A->dim > 16 || !(A->bandwidth > 0.0) ||
+          !std::isfinite(A->bandwidth))
+        return RR_ERR_INVALID_ARG;
+      break;
+    default:
+      return RR_ERR_INVALID_ARG;
+  }
+  return RR_OK;
+}
+
+}  // namespace
+
+struct rr_handle {
+  OpDev op;
+  double mu;
+  int k;
+  int sketch;
+  uint64_t seed;
+  rr_build_opts o;
+  cudaStream_t st;
+  bool f64;
+  int mp;
+  int64_t n;
+  Layout L;
+  unsigned char* ws;
+  // build products
+  void* Om;
+  __nv_bfloat16* Omb;
+  int32_t* ss_cols;
+  int8_t* ss_sgn;
+  void* Y;
+  void* Q;
+  void* QH;
+  double* kk[kKK];
+  void* kkT;
+  double* gpart;
+  int gsplit;
+  double* cholw;
+  int* dstatus;
+  void* mvs;
+  // solve state
+  void* V[7];  // R P W Z E U V
+  double* v64[4];  // B X R W
+  double* stage[2];
+  double* tpart;
+  double* t[3];
+  double* rpart;
+  unsigned* cnt;
+  ColState* cs;
+  double* norms;
+  ColState* cs_host;  // pinned
+  double* norms_host; // pinned
+  // scalars
+  double tau, normE, lam_max;
+  // captured iteration graphs (per mp width)
+  cudaGraphExec_t graph;
+  bool graph_ok;
+  // profiling (opts.profile): event pairs around the hot kernels
+  struct EvPair {
+    cudaEvent_t e[2];
+    int cat;
+  };
+  bool prof;
+  rr_profile pacc;
+  std::vector<EvPair> ev_free, ev_pending;
+  std::vector<EvPair> ev_graph;  // one pair per captured iteration
+  bool graph_pending;
+};
+
+namespace {
+
+enum { kR = 0, kP = 1, kW = 2, kZ = 3, kE = 4, kU = 5, kV = 6 };
+enum { kB64 = 0, kX64 = 1, kR64 = 2, kW64 = 3 };
+// k x k slots
+enum { kR1 = 0, kR2 = 1, kRinvA = 2, kRinvB = 3, kRinv = 4, kRfull = 5, kM = 6, kG = 7, kH = 8,
+       kTm = 9, kScA = 10, kScB = 11 };
+
+template <typename T>
+T* vt(rr_handle* h, int i) {
+  return reinterpret_cast<T*>(h->V[i]);
+}
+
+void carve(rr_handle* h) {
+  auto at = [&](int r) -> void* { return h->L.size[r] ? (void*)(h->ws + h->L.off[r]) : nullptr; };
+  h->Om = at(R_OM);
+  h->Omb = (__nv_bfloat16*)at(R_OMB);
+  h->ss_cols = (int32_t*)at(R_SSC);
+  h->ss_sgn = (int8_t*)at(R_SSS);
+  h->Y = at(R_Y);
+  h->Q = at(R_Q);
+  h->QH = nullptr;
+  double* kkbase = (double*)at(R_KK);
+  for (int i = 0; i < kKK; ++i) h->kk[i] = kkbase + (size_t)i * h->k * h->k;
+  h->kkT = at(R_KKT);
+  h->gpart = (double*)at(R_GPART);
+  h->cholw = (double*)at(R_CHOLW);
+  h->dstatus = (int*)at(R_STATUS);
+  h->op.xs = (float*)at(R_XS);
+  h->op.cn = (float*)at(R_CN);
+  h->mvs = at(R_MVS);
+  const size_t ts = h->f64 ? 8 : 4;
+  const size_t vec = (size_t)h->n * h->mp;
+  unsigned char* vb = (unsigned char*)at(R_VT);
+  for (int i = 0; i < 7; ++i) h->V[i] = vb + i * vec * ts;
+  double* v64 = (double*)at(R_V64);
+  for (int i = 0; i < 4; ++i) h->v64[i] = v64 + i * vec;
+  double* stg = (double*)at(R_STAGE);
+  h->stage[0] = stg;
+  h->stage[1] = stg + vec;
+  h->tpart = (double*)at(R_TPART);
+  double* tv = (double*)at(R_TVEC);
+  for (int i = 0; i < 3; ++i) h->t[i] = tv + (size_t)i * h->k * h->mp;
+  h->rpart = (double*)at(R_RPART);
+  h->cnt = (unsigned*)at(R_CNT);
+  h->cs = (ColState*)at(R_CS);
+  h->norms = (double*)at(R_NORMS);
+}
+
+// a pair of timing events for one launch of category `cat` (nullptr when the
+// handle is not profiled or the pool is exhausted)
+const cudaEvent_t* ev_take(rr_handle* h, int cat) {
+  if (!h->prof || h->ev_free.empty()) return nullptr;
+  rr_handle::EvPair p = h->ev_free.back();
+  h->ev_free.pop_back();
+  p.cat = cat;
+  h->ev_pending.push_back(p);
+  return h->ev_pending.back().e;
+}
+
+void ev_accumulate(rr_handle* h, const rr_handle::EvPair& p) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, p.e[0], p.e[1]) == cudaSuccess) {
+    h->pacc.launches[p.cat] += 1;
+    h->pacc.ms[p.cat] += ms;
+  } else {
+    cudaGetLastError();
+  }
+}
+
+// called after the stream is idle: fold finished event pairs into the profile
+void harvest(rr_handle* h) {
+  if (!h->prof) return;
+  for (const auto& p : h->ev_pending) {
+    ev_accumulate(h, p);
+    h->ev_free.push_back(p);
+  }
+  h->ev_pending.clear();
+  if (h->graph_pending) {
+    for (const auto& p : h->ev_graph) ev_accumulate(h, p);
+    h->graph_pending = false;
+  }
+}
+
+rr_status sync_status(rr_handle* h) {
+  RR_CUDA_TRY(cudaGetLastError());
+  RR_CUDA_TRY(cudaStreamSynchronize(h->st));
+  harvest(h);
+  return RR_OK;
+}
+
+// read the k x k pivot status written by potrf_upper
+rr_status read_int(rr_handle* h, const int* dptr, int* out) {
+  RR_CUDA_TRY(cudaMemcpyAsync(h->norms_host, dptr, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  RR_TRY(sync_status(h));
+  memcpy(out, h->norms_host, sizeof(int));
+  return RR_OK;
+}
+
+rr_status read_doubles(rr_handle* h, const double* dptr, int cnt, double* out) {
+  RR_CUDA_TRY(cudaMemcpyAsync(h->norms_host, dptr, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  RR_TRY(sync_status(h));
+  memcpy(out, h->norms_host, cnt * sizeof(double));
+  return RR_OK;
+}
+
+rr_status read_cs(rr_handle* h) {
+  RR_CUDA_TRY(cudaMemcpyAsync(h->cs_host, h->cs, h->mp * sizeof(ColState), cudaMemcpyDeviceToHost, h->st));
+  return sync_status(h);
+}
+
+// Cholesky of the k x k matrix in `A` (in place); returns RR_ERR_NOT_SPD on a
+// non-positive pivot.
+rr_status chol(rr_handle* h, double* A) {
+  RR_CUDA_TRY(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
+  potrf_upper(A, h->k, h->cholw, h->dstatus, h->st);
+  int s = 0;
+  RR_TRY(read_int(h, h->dstatus, &s));
+  return s == 0 ? RR_OK : RR_ERR_NOT_SPD;
+}
+
+// Gram G = X^T X of an n x k matrix in the working type (float64 partials)
+template <typename T>
+void gram(rr_handle* h, const T* X, double* G) {
+  gram_partial<T>(X, h->k, X, h->k, h->n, h->k, h->k, true, h->gsplit, h->gpart, h->st);
+  reduce_gram(h->gpart, h->gsplit, h->k, h->k, true, false, G, h->st);
+}
+
+template <typename T>
+void right_mult(rr_handle* h, const T* X, const double* Mkk, T* out) {
+  // out = X Mkk  (n x k times k x k), Mkk converted to the working type
+  const T* Mt;
+  if (sizeof(T) == 8) {
+    Mt = reinterpret_cast<const T*>(Mkk);
+  } else {
+    convert<double, float>(Mkk, (float*)h->kkT, (int64_t)h->k * h->k, h->st);
+    Mt = reinterpret_cast<const T*>(h->kkT);
+  }
+  gemm_nn<T>(h->n, h->k, h->k, 1.0, X, h->k, Mt, h->k, 0.0, nullptr, 0, out, h->k, h->st);
+}
+
+__global__ void k_trace(const double* A, int k, double* out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) s += A[(int64_t)i * k + i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) *out = s;
+}
+__global__ void k_maxdiag(const double* A, int k, double* out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) s = fmax(s, fabs(A[(int64_t)i * k + i]));
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if (threadIdx.x == 0) *out = s;
+}
+
+// CholeskyQR2 of Y_mu (Sec. 4.2 Alg. 2 applied twice): Q = Y R^-1, R upper
+// with positive diagonal.  If the first Gram is numerically singular, a
+// shifted first pass (shifted CholeskyQR, Fukaya et al. 2020, the shift of
+// Sec. 5.1) is followed by two plain passes.
+template <typename T>
+rr_status orthogonalize(rr_handle* h) {
+  const int k = h->k;
+  double* G1 = h->kk[kScA];
+  double* Rp = h->kk[kR1];
+  double* Rip = h->kk[kRinvA];
+  double* RinvAcc = h->kk[kRinv];
+  double* Racc = h->kk[kRfull];
+  T* src = (T*)h->Y;
+  T* dst = (T*)h->Q;
+  int passes = 2;
+  bool shifted = false;
+  gram<T>(h, src, G1);
+  RR_CUDA_TRY(cudaMemcpyAsync(Rp, G1, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+  rr_status s = chol(h, Rp);
+  if (s == RR_ERR_NOT_SPD) {
+    double tr = 0.0;
+    k_trace<<<1, 32, 0, h->st>>>(G1, k, h->norms);
+    RR_TRY(read_doubles(h, h->norms, 1, &tr));
+    const double u = h->f64 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
+    const double shift = 11.0 * ((double)h->n * k + (double)k * (k + 1)) * u * tr;
+    RR_CUDA_TRY(cudaMemcpyAsync(Rp, G1, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+    add_diag(Rp, k, shift, h->st);
+    RR_TRY(chol(h, Rp));
+    passes = 3;
+    shifted = true;
+  } else if (s != RR_OK) {
+    return s;
+  }
+  (void)shifted;
+  for (int p = 0; p < passes; ++p) {
+    if (p > 0) {
+      gram<T>(h, src, Rp);
+      RR_TRY(chol(h, Rp));
+    }
+    trtri_upper_with(Rp, k, h->kk[kScB], Rip, h->st);
+    right_mult<T>(h, src, Rip, dst);
+    if (p == 0) {
+      RR_CUDA_TRY(cudaMemcpyAsync(RinvAcc, Rip, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+      RR_CUDA_TRY(cudaMemcpyAsync(Racc, Rp, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+    } else {
+      // RinvAcc <- RinvAcc Rip ; Racc <- Rp Racc   (all upper triangular)
+      gemm_upper_upper(k, RinvAcc, Rip, h->kk[kScB], h->st);
+      RR_CUDA_TRY(cudaMemcpyAsync(RinvAcc, h->kk[kScB], (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+      gemm_upper_upper(k, Rp, Racc, h->kk[kScB], h->st);
+      RR_CUDA_TRY(cudaMemcpyAsync(Racc, h->kk[kScB], (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+    }
+    std::swap(src, dst);
+  }
+  // the orthonormal factor is in `src`
+  h->Q = src;
+  h->Y = dst;  // free buffer from here on
+  return RR_OK;
+}
+
+// C-RandRAND core matrix G = (R_M R^-1)^T (R_M R^-1), R_M^T R_M = sym(Omega^T
+// Y_mu) (remark after Alg. 7).  M is in kk[kM].  Jitter ladder of App. C
+// (alpha = 10^-14 .. 10^-1 times the largest diagonal entry) on failure.
+rr_status core_matrix(rr_handle* h) {
+  const int k = h->k;
+  double* RM = h->kk[kScA];
+  RR_CUDA_TRY(cudaMemcpyAsync(RM, h->kk[kM], (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+  rr_status s = chol(h, RM);
+  if (s == RR_ERR_NOT_SPD) {
+    double md = 0.0;
+    k_maxdiag<<<1, 32, 0, h->st>>>(h->kk[kM], k, h->norms);
+    RR_TRY(read_doubles(h, h->norms, 1, &md));
+    s = RR_ERR_NOT_SPD;
+    for (int e = -14; e <= -1 && s == RR_ERR_NOT_SPD; ++e) {
+      RR_CUDA_TRY(cudaMemcpyAsync(RM, h->kk[kM], (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+      add_diag(RM, k, std::pow(10.0, e) * md, h->st);
+      s = chol(h, RM);
+    }
+  }
+  if (s != RR_OK) return s;
+  gemm_upper_upper(k, RM, h->kk[kRinv], h->kk[kTm], h->st);   // T = R_M R^-1
+  gram_upper(h->kk[kTm], k, h->gpart, h->kk[kG], h->st);        // G = T^T T
+  return RR_OK;
+}
+
+// -------------------------------------------------------------- Krylov
+template <typename T>
+void matvec(rr_handle* h, const T* V, T* W, const cudaEvent_t* ev) {
+  op_matvec<T>(h->op, h->mu, V, W, h->mp, (T*)h->mvs, h->st, ev);
+}
+
+// t_out = c_sum * Q^T V  (slab partials + reduction)
+template <typename T>
+void qt(rr_handle* h, const T* V, double* tout, bool gated) {
+  if (gated) {
+    qt_partial_gated<T>((const T*)h->Q, V, h->n, h->k, h->mp, h->tpart, h->cs, h->st);
+    reduce_slabs_gated(h->tpart, qt_nslab(h->n), h->k * h->mp, tout, h->cs, h->mp, h->st);
+  } else {
+    qt_partial<T>((const T*)h->Q, V, h->n, h->k, h->mp, qt_nslab(h->n), h->tpart, h->st);
+    reduce_slabs(h->tpart, qt_nslab(h->n), h->k * h->mp, tout, h->st);
+  }
+}
+
+// power iterations for |E| (column 0) and lambda_max(Pi A_mu Pi~) (column 1, C only)
+template <typename T>
+rr_status power_iterations(rr_handle* h) {
+  const int64_t n = h->n;
+  const int mp = h->mp;
+  const bool isC = h->o.variant == RR_VARIANT_C;
+  T* Vv = vt<T>(h, kV);
+  T* Uv = vt<T>(h, kU);
+  T* Wv = vt<T>(h, kW);
+  T* Zv = vt<T>(h, kZ);
+  RR_CUDA_TRY(cudaMemsetAsync(Vv, 0, (size_t)n * mp * sizeof(T), h->st));
+  gen_power_start<T>(Vv, n, mp, 0, 0, h->seed, h->st);
+  if (isC) gen_power_start<T>(Vv, n, mp, 1, 1, h->seed, h->st);
+  dot_cols<T>(Vv, Vv, n, mp, kModeNorm, h->rpart, h->cnt, h->cs, false, nullptr, h->st);
+  scale_cols<T>(Vv, Vv, n, mp, h->cs, h->st);
+  const Coefs8 a = coefs(1.0, 0.0);
+  for (int it = 0; it < h->o.power_iters; ++it) {
+    qt<T>(h, Vv, h->t[0], false);
+    // column 0: -Q^T v (-> (I - Pi) v); column 1: G Q^T v (-> Q G Q^T v)
+    kxk_apply(isC ? h->kk[kG] : nullptr, h->t[0], h->k, mp, coefs(-1.0, 0.0),
+              coefs(0.0, isC ? 1.0 : 0.0), h->t[1], h->st);
+    qcomb<T>((const T*)h->Q, n, h->k, mp, h->t[1], a, Vv, Uv, nullptr, kModeNone, h->rpart,
+             h->cnt, h->cs, false, h->st);
+    matvec<T>(h, Uv, Wv, ev_take(h, RR_PROF_POWER));
+    qt<T>(h, Wv, h->t[0], false);
+    // column 0: (I - Pi) w ; column 1: Pi w
+    kxk_apply(nullptr, h->t[0], h->k, mp, coefs(-1.0, 1.0), coefs(0.0, 0.0), h->t[1], h->st);
+    qcomb<T>((const T*)h->Q, n, h->k, mp, h->t[1], a, Wv, Zv, nullptr, kModeNone, h->rpart,
+             h->cnt, h->cs, false, h->st);
+    dot_cols<T>(Zv, Zv, n, mp, kModeNorm, h->rpart, h->cnt, h->cs, false, nullptr, h->st);
+    scale_cols<T>(Zv, Vv, n, mp, h->cs, h->st);
+  }
+  RR_TRY(read_cs(h));
+  h->normE = h->cs_host[0].lam;
+  h->lam_max = isC ? h->cs_host[1].lam : 0.0;
+  return RR_OK;
+}
+
+// tau: eq:c_randrand_tau with rho from eq:optimal_rho (F = 1/mu) for C;
+// tau = |E| (Alg. 4 step 2) for R.  |E| is clamped below at mu: for k < n
+// interlacing gives |E| >= lambda_min(A_mu) >= mu, and the clamp keeps tau
+// positive in the degenerate case k = n (E = 0).
+void choose_tau(rr_handle* h) {
+  const double nE = std::max(h->normE, h->mu);
+  if (h->o.variant == RR_VARIANT_C) {
+    double rho;
+    if (h->o.rho > 0.0) rho = h->o.rho;
+    else rho = (h->mu > 0.0) ? std::sqrt(h->mu * h->lam_max / nE) : 0.5;
+    h->tau = (h->lam_max > 0.0) ? rho * nE / h->lam_max : 0.0;
+    if (!(h->tau > 0.0)) h->tau = (h->lam_max > 0.0) ? 1.0 / h->lam_max : 1.0;
+  } else {
+    h->tau = nE > 0.0 ? nE : 1.0;
+  }
+}
+
+template <typename T>
+rr_status build_impl(rr_handle* h) {
+  const int64_t n = h->n;
+  const int k = h->k;
+  cudaStream_t st = h->st;
+  RR_CUDA_TRY(cudaMemsetAsync(h->cnt, 0, h->L.size[R_CNT], st));
+  RR_CUDA_TRY(cudaMemsetAsync(h->cs, 0, h->L.size[R_CS], st));
+  if (h->op.kind == RR_OP_GAUSS_KERNEL) prepare_kernel_points(h->op, st);
+  const bool mixed = h->o.precision == RR_PREC_MIXED;
+  // Alg. 7 step 1: Omega (eq:testmatrix with q = 0) and Y_mu = A Omega + mu Omega
+  if (h->sketch == RR_SKETCH_GAUSSIAN) {
+    gen_gaussian_omega<T>((T*)h->Om, h->Omb, n, k, h->seed, mixed, st);
+  } else {
+    gen_sparse_sign(h->ss_cols, h->ss_sgn, n, k, h->o.gamma, h->seed, 2u, st);
+    sparse_to_dense_omega<T>((T*)h->Om, h->ss_cols, h->ss_sgn, n, k, h->o.gamma, st);
+  }
+  if (h->op.kind == RR_OP_CSR && h->sketch == RR_SKETCH_SPARSE_SIGN)
+    csr_sketch_sparse<T>(h->op, h->mu, h->ss_cols, h->ss_sgn, h->o.gamma, (T*)h->Y, k, st,
+                         ev_take(h, RR_PROF_SKETCH));
+  else
+    op_sketch<T>(h->op, h->mu, (const T*)h->Om, (T*)h->Y, k,
+                 mixed && h->op.kind == RR_OP_GAUSS_KERNEL, st, ev_take(h, RR_PROF_SKETCH));
+  // M = sym(Omega^T Y_mu) = Omega^T A_mu Omega (C variant), before Y is reused
+  if (h->o.variant == RR_VARIANT_C) {
+    gram_partial<T>((const T*)h->Om, k, (const T*)h->Y, k, n, k, k, false, h->gsplit, h->gpart, st);
+    reduce_gram(h->gpart, h->gsplit, k, k, false, true, h->kk[kM], st);
+  }
+  RR_TRY(orthogonalize<T>(h));
+  if (h->o.variant == RR_VARIANT_C) RR_TRY(core_matrix(h));
+  RR_TRY(power_iterations<T>(h));
+  choose_tau(h);
+  if (h->o.variant == RR_VARIANT_C) {
+    // P = I + Q (tau G - I) Q^T; keep QH = Q H so that z = r + QH (Q^T r)
+    form_H(h->kk[kG], h->tau, h->kk[kH], k, st);
+    h->QH = h->Y;
+    right_mult<T>(h, (const T*)h->Q, h->kk[kH], (T*)h->QH);
+  }
+  return sync_status(h);
+}
+
+// ------------------------------------------------------------------ solve
+template <typename T>
+void iter_C(rr_handle* h, const cudaEvent_t* ev) {
+  const int64_t n = h->n;
+  const int mp = h->mp, k = h->k;
+  T *Rv = vt<T>(h, kR), *Pv = vt<T>(h, kP), *Wv = vt<T>(h, kW), *Zv = vt<T>(h, kZ),
+    *Ev = vt<T>(h, kE);
+  matvec<T>(h, Pv, Wv, ev);                                               // w = A_mu p
+  dot_cols<T>(Pv, Wv, n, mp, kModeAlpha, h->rpart, h->cnt, h->cs, true, nullptr, h->st);
+  update_qt<T>(Ev, Rv, Pv, Wv, (const T*)h->Q, n, k, mp, h->tpart, h->rpart, h->cnt, h->cs, h->st);
+  reduce_slabs_gated(h->tpart, qt_nslab(n), k * mp, h->t[0], h->cs, mp, h->st);  // t = Q^T r
+  qcomb<T>((const T*)h->QH, n, k, mp, h->t[0], coefs_all(1.0), Rv, Zv, Rv, kModeBeta, h->rpart,
+           h->cnt, h->cs, true, h->st);                                   // z = r + Q H t
+  p_update<T>(Pv, Zv, n, mp, h->cs, false, h->st);                        // p = z + beta p
+}
+
+// Reduce slab partials into c_sum * sum + c_other * other
+__global__ void k_reduce_comb(const double* __restrict__ part, int nslab, int len,
+                              double c_sum, const double* __restrict__ other, double c_other,
+                              double* __restrict__ out, const ColState* __restrict__ cs, int mp) {
+  bool any = false;
+  for (int c = 0; c < mp; ++c) any |= cs[c].active != 0;
+  if (!any) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= len) return;
+  double s = 0.0;
+  for (int b = 0; b < nslab; ++b) s += part[(int64_t)b * len + e];
+  out[e] = c_sum * s + (other ? c_other * other[e] : 0.0);
+}
+
+template <typename T>
+void qt_comb(rr_handle* h, const T* V, double c_sum, const double* other, double c_other,
+             double* out) {
+  qt_partial_gated<T>((const T*)h->Q, V, h->n, h->k, h->mp, h->tpart, h->cs, h->st);
+  const int len = h->k * h->mp;
+  k_reduce_comb<<<(unsigned)cdiv(len, 256), 256, 0, h->st>>>(h->tpart, qt_nslab(h->n), len, c_sum,
+                                                            other, c_other, out, h->cs, h->mp);
+}
+
+template <typename T>
+void iter_R(rr_handle* h, const cudaEvent_t* ev) {
+  const int64_t n = h->n;
+  const int mp = h->mp, k = h->k;
+  T *Rv = vt<T>(h, kR), *Pv = vt<T>(h, kP), *Wv = vt<T>(h, kW), *Zv = vt<T>(h, kZ),
+    *Ev = vt<T>(h, kE), *Uv = vt<T>(h, kU);
+  const T* Q = (const T*)h->Q;
+  qt_comb<T>(h, Pv, -1.0, nullptr, 0.0, h->t[0]);                          // t1n = -Q^T p
+  qcomb<T>(Q, n, k, mp, h->t[0], coefs_all(1.0), Pv, Uv, nullptr, kModeNone, h->rpart, h->cnt,
+           h->cs, true, h->st);                                             // u = (I - Pi) p
+  matvec<T>(h, Uv, Wv, ev);                                                // w = A_mu u
+  qt_comb<T>(h, Wv, -1.0, h->t[0], -h->tau, h->t[1]);                      // tau Q^T p - Q^T w
+  qcomb<T>(Q, n, k, mp, h->t[1], coefs_all(1.0), Wv, Zv, Pv, kModeAlpha, h->rpart, h->cnt, h->cs,
+           true, h->st);                                                    // B p, alpha
+  update_cg<T>(Ev, Rv, Pv, Zv, n, mp, h->rpart, h->cnt, h->cs, h->st);     // y, r, beta
+  p_update<T>(Pv, Rv, n, mp, h->cs, false, h->st);                         // p = r + beta p
+}
+
+template <typename T>
+rr_status run_chunk(rr_handle* h) {
+  if (!h->graph_ok) {
+    // capture kChunk iterations once per handle; replays reuse the same
+    // pointers and scalars (tau is fixed at build)
+    cudaGraph_t g = nullptr;
+    RR_CUDA_TRY(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < kChunk; ++i) {
+      const cudaEvent_t* ev = h->prof ? h->ev_graph[i].e : nullptr;
+      if (h->o.variant == RR_VARIANT_C) iter_C<T>(h, ev);
+      else iter_R<T>(h, ev);
+    }
+    cudaError_t e = cudaStreamEndCapture(h->st, &g);
+    if (e != cudaSuccess || !g) return RR_ERR_CUDA;
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return RR_ERR_CUDA;
+    h->graph_ok = true;
+  }
+  RR_CUDA_TRY(cudaGraphLaunch(h->graph, h->st));
+  h->graph_pending = h->prof;
+  return RR_OK;
+}
+
+// variant R recovery: e = Omega R^-1 Q^T (tau y - A_mu (I - Pi) y) + (I - Pi) y (eq:APdef3)
+template <typename T>
+void recover_R(rr_handle* h) {
+  const int64_t n = h->n;
+  const int mp = h->mp, k = h->k;
+  T *Ev = vt<T>(h, kE), *Uv = vt<T>(h, kU), *Wv = vt<T>(h, kW), *Zv = vt<T>(h, kZ);
+  const T* Q = (const T*)h->Q;
+  qt<T>(h, Ev, h->t[0], false);
+  kxk_apply(nullptr, h->t[0], k, mp, coefs_all(-1.0), coefs_all(0.0), h->t[1], h->st);
+  qcomb<T>(Q, n, k, mp, h->t[1], coefs_all(1.0), Ev, Uv, nullptr, kModeNone, h->rpart, h->cnt,
+           h->cs, false, h->st);                                            // u = (I - Pi) y
+  matvec<T>(h, Uv, Wv, ev_take(h, RR_PROF_MATVEC));                        // w = A_mu u
+  axpby<T, T, T>(Ev, coefs_all(h->tau), Wv, coefs_all(-1.0), Zv, n, mp, h->st);  // tau y - w
+  qt<T>(h, Zv, h->t[0], false);
+  kxk_apply(h->kk[kRinv], h->t[0], k, mp, coefs_all(0.0), coefs_all(1.0), h->t[1], h->st);
+  qcomb<T>((const T*)h->Om, n, k, mp, h->t[1], coefs_all(1.0), Uv, Ev, nullptr, kModeNone,
+           h->rpart, h->cnt, h->cs, false, h->st);                          // e = Omega s + u
+}
+
+template <typename T>
+rr_status residual(rr_handle* h) {
+  const int64_t n = h->n;
+  const int mp = h->mp;
+  double* B = h->v64[kB64];
+  double* X = h->v64[kX64];
+  double* R = h->v64[kR64];
+  if (h->o.precision == RR_PREC_FP32) {
+    // plain float32 residual
+    float* Xf = (float*)h->V[kV];
+    float* Wf = (float*)h->V[kW];
+    axpby<double, double, float>(X, coefs_all(1.0), nullptr, coefs_all(0.0), Xf, n, mp, h->st);
+    op_matvec<float>(h->op, h->mu, Xf, Wf, mp, (float*)h->mvs, h->st, ev_take(h, RR_PROF_RESIDUAL));
+    axpby<double, float, double>(B, coefs_all(1.0), Wf, coefs_all(-1.0), R, n, mp, h->st);
+  } else {
+    double* W = h->v64[kW64];
+    op_matvec<double>(h->op, h->mu, X, W, mp, (double*)h->mvs, h->st, ev_take(h, RR_PROF_RESIDUAL));
+    axpby<double, double, double>(B, coefs_all(1.0), W, coefs_all(-1.0), R, n, mp, h->st);
+  }
+  dot_cols<double>(R, R, n, mp, kModeNone, h->rpart, h->cnt, nullptr, false, h->norms, h->st);
+  return RR_OK;
+}
+
+template <typename T>
+rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
+                     rr_solve_info* info) {
+  const int64_t n = h->n;
+  const int mp = h->mp;
+  cudaStream_t st = h->st;
+  double* B = h->v64[kB64];
+  double* X = h->v64[kX64];
+  double* R64 = h->v64[kR64];
+  double bn2[8] = {0}, rn2[8] = {0};
+  dot_cols<double>(B, B, n, mp, kModeNone, h->rpart, h->cnt, nullptr, false, h->norms, st);
+  RR_TRY(read_doubles(h, h->norms, mp, bn2));
+  int used[8] = {0}, outer[8] = {0}, mv[8] = {0}, stat[8] = {0};
+  bool done[8] = {false};
+  double rel[8];
+  for (int c = 0; c < 8; ++c) rel[c] = 0.0;
+  for (int c = m; c < mp; ++c) done[c] = true;
+  const int mv_per_iter = 1;
+  for (int restart = 0; restart <= kMaxRestarts; ++restart) {
+    if (restart == 0 && !x_guess) {
+      RR_CUDA_TRY(cudaMemcpyAsync(R64, B, (size_t)n * mp * 8, cudaMemcpyDeviceToDevice, st));
+      for (int c = 0; c < mp; ++c) rn2[c] = bn2[c];
+    } else {
+      RR_TRY(residual<T>(h));
+      RR_TRY(read_doubles(h, h->norms, mp, rn2));
+      for (int c = 0; c < m; ++c)
+        if (!done[c]) mv[c] += 1;
+    }
+    RestartParams rp;
+    memset(&rp, 0, sizeof(rp));
+    bool any = false;
+    for (int c = 0; c < mp; ++c) {
+      if (c >= m) continue;
+      const double bn = std::sqrt(bn2[c]);
+      rel[c] = bn > 0.0 ? std::sqrt(rn2[c]) / bn : 0.0;
+      if (done[c]) continue;
+      if (!std::isfinite(rel[c])) { done[c] = true; stat[c] = RR_ERR_BREAKDOWN; continue; }
+      if (rel[c] <= rtol) { done[c] = true; stat[c] = RR_OK; continue; }
+      if (used[c] >= maxit || restart == kMaxRestarts) { done[c] = true; stat[c] = RR_ERR_MAXIT; continue; }
+      const double stop = std::max(h->o.restart_eta * rel[c] * bn, 0.5 * rtol * bn);
+      rp.stop2[c] = stop * stop;
+      rp.budget[c] = maxit - used[c];
+      rp.active[c] = 1;
+      any = true;
+    }
+    if (!any) break;
+    restart_init(h->cs, mp, rp, st);
+    // inner state: r = (working type) r64, e = 0
+    T* Rv = vt<T>(h, kR);
+    T* Ev = vt<T>(h, kE);
+    axpby<double, double, T>(R64, coefs_all(1.0), nullptr, coefs_all(0.0), Rv, n, mp, st);
+    RR_CUDA_TRY(cudaMemsetAsync(Ev, 0, (size_t)n * mp * sizeof(T), st));
+    if (h->o.variant == RR_VARIANT_C) {
+      // z = P r, p = z, rho = r^T z
+      qt<T>(h, Rv, h->t[0], false);
+      qcomb<T>((const T*)h->QH, n, h->k, mp, h->t[0], coefs_all(1.0), Rv, vt<T>(h, kZ), Rv,
+               kModeRhoInit, h->rpart, h->cnt, h->cs, false, st);
+      p_update<T>(vt<T>(h, kP), vt<T>(h, kZ), n, mp, h->cs, true, st);
+    } else {
+      p_update<T>(vt<T>(h, kP), Rv, n, mp, h->cs, true, st);
+      dot_cols<T>(Rv, Rv, n, mp, kModeRhoInit, h->rpart, h->cnt, h->cs, false, nullptr, st);
+    }
+    for (;;) {
+      RR_TRY(run_chunk<T>(h));
+      RR_TRY(read_cs(h));
+      bool act = false;
+      for (int c = 0; c < m; ++c) act |= h->cs_host[c].active != 0;
+      if (!act) break;
+    }
+    for (int c = 0; c < m; ++c) {
+      if (done[c] || !rp.active[c]) continue;
+      const ColState& s = h->cs_host[c];
+      used[c] += s.iters;
+      mv[c] += s.iters * mv_per_iter + (h->o.variant == RR_VARIANT_R ? 1 : 0);
+      outer[c] += 1;
+      if (s.status == RR_ERR_BREAKDOWN && s.iters == 0) { done[c] = true; stat[c] = RR_ERR_BREAKDOWN; }
+    }
+    if (h->o.variant == RR_VARIANT_R) recover_R<T>(h);
+    // x += e for the columns that ran (e = 0 elsewhere)
+    axpby<double, T, double>(X, coefs_all(1.0), Ev, coefs_all(1.0), X, n, mp, st);
+  }
+  RR_TRY(sync_status(h));
+  rr_status worst = RR_OK;
+  for (int c = 0; c < m; ++c) {
+    if (stat[c] != RR_OK && worst == RR_OK) worst = stat[c];
+    if (info) {
+      info[c].inner_iters = used[c];
+      info[c].outer_iters = outer[c];
+      info[c].matvecs = mv[c];
+      info[c].status = stat[c];
+      info[c].rel_residual = rel[c];
+      info[c].tau = h->tau;
+      info[c].normE = h->normE;
+      info[c].lam_max = h->lam_max;
+    }
+  }
+  return worst;
+}
+
+rr_status solve_dev(rr_handle* h, const double* b, int m, int64_t ldb, double* x, int64_t ldx,
+                    bool x_guess, double rtol, int maxit, rr_solve_info* info) {
+  gather_cols(b, ldb, m, h->n, h->mp, h->v64[kB64], h->st);
+  if (x_guess) gather_cols(x, ldx, m, h->n, h->mp, h->v64[kX64], h->st);
+  else RR_CUDA_TRY(cudaMemsetAsync(h->v64[kX64], 0, (size_t)h->n * h->mp * 8, h->st));
+  const rr_status s = h->f64 ? solve_impl<double>(h, m, rtol, maxit, x_guess, info)
+                             : solve_impl<float>(h, m, rtol, maxit, x_guess, info);
+  if (s != RR_OK && s != RR_ERR_MAXIT && s != RR_ERR_BREAKDOWN) return s;
+  scatter_cols(h->v64[kX64], h->n, h->mp, m, x, ldx, h->st);
+  RR_TRY(sync_status(h));
+  return s;
+}
+
+template <typename T>
+void apply_impl(rr_handle* h) {
+  const int64_t n = h->n;
+  const int mp = h->mp, k = h->k;
+  T *Rv = vt<T>(h, kR), *Zv = vt<T>(h, kZ), *Uv = vt<T>(h, kU), *Wv = vt<T>(h, kW);
+  axpby<double, double, T>(h->v64[kR64], coefs_all(1.0), nullptr, coefs_all(0.0), Rv, n, mp, h->st);
+  if (h->o.variant == RR_VARIANT_C) {
+    qt<T>(h, Rv, h->t[0], false);
+    qcomb<T>((const T*)h->QH, n, k, mp, h->t[0], coefs_all(1.0), Rv, Zv, nullptr, kModeNone,
+             h->rpart, h->cnt, h->cs, false, h->st);
+  } else {
+    const T* Q = (const T*)h->Q;
+    qt<T>(h, Rv, h->t[0], false);
+    kxk_apply(nullptr, h->t[0], k, mp, coefs_all(-1.0), coefs_all(0.0), h->t[1], h->st);
+    qcomb<T>(Q, n, k, mp, h->t[1], coefs_all(1.0), Rv, Uv, nullptr, kModeNone, h->rpart, h->cnt,
+             h->cs, false, h->st);
+    matvec<T>(h, Uv, Wv, nullptr);
+    qt<T>(h, Wv, h->t[2], false);
+    // tau Q^T r - Q^T w  =  -tau t1n - t2
+    kxk_apply(nullptr, h->t[0], k, mp, coefs_all(h->tau), coefs_all(0.0), h->t[1], h->st);
+    axpby<double, double, double>(h->t[1], coefs_all(1.0), h->t[2], coefs_all(-1.0), h->t[1], k, mp, h->st);
+    qcomb<T>(Q, n, k, mp, h->t[1], coefs_all(1.0), Wv, Zv, nullptr, kModeNone, h->rpart, h->cnt,
+             h->cs, false, h->st);
+  }
+  axpby<double, T, double>(nullptr, coefs_all(0.0), Zv, coefs_all(1.0), h->v64[kW64], n, mp, h->st);
+}
+
+}  // namespace
+
+// ======================================================================
+// C ABI
+// ======================================================================
+extern "C" {
+
+void rr_build_opts_default(rr_build_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->variant = RR_VARIANT_C;
+  o->precision = RR_PREC_FP64;
+  o->orth = RR_ORTH_CHOLQR2;
+  o->gamma = 8;
+  o->l_sk = 0;
+  o->gamma_sk = 8;
+  o->power_iters = 20;
+  o->max_rhs = 1;
+  o->rho = 0.0;
+  o->restart_eta = 1e-2;
+  o->profile = 0;
+}
+
+const char* randrand_status_str(rr_status s) {
+  switch (s) {
+    case RR_OK: return "ok";
+    case RR_ERR_INVALID_ARG: return "invalid argument";
+    case RR_ERR_WORKSPACE: return "workspace too small";
+    case RR_ERR_NOT_SPD: return "k x k matrix not positive definite";
+    case RR_ERR_BREAKDOWN: return "Krylov breakdown";
+    case RR_ERR_MAXIT: return "iteration budget reached";
+    case RR_ERR_TIMEOUT: return "device wait timed out";
+    case RR_ERR_CUDA: return "CUDA error";
+    case RR_ERR_UNSUPPORTED: return "unsupported option combination";
+    default: return "unknown status";
+  }
+}
+
+rr_status randrand_workspace_bytes(const rr_operator* A, int32_t k, const rr_build_opts* opts,
+                                   size_t* bytes) {
+  if (!bytes) return RR_ERR_INVALID_ARG;
+  rr_build_opts o;
+  if (opts) o = *opts;
+  else rr_build_opts_default(&o);
+  RR_TRY(validate(A, k, o));
+  *bytes = make_layout(*A, k, o).total;
+  return RR_OK;
+}
+
+rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t sketch,
+                         uint64_t seed, const rr_build_opts* opts, void* workspace,
+                         size_t ws_bytes, void* stream, rr_handle** out) {
+  if (!out) return RR_ERR_INVALID_ARG;
+  *out = nullptr;
+  rr_build_opts o;
+  if (opts) o = *opts;
+  else rr_build_opts_default(&o);
+  RR_TRY(validate(A, k, o));
+  if (!(mu >= 0.0) || !std::isfinite(mu)) return RR_ERR_INVALID_ARG;
+  if (sketch != RR_SKETCH_GAUSSIAN && sketch != RR_SKETCH_SPARSE_SIGN) return RR_ERR_INVALID_ARG;
+  if (!workspace || ((uintptr_t)workspace & 255)) return RR_ERR_INVALID_ARG;
+  const Layout L = make_layout(*A, k, o);
+  if (ws_bytes < L.total) return RR_ERR_WORKSPACE;
+  rr_handle* h = new (std::nothrow) rr_handle();
+  if (!h) return RR_ERR_INVALID_ARG;
+  memset(&h->op, 0, sizeof(h->op));
+  h->op.kind = A->kind;
+  h->op.dtype = A->dtype;
+  h->op.n = A->n;
+  h->op.dense = A->dense;
+  h->op.ld = A->ld;
+  h->op.rowptr = A->rowptr;
+  h->op.colidx = A->colidx;
+  h->op.vals = A->vals;
+  h->op.nnz = A->nnz;
+  h->op.points = A->points;
+  h->op.dim = A->dim;
+  h->op.bw = A->bandwidth;
+  h->mu = mu;
+  h->k = k;
+  h->sketch = sketch;
+  h->seed = seed;
+  h->o = o;
+  h->st = (cudaStream_t)stream;
+  h->f64 = uses_f64(o);
+  h->mp = pad_mp(o.max_rhs);
+  h->n = A->n;
+  h->L = L;
+  h->ws = (unsigned char*)workspace;
+  h->gsplit = gram_nsplit(A->n, k, k);
+  h->graph_ok = false;
+  h->graph = nullptr;
+  h->prof = o.profile != 0;
+  memset(&h->pacc, 0, sizeof(h->pacc));
+  h->graph_pending = false;
+  if (h->prof) {
+    for (int i = 0; i < 64 + kChunk; ++i) {
+      rr_handle::EvPair p;
+      p.cat = 0;
+      if (cudaEventCreate(&p.e[0]) != cudaSuccess || cudaEventCreate(&p.e[1]) != cudaSuccess) {
+        randrand_free(h);
+        return RR_ERR_CUDA;
+      }
+      if (i < kChunk) h->ev_graph.push_back(p);
+      else h->ev_free.push_back(p);
+    }
+  }
+  carve(h);
+  if (cudaMallocHost(&h->cs_host, 8 * sizeof(ColState)) != cudaSuccess ||
+      cudaMallocHost(&h->norms_host, 64 * sizeof(double)) != cudaSuccess) {
+    randrand_free(h);
+    return RR_ERR_CUDA;
+  }
+  const rr_status s = h->f64 ? build_impl<double>(h) : build_impl<float>(h);
+  if (s != RR_OK) {
+    randrand_free(h);
+    return s;
+  }
+  *out = h;
+  return RR_OK;
+}
+
+rr_status randrand_solve(rr_handle* h, const double* b, int32_t nrhs, int64_t ldb, double* x,
+                         int64_t ldx, int32_t x_is_guess, double rtol, int32_t maxit,
+                         rr_solve_info* info) {
+  if (!h || !b || !x) return RR_ERR_INVALID_ARG;
+  if (nrhs < 1 || nrhs > h->o.max_rhs || ldb < h->n || ldx < h->n) return RR_ERR_INVALID_ARG;
+  if (!(rtol > 0.0) || !std::isfinite(rtol) || maxit < 1) return RR_ERR_INVALID_ARG;
+  return solve_dev(h, b, nrhs, ldb, x, ldx, x_is_guess != 0, rtol, maxit, info);
+}
+
+rr_status randrand_solve_host(rr_handle* h, const double* b_host, int32_t nrhs, int64_t ldb,
+                              double* x_host, int64_t ldx, double rtol, int32_t maxit,
+                              rr_solve_info* info) {
+  if (!h || !b_host || !x_host) return RR_ERR_INVALID_ARG;
+  if (nrhs < 1 || nrhs > h->o.max_rhs || ldb < h->n || ldx < h->n) return RR_ERR_INVALID_ARG;
+  if (!(rtol > 0.0) || !std::isfinite(rtol) || maxit < 1) return RR_ERR_INVALID_ARG;
+  const size_t col = (size_t)h->n * sizeof(double);
+  RR_CUDA_TRY(cudaMemcpy2DAsync(h->stage[0], col, b_host, (size_t)ldb * sizeof(double), col,
+                                (size_t)nrhs, cudaMemcpyHostToDevice, h->st));
+  const rr_status s = solve_dev(h, h->stage[0], nrhs, h->n, h->stage[1], h->n, false, rtol,
+                                maxit, info);
+  if (s != RR_OK && s != RR_ERR_MAXIT && s != RR_ERR_BREAKDOWN) return s;
+  RR_CUDA_TRY(cudaMemcpy2DAsync(x_host, (size_t)ldx * sizeof(double), h->stage[1], col, col,
+                                (size_t)nrhs, cudaMemcpyDeviceToHost, h->st));
+  RR_CUDA_TRY(cudaStreamSynchronize(h->st));
+  return s;
+}
+
+void randrand_free(rr_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  if (h->graph_ok) cudaGraphExecDestroy(h->graph);
+  if (h->cs_host) cudaFreeHost(h->cs_host);
+  if (h->norms_host) cudaFreeHost(h->norms_host);
+  for (auto* v : {&h->ev_free, &h->ev_pending, &h->ev_graph})
+    for (auto& p : *v) {
+      cudaEventDestroy(p.e[0]);
+      cudaEventDestroy(p.e[1]);
+    }
+  delete h;
+}
+
+rr_status randrand_profile(rr_handle* h, rr_profile* out) {
+  if (!h || !out) return RR_ERR_INVALID_ARG;
+  RR_CUDA_TRY(cudaStreamSynchronize(h->st));
+  harvest(h);
+  *out = h->pacc;
+  return RR_OK;
+}
+
+rr_status randrand_export(rr_handle* h, int32_t what, double* dst) {
+  if (!h || !dst) return RR_ERR_INVALID_ARG;
+  const int64_t nk = h->n * h->k, kk = (int64_t)h->k * h->k;
+  const void* src = nullptr;
+  int64_t count = 0;
+  bool is_t = false;
+  switch (what) {
+    case 0: src = h->Om; count = nk; is_t = true; break;
+    case 1: src = h->Q; count = nk; is_t = true; break;
+    case 2: src = h->kk[kRfull]; count = kk; break;
+    case 3:
+      if (h->o.variant != RR_VARIANT_C) return RR_ERR_INVALID_ARG;
+      src = h->kk[kG]; count = kk; break;
+    default: return RR_ERR_INVALID_ARG;
+  }
+  if (is_t && !h->f64) convert<float, double>((const float*)src, dst, count, h->st);
+  else convert<double, double>((const double*)src, dst, count, h->st);
+  RR_CUDA_TRY(cudaGetLastError());
+  return RR_OK;
+}
+
+rr_status randrand_scalars(const rr_handle* h, double* tau, double* normE, double* lam_max) {
+  if (!h) return RR_ERR_INVALID_ARG;
+  if (tau) *tau = h->tau;
+  if (normE) *normE = h->normE;
+  if (lam_max) *lam_max = h->lam_max;
+  return RR_OK;
+}
+
+rr_status randrand_apply(rr_handle* h, const double* r, double* z, int32_t m, int64_t ld) {
+  if (!h || !r || !z || m < 1 || m > h->o.max_rhs || ld < h->n) return RR_ERR_INVALID_ARG;
+  gather_cols(r, ld, m, h->n, h->mp, h->v64[kR64], h->st);
+  if (h->f64) apply_impl<double>(h);
+  else apply_impl<float>(h);
+  scatter_cols(h->v64[kW64], h->n, h->mp, m, z, ld, h->st);
+  RR_CUDA_TRY(cudaGetLastError());
+  return RR_OK;
+}
+
+rr_status randrand_matvec(rr_handle* h, const double* v, double* w, int32_t m, int64_t ld) {
+  if (!h || !v || !w || m < 1 || m > h->o.max_rhs || ld < h->n) return RR_ERR_INVALID_ARG;
+  gather_cols(v, ld, m, h->n, h->mp, h->v64[kX64], h->st);
+  op_matvec<double>(h->op, h->mu, h->v64[kX64], h->v64[kW64], h->mp, (double*)h->mvs, h->st);
+  scatter_cols(h->v64[kW64], h->n, h->mp, m, w, ld, h->st);
+  RR_CUDA_TRY(cudaGetLastError());
+  return RR_OK;
+}
+
+}  // extern "C"

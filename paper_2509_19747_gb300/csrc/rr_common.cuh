@@ -1,0 +1,133 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/randrand.h"
+
+namespace rr {
+
+// ---------------------------------------------------------------- errors
+#define RR_CUDA_TRY(expr)                                  \
+  do {                                                     \
+    cudaError_t _e = (expr);                               \
+    if (_e != cudaSuccess) return RR_ERR_CUDA;             \
+  } while (0)
+
+#define RR_TRY(expr)                                       \
+  do {                                                     \
+    rr_status _s = (expr);                                 \
+    if (_s != RR_OK) return _s;                            \
+  } while (0)
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+constexpr int kSmSlabs = 304;      // row slabs of the tall-skinny reductions (2 x 152 SMs)
+
+// ---------------------------------------------------------------- operator
+// Device view of the operator plus the preprocessed kernel points.
+struct OpDev {
+  int kind;
+  int dtype;          // 0 f64, 1 f32 (dense / csr values)
+  int64_t n;
+  const void* dense;
+  int64_t ld;
+  const int32_t* rowptr;
+  const int32_t* colidx;
+  const void* vals;
+  int64_t nnz;
+  const float* points;
+  int dim;
+  double bw;
+  // kernel operator, float path: xs = x sqrt(log2 e) / h, cn = -|xs|^2 / 2,
+  // so that K_ij = exp2(xs_i . xs_j + cn_i + cn_j)
+  float* xs;
+  float* cn;
+};
+
+// Per right-hand-side Krylov scalars, device resident.
+struct ColState {
+  double rho;     // r^T z (C) or r^T r (R)
+  double alpha;
+  double beta;
+  double rr;      // |r|^2 of the recursive residual
+  double stop2;   // inner stop threshold squared
+  double pw;      // p^T A p (C) or p^T B p (R)
+  double lam;     // power-iteration norm
+  double pad;
+  int active;     // 1 while the inner solve runs on this column
+  int iters;      // inner iterations of the current restart
+  int budget;     // iteration budget of the current restart
+  int status;     // RR_OK or RR_ERR_BREAKDOWN
+};
+
+// ------------------------------------------------------------ launchers
+// k_rng.cu
+template <typename T>
+void gen_gaussian_omega(T* Om, __nv_bfloat16* Om_bf16, int64_t n, int k, uint64_t seed,
+                        bool round_bf16, cudaStream_t st);
+void gen_sparse_sign(int32_t* cols, int8_t* sgn, int64_t nlines, int ncols, int gamma,
+                     uint64_t seed, uint32_t stream_id, cudaStream_t st);
+template <typename T>
+void sparse_to_dense_omega(T* Om, const int32_t* cols, const int8_t* sgn, int64_t n, int k,
+                           int gamma, cudaStream_t st);
+template <typename T>
+void gen_power_start(T* V, int64_t n, int mp, int col, int which, uint64_t seed,
+                     cudaStream_t st);
+
+// k_dense.cu -- dense building blocks (row-major)
+template <typename T>
+void gemm_nn(int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t lda,
+             const T* B, int64_t ldb, double beta, const T* D, int64_t ldd, T* C,
+             int64_t ldc, cudaStream_t st);
+// part[s] = A[rows of split s]^T B[rows of split s]  (k1 x k2, float64)
+template <typename T>
+void gram_partial(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t nrows, int k1,
+                  int k2, bool symmetric, int nsplit, double* part, cudaStream_t st);
+// out = sum_s part[s]; symmetric: mirror the upper tiles; symmetrize: (P + P^T)/2
+void reduce_gram(const double* part, int nsplit, int k1, int k2, bool symmetric,
+                 bool symmetrize, double* out, cudaStream_t st);
+int gram_nsplit(int64_t nrows, int k1, int k2);
+// in-place upper Cholesky of a k x k SPD matrix; *status = 0 ok, j+1 on a
+// non-positive pivot j.  Lower triangle zeroed.
+void potrf_upper(double* A, int k, double* work, int* status, cudaStream_t st);
+// Rinv = R^-1 for upper-triangular R (Rt: k x k scratch for R^T)
+void trtri_upper_with(const double* R, int k, double* Rt, double* Rinv, cudaStream_t st);
+// C = A B for upper-triangular k x k A, B (float64)
+void gemm_upper_upper(int k, const double* A, const double* B, double* C, cudaStream_t st);
+// out = T^T T for upper-triangular k x k T; part: k x k scratch
+void gram_upper(const double* Tm, int k, double* part, double* out, cudaStream_t st);
+void add_diag(double* A, int k, double alpha, cudaStream_t st);
+// H = tau G - I
+void form_H(const double* G, double tau, double* H, int k, cudaStream_t st);
+template <typename Tin, typename Tout>
+void convert(const Tin* in, Tout* out, int64_t count, cudaStream_t st);
+void transpose_kxk(const double* in, double* out, int k, cudaStream_t st);
+
+// k_operator.cu -- products with A_mu
+void prepare_kernel_points(OpDev& op, cudaStream_t st);
+// W = (A + mu I) V, V and W n x mp interleaved (row i holds the mp columns)
+// ev (optional): two events recorded around the main product kernel
+template <typename T>
+void op_matvec(const OpDev& op, double mu, const T* V, T* W, int mp, T* split_scratch,
+               cudaStream_t st, const cudaEvent_t* ev = nullptr);
+size_t op_matvec_scratch_elems(const OpDev& op, int mp);
+// Y = (A + mu I) Omega, Omega n x k row-major; bf16: round K and Omega to bf16
+template <typename T>
+void op_sketch(const OpDev& op, double mu, const T* Om, T* Y, int k, bool bf16,
+               cudaStream_t st, const cudaEvent_t* ev = nullptr);
+// sparse-sign Omega given by its pattern (CSR operator): Y = A_mu Omega
+template <typename T>
+void csr_sketch_sparse(const OpDev& op, double mu, const int32_t* cols, const int8_t* sgn,
+                       int gamma, T* Y, int k, cudaStream_t st, const cudaEvent_t* ev = nullptr);
+
+// k_krylov.cu -- tall-skinny projector pieces and Krylov updates
+template <typename T>
+void qt_partial(const T* Q, const T* V, int64_t n, int k, int mp, int nslab, double* part,
+                cudaStream_t st);
+void reduce_slabs(const double* part, int nslab, int len, double* out, cudaStream_t st);
+int qt_nslab(int64_t n);
+
+}  // namespace rr

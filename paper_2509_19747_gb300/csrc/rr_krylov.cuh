@@ -1,0 +1,65 @@
+// Declarations of the Krylov / projector launchers (k_krylov.cu).
+#pragma once
+#include "rr_common.cuh"
+
+namespace rr {
+
+struct Coefs8 {
+  double v[8];
+};
+
+inline Coefs8 coefs(double c0, double c1 = 0, double c2 = 0, double c3 = 0, double c4 = 0,
+                    double c5 = 0, double c6 = 0, double c7 = 0) {
+  Coefs8 r = {{c0, c1, c2, c3, c4, c5, c6, c7}};
+  return r;
+}
+inline Coefs8 coefs_all(double c) { return coefs(c, c, c, c, c, c, c, c); }
+
+struct RestartParams {
+  double stop2[8];
+  int budget[8];
+  int active[8];
+};
+
+// what the last block of a fused reduction does with the per-column sums
+enum { kModeNone = 0, kModeAlpha = 1, kModeBeta = 2, kModeRhoInit = 3, kModeNorm = 4 };
+
+int qt_rows_per_slab(int64_t n);
+
+template <typename T>
+void qt_partial_gated(const T* Q, const T* V, int64_t n, int k, int mp, double* part,
+                      const ColState* cs, cudaStream_t st);
+void reduce_slabs_gated(const double* part, int nslab, int len, double* out, const ColState* cs,
+                        int mp, cudaStream_t st);
+void kxk_apply(const double* M, const double* t, int k, int mp, Coefs8 ca, Coefs8 cb,
+               double* out, cudaStream_t st);
+template <typename T>
+void qcomb(const T* Q, int64_t n, int k, int mp, const double* t, Coefs8 a, const T* X, T* out,
+           const T* D, int mode, double* part, unsigned* counter, ColState* cs, bool gated,
+           cudaStream_t st);
+template <typename T>
+void dot_cols(const T* X, const T* Y, int64_t n, int mp, int mode, double* part,
+              unsigned* counter, ColState* cs, bool gated, double* out_raw, cudaStream_t st);
+template <typename T>
+void update_qt(T* E, T* R, const T* P, const T* W, const T* Q, int64_t n, int k, int mp,
+               double* tpart, double* part, unsigned* counter, ColState* cs, cudaStream_t st);
+template <typename T>
+void update_cg(T* Yv, T* R, const T* P, const T* Bp, int64_t n, int mp, double* part,
+               unsigned* counter, ColState* cs, cudaStream_t st);
+template <typename T>
+void p_update(T* P, const T* Z, int64_t n, int mp, const ColState* cs, bool init,
+              cudaStream_t st);
+template <typename TX, typename TY, typename TO>
+void axpby(const TX* X, Coefs8 a, const TY* Y, Coefs8 b, TO* out, int64_t n, int mp,
+           cudaStream_t st);
+template <typename T>
+void scale_cols(const T* X, T* out, int64_t n, int mp, const ColState* cs, cudaStream_t st);
+void gather_cols(const double* B, int64_t ld, int m, int64_t n, int mp, double* out,
+                 cudaStream_t st);
+void scatter_cols(const double* X, int64_t n, int mp, int m, double* out, int64_t ld,
+                  cudaStream_t st);
+void restart_init(ColState* cs, int mp, const RestartParams& p, cudaStream_t st);
+
+constexpr int kMaxReduceBlocks = 8 * 152;  // upper bound on CTAs of the fused reductions
+
+}  // namespace rr

@@ -1,0 +1,126 @@
+"""The C-ABI library builds, loads and exports every symbol the header
+declares; host-side argument checks work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "randrand.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(\w+)\s*\(", src, flags=re.M)
+    return sorted({n for n in names if n.startswith(("randrand_", "rr_"))})
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2509_19747_gb300 import build as B
+    B.build()
+    import paper_2509_19747_gb300 as rr
+    return rr
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("randrand_build", "randrand_solve", "randrand_workspace_bytes", "randrand_free",
+                 "randrand_status_str", "rr_build_opts_default"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    cdll = lib.load_library()
+    for name in declared_functions():
+        assert hasattr(cdll, name), f"{name} declared in randrand.h but not exported"
+
+
+def test_struct_layouts_match_header(lib):
+    # sizes the C compiler gives the header structs (checked by a tiny host program)
+    import subprocess
+    import tempfile
+    src = r'''
+    #include <stdio.h>
+    #include <stddef.h>
+    #include "randrand.h"
+    int main(void){
+      printf("%zu %zu %zu %zu %zu\n", sizeof(rr_operator), sizeof(rr_build_opts), sizeof(rr_solve_info),
+             offsetof(rr_operator, bandwidth), offsetof(rr_build_opts, rho));
+      return 0; }
+    '''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    sizes = list(map(int, out))
+    assert sizes[0] == ctypes.sizeof(lib.rr_operator)
+    assert sizes[1] == ctypes.sizeof(lib.rr_build_opts)
+    assert sizes[2] == ctypes.sizeof(lib.rr_solve_info)
+    assert sizes[3] == lib.rr_operator.bandwidth.offset
+    assert sizes[4] == lib.rr_build_opts.rho.offset
+
+
+def test_defaults_and_status_strings(lib):
+    o = lib.rr_build_opts_default()
+    assert (o.gamma, o.power_iters, o.max_rhs, o.restart_eta) == (8, 20, 1, 1e-2)
+    assert lib.randrand_status_str(lib.RR_OK) == "ok"
+    assert "invalid" in lib.randrand_status_str(lib.RR_ERR_INVALID_ARG)
+    assert lib.randrand_status_str(999) == "unknown status"
+
+
+def test_workspace_query_and_argument_checks(lib):
+    # host-only entry point: works without a GPU, touches no device memory
+    op = lib.rr_operator(kind=lib.RR_OP_GAUSS_KERNEL, dtype=1, n=20000, points=0x1000, dim=8,
+                         bandwidth=1.0)
+    o = lib.rr_build_opts_default()
+    o.precision = lib.RR_PREC_MIXED
+    o.max_rhs = 4
+    nbytes = lib.randrand_workspace_bytes(op, 500, o)
+    # at least Omega, Y and Q in float32 plus the k x k float64 work matrices
+    assert nbytes >= 3 * 20000 * 500 * 4 + 12 * 500 * 500 * 8
+    for bad_k in (0, 20001):
+        with pytest.raises(lib.RandRandError) as e:
+            lib.randrand_workspace_bytes(op, bad_k, o)
+        assert e.value.status == lib.RR_ERR_INVALID_ARG
+    o.max_rhs = 9
+    with pytest.raises(lib.RandRandError):
+        lib.randrand_workspace_bytes(op, 10, o)
+    o.max_rhs = 1
+    bad = lib.rr_operator(kind=lib.RR_OP_GAUSS_KERNEL, dtype=1, n=100, points=0, dim=8, bandwidth=1.0)
+    with pytest.raises(lib.RandRandError):
+        lib.randrand_workspace_bytes(bad, 10, o)
+    dense = lib.rr_operator(kind=lib.RR_OP_DENSE, dtype=0, n=100, dense=0x1000, ld=50)
+    with pytest.raises(lib.RandRandError):
+        lib.randrand_workspace_bytes(dense, 10, o)
+
+
+def test_build_rejects_bad_arguments_before_any_launch(lib):
+    op = lib.rr_operator(kind=lib.RR_OP_DENSE, dtype=0, n=100, dense=0x1000, ld=100)
+    o = lib.rr_build_opts_default()
+    for mu in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(lib.RandRandError) as e:
+            lib.randrand_build(op, mu, 10, 0, 1, o, 0x100000, 1 << 30, 0)
+        assert e.value.status == lib.RR_ERR_INVALID_ARG
+    with pytest.raises(lib.RandRandError) as e:     # misaligned workspace
+        lib.randrand_build(op, 0.0, 10, 0, 1, o, 0x100001, 1 << 30, 0)
+    assert e.value.status == lib.RR_ERR_INVALID_ARG
+    with pytest.raises(lib.RandRandError) as e:     # workspace too small
+        lib.randrand_build(op, 0.0, 10, 0, 1, o, 0x100000, 16, 0)
+    assert e.value.status == lib.RR_ERR_WORKSPACE
+    with pytest.raises(lib.RandRandError) as e:     # unknown sketch kind
+        lib.randrand_build(op, 0.0, 10, 7, 1, o, 0x100000, 1 << 30, 0)
+    assert e.value.status == lib.RR_ERR_INVALID_ARG
+
+
+def test_oracle_not_imported_by_product():
+    # the product path never imports the oracle
+    for dirpath, _, files in os.walk(os.path.join(ROOT, "paper_2509_19747_gb300")):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f

@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA library through its C ABI against the float64 oracle.
+
+Tolerances: float64 path 1e-10 relative (iterates, factors, solutions);
+float32 / bf16-mixed paths: float32 unit roundoff times the condition
+numbers involved, stated per test.  Sparse-sign patterns and seeds are
+integer work and compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import philox
+from oracle import randrand as O
+from workloads import generators as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def dense_problem(n, seed=W.SEED_DENSE, power=2.0):
+    P = W.dense_power_spectrum(n, seed=seed, power=power)
+    return P, O.DenseOp(P.A)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+# ---------------------------------------------------------------- Omega
+@pytest.mark.parametrize("n,k", [(1, 1), (37, 5), (1000, 100), (333, 64)])
+def test_gaussian_omega_fp64_matches_oracle(cuda_lib, n, k):
+    rr = cuda_lib
+    A = dev(np.eye(n))
+    h = rr.Handle(rr.Operator.dense(A), 0.1, k, "gaussian", seed=0xABCDEF12345)
+    Om = h.export("omega").cpu().numpy()
+    ref = philox.gaussian_omega(n, k, 0xABCDEF12345)
+    assert np.max(np.abs(Om - ref)) <= 1e-14 * max(1.0, np.abs(ref).max())
+
+
+def test_gaussian_omega_bf16_matches_oracle(cuda_lib):
+    rr = cuda_lib
+    n, k = 3000, 96
+    X = W.mixture_points(n, seed=5)
+    h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), 1e-3, k, "gaussian", seed=99,
+                  precision="mixed")
+    Om = h.export("omega").cpu().numpy()
+    ref = philox.round_bf16(philox.gaussian_omega(n, k, 99))
+    diff = Om != ref
+    # float32 Box-Muller (<= a few ulp) then bf16 rounding: rare one-ulp flips
+    assert diff.mean() < 1e-3
+    ulp = np.abs(ref) * 2.0 ** -7
+    assert np.all(np.abs(Om - ref)[diff] <= ulp[diff] * 1.01)
+
+
+def test_sparse_sign_omega_bitwise(cuda_lib):
+    rr = cuda_lib
+    n, k = 2000, 40
+    A = dev(np.eye(n))
+    h = rr.Handle(rr.Operator.dense(A), 0.5, k, "sparse_sign", seed=0x52523, gamma=8)
+    Om = h.export("omega").cpu().numpy()
+    ref = philox.sparse_sign_omega_dense(n, k, 8, 0x52523)
+    assert np.array_equal(Om, ref)
+
+
+# ------------------------------------------------------- build products
+@pytest.mark.parametrize("n,k,variant", [(300, 30, "C"), (517, 37, "C"), (517, 37, "R"),
+                                         (129, 1, "C"), (64, 64, "C")])
+def test_build_factors_fp64(cuda_lib, n, k, variant):
+    rr = cuda_lib
+    P, op = dense_problem(n)
+    mu = 1e-4
+    h = rr.Handle(rr.Operator.dense(dev(P.A)), mu, k, "gaussian", seed=11, variant=variant)
+    bd = O.build(op, mu, k, "gaussian", seed=11, variant=variant)
+    Q = h.export("Q").cpu().numpy()
+    R = h.export("R").cpu().numpy()
+    cond = np.linalg.cond(bd.R)
+    # R with positive diagonal is unique: CholeskyQR2 vs Householder
+    assert rel(R, bd.R) <= 1e-15 * cond * 100
+    assert rel(Q, bd.Q) <= 1e-15 * cond * 100
+    assert np.linalg.norm(Q.T @ Q - np.eye(k), 2) <= 1e-13
+    tau, nE, lmax = h.scalars()
+    assert nE == pytest.approx(bd.normE, rel=1e-9)
+    assert tau == pytest.approx(bd.tau, rel=1e-9)
+    if variant == "C":
+        G = h.export("G").cpu().numpy()
+        assert rel(G, bd.G) <= 1e-15 * cond ** 2 * 100
+        assert lmax == pytest.approx(bd.lam_max, rel=1e-9)
+
+
+@pytest.mark.parametrize("variant", ["C", "R"])
+def test_preconditioner_apply_fp64(cuda_lib, variant):
+    rr = cuda_lib
+    n, k, mu = 401, 41, 1e-3
+    P, op = dense_problem(n)
+    h = rr.Handle(rr.Operator.dense(dev(P.A)), mu, k, "gaussian", seed=3, variant=variant, max_rhs=3)
+    bd = O.build(op, mu, k, "gaussian", seed=3, variant=variant)
+    r = np.random.default_rng(0).standard_normal((n, 3))
+    z = h.apply(dev(r)).cpu().numpy()
+    ref = bd.apply_P(r) if variant == "C" else bd.apply_B(r)
+    assert rel(z, ref) <= 1e-11
+    w = h.matvec(dev(r)).cpu().numpy()
+    assert rel(w, P.A @ r + mu * r) <= 1e-14
+
+
+# ---------------------------------------------------------------- solves
+@pytest.mark.parametrize("variant", ["C", "R"])
+@pytest.mark.parametrize("n,k,m", [(300, 30, 1), (777, 61, 3), (1025, 100, 2)])
+def test_solve_fp64_iteration_level(cuda_lib, variant, n, k, m):
+    """Same seeds, same restarts: after a fixed budget of inner iterations the
+    GPU iterate equals the oracle iterate to 1e-10 (iteration-level parity)."""
+    rr = cuda_lib
+    P, op = dense_problem(n)
+    mu = 1e-4
+    B = W.gaussian_rhs(n, m, 5)
+    h = rr.Handle(rr.Operator.dense(dev(P.A)), mu, k, "gaussian", seed=5, variant=variant, max_rhs=m)
+    bd = O.build(op, mu, k, "gaussian", seed=5, variant=variant)
+    for budget in (3, 12):
+        x, status, infos = h.solve(dev(B), rtol=1e-14, maxit=budget)
+        xo, oinfo = O.solve(bd, B, rtol=1e-14, maxit=budget)
+        assert status == rr.RR_ERR_MAXIT
+        assert [i["inner_iters"] for i in infos] == [i.inner_iters for i in oinfo]
+        assert rel(x.cpu().numpy(), xo) <= 1e-10
+
+
+@pytest.mark.parametrize("variant", ["C", "R"])
+def test_solve_fp64_config_dense_full_size(cuda_lib, variant):
+    """n=2000, lambda_i = i^-2, mu=1e-4, k=100, CG to rtol 1e-8: the oracle-measured
+    float64 residual meets rtol; a tighter parity solve matches x* = A_mu^-1 b."""
+    rr = cuda_lib
+    n, k, mu = 2000, 100, 1e-4
+    P, op = dense_problem(n)
+    b = W.gaussian_rhs(n, 1, W.SEED_DENSE)
+    h = rr.Handle(rr.Operator.dense(dev(P.A)), mu, k, "gaussian", seed=W.SEED_DENSE, variant=variant)
+    x, status, infos = h.solve(dev(b), rtol=1e-8)
+    assert status == rr.RR_OK
+    xn = x.cpu().numpy()
+    assert O.true_rel_residual(op, mu, xn, b)[0] <= 1e-8
+    bd = O.build(op, mu, k, "gaussian", seed=W.SEED_DENSE, variant=variant)
+    xo, oinfo = O.solve(bd, b, rtol=1e-8)
+    assert abs(infos[0]["inner_iters"] - oinfo[0].inner_iters) <= 3
+    xs = O.exact_solve(op, mu, b)
+    x2, status, _ = h.solve(dev(b), rtol=1e-13, maxit=5000)
+    assert rel(x2.cpu().numpy(), xs) <= 1e-10
+
+
+def test_solve_initial_guess_and_zero_rhs(cuda_lib):
+    rr = cuda_lib
+    n, k, mu = 300, 20, 1e-3
+    P, op = dense_problem(n)
+    h = rr.Handle(rr.Operator.dense(dev(P.A)), mu, k, "gaussian", seed=1, max_rhs=2)
+    b = W.gaussian_rhs(n, 2, 1)
+    b[:, 1] = 0.0                                   # a zero column converges at once
+    xs = O.exact_solve(op, mu, b)
+    x0 = xs + 1e-3 * np.random.default_rng(1).standard_normal(xs.shape)
+    x, status, infos = h.solve(dev(b), rtol=1e-10, x0=dev(x0))
+    assert status == rr.RR_OK
+    xn = x.cpu().numpy()
+    assert np.all(xn[:, 1] == 0.0)
+    assert O.true_rel_residual(op, mu, xn[:, :1], b[:, :1])[0] <= 1e-10
+
+
+def test_maxit_returns_last_iterate(cuda_lib):
+    rr = cuda_lib
+    n, k, mu = 500, 5, 1e-6
+    P, op = dense_problem(n)
+    h = rr.Handle(rr.Operator.dense(dev(P.A)), mu, k, "gaussian", seed=2)
+    b = W.gaussian_rhs(n, 1, 2)[:, 0]
+    x, status, infos = h.solve(dev(b), rtol=1e-14, maxit=4)
+    assert status == rr.RR_ERR_MAXIT and infos[0]["status"] == rr.RR_ERR_MAXIT
+    assert infos[0]["inner_iters"] == 4
+    r = O.true_rel_residual(op, mu, x.cpu().numpy(), b)[0]
+    assert r == pytest.approx(infos[0]["rel_residual"], rel=1e-8)
+    assert r < 1.0
+
+
+def test_invalid_solve_arguments(cuda_lib):
+    rr = cuda_lib
+    P, op = dense_problem(50)
+    h = rr.Handle(rr.Operator.dense(dev(P.A)), 0.1, 5, "gaussian", seed=1)
+    b = torch.zeros(50, dtype=torch.float64, device="cuda")
+    with pytest.raises(rr.RandRandError):
+        rr.randrand_solve(h.h, b.data_ptr(), 2, 50, b.data_ptr(), 50, 0, 1e-6, 10)  # nrhs > max_rhs
+    with pytest.raises(rr.RandRandError):
+        rr.randrand_solve(h.h, b.data_ptr(), 1, 49, b.data_ptr(), 50, 0, 1e-6, 10)  # ld < n
+    with pytest.raises(rr.RandRandError):
+        rr.randrand_solve(h.h, b.data_ptr(), 1, 50, b.data_ptr(), 50, 0, -1.0, 10)
+
+
+# --------------------------------------------------------- kernel operator
+def test_kernel_operator_fp64_solve(cuda_lib):
+    rr = cuda_lib
+    n, k, mu = 700, 40, 1e-3
+    X = W.mixture_points(n, seed=21)
+    op = O.GaussKernelOp(X)
+    B = W.gaussian_rhs(n, 2, 21)
+    h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=21, max_rhs=2)
+    w = h.matvec(dev(B)).cpu().numpy()
+    assert rel(w, op.matmat(B) + mu * B) <= 1e-13
+    bd = O.build(op, mu, k, "gaussian", seed=21)
+    assert h.scalars()[0] == pytest.approx(bd.tau, rel=1e-8)
+    x, status, infos = h.solve(dev(B), rtol=1e-12)
+    assert status == rr.RR_OK
+    assert rel(x.cpu().numpy(), O.exact_solve(op, mu, B)) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+def test_kernel_operator_low_precision(cuda_lib, precision):
+    """bf16 sketch + float32 iterations + float64 refinement reaches the
+    float64 oracle solution; the plain float32 path reaches float32-level
+    residuals."""
+    rr = cuda_lib
+    n, k, mu = 2500, 100, 1e-3
+    X = W.mixture_points(n, seed=22)
+    op = O.GaussKernelOp(X)
+    B = W.gaussian_rhs(n, 4, 22)
+    h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=22,
+                  precision=precision, max_rhs=4)
+    xs = O.exact_solve(op, mu, B)
+    if precision == "mixed":
+        x, status, infos = h.solve(dev(B), rtol=1e-6)
+        assert status == rr.RR_OK
+        assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), B) <= 1e-6)
+        x, status, infos = h.solve(dev(B), rtol=1e-10)
+        assert status == rr.RR_OK
+        assert rel(x.cpu().numpy(), xs) <= 1e-5
+    else:
+        x, status, infos = h.solve(dev(B), rtol=1e-4)
+        assert status == rr.RR_OK
+        assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), B) <= 2e-4)
+
+
+def test_kernel_sketch_matches_oracle_fp32(cuda_lib):
+    """Y_mu = K_mu Omega with float32 kernel tiles: basis and tau close to the oracle."""
+    rr = cuda_lib
+    n, k, mu = 1500, 64, 1e-3
+    X = W.mixture_points(n, seed=23)
+    op = O.GaussKernelOp(X)
+    h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=23, precision="fp32")
+    bd = O.build(op, mu, k, "gaussian", seed=23, omega_precision="fp32")
+    R = h.export("R").cpu().numpy()
+    cond = np.linalg.cond(bd.R)
+    assert rel(R, bd.R) <= 1e-6 * cond * 10
+    tau, nE, lmax = h.scalars()
+    assert tau == pytest.approx(bd.tau, rel=1e-3)
+
+
+# ------------------------------------------------------------------- CSR
+@pytest.mark.parametrize("sketch", ["sparse_sign", "gaussian"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_csr_solve(cuda_lib, sketch, precision):
+    rr = cuda_lib
+    C = W.diffusion_csr(side=40, seed=31, corr_len=4.0)
+    op = O.CsrOp(C.rowptr, C.colidx, C.vals, C.n)
+    mu, k = 1e-6, 32
+    b = W.gaussian_rhs(C.n, 1, 31)
+    vals = dev(C.vals.astype(np.float64)) if precision == "fp64" else dev(C.vals)
+    h = rr.Handle(rr.Operator.csr(dev(C.rowptr), dev(C.colidx), vals), mu, k, sketch, seed=31,
+                  precision=precision)
+    x, status, infos = h.solve(dev(b), rtol=1e-6, maxit=20000)
+    assert status == rr.RR_OK
+    assert O.true_rel_residual(op, mu, x.cpu().numpy(), b)[0] <= 1e-6
+    if precision == "fp64":
+        bd = O.build(op, mu, k, sketch, seed=31)
+        assert h.scalars()[0] == pytest.approx(bd.tau, rel=1e-8)
