@@ -9,6 +9,7 @@
 // columns.
 #include <cmath>
 
+#include "df.cuh"
 #include "rr_common.cuh"
 
 namespace rr {
@@ -33,12 +34,17 @@ __global__ void k_prepare_points(const float* __restrict__ x, int64_t n, int dim
   cn[i] = (float)(-0.5 * s2);
 }
 
+__global__ void k_point_norms(const float* __restrict__ x, int64_t n, int dim,
+                              float2* __restrict__ pn);
+
 void prepare_kernel_points(OpDev& op, cudaStream_t st) {
   // exp(-|xi - xj|^2 / (2h^2)) = exp2(xs_i . xs_j + cn_i + cn_j) with
   // xs = x sqrt(log2 e) / h and cn = -|xs|^2 / 2.
   const double scale = sqrt(1.4426950408889634) / op.bw;
   k_prepare_points<<<(unsigned)cdiv(op.n, 256), 256, 0, st>>>(op.points, op.n, op.dim, scale,
                                                               op.xs, op.cn);
+  if (op.pn)
+    k_point_norms<<<(unsigned)cdiv(op.n, 256), 256, 0, st>>>(op.points, op.n, op.dim, op.pn);
 }
 
 // ================================================================ dense
@@ -98,62 +104,84 @@ constexpr int kKmvRows = 128;   // rows per CTA (one thread per row)
 constexpr int kKmvTile = 128;   // points staged per shared-memory tile
 constexpr int kMaxDim = 16;
 
-template <int MP>
+// Each thread owns kRpt rows; the point tile is staged in shared memory and
+// read with broadcast vector loads.  Per entry: dim FMA (dot product) + 1
+// add + 1 MUFU ex2 + MP FMA (accumulate), all on the float32 pipes.
+constexpr int kRpt = 2;
+
+template <int MP, bool DIM8>
 __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_f32(const float* __restrict__ xs,
                                                           const float* __restrict__ cn,
                                                           int64_t n, int dim,
                                                           int64_t cols_per_split,
                                                           const float* __restrict__ V,
                                                           float* __restrict__ part) {
-  __shared__ float sx[kKmvTile * kMaxDim];
+  __shared__ __align__(16) float sx[kKmvTile * kMaxDim];
   __shared__ float sc[kKmvTile];
-  __shared__ float sv[kKmvTile * MP];
-  const int64_t i = (int64_t)blockIdx.x * kKmvRows + threadIdx.x;
-  const bool live = i < n;
-  float xi[kMaxDim];
+  __shared__ __align__(16) float sv[kKmvTile * MP];
+  constexpr int D = DIM8 ? 8 : kMaxDim;
+  float xi[kRpt][D];
+  float ci[kRpt];
+  float acc[kRpt][MP];
+  int64_t rows[kRpt];
 #pragma unroll
-  for (int d = 0; d < kMaxDim; ++d) xi[d] = (live && d < dim) ? xs[i * dim + d] : 0.f;
-  const float ci = live ? cn[i] : 0.f;
-  float acc[MP];
+  for (int r = 0; r < kRpt; ++r) {
+    rows[r] = (int64_t)blockIdx.x * (kKmvRows * kRpt) + r * kKmvRows + threadIdx.x;
+    const bool live = rows[r] < n;
 #pragma unroll
-  for (int c = 0; c < MP; ++c) acc[c] = 0.f;
+    for (int d = 0; d < D; ++d) xi[r][d] = (live && d < dim) ? xs[rows[r] * dim + d] : 0.f;
+    ci[r] = live ? cn[rows[r]] : -1e30f;   // dead rows: exp2 -> 0
+#pragma unroll
+    for (int c = 0; c < MP; ++c) acc[r][c] = 0.f;
+  }
   const int64_t j0 = (int64_t)blockIdx.y * cols_per_split;
   int64_t j1 = j0 + cols_per_split;
   if (j1 > n) j1 = n;
   for (int64_t jt = j0; jt < j1; jt += kKmvTile) {
     const int cnt = (int)((j1 - jt < kKmvTile) ? (j1 - jt) : kKmvTile);
     __syncthreads();
-    for (int e = threadIdx.x; e < cnt * dim; e += kKmvRows) sx[(e / dim) * kMaxDim + e % dim] = xs[jt * dim + e];
+    for (int e = threadIdx.x; e < cnt * dim; e += kKmvRows) sx[(e / dim) * D + e % dim] = xs[jt * dim + e];
     for (int e = threadIdx.x; e < cnt; e += kKmvRows) sc[e] = cn[jt + e];
     for (int e = threadIdx.x; e < cnt * MP; e += kKmvRows) sv[e] = V[jt * MP + e];
     __syncthreads();
-    if (dim == 8) {
-      for (int jj = 0; jj < cnt; ++jj) {
-        const float* xj = sx + jj * kMaxDim;
-        float a = ci + sc[jj];
+#pragma unroll 2
+    for (int jj = 0; jj < cnt; ++jj) {
+      float xj[D];
+      if (DIM8) {
+        const float4 a = reinterpret_cast<const float4*>(sx + jj * 8)[0];
+        const float4 b = reinterpret_cast<const float4*>(sx + jj * 8)[1];
+        xj[0] = a.x; xj[1] = a.y; xj[2] = a.z; xj[3] = a.w;
+        xj[4] = b.x; xj[5] = b.y; xj[6] = b.z; xj[7] = b.w;
+      } else {
 #pragma unroll
-        for (int d = 0; d < 8; ++d) a = fmaf(xi[d], xj[d], a);
-        const float kij = ex2_approx(a);
-#pragma unroll
-        for (int c = 0; c < MP; ++c) acc[c] = fmaf(kij, sv[jj * MP + c], acc[c]);
+        for (int d = 0; d < D; ++d) xj[d] = sx[jj * D + d];
       }
-    } else {
-      for (int jj = 0; jj < cnt; ++jj) {
-        const float* xj = sx + jj * kMaxDim;
-        float a = ci + sc[jj];
+      float vj[MP];
+      if (MP == 4) {
+        const float4 v4 = reinterpret_cast<const float4*>(sv)[jj];
+        vj[0] = v4.x; vj[1] = v4.y; vj[2] = v4.z; vj[3] = v4.w;
+      } else {
 #pragma unroll
-        for (int d = 0; d < kMaxDim; ++d)
-          if (d < dim) a = fmaf(xi[d], xj[d], a);
+        for (int c = 0; c < MP; ++c) vj[c] = sv[jj * MP + c];
+      }
+      const float cj = sc[jj];
+#pragma unroll
+      for (int r = 0; r < kRpt; ++r) {
+        float a = ci[r] + cj;
+#pragma unroll
+        for (int d = 0; d < D; ++d) a = fmaf(xi[r][d], xj[d], a);
         const float kij = ex2_approx(a);
 #pragma unroll
-        for (int c = 0; c < MP; ++c) acc[c] = fmaf(kij, sv[jj * MP + c], acc[c]);
+        for (int c = 0; c < MP; ++c) acc[r][c] = fmaf(kij, vj[c], acc[r][c]);
       }
     }
   }
-  if (live) {
-    float* out = part + ((int64_t)blockIdx.y * n + i) * MP;
 #pragma unroll
-    for (int c = 0; c < MP; ++c) out[c] = acc[c];
+  for (int r = 0; r < kRpt; ++r) {
+    if (rows[r] >= n) continue;
+    float* out = part + ((int64_t)blockIdx.y * n + rows[r]) * MP;
+#pragma unroll
+    for (int c = 0; c < MP; ++c) out[c] = acc[r][c];
   }
 }
 
@@ -204,6 +232,129 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_f64(const float* __restr
   }
 }
 
+// float64-accurate product on the float32 pipes (double-float arithmetic):
+//   d2_ij = |p_i|^2 + |p_j|^2 - 2 p_i . p_j   (p_i . p_j by TwoProd/TwoSum)
+//   t = -d2 log2(e) / (2 h^2) = k + j/64 + r,  |r| <= 1/128
+//   K_ij = 2^k * T[j] * exp(r ln 2),  T[j] = 2^(j/64) from a 65-entry table,
+//   exp(z) = 1 + z + z^2/2 + z^3/6 + z^4/24 + z^5/120 for |z| <= ln2/128
+//   (truncation < 5e-14), evaluated with the low-order terms in float.
+// Entries below 2^-100 are flushed to zero.  Relative error per entry
+// ~1e-13; the sums over j are accumulated in double-float.
+template <int MP>
+__global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df(const float* __restrict__ x,
+                                                         const float2* __restrict__ pn,
+                                                         int64_t n, int dim, float sch, float scl,
+                                                         int64_t cols_per_split,
+                                                         const double* __restrict__ V,
+                                                         double* __restrict__ part) {
+  __shared__ __align__(16) float sx[kKmvTile * kMaxDim];
+  __shared__ float2 spn[kKmvTile];
+  __shared__ float2 sv[kKmvTile * MP];
+  __shared__ float2 tab[65];
+  if (threadIdx.x < 65) {
+    const double t = exp2((double)((int)threadIdx.x - 32) / 64.0);
+    const float h = (float)t;
+    tab[threadIdx.x] = make_float2(h, (float)(t - (double)h));
+  }
+  const int64_t i = (int64_t)blockIdx.x * kKmvRows + threadIdx.x;
+  const bool live = i < n;
+  float xi[kMaxDim];
+#pragma unroll
+  for (int d = 0; d < kMaxDim; ++d) xi[d] = (live && d < dim) ? x[i * dim + d] : 0.f;
+  const float2 pni = live ? pn[i] : make_float2(0.f, 0.f);
+  df acc[MP];
+#pragma unroll
+  for (int c = 0; c < MP; ++c) acc[c] = {0.f, 0.f};
+  const float kLn2h = 0.693147182464599609375f;          // ln 2 split: hi + lo
+  const float kLn2l = -1.904654323148236e-09f;
+  const int64_t j0 = (int64_t)blockIdx.y * cols_per_split;
+  int64_t j1 = j0 + cols_per_split;
+  if (j1 > n) j1 = n;
+  for (int64_t jt = j0; jt < j1; jt += kKmvTile) {
+    const int cnt = (int)((j1 - jt < kKmvTile) ? (j1 - jt) : kKmvTile);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * dim; e += kKmvRows) sx[(e / dim) * kMaxDim + e % dim] = x[jt * dim + e];
+    for (int e = threadIdx.x; e < cnt; e += kKmvRows) spn[e] = pn[jt + e];
+    for (int e = threadIdx.x; e < cnt * MP; e += kKmvRows) {
+      const df v = df_from_double(V[jt * MP + e]);
+      sv[e] = make_float2(v.h, v.l);
+    }
+    __syncthreads();
+    for (int jj = 0; jj < cnt; ++jj) {
+      const float* xj = sx + jj * kMaxDim;
+      // p_i . p_j in double-float
+      df c = two_prod(xi[0], xj[0]);
+#pragma unroll
+      for (int d = 1; d < kMaxDim; ++d) {
+        if (d < dim) {
+          const df t = two_prod(xi[d], xj[d]);
+          const df s2 = two_sum(c.h, t.h);
+          c = {s2.h, __fadd_rn(__fadd_rn(c.l, t.l), s2.l)};
+        }
+      }
+      const float2 pnj = spn[jj];
+      df a = two_sum(pni.x, pnj.x);
+      a.l = __fadd_rn(a.l, __fadd_rn(pni.y, pnj.y));
+      df b = two_sum(a.h, -2.f * c.h);
+      b.l = __fadd_rn(b.l, __fsub_rn(a.l, 2.f * c.l));
+      const df d2 = fast_two_sum(b.h, b.l);
+      // t = -d2 * s  (s = log2(e) / (2 h^2) as sch + scl)
+      const float th = -__fmul_rn(d2.h, sch);
+      if (!(th > -100.f)) continue;                 // K < 2^-100: below float64 resolution
+      float tl = -__fmaf_rn(d2.h, sch, th);          // exact low part of -d2.h * sch
+      tl = __fmaf_rn(-d2.h, scl, tl);
+      tl = __fmaf_rn(-d2.l, sch, tl);
+      const float kf = rintf(th);
+      const float f = __fsub_rn(th, kf);             // exact, |f| <= 1/2
+      const float jf = rintf(f * 64.f);
+      const float r = __fsub_rn(f, jf * 0.015625f);  // exact, |r| <= 1/128
+      const df rr = two_sum(r, tl);
+      const df z = df_mul(rr, df{kLn2h, kLn2l});
+      const float zh = z.h;
+      const float p3 = zh * zh * zh * (0.16666667f + zh * (0.041666668f + zh * 0.0083333338f));
+      df q = two_prod(zh, zh);
+      q.h *= 0.5f;
+      q.l = __fmaf_rn(zh, z.l, q.l * 0.5f);
+      const df ah = fast_two_sum(1.f, zh);
+      const df bh = two_sum(ah.h, q.h);
+      const float low = __fadd_rn(__fadd_rn(__fadd_rn(ah.l, bh.l), __fadd_rn(z.l, q.l)), p3);
+      const df E = fast_two_sum(bh.h, low);
+      const float2 tj = tab[(int)jf + 32];
+      df K = df_mul(df{tj.x, tj.y}, E);
+      const float sc = __int_as_float(((int)kf + 127) << 23);   // 2^k, k in [-100, 0]
+      K.h *= sc;
+      K.l *= sc;
+#pragma unroll
+      for (int cc = 0; cc < MP; ++cc) {
+        const float2 v = sv[jj * MP + cc];
+        df pr = two_prod(K.h, v.x);
+        pr.l = __fmaf_rn(K.h, v.y, pr.l);
+        pr.l = __fmaf_rn(K.l, v.x, pr.l);
+        const df s2 = two_sum(acc[cc].h, pr.h);
+        acc[cc] = {s2.h, __fadd_rn(acc[cc].l, __fadd_rn(s2.l, pr.l))};
+      }
+    }
+  }
+  if (live) {
+    double* out = part + ((int64_t)blockIdx.y * n + i) * MP;
+#pragma unroll
+    for (int cc = 0; cc < MP; ++cc) out[cc] = df_to_double(acc[cc]);
+  }
+}
+
+__global__ void k_point_norms(const float* __restrict__ x, int64_t n, int dim,
+                              float2* __restrict__ pn) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s2 = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    const double v = (double)x[i * dim + d];
+    s2 = fma(v, v, s2);
+  }
+  const df p = df_from_double(s2);
+  pn[i] = make_float2(p.h, p.l);
+}
+
 template <typename T>
 __global__ void k_sum_splits(const T* __restrict__ part, int nsplit, int64_t n, int mp,
                              double mu, const T* __restrict__ V, T* __restrict__ W) {
@@ -229,8 +380,17 @@ size_t op_matvec_scratch_elems(const OpDev& op, int mp) {
   return (size_t)kernel_nsplit(op.n) * (size_t)op.n * (size_t)mp;
 }
 
+// Inside a stream capture a plain event record only orders the capture; the
+// External flag makes it a real event-record node of the graph, so that the
+// elapsed time between the pair can be read after each replay.
 static inline void rec(const cudaEvent_t* ev, int i, cudaStream_t st) {
-  if (ev) cudaEventRecord(ev[i], st);
+  if (!ev) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(ev[i], st);
 }
 
 template <typename T>
@@ -242,14 +402,19 @@ void kernel_mv<float>(const OpDev& op, double mu, const float* V, float* W, int 
                       cudaStream_t st, const cudaEvent_t* ev) {
   const int ns = kernel_nsplit(op.n);
   const int64_t cps = cdiv(cdiv(op.n, ns), kKmvTile) * kKmvTile;
-  dim3 grid((unsigned)cdiv(op.n, kKmvRows), (unsigned)ns);
+  dim3 grid((unsigned)cdiv(op.n, kKmvRows * kRpt), (unsigned)ns);
   rec(ev, 0, st);
+  const bool d8 = op.dim == 8;
+#define RR_KMV(MPV)                                                                                  \
+  if (d8) k_kernel_mv_f32<MPV, true><<<grid, kKmvRows, 0, st>>>(op.xs, op.cn, op.n, op.dim, cps, V, part); \
+  else k_kernel_mv_f32<MPV, false><<<grid, kKmvRows, 0, st>>>(op.xs, op.cn, op.n, op.dim, cps, V, part);
   switch (mp) {
-    case 1: k_kernel_mv_f32<1><<<grid, kKmvRows, 0, st>>>(op.xs, op.cn, op.n, op.dim, cps, V, part); break;
-    case 2: k_kernel_mv_f32<2><<<grid, kKmvRows, 0, st>>>(op.xs, op.cn, op.n, op.dim, cps, V, part); break;
-    case 4: k_kernel_mv_f32<4><<<grid, kKmvRows, 0, st>>>(op.xs, op.cn, op.n, op.dim, cps, V, part); break;
-    default: k_kernel_mv_f32<8><<<grid, kKmvRows, 0, st>>>(op.xs, op.cn, op.n, op.dim, cps, V, part); break;
+    case 1: RR_KMV(1) break;
+    case 2: RR_KMV(2) break;
+    case 4: RR_KMV(4) break;
+    default: RR_KMV(8) break;
   }
+#undef RR_KMV
   rec(ev, 1, st);
   k_sum_splits<float><<<(unsigned)cdiv(op.n * mp, 256), 256, 0, st>>>(part, ns, op.n, mp, mu, V, W);
 }
@@ -262,6 +427,20 @@ void kernel_mv<double>(const OpDev& op, double mu, const double* V, double* W, i
   const double inv2h2 = 1.0 / (2.0 * op.bw * op.bw);
   dim3 grid((unsigned)cdiv(op.n, kKmvRows), (unsigned)ns);
   rec(ev, 0, st);
+  if (op.f64_df) {
+    const double s64 = 1.4426950408889634 * inv2h2;
+    const float sch = (float)s64;
+    const float scl = (float)(s64 - (double)sch);
+    switch (mp) {
+      case 1: k_kernel_mv_df<1><<<grid, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, cps, V, part); break;
+      case 2: k_kernel_mv_df<2><<<grid, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, cps, V, part); break;
+      case 4: k_kernel_mv_df<4><<<grid, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, cps, V, part); break;
+      default: k_kernel_mv_df<8><<<grid, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, cps, V, part); break;
+    }
+    rec(ev, 1, st);
+    k_sum_splits<double><<<(unsigned)cdiv(op.n * mp, 256), 256, 0, st>>>(part, ns, op.n, mp, mu, V, W);
+    return;
+  }
   switch (mp) {
     case 1: k_kernel_mv_f64<1><<<grid, kKmvRows, 0, st>>>(op.points, op.n, op.dim, inv2h2, cps, V, part); break;
     case 2: k_kernel_mv_f64<2><<<grid, kKmvRows, 0, st>>>(op.points, op.n, op.dim, inv2h2, cps, V, part); break;
@@ -302,40 +481,9 @@ void op_matvec(const OpDev& op, double mu, const T* V, T* W, int mp, T* scratch,
 }
 
 // ==================================================== sketch Y = A_mu Omega
-// Gaussian kernel: CTA tile 64 rows x 128 sketch columns; the 64 x 32 block
-// of K for each step of the reduction is generated in shared memory and
-// multiplied by the staged 32 x 128 block of Omega.
-template <typename T>
-struct KGen;
-
-template <>
-struct KGen<float> {
-  // float path: exp2(xs_i . xs_j + cn_i + cn_j)
-  static __device__ __forceinline__ float entry(const OpDev& op, int64_t i, int64_t j, bool bf16) {
-    float a = op.cn[i] + op.cn[j];
-    const float* xi = op.xs + i * op.dim;
-    const float* xj = op.xs + j * op.dim;
-    for (int d = 0; d < op.dim; ++d) a = fmaf(xi[d], xj[d], a);
-    float v = ex2_approx(a);
-    if (bf16) v = __bfloat162float(__float2bfloat16_rn(v));
-    return v;
-  }
-};
-
-template <>
-struct KGen<double> {
-  static __device__ __forceinline__ double entry(const OpDev& op, int64_t i, int64_t j, bool) {
-    double d2 = 0.0;
-    const float* xi = op.points + i * op.dim;
-    const float* xj = op.points + j * op.dim;
-    for (int d = 0; d < op.dim; ++d) {
-      const double df = (double)xi[d] - (double)xj[d];
-      d2 = fma(df, df, d2);
-    }
-    return exp(-d2 / (2.0 * op.bw * op.bw));
-  }
-};
-
+// Gaussian kernel (float32 cores): CTA tile 64 rows x 128 sketch columns; the
+// 64 x 32 block of K of each reduction step is generated in shared memory
+// from staged points and multiplied by the staged 32 x 128 block of Omega.
 template <typename T>
 __global__ void __launch_bounds__(256) k_kernel_sketch(OpDev op, double mu,
                                                        const T* __restrict__ Om, int k,
@@ -343,25 +491,62 @@ __global__ void __launch_bounds__(256) k_kernel_sketch(OpDev op, double mu,
   constexpr int BM = 64, BN = 128, BK = 32;
   __shared__ T Ks[BK][BM + 1];
   __shared__ T Os[BK][BN];
+  __shared__ float Xi[BM][kMaxDim + 1];
+  __shared__ float Xj[BK][kMaxDim + 1];
+  __shared__ float Ci[BM], Cj[BK];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const int64_t i0 = (int64_t)blockIdx.y * BM;
   const int c0 = blockIdx.x * BN;
   const int64_t n = op.n;
+  const int dim = op.dim;
+  // float path: xs / cn (exp2 form); float64 path: raw points
+  const float* P = (sizeof(T) == 4) ? op.xs : op.points;
+  for (int e = tid; e < BM * dim; e += 256) {
+    const int r = e / dim, d = e % dim;
+    Xi[r][d] = (i0 + r < n) ? P[(i0 + r) * dim + d] : 0.f;
+  }
+  if (sizeof(T) == 4)
+    for (int r = tid; r < BM; r += 256) Ci[r] = (i0 + r < n) ? op.cn[i0 + r] : 0.f;
   T acc[4][8];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 8; ++b) acc[a][b] = (T)0;
+  const double inv2h2 = 1.0 / (2.0 * op.bw * op.bw);
   for (int64_t j0 = 0; j0 < n; j0 += BK) {
-    for (int e = tid; e < BM * BK; e += 256) {
-      const int r = e / BK, c = e % BK;
-      const int64_t gi = i0 + r, gj = j0 + c;
-      Ks[c][r] = (gi < n && gj < n) ? KGen<T>::entry(op, gi, gj, bf16 != 0) : (T)0;
+    __syncthreads();
+    for (int e = tid; e < BK * dim; e += 256) {
+      const int r = e / dim, d = e % dim;
+      Xj[r][d] = (j0 + r < n) ? P[(j0 + r) * dim + d] : 0.f;
     }
+    if (sizeof(T) == 4)
+      for (int r = tid; r < BK; r += 256) Cj[r] = (j0 + r < n) ? op.cn[j0 + r] : 0.f;
     for (int e = tid; e < BK * BN; e += 256) {
       const int r = e / BN, c = e % BN;
       const int64_t gj = j0 + r;
       Os[r][c] = (gj < n && c0 + c < k) ? Om[gj * k + c0 + c] : (T)0;
+    }
+    __syncthreads();
+    for (int e = tid; e < BM * BK; e += 256) {
+      const int r = e / BK, c = e % BK;
+      T v = (T)0;
+      if (i0 + r < n && j0 + c < n) {
+        if (sizeof(T) == 4) {
+          float a = Ci[r] + Cj[c];
+          for (int d = 0; d < dim; ++d) a = fmaf(Xi[r][d], Xj[c][d], a);
+          float kv = ex2_approx(a);
+          if (bf16) kv = __bfloat162float(__float2bfloat16_rn(kv));
+          v = (T)kv;
+        } else {
+          double d2 = 0.0;
+          for (int d = 0; d < dim; ++d) {
+            const double df_ = (double)Xi[r][d] - (double)Xj[c][d];
+            d2 = fma(df_, df_, d2);
+          }
+          v = (T)exp(-d2 * inv2h2);
+        }
+      }
+      Ks[c][r] = v;
     }
     __syncthreads();
 #pragma unroll 8
@@ -376,7 +561,6 @@ __global__ void __launch_bounds__(256) k_kernel_sketch(OpDev op, double mu,
 #pragma unroll
         for (int y = 0; y < 8; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int x = 0; x < 4; ++x) {

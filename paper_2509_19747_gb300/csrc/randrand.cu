@@ -25,7 +25,7 @@ constexpr int kMaxRestarts = 400;
 
 enum Region {
   R_OM, R_OMB, R_SSC, R_SSS, R_Y, R_Q, R_KK, R_KKT, R_GPART, R_CHOLW, R_STATUS, R_XS, R_CN,
-  R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT, R_CS, R_NORMS, R_NREG
+  R_PN, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT, R_CS, R_NORMS, R_NREG
 };
 
 struct Layout {
@@ -68,6 +68,7 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_STATUS] = 64;
   L.size[R_XS] = (A.kind == RR_OP_GAUSS_KERNEL) ? n * (size_t)A.dim * 4 : 0;
   L.size[R_CN] = (A.kind == RR_OP_GAUSS_KERNEL) ? n * 4 : 0;
+  L.size[R_PN] = (A.kind == RR_OP_GAUSS_KERNEL) ? n * 8 : 0;
   L.size[R_MVS] = op_matvec_scratch_elems(od, mp) * 8;
   L.size[R_VT] = 7 * n * (size_t)mp * ts;
   L.size[R_V64] = 4 * n * (size_t)mp * 8;
@@ -95,7 +96,7 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
   if (o.variant != RR_VARIANT_C && o.variant != RR_VARIANT_R) return RR_ERR_INVALID_ARG;
   if (o.precision < RR_PREC_FP64 || o.precision > RR_PREC_MIXED) return RR_ERR_INVALID_ARG;
   if (o.orth != RR_ORTH_CHOLQR2) return RR_ERR_UNSUPPORTED;
-  if (o.gamma < 1 || o.gamma > kMaxGammaHost || o.gamma > k) return RR_ERR_INVALID_ARG;
+  if (o.gamma < 1 || o.gamma > kMaxGammaHost) return RR_ERR_INVALID_ARG;
   if (o.power_iters < 1 || o.power_iters > 1000) return RR_ERR_INVALID_ARG;
   if (!(o.restart_eta > 0.0 && o.restart_eta < 1.0)) return RR_ERR_INVALID_ARG;
   switch (A->kind) {
@@ -208,6 +209,9 @@ void carve(rr_handle* h) {
   h->dstatus = (int*)at(R_STATUS);
   h->op.xs = (float*)at(R_XS);
   h->op.cn = (float*)at(R_CN);
+  h->op.pn = (float2*)at(R_PN);
+  // the refinement residual of the mixed path runs in double-float
+  h->op.f64_df = (h->o.precision == RR_PREC_MIXED) ? 1 : 0;
   h->mvs = at(R_MVS);
   const size_t ts = h->f64 ? 8 : 4;
   const size_t vec = (size_t)h->n * h->mp;
@@ -588,6 +592,17 @@ void iter_R(rr_handle* h, const cudaEvent_t* ev) {
 
 template <typename T>
 rr_status run_chunk(rr_handle* h) {
+  // the legacy default stream cannot be captured, and a profiled handle times
+  // each product with its own event pair: launch the iterations directly
+  if (h->st == nullptr || h->st == cudaStreamLegacy || h->prof) {
+    for (int i = 0; i < kChunk; ++i) {
+      const cudaEvent_t* ev = ev_take(h, RR_PROF_MATVEC);
+      if (h->o.variant == RR_VARIANT_C) iter_C<T>(h, ev);
+      else iter_R<T>(h, ev);
+    }
+    RR_CUDA_TRY(cudaGetLastError());
+    return RR_OK;
+  }
   if (!h->graph_ok) {
     // capture kChunk iterations once per handle; replays reuse the same
     // pointers and scalars (tau is fixed at build)
@@ -669,6 +684,18 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
   double rel[8];
   for (int c = 0; c < 8; ++c) rel[c] = 0.0;
   for (int c = m; c < mp; ++c) done[c] = true;
+  // a zero right-hand side has the solution x = 0 (whatever the guess)
+  {
+    Coefs8 keep = coefs_all(1.0);
+    bool any_zero = false;
+    for (int c = 0; c < m; ++c)
+      if (bn2[c] == 0.0) {
+        keep.v[c] = 0.0;
+        done[c] = true;
+        any_zero = true;
+      }
+    if (any_zero) axpby<double, double, double>(X, keep, nullptr, coefs_all(0.0), X, n, mp, st);
+  }
   const int mv_per_iter = 1;
   for (int restart = 0; restart <= kMaxRestarts; ++restart) {
     if (restart == 0 && !x_guess) {
@@ -851,6 +878,7 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
   RR_TRY(validate(A, k, o));
   if (!(mu >= 0.0) || !std::isfinite(mu)) return RR_ERR_INVALID_ARG;
   if (sketch != RR_SKETCH_GAUSSIAN && sketch != RR_SKETCH_SPARSE_SIGN) return RR_ERR_INVALID_ARG;
+  if (sketch == RR_SKETCH_SPARSE_SIGN && o.gamma > k) return RR_ERR_INVALID_ARG;
   if (!workspace || ((uintptr_t)workspace & 255)) return RR_ERR_INVALID_ARG;
   const Layout L = make_layout(*A, k, o);
   if (ws_bytes < L.total) return RR_ERR_WORKSPACE;

@@ -45,6 +45,10 @@ struct OpDev {
   // so that K_ij = exp2(xs_i . xs_j + cn_i + cn_j)
   float* xs;
   float* cn;
+  // float64-accurate products of the kernel operator in double-float
+  // (float32 pipes) instead of native float64; pn = |p_i|^2 as hi + lo
+  int f64_df;
+  float2* pn;
 };
 
 // Per right-hand-side Krylov scalars, device resident.

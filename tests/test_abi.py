@@ -19,8 +19,8 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2509_19747_gb300 import build as B
-    B.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_2509_19747_gb300 as rr
     return rr
 

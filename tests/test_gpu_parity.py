@@ -54,10 +54,11 @@ def test_gaussian_omega_bf16_matches_oracle(cuda_lib):
     Om = h.export("omega").cpu().numpy()
     ref = philox.round_bf16(philox.gaussian_omega(n, k, 99))
     diff = Om != ref
-    # float32 Box-Muller (<= a few ulp) then bf16 rounding: rare one-ulp flips
+    # float32 Box-Muller then bf16 rounding: rare flips of one bf16 ulp, or of
+    # the float32 absolute error sqrt(-2 ln u) * 2^-23 near zeros of cos / sin
     assert diff.mean() < 1e-3
-    ulp = np.abs(ref) * 2.0 ** -7
-    assert np.all(np.abs(Om - ref)[diff] <= ulp[diff] * 1.01)
+    tol = np.abs(ref) * 2.0 ** -7 + 6.0 * 2.0 ** -23 / np.sqrt(k)
+    assert np.all(np.abs(Om - ref) <= tol)
 
 
 def test_sparse_sign_omega_bitwise(cuda_lib):
@@ -87,7 +88,8 @@ def test_build_factors_fp64(cuda_lib, n, k, variant):
     assert rel(Q, bd.Q) <= 1e-15 * cond * 100
     assert np.linalg.norm(Q.T @ Q - np.eye(k), 2) <= 1e-13
     tau, nE, lmax = h.scalars()
-    assert nE == pytest.approx(bd.normE, rel=1e-9)
+    if k < n:                          # k = n: E = 0, both estimates are rounding noise
+        assert nE == pytest.approx(bd.normE, rel=1e-9)
     assert tau == pytest.approx(bd.tau, rel=1e-9)
     if variant == "C":
         G = h.export("G").cpu().numpy()
@@ -270,3 +272,21 @@ def test_csr_solve(cuda_lib, sketch, precision):
     if precision == "fp64":
         bd = O.build(op, mu, k, sketch, seed=31)
         assert h.scalars()[0] == pytest.approx(bd.tau, rel=1e-8)
+
+
+@pytest.mark.parametrize("n,m", [(3001, 4), (1000, 1), (777, 3)])
+def test_kernel_product_double_float_accuracy(cuda_lib, n, m):
+    """The refinement residual of the mixed path evaluates (K + mu I) v in
+    double-float on the float32 pipes: it must match the float64 oracle product
+    to ~1e-12 relative to the row magnitudes (float32 would give ~1e-7)."""
+    rr = cuda_lib
+    X = W.mixture_points(n, seed=24)
+    op = O.GaussKernelOp(X)
+    mu = 1e-3
+    h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, 16, "gaussian", seed=24,
+                  precision="mixed", max_rhs=m)
+    V = np.random.default_rng(2).standard_normal((n, m))
+    w = h.matvec(dev(V)).cpu().numpy().reshape(n, m)
+    ref = op.matmat(V) + mu * V
+    scale = op.matmat(np.abs(V)) + mu * np.abs(V)          # sum_j |K_ij v_j|
+    assert np.max(np.abs(w - ref) / scale) <= 1e-11
