@@ -266,6 +266,35 @@ rr_status randrand_apply(rr_handle* h, const double* r, double* z, int32_t m, in
  */
 rr_status randrand_matvec(rr_handle* h, const double* v, double* w, int32_t m, int64_t ld);
 
+/*
+ * Allocation-free float64-accurate Gaussian-kernel product
+ *     w = (K + mu I) v,   K_ij = exp(-|p_i - p_j|^2 / (2 h^2)),
+ * the same double-float arithmetic as the restart residual of
+ * RR_PREC_MIXED (randrand_matvec on such a handle), for callers that cannot
+ * allocate device memory at the point of use: a plugin inside a framework
+ * that owns all device memory through its own pool, a serving loop that
+ * bans allocator calls on its hot path, a process whose memory is fully
+ * committed.  The paper has no counterpart of this entry point; it exists
+ * for those callers only.
+ *   points  device, n x dim float32 row-major (dim <= 16); bandwidth h > 0.
+ *   v, w    device, n x m float64 column-major, leading dimension ld >= n;
+ *           1 <= m <= 8.  Caller-owned.
+ *   stream  cudaStream_t (as void*).  Enqueued only; does not synchronise.
+ * Scratch: a fixed 32 MiB static device array inside the library (held on
+ * every GPU that loads it until the library is unloaded), nothing else; no
+ * cudaMalloc, cudaFree or allocating library call.  Limit: with mp the
+ * smallest power of two >= m, 16 * n * mp + 8 * n + 8 * n * mp bytes
+ * (rounded up to 256-byte blocks) must fit in 32 MiB, else RR_ERR_WORKSPACE
+ * and nothing is launched.  All calls share the array: calls that overlap
+ * on the GPU race; serialise them.  Nothing in it needs to start at zero.
+ * The first call on a device looks up the array's device address (once,
+ * with that device current); make that first call before any stream
+ * capture.  Errors: RR_ERR_INVALID_ARG, RR_ERR_WORKSPACE, RR_ERR_CUDA.
+ */
+rr_status randrand_kernel_matvec_noalloc(const float* points, int64_t n, int32_t dim,
+                                         double bandwidth, double mu, const double* v, double* w,
+                                         int32_t m, int64_t ld, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

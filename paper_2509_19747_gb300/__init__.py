@@ -110,6 +110,9 @@ _SIGNATURES = [
     ("randrand_apply", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     ("randrand_profile", ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rr_profile)]),
+    ("randrand_kernel_matvec_noalloc", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p]),
     ("randrand_matvec", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
 ]
@@ -224,6 +227,15 @@ def randrand_matvec(h, v_ptr, w_ptr, m, ld) -> None:
     s = _lib().randrand_matvec(h, ctypes.c_void_p(v_ptr), ctypes.c_void_p(w_ptr), int(m), int(ld))
     if s != RR_OK:
         raise RandRandError(s, "randrand_matvec")
+
+
+def randrand_kernel_matvec_noalloc(points_ptr, n, dim, bandwidth, mu, v_ptr, w_ptr, m, ld,
+                                   stream_ptr) -> int:
+    """Status of the allocation-free kernel product (raises nothing: callers
+    check RR_OK / RR_ERR_WORKSPACE themselves)."""
+    return int(_lib().randrand_kernel_matvec_noalloc(
+        ctypes.c_void_p(points_ptr), int(n), int(dim), float(bandwidth), float(mu),
+        ctypes.c_void_p(v_ptr), ctypes.c_void_p(w_ptr), int(m), int(ld), ctypes.c_void_p(stream_ptr)))
 
 
 # ------------------------------------------------------------- conveniences

@@ -451,6 +451,28 @@ void kernel_mv<double>(const OpDev& op, double mu, const double* V, double* W, i
   k_sum_splits<double><<<(unsigned)cdiv(op.n * mp, 256), 256, 0, st>>>(part, ns, op.n, mp, mu, V, W);
 }
 
+// Float64-accurate Gaussian-kernel product in double-float with caller-given
+// scratch: pn (n float2) and nsplit x n x mp doubles of partial sums.
+void kernel_mv_df_raw(const float* points, int64_t n, int dim, double bw, double mu,
+                      const double* V, double* W, int mp, float2* pn, double* part, int nsplit,
+                      cudaStream_t st) {
+  k_point_norms<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(points, n, dim, pn);
+  const int64_t cps = cdiv(cdiv(n, nsplit), kKmvTile) * kKmvTile;
+  const double s64 = 1.4426950408889634 / (2.0 * bw * bw);
+  const float sch = (float)s64;
+  const float scl = (float)(s64 - (double)sch);
+  dim3 grid((unsigned)cdiv(n, kKmvRows), (unsigned)nsplit);
+  switch (mp) {
+    case 1: k_kernel_mv_df<1><<<grid, kKmvRows, 0, st>>>(points, pn, n, dim, sch, scl, cps, V, part); break;
+    case 2: k_kernel_mv_df<2><<<grid, kKmvRows, 0, st>>>(points, pn, n, dim, sch, scl, cps, V, part); break;
+    case 4: k_kernel_mv_df<4><<<grid, kKmvRows, 0, st>>>(points, pn, n, dim, sch, scl, cps, V, part); break;
+    default: k_kernel_mv_df<8><<<grid, kKmvRows, 0, st>>>(points, pn, n, dim, sch, scl, cps, V, part); break;
+  }
+  k_sum_splits<double><<<(unsigned)cdiv(n * mp, 256), 256, 0, st>>>(part, nsplit, n, mp, mu, V, W);
+}
+
+int kernel_mv_nsplit(int64_t n) { return kernel_nsplit(n); }
+
 template <typename T>
 void op_matvec(const OpDev& op, double mu, const T* V, T* W, int mp, T* scratch,
                cudaStream_t st, const cudaEvent_t* ev) {

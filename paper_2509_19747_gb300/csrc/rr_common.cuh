@@ -118,6 +118,10 @@ template <typename T>
 void op_matvec(const OpDev& op, double mu, const T* V, T* W, int mp, T* split_scratch,
                cudaStream_t st, const cudaEvent_t* ev = nullptr);
 size_t op_matvec_scratch_elems(const OpDev& op, int mp);
+void kernel_mv_df_raw(const float* points, int64_t n, int dim, double bw, double mu,
+                      const double* V, double* W, int mp, float2* pn, double* part, int nsplit,
+                      cudaStream_t st);
+int kernel_mv_nsplit(int64_t n);
 // Y = (A + mu I) Omega, Omega n x k row-major; bf16: round K and Omega to bf16
 template <typename T>
 void op_sketch(const OpDev& op, double mu, const T* Om, T* Y, int k, bool bf16,
