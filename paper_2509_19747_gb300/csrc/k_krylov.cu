@@ -87,68 +87,100 @@ static unsigned grid_rows(int64_t n, int rows_per_thread_block) {
 
 // ============================================================ Q^T V slabs
 // part[slab][j][c] = sum_{i in slab} Q[i][j] V[i][c]
-template <typename T>
+template <typename T, int MP>
 __global__ void __launch_bounds__(kNT) k_qt_partial(const T* __restrict__ Q, const T* __restrict__ V,
-                                                    int64_t n, int k, int mp, int rps,
+                                                    int64_t n, int k, int rps,
                                                     double* __restrict__ part,
                                                     const ColState* __restrict__ cs_gate) {
-  if (cs_gate && !any_active(cs_gate, mp)) return;
+  if (cs_gate && !any_active(cs_gate, MP)) return;
   extern __shared__ unsigned char smem_raw[];
-  T* Vs = reinterpret_cast<T*>(smem_raw);  // rps x mp
+  T* Vs = reinterpret_cast<T*>(smem_raw);  // rps x MP
   const int64_t r0 = (int64_t)blockIdx.x * rps;
   const int cnt = (int)((n - r0 < rps) ? (n - r0) : rps);
-  for (int e = threadIdx.x; e < cnt * mp; e += kNT) Vs[e] = V[r0 * mp + e];
+  for (int e = threadIdx.x; e < cnt * MP; e += kNT) Vs[e] = V[r0 * MP + e];
   __syncthreads();
-  double* out = part + (int64_t)blockIdx.x * k * mp;
+  double* out = part + (int64_t)blockIdx.x * k * MP;
   for (int j = threadIdx.x; j < k; j += kNT) {
-    T acc[8];
+    T acc[MP];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = (T)0;
+    for (int c = 0; c < MP; ++c) acc[c] = (T)0;
     const T* q = Q + r0 * k + j;
+#pragma unroll 4
     for (int i = 0; i < cnt; ++i) {
       const T qij = q[(int64_t)i * k];
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
-        if (c < mp) acc[c] = fma(qij, Vs[i * mp + c], acc[c]);
+      for (int c = 0; c < MP; ++c) acc[c] = fma(qij, Vs[i * MP + c], acc[c]);
     }
-    for (int c = 0; c < mp; ++c) out[(int64_t)j * mp + c] = (double)acc[c];
+#pragma unroll
+    for (int c = 0; c < MP; ++c) out[(int64_t)j * MP + c] = (double)acc[c];
+  }
+}
+
+template <typename T>
+static void qt_partial_launch(const T* Q, const T* V, int64_t n, int k, int mp, int nslab,
+                              double* part, const ColState* cs, cudaStream_t st) {
+  const int rps = qt_rows_per_slab(n);
+  const size_t smem = (size_t)rps * mp * sizeof(T);
+  switch (mp) {
+    case 1: k_qt_partial<T, 1><<<(unsigned)nslab, kNT, smem, st>>>(Q, V, n, k, rps, part, cs); break;
+    case 2: k_qt_partial<T, 2><<<(unsigned)nslab, kNT, smem, st>>>(Q, V, n, k, rps, part, cs); break;
+    case 4: k_qt_partial<T, 4><<<(unsigned)nslab, kNT, smem, st>>>(Q, V, n, k, rps, part, cs); break;
+    default: k_qt_partial<T, 8><<<(unsigned)nslab, kNT, smem, st>>>(Q, V, n, k, rps, part, cs); break;
   }
 }
 
 template <typename T>
 void qt_partial(const T* Q, const T* V, int64_t n, int k, int mp, int nslab, double* part,
                 cudaStream_t st) {
-  const int rps = qt_rows_per_slab(n);
-  k_qt_partial<T><<<(unsigned)nslab, kNT, (size_t)rps * mp * sizeof(T), st>>>(Q, V, n, k, mp, rps,
-                                                                             part, nullptr);
+  qt_partial_launch<T>(Q, V, n, k, mp, nslab, part, nullptr, st);
 }
 
 template <typename T>
 void qt_partial_gated(const T* Q, const T* V, int64_t n, int k, int mp, double* part,
                       const ColState* cs, cudaStream_t st) {
-  const int rps = qt_rows_per_slab(n);
-  const int nslab = qt_nslab(n);
-  k_qt_partial<T><<<(unsigned)nslab, kNT, (size_t)rps * mp * sizeof(T), st>>>(Q, V, n, k, mp, rps,
-                                                                             part, cs);
+  qt_partial_launch<T>(Q, V, n, k, mp, qt_nslab(n), part, cs, st);
 }
 
-__global__ void k_reduce_slabs(const double* __restrict__ part, int nslab, int len,
-                               double* __restrict__ out, const ColState* __restrict__ cs_gate,
-                               int mp) {
+// out[e] = c_sum * sum_b part[b][e] + c_other * other[e]; a CTA reduces 32
+// consecutive entries with 8 slab groups (fixed order: deterministic).
+__global__ void __launch_bounds__(256) k_reduce_slabs(const double* __restrict__ part, int nslab,
+                                                      int len, double c_sum,
+                                                      const double* __restrict__ other,
+                                                      double c_other, double* __restrict__ out,
+                                                      const ColState* __restrict__ cs_gate,
+                                                      int mp) {
   if (cs_gate && !any_active(cs_gate, mp)) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= len) return;
+  __shared__ double sh[8][33];
+  const int lx = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lx;
   double s = 0.0;
-  for (int b = 0; b < nslab; ++b) s += part[(int64_t)b * len + e];
-  out[e] = s;
+  if (e < len) {
+#pragma unroll 4
+    for (int b = g; b < nslab; b += 8) s += part[(int64_t)b * len + e];
+  }
+  sh[g][lx] = s;
+  __syncthreads();
+  if (g == 0 && e < len) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += sh[q][lx];
+    out[e] = c_sum * t + (other ? c_other * other[e] : 0.0);
+  }
 }
 
 void reduce_slabs(const double* part, int nslab, int len, double* out, cudaStream_t st) {
-  k_reduce_slabs<<<(unsigned)cdiv(len, 256), 256, 0, st>>>(part, nslab, len, out, nullptr, 1);
+  k_reduce_slabs<<<(unsigned)cdiv(len, 32), 256, 0, st>>>(part, nslab, len, 1.0, nullptr, 0.0, out,
+                                                          nullptr, 1);
 }
 void reduce_slabs_gated(const double* part, int nslab, int len, double* out, const ColState* cs,
                         int mp, cudaStream_t st) {
-  k_reduce_slabs<<<(unsigned)cdiv(len, 256), 256, 0, st>>>(part, nslab, len, out, cs, mp);
+  k_reduce_slabs<<<(unsigned)cdiv(len, 32), 256, 0, st>>>(part, nslab, len, 1.0, nullptr, 0.0, out,
+                                                          cs, mp);
+}
+void reduce_slabs_comb(const double* part, int nslab, int len, double c_sum, const double* other,
+                       double c_other, double* out, const ColState* cs, int mp, cudaStream_t st) {
+  k_reduce_slabs<<<(unsigned)cdiv(len, 32), 256, 0, st>>>(part, nslab, len, c_sum, other, c_other,
+                                                          out, cs, mp);
 }
 
 // ============================================== small k x k column transforms
@@ -186,124 +218,178 @@ void kxk_apply(const double* M, const double* t, int k, int mp, Coefs8 ca, Coefs
 }
 
 // ======================================================= out = a X + Q t
-// One warp per row; t (k x mp) staged in shared memory in the working type.
-// Optional fused dot: dot[c] = sum_i D[i][c] out[i][c] -> last block writes
-// per-column results according to `mode`.
-template <typename T>
-__global__ void __launch_bounds__(kNT) k_qcomb(const T* __restrict__ Q, int64_t n, int k, int mp,
+// One warp per row, lanes over the k columns of Q (coalesced); t (k x MP) is
+// staged column-major in shared memory (lane-consecutive, conflict-free).
+// The MP row sums are reduced with a transpose-reduce: at each of the first
+// log2(MP) butterfly levels a lane keeps half of its columns and trades the
+// other half, so MP sums cost log2(MP) + ... shuffles instead of 5 MP.
+// Optional fused dot: dot[c] = sum_i D[i][c] out[i][c] -> the last block
+// applies `mode` to the per-column scalars.
+template <int MP>
+__device__ __forceinline__ float warp_transpose_reduce(float (&v)[MP], int lane) {
+  // after the loop, lane holds in v[0] the partial of column col(lane)
+#pragma unroll
+  for (int half = MP / 2, o = 16; half >= 1; half >>= 1, o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int c = 0; c < half; ++c) {
+      const float send = upper ? v[c] : v[c + half];
+      const float keep = upper ? v[c + half] : v[c];
+      v[c] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  float x = v[0];
+  constexpr int lvl = (MP == 1) ? 0 : (MP == 2) ? 1 : (MP == 4) ? 2 : 3;
+#pragma unroll
+  for (int o = 16 >> lvl; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+template <int MP>
+__device__ __forceinline__ double warp_transpose_reduce(double (&v)[MP], int lane) {
+#pragma unroll
+  for (int half = MP / 2, o = 16; half >= 1; half >>= 1, o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int c = 0; c < half; ++c) {
+      const double send = upper ? v[c] : v[c + half];
+      const double keep = upper ? v[c + half] : v[c];
+      v[c] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  double x = v[0];
+  constexpr int lvl = (MP == 1) ? 0 : (MP == 2) ? 1 : (MP == 4) ? 2 : 3;
+#pragma unroll
+  for (int o = 16 >> lvl; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+// column whose total lane holds after warp_transpose_reduce<MP>, and whether
+// it is the writer lane for that column
+template <int MP>
+__device__ __forceinline__ int tr_col(int lane) {
+  if (MP == 1) return 0;
+  if (MP == 2) return (lane >> 4) & 1;
+  if (MP == 4) return ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+template <int MP>
+__device__ __forceinline__ bool tr_writer(int lane) {
+  return (lane & (32 / MP - 1)) == 0;
+}
+
+__device__ __forceinline__ void finish_mode(ColState& st, int mode, double s) {
+  if (mode == kModeRhoInit) {          // rho = r^T z (C) / r^T r (R)
+    st.rho = s;
+    st.rr = s;
+    if (st.active && !(s > 0.0 && isfinite(s))) {
+      if (s == 0.0) st.active = 0;      // r = 0 already
+      else { st.status = RR_ERR_BREAKDOWN; st.active = 0; }
+    }
+  } else if (mode == kModeBeta) {      // beta = rho_new / rho, rho = rho_new
+    if (st.active) {
+      if (!(s > 0.0 && isfinite(s))) { st.status = RR_ERR_BREAKDOWN; st.active = 0; st.beta = 0.0; }
+      else { st.beta = s / st.rho; st.rho = s; }
+    }
+  } else if (mode == kModeAlpha) {     // alpha = rho / (p^T A p)
+    st.pw = s;
+    if (st.active) {
+      if (!(s > 0.0 && isfinite(s))) { st.status = RR_ERR_BREAKDOWN; st.active = 0; st.alpha = 0.0; }
+      else st.alpha = st.rho / s;
+    } else {
+      st.alpha = 0.0;
+    }
+  } else if (mode == kModeNorm) {      // lam = |out|
+    st.lam = sqrt(s);
+  }
+}
+
+template <typename T, int MP>
+__global__ void __launch_bounds__(kNT) k_qcomb(const T* __restrict__ Q, int64_t n, int k,
                                                const double* __restrict__ t, Coefs8 a,
                                                const T* __restrict__ X, T* __restrict__ out,
                                                const T* __restrict__ D, int mode,
                                                double* __restrict__ part,
                                                unsigned* __restrict__ counter,
                                                ColState* __restrict__ cs, int gated) {
-  if (gated && !any_active(cs, mp)) return;
+  if (gated && !any_active(cs, MP)) return;
   extern __shared__ unsigned char smem_raw[];
-  T* ts = reinterpret_cast<T*>(smem_raw);  // k x mp
+  T* ts = reinterpret_cast<T*>(smem_raw);  // MP x k, column-major in t's sense
   __shared__ double red[kNT / 32 * 8];
-  for (int e = threadIdx.x; e < k * mp; e += kNT) ts[e] = (T)t[e];
+  for (int e = threadIdx.x; e < k * MP; e += kNT) {
+    const int j = e / MP, c = e % MP;
+    ts[c * k + j] = (T)t[e];
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  const int col = tr_col<MP>(lane);
+  const bool writer = tr_writer<MP>(lane);
+  const T acoef = (T)a.v[col];
   const int64_t warps_total = (int64_t)gridDim.x * (kNT / 32);
-  double dacc[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) dacc[c] = 0.0;
+  double dacc = 0.0;
   for (int64_t row = (int64_t)blockIdx.x * (kNT / 32) + (threadIdx.x >> 5); row < n;
        row += warps_total) {
-    T acc[8];
+    T acc[MP];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = (T)0;
+    for (int c = 0; c < MP; ++c) acc[c] = (T)0;
     const T* q = Q + row * k;
+#pragma unroll 4
     for (int j = lane; j < k; j += 32) {
       const T qj = q[j];
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
-        if (c < mp) acc[c] = fma(qj, ts[j * mp + c], acc[c]);
+      for (int c = 0; c < MP; ++c) acc[c] = fma(qj, ts[c * k + j], acc[c]);
     }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      if (c >= mp) break;
-      T v = acc[c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      acc[c] = v;
-    }
-    if (lane < mp) {
-      T v = (T)0;
-#pragma unroll
-      for (int c = 0; c < 8; ++c)
-        if (c == lane) v = acc[c];
-      const int64_t idx = row * mp + lane;
-      const T o = (X ? (T)a.v[lane] * X[idx] : (T)0) + v;
+    const T v = warp_transpose_reduce<MP>(acc, lane);
+    if (writer) {
+      const int64_t idx = row * MP + col;
+      const T o = (X ? acoef * X[idx] : (T)0) + v;
       out[idx] = o;
-      if (D) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (c == lane) dacc[c] += (double)D[idx] * (double)o;
-      }
+      if (D) dacc += (double)D[idx] * (double)o;
     }
   }
   if (mode == kModeNone) return;
-  // lanes hold their own column's partial in dacc[lane]; gather to warp lane 0
-  double v[8];
+  double vv[8];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) v[c] = dacc[c];
-  block_sum_cols<kNT>(v, mp, red);
+  for (int c = 0; c < 8; ++c) vv[c] = (c == col && writer) ? dacc : 0.0;
+  block_sum_cols<kNT>(vv, MP, red);
   if (threadIdx.x == 0)
-    for (int c = 0; c < mp; ++c) part[(int64_t)blockIdx.x * mp + c] = v[c];
+    for (int c = 0; c < MP; ++c) part[(int64_t)blockIdx.x * MP + c] = vv[c];
   if (!last_block(counter)) return;
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < mp; ++c) {
-      const double s = sum_parts(part, gridDim.x, mp, c);
-      ColState& st = cs[c];
-      if (mode == kModeRhoInit) {          // rho = r^T z (C) / r^T r (R)
-        st.rho = s;
-        if (st.active && !(s > 0.0 && isfinite(s))) {
-          if (s == 0.0) st.active = 0;      // r = 0 already
-          else { st.status = RR_ERR_BREAKDOWN; st.active = 0; }
-        }
-      } else if (mode == kModeBeta) {      // beta = rho_new / rho, rho = rho_new
-        if (st.active) {
-          if (!(s > 0.0 && isfinite(s))) { st.status = RR_ERR_BREAKDOWN; st.active = 0; st.beta = 0.0; }
-          else { st.beta = s / st.rho; st.rho = s; }
-        }
-      } else if (mode == kModeAlpha) {     // alpha = rho / (p^T A p)
-        st.pw = s;
-        if (st.active) {
-          if (!(s > 0.0 && isfinite(s))) { st.status = RR_ERR_BREAKDOWN; st.active = 0; st.alpha = 0.0; }
-          else st.alpha = st.rho / s;
-        } else {
-          st.alpha = 0.0;
-        }
-      } else if (mode == kModeNorm) {      // lam = |out|
-        st.lam = sqrt(s);
-      }
-    }
-  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < MP; ++c) finish_mode(cs[c], mode, sum_parts(part, gridDim.x, MP, c));
 }
 
 template <typename T>
 void qcomb(const T* Q, int64_t n, int k, int mp, const double* t, Coefs8 a, const T* X, T* out,
            const T* D, int mode, double* part, unsigned* counter, ColState* cs, bool gated,
            cudaStream_t st) {
-  const unsigned blocks = grid_rows(n, kNT / 32 * 4);
+  // ~8 rows per warp: t is staged once per CTA, so fewer, longer-lived CTAs
+  const unsigned blocks = grid_rows(n, kNT / 32 * 8);
   const size_t smem = (size_t)k * mp * sizeof(T);
-  auto kern = k_qcomb<T>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kern<<<blocks, kNT, smem, st>>>(Q, n, k, mp, t, a, X, out, D, mode, part, counter, cs,
-                                  gated ? 1 : 0);
+#define RR_QC(MPV)                                                                           \
+  {                                                                                          \
+    auto kern = k_qcomb<T, MPV>;                                                             \
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    kern<<<blocks, kNT, smem, st>>>(Q, n, k, t, a, X, out, D, mode, part, counter, cs,       \
+                                    gated ? 1 : 0);                                          \
+  }
+  switch (mp) {
+    case 1: RR_QC(1) break;
+    case 2: RR_QC(2) break;
+    case 4: RR_QC(4) break;
+    default: RR_QC(8) break;
+  }
+#undef RR_QC
 }
 
 // ==================================================== column dot products
-// dot[c] = sum_i X[i][c] Y[i][c]; last block applies `mode` (alpha/beta/rho/norm)
-template <typename T>
+// dot[c] = sum_i X[i][c] Y[i][c]; last block applies `mode` (alpha/rho/norm)
+template <typename T, int MP>
 __global__ void __launch_bounds__(kNT) k_dot_cols(const T* __restrict__ X, const T* __restrict__ Y,
-                                                  int64_t n, int mp, int mode,
+                                                  int64_t n, int mode,
                                                   double* __restrict__ part,
                                                   unsigned* __restrict__ counter,
                                                   ColState* __restrict__ cs, int gated,
                                                   double* __restrict__ out_raw) {
-  if (gated && !any_active(cs, mp)) return;
+  if (gated && !any_active(cs, MP)) return;
   __shared__ double red[kNT / 32 * 8];
   double v[8];
 #pragma unroll
@@ -311,37 +397,17 @@ __global__ void __launch_bounds__(kNT) k_dot_cols(const T* __restrict__ X, const
   const int64_t stride = (int64_t)gridDim.x * kNT;
   for (int64_t i = (int64_t)blockIdx.x * kNT + threadIdx.x; i < n; i += stride) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
-      if (c < mp) v[c] += (double)X[i * mp + c] * (double)Y[i * mp + c];
+    for (int c = 0; c < MP; ++c) v[c] += (double)X[i * MP + c] * (double)Y[i * MP + c];
   }
-  block_sum_cols<kNT>(v, mp, red);
+  block_sum_cols<kNT>(v, MP, red);
   if (threadIdx.x == 0)
-    for (int c = 0; c < mp; ++c) part[(int64_t)blockIdx.x * mp + c] = v[c];
+    for (int c = 0; c < MP; ++c) part[(int64_t)blockIdx.x * MP + c] = v[c];
   if (!last_block(counter)) return;
   if (threadIdx.x == 0) {
-    for (int c = 0; c < mp; ++c) {
-      const double s = sum_parts(part, gridDim.x, mp, c);
+    for (int c = 0; c < MP; ++c) {
+      const double s = sum_parts(part, gridDim.x, MP, c);
       if (out_raw) out_raw[c] = s;
-      if (!cs) continue;
-      ColState& st = cs[c];
-      if (mode == kModeAlpha) {
-        st.pw = s;
-        if (st.active) {
-          if (!(s > 0.0 && isfinite(s))) { st.status = RR_ERR_BREAKDOWN; st.active = 0; st.alpha = 0.0; }
-          else st.alpha = st.rho / s;
-        } else {
-          st.alpha = 0.0;
-        }
-      } else if (mode == kModeRhoInit) {
-        st.rho = s;
-        st.rr = s;
-        if (st.active && !(s > 0.0 && isfinite(s))) {
-          if (s == 0.0) st.active = 0;
-          else { st.status = RR_ERR_BREAKDOWN; st.active = 0; }
-        }
-      } else if (mode == kModeNorm) {
-        st.lam = sqrt(s);
-      }
+      if (cs && mode != kModeNone) finish_mode(cs[c], mode, s);
     }
   }
 }
@@ -349,71 +415,76 @@ __global__ void __launch_bounds__(kNT) k_dot_cols(const T* __restrict__ X, const
 template <typename T>
 void dot_cols(const T* X, const T* Y, int64_t n, int mp, int mode, double* part,
               unsigned* counter, ColState* cs, bool gated, double* out_raw, cudaStream_t st) {
-  const unsigned blocks = grid_rows(n, kNT * 4);
-  k_dot_cols<T><<<blocks, kNT, 0, st>>>(X, Y, n, mp, mode, part, counter, cs, gated ? 1 : 0,
-                                        out_raw);
+  const unsigned blocks = grid_rows(n, kNT * 2);
+  switch (mp) {
+    case 1: k_dot_cols<T, 1><<<blocks, kNT, 0, st>>>(X, Y, n, mode, part, counter, cs, gated ? 1 : 0, out_raw); break;
+    case 2: k_dot_cols<T, 2><<<blocks, kNT, 0, st>>>(X, Y, n, mode, part, counter, cs, gated ? 1 : 0, out_raw); break;
+    case 4: k_dot_cols<T, 4><<<blocks, kNT, 0, st>>>(X, Y, n, mode, part, counter, cs, gated ? 1 : 0, out_raw); break;
+    default: k_dot_cols<T, 8><<<blocks, kNT, 0, st>>>(X, Y, n, mode, part, counter, cs, gated ? 1 : 0, out_raw); break;
+  }
 }
 
 // ===================================== C variant: e += a p, r -= a w, rr
 // Fused with the Q^T r slab partials.  Last block: convergence check.
-template <typename T>
+template <typename T, int MP>
 __global__ void __launch_bounds__(kNT) k_update_qt(T* __restrict__ E, T* __restrict__ R,
                                                    const T* __restrict__ P,
                                                    const T* __restrict__ W,
                                                    const T* __restrict__ Q, int64_t n, int k,
-                                                   int mp, int rps, double* __restrict__ tpart,
+                                                   int rps, double* __restrict__ tpart,
                                                    double* __restrict__ part,
                                                    unsigned* __restrict__ counter,
                                                    ColState* __restrict__ cs) {
-  if (!any_active(cs, mp)) return;
+  if (!any_active(cs, MP)) return;
   extern __shared__ unsigned char smem_raw[];
-  T* Rs = reinterpret_cast<T*>(smem_raw);  // rps x mp
+  T* Rs = reinterpret_cast<T*>(smem_raw);  // rps x MP
   __shared__ double red[kNT / 32 * 8];
   __shared__ T al[8];
-  if (threadIdx.x < 8) al[threadIdx.x] = (threadIdx.x < mp && cs[threadIdx.x].active) ? (T)cs[threadIdx.x].alpha : (T)0;
+  if (threadIdx.x < 8) al[threadIdx.x] = (threadIdx.x < MP && cs[threadIdx.x].active) ? (T)cs[threadIdx.x].alpha : (T)0;
   __syncthreads();
   const int64_t r0 = (int64_t)blockIdx.x * rps;
   const int cnt = (int)((n - r0 < rps) ? (n - r0) : rps);
   double v[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) v[c] = 0.0;
-  for (int e = threadIdx.x; e < cnt * mp; e += kNT) {
-    const int64_t g = r0 * mp + e;
-    const int c = e % mp;
+  for (int e = threadIdx.x; e < cnt * MP; e += kNT) {
+    const int64_t g = r0 * MP + e;
+    const int c = e % MP;
     const T a = al[c];
     E[g] = fma(a, P[g], E[g]);
     const T r = fma(-a, W[g], R[g]);
     R[g] = r;
     Rs[e] = r;
 #pragma unroll
-    for (int cc = 0; cc < 8; ++cc)
+    for (int cc = 0; cc < MP; ++cc)
       if (cc == c) v[cc] += (double)r * (double)r;
   }
   __syncthreads();
   if (tpart) {
-    double* out = tpart + (int64_t)blockIdx.x * k * mp;
+    double* out = tpart + (int64_t)blockIdx.x * k * MP;
     for (int j = threadIdx.x; j < k; j += kNT) {
-      T acc[8];
+      T acc[MP];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) acc[c] = (T)0;
+      for (int c = 0; c < MP; ++c) acc[c] = (T)0;
       const T* q = Q + r0 * k + j;
+#pragma unroll 4
       for (int i = 0; i < cnt; ++i) {
         const T qij = q[(int64_t)i * k];
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (c < mp) acc[c] = fma(qij, Rs[i * mp + c], acc[c]);
+        for (int c = 0; c < MP; ++c) acc[c] = fma(qij, Rs[i * MP + c], acc[c]);
       }
-      for (int c = 0; c < mp; ++c) out[(int64_t)j * mp + c] = (double)acc[c];
+#pragma unroll
+      for (int c = 0; c < MP; ++c) out[(int64_t)j * MP + c] = (double)acc[c];
     }
   }
-  block_sum_cols<kNT>(v, mp, red);
+  block_sum_cols<kNT>(v, MP, red);
   if (threadIdx.x == 0)
-    for (int c = 0; c < mp; ++c) part[(int64_t)blockIdx.x * mp + c] = v[c];
+    for (int c = 0; c < MP; ++c) part[(int64_t)blockIdx.x * MP + c] = v[c];
   if (!last_block(counter)) return;
   if (threadIdx.x == 0) {
-    for (int c = 0; c < mp; ++c) {
+    for (int c = 0; c < MP; ++c) {
       ColState& st = cs[c];
-      const double s = sum_parts(part, gridDim.x, mp, c);
+      const double s = sum_parts(part, gridDim.x, MP, c);
       st.rr = s;
       if (!st.active) continue;
       st.iters += 1;
@@ -428,8 +499,13 @@ void update_qt(T* E, T* R, const T* P, const T* W, const T* Q, int64_t n, int k,
                double* tpart, double* part, unsigned* counter, ColState* cs, cudaStream_t st) {
   const int rps = qt_rows_per_slab(n);
   const int nslab = qt_nslab(n);
-  k_update_qt<T><<<(unsigned)nslab, kNT, (size_t)rps * mp * sizeof(T), st>>>(
-      E, R, P, W, Q, n, k, mp, rps, tpart, part, counter, cs);
+  const size_t smem = (size_t)rps * mp * sizeof(T);
+  switch (mp) {
+    case 1: k_update_qt<T, 1><<<(unsigned)nslab, kNT, smem, st>>>(E, R, P, W, Q, n, k, rps, tpart, part, counter, cs); break;
+    case 2: k_update_qt<T, 2><<<(unsigned)nslab, kNT, smem, st>>>(E, R, P, W, Q, n, k, rps, tpart, part, counter, cs); break;
+    case 4: k_update_qt<T, 4><<<(unsigned)nslab, kNT, smem, st>>>(E, R, P, W, Q, n, k, rps, tpart, part, counter, cs); break;
+    default: k_update_qt<T, 8><<<(unsigned)nslab, kNT, smem, st>>>(E, R, P, W, Q, n, k, rps, tpart, part, counter, cs); break;
+  }
 }
 
 // ========================== R variant: y += a p, r -= a q, rho = r^T r, beta

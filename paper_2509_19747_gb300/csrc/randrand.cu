@@ -549,27 +549,12 @@ void iter_C(rr_handle* h, const cudaEvent_t* ev) {
   p_update<T>(Pv, Zv, n, mp, h->cs, false, h->st);                        // p = z + beta p
 }
 
-// Reduce slab partials into c_sum * sum + c_other * other
-__global__ void k_reduce_comb(const double* __restrict__ part, int nslab, int len,
-                              double c_sum, const double* __restrict__ other, double c_other,
-                              double* __restrict__ out, const ColState* __restrict__ cs, int mp) {
-  bool any = false;
-  for (int c = 0; c < mp; ++c) any |= cs[c].active != 0;
-  if (!any) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= len) return;
-  double s = 0.0;
-  for (int b = 0; b < nslab; ++b) s += part[(int64_t)b * len + e];
-  out[e] = c_sum * s + (other ? c_other * other[e] : 0.0);
-}
-
 template <typename T>
 void qt_comb(rr_handle* h, const T* V, double c_sum, const double* other, double c_other,
              double* out) {
   qt_partial_gated<T>((const T*)h->Q, V, h->n, h->k, h->mp, h->tpart, h->cs, h->st);
-  const int len = h->k * h->mp;
-  k_reduce_comb<<<(unsigned)cdiv(len, 256), 256, 0, h->st>>>(h->tpart, qt_nslab(h->n), len, c_sum,
-                                                            other, c_other, out, h->cs, h->mp);
+  reduce_slabs_comb(h->tpart, qt_nslab(h->n), h->k * h->mp, c_sum, other, c_other, out, h->cs,
+                    h->mp, h->st);
 }
 
 template <typename T>

@@ -31,6 +31,8 @@ void qt_partial_gated(const T* Q, const T* V, int64_t n, int k, int mp, double* 
                       const ColState* cs, cudaStream_t st);
 void reduce_slabs_gated(const double* part, int nslab, int len, double* out, const ColState* cs,
                         int mp, cudaStream_t st);
+void reduce_slabs_comb(const double* part, int nslab, int len, double c_sum, const double* other,
+                       double c_other, double* out, const ColState* cs, int mp, cudaStream_t st);
 void kxk_apply(const double* M, const double* t, int k, int mp, Coefs8 ca, Coefs8 cb,
                double* out, cudaStream_t st);
 template <typename T>
