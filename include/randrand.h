@@ -121,7 +121,8 @@ typedef struct {
   int32_t power_iters;   /* power iterations per estimate, default 20           */
   int32_t max_rhs;       /* right-hand sides a solve may pass (1..8), default 1 */
   int32_t profile;       /* 1: time the hot kernels with CUDA events (rr_profile) */
-  int32_t pad_;
+  int32_t sketch_impl;   /* kernel-operator sketch in RR_PREC_MIXED: 0 auto (tensor
+                            cores when dim == 8), 1 float32 cores, 2 tensor cores */
   double rho;            /* C variant: <= 0 -> eq:optimal_rho with F = 1/mu     */
   double restart_eta;    /* restart after this residual reduction, default 1e-2 */
 } rr_build_opts;

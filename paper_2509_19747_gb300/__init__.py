@@ -53,7 +53,7 @@ class rr_build_opts(ctypes.Structure):
         ("variant", ctypes.c_int32), ("precision", ctypes.c_int32), ("orth", ctypes.c_int32),
         ("gamma", ctypes.c_int32), ("l_sk", ctypes.c_int32), ("gamma_sk", ctypes.c_int32),
         ("power_iters", ctypes.c_int32), ("max_rhs", ctypes.c_int32), ("profile", ctypes.c_int32),
-        ("pad_", ctypes.c_int32), ("rho", ctypes.c_double), ("restart_eta", ctypes.c_double),
+        ("sketch_impl", ctypes.c_int32), ("rho", ctypes.c_double), ("restart_eta", ctypes.c_double),
     ]
 
 
@@ -280,7 +280,7 @@ class Handle:
     def __init__(self, op: Operator, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
                  variant: str = "C", precision: str = "fp64", max_rhs: int = 1,
                  power_iters: int = 20, rho: float = 0.0, restart_eta: float = 1e-2,
-                 gamma: int = 8, profile: bool = False, stream=None):
+                 gamma: int = 8, profile: bool = False, sketch_impl: int = 0, stream=None):
         import torch
         self.op = op
         self.n = op.n
@@ -294,6 +294,7 @@ class Handle:
         o.restart_eta = restart_eta
         o.gamma = gamma
         o.profile = 1 if profile else 0
+        o.sketch_impl = sketch_impl
         self.opts = o
         self.ws_bytes = randrand_workspace_bytes(op.c, k, o)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")

@@ -37,7 +37,18 @@ __global__ void k_prepare_points(const float* __restrict__ x, int64_t n, int dim
 __global__ void k_point_norms(const float* __restrict__ x, int64_t n, int dim,
                               float2* __restrict__ pn);
 
+__global__ void k_pad_points(float* __restrict__ xs, float* __restrict__ cn, int64_t n,
+                             int64_t npad, int dim) {
+  const int64_t i = n + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  for (int d = 0; d < dim; ++d) xs[i * dim + d] = 0.f;
+  cn[i] = -1e30f;   // exp2 of the padded entries is 0
+}
+
 void prepare_kernel_points(OpDev& op, cudaStream_t st) {
+  const int64_t npad = cdiv(op.n, kPointPad) * kPointPad;
+  if (npad > op.n)
+    k_pad_points<<<1, 64, 0, st>>>(op.xs, op.cn, op.n, npad, op.dim);
   // exp(-|xi - xj|^2 / (2h^2)) = exp2(xs_i . xs_j + cn_i + cn_j) with
   // xs = x sqrt(log2 e) / h and cn = -|xs|^2 / 2.
   const double scale = sqrt(1.4426950408889634) / op.bw;

@@ -7,7 +7,7 @@ namespace rr {
 
 template <typename T>
 __global__ void k_gaussian_omega(T* __restrict__ Om, __nv_bfloat16* __restrict__ Ob, int64_t n,
-                                 int k, uint64_t seed, int round_bf16) {
+                                 int k, uint64_t seed, int round_bf16, int64_t ldo) {
   const int q4 = (k + 3) >> 2;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n * q4) return;
@@ -25,18 +25,18 @@ __global__ void k_gaussian_omega(T* __restrict__ Om, __nv_bfloat16* __restrict__
     if (round_bf16) {
       const __nv_bfloat16 b = __float2bfloat16_rn((float)v);
       v = (T)__bfloat162float(b);
-      if (Ob) Ob[i * k + j] = b;
+      if (Ob) Ob[(int64_t)j * ldo + i] = b;   // Omega^T, K-major operand of the sketch MMA
     }
     Om[i * k + j] = v;
   }
 }
 
 template <typename T>
-void gen_gaussian_omega(T* Om, __nv_bfloat16* Om_bf16, int64_t n, int k, uint64_t seed,
-                        bool round_bf16, cudaStream_t st) {
+void gen_gaussian_omega(T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, int k,
+                        uint64_t seed, bool round_bf16, cudaStream_t st) {
   const int64_t total = n * ((k + 3) / 4);
-  k_gaussian_omega<T><<<(unsigned)cdiv(total, 256), 256, 0, st>>>(Om, Om_bf16, n, k, seed,
-                                                                   round_bf16 ? 1 : 0);
+  k_gaussian_omega<T><<<(unsigned)cdiv(total, 256), 256, 0, st>>>(Om, OmT_bf16, n, k, seed,
+                                                                   round_bf16 ? 1 : 0, ldo);
 }
 
 __global__ void k_sparse_sign(int32_t* __restrict__ cols, int8_t* __restrict__ sgn,
@@ -94,10 +94,10 @@ void gen_power_start(T* V, int64_t n, int mp, int col, int which, uint64_t seed,
   k_power_start<T><<<(unsigned)cdiv(n, 256), 256, 0, st>>>(V, n, mp, col, which, seed);
 }
 
-template void gen_gaussian_omega<float>(float*, __nv_bfloat16*, int64_t, int, uint64_t, bool,
-                                        cudaStream_t);
-template void gen_gaussian_omega<double>(double*, __nv_bfloat16*, int64_t, int, uint64_t, bool,
-                                         cudaStream_t);
+template void gen_gaussian_omega<float>(float*, __nv_bfloat16*, int64_t, int64_t, int, uint64_t,
+                                        bool, cudaStream_t);
+template void gen_gaussian_omega<double>(double*, __nv_bfloat16*, int64_t, int64_t, int, uint64_t,
+                                         bool, cudaStream_t);
 template void sparse_to_dense_omega<float>(float*, const int32_t*, const int8_t*, int64_t, int,
                                            int, cudaStream_t);
 template void sparse_to_dense_omega<double>(double*, const int32_t*, const int8_t*, int64_t,

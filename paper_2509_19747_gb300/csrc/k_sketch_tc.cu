@@ -1,0 +1,412 @@
+// Tensor-core sketch of the Gaussian-kernel operator,
+//     Y_mu = (K + mu I) Omega,   K_ij = exp(-|x_i - x_j|^2 / (2 h^2)),
+// (Alg. 7 step 1 with the on-the-fly kernel generator of Sec. 7.2.2) on the
+// 5th-generation tensor cores: bf16 operands, float32 accumulation in TMEM.
+//
+// CTA tile: 128 rows of Y x 256 sketch columns; the reduction over j runs
+// in steps of 64 through a 4-stage shared-memory ring:
+//   warp 0      TMA: the 256 x 64 bf16 tile of Omega^T (K-major, 128-byte
+//               swizzle) -> B stage, completion on a transaction mbarrier;
+//   warp 1      TMEM allocation, and one thread issuing tcgen05.mma
+//               (M=128, N=256, K=16, four per stage) + tcgen05.commit;
+//   warps 2-9   generate the 128 x 64 bf16 block of K for the stage,
+//               exp2(xs_i . xs_j + cn_i + cn_j) on the float32 pipes, straight
+//               into the 128-byte-swizzled K-major layout the MMA reads; after
+//               the last stage they drain the accumulator with tcgen05.ld and
+//               write Y = acc + mu Omega.
+// Every mbarrier wait is bounded: on timeout the kernel raises *err and
+// unwinds (RR_ERR_TIMEOUT on the host) instead of hanging.
+#include <cuda.h>
+
+#include <cmath>
+
+#include "rr_common.cuh"
+
+namespace rr {
+namespace {
+
+constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 4;
+constexpr int kGenWarps = 8;
+constexpr int kThreads = 32 * (2 + kGenWarps);
+constexpr int kABytes = kBM * kBK * 2;   // 16 KB
+constexpr int kBBytes = kBN * kBK * 2;   // 32 KB
+constexpr int kXsBytes = kBK * 8 * 4;    // 64 points x 8 coordinates
+constexpr int kCnBytes = kBK * 4;        // 64 values of cn
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+struct __align__(16) SmemTail {
+  float xs[kStages][kBK * 8];
+  float cn[kStages][kBK];
+  unsigned long long full_a[kStages];
+  unsigned long long full_b[kStages];
+  unsigned long long empty[kStages];
+  unsigned long long done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+constexpr size_t kSmemBytes = 1024 /*align slack*/ + (size_t)kStages * (kABytes + kBBytes) + sizeof(SmemTail);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// bounded wait for the phase with parity `parity` to complete
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, int* err,
+                                          volatile int* abort) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 1023) == 1023 && *abort) return false;
+  }
+  atomicExch(err, 1);
+  *abort = 1;
+  return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// plain bulk copy global -> shared (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor: K-major operand in the canonical
+// 128-byte-swizzled layout (8-row x 128-byte atoms, 1024 bytes apart).
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);        // start address
+  d |= (uint64_t)(16 >> 4) << 16;                  // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: kind::f16, bf16 x bf16 -> f32, both K-major, M=128, N=256
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_kernel_sketch_tc(const __grid_constant__ CUtensorMap omt_map, const float* __restrict__ xs,
+                       const float* __restrict__ cn, int64_t n, int k, double mu,
+                       const float* __restrict__ Om, float* __restrict__ Y, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = base;                                   // kStages x 16 KB
+  unsigned char* sB = base + (size_t)kStages * kABytes;       // kStages x 32 KB
+  SmemTail* tail = (SmemTail*)(sB + (size_t)kStages * kBBytes);
+  volatile int* abort = &tail->abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = (int64_t)blockIdx.x * kBM;
+  const int c0 = blockIdx.y * kBN;
+  const int nsteps = (int)((n + kBK - 1) / kBK);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&tail->full_a[s], kGenWarps * 32);
+      mbar_init(&tail->full_b[s], 1);
+      mbar_init(&tail->empty[s], 1);
+    }
+    mbar_init(&tail->done, 1);
+    tail->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tail->tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tail->tmem_base;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA
+    if (lane == 0) {
+      int issued = 0;
+      for (int st = 0; st < nsteps; ++st) {
+        const int s = st % kStages;
+        if (st >= kStages && !mbar_wait(&tail->empty[s], ((st / kStages) - 1) & 1, err, abort)) break;
+        // Omega^T tile + the step's 64 points (xs, cn are padded to a multiple
+        // of 64 points, so the bulk copies never read past their arrays)
+        mbar_arrive_tx(&tail->full_b[s], kBBytes + kXsBytes + kCnBytes);
+        tma_load_2d(sB + (size_t)s * kBBytes, &omt_map, st * kBK, c0, &tail->full_b[s]);
+        bulk_load(tail->xs[s], xs + (size_t)st * kBK * 8, kXsBytes, &tail->full_b[s]);
+        bulk_load(tail->cn[s], cn + (size_t)st * kBK, kCnBytes, &tail->full_b[s]);
+        ++issued;
+      }
+      // never leave a bulk copy in flight into shared memory that is about to be released
+      for (int st = (issued > kStages ? issued - kStages : 0); st < issued; ++st)
+        mbar_wait(&tail->full_b[st % kStages], (st / kStages) & 1, err, abort);
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA
+    if (lane == 0) {
+      bool ok = true;
+      for (int st = 0; st < nsteps && ok; ++st) {
+        const int s = st % kStages;
+        const uint32_t par = (st / kStages) & 1;
+        ok = mbar_wait(&tail->full_b[s], par, err, abort) && mbar_wait(&tail->full_a[s], par, err, abort);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(sA + (size_t)s * kABytes);
+        const uint32_t b0 = smem_u32(sB + (size_t)s * kBBytes);
+#pragma unroll
+        for (int kk = 0; kk < kBK / 16; ++kk)
+          mma_bf16(tmem, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32),
+                   (st > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(&tail->empty[s]);
+      }
+      mma_commit(&tail->done);
+    }
+  } else {
+    // ------------------------------------------------- generators / epilogue
+    const int g = threadIdx.x - 64;        // 0 .. 255
+    const int r = g & (kBM - 1);           // row of the tile
+    const int h = g >> 7;                  // which 32 of the 64 columns
+    const int64_t gi = i0 + r;
+    float xi[8];
+    float ci = -1e30f;
+    if (gi < n) {
+#pragma unroll
+      for (int d = 0; d < 8; ++d) xi[d] = xs[gi * 8 + d];
+      ci = cn[gi];
+    } else {
+#pragma unroll
+      for (int d = 0; d < 8; ++d) xi[d] = 0.f;
+    }
+    bool ok = true;
+    for (int st = 0; st < nsteps; ++st) {
+      const int s = st % kStages;
+      if (st >= kStages && !mbar_wait(&tail->empty[s], ((st / kStages) - 1) & 1, err, abort)) {
+        ok = false;
+        break;
+      }
+      // the step's points arrive with the Omega^T tile (same barrier)
+      if (!mbar_wait(&tail->full_b[s], (st / kStages) & 1, err, abort)) {
+        ok = false;
+        break;
+      }
+      const float* xsb = tail->xs[s];
+      const float* cnb = tail->cn[s];
+      // 32 entries of row r: columns 32h .. 32h+31 of the step
+      uint32_t packed[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        float v2[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int p = 32 * h + 2 * q + u;
+          const float* pj = xsb + p * 8;
+          float a = ci + cnb[p];
+#pragma unroll
+          for (int d = 0; d < 8; ++d) a = fmaf(xi[d], pj[d], a);
+          v2[u] = ex2_approx(a);
+        }
+        packed[q] = pack_bf16x2(v2[0], v2[1]);
+      }
+      // canonical K-major SW128 layout: row r at r*128 bytes, 16-byte chunk
+      // c stored at chunk position c ^ (r & 7)
+      unsigned char* arow = sA + (size_t)s * kABytes + (size_t)r * 128;
+#pragma unroll
+      for (int cq = 0; cq < 4; ++cq) {
+        const int chunk = 4 * h + cq;
+        const int phys = chunk ^ (r & 7);
+        uint4 v;
+        v.x = packed[4 * cq + 0];
+        v.y = packed[4 * cq + 1];
+        v.z = packed[4 * cq + 2];
+        v.w = packed[4 * cq + 3];
+        *reinterpret_cast<uint4*>(arow + phys * 16) = v;
+      }
+      fence_proxy_async();
+      mbar_arrive(&tail->full_a[s]);
+    }
+    // ----------------------------------------------------------- epilogue
+    // tcgen05.ld is warp-collective: enter only if the whole warp is healthy
+    ok = __all_sync(0xffffffffu, ok);
+    if (ok) ok = mbar_wait(&tail->done, 0, err, abort);
+    ok = __all_sync(0xffffffffu, ok);
+    if (ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int quarter = warp & 3;                 // TMEM lanes this warp may read
+      const int colhalf = (warp - 2) >> 2;          // 0 or 1: columns 128*colhalf ...
+      const int row = quarter * 32 + lane;
+      const int64_t yi = i0 + row;
+      for (int chunk = 0; chunk < 4; ++chunk) {
+        const int col0 = colhalf * 128 + chunk * 32;
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+              "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+              "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+              "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (yi < n) {
+          const float muf = (float)mu;
+          const int cb = c0 + col0;
+          if ((k & 3) == 0 && cb + 32 <= k) {
+            float4* yrow = reinterpret_cast<float4*>(Y + yi * k + cb);
+            const float4* orow = reinterpret_cast<const float4*>(Om + yi * k + cb);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const float4 o = orow[t];
+              float4 y;
+              y.x = __uint_as_float(v[4 * t + 0]) + muf * o.x;
+              y.y = __uint_as_float(v[4 * t + 1]) + muf * o.y;
+              y.z = __uint_as_float(v[4 * t + 2]) + muf * o.z;
+              y.w = __uint_as_float(v[4 * t + 3]) + muf * o.w;
+              yrow[t] = y;
+            }
+          } else {
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+              const int c = cb + t;
+              if (c < k) Y[yi * k + c] = __uint_as_float(v[t]) + muf * Om[yi * k + c];
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+}  // namespace
+
+size_t sketch_tc_smem_bytes() { return kSmemBytes; }
+
+// Y = (K + mu I) Omega on the tensor cores.  omt: Omega^T in bf16, k rows of
+// pitch ldo >= n elements (ldo a multiple of 8; the tensor map zero-fills
+// columns >= n).  xs / cn: the exp2-form points (dim must be 8), padded to a
+// multiple of 64 points with xs = 0, cn = -1e30.  Returns RR_ERR_UNSUPPORTED
+// if the tensor map cannot be encoded (the caller then uses the float32
+// sketch).
+rr_status sketch_kernel_tc(const OpDev& op, double mu, const __nv_bfloat16* omt, int64_t ldo,
+                           const float* Om, float* Y, int k, int* err, cudaStream_t st) {
+  if (op.dim != 8 || (ldo % 8) != 0) return RR_ERR_UNSUPPORTED;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return RR_ERR_UNSUPPORTED;
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {(cuuint64_t)op.n, (cuuint64_t)k};
+  const cuuint64_t gstride[1] = {(cuuint64_t)ldo * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBN};
+  const cuuint32_t estride[2] = {1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)omt, gdim, gstride, box, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return RR_ERR_UNSUPPORTED;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_kernel_sketch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes) != cudaSuccess)
+      return RR_ERR_CUDA;
+    attr = true;
+  }
+  dim3 grid((unsigned)cdiv(op.n, kBM), (unsigned)cdiv(k, kBN));
+  k_kernel_sketch_tc<<<grid, kThreads, kSmemBytes, st>>>(map, op.xs, op.cn, op.n, k, mu, Om, Y,
+                                                          err);
+  return cudaGetLastError() == cudaSuccess ? RR_OK : RR_ERR_CUDA;
+}
+
+}  // namespace rr

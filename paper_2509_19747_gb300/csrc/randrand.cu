@@ -56,7 +56,7 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   od.n = A.n;
   const int gs_max = std::max(gram_nsplit(A.n, k, k), 1);
   L.size[R_OM] = n * kk * ts;
-  L.size[R_OMB] = (o.precision == RR_PREC_MIXED) ? n * kk * 2 : 0;
+  L.size[R_OMB] = (o.precision == RR_PREC_MIXED) ? kk * (size_t)cdiv(A.n, 8) * 8 * 2 : 0;
   L.size[R_SSC] = n * (size_t)o.gamma * 4;
   L.size[R_SSS] = n * (size_t)o.gamma;
   L.size[R_Y] = n * kk * ts;
@@ -66,8 +66,9 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_GPART] = (size_t)gs_max * kk * kk * 8;
   L.size[R_CHOLW] = 32 * 32 * 8;
   L.size[R_STATUS] = 64;
-  L.size[R_XS] = (A.kind == RR_OP_GAUSS_KERNEL) ? n * (size_t)A.dim * 4 : 0;
-  L.size[R_CN] = (A.kind == RR_OP_GAUSS_KERNEL) ? n * 4 : 0;
+  const size_t npts = (size_t)cdiv(A.n, kPointPad) * kPointPad;
+  L.size[R_XS] = (A.kind == RR_OP_GAUSS_KERNEL) ? npts * (size_t)A.dim * 4 : 0;
+  L.size[R_CN] = (A.kind == RR_OP_GAUSS_KERNEL) ? npts * 4 : 0;
   L.size[R_PN] = (A.kind == RR_OP_GAUSS_KERNEL) ? n * 8 : 0;
   L.size[R_MVS] = op_matvec_scratch_elems(od, mp) * 8;
   L.size[R_VT] = 7 * n * (size_t)mp * ts;
@@ -503,13 +504,35 @@ rr_status build_impl(rr_handle* h) {
   if (h->op.kind == RR_OP_GAUSS_KERNEL) prepare_kernel_points(h->op, st);
   const bool mixed = h->o.precision == RR_PREC_MIXED;
   // Alg. 7 step 1: Omega (eq:testmatrix with q = 0) and Y_mu = A Omega + mu Omega
+  const int64_t ldo = cdiv(n, 8) * 8;
   if (h->sketch == RR_SKETCH_GAUSSIAN) {
-    gen_gaussian_omega<T>((T*)h->Om, h->Omb, n, k, h->seed, mixed, st);
+    gen_gaussian_omega<T>((T*)h->Om, h->Omb, ldo, n, k, h->seed, mixed, st);
   } else {
     gen_sparse_sign(h->ss_cols, h->ss_sgn, n, k, h->o.gamma, h->seed, 2u, st);
     sparse_to_dense_omega<T>((T*)h->Om, h->ss_cols, h->ss_sgn, n, k, h->o.gamma, st);
   }
-  if (h->op.kind == RR_OP_CSR && h->sketch == RR_SKETCH_SPARSE_SIGN)
+  // tensor cores for the mixed-precision Gaussian-kernel sketch (bf16 operands)
+  const bool tc = mixed && h->op.kind == RR_OP_GAUSS_KERNEL && h->sketch == RR_SKETCH_GAUSSIAN &&
+                  h->op.dim == 8 && h->o.sketch_impl != 1 && sizeof(T) == 4;
+  bool done_tc = false;
+  if (tc) {
+    RR_CUDA_TRY(cudaMemsetAsync(h->dstatus + 1, 0, sizeof(int), st));
+    const cudaEvent_t* ev = ev_take(h, RR_PROF_SKETCH);
+    if (ev) cudaEventRecord(ev[0], st);
+    const rr_status s = sketch_kernel_tc(h->op, h->mu, h->Omb, ldo, (const float*)h->Om,
+                                         (float*)h->Y, k, h->dstatus + 1, st);
+    if (ev) cudaEventRecord(ev[1], st);
+    if (s == RR_OK) {
+      int err = 0;
+      RR_TRY(read_int(h, h->dstatus + 1, &err));
+      if (err) return RR_ERR_TIMEOUT;
+      done_tc = true;
+    } else if (s != RR_ERR_UNSUPPORTED || h->o.sketch_impl == 2) {
+      return s;
+    }
+  }
+  if (done_tc) {
+  } else if (h->op.kind == RR_OP_CSR && h->sketch == RR_SKETCH_SPARSE_SIGN)
     csr_sketch_sparse<T>(h->op, h->mu, h->ss_cols, h->ss_sgn, h->o.gamma, (T*)h->Y, k, st,
                          ev_take(h, RR_PROF_SKETCH));
   else

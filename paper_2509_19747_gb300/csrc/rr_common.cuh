@@ -69,9 +69,10 @@ struct ColState {
 
 // ------------------------------------------------------------ launchers
 // k_rng.cu
+// Om: n x k row-major; OmT_bf16 (optional): bf16 Omega^T, k rows of pitch ldo
 template <typename T>
-void gen_gaussian_omega(T* Om, __nv_bfloat16* Om_bf16, int64_t n, int k, uint64_t seed,
-                        bool round_bf16, cudaStream_t st);
+void gen_gaussian_omega(T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, int k,
+                        uint64_t seed, bool round_bf16, cudaStream_t st);
 void gen_sparse_sign(int32_t* cols, int8_t* sgn, int64_t nlines, int ncols, int gamma,
                      uint64_t seed, uint32_t stream_id, cudaStream_t st);
 template <typename T>
@@ -111,6 +112,8 @@ void convert(const Tin* in, Tout* out, int64_t count, cudaStream_t st);
 void transpose_kxk(const double* in, double* out, int k, cudaStream_t st);
 
 // k_operator.cu -- products with A_mu
+// points padded to a multiple of kPointPad rows (xs = 0, cn = -1e30 beyond n)
+constexpr int kPointPad = 64;
 void prepare_kernel_points(OpDev& op, cudaStream_t st);
 // W = (A + mu I) V, V and W n x mp interleaved (row i holds the mp columns)
 // ev (optional): two events recorded around the main product kernel
@@ -130,6 +133,11 @@ void op_sketch(const OpDev& op, double mu, const T* Om, T* Y, int k, bool bf16,
 template <typename T>
 void csr_sketch_sparse(const OpDev& op, double mu, const int32_t* cols, const int8_t* sgn,
                        int gamma, T* Y, int k, cudaStream_t st, const cudaEvent_t* ev = nullptr);
+
+// k_sketch_tc.cu -- tensor-core sketch of the Gaussian-kernel operator
+size_t sketch_tc_smem_bytes();
+rr_status sketch_kernel_tc(const OpDev& op, double mu, const __nv_bfloat16* omt, int64_t ldo,
+                           const float* Om, float* Y, int k, int* err, cudaStream_t st);
 
 // k_krylov.cu -- tall-skinny projector pieces and Krylov updates
 template <typename T>

@@ -293,3 +293,24 @@ def test_kernel_product_double_float_accuracy(cuda_lib, n, m):
     ref = op.matmat(V) + mu * V
     scale = op.matmat(np.abs(V)) + mu * np.abs(V)          # sum_j |K_ij v_j|
     assert np.max(np.abs(w - ref) / scale) <= 1e-11
+
+
+@pytest.mark.parametrize("n,k", [(3001, 300), (1000, 256), (777, 40)])
+def test_tensor_core_sketch_matches_float_cores(cuda_lib, n, k):
+    """The tcgen05 bf16 sketch (TMA-staged Omega^T, generated K tiles, TMEM
+    accumulators) and the float32-core bf16 sketch compute the same
+    Y_mu = K_bf16 Omega_bf16 + mu Omega up to float32 summation order, so the
+    resulting R factors and tau agree to float32 rounding."""
+    rr = cuda_lib
+    X = W.mixture_points(n, seed=25)
+    mu = 1e-3
+    hs = [rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=25,
+                    precision="mixed", sketch_impl=impl) for impl in (1, 2)]
+    R1, R2 = (h.export("R").cpu().numpy() for h in hs)
+    cond = np.linalg.cond(R1)
+    assert rel(R2, R1) <= 2e-6 * cond
+    assert hs[1].scalars()[0] == pytest.approx(hs[0].scalars()[0], rel=1e-3)
+    b = W.gaussian_rhs(n, 1, 25)[:, 0]
+    x, status, _ = hs[1].solve(dev(b), rtol=1e-8)
+    assert status == rr.RR_OK
+    assert O.true_rel_residual(O.GaussKernelOp(X), mu, x.cpu().numpy(), b)[0] <= 1e-8
