@@ -178,6 +178,7 @@ struct rr_handle {
   std::vector<EvPair> ev_free, ev_pending;
   std::vector<EvPair> ev_graph;  // one pair per captured iteration
   bool graph_pending;
+  bool graph_prof_broken;        // captured event records gave no timings
 };
 
 namespace {
@@ -243,14 +244,15 @@ const cudaEvent_t* ev_take(rr_handle* h, int cat) {
   return h->ev_pending.back().e;
 }
 
-void ev_accumulate(rr_handle* h, const rr_handle::EvPair& p) {
+bool ev_accumulate(rr_handle* h, const rr_handle::EvPair& p) {
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, p.e[0], p.e[1]) == cudaSuccess) {
     h->pacc.launches[p.cat] += 1;
     h->pacc.ms[p.cat] += ms;
-  } else {
-    cudaGetLastError();
+    return true;
   }
+  cudaGetLastError();
+  return false;
 }
 
 // called after the stream is idle: fold finished event pairs into the profile
@@ -262,7 +264,12 @@ void harvest(rr_handle* h) {
   }
   h->ev_pending.clear();
   if (h->graph_pending) {
-    for (const auto& p : h->ev_graph) ev_accumulate(h, p);
+    bool ok = true;
+    for (auto& p : h->ev_graph) {
+      p.cat = RR_PROF_MATVEC;
+      ok &= ev_accumulate(h, p);
+    }
+    if (!ok) h->graph_prof_broken = true;   // fall back to direct launches
     h->graph_pending = false;
   }
 }
@@ -600,9 +607,9 @@ void iter_R(rr_handle* h, const cudaEvent_t* ev) {
 
 template <typename T>
 rr_status run_chunk(rr_handle* h) {
-  // the legacy default stream cannot be captured, and a profiled handle times
-  // each product with its own event pair: launch the iterations directly
-  if (h->st == nullptr || h->st == cudaStreamLegacy || h->prof) {
+  // the legacy default stream cannot be captured; a profiled handle whose
+  // captured event records gave no timings launches directly as well
+  if (h->st == nullptr || h->st == cudaStreamLegacy || (h->prof && h->graph_prof_broken)) {
     for (int i = 0; i < kChunk; ++i) {
       const cudaEvent_t* ev = ev_take(h, RR_PROF_MATVEC);
       if (h->o.variant == RR_VARIANT_C) iter_C<T>(h, ev);
@@ -922,6 +929,7 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
   h->prof = o.profile != 0;
   memset(&h->pacc, 0, sizeof(h->pacc));
   h->graph_pending = false;
+  h->graph_prof_broken = false;
   if (h->prof) {
     for (int i = 0; i < 64 + kChunk; ++i) {
       rr_handle::EvPair p;
