@@ -87,6 +87,92 @@ static unsigned grid_rows(int64_t n, int rows_per_thread_block) {
 
 // ============================================================ Q^T V slabs
 // part[slab][j][c] = sum_{i in slab} Q[i][j] V[i][c]
+
+// Q^T V over a row slab, 4 consecutive columns of Q per thread (16-byte
+// loads) and several rows in flight, so that enough bytes are outstanding
+// to stream Q at memory bandwidth.  Vs: the slab's rows of V (cnt x MP) in
+// shared memory; red: scratch of (kNT / nq) * 4 * MP * ... floats.
+// Threads t < nq * rph own quad q = t % nq and rows i = t / nq + rph * u.
+template <int MP>
+__device__ __forceinline__ void slab_qt_vec4(const float* __restrict__ Q, int64_t r0, int cnt,
+                                             int k, const float* Vs, double* __restrict__ out,
+                                             float* red) {
+  const int nq = k >> 2;
+  const int rph = kNT / nq;                 // row phases (>= 1 for k <= 4 * kNT)
+  const int t = threadIdx.x;
+  const int q = t % nq, ph = t / nq;
+  float acc[4][MP];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < MP; ++c) acc[a][c] = 0.f;
+  if (ph < rph) {
+    const float4* qb = reinterpret_cast<const float4*>(Q + r0 * k) + q;
+    int i = ph;
+#pragma unroll 1
+    for (; i + 3 * rph < cnt; i += 4 * rph) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = qb[(int64_t)(i + u * rph) * nq];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float* vr = Vs + (i + u * rph) * MP;
+#pragma unroll
+        for (int c = 0; c < MP; ++c) {
+          const float r = vr[c];
+          acc[0][c] = fmaf(v[u].x, r, acc[0][c]);
+          acc[1][c] = fmaf(v[u].y, r, acc[1][c]);
+          acc[2][c] = fmaf(v[u].z, r, acc[2][c]);
+          acc[3][c] = fmaf(v[u].w, r, acc[3][c]);
+        }
+      }
+    }
+    for (; i < cnt; i += rph) {
+      const float4 v = qb[(int64_t)i * nq];
+      const float* vr = Vs + i * MP;
+#pragma unroll
+      for (int c = 0; c < MP; ++c) {
+        const float r = vr[c];
+        acc[0][c] = fmaf(v.x, r, acc[0][c]);
+        acc[1][c] = fmaf(v.y, r, acc[1][c]);
+        acc[2][c] = fmaf(v.z, r, acc[2][c]);
+        acc[3][c] = fmaf(v.w, r, acc[3][c]);
+      }
+    }
+  }
+  // reduce the row phases in fixed order (deterministic)
+  if (rph > 1) {
+    if (ph < rph && ph > 0) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < MP; ++c) red[((ph - 1) * nq + q) * 4 * MP + a * MP + c] = acc[a][c];
+    }
+    __syncthreads();
+    if (ph == 0) {
+      for (int p2 = 1; p2 < rph; ++p2)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < MP; ++c) acc[a][c] += red[((p2 - 1) * nq + q) * 4 * MP + a * MP + c];
+    }
+  }
+  if (ph == 0) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < MP; ++c) out[(int64_t)(4 * q + a) * MP + c] = (double)acc[a][c];
+  }
+}
+
+// red scratch floats needed by slab_qt_vec4
+__host__ __device__ inline size_t slab_red_floats(int k, int mp) {
+  const int nq = k / 4;
+  const int rph = nq > 0 ? kNT / nq : 1;
+  return (size_t)(rph > 1 ? rph - 1 : 0) * nq * 4 * mp;
+}
+__host__ __device__ inline bool vec4_ok(int k) { return (k % 4) == 0 && k / 4 <= kNT && k >= 4; }
+
 template <typename T, int MP>
 __global__ void __launch_bounds__(kNT) k_qt_partial(const T* __restrict__ Q, const T* __restrict__ V,
                                                     int64_t n, int k, int rps,
@@ -100,6 +186,11 @@ __global__ void __launch_bounds__(kNT) k_qt_partial(const T* __restrict__ Q, con
   for (int e = threadIdx.x; e < cnt * MP; e += kNT) Vs[e] = V[r0 * MP + e];
   __syncthreads();
   double* out = part + (int64_t)blockIdx.x * k * MP;
+  if (sizeof(T) == 4 && vec4_ok(k)) {
+    slab_qt_vec4<MP>((const float*)Q, r0, cnt, k, (const float*)Vs, out,
+                     (float*)(smem_raw + (size_t)rps * MP * sizeof(T)));
+    return;
+  }
   for (int j = threadIdx.x; j < k; j += kNT) {
     T acc[MP];
 #pragma unroll
@@ -120,7 +211,7 @@ template <typename T>
 static void qt_partial_launch(const T* Q, const T* V, int64_t n, int k, int mp, int nslab,
                               double* part, const ColState* cs, cudaStream_t st) {
   const int rps = qt_rows_per_slab(n);
-  const size_t smem = (size_t)rps * mp * sizeof(T);
+  const size_t smem = (size_t)rps * mp * sizeof(T) + slab_red_floats(k, mp) * sizeof(float);
   switch (mp) {
     case 1: k_qt_partial<T, 1><<<(unsigned)nslab, kNT, smem, st>>>(Q, V, n, k, rps, part, cs); break;
     case 2: k_qt_partial<T, 2><<<(unsigned)nslab, kNT, smem, st>>>(Q, V, n, k, rps, part, cs); break;
@@ -325,6 +416,44 @@ __global__ void __launch_bounds__(kNT) k_qcomb(const T* __restrict__ Q, int64_t 
   const T acoef = (T)a.v[col];
   const int64_t warps_total = (int64_t)gridDim.x * (kNT / 32);
   double dacc = 0.0;
+  if (sizeof(T) == 4 && (k % 4) == 0) {
+    // 16-byte loads of Q, two rows per step: 2 x ceil(k/128) loads in flight per lane
+    const int nq = k >> 2;
+    const float4* ts4 = reinterpret_cast<const float4*>(ts);
+    for (int64_t row = ((int64_t)blockIdx.x * (kNT / 32) + (threadIdx.x >> 5)) * 2; row < n;
+         row += 2 * warps_total) {
+      const bool two = row + 1 < n;
+      float acc0[MP], acc1[MP];
+#pragma unroll
+      for (int c = 0; c < MP; ++c) { acc0[c] = 0.f; acc1[c] = 0.f; }
+      const float4* q0 = reinterpret_cast<const float4*>(Q + row * k);
+      const float4* q1 = reinterpret_cast<const float4*>(Q + (two ? row + 1 : row) * k);
+#pragma unroll 4
+      for (int jq = lane; jq < nq; jq += 32) {
+        const float4 a = q0[jq];
+        const float4 b = q1[jq];
+#pragma unroll
+        for (int c = 0; c < MP; ++c) {
+          const float4 tv = ts4[c * nq + jq];
+          acc0[c] = fmaf(a.x, tv.x, fmaf(a.y, tv.y, fmaf(a.z, tv.z, fmaf(a.w, tv.w, acc0[c]))));
+          acc1[c] = fmaf(b.x, tv.x, fmaf(b.y, tv.y, fmaf(b.z, tv.z, fmaf(b.w, tv.w, acc1[c]))));
+        }
+      }
+      const float v0 = warp_transpose_reduce<MP>(acc0, lane);
+      const float v1 = warp_transpose_reduce<MP>(acc1, lane);
+      if (writer) {
+#pragma unroll
+        for (int rr2 = 0; rr2 < 2; ++rr2) {
+          if (rr2 == 1 && !two) break;
+          const int64_t idx = (row + rr2) * MP + col;
+          const float v = rr2 ? v1 : v0;
+          const float o = (X ? (float)acoef * (float)X[idx] : 0.f) + v;
+          out[idx] = (T)o;
+          if (D) dacc += (double)D[idx] * (double)o;
+        }
+      }
+    }
+  } else
   for (int64_t row = (int64_t)blockIdx.x * (kNT / 32) + (threadIdx.x >> 5); row < n;
        row += warps_total) {
     T acc[MP];
@@ -460,7 +589,11 @@ __global__ void __launch_bounds__(kNT) k_update_qt(T* __restrict__ E, T* __restr
       if (cc == c) v[cc] += (double)r * (double)r;
   }
   __syncthreads();
-  if (tpart) {
+  if (tpart && sizeof(T) == 4 && vec4_ok(k)) {
+    slab_qt_vec4<MP>((const float*)Q, r0, cnt, k, (const float*)Rs,
+                     tpart + (int64_t)blockIdx.x * k * MP,
+                     (float*)(smem_raw + (size_t)rps * MP * sizeof(T)));
+  } else if (tpart) {
     double* out = tpart + (int64_t)blockIdx.x * k * MP;
     for (int j = threadIdx.x; j < k; j += kNT) {
       T acc[MP];
@@ -499,7 +632,7 @@ void update_qt(T* E, T* R, const T* P, const T* W, const T* Q, int64_t n, int k,
                double* tpart, double* part, unsigned* counter, ColState* cs, cudaStream_t st) {
   const int rps = qt_rows_per_slab(n);
   const int nslab = qt_nslab(n);
-  const size_t smem = (size_t)rps * mp * sizeof(T);
+  const size_t smem = (size_t)rps * mp * sizeof(T) + slab_red_floats(k, mp) * sizeof(float);
   switch (mp) {
     case 1: k_update_qt<T, 1><<<(unsigned)nslab, kNT, smem, st>>>(E, R, P, W, Q, n, k, rps, tpart, part, counter, cs); break;
     case 2: k_update_qt<T, 2><<<(unsigned)nslab, kNT, smem, st>>>(E, R, P, W, Q, n, k, rps, tpart, part, counter, cs); break;
