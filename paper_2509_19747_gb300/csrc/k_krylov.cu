@@ -56,11 +56,33 @@ __device__ __forceinline__ void block_sum_cols(double* v, int mp, double* sh /*[
   __syncthreads();
 }
 
-// sum over blocks of part[b][c] in block order, by thread 0 of the last block
+// sum over blocks of part[b][c], by thread 0 of the last block (small nb)
 __device__ __forceinline__ double sum_parts(const double* part, int nb, int mp, int c) {
   double s = 0.0;
   for (int b = 0; b < nb; ++b) s += part[(int64_t)b * mp + c];
   return s;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum_cols(double* v, int mp, double* sh);
+
+// All threads of the last block: tot[c] = sum_b part[b][c] for c < mp, in a
+// fixed order (thread t takes blocks t, t+NT, ...; then a fixed tree), so
+// the result does not depend on timing.  Result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ void sum_parts_block(const double* part, int nb, int mp, double* tot,
+                                                double* sh) {
+  double v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += NT) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (c < mp) v[c] += part[(int64_t)b * mp + c];
+  }
+  block_sum_cols<NT>(v, mp, sh);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) tot[c] = v[c];
 }
 
 __device__ __forceinline__ bool any_active(const ColState* cs, int mp) {
@@ -482,8 +504,10 @@ __global__ void __launch_bounds__(kNT) k_qcomb(const T* __restrict__ Q, int64_t 
   if (threadIdx.x == 0)
     for (int c = 0; c < MP; ++c) part[(int64_t)blockIdx.x * MP + c] = vv[c];
   if (!last_block(counter)) return;
+  double tot[8];
+  sum_parts_block<kNT>(part, gridDim.x, MP, tot, red);
   if (threadIdx.x == 0)
-    for (int c = 0; c < MP; ++c) finish_mode(cs[c], mode, sum_parts(part, gridDim.x, MP, c));
+    for (int c = 0; c < MP; ++c) finish_mode(cs[c], mode, tot[c]);
 }
 
 template <typename T>
@@ -532,9 +556,11 @@ __global__ void __launch_bounds__(kNT) k_dot_cols(const T* __restrict__ X, const
   if (threadIdx.x == 0)
     for (int c = 0; c < MP; ++c) part[(int64_t)blockIdx.x * MP + c] = v[c];
   if (!last_block(counter)) return;
+  double tot[8];
+  sum_parts_block<kNT>(part, gridDim.x, MP, tot, red);
   if (threadIdx.x == 0) {
     for (int c = 0; c < MP; ++c) {
-      const double s = sum_parts(part, gridDim.x, MP, c);
+      const double s = tot[c];
       if (out_raw) out_raw[c] = s;
       if (cs && mode != kModeNone) finish_mode(cs[c], mode, s);
     }
@@ -614,10 +640,12 @@ __global__ void __launch_bounds__(kNT) k_update_qt(T* __restrict__ E, T* __restr
   if (threadIdx.x == 0)
     for (int c = 0; c < MP; ++c) part[(int64_t)blockIdx.x * MP + c] = v[c];
   if (!last_block(counter)) return;
+  double tot[8];
+  sum_parts_block<kNT>(part, gridDim.x, MP, tot, red);
   if (threadIdx.x == 0) {
     for (int c = 0; c < MP; ++c) {
       ColState& st = cs[c];
-      const double s = sum_parts(part, gridDim.x, MP, c);
+      const double s = tot[c];
       st.rr = s;
       if (!st.active) continue;
       st.iters += 1;
@@ -673,10 +701,12 @@ __global__ void __launch_bounds__(kNT) k_update_cg(T* __restrict__ Yv, T* __rest
   if (threadIdx.x == 0)
     for (int c = 0; c < mp; ++c) part[(int64_t)blockIdx.x * mp + c] = v[c];
   if (!last_block(counter)) return;
+  double tot[8];
+  sum_parts_block<kNT>(part, gridDim.x, mp, tot, red);
   if (threadIdx.x == 0) {
     for (int c = 0; c < mp; ++c) {
       ColState& st = cs[c];
-      const double s = sum_parts(part, gridDim.x, mp, c);
+      const double s = tot[c];
       st.rr = s;
       if (!st.active) continue;
       st.iters += 1;
