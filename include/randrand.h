@@ -121,8 +121,9 @@ typedef struct {
   int32_t power_iters;   /* power iterations per estimate, default 20           */
   int32_t max_rhs;       /* right-hand sides a solve may pass (1..8), default 1 */
   int32_t profile;       /* 1: time the hot kernels with CUDA events (rr_profile) */
-  int32_t sketch_impl;   /* kernel-operator sketch in RR_PREC_MIXED: 0 auto (tensor
-                            cores when dim == 8), 1 float32 cores, 2 tensor cores */
+  int32_t kernel_impl;   /* Gaussian-kernel sketch (RR_PREC_MIXED) and float32
+                            products (FP32 / MIXED), dim == 8: 0 auto (tensor
+                            cores), 1 float32 cores only, 2 tensor cores required */
   double rho;            /* C variant: <= 0 -> eq:optimal_rho with F = 1/mu     */
   double restart_eta;    /* restart after this residual reduction, default 1e-2 */
 } rr_build_opts;
@@ -259,6 +260,14 @@ rr_status randrand_scalars(const rr_handle* h, double* tau, double* normE, doubl
  * Enqueued on the handle stream; does not synchronise.
  */
 rr_status randrand_apply(rr_handle* h, const double* r, double* z, int32_t m, int64_t ld);
+
+/*
+ * Product with the shifted operator in the handle's working precision
+ * (float32 for RR_PREC_FP32 / RR_PREC_MIXED, the arithmetic of the Krylov
+ * iterations), w = (A + mu I) v.  v, w device n x m float64 column-major
+ * (converted at the boundary), ld >= n, m <= max_rhs.  Test hook.
+ */
+rr_status randrand_apply_operator(rr_handle* h, const double* v, double* w, int32_t m, int64_t ld);
 
 /*
  * Product with the shifted operator, w = (A + mu I) v, float64 accurate

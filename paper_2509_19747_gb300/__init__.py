@@ -53,7 +53,7 @@ class rr_build_opts(ctypes.Structure):
         ("variant", ctypes.c_int32), ("precision", ctypes.c_int32), ("orth", ctypes.c_int32),
         ("gamma", ctypes.c_int32), ("l_sk", ctypes.c_int32), ("gamma_sk", ctypes.c_int32),
         ("power_iters", ctypes.c_int32), ("max_rhs", ctypes.c_int32), ("profile", ctypes.c_int32),
-        ("sketch_impl", ctypes.c_int32), ("rho", ctypes.c_double), ("restart_eta", ctypes.c_double),
+        ("kernel_impl", ctypes.c_int32), ("rho", ctypes.c_double), ("restart_eta", ctypes.c_double),
     ]
 
 
@@ -114,6 +114,8 @@ _SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p]),
     ("randrand_matvec", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
+    ("randrand_apply_operator", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
 ]
 
@@ -223,6 +225,12 @@ def randrand_profile(h) -> dict:
     return {nm: (int(p.launches[i]), float(p.ms[i])) for i, nm in enumerate(names)}
 
 
+def randrand_apply_operator(h, v_ptr, w_ptr, m, ld) -> None:
+    s = _lib().randrand_apply_operator(h, ctypes.c_void_p(v_ptr), ctypes.c_void_p(w_ptr), int(m), int(ld))
+    if s != RR_OK:
+        raise RandRandError(s, "randrand_apply_operator")
+
+
 def randrand_matvec(h, v_ptr, w_ptr, m, ld) -> None:
     s = _lib().randrand_matvec(h, ctypes.c_void_p(v_ptr), ctypes.c_void_p(w_ptr), int(m), int(ld))
     if s != RR_OK:
@@ -280,7 +288,7 @@ class Handle:
     def __init__(self, op: Operator, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
                  variant: str = "C", precision: str = "fp64", max_rhs: int = 1,
                  power_iters: int = 20, rho: float = 0.0, restart_eta: float = 1e-2,
-                 gamma: int = 8, profile: bool = False, sketch_impl: int = 0, stream=None):
+                 gamma: int = 8, profile: bool = False, kernel_impl: int = 0, stream=None):
         import torch
         self.op = op
         self.n = op.n
@@ -294,7 +302,7 @@ class Handle:
         o.restart_eta = restart_eta
         o.gamma = gamma
         o.profile = 1 if profile else 0
-        o.sketch_impl = sketch_impl
+        o.kernel_impl = kernel_impl
         self.opts = o
         self.ws_bytes = randrand_workspace_bytes(op.c, k, o)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
@@ -344,6 +352,16 @@ class Handle:
         randrand_apply(self.h, Rc.data_ptr(), Zc.data_ptr(), Rc.shape[0], self.n)
         self.stream.synchronize()
         return Zc.t().reshape(r.shape)
+
+    def apply_operator(self, v):
+        """(A + mu I) v in the handle's working precision (float32 paths)."""
+        import torch
+        V = v.reshape(self.n, -1)
+        Vc = V.t().contiguous()
+        Wc = torch.empty_like(Vc)
+        randrand_apply_operator(self.h, Vc.data_ptr(), Wc.data_ptr(), Vc.shape[0], self.n)
+        self.stream.synchronize()
+        return Wc.t().reshape(v.shape)
 
     def matvec(self, v):
         import torch

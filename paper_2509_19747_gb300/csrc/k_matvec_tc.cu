@@ -1,0 +1,358 @@
+// Gaussian-kernel product w = K v (float32 result) with the exponent
+// arguments computed on the 5th-generation tensor cores.
+//
+// K_ij = 2^(a_ij), a_ij = xs_i . xs_j + cn_i + cn_j (the exp2 form of
+// exp(-|x_i - x_j|^2 / (2 h^2)), see prepare_kernel_points).  Writing
+// u_i = [xs_i, cn_i, 1, 0...] and w_j = [xs_j, 1, cn_j, 0...] (16 floats),
+// a_ij = u_i . w_j is a K = 16 contraction.  Each vector is split into a
+// TF32 head and a TF32 tail (x = hi + lo); the three-term product
+// hi.hi + hi.lo + lo.hi (the published "3xTF32" split) gives ~float32
+// accuracy, so the CTA contracts augmented rows [u_hi u_hi u_lo] with
+// [w_hi w_lo w_hi]: K = 48, six tcgen05.mma kind::tf32 instructions.
+//
+// CTA: two blocks of 128 rows (TMEM lanes) x a range of points, in tiles of
+// 128 points; per tile the MMA writes 128 x 128 exponent arguments per row
+// block into TMEM (double-buffered: 2 row blocks x 2 buffers x 128 columns =
+// all 512 columns), and 8 epilogue warps read them with tcgen05.ld (thread =
+// row), apply ex2 (MUFU) and accumulate w_i += K_ij v_j in registers with
+// v_j broadcast from shared memory.  No cross-thread reduction is needed.
+//   warp 0   TMA: augmented row blocks (once), point tiles (3 stages), and
+//            the matching rows of v (bulk copy, 4 stages);
+//   warp 1   TMEM allocation; one thread issues the MMAs and commits;
+//   warps 2-9 epilogue.
+// All waits are bounded (error flag instead of a hang).
+#include <cuda.h>
+
+#include <cmath>
+
+#include "rr_common.cuh"
+#include "tc_common.cuh"
+
+namespace rr {
+namespace {
+using namespace tc;
+
+constexpr int kRows = 128;           // rows per row block (TMEM lanes)
+constexpr int kRB = 2;               // row blocks per CTA
+constexpr int kPts = 128;            // points per tile (MMA N)
+constexpr int kKf = 64;              // floats per augmented vector (48 used)
+constexpr int kKSteps = 6;           // 48 / 8 tf32 MMAs
+constexpr int kStagesB = 3;
+constexpr int kStagesV = 4;
+constexpr int kEpiWarps = 8;
+constexpr int kThreadsMv = 32 * (2 + kEpiWarps);
+constexpr int kAtomA = kRows * 128;  // one 32-float K atom of a row block (16 KB)
+constexpr int kAtomB = kPts * 128;   // one 32-float K atom of a point tile (16 KB)
+constexpr int kABytes = kRB * 2 * kAtomA;    // 64 KB
+constexpr int kBBytes = 2 * kAtomB;          // 32 KB per stage
+constexpr uint32_t kTmemCols = 512;
+
+template <int MP>
+struct MvSmem {
+  float v[kStagesV][kPts * MP];
+  unsigned long long a_full;
+  unsigned long long b_full[kStagesB], b_empty[kStagesB];
+  unsigned long long v_full[kStagesV], v_empty[kStagesV];
+  unsigned long long t_full[2], t_empty[2];
+  uint32_t tmem_base;
+  int abort;
+};
+
+template <int MP>
+constexpr size_t mv_smem_bytes() {
+  return 1024 + (size_t)kABytes + (size_t)kStagesB * kBBytes + sizeof(MvSmem<MP>);
+}
+
+template <int MP>
+__global__ void __launch_bounds__(kThreadsMv, 1)
+    k_kernel_mv_tc(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+                   int64_t n, int64_t pts_per_split, const float* __restrict__ V,
+                   float* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = base;
+  unsigned char* sB = base + kABytes;
+  MvSmem<MP>* sm = (MvSmem<MP>*)(sB + (size_t)kStagesB * kBBytes);
+  volatile int* abort = &sm->abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = (int64_t)blockIdx.x * (kRows * kRB);
+  const int64_t j0 = (int64_t)blockIdx.y * pts_per_split;
+  int64_t j1 = j0 + pts_per_split;
+  if (j1 > n) j1 = n;
+  const int ntiles = (j1 > j0) ? (int)((j1 - j0 + kPts - 1) / kPts) : 0;
+  constexpr uint32_t kVBytes = kPts * MP * 4;
+  constexpr uint32_t idesc = make_idesc(kFmtTF32, kRows, kPts);
+
+  if (threadIdx.x == 0) {
+    mbar_init(&sm->a_full, 1);
+    for (int s = 0; s < kStagesB; ++s) {
+      mbar_init(&sm->b_full[s], 1);
+      mbar_init(&sm->b_empty[s], 1);
+    }
+    for (int s = 0; s < kStagesV; ++s) {
+      mbar_init(&sm->v_full[s], 1);
+      mbar_init(&sm->v_empty[s], kEpiWarps);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&sm->t_full[s], 1);
+      mbar_init(&sm->t_empty[s], kEpiWarps);
+    }
+    sm->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(&sm->tmem_base, kTmemCols);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = sm->tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0 && ntiles > 0) {
+      mbar_arrive_tx(&sm->a_full, kABytes);
+      for (int b = 0; b < kRB; ++b)
+        for (int a = 0; a < 2; ++a)
+          tma_load_2d(sA + (size_t)(b * 2 + a) * kAtomA, &amap, 32 * a, (int)(row0 + b * kRows),
+                      &sm->a_full);
+      int issued_b = 0, issued_v = 0;
+      for (int t = 0; t < ntiles; ++t) {
+        const int sb = t % kStagesB, sv = t % kStagesV;
+        const int64_t jt = j0 + (int64_t)t * kPts;
+        if (t >= kStagesB && !mbar_wait(&sm->b_empty[sb], ((t / kStagesB) - 1) & 1, err, abort)) break;
+        mbar_arrive_tx(&sm->b_full[sb], kBBytes);
+        for (int a = 0; a < 2; ++a)
+          tma_load_2d(sB + (size_t)sb * kBBytes + (size_t)a * kAtomB, &bmap, 32 * a, (int)jt,
+                      &sm->b_full[sb]);
+        ++issued_b;
+        if (t >= kStagesV && !mbar_wait(&sm->v_empty[sv], ((t / kStagesV) - 1) & 1, err, abort)) break;
+        mbar_arrive_tx(&sm->v_full[sv], kVBytes);
+        bulk_load(sm->v[sv], V + jt * MP, kVBytes, &sm->v_full[sv]);
+        ++issued_v;
+      }
+      // no bulk copy may still be writing shared memory when the CTA exits
+      mbar_wait(&sm->a_full, 0, err, abort);
+      for (int t = (issued_b > kStagesB ? issued_b - kStagesB : 0); t < issued_b; ++t)
+        mbar_wait(&sm->b_full[t % kStagesB], (t / kStagesB) & 1, err, abort);
+      for (int t = (issued_v > kStagesV ? issued_v - kStagesV : 0); t < issued_v; ++t)
+        mbar_wait(&sm->v_full[t % kStagesV], (t / kStagesV) & 1, err, abort);
+    }
+  } else if (warp == 1) {
+    // ----------------------------------------------------------------- MMA
+    if (lane == 0 && ntiles > 0) {
+      bool ok = mbar_wait(&sm->a_full, 0, err, abort);
+      for (int t = 0; t < ntiles && ok; ++t) {
+        const int sb = t % kStagesB, buf = t & 1;
+        ok = mbar_wait(&sm->b_full[sb], (t / kStagesB) & 1, err, abort);
+        if (ok && t >= 2) ok = mbar_wait(&sm->t_empty[buf], ((t >> 1) - 1) & 1, err, abort);
+        if (!ok) break;
+        fence_after();
+        const uint32_t bbase = smem_u32(sB + (size_t)sb * kBBytes);
+        for (int b = 0; b < kRB; ++b) {
+          const uint32_t abase = smem_u32(sA + (size_t)b * 2 * kAtomA);
+          const uint32_t d = tmem + (uint32_t)(b * 256 + buf * kPts);
+#pragma unroll
+          for (int kk = 0; kk < kKSteps; ++kk) {
+            const uint32_t off = (uint32_t)(kk & 3) * 32;
+            const uint64_t ad = umma_desc_sw128(abase + (kk >> 2) * kAtomA + off);
+            const uint64_t bd = umma_desc_sw128(bbase + (kk >> 2) * kAtomB + off);
+            mma_tf32(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+          }
+        }
+        mma_commit(&sm->b_empty[sb]);
+        mma_commit(&sm->t_full[buf]);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;                     // TMEM lane quarter of this warp
+    const int b = (warp - 2) >> 2;              // row block
+    const int64_t gi = row0 + b * kRows + q * 32 + lane;
+    float acc[MP];
+#pragma unroll
+    for (int c = 0; c < MP; ++c) acc[c] = 0.f;
+    bool ok = true;
+    for (int t = 0; t < ntiles; ++t) {
+      const int buf = t & 1, sv = t % kStagesV;
+      ok = ok && mbar_wait(&sm->t_full[buf], (t >> 1) & 1, err, abort);
+      ok = ok && mbar_wait(&sm->v_full[sv], (t / kStagesV) & 1, err, abort);
+      ok = __all_sync(0xffffffffu, ok);            // tcgen05.ld is warp-collective
+      if (!ok) break;
+      fence_after();
+      const float* vs = sm->v[sv];
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256 + buf * kPts);
+#pragma unroll 1
+      for (int ch = 0; ch < kPts / 32; ++ch) {
+        uint32_t a[32];
+        tmem_ld32(tbase + (uint32_t)(ch * 32), a);
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const float kij = ex2_approx(__uint_as_float(a[u]));
+          const float* vj = vs + (ch * 32 + u) * MP;
+          if (MP == 4) {
+            const float4 v4 = *reinterpret_cast<const float4*>(vj);
+            acc[0] = fmaf(kij, v4.x, acc[0]);
+            acc[1] = fmaf(kij, v4.y, acc[1]);
+            acc[2 % MP] = fmaf(kij, v4.z, acc[2 % MP]);
+            acc[3 % MP] = fmaf(kij, v4.w, acc[3 % MP]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < MP; ++c) acc[c] = fmaf(kij, vj[c], acc[c]);
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&sm->t_empty[buf]);
+        mbar_arrive(&sm->v_empty[sv]);
+      }
+    }
+    if (ok && gi < n) {
+      float* out = part + ((int64_t)blockIdx.y * n + gi) * MP;
+#pragma unroll
+      for (int c = 0; c < MP; ++c) out[c] = acc[c];
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// augmented TF32-split vectors: A rows [u_hi u_hi u_lo 0], B rows [w_hi w_lo w_hi 0]
+__device__ __forceinline__ float tf32_head(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__global__ void k_prep_aug(const float* __restrict__ xs, const float* __restrict__ cn, int64_t n,
+                           int64_t npad, float* __restrict__ A, float* __restrict__ B) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  float u[16], w[16];
+#pragma unroll
+  for (int d = 0; d < 16; ++d) { u[d] = 0.f; w[d] = 0.f; }
+  if (i < n) {
+#pragma unroll
+    for (int d = 0; d < 8; ++d) { u[d] = xs[i * 8 + d]; w[d] = u[d]; }
+    u[8] = cn[i];
+    u[9] = 1.f;
+    w[8] = 1.f;
+    w[9] = cn[i];
+  } else {
+    w[8] = 1.f;
+    w[9] = -1e30f;     // padded points: exponent -inf, K = 0
+  }
+  float* ar = A + i * kKf;
+  float* br = B + i * kKf;
+#pragma unroll
+  for (int d = 0; d < 16; ++d) {
+    const float uh = tf32_head(u[d]), ul = u[d] - uh;
+    const float wh = tf32_head(w[d]), wl = w[d] - wh;
+    ar[d] = uh; ar[16 + d] = uh; ar[32 + d] = ul; ar[48 + d] = 0.f;
+    br[d] = wh; br[16 + d] = wl; br[32 + d] = wh; br[48 + d] = 0.f;
+  }
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+bool encode_aug(CUtensorMap* map, const float* base, int64_t npad) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t gdim[2] = {(cuuint64_t)kKf, (cuuint64_t)npad};
+  const cuuint64_t gstride[1] = {(cuuint64_t)kKf * 4};
+  const cuuint32_t box[2] = {32, (cuuint32_t)kRows};
+  const cuuint32_t estride[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, gdim, gstride, box, estride,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MP>
+bool set_attr() {
+  static bool done = false;
+  if (!done) {
+    if (cudaFuncSetAttribute(k_kernel_mv_tc<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)mv_smem_bytes<MP>()) != cudaSuccess)
+      return false;
+    done = true;
+  }
+  return true;
+}
+
+}  // namespace
+
+int64_t mv_tc_pad(int64_t n) { return cdiv(n, kRows * kRB) * (kRows * kRB); }
+
+void prepare_mv_tc(const OpDev& op, float* Aaug, float* Baug, cudaStream_t st) {
+  const int64_t npad = mv_tc_pad(op.n);
+  k_prep_aug<<<(unsigned)cdiv(npad, 128), 128, 0, st>>>(op.xs, op.cn, op.n, npad, Aaug, Baug);
+}
+
+// maps are encoded once per handle (the augmented arrays do not move)
+bool encode_mv_tc(const float* Aaug, const float* Baug, int64_t n, void* amap, void* bmap) {
+  const int64_t npad = mv_tc_pad(n);
+  return encode_aug((CUtensorMap*)amap, Aaug, npad) && encode_aug((CUtensorMap*)bmap, Baug, npad);
+}
+
+int mv_tc_nsplit(int64_t n) {
+  const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
+  int64_t s = cdiv(4 * 152, pairs);     // about 4 waves of one CTA per SM
+  const int64_t tiles = cdiv(n, kPts);
+  if (s > tiles / 8) s = tiles / 8;     // at least ~8 tiles per CTA
+  if (s < 1) s = 1;
+  return (int)s;
+}
+
+// part[s][i][c] = sum_{j in split s} K_ij V[j][c]; V must have mv_tc_pad(n)
+// rows (zero beyond n).  Returns false if the kernel cannot be launched.
+bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const float* V,
+                  float* part, int nsplit, int* err, cudaStream_t st) {
+  const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
+  const int64_t tiles = cdiv(n, kPts);
+  const int64_t pps = cdiv(tiles, nsplit) * kPts;
+  dim3 grid((unsigned)pairs, (unsigned)nsplit);
+  const CUtensorMap& am = *(const CUtensorMap*)amap;
+  const CUtensorMap& bm = *(const CUtensorMap*)bmap;
+  switch (mp) {
+    case 1:
+      if (!set_attr<1>()) return false;
+      k_kernel_mv_tc<1><<<grid, kThreadsMv, mv_smem_bytes<1>(), st>>>(am, bm, n, pps, V, part, err);
+      break;
+    case 2:
+      if (!set_attr<2>()) return false;
+      k_kernel_mv_tc<2><<<grid, kThreadsMv, mv_smem_bytes<2>(), st>>>(am, bm, n, pps, V, part, err);
+      break;
+    case 4:
+      if (!set_attr<4>()) return false;
+      k_kernel_mv_tc<4><<<grid, kThreadsMv, mv_smem_bytes<4>(), st>>>(am, bm, n, pps, V, part, err);
+      break;
+    default:
+      if (!set_attr<8>()) return false;
+      k_kernel_mv_tc<8><<<grid, kThreadsMv, mv_smem_bytes<8>(), st>>>(am, bm, n, pps, V, part, err);
+      break;
+  }
+  return cudaGetLastError() == cudaSuccess;
+}
+
+}  // namespace rr

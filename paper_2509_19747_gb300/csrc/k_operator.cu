@@ -388,7 +388,10 @@ static int kernel_nsplit(int64_t n) {
 
 size_t op_matvec_scratch_elems(const OpDev& op, int mp) {
   if (op.kind != RR_OP_GAUSS_KERNEL) return 0;
-  return (size_t)kernel_nsplit(op.n) * (size_t)op.n * (size_t)mp;
+  int ns = kernel_nsplit(op.n);
+  const int nt = mv_tc_nsplit(op.n);
+  if (nt > ns) ns = nt;
+  return (size_t)ns * (size_t)op.n * (size_t)mp;
 }
 
 // Inside a stream capture a plain event record only orders the capture; the
@@ -411,6 +414,15 @@ static void kernel_mv(const OpDev& op, double mu, const T* V, T* W, int mp, T* p
 template <>
 void kernel_mv<float>(const OpDev& op, double mu, const float* V, float* W, int mp, float* part,
                       cudaStream_t st, const cudaEvent_t* ev) {
+  if (op.use_tc) {
+    const int nt = mv_tc_nsplit(op.n);
+    rec(ev, 0, st);
+    if (kernel_mv_tc(op.amap, op.bmap, op.n, mp, V, part, nt, op.tc_err, st)) {
+      rec(ev, 1, st);
+      k_sum_splits<float><<<(unsigned)cdiv(op.n * mp, 256), 256, 0, st>>>(part, nt, op.n, mp, mu, V, W);
+      return;
+    }
+  }
   const int ns = kernel_nsplit(op.n);
   const int64_t cps = cdiv(cdiv(op.n, ns), kKmvTile) * kKmvTile;
   dim3 grid((unsigned)cdiv(op.n, kKmvRows * kRpt), (unsigned)ns);

@@ -21,9 +21,11 @@
 #include <cmath>
 
 #include "rr_common.cuh"
+#include "tc_common.cuh"
 
 namespace rr {
 namespace {
+using namespace tc;
 
 constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 4;
 constexpr int kGenWarps = 8;
@@ -33,7 +35,6 @@ constexpr int kBBytes = kBN * kBK * 2;   // 32 KB
 constexpr int kXsBytes = kBK * 8 * 4;    // 64 points x 8 coordinates
 constexpr int kCnBytes = kBK * 4;        // 64 values of cn
 constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kWaitLimit = 1u << 26;
 
 struct __align__(16) SmemTail {
   float xs[kStages][kBK * 8];
@@ -47,110 +48,6 @@ struct __align__(16) SmemTail {
 };
 
 constexpr size_t kSmemBytes = 1024 /*align slack*/ + (size_t)kStages * (kABytes + kBBytes) + sizeof(SmemTail);
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, uint32_t bytes) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
-                   smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// bounded wait for the phase with parity `parity` to complete
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, int* err,
-                                          volatile int* abort) {
-  const uint32_t a = smem_u32(bar);
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if ((it & 1023) == 1023 && *abort) return false;
-  }
-  atomicExch(err, 1);
-  *abort = 1;
-  return false;
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// plain bulk copy global -> shared (16-byte aligned, size a multiple of 16)
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
-                                          unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// tcgen05 shared-memory matrix descriptor: K-major operand in the canonical
-// 128-byte-swizzled layout (8-row x 128-byte atoms, 1024 bytes apart).
-__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);        // start address
-  d |= (uint64_t)(16 >> 4) << 16;                  // leading byte offset (unused for SW128 K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row atom
-  d |= (uint64_t)1 << 46;                          // descriptor version
-  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
-  return d;
-}
-
-// instruction descriptor: kind::f16, bf16 x bf16 -> f32, both K-major, M=128, N=256
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
-}
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_kernel_sketch_tc(const __grid_constant__ CUtensorMap omt_map, const float* __restrict__ xs,
@@ -223,8 +120,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t b0 = smem_u32(sB + (size_t)s * kBBytes);
 #pragma unroll
         for (int kk = 0; kk < kBK / 16; ++kk)
-          mma_bf16(tmem, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32),
-                   (st > 0 || kk > 0) ? 1u : 0u);
+          mma_f16(tmem, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32),
+                  make_idesc(kFmtBF16, kBM, kBN), (st > 0 || kk > 0) ? 1u : 0u);
         mma_commit(&tail->empty[s]);
       }
       mma_commit(&tail->done);

@@ -25,7 +25,7 @@ constexpr int kMaxRestarts = 400;
 
 enum Region {
   R_OM, R_OMB, R_SSC, R_SSS, R_Y, R_Q, R_KK, R_KKT, R_GPART, R_CHOLW, R_STATUS, R_XS, R_CN,
-  R_PN, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT, R_CS, R_NORMS, R_NREG
+  R_PN, R_AUG, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT, R_CS, R_NORMS, R_NREG
 };
 
 struct Layout {
@@ -70,8 +70,12 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_XS] = (A.kind == RR_OP_GAUSS_KERNEL) ? npts * (size_t)A.dim * 4 : 0;
   L.size[R_CN] = (A.kind == RR_OP_GAUSS_KERNEL) ? npts * 4 : 0;
   L.size[R_PN] = (A.kind == RR_OP_GAUSS_KERNEL) ? n * 8 : 0;
+  // tensor-core product: two augmented arrays of 64 floats per (padded) point
+  const size_t npad_tc = (size_t)mv_tc_pad(A.n);
+  L.size[R_AUG] = (A.kind == RR_OP_GAUSS_KERNEL && A.dim == 8 && !uses_f64(o)) ? 2 * npad_tc * 64 * 4 : 0;
   L.size[R_MVS] = op_matvec_scratch_elems(od, mp) * 8;
-  L.size[R_VT] = 7 * n * (size_t)mp * ts;
+  // Krylov vectors carry zero rows up to the tensor-core tile multiple
+  L.size[R_VT] = 7 * (size_t)mv_tc_pad(A.n) * (size_t)mp * ts;
   L.size[R_V64] = 4 * n * (size_t)mp * 8;
   L.size[R_STAGE] = 2 * n * (size_t)mp * 8;
   L.size[R_TPART] = (size_t)qt_nslab(A.n) * kk * (size_t)mp * 8;
@@ -179,6 +183,8 @@ struct rr_handle {
   std::vector<EvPair> ev_graph;  // one pair per captured iteration
   bool graph_pending;
   bool graph_prof_broken;        // captured event records gave no timings
+  alignas(64) unsigned char amap[128];  // tensor maps of the augmented point arrays
+  alignas(64) unsigned char bmap[128];
 };
 
 namespace {
@@ -217,8 +223,12 @@ void carve(rr_handle* h) {
   h->mvs = at(R_MVS);
   const size_t ts = h->f64 ? 8 : 4;
   const size_t vec = (size_t)h->n * h->mp;
+  const size_t vecp = (size_t)mv_tc_pad(h->n) * h->mp;
   unsigned char* vb = (unsigned char*)at(R_VT);
-  for (int i = 0; i < 7; ++i) h->V[i] = vb + i * vec * ts;
+  for (int i = 0; i < 7; ++i) h->V[i] = vb + i * vecp * ts;
+  float* aug = (float*)at(R_AUG);
+  h->op.aug_a = aug;
+  h->op.aug_b = aug ? aug + (size_t)mv_tc_pad(h->n) * 64 : nullptr;
   double* v64 = (double*)at(R_V64);
   for (int i = 0; i < 4; ++i) h->v64[i] = v64 + i * vec;
   double* stg = (double*)at(R_STAGE);
@@ -508,7 +518,22 @@ rr_status build_impl(rr_handle* h) {
   cudaStream_t st = h->st;
   RR_CUDA_TRY(cudaMemsetAsync(h->cnt, 0, h->L.size[R_CNT], st));
   RR_CUDA_TRY(cudaMemsetAsync(h->cs, 0, h->L.size[R_CS], st));
+  RR_CUDA_TRY(cudaMemsetAsync(h->dstatus, 0, h->L.size[R_STATUS], st));
+  RR_CUDA_TRY(cudaMemsetAsync(h->V[0], 0, h->L.size[R_VT], st));   // zero pad rows
   if (h->op.kind == RR_OP_GAUSS_KERNEL) prepare_kernel_points(h->op, st);
+  // float32 kernel products on the tensor cores (kernel_impl 0 = auto, 2 = on)
+  h->op.use_tc = 0;
+  if (h->op.aug_a && h->o.kernel_impl != 1) {
+    prepare_mv_tc(h->op, h->op.aug_a, h->op.aug_b, st);
+    if (encode_mv_tc(h->op.aug_a, h->op.aug_b, n, h->amap, h->bmap)) {
+      h->op.amap = h->amap;
+      h->op.bmap = h->bmap;
+      h->op.tc_err = h->dstatus + 2;
+      h->op.use_tc = 1;
+    } else if (h->o.kernel_impl == 2) {
+      return RR_ERR_UNSUPPORTED;
+    }
+  }
   const bool mixed = h->o.precision == RR_PREC_MIXED;
   // Alg. 7 step 1: Omega (eq:testmatrix with q = 0) and Y_mu = A Omega + mu Omega
   const int64_t ldo = cdiv(n, 8) * 8;
@@ -520,7 +545,7 @@ rr_status build_impl(rr_handle* h) {
   }
   // tensor cores for the mixed-precision Gaussian-kernel sketch (bf16 operands)
   const bool tc = mixed && h->op.kind == RR_OP_GAUSS_KERNEL && h->sketch == RR_SKETCH_GAUSSIAN &&
-                  h->op.dim == 8 && h->o.sketch_impl != 1 && sizeof(T) == 4;
+                  h->op.dim == 8 && h->o.kernel_impl != 1 && sizeof(T) == 4;
   bool done_tc = false;
   if (tc) {
     RR_CUDA_TRY(cudaMemsetAsync(h->dstatus + 1, 0, sizeof(int), st));
@@ -534,7 +559,7 @@ rr_status build_impl(rr_handle* h) {
       RR_TRY(read_int(h, h->dstatus + 1, &err));
       if (err) return RR_ERR_TIMEOUT;
       done_tc = true;
-    } else if (s != RR_ERR_UNSUPPORTED || h->o.sketch_impl == 2) {
+    } else if (s != RR_ERR_UNSUPPORTED || h->o.kernel_impl == 2) {
       return s;
     }
   }
@@ -554,6 +579,11 @@ rr_status build_impl(rr_handle* h) {
   if (h->o.variant == RR_VARIANT_C) RR_TRY(core_matrix(h));
   RR_TRY(power_iterations<T>(h));
   choose_tau(h);
+  if (h->op.use_tc) {
+    int err = 0;
+    RR_TRY(read_int(h, h->dstatus + 2, &err));
+    if (err) return RR_ERR_TIMEOUT;
+  }
   if (h->o.variant == RR_VARIANT_C) {
     // P = I + Q (tau G - I) Q^T; keep QH = Q H so that z = r + QH (Q^T r)
     form_H(h->kk[kG], h->tau, h->kk[kH], k, st);
@@ -776,6 +806,11 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
     axpby<double, T, double>(X, coefs_all(1.0), Ev, coefs_all(1.0), X, n, mp, st);
   }
   RR_TRY(sync_status(h));
+  if (h->op.use_tc) {
+    int err = 0;
+    RR_TRY(read_int(h, h->dstatus + 2, &err));
+    if (err) return RR_ERR_TIMEOUT;
+  }
   rr_status worst = RR_OK;
   for (int c = 0; c < m; ++c) {
     if (stat[c] != RR_OK && worst == RR_OK) worst = stat[c];
@@ -854,6 +889,7 @@ void rr_build_opts_default(rr_build_opts* o) {
   o->rho = 0.0;
   o->restart_eta = 1e-2;
   o->profile = 0;
+  o->kernel_impl = 0;
 }
 
 const char* randrand_status_str(rr_status s) {
@@ -1041,6 +1077,26 @@ rr_status randrand_apply(rr_handle* h, const double* r, double* z, int32_t m, in
   if (h->f64) apply_impl<double>(h);
   else apply_impl<float>(h);
   scatter_cols(h->v64[kW64], h->n, h->mp, m, z, ld, h->st);
+  RR_CUDA_TRY(cudaGetLastError());
+  return RR_OK;
+}
+
+rr_status randrand_apply_operator(rr_handle* h, const double* v, double* w, int32_t m,
+                                  int64_t ld) {
+  if (!h || !v || !w || m < 1 || m > h->o.max_rhs || ld < h->n) return RR_ERR_INVALID_ARG;
+  gather_cols(v, ld, m, h->n, h->mp, h->v64[kX64], h->st);
+  if (h->f64) {
+    op_matvec<double>(h->op, h->mu, h->v64[kX64], h->v64[kW64], h->mp, (double*)h->mvs, h->st);
+  } else {
+    float* Vf = (float*)h->V[kU];
+    float* Wf = (float*)h->V[kW];
+    axpby<double, double, float>(h->v64[kX64], coefs_all(1.0), nullptr, coefs_all(0.0), Vf, h->n,
+                                 h->mp, h->st);
+    op_matvec<float>(h->op, h->mu, Vf, Wf, h->mp, (float*)h->mvs, h->st);
+    axpby<double, float, double>(nullptr, coefs_all(0.0), Wf, coefs_all(1.0), h->v64[kW64], h->n,
+                                 h->mp, h->st);
+  }
+  scatter_cols(h->v64[kW64], h->n, h->mp, m, w, ld, h->st);
   RR_CUDA_TRY(cudaGetLastError());
   return RR_OK;
 }

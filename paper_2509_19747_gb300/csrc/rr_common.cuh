@@ -49,6 +49,14 @@ struct OpDev {
   // (float32 pipes) instead of native float64; pn = |p_i|^2 as hi + lo
   int f64_df;
   float2* pn;
+  // tensor-core float32 product (k_matvec_tc.cu): augmented TF32-split
+  // point arrays, their tensor maps (host copies) and an error flag
+  int use_tc;
+  float* aug_a;
+  float* aug_b;
+  const void* amap;
+  const void* bmap;
+  int* tc_err;
 };
 
 // Per right-hand-side Krylov scalars, device resident.
@@ -133,6 +141,14 @@ void op_sketch(const OpDev& op, double mu, const T* Om, T* Y, int k, bool bf16,
 template <typename T>
 void csr_sketch_sparse(const OpDev& op, double mu, const int32_t* cols, const int8_t* sgn,
                        int gamma, T* Y, int k, cudaStream_t st, const cudaEvent_t* ev = nullptr);
+
+// k_matvec_tc.cu -- tensor-core float32 Gaussian-kernel product
+int64_t mv_tc_pad(int64_t n);
+void prepare_mv_tc(const OpDev& op, float* Aaug, float* Baug, cudaStream_t st);
+bool encode_mv_tc(const float* Aaug, const float* Baug, int64_t n, void* amap, void* bmap);
+int mv_tc_nsplit(int64_t n);
+bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const float* V,
+                  float* part, int nsplit, int* err, cudaStream_t st);
 
 // k_sketch_tc.cu -- tensor-core sketch of the Gaussian-kernel operator
 size_t sketch_tc_smem_bytes();

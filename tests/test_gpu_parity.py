@@ -305,7 +305,7 @@ def test_tensor_core_sketch_matches_float_cores(cuda_lib, n, k):
     X = W.mixture_points(n, seed=25)
     mu = 1e-3
     hs = [rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=25,
-                    precision="mixed", sketch_impl=impl) for impl in (1, 2)]
+                    precision="mixed", kernel_impl=impl) for impl in (1, 2)]
     R1, R2 = (h.export("R").cpu().numpy() for h in hs)
     cond = np.linalg.cond(R1)
     assert rel(R2, R1) <= 2e-6 * cond
@@ -314,3 +314,31 @@ def test_tensor_core_sketch_matches_float_cores(cuda_lib, n, k):
     x, status, _ = hs[1].solve(dev(b), rtol=1e-8)
     assert status == rr.RR_OK
     assert O.true_rel_residual(O.GaussKernelOp(X), mu, x.cpu().numpy(), b)[0] <= 1e-8
+
+
+@pytest.mark.parametrize("n,m", [(20000, 4), (3001, 4), (777, 1), (1000, 2), (515, 8)])
+def test_tensor_core_kernel_product(cuda_lib, n, m):
+    """Float32 Gaussian-kernel product with the exponent arguments contracted
+    on the tensor cores (augmented 3xTF32 split): agrees with the float64
+    oracle to float32-level accuracy relative to sum_j |K_ij v_j|, like the
+    float32-core product."""
+    rr = cuda_lib
+    X = W.mixture_points(n, seed=26)
+    mu = 1e-3
+    V = np.random.default_rng(3).standard_normal((n, m))
+    if n > 5000:
+        idx = np.random.default_rng(4).choice(n, 64, replace=False)
+        op_rows = O.GaussKernelOp(X)
+        K = np.exp(-((X[idx, None, :].astype(np.float64) - X[None, :, :].astype(np.float64)) ** 2).sum(-1) / 2)
+        ref = K @ V + mu * V[idx]
+        scale = np.abs(K) @ np.abs(V) + mu * np.abs(V[idx])
+    else:
+        op = O.GaussKernelOp(X)
+        ref = op.matmat(V) + mu * V
+        scale = op.matmat(np.abs(V)) + mu * np.abs(V)
+        idx = slice(None)
+    for impl in (1, 2):
+        h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, 16, "gaussian", seed=26,
+                      precision="mixed", max_rhs=m, kernel_impl=impl)
+        w = h.apply_operator(dev(V)).cpu().numpy().reshape(n, m)[idx]
+        assert np.max(np.abs(w - ref) / scale) <= 2e-5, impl
