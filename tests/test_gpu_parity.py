@@ -319,9 +319,13 @@ def test_tensor_core_sketch_matches_float_cores(cuda_lib, n, k):
 @pytest.mark.parametrize("n,m", [(20000, 4), (3001, 4), (777, 1), (1000, 2), (515, 8)])
 def test_tensor_core_kernel_product(cuda_lib, n, m):
     """Float32 Gaussian-kernel product with the exponent arguments contracted
-    on the tensor cores (augmented 3xTF32 split): agrees with the float64
-    oracle to float32-level accuracy relative to sum_j |K_ij v_j|, like the
-    float32-core product."""
+    on the tensor cores (augmented 3xTF32 split) against the float64 oracle,
+    relative to sum_j |K_ij v_j|.  The exponent a_ij = xs_i.xs_j + cn_i + cn_j
+    cancels terms of size |xs|^2 ~ 60 down to O(10); the split products carry
+    ~2^-22 relative error and the tensor-core float32 accumulation a few
+    ulps of 60, so |delta a| ~ 1e-5..4e-5 and K_ij is off by ln2 |delta a|:
+    bound 1e-4 (float32 cores: 2e-5).  The restart residual is float64-accurate,
+    so this only affects the inner iterations."""
     rr = cuda_lib
     X = W.mixture_points(n, seed=26)
     mu = 1e-3
@@ -341,4 +345,4 @@ def test_tensor_core_kernel_product(cuda_lib, n, m):
         h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, 16, "gaussian", seed=26,
                       precision="mixed", max_rhs=m, kernel_impl=impl)
         w = h.apply_operator(dev(V)).cpu().numpy().reshape(n, m)[idx]
-        assert np.max(np.abs(w - ref) / scale) <= 2e-5, impl
+        assert np.max(np.abs(w - ref) / scale) <= (2e-5 if impl == 1 else 1e-4), impl
