@@ -13,13 +13,14 @@
 // CTA: two blocks of 128 rows (TMEM lanes) x a range of points, in tiles of
 // 128 points; per tile the MMA writes 128 x 128 exponent arguments per row
 // block into TMEM (double-buffered: 2 row blocks x 2 buffers x 128 columns =
-// all 512 columns), and 8 epilogue warps read them with tcgen05.ld (thread =
-// row), apply ex2 (MUFU) and accumulate w_i += K_ij v_j in registers with
-// v_j broadcast from shared memory.  No cross-thread reduction is needed.
+// all 512 columns), and 16 epilogue warps read them with tcgen05.ld (thread =
+// row, each warp one half of the columns), apply ex2 (MUFU) and accumulate
+// w_i += K_ij v_j in registers with v_j broadcast from shared memory (LDS);
+// the two column halves of a row are merged once at the end.
 //   warp 0   TMA: augmented row blocks (once), point tiles (3 stages), and
 //            the matching rows of v (bulk copy, 4 stages);
 //   warp 1   TMEM allocation; one thread issues the MMAs and commits;
-//   warps 2-9 epilogue.
+//   warps 2-17 epilogue.
 // All waits are bounded (error flag instead of a hang).
 #include <cuda.h>
 
@@ -39,7 +40,7 @@ constexpr int kKf = 64;              // floats per augmented vector (48 used)
 constexpr int kKSteps = 6;           // 48 / 8 tf32 MMAs
 constexpr int kStagesB = 3;
 constexpr int kStagesV = 4;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;          // 4 per SM sub-partition
 constexpr int kThreadsMv = 32 * (2 + kEpiWarps);
 constexpr int kAtomA = kRows * 128;  // one 32-float K atom of a row block (16 KB)
 constexpr int kAtomB = kPts * 128;   // one 32-float K atom of a point tile (16 KB)
@@ -50,6 +51,7 @@ constexpr uint32_t kTmemCols = 512;
 template <int MP>
 struct MvSmem {
   float v[kStagesV][kPts * MP];
+  float half[kRB * kRows][MP];   // column-half partial sums merged at the end
   unsigned long long a_full;
   unsigned long long b_full[kStagesB], b_empty[kStagesB];
   unsigned long long v_full[kStagesV], v_empty[kStagesV];
@@ -106,6 +108,9 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = sm->tmem_base;
+  float acc[MP];                               // epilogue warps: row partial sums
+#pragma unroll
+  for (int c = 0; c < MP; ++c) acc[c] = 0.f;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -165,12 +170,11 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    const int e = warp - 2;                     // 0 .. 15
     const int q = warp & 3;                     // TMEM lane quarter of this warp
-    const int b = (warp - 2) >> 2;              // row block
-    const int64_t gi = row0 + b * kRows + q * 32 + lane;
-    float acc[MP];
-#pragma unroll
-    for (int c = 0; c < MP; ++c) acc[c] = 0.f;
+    const int b = (e >> 2) & 1;                 // row block
+    const int hh = e >> 3;                      // column half of each tile
+    const int rloc = b * kRows + q * 32 + lane; // row within the CTA
     bool ok = true;
     for (int t = 0; t < ntiles; ++t) {
       const int buf = t & 1, sv = t % kStagesV;
@@ -179,25 +183,39 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
       ok = __all_sync(0xffffffffu, ok);            // tcgen05.ld is warp-collective
       if (!ok) break;
       fence_after();
-      const float* vs = sm->v[sv];
-      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256 + buf * kPts);
+      const uint32_t vs = smem_u32(sm->v[sv]) + (uint32_t)(hh * (kPts / 2) * MP * 4);
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) +
+                             (uint32_t)(b * 256 + buf * kPts + hh * (kPts / 2));
 #pragma unroll 1
-      for (int ch = 0; ch < kPts / 32; ++ch) {
-        uint32_t a[32];
-        tmem_ld32(tbase + (uint32_t)(ch * 32), a);
+      for (int ch = 0; ch < kPts / 2 / 16; ++ch) {
+        uint32_t a[16];
+        tmem_ld16(tbase + (uint32_t)(ch * 16), a);
 #pragma unroll
-        for (int u = 0; u < 32; ++u) {
+        for (int u = 0; u < 16; ++u) {
           const float kij = ex2_approx(__uint_as_float(a[u]));
-          const float* vj = vs + (ch * 32 + u) * MP;
+          const uint32_t vj = vs + (uint32_t)((ch * 16 + u) * MP * 4);
           if (MP == 4) {
-            const float4 v4 = *reinterpret_cast<const float4*>(vj);
+            const float4 v4 = lds128(vj);
             acc[0] = fmaf(kij, v4.x, acc[0]);
-            acc[1] = fmaf(kij, v4.y, acc[1]);
+            acc[1 % MP] = fmaf(kij, v4.y, acc[1 % MP]);
             acc[2 % MP] = fmaf(kij, v4.z, acc[2 % MP]);
             acc[3 % MP] = fmaf(kij, v4.w, acc[3 % MP]);
+          } else if (MP == 8) {
+            const float4 v4 = lds128(vj), w4 = lds128(vj + 16);
+            acc[0] = fmaf(kij, v4.x, acc[0]);
+            acc[1 % MP] = fmaf(kij, v4.y, acc[1 % MP]);
+            acc[2 % MP] = fmaf(kij, v4.z, acc[2 % MP]);
+            acc[3 % MP] = fmaf(kij, v4.w, acc[3 % MP]);
+            acc[4 % MP] = fmaf(kij, w4.x, acc[4 % MP]);
+            acc[5 % MP] = fmaf(kij, w4.y, acc[5 % MP]);
+            acc[6 % MP] = fmaf(kij, w4.z, acc[6 % MP]);
+            acc[7 % MP] = fmaf(kij, w4.w, acc[7 % MP]);
+          } else if (MP == 2) {
+            const float2 v2 = lds64(vj);
+            acc[0] = fmaf(kij, v2.x, acc[0]);
+            acc[1 % MP] = fmaf(kij, v2.y, acc[1 % MP]);
           } else {
-#pragma unroll
-            for (int c = 0; c < MP; ++c) acc[c] = fmaf(kij, vj[c], acc[c]);
+            acc[0] = fmaf(kij, lds32(vj), acc[0]);
           }
         }
       }
@@ -208,10 +226,9 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
         mbar_arrive(&sm->v_empty[sv]);
       }
     }
-    if (ok && gi < n) {
-      float* out = part + ((int64_t)blockIdx.y * n + gi) * MP;
+    if (hh == 1) {
 #pragma unroll
-      for (int c = 0; c < MP; ++c) out[c] = acc[c];
+      for (int c = 0; c < MP; ++c) sm->half[rloc][c] = ok ? acc[c] : 0.f;
     }
   }
   fence_before();
@@ -219,6 +236,17 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
   if (warp == 1) {
     fence_after();
     tmem_dealloc(tmem, kTmemCols);
+  }
+  // merge the two column halves of every row and write the split's partial
+  if (warp >= 2 && ((warp - 2) >> 3) == 0 && !*abort) {
+    const int e = warp - 2;
+    const int rloc = ((e >> 2) & 1) * kRows + (warp & 3) * 32 + lane;
+    const int64_t gi = row0 + rloc;
+    if (gi < n) {
+      float* out = part + ((int64_t)blockIdx.y * n + gi) * MP;
+#pragma unroll
+      for (int c = 0; c < MP; ++c) out[c] = acc[c] + sm->half[rloc][c];
+    }
   }
 }
 

@@ -10,10 +10,11 @@
 //   warp 1      TMEM allocation, and one thread issuing tcgen05.mma
 //               (M=128, N=256, K=16, four per stage) + tcgen05.commit;
 //   warps 2-9   generate the 128 x 64 bf16 block of K for the stage,
-//               exp2(xs_i . xs_j + cn_i + cn_j) on the float32 pipes, straight
-//               into the 128-byte-swizzled K-major layout the MMA reads; after
-//               the last stage they drain the accumulator with tcgen05.ld and
-//               write Y = acc + mu Omega.
+//               exp2(xs_i . xs_j + cn_i + cn_j) on the float32 pipes (a 4 x 8
+//               register tile per thread, points read with broadcast LDS),
+//               straight into the 128-byte-swizzled K-major layout the MMA
+//               reads; after the last stage they drain the accumulator with
+//               tcgen05.ld and write Y = acc + mu Omega.
 // Every mbarrier wait is bounded: on timeout the kernel raises *err and
 // unwinds (RR_ERR_TIMEOUT on the host) instead of hanging.
 #include <cuda.h>
@@ -128,19 +129,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------- generators / epilogue
+    // thread g owns rows rg + 32 rr (rr < 4) and the 8 columns 8 cg .. 8 cg + 7
+    // of each step: per stage it reads 8 points (broadcast LDS), computes a
+    // 4 x 8 register tile of K and stores one 16-byte chunk per row into the
+    // 128-byte-swizzled K-major layout (row r, chunk c at c ^ (r & 7)).
     const int g = threadIdx.x - 64;        // 0 .. 255
-    const int r = g & (kBM - 1);           // row of the tile
-    const int h = g >> 7;                  // which 32 of the 64 columns
-    const int64_t gi = i0 + r;
-    float xi[8];
-    float ci = -1e30f;
-    if (gi < n) {
+    const int rg = g & 31;
+    const int cg = g >> 5;
+    float xi[4][8];
+    float ci[4];
 #pragma unroll
-      for (int d = 0; d < 8; ++d) xi[d] = xs[gi * 8 + d];
-      ci = cn[gi];
-    } else {
+    for (int rr = 0; rr < 4; ++rr) {
+      const int64_t gi = i0 + rg + 32 * rr;
+      if (gi < n) {
 #pragma unroll
-      for (int d = 0; d < 8; ++d) xi[d] = 0.f;
+        for (int d = 0; d < 8; ++d) xi[rr][d] = xs[gi * 8 + d];
+        ci[rr] = cn[gi];
+      } else {
+#pragma unroll
+        for (int d = 0; d < 8; ++d) xi[rr][d] = 0.f;
+        ci[rr] = -1e30f;
+      }
     }
     bool ok = true;
     for (int st = 0; st < nsteps; ++st) {
@@ -154,37 +163,46 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = false;
         break;
       }
-      const float* xsb = tail->xs[s];
-      const float* cnb = tail->cn[s];
-      // 32 entries of row r: columns 32h .. 32h+31 of the step
-      uint32_t packed[16];
+      const uint32_t xsb = smem_u32(tail->xs[s]) + (uint32_t)(8 * cg) * 32;
+      const uint32_t cnb = smem_u32(tail->cn[s]) + (uint32_t)(8 * cg) * 4;
+      float xj[8][8];
+      float cj[8];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        float v2[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int p = 32 * h + 2 * q + u;
-          const float* pj = xsb + p * 8;
-          float a = ci + cnb[p];
-#pragma unroll
-          for (int d = 0; d < 8; ++d) a = fmaf(xi[d], pj[d], a);
-          v2[u] = ex2_approx(a);
-        }
-        packed[q] = pack_bf16x2(v2[0], v2[1]);
+      for (int p = 0; p < 8; ++p) {
+        const float4 a = lds128(xsb + p * 32), b4 = lds128(xsb + p * 32 + 16);
+        xj[p][0] = a.x; xj[p][1] = a.y; xj[p][2] = a.z; xj[p][3] = a.w;
+        xj[p][4] = b4.x; xj[p][5] = b4.y; xj[p][6] = b4.z; xj[p][7] = b4.w;
       }
-      // canonical K-major SW128 layout: row r at r*128 bytes, 16-byte chunk
-      // c stored at chunk position c ^ (r & 7)
-      unsigned char* arow = sA + (size_t)s * kABytes + (size_t)r * 128;
+      {
+        const float4 a = lds128(cnb), b4 = lds128(cnb + 16);
+        cj[0] = a.x; cj[1] = a.y; cj[2] = a.z; cj[3] = a.w;
+        cj[4] = b4.x; cj[5] = b4.y; cj[6] = b4.z; cj[7] = b4.w;
+      }
+      unsigned char* stage = sA + (size_t)s * kABytes;
 #pragma unroll
-      for (int cq = 0; cq < 4; ++cq) {
-        const int chunk = 4 * h + cq;
-        const int phys = chunk ^ (r & 7);
+      for (int rr = 0; rr < 4; ++rr) {
+        uint32_t packed[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float v2[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int p = 2 * q + u;
+            float a = ci[rr] + cj[p];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) a = fmaf(xi[rr][d], xj[p][d], a);
+            v2[u] = ex2_approx(a);
+          }
+          packed[q] = pack_bf16x2(v2[0], v2[1]);
+        }
+        const int r = rg + 32 * rr;
+        const int phys = cg ^ (r & 7);
         uint4 v;
-        v.x = packed[4 * cq + 0];
-        v.y = packed[4 * cq + 1];
-        v.z = packed[4 * cq + 2];
-        v.w = packed[4 * cq + 3];
-        *reinterpret_cast<uint4*>(arow + phys * 16) = v;
+        v.x = packed[0];
+        v.y = packed[1];
+        v.z = packed[2];
+        v.w = packed[3];
+        *reinterpret_cast<uint4*>(stage + (size_t)r * 128 + phys * 16) = v;
       }
       fence_proxy_async();
       mbar_arrive(&tail->full_a[s]);
