@@ -83,11 +83,15 @@ class GaussKernelOp:
     given (float32) coordinates, never stored whole (Sec. 7.2.2 eq:kernel,
     with the kernel matrix itself as A)."""
 
-    def __init__(self, points: np.ndarray, bandwidth: float = 1.0, block: int = 2048):
+    def __init__(self, points: np.ndarray, bandwidth: float = 1.0, block: int = 2048,
+                 materialize: bool = False):
         self.X = np.asarray(points, dtype=np.float64)
         self.n = self.X.shape[0]
         self.h = float(bandwidth)
         self.block = block
+        # materialize=True keeps the dense K (n^2 float64) so that repeated
+        # products are plain matrix products; same values as the blockwise path
+        self.K = self.rows(0, self.n) if materialize else None
 
     def rows(self, lo: int, hi: int) -> np.ndarray:
         diff2 = ((self.X[lo:hi, None, :] - self.X[None, :, :]) ** 2).sum(-1) \
@@ -101,6 +105,8 @@ class GaussKernelOp:
 
     def matmat(self, V: np.ndarray) -> np.ndarray:
         V = np.asarray(V, dtype=np.float64)
+        if self.K is not None:
+            return self.K @ V
         out = np.empty((self.n,) + V.shape[1:])
         for lo in range(0, self.n, self.block):
             hi = min(self.n, lo + self.block)
@@ -108,7 +114,7 @@ class GaussKernelOp:
         return out
 
     def dense(self) -> np.ndarray:
-        return self.rows(0, self.n)
+        return self.K if self.K is not None else self.rows(0, self.n)
 
 
 def shifted(op, mu: float):
