@@ -80,7 +80,14 @@ enum {
 /* Orthogonalisation of Y_mu = A_mu Omega */
 enum {
   RR_ORTH_CHOLQR2 = 0,      /* Cholesky QR applied twice (Sec. 4.2 Alg. 2 as first pass) */
-  RR_ORTH_RAND_CHOLQR = 1   /* Alg. 3 (sketch-preconditioned Cholesky QR) + one CholQR pass */
+  RR_ORTH_RAND_CHOLQR = 1   /* Alg. 3, randomized Q-less QR: S = Theta Y_mu (Theta a
+                               sparse-sign l_sk x n embedding), R_sk from a float64
+                               Cholesky QR of S, W = Y_mu R_sk^-1, R = chol(W^T W) R_sk.
+                               With a CSR operator no basis is kept (Sec. 4.2
+                               basis-less form: Q^T v = R^-T Omega^T A_mu v and
+                               Q s = A_mu Omega R^-1 s; C variant only, three
+                               products with A_mu per iteration); other operators
+                               form Q = W chol(W^T W)^-1. */
 };
 
 /*
@@ -234,14 +241,12 @@ void randrand_free(rr_handle* h);
  * Test and inspection hooks (used by the parity tests): copy device-resident
  * build products into caller device buffers, enqueued on the handle stream.
  *   what = 0: Omega  (n x k row-major, float64)
- *          1: Q      (n x k row-major, float64)
+ *          1: Q      (n x k row-major, float64; RR_ERR_UNSUPPORTED for a
+ *                     basis-less build, which keeps no Q)
  *          2: R      (k x k row-major, float64, upper triangular)
  *          3: G      (k x k row-major, float64; C variant core matrix)
- *          4: Y_mu   (n x k row-major, float64; A_mu Omega before
- *                     orthogonalisation, kept only when opts were built
- *                     with max_rhs >= 1 and the build is done)
  *   dst   device buffer of float64 of the stated size.
- * Errors: RR_ERR_INVALID_ARG, RR_ERR_CUDA.
+ * Errors: RR_ERR_INVALID_ARG, RR_ERR_UNSUPPORTED, RR_ERR_CUDA.
  */
 rr_status randrand_export(rr_handle* h, int32_t what, double* dst);
 

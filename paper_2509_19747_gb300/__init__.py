@@ -36,6 +36,7 @@ RR_ORTH_CHOLQR2, RR_ORTH_RAND_CHOLQR = 0, 1
 SKETCHES = {"gaussian": RR_SKETCH_GAUSSIAN, "sparse_sign": RR_SKETCH_SPARSE_SIGN}
 PRECISIONS = {"fp64": RR_PREC_FP64, "fp32": RR_PREC_FP32, "mixed": RR_PREC_MIXED}
 VARIANTS = {"C": RR_VARIANT_C, "R": RR_VARIANT_R}
+ORTHS = {"cholqr2": RR_ORTH_CHOLQR2, "rand_cholqr": RR_ORTH_RAND_CHOLQR}
 
 
 class rr_operator(ctypes.Structure):
@@ -288,7 +289,8 @@ class Handle:
     def __init__(self, op: Operator, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
                  variant: str = "C", precision: str = "fp64", max_rhs: int = 1,
                  power_iters: int = 20, rho: float = 0.0, restart_eta: float = 1e-2,
-                 gamma: int = 8, profile: bool = False, kernel_impl: int = 0, stream=None):
+                 gamma: int = 8, profile: bool = False, kernel_impl: int = 0, stream=None,
+                 orth: str = "cholqr2", l_sk: int = 0, gamma_sk: int = 8):
         import torch
         self.op = op
         self.n = op.n
@@ -301,6 +303,9 @@ class Handle:
         o.rho = rho
         o.restart_eta = restart_eta
         o.gamma = gamma
+        o.orth = ORTHS[orth]
+        o.l_sk = l_sk
+        o.gamma_sk = gamma_sk
         o.profile = 1 if profile else 0
         o.kernel_impl = kernel_impl
         self.opts = o

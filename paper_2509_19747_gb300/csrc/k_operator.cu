@@ -58,6 +58,19 @@ void prepare_kernel_points(OpDev& op, cudaStream_t st) {
     k_point_norms<<<(unsigned)cdiv(op.n, 256), 256, 0, st>>>(op.points, op.n, op.dim, op.pn);
 }
 
+// Inside a stream capture a plain event record only orders the capture; the
+// External flag makes it a real event-record node of the graph, so that the
+// elapsed time between the pair can be read after each replay.
+static inline void rec(const cudaEvent_t* ev, int i, cudaStream_t st) {
+  if (!ev) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(ev[i], st);
+}
+
 // ================================================================ dense
 template <typename T, typename TA>
 __global__ void __launch_bounds__(256) k_dense_mv(const TA* __restrict__ A, int64_t lda,
@@ -107,6 +120,53 @@ __global__ void k_csr_mv(const int32_t* __restrict__ rowptr, const int32_t* __re
 #pragma unroll
   for (int c = 0; c < 8; ++c)
     if (c < mp) W[i * mp + c] = acc[c] + (T)mu * V[i * mp + c];
+}
+
+// out = (A + mu I) V + a[c] X[:, c]   (X may be null); skipped when no column is active
+template <typename T, typename TV>
+__global__ void k_csr_mv_add(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                             const TV* __restrict__ vals, int64_t n, double mu,
+                             const T* __restrict__ V, const T* __restrict__ X, Coefs8s a,
+                             T* __restrict__ W, int mp, const ColState* __restrict__ cs) {
+  if (cs) {
+    bool any = false;
+    for (int c = 0; c < mp; ++c) any |= cs[c].active != 0;
+    if (!any) return;
+  }
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = (T)0;
+  const int32_t lo = rowptr[i], hi = rowptr[i + 1];
+  for (int32_t p = lo; p < hi; ++p) {
+    const T av = (T)vals[p];
+    const int64_t j = colidx[p];
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (c < mp) acc[c] = fma(av, V[j * mp + c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    if (c < mp) {
+      T o = acc[c] + (T)mu * V[i * mp + c];
+      if (X) o = fma((T)a.v[c], X[i * mp + c], o);
+      W[i * mp + c] = o;
+    }
+}
+
+template <typename T>
+void csr_matvec_add(const OpDev& op, double mu, const T* V, const T* X, const double* a, T* W,
+                    int mp, const ColState* cs, cudaStream_t st, const cudaEvent_t* ev) {
+  Coefs8s cf;
+  for (int c = 0; c < 8; ++c) cf.v[c] = a ? a[c] : 0.0;
+  const unsigned blocks = (unsigned)cdiv(op.n, 256);
+  rec(ev, 0, st);
+  if (op.dtype == 0)
+    k_csr_mv_add<T, double><<<blocks, 256, 0, st>>>(op.rowptr, op.colidx, (const double*)op.vals, op.n, mu, V, X, cf, W, mp, cs);
+  else
+    k_csr_mv_add<T, float><<<blocks, 256, 0, st>>>(op.rowptr, op.colidx, (const float*)op.vals, op.n, mu, V, X, cf, W, mp, cs);
+  rec(ev, 1, st);
 }
 
 // ======================================================= Gaussian kernel
@@ -392,19 +452,6 @@ size_t op_matvec_scratch_elems(const OpDev& op, int mp) {
   const int nt = mv_tc_nsplit(op.n);
   if (nt > ns) ns = nt;
   return (size_t)ns * (size_t)op.n * (size_t)mp;
-}
-
-// Inside a stream capture a plain event record only orders the capture; the
-// External flag makes it a real event-record node of the graph, so that the
-// elapsed time between the pair can be read after each replay.
-static inline void rec(const cudaEvent_t* ev, int i, cudaStream_t st) {
-  if (!ev) return;
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(st, &cs);
-  if (cs == cudaStreamCaptureStatusActive)
-    cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
-  else
-    cudaEventRecord(ev[i], st);
 }
 
 template <typename T>
@@ -719,6 +766,8 @@ void csr_sketch_sparse(const OpDev& op, double mu, const int32_t* cols, const in
   rec(ev, 1, st);
 }
 
+template void csr_matvec_add<float>(const OpDev&, double, const float*, const float*, const double*, float*, int, const ColState*, cudaStream_t, const cudaEvent_t*);
+template void csr_matvec_add<double>(const OpDev&, double, const double*, const double*, const double*, double*, int, const ColState*, cudaStream_t, const cudaEvent_t*);
 template void op_matvec<float>(const OpDev&, double, const float*, float*, int, float*, cudaStream_t, const cudaEvent_t*);
 template void op_matvec<double>(const OpDev&, double, const double*, double*, int, double*, cudaStream_t, const cudaEvent_t*);
 template void op_sketch<float>(const OpDev&, double, const float*, float*, int, bool, cudaStream_t, const cudaEvent_t*);

@@ -18,14 +18,15 @@ using namespace rr;
 
 namespace {
 
-constexpr int kKK = 12;           // k x k float64 work matrices
+constexpr int kKK = 16;           // k x k float64 work matrices
 constexpr int kMaxGammaHost = 16; // sparse-sign nonzeros per row, at most
 constexpr int kChunk = 8;         // Krylov iterations per captured graph
 constexpr int kMaxRestarts = 400;
 
 enum Region {
-  R_OM, R_OMB, R_SSC, R_SSS, R_Y, R_Q, R_KK, R_KKT, R_GPART, R_CHOLW, R_STATUS, R_XS, R_CN,
-  R_PN, R_AUG, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT, R_CS, R_NORMS, R_NREG
+  R_OM, R_OMB, R_SSC, R_SSS, R_THC, R_THS, R_SK, R_Y, R_Q, R_KK, R_KKT, R_GPART, R_CHOLW,
+  R_STATUS, R_XS, R_CN, R_PN, R_AUG, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT,
+  R_CS, R_NORMS, R_NREG
 };
 
 struct Layout {
@@ -44,6 +45,15 @@ int pad_mp(int m) {
 
 bool uses_f64(const rr_build_opts& o) { return o.precision == RR_PREC_FP64; }
 
+// Alg. 3 (randomized Q-less QR) replaces CholeskyQR2 when asked for
+bool uses_alg3(const rr_build_opts& o) { return o.orth == RR_ORTH_RAND_CHOLQR; }
+// basis-less representation (Sec. 4.2): no n x k basis is kept, Q is applied
+// through A_mu, Omega and R^-1 (sparse operators only)
+bool basis_less(const rr_operator& A, const rr_build_opts& o) {
+  return uses_alg3(o) && A.kind == RR_OP_CSR;
+}
+int sketch_rows(int k, const rr_build_opts& o) { return o.l_sk > 0 ? o.l_sk : 4 * k; }
+
 Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   Layout L;
   memset(&L, 0, sizeof(L));
@@ -59,6 +69,10 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_OMB] = (o.precision == RR_PREC_MIXED) ? kk * (size_t)cdiv(A.n, 8) * 8 * 2 : 0;
   L.size[R_SSC] = n * (size_t)o.gamma * 4;
   L.size[R_SSS] = n * (size_t)o.gamma;
+  const size_t lsk = uses_alg3(o) ? (size_t)sketch_rows(k, o) : 0;
+  L.size[R_THC] = uses_alg3(o) ? n * (size_t)o.gamma_sk * 4 : 0;
+  L.size[R_THS] = uses_alg3(o) ? n * (size_t)o.gamma_sk : 0;
+  L.size[R_SK] = 2 * lsk * kk * 8;   // S = Theta Y_mu and one copy for CholeskyQR passes
   L.size[R_Y] = n * kk * ts;
   L.size[R_Q] = n * kk * ts;
   L.size[R_KK] = (size_t)kKK * kk * kk * 8;
@@ -100,8 +114,20 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
   if (o.max_rhs < 1 || o.max_rhs > 8) return RR_ERR_INVALID_ARG;
   if (o.variant != RR_VARIANT_C && o.variant != RR_VARIANT_R) return RR_ERR_INVALID_ARG;
   if (o.precision < RR_PREC_FP64 || o.precision > RR_PREC_MIXED) return RR_ERR_INVALID_ARG;
-  if (o.orth != RR_ORTH_CHOLQR2) return RR_ERR_UNSUPPORTED;
+  if (o.orth != RR_ORTH_CHOLQR2 && o.orth != RR_ORTH_RAND_CHOLQR) return RR_ERR_INVALID_ARG;
   if (o.gamma < 1 || o.gamma > kMaxGammaHost) return RR_ERR_INVALID_ARG;
+  if (uses_alg3(o)) {
+    if (o.l_sk < 0 || o.gamma_sk < 1 || o.gamma_sk > kMaxGammaHost) return RR_ERR_INVALID_ARG;
+    const int64_t l = o.l_sk > 0 ? o.l_sk : 4 * (int64_t)k;
+    if (l < k || l > (int64_t)INT32_MAX / 2 || o.gamma_sk > l) return RR_ERR_INVALID_ARG;
+    if (basis_less(*A, o)) {
+      // the preconditioner of Alg. 4 needs Q^T p, Q t and Pi p per step: not
+      // provided without a basis
+      if (o.variant != RR_VARIANT_C) return RR_ERR_UNSUPPORTED;
+      // Omega^T v partials and Omega s stage k x m values in shared memory
+      if ((size_t)k * pad_mp(o.max_rhs) * (uses_f64(o) ? 8 : 4) > 200 * 1024) return RR_ERR_UNSUPPORTED;
+    }
+  }
   if (o.power_iters < 1 || o.power_iters > 1000) return RR_ERR_INVALID_ARG;
   if (!(o.restart_eta > 0.0 && o.restart_eta < 1.0)) return RR_ERR_INVALID_ARG;
   switch (A->kind) {
@@ -145,6 +171,12 @@ struct rr_handle {
   __nv_bfloat16* Omb;
   int32_t* ss_cols;
   int8_t* ss_sgn;
+  int32_t* th_cols;   // Theta pattern of Alg. 3
+  int8_t* th_sgn;
+  double* S;          // S = Theta Y_mu (l_sk x k) and a second l_sk x k buffer
+  double* S2;
+  int lsk;
+  bool implicit;      // basis-less: Q applied through A_mu, Omega and R^-1
   void* Y;
   void* Q;
   void* QH;
@@ -193,7 +225,9 @@ enum { kR = 0, kP = 1, kW = 2, kZ = 3, kE = 4, kU = 5, kV = 6 };
 enum { kB64 = 0, kX64 = 1, kR64 = 2, kW64 = 3 };
 // k x k slots
 enum { kR1 = 0, kR2 = 1, kRinvA = 2, kRinvB = 3, kRinv = 4, kRfull = 5, kM = 6, kG = 7, kH = 8,
-       kTm = 9, kScA = 10, kScB = 11 };
+       kTm = 9, kScA = 10, kScB = 11,
+       // basis-less: R_sk, R^-1 H R^-T, R^-1 R^-T, R^-1 G R^-T
+       kRsk = 12, kHb = 13, kCinv = 14, kGb = 15 };
 
 template <typename T>
 T* vt(rr_handle* h, int i) {
@@ -206,6 +240,10 @@ void carve(rr_handle* h) {
   h->Omb = (__nv_bfloat16*)at(R_OMB);
   h->ss_cols = (int32_t*)at(R_SSC);
   h->ss_sgn = (int8_t*)at(R_SSS);
+  h->th_cols = (int32_t*)at(R_THC);
+  h->th_sgn = (int8_t*)at(R_THS);
+  h->S = (double*)at(R_SK);
+  h->S2 = h->S ? h->S + (size_t)h->lsk * h->k : nullptr;
   h->Y = at(R_Y);
   h->Q = at(R_Q);
   h->QH = nullptr;
@@ -413,6 +451,89 @@ rr_status orthogonalize(rr_handle* h) {
   return RR_OK;
 }
 
+// R factor of the l x k float64 sketch S (Alg. 3 step 2).  The factor is
+// unique once its diagonal is positive, so any backward-stable QR gives it to
+// rounding; here CholeskyQR2, or shifted CholeskyQR3 (Fukaya et al. 2020: a
+// shifted first pass, then two plain passes) when the first Gram is
+// numerically singular, stable up to cond(S) ~ 1/u.  S is overwritten.
+rr_status sketch_qr_R(rr_handle* h, double* Rout) {
+  const int k = h->k;
+  const int64_t l = h->lsk;
+  cudaStream_t st = h->st;
+  const int ns = std::min(gram_nsplit(l, k, k), h->gsplit);
+  double* G1 = h->kk[kScA];
+  double* Rp = h->kk[kR1];
+  double* Rip = h->kk[kRinvA];
+  double* src = h->S;
+  double* dst = h->S2;
+  auto gram_S = [&](const double* X, double* G) {
+    gram_partial<double>(X, k, X, k, l, k, k, true, ns, h->gpart, st);
+    reduce_gram(h->gpart, ns, k, k, true, false, G, st);
+  };
+  gram_S(src, G1);
+  RR_CUDA_TRY(cudaMemcpyAsync(Rp, G1, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, st));
+  int passes = 2;
+  rr_status s = chol(h, Rp);
+  if (s == RR_ERR_NOT_SPD) {
+    double tr = 0.0;
+    k_trace<<<1, 32, 0, st>>>(G1, k, h->norms);
+    RR_TRY(read_doubles(h, h->norms, 1, &tr));
+    const double shift = 11.0 * ((double)l * k + (double)k * (k + 1)) * 1.1102230246251565e-16 * tr;
+    RR_CUDA_TRY(cudaMemcpyAsync(Rp, G1, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, st));
+    add_diag(Rp, k, shift, st);
+    RR_TRY(chol(h, Rp));
+    passes = 3;
+  } else if (s != RR_OK) {
+    return s;
+  }
+  RR_CUDA_TRY(cudaMemcpyAsync(Rout, Rp, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, st));
+  for (int p = 1; p < passes; ++p) {
+    // next pass on S R_p^-1
+    trtri_upper_with(Rp, k, h->kk[kScB], Rip, st);
+    gemm_nn<double>(l, k, k, 1.0, src, k, Rip, k, 0.0, nullptr, 0, dst, k, st);
+    std::swap(src, dst);
+    gram_S(src, Rp);
+    RR_TRY(chol(h, Rp));
+    gemm_upper_upper(k, Rp, Rout, h->kk[kScB], st);     // R <- R_p R
+    RR_CUDA_TRY(cudaMemcpyAsync(Rout, h->kk[kScB], (size_t)k * k * 8, cudaMemcpyDeviceToDevice, st));
+  }
+  return RR_OK;
+}
+
+// Alg. 3, randomized Q-less QR of Y_mu:
+//   S = Theta Y_mu, R_sk = R(S), W = Y_mu R_sk^-1, R_chol = chol(W^T W),
+//   R = R_chol R_sk.
+// W is formed before its Gram (forming R_sk^-T (Y^T Y) R_sk^-1 instead would
+// square cond(Y_mu) again).  With a basis the orthonormal factor is
+// Q = W R_chol^-1; a basis-less build keeps R and R^-1 only.
+template <typename T>
+rr_status rand_qless_qr(rr_handle* h) {
+  const int k = h->k;
+  const int64_t n = h->n;
+  cudaStream_t st = h->st;
+  T* Yb = (T*)h->Y;
+  T* Wb = (T*)h->Q;
+  RR_CUDA_TRY(cudaMemsetAsync(h->S, 0, (size_t)h->lsk * k * 8, st));
+  gen_sparse_sign(h->th_cols, h->th_sgn, n, h->lsk, h->o.gamma_sk, h->seed, 3u, st);
+  theta_scatter<T>(Yb, n, k, h->th_cols, h->th_sgn, h->o.gamma_sk, h->S, st);
+  RR_TRY(sketch_qr_R(h, h->kk[kRsk]));
+  trtri_upper_with(h->kk[kRsk], k, h->kk[kScB], h->kk[kRinvA], st);
+  right_mult<T>(h, Yb, h->kk[kRinvA], Wb);                       // W = Y_mu R_sk^-1
+  gram<T>(h, Wb, h->kk[kR2]);
+  RR_TRY(chol(h, h->kk[kR2]));                                   // R_chol
+  gemm_upper_upper(k, h->kk[kR2], h->kk[kRsk], h->kk[kRfull], st);   // R = R_chol R_sk
+  trtri_upper_with(h->kk[kR2], k, h->kk[kScB], h->kk[kRinvB], st);
+  gemm_upper_upper(k, h->kk[kRinvA], h->kk[kRinvB], h->kk[kRinv], st);  // R^-1
+  if (h->implicit) {
+    h->Q = nullptr;
+    return RR_OK;
+  }
+  right_mult<T>(h, Wb, h->kk[kRinvB], Yb);                       // Q = W R_chol^-1
+  h->Q = Yb;
+  h->Y = Wb;
+  return RR_OK;
+}
+
 // C-RandRAND core matrix G = (R_M R^-1)^T (R_M R^-1), R_M^T R_M = sym(Omega^T
 // Y_mu) (remark after Alg. 7).  M is in kk[kM].  Jitter ladder of App. C
 // (alpha = 10^-14 .. 10^-1 times the largest diagonal entry) on failure.
@@ -492,6 +613,111 @@ rr_status power_iterations(rr_handle* h) {
   h->normE = h->cs_host[0].lam;
   h->lam_max = isC ? h->cs_host[1].lam : 0.0;
   return RR_OK;
+}
+
+// ------------------------------------------------- basis-less (Sec. 4.2)
+// g = Omega^T V  (k x mp, float64)
+template <typename T>
+void omega_t(rr_handle* h, const T* V, double* out, bool gated) {
+  const int nslab = qt_nslab(h->n);
+  if (h->sketch == RR_SKETCH_SPARSE_SIGN)
+    omega_t_partial<T>(V, h->n, h->k, h->mp, h->ss_cols, h->ss_sgn, h->o.gamma, nslab,
+                       qt_rows_per_slab(h->n), h->tpart, gated ? h->cs : nullptr, h->st);
+  else if (gated)
+    qt_partial_gated<T>((const T*)h->Om, V, h->n, h->k, h->mp, h->tpart, h->cs, h->st);
+  else
+    qt_partial<T>((const T*)h->Om, V, h->n, h->k, h->mp, nslab, h->tpart, h->st);
+  if (gated) reduce_slabs_gated(h->tpart, nslab, h->k * h->mp, out, h->cs, h->mp, h->st);
+  else reduce_slabs(h->tpart, nslab, h->k * h->mp, out, h->st);
+}
+
+// U = Omega s
+template <typename T>
+void omega_mul(rr_handle* h, const double* s, T* U, bool gated) {
+  if (h->sketch == RR_SKETCH_SPARSE_SIGN)
+    omega_expand<T>(s, h->n, h->k, h->mp, h->ss_cols, h->ss_sgn, h->o.gamma, U,
+                    gated ? h->cs : nullptr, h->st);
+  else
+    qcomb<T>((const T*)h->Om, h->n, h->k, h->mp, s, coefs_all(0.0), nullptr, U, nullptr,
+             kModeNone, h->rpart, h->cnt, h->cs, gated, h->st);
+}
+
+// out = A_mu V + a X (CSR), skipped once no column is active when gated
+template <typename T>
+void amul(rr_handle* h, const T* V, const T* X, const double* a, T* out, bool gated,
+          const cudaEvent_t* ev = nullptr) {
+  csr_matvec_add<T>(h->op, h->mu, V, X, a, out, h->mp, gated ? h->cs : nullptr, h->st, ev);
+}
+
+// z = P r = r + Q H Q^T r with Q^T r = R^-T Omega^T A_mu r and Q s = A_mu Omega R^-1 s:
+//   z = r + A_mu Omega Hb Omega^T A_mu r,   Hb = R^-1 (tau G - I) R^-T
+template <typename T>
+void precond_implicit(rr_handle* h, const T* Rv, T* Zv, bool gated, const cudaEvent_t* ev) {
+  T* U = vt<T>(h, kU);
+  T* V = vt<T>(h, kV);
+  amul<T>(h, Rv, nullptr, nullptr, U, gated, ev);
+  omega_t<T>(h, U, h->t[0], gated);
+  kxk_apply(h->kk[kHb], h->t[0], h->k, h->mp, coefs_all(0.0), coefs_all(1.0), h->t[1], h->st);
+  omega_mul<T>(h, h->t[1], V, gated);
+  const Coefs8 one = coefs_all(1.0);
+  amul<T>(h, V, Rv, one.v, Zv, gated);
+}
+
+// The power iterations of power_iterations() with the basis-less Q:
+//   column 0: v -> (I - Pi) A_mu (I - Pi) v          (|E|)
+//   column 1: v -> Pi A_mu Q G Q^T v                 (lambda_max, C variant)
+// Q^T v = R^-T g with g = Omega^T A_mu v, so (I - Pi) v = v + A_mu Omega (-Cinv g)
+// and Q G Q^T v = A_mu Omega Gb g, Cinv = R^-1 R^-T, Gb = R^-1 G R^-T.
+template <typename T>
+rr_status power_iterations_implicit(rr_handle* h) {
+  const int64_t n = h->n;
+  const int mp = h->mp, k = h->k;
+  T* Vv = vt<T>(h, kV);
+  T* Uv = vt<T>(h, kU);
+  T* Wv = vt<T>(h, kW);
+  T* Zv = vt<T>(h, kZ);
+  T* Av = vt<T>(h, kP);
+  T* Bv = vt<T>(h, kR);
+  RR_CUDA_TRY(cudaMemsetAsync(Vv, 0, (size_t)n * mp * sizeof(T), h->st));
+  gen_power_start<T>(Vv, n, mp, 0, 0, h->seed, h->st);
+  gen_power_start<T>(Vv, n, mp, 1, 1, h->seed, h->st);
+  dot_cols<T>(Vv, Vv, n, mp, kModeNorm, h->rpart, h->cnt, h->cs, false, nullptr, h->st);
+  scale_cols<T>(Vv, Vv, n, mp, h->cs, h->st);
+  const Coefs8 keep0 = coefs(1.0, 0.0);
+  for (int it = 0; it < h->o.power_iters; ++it) {
+    amul<T>(h, Vv, nullptr, nullptr, Av, false, ev_take(h, RR_PROF_POWER));
+    omega_t<T>(h, Av, h->t[0], false);
+    kxk_apply(h->kk[kCinv], h->t[0], k, mp, coefs_all(0.0), coefs(-1.0, 0.0), h->t[1], h->st);
+    kxk_apply(h->kk[kGb], h->t[0], k, mp, coefs_all(0.0), coefs(0.0, 1.0), h->t[2], h->st);
+    axpby<double, double, double>(h->t[1], coefs_all(1.0), h->t[2], coefs_all(1.0), h->t[1], k, mp,
+                                  h->st);
+    omega_mul<T>(h, h->t[1], Bv, false);
+    amul<T>(h, Bv, Vv, keep0.v, Uv, false);                       // u
+    amul<T>(h, Uv, nullptr, nullptr, Wv, false, ev_take(h, RR_PROF_POWER));   // w = A_mu u
+    amul<T>(h, Wv, nullptr, nullptr, Av, false);
+    omega_t<T>(h, Av, h->t[0], false);
+    kxk_apply(h->kk[kCinv], h->t[0], k, mp, coefs_all(0.0), coefs(-1.0, 1.0), h->t[1], h->st);
+    omega_mul<T>(h, h->t[1], Bv, false);
+    amul<T>(h, Bv, Wv, keep0.v, Zv, false);                       // (I - Pi) w | Pi w
+    dot_cols<T>(Zv, Zv, n, mp, kModeNorm, h->rpart, h->cnt, h->cs, false, nullptr, h->st);
+    scale_cols<T>(Zv, Vv, n, mp, h->cs, h->st);
+  }
+  RR_TRY(read_cs(h));
+  h->normE = h->cs_host[0].lam;
+  h->lam_max = h->cs_host[1].lam;
+  return RR_OK;
+}
+
+// Cinv = R^-1 R^-T and Gb = R^-1 G R^-T (k x k float64)
+void implicit_core(rr_handle* h) {
+  const int k = h->k;
+  transpose_kxk(h->kk[kRinv], h->kk[kScA], k, h->st);            // R^-T
+  gemm_nn<double>(k, k, k, 1.0, h->kk[kRinv], k, h->kk[kScA], k, 0.0, nullptr, 0, h->kk[kCinv], k,
+                  h->st);
+  gemm_nn<double>(k, k, k, 1.0, h->kk[kRinv], k, h->kk[kG], k, 0.0, nullptr, 0, h->kk[kTm], k,
+                  h->st);
+  gemm_nn<double>(k, k, k, 1.0, h->kk[kTm], k, h->kk[kScA], k, 0.0, nullptr, 0, h->kk[kGb], k,
+                  h->st);
 }
 
 // tau: eq:c_randrand_tau with rho from eq:optimal_rho (F = 1/mu) for C;
@@ -575,16 +801,26 @@ rr_status build_impl(rr_handle* h) {
     gram_partial<T>((const T*)h->Om, k, (const T*)h->Y, k, n, k, k, false, h->gsplit, h->gpart, st);
     reduce_gram(h->gpart, h->gsplit, k, k, false, true, h->kk[kM], st);
   }
-  RR_TRY(orthogonalize<T>(h));
+  if (uses_alg3(h->o)) RR_TRY(rand_qless_qr<T>(h));
+  else RR_TRY(orthogonalize<T>(h));
   if (h->o.variant == RR_VARIANT_C) RR_TRY(core_matrix(h));
-  RR_TRY(power_iterations<T>(h));
+  if (h->implicit) {
+    implicit_core(h);
+    RR_TRY(power_iterations_implicit<T>(h));
+  } else {
+    RR_TRY(power_iterations<T>(h));
+  }
   choose_tau(h);
   if (h->op.use_tc) {
     int err = 0;
     RR_TRY(read_int(h, h->dstatus + 2, &err));
     if (err) return RR_ERR_TIMEOUT;
   }
-  if (h->o.variant == RR_VARIANT_C) {
+  if (h->implicit) {
+    // Hb = R^-1 (tau G - I) R^-T = tau Gb - Cinv
+    axpby<double, double, double>(h->kk[kGb], coefs_all(h->tau), h->kk[kCinv], coefs_all(-1.0),
+                                  h->kk[kHb], (int64_t)k * k, 1, st);
+  } else if (h->o.variant == RR_VARIANT_C) {
     // P = I + Q (tau G - I) Q^T; keep QH = Q H so that z = r + QH (Q^T r)
     form_H(h->kk[kG], h->tau, h->kk[kH], k, st);
     h->QH = h->Y;
@@ -607,6 +843,31 @@ void iter_C(rr_handle* h, const cudaEvent_t* ev) {
   qcomb<T>((const T*)h->QH, n, k, mp, h->t[0], coefs_all(1.0), Rv, Zv, Rv, kModeBeta, h->rpart,
            h->cnt, h->cs, true, h->st);                                   // z = r + Q H t
   p_update<T>(Pv, Zv, n, mp, h->cs, false, h->st);                        // p = z + beta p
+}
+
+// C-RandRAND PCG step with the basis-less Q: three products with A_mu
+template <typename T>
+void iter_C_implicit(rr_handle* h, const cudaEvent_t* ev) {
+  const int64_t n = h->n;
+  const int mp = h->mp, k = h->k;
+  T *Rv = vt<T>(h, kR), *Pv = vt<T>(h, kP), *Wv = vt<T>(h, kW), *Zv = vt<T>(h, kZ),
+    *Ev = vt<T>(h, kE);
+  amul<T>(h, Pv, nullptr, nullptr, Wv, true, ev);                          // w = A_mu p
+  dot_cols<T>(Pv, Wv, n, mp, kModeAlpha, h->rpart, h->cnt, h->cs, true, nullptr, h->st);
+  update_qt<T>(Ev, Rv, Pv, Wv, nullptr, n, k, mp, nullptr, h->rpart, h->cnt, h->cs, h->st);
+  precond_implicit<T>(h, Rv, Zv, true, nullptr);                           // z = P r
+  dot_cols<T>(Rv, Zv, n, mp, kModeBeta, h->rpart, h->cnt, h->cs, true, nullptr, h->st);
+  p_update<T>(Pv, Zv, n, mp, h->cs, false, h->st);                          // p = z + beta p
+}
+
+template <typename T>
+void iter_R(rr_handle* h, const cudaEvent_t* ev);
+
+template <typename T>
+void iter_any(rr_handle* h, const cudaEvent_t* ev) {
+  if (h->implicit) iter_C_implicit<T>(h, ev);
+  else if (h->o.variant == RR_VARIANT_C) iter_C<T>(h, ev);
+  else iter_R<T>(h, ev);
 }
 
 template <typename T>
@@ -641,9 +902,7 @@ rr_status run_chunk(rr_handle* h) {
   // captured event records gave no timings launches directly as well
   if (h->st == nullptr || h->st == cudaStreamLegacy || (h->prof && h->graph_prof_broken)) {
     for (int i = 0; i < kChunk; ++i) {
-      const cudaEvent_t* ev = ev_take(h, RR_PROF_MATVEC);
-      if (h->o.variant == RR_VARIANT_C) iter_C<T>(h, ev);
-      else iter_R<T>(h, ev);
+      iter_any<T>(h, ev_take(h, RR_PROF_MATVEC));
     }
     RR_CUDA_TRY(cudaGetLastError());
     return RR_OK;
@@ -654,9 +913,7 @@ rr_status run_chunk(rr_handle* h) {
     cudaGraph_t g = nullptr;
     RR_CUDA_TRY(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kChunk; ++i) {
-      const cudaEvent_t* ev = h->prof ? h->ev_graph[i].e : nullptr;
-      if (h->o.variant == RR_VARIANT_C) iter_C<T>(h, ev);
-      else iter_R<T>(h, ev);
+      iter_any<T>(h, h->prof ? h->ev_graph[i].e : nullptr);
     }
     cudaError_t e = cudaStreamEndCapture(h->st, &g);
     if (e != cudaSuccess || !g) return RR_ERR_CUDA;
@@ -741,7 +998,7 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
       }
     if (any_zero) axpby<double, double, double>(X, keep, nullptr, coefs_all(0.0), X, n, mp, st);
   }
-  const int mv_per_iter = 1;
+  const int mv_per_iter = h->implicit ? 3 : 1;
   for (int restart = 0; restart <= kMaxRestarts; ++restart) {
     if (restart == 0 && !x_guess) {
       RR_CUDA_TRY(cudaMemcpyAsync(R64, B, (size_t)n * mp * 8, cudaMemcpyDeviceToDevice, st));
@@ -776,7 +1033,11 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
     T* Ev = vt<T>(h, kE);
     axpby<double, double, T>(R64, coefs_all(1.0), nullptr, coefs_all(0.0), Rv, n, mp, st);
     RR_CUDA_TRY(cudaMemsetAsync(Ev, 0, (size_t)n * mp * sizeof(T), st));
-    if (h->o.variant == RR_VARIANT_C) {
+    if (h->implicit) {
+      precond_implicit<T>(h, Rv, vt<T>(h, kZ), false, nullptr);
+      dot_cols<T>(Rv, vt<T>(h, kZ), n, mp, kModeRhoInit, h->rpart, h->cnt, h->cs, false, nullptr, st);
+      p_update<T>(vt<T>(h, kP), vt<T>(h, kZ), n, mp, h->cs, true, st);
+    } else if (h->o.variant == RR_VARIANT_C) {
       // z = P r, p = z, rho = r^T z
       qt<T>(h, Rv, h->t[0], false);
       qcomb<T>((const T*)h->QH, n, h->k, mp, h->t[0], coefs_all(1.0), Rv, vt<T>(h, kZ), Rv,
@@ -797,7 +1058,7 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
       if (done[c] || !rp.active[c]) continue;
       const ColState& s = h->cs_host[c];
       used[c] += s.iters;
-      mv[c] += s.iters * mv_per_iter + (h->o.variant == RR_VARIANT_R ? 1 : 0);
+      mv[c] += s.iters * mv_per_iter + (h->o.variant == RR_VARIANT_R ? 1 : 0) + (h->implicit ? 2 : 0);
       outer[c] += 1;
       if (s.status == RR_ERR_BREAKDOWN && s.iters == 0) { done[c] = true; stat[c] = RR_ERR_BREAKDOWN; }
     }
@@ -847,7 +1108,9 @@ void apply_impl(rr_handle* h) {
   const int mp = h->mp, k = h->k;
   T *Rv = vt<T>(h, kR), *Zv = vt<T>(h, kZ), *Uv = vt<T>(h, kU), *Wv = vt<T>(h, kW);
   axpby<double, double, T>(h->v64[kR64], coefs_all(1.0), nullptr, coefs_all(0.0), Rv, n, mp, h->st);
-  if (h->o.variant == RR_VARIANT_C) {
+  if (h->implicit) {
+    precond_implicit<T>(h, Rv, Zv, false, nullptr);
+  } else if (h->o.variant == RR_VARIANT_C) {
     qt<T>(h, Rv, h->t[0], false);
     qcomb<T>((const T*)h->QH, n, k, mp, h->t[0], coefs_all(1.0), Rv, Zv, nullptr, kModeNone,
              h->rpart, h->cnt, h->cs, false, h->st);
@@ -960,6 +1223,8 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
   h->L = L;
   h->ws = (unsigned char*)workspace;
   h->gsplit = gram_nsplit(A->n, k, k);
+  h->lsk = uses_alg3(o) ? sketch_rows(k, o) : 0;
+  h->implicit = basis_less(*A, o);
   h->graph_ok = false;
   h->graph = nullptr;
   h->prof = o.profile != 0;
@@ -1050,7 +1315,9 @@ rr_status randrand_export(rr_handle* h, int32_t what, double* dst) {
   bool is_t = false;
   switch (what) {
     case 0: src = h->Om; count = nk; is_t = true; break;
-    case 1: src = h->Q; count = nk; is_t = true; break;
+    case 1:
+      if (h->implicit) return RR_ERR_UNSUPPORTED;
+      src = h->Q; count = nk; is_t = true; break;
     case 2: src = h->kk[kRfull]; count = kk; break;
     case 3:
       if (h->o.variant != RR_VARIANT_C) return RR_ERR_INVALID_ARG;

@@ -59,6 +59,11 @@ struct OpDev {
   int* tc_err;
 };
 
+// per-column coefficients passed by value to kernels
+struct Coefs8s {
+  double v[8];
+};
+
 // Per right-hand-side Krylov scalars, device resident.
 struct ColState {
   double rho;     // r^T z (C) or r^T r (R)
@@ -133,6 +138,10 @@ void kernel_mv_df_raw(const float* points, int64_t n, int dim, double bw, double
                       const double* V, double* W, int mp, float2* pn, double* part, int nsplit,
                       cudaStream_t st);
 int kernel_mv_nsplit(int64_t n);
+// CSR: out = (A + mu I) V + a[c] X[:, c] (X may be null), gated on cs
+template <typename T>
+void csr_matvec_add(const OpDev& op, double mu, const T* V, const T* X, const double* a, T* W,
+                    int mp, const ColState* cs, cudaStream_t st, const cudaEvent_t* ev = nullptr);
 // Y = (A + mu I) Omega, Omega n x k row-major; bf16: round K and Omega to bf16
 template <typename T>
 void op_sketch(const OpDev& op, double mu, const T* Om, T* Y, int k, bool bf16,
@@ -154,6 +163,18 @@ bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const f
 size_t sketch_tc_smem_bytes();
 rr_status sketch_kernel_tc(const OpDev& op, double mu, const __nv_bfloat16* omt, int64_t ldo,
                            const float* Om, float* Y, int k, int* err, cudaStream_t st);
+
+// k_sparse.cu -- sparse-sign Omega / Theta applications (basis-less Q)
+template <typename T>
+void theta_scatter(const T* Y, int64_t n, int k, const int32_t* cols, const int8_t* sgn,
+                   int gamma_sk, double* S, cudaStream_t st);
+template <typename T>
+void omega_t_partial(const T* W, int64_t n, int k, int mp, const int32_t* cols, const int8_t* sgn,
+                     int gamma, int nslab, int rps, double* part, const ColState* cs,
+                     cudaStream_t st);
+template <typename T>
+void omega_expand(const double* s, int64_t n, int k, int mp, const int32_t* cols,
+                  const int8_t* sgn, int gamma, T* U, const ColState* cs, cudaStream_t st);
 
 // k_krylov.cu -- tall-skinny projector pieces and Krylov updates
 template <typename T>

@@ -1,0 +1,171 @@
+"""GPU parity of Alg. 3 (randomized Q-less QR) and of the basis-less C-RandRAND
+path for sparse operators (Sec. 4.2), through the C ABI, against the float64
+oracle built with orth="qless" (same Theta pattern from the same seed).
+
+Tolerances: float64 factors and iterates 1e-10 relative (the R factor is unique
+once its diagonal is positive; the GPU takes it from a Cholesky QR of the
+sketch S, the oracle from Householder QR, so they agree to u * cond(S));
+low-precision solves are judged by their float64 residual (oracle product).
+"""
+import numpy as np
+import pytest
+
+from oracle import randrand as O
+from workloads import generators as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def csr_problem(side, seed, fp64=True):
+    C = W.diffusion_csr(side=side, seed=seed, corr_len=4.0)
+    op = O.CsrOp(C.rowptr, C.colidx, C.vals, C.n)
+    vals = dev(C.vals.astype(np.float64)) if fp64 else dev(C.vals)
+    return C, op, vals
+
+
+def csr_handle(rr, C, vals, mu, k, sketch, seed, **kw):
+    return rr.Handle(rr.Operator.csr(dev(C.rowptr), dev(C.colidx), vals), mu, k, sketch,
+                     seed=seed, orth="rand_cholqr", **kw)
+
+
+# ------------------------------------------------------------ Alg. 3 factors
+@pytest.mark.parametrize("sketch", ["sparse_sign", "gaussian"])
+@pytest.mark.parametrize("side,k,l_sk", [(24, 40, 0), (30, 17, 50)])
+def test_alg3_basis_less_factors_fp64(cuda_lib, sketch, side, k, l_sk):
+    """Basis-less build on a CSR operator: R, G, tau and the power-iteration
+    estimates equal the oracle's Alg. 3 build."""
+    rr = cuda_lib
+    C, op, vals = csr_problem(side, 41)
+    mu = 1e-4
+    h = csr_handle(rr, C, vals, mu, k, sketch, 41, l_sk=l_sk, max_rhs=2)
+    bd = O.build(op, mu, k, sketch, seed=41, orth="qless", l_sk=l_sk or None)
+    cond = np.linalg.cond(bd.R)
+    R = h.export("R").cpu().numpy()
+    assert np.allclose(np.tril(R, -1), 0.0)
+    assert np.all(np.diag(R) > 0)
+    assert rel(R, bd.R) <= max(1e-12, 1e-15 * cond) * 100
+    G = h.export("G").cpu().numpy()
+    assert rel(G, bd.G) <= max(1e-12, 1e-15 * cond ** 2) * 100
+    tau, nE, lmax = h.scalars()
+    assert nE == pytest.approx(bd.normE, rel=1e-8)
+    assert lmax == pytest.approx(bd.lam_max, rel=1e-8)
+    assert tau == pytest.approx(bd.tau, rel=1e-8)
+    with pytest.raises(rr.RandRandError):
+        h.export("Q")          # no basis is kept
+
+
+def test_alg3_explicit_basis_dense_fp64(cuda_lib):
+    """Alg. 3 on a dense operator keeps Q = W chol(W^T W)^-1: Q and R equal the
+    oracle's (which forms Q = Y_mu R^-1)."""
+    rr = cuda_lib
+    n, k, mu = 700, 60, 1e-4
+    P = W.dense_power_spectrum(n, seed=W.SEED_DENSE, power=2.0)
+    op = O.DenseOp(P.A)
+    h = rr.Handle(rr.Operator.dense(dev(P.A)), mu, k, "gaussian", seed=7, orth="rand_cholqr")
+    bd = O.build(op, mu, k, "gaussian", seed=7, orth="qless")
+    cond = np.linalg.cond(bd.R)
+    assert rel(h.export("R").cpu().numpy(), bd.R) <= max(1e-12, 1e-15 * cond) * 100
+    Q = h.export("Q").cpu().numpy()
+    assert rel(Q, bd.Q) <= max(1e-12, 1e-15 * cond) * 100
+    assert np.linalg.norm(Q.T @ Q - np.eye(k)) <= 1e-13
+
+
+# ------------------------------------------------------- preconditioner apply
+@pytest.mark.parametrize("sketch", ["sparse_sign", "gaussian"])
+def test_basis_less_apply_fp64(cuda_lib, sketch):
+    """z = P r with Q applied through A_mu, Omega and R^-1 equals the oracle's
+    P r = r - Q Q^T r + tau Q G Q^T r with its explicit Q."""
+    rr = cuda_lib
+    C, op, vals = csr_problem(24, 42)
+    mu, k = 1e-4, 40
+    h = csr_handle(rr, C, vals, mu, k, sketch, 42, max_rhs=3)
+    bd = O.build(op, mu, k, sketch, seed=42, orth="qless")
+    r = np.random.default_rng(1).standard_normal((C.n, 3))
+    z = h.apply(dev(r)).cpu().numpy()
+    cond = np.linalg.cond(bd.R)
+    assert rel(z, bd.apply_P(r)) <= max(1e-12, 1e-15 * cond ** 2) * 100
+
+
+# ---------------------------------------------------------------- solves
+@pytest.mark.parametrize("sketch", ["sparse_sign", "gaussian"])
+@pytest.mark.parametrize("m", [1, 3])
+def test_basis_less_iteration_level_fp64(cuda_lib, sketch, m):
+    """After a fixed inner budget the GPU iterate equals the oracle iterate."""
+    rr = cuda_lib
+    C, op, vals = csr_problem(30, 43)
+    mu, k = 1e-4, 48
+    B = W.gaussian_rhs(C.n, m, 43)
+    h = csr_handle(rr, C, vals, mu, k, sketch, 43, max_rhs=m)
+    bd = O.build(op, mu, k, sketch, seed=43, orth="qless")
+    for budget in (3, 12):
+        x, status, infos = h.solve(dev(B), rtol=1e-14, maxit=budget)
+        xo, oinfo = O.solve(bd, B, rtol=1e-14, maxit=budget)
+        assert status == rr.RR_ERR_MAXIT
+        assert [i["inner_iters"] for i in infos] == [i.inner_iters for i in oinfo]
+        assert rel(x.cpu().numpy(), xo) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "fp32"])
+def test_basis_less_solve(cuda_lib, precision):
+    """Solves to rtol 1e-6 with the float64 residual as the judge; the float64
+    path also reaches the dense Cholesky solution."""
+    rr = cuda_lib
+    C, op, vals = csr_problem(40, 44, fp64=(precision == "fp64"))
+    mu, k = 1e-6, 32
+    b = W.gaussian_rhs(C.n, 2, 44)
+    h = csr_handle(rr, C, vals, mu, k, "sparse_sign", 44, precision=precision, max_rhs=2)
+    if precision == "fp32":
+        x, status, infos = h.solve(dev(b), rtol=1e-4, maxit=20000)
+        assert status == rr.RR_OK
+        assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), b) <= 2e-4)
+        return
+    x, status, infos = h.solve(dev(b), rtol=1e-6, maxit=20000)
+    assert status == rr.RR_OK
+    assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), b) <= 1e-6)
+    assert all(i["matvecs"] >= 3 * i["inner_iters"] for i in infos)
+    if precision == "fp64":
+        x, status, infos = h.solve(dev(b), rtol=1e-12, maxit=20000)
+        assert status == rr.RR_OK
+        xs = O.exact_solve(op, mu, b)
+        assert rel(x.cpu().numpy(), xs) <= 1e-7
+
+
+def test_basis_less_variant_R_unsupported(cuda_lib):
+    rr = cuda_lib
+    C, op, vals = csr_problem(16, 45)
+    with pytest.raises(rr.RandRandError):
+        csr_handle(rr, C, vals, 1e-4, 8, "sparse_sign", 45, variant="R")
+
+
+def test_sparse_operator_full_size(cuda_lib):
+    """The 512 x 512 variable-coefficient diffusion operator (n = 262144, CSR
+    float32, log-normal coefficients sigma = 1, correlation length 16),
+    mu = 1e-6, k = 256, sparse-sign Omega with 8 nonzeros per row, Alg. 3 with
+    l_sk = 1024, basis-less C-RandRAND PCG with float32 iterations and float64
+    refinement to rtol 1e-6.  Judge: the float64 residual of the oracle's
+    product, per column."""
+    rr = cuda_lib
+    C = W.diffusion_csr(side=512, seed=W.SEED_CSR)
+    op = O.CsrOp(C.rowptr, C.colidx, C.vals, C.n)
+    mu, k = 1e-6, 256
+    b = W.gaussian_rhs(C.n, 1, W.SEED_CSR)
+    h = rr.Handle(rr.Operator.csr(dev(C.rowptr), dev(C.colidx), dev(C.vals)), mu, k,
+                  "sparse_sign", seed=W.SEED_CSR, precision="mixed", orth="rand_cholqr",
+                  l_sk=1024)
+    x, status, infos = h.solve(dev(b), rtol=1e-6, maxit=50000)
+    assert status == rr.RR_OK
+    res = O.true_rel_residual(op, mu, x.cpu().numpy(), b)
+    assert res[0] <= 1e-6
+    assert infos[0]["rel_residual"] == pytest.approx(res[0], rel=1e-3)
