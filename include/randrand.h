@@ -47,7 +47,8 @@ enum {
   RR_ERR_MAXIT = 5,         /* iteration budget reached before rtol; x holds the last iterate */
   RR_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
   RR_ERR_CUDA = 7,          /* a CUDA runtime call failed */
-  RR_ERR_UNSUPPORTED = 8    /* the combination of options is not implemented */
+  RR_ERR_UNSUPPORTED = 8,   /* the combination of options is not implemented */
+  RR_PENDING = 9            /* server request queued or running (rr_server_poll) */
 };
 
 /* Operator kinds: A is only accessed through u -> A u (Sec. 1) */
@@ -309,6 +310,89 @@ rr_status randrand_matvec(rr_handle* h, const double* v, double* w, int32_t m, i
 rr_status randrand_kernel_matvec_noalloc(const float* points, int64_t n, int32_t dim,
                                          double bandwidth, double mu, const double* v, double* w,
                                          int32_t m, int64_t ld, void* stream);
+
+/* ======================================================================
+ * Many systems on one GPU: batched execution and a serving loop.
+ * Neither is in the paper; they run its solver (randrand_build +
+ * randrand_solve + randrand_free per system) for many independent systems
+ * at once.  Worker threads of the library each own a CUDA stream and run
+ * one system at a time in a slice of a caller-provided device arena; the
+ * kernels of the systems resident at the same time overlap on the GPU.
+ * ====================================================================== */
+
+/* One system to solve.  Everything the pointers reference is borrowed until
+ * the request has completed (its result is no longer RR_PENDING). */
+typedef struct {
+  rr_operator op;
+  double mu;
+  int32_t k;
+  int32_t sketch;          /* RR_SKETCH_*                                     */
+  uint64_t seed;
+  rr_build_opts opts;      /* opts.max_rhs >= nrhs                            */
+  const double* b;         /* device, n x nrhs column-major, leading dim ldb */
+  double* x;               /* device, n x nrhs column-major, leading dim ldx:
+                              the solution, written before completion        */
+  int64_t ldb;
+  int64_t ldx;
+  int32_t nrhs;            /* 1..8                                            */
+  int32_t maxit;
+  double rtol;
+} rr_request;
+
+/* Outcome of one request.  Times are host wall-clock milliseconds since the
+ * server (or batch) was created: submit, admission (start) and completion
+ * (end); queue = start - submit, build and solve are the two phases. */
+typedef struct {
+  rr_status status;        /* RR_PENDING until done, then the solve's status
+                              (or the build's, if the build failed)          */
+  int32_t nrhs;
+  size_t ws_bytes;         /* arena bytes the request held                    */
+  double submit_ms, start_ms, end_ms;
+  double queue_ms, build_ms, solve_ms;
+  rr_solve_info info[8];   /* per right-hand side                             */
+} rr_result;
+
+/* First-fit allocator of the serving loop over byte offsets [0, bytes),
+ * 256-byte granularity, neighbouring free blocks coalesced.  Host only (no
+ * CUDA call); exposed for inspection and tests.  alloc returns
+ * RR_ERR_WORKSPACE when no free block is large enough; free returns
+ * RR_ERR_INVALID_ARG for an offset that is not allocated. */
+typedef struct rr_arena rr_arena;
+rr_status rr_arena_create(size_t bytes, rr_arena** out);
+rr_status rr_arena_alloc(rr_arena* a, size_t bytes, size_t* offset);
+rr_status rr_arena_free(rr_arena* a, size_t offset);
+rr_status rr_arena_stats(const rr_arena* a, size_t* in_use, size_t* largest_free);
+void rr_arena_destroy(rr_arena* a);
+
+/*
+ * Serving loop.  rr_server_create: `arena` (device, 256-byte aligned,
+ * caller-owned, arena_bytes >= 256) is the HBM budget shared by all resident
+ * requests; `workers` (1..256) threads on the current device.  Requests are
+ * admitted in arrival order: the oldest waiting request starts as soon as a
+ * worker is idle and randrand_workspace_bytes of it fits in the arena.
+ * rr_server_submit copies the request and returns a ticket at once
+ * (RR_ERR_WORKSPACE if the request could never fit, RR_ERR_INVALID_ARG on
+ * bad arguments).  rr_server_poll fills *out for a ticket (wait != 0: block
+ * until it is done).  rr_server_drain waits until every submitted request is
+ * done.  rr_server_destroy drains, then stops the workers.
+ */
+typedef struct rr_server rr_server;
+rr_status rr_server_create(void* arena, size_t arena_bytes, int32_t workers, rr_server** out);
+rr_status rr_server_submit(rr_server* s, const rr_request* req, uint64_t* ticket);
+rr_status rr_server_poll(rr_server* s, uint64_t ticket, int32_t wait, rr_result* out);
+rr_status rr_server_drain(rr_server* s);
+rr_status rr_server_stats(rr_server* s, int32_t* queued, int32_t* running, size_t* bytes_in_use,
+                          size_t* peak_bytes);
+void rr_server_destroy(rr_server* s);
+
+/*
+ * Batched execution of nsys independent systems: a server over `arena` with
+ * min(workers, nsys) workers, the systems submitted largest workspace first,
+ * drained; results[i] belongs to reqs[i].  Returns RR_OK when every system
+ * converged, else the first non-OK status in input order.
+ */
+rr_status randrand_solve_batch(const rr_request* reqs, int32_t nsys, void* arena,
+                               size_t arena_bytes, int32_t workers, rr_result* results);
 
 #ifdef __cplusplus
 }

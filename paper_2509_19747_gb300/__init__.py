@@ -18,15 +18,16 @@ from .build import lib_path
 
 __all__ = [
     "RR_OK", "RR_ERR_INVALID_ARG", "RR_ERR_WORKSPACE", "RR_ERR_NOT_SPD", "RR_ERR_BREAKDOWN",
-    "RR_ERR_MAXIT", "RR_ERR_TIMEOUT", "RR_ERR_CUDA", "RR_ERR_UNSUPPORTED",
+    "RR_ERR_MAXIT", "RR_ERR_TIMEOUT", "RR_ERR_CUDA", "RR_ERR_UNSUPPORTED", "RR_PENDING",
     "RR_OP_DENSE", "RR_OP_CSR", "RR_OP_GAUSS_KERNEL", "RR_SKETCH_GAUSSIAN",
     "RR_SKETCH_SPARSE_SIGN", "RR_PREC_FP64", "RR_PREC_FP32", "RR_PREC_MIXED", "RR_VARIANT_C",
     "RR_VARIANT_R", "rr_operator", "rr_build_opts", "rr_solve_info", "rr_profile", "RandRandError",
-    "load_library", "Operator", "Handle",
+    "load_library", "Operator", "Handle", "rr_request", "rr_result", "Arena", "Server",
+    "Request", "solve_batch",
 ]
 
 RR_OK, RR_ERR_INVALID_ARG, RR_ERR_WORKSPACE, RR_ERR_NOT_SPD, RR_ERR_BREAKDOWN = 0, 1, 2, 3, 4
-RR_ERR_MAXIT, RR_ERR_TIMEOUT, RR_ERR_CUDA, RR_ERR_UNSUPPORTED = 5, 6, 7, 8
+RR_ERR_MAXIT, RR_ERR_TIMEOUT, RR_ERR_CUDA, RR_ERR_UNSUPPORTED, RR_PENDING = 5, 6, 7, 8, 9
 RR_OP_DENSE, RR_OP_CSR, RR_OP_GAUSS_KERNEL = 0, 1, 2
 RR_SKETCH_GAUSSIAN, RR_SKETCH_SPARSE_SIGN = 0, 1
 RR_PREC_FP64, RR_PREC_FP32, RR_PREC_MIXED = 0, 1, 2
@@ -77,6 +78,30 @@ class rr_solve_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class rr_request(ctypes.Structure):
+    _fields_ = [
+        ("op", rr_operator), ("mu", ctypes.c_double), ("k", ctypes.c_int32),
+        ("sketch", ctypes.c_int32), ("seed", ctypes.c_uint64), ("opts", rr_build_opts),
+        ("b", ctypes.c_void_p), ("x", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+        ("ldx", ctypes.c_int64), ("nrhs", ctypes.c_int32), ("maxit", ctypes.c_int32),
+        ("rtol", ctypes.c_double),
+    ]
+
+
+class rr_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("ws_bytes", ctypes.c_size_t),
+        ("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double),
+        ("queue_ms", ctypes.c_double), ("build_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+        ("info", rr_solve_info * 8),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "info"}
+        d["info"] = [self.info[i].as_dict() for i in range(self.nrhs)]
+        return d
+
+
 class RandRandError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -118,6 +143,27 @@ _SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     ("randrand_apply_operator", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
+    ("rr_arena_create", ctypes.c_int32, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
+    ("rr_arena_alloc", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    ("rr_arena_free", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_size_t]),
+    ("rr_arena_stats", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    ("rr_arena_destroy", None, [ctypes.c_void_p]),
+    ("rr_server_create", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    ("rr_server_submit", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.POINTER(rr_request), ctypes.POINTER(ctypes.c_uint64)]),
+    ("rr_server_poll", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(rr_result)]),
+    ("rr_server_drain", ctypes.c_int32, [ctypes.c_void_p]),
+    ("rr_server_stats", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+      ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    ("rr_server_destroy", None, [ctypes.c_void_p]),
+    ("randrand_solve_batch", ctypes.c_int32,
+     [ctypes.POINTER(rr_request), ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
+      ctypes.POINTER(rr_result)]),
 ]
 
 
@@ -387,6 +433,158 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+
+
+# ------------------------------------------------- many systems on one GPU
+class Arena:
+    """Host-side first-fit allocator over byte offsets (rr_arena_*)."""
+
+    def __init__(self, nbytes: int):
+        self.a = ctypes.c_void_p(None)
+        s = _lib().rr_arena_create(int(nbytes), ctypes.byref(self.a))
+        if s != RR_OK:
+            raise RandRandError(s, "rr_arena_create")
+
+    def alloc(self, nbytes: int):
+        """Offset of a new block, or None when no free block is large enough."""
+        off = ctypes.c_size_t(0)
+        s = _lib().rr_arena_alloc(self.a, int(nbytes), ctypes.byref(off))
+        if s == RR_ERR_WORKSPACE:
+            return None
+        if s != RR_OK:
+            raise RandRandError(s, "rr_arena_alloc")
+        return int(off.value)
+
+    def free(self, offset: int):
+        s = _lib().rr_arena_free(self.a, int(offset))
+        if s != RR_OK:
+            raise RandRandError(s, "rr_arena_free")
+
+    def stats(self):
+        used, largest = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        _lib().rr_arena_stats(self.a, ctypes.byref(used), ctypes.byref(largest))
+        return int(used.value), int(largest.value)
+
+    def close(self):
+        if self.a.value:
+            _lib().rr_arena_destroy(self.a)
+            self.a = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Request:
+    """One system for Server / solve_batch.  b: (n,) or (n, m) float64 CUDA
+    tensor; the solution is written to ``self.x`` (same shape) on completion.
+    Keeps every tensor it points to alive."""
+
+    def __init__(self, op: Operator, mu: float, k: int, b, rtol: float, sketch: str = "gaussian",
+                 seed: int = 0, maxit: int = 20000, variant: str = "C", precision: str = "mixed",
+                 orth: str = "cholqr2", power_iters: int = 20, gamma: int = 8, l_sk: int = 0,
+                 gamma_sk: int = 8, kernel_impl: int = 0):
+        import torch
+        B = b.reshape(op.n, -1)
+        m = B.shape[1]
+        self.shape = b.shape
+        self.bc = B.t().contiguous()            # column-major n x m
+        self.xc = torch.zeros_like(self.bc)
+        o = rr_build_opts_default()
+        o.variant = VARIANTS[variant]
+        o.precision = PRECISIONS[precision]
+        o.orth = ORTHS[orth]
+        o.max_rhs = m
+        o.power_iters = power_iters
+        o.gamma = gamma
+        o.l_sk = l_sk
+        o.gamma_sk = gamma_sk
+        o.kernel_impl = kernel_impl
+        self.op = op
+        self.c = rr_request(op=op.c, mu=float(mu), k=int(k), sketch=SKETCHES[sketch],
+                            seed=int(seed) & 0xFFFFFFFFFFFFFFFF, opts=o, b=self.bc.data_ptr(),
+                            x=self.xc.data_ptr(), ldb=op.n, ldx=op.n, nrhs=m, maxit=int(maxit),
+                            rtol=float(rtol))
+
+    @property
+    def x(self):
+        X = self.xc.t()
+        return X.reshape(self.shape)
+
+    def workspace_bytes(self) -> int:
+        return randrand_workspace_bytes(self.op.c, self.c.k, self.c.opts)
+
+
+class Server:
+    """Serving loop (rr_server_*) over a device arena of ``budget_bytes``."""
+
+    def __init__(self, budget_bytes: int, workers: int = 8):
+        import torch
+        self.arena = torch.empty(int(budget_bytes), dtype=torch.uint8, device="cuda")
+        self.s = ctypes.c_void_p(None)
+        st = _lib().rr_server_create(ctypes.c_void_p(self.arena.data_ptr()), int(budget_bytes),
+                                     int(workers), ctypes.byref(self.s))
+        if st != RR_OK:
+            raise RandRandError(st, "rr_server_create")
+        self._keep = {}
+
+    def submit(self, req: Request) -> int:
+        t = ctypes.c_uint64(0)
+        st = _lib().rr_server_submit(self.s, ctypes.byref(req.c), ctypes.byref(t))
+        if st != RR_OK:
+            raise RandRandError(st, "rr_server_submit")
+        self._keep[int(t.value)] = req
+        return int(t.value)
+
+    def poll(self, ticket: int, wait: bool = False) -> dict:
+        r = rr_result()
+        st = _lib().rr_server_poll(self.s, int(ticket), 1 if wait else 0, ctypes.byref(r))
+        if st != RR_OK:
+            raise RandRandError(st, "rr_server_poll")
+        if r.status != RR_PENDING:
+            self._keep.pop(int(ticket), None)
+        return r.as_dict()
+
+    def drain(self):
+        _lib().rr_server_drain(self.s)
+
+    def stats(self) -> dict:
+        q, r = ctypes.c_int32(0), ctypes.c_int32(0)
+        used, peak = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        _lib().rr_server_stats(self.s, ctypes.byref(q), ctypes.byref(r), ctypes.byref(used),
+                               ctypes.byref(peak))
+        return {"queued": q.value, "running": r.value, "bytes_in_use": used.value,
+                "peak_bytes": peak.value}
+
+    def close(self):
+        if self.s.value:
+            _lib().rr_server_destroy(self.s)
+            self.s = ctypes.c_void_p(None)
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batch(reqs: list, workers: int = 8, arena_bytes: int | None = None):
+    """randrand_solve_batch over the requests; returns (status, [result dicts])."""
+    import torch
+    n = len(reqs)
+    arr = (rr_request * n)(*[r.c for r in reqs])
+    res = (rr_result * n)()
+    if arena_bytes is None:
+        arena_bytes = sum((r.workspace_bytes() + 255) // 256 * 256 for r in reqs)
+    arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
+    st = _lib().randrand_solve_batch(arr, n, ctypes.c_void_p(arena.data_ptr()), int(arena_bytes),
+                                     int(workers), res)
+    del arena
+    return st, [res[i].as_dict() for i in range(n)]
 
 
 load_library()

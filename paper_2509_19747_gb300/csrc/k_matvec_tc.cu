@@ -292,16 +292,19 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  static std::atomic<EncodeTiledFn> fn{nullptr};
+  EncodeTiledFn f = fn.load(std::memory_order_acquire);
+  if (!f) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
+        q == cudaDriverEntryPointSuccess) {
+      f = (EncodeTiledFn)p;
+      fn.store(f, std::memory_order_release);
+    }
   }
-  return fn;
+  return f;
 }
 
 bool encode_aug(CUtensorMap* map, const float* base, int64_t npad) {
@@ -318,14 +321,11 @@ bool encode_aug(CUtensorMap* map, const float* base, int64_t npad) {
 
 template <int MP>
 bool set_attr() {
-  static bool done = false;
-  if (!done) {
-    if (cudaFuncSetAttribute(k_kernel_mv_tc<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)mv_smem_bytes<MP>()) != cudaSuccess)
-      return false;
-    done = true;
-  }
-  return true;
+  static std::atomic<uint64_t> done{0};
+  return once_per_device(done, [] {
+    return cudaFuncSetAttribute(k_kernel_mv_tc<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)mv_smem_bytes<MP>()) == cudaSuccess;
+  });
 }
 
 }  // namespace

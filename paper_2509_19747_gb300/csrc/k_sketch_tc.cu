@@ -275,16 +275,19 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  static std::atomic<EncodeTiledFn> fn{nullptr};
+  EncodeTiledFn f = fn.load(std::memory_order_acquire);
+  if (!f) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
+        q == cudaDriverEntryPointSuccess) {
+      f = (EncodeTiledFn)p;
+      fn.store(f, std::memory_order_release);
+    }
   }
-  return fn;
+  return f;
 }
 
 }  // namespace
@@ -311,13 +314,12 @@ rr_status sketch_kernel_tc(const OpDev& op, double mu, const __nv_bfloat16* omt,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return RR_ERR_UNSUPPORTED;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_kernel_sketch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes) != cudaSuccess)
-      return RR_ERR_CUDA;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  if (!once_per_device(attr, [] {
+        return cudaFuncSetAttribute(k_kernel_sketch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSmemBytes) == cudaSuccess;
+      }))
+    return RR_ERR_CUDA;
   dim3 grid((unsigned)cdiv(op.n, kBM), (unsigned)cdiv(k, kBN));
   k_kernel_sketch_tc<<<grid, kThreads, kSmemBytes, st>>>(map, op.xs, op.cn, op.n, k, mu, Om, Y,
                                                           err);

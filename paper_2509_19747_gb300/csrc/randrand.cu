@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -149,6 +150,37 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
       return RR_ERR_INVALID_ARG;
   }
   return RR_OK;
+}
+
+// Pinned host blocks for the per-handle scalar read-backs.  Taken from a
+// process-wide pool that grows in chunks and is never returned to the
+// driver: pinned allocation and release can stall other streams, and the
+// serving loop builds and frees handles while other systems run.
+constexpr size_t kPinnedBlock = 4096;
+constexpr int kPinnedChunk = 64;
+struct PinnedPool {
+  std::mutex m;
+  std::vector<void*> free_;
+  void* get() {
+    std::lock_guard<std::mutex> lk(m);
+    if (free_.empty()) {
+      void* chunk = nullptr;
+      if (cudaMallocHost(&chunk, kPinnedBlock * kPinnedChunk) != cudaSuccess) return nullptr;
+      for (int i = 0; i < kPinnedChunk; ++i) free_.push_back((unsigned char*)chunk + i * kPinnedBlock);
+    }
+    void* b = free_.back();
+    free_.pop_back();
+    return b;
+  }
+  void put(void* b) {
+    if (!b) return;
+    std::lock_guard<std::mutex> lk(m);
+    free_.push_back(b);
+  }
+};
+PinnedPool& pinned_pool() {
+  static PinnedPool* pool = new PinnedPool();   // lives until process exit
+  return *pool;
 }
 
 }  // namespace
@@ -1244,8 +1276,12 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
     }
   }
   carve(h);
-  if (cudaMallocHost(&h->cs_host, 8 * sizeof(ColState)) != cudaSuccess ||
-      cudaMallocHost(&h->norms_host, 64 * sizeof(double)) != cudaSuccess) {
+  static_assert(8 * sizeof(ColState) <= kPinnedBlock / 2 && 64 * sizeof(double) <= kPinnedBlock / 2,
+                "pinned block too small");
+  unsigned char* pin = (unsigned char*)pinned_pool().get();
+  h->cs_host = (ColState*)pin;
+  h->norms_host = pin ? (double*)(pin + kPinnedBlock / 2) : nullptr;
+  if (!pin) {
     randrand_free(h);
     return RR_ERR_CUDA;
   }
@@ -1289,8 +1325,7 @@ void randrand_free(rr_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
   if (h->graph_ok) cudaGraphExecDestroy(h->graph);
-  if (h->cs_host) cudaFreeHost(h->cs_host);
-  if (h->norms_host) cudaFreeHost(h->norms_host);
+  pinned_pool().put(h->cs_host);
   for (auto* v : {&h->ev_free, &h->ev_pending, &h->ev_graph})
     for (auto& p : *v) {
       cudaEventDestroy(p.e[0]);

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
@@ -58,6 +59,20 @@ struct OpDev {
   const void* bmap;
   int* tc_err;
 };
+
+// One-time host setup per device (function attributes): bit d of `mask` is
+// set once fn() has succeeded with device d current.  Safe to call from
+// several host threads (a repeated fn() call is harmless).
+template <typename F>
+inline bool once_per_device(std::atomic<uint64_t>& mask, F fn) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fn();
+  const uint64_t bit = 1ull << dev;
+  if (mask.load(std::memory_order_acquire) & bit) return true;
+  if (!fn()) return false;
+  mask.fetch_or(bit, std::memory_order_acq_rel);
+  return true;
+}
 
 // per-column coefficients passed by value to kernels
 struct Coefs8s {

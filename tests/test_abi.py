@@ -47,8 +47,10 @@ def test_struct_layouts_match_header(lib):
     #include <stddef.h>
     #include "randrand.h"
     int main(void){
-      printf("%zu %zu %zu %zu %zu\n", sizeof(rr_operator), sizeof(rr_build_opts), sizeof(rr_solve_info),
-             offsetof(rr_operator, bandwidth), offsetof(rr_build_opts, rho));
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rr_operator), sizeof(rr_build_opts),
+             sizeof(rr_solve_info), offsetof(rr_operator, bandwidth), offsetof(rr_build_opts, rho),
+             sizeof(rr_request), sizeof(rr_result), offsetof(rr_request, rtol),
+             offsetof(rr_result, info));
       return 0; }
     '''
     with tempfile.TemporaryDirectory() as d:
@@ -63,6 +65,10 @@ def test_struct_layouts_match_header(lib):
     assert sizes[2] == ctypes.sizeof(lib.rr_solve_info)
     assert sizes[3] == lib.rr_operator.bandwidth.offset
     assert sizes[4] == lib.rr_build_opts.rho.offset
+    assert sizes[5] == ctypes.sizeof(lib.rr_request)
+    assert sizes[6] == ctypes.sizeof(lib.rr_result)
+    assert sizes[7] == lib.rr_request.rtol.offset
+    assert sizes[8] == lib.rr_result.info.offset
 
 
 def test_defaults_and_status_strings(lib):
@@ -124,3 +130,71 @@ def test_oracle_not_imported_by_product():
             if f.endswith((".py", ".cu", ".cuh")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_arena_first_fit_and_coalescing(lib):
+    """The serving loop's HBM-budget allocator (host only)."""
+    a = lib.Arena(10 * 256 + 100)             # usable: 10 blocks of 256 bytes
+    assert a.stats() == (0, 2560)
+    o1 = a.alloc(256)
+    o2 = a.alloc(300)                          # rounds up to 512
+    o3 = a.alloc(256)
+    assert (o1, o2, o3) == (0, 256, 768)
+    assert a.stats() == (1024, 1536)
+    assert a.alloc(2000) is None               # larger than any free block
+    a.free(o2)
+    assert a.alloc(512) == 256                 # first fit reuses the hole
+    a.free(256)
+    a.free(o1)                                 # coalesces with the hole after it
+    assert a.stats() == (256, 1536)
+    assert a.alloc(768) == 0
+    a.free(0)
+    a.free(o3)                                 # everything merges back
+    assert a.stats() == (0, 2560)
+    with pytest.raises(lib.RandRandError):
+        a.free(12345)                          # not an allocated offset
+    a.close()
+
+
+def test_arena_random_sequence_matches_model(lib):
+    """Random alloc/free sequences against a plain list model of first fit."""
+    import random
+    rng = random.Random(7)
+    nblk = 64
+    a = lib.Arena(nblk * 256)
+    owner = [None] * nblk                      # model: which allocation holds each block
+    live = {}
+    for step in range(2000):
+        if live and rng.random() < 0.45:
+            off = rng.choice(list(live))
+            a.free(off)
+            for b in range(off // 256, off // 256 + live.pop(off)):
+                owner[b] = None
+        else:
+            want = rng.randint(1, 8)
+            got = a.alloc(want * 256 - rng.randint(0, 255))
+            exp = None
+            for s in range(nblk - want + 1):
+                if all(owner[b] is None for b in range(s, s + want)):
+                    exp = s
+                    break
+            assert (got is None) == (exp is None)
+            if got is not None:
+                assert got == exp * 256
+                for b in range(exp, exp + want):
+                    owner[b] = got
+                live[got] = want
+        used, largest = a.stats()
+        assert used == 256 * sum(live.values())
+    a.close()
+
+
+def test_server_rejects_bad_arguments_without_gpu_work(lib):
+    import ctypes as C
+    s = C.c_void_p(None)
+    cdll = lib.load_library()
+    assert cdll.rr_server_create(None, 1 << 20, 2, C.byref(s)) == lib.RR_ERR_INVALID_ARG
+    assert cdll.rr_server_create(C.c_void_p(0x100001), 1 << 20, 2, C.byref(s)) == lib.RR_ERR_INVALID_ARG
+    assert cdll.rr_server_create(C.c_void_p(0x100000), 1 << 20, 0, C.byref(s)) == lib.RR_ERR_INVALID_ARG
+    res = (lib.rr_result * 1)()
+    assert cdll.randrand_solve_batch(None, 1, C.c_void_p(0x100000), 1 << 20, 1, res) == lib.RR_ERR_INVALID_ARG
