@@ -12,6 +12,18 @@ ridge datasets are not available offline; the mixture stands in for them).
 
 Prints ONE JSON line (rank 0).  --impl reference times the float64 CPU oracle
 instead, on a bounded sample of the same workload.
+
+Other workloads (--workload; each prints its own JSON line):
+  sparse_diffusion  512 x 512 variable-coefficient diffusion (CSR float32,
+                    n = 262144), mu = 1e-6, k = 256, sparse-sign Omega,
+                    Alg. 3 with the basis-less iteration, rtol 1e-6.
+  batched           64 independent kernel ridge systems, n ~ U{2000..16000},
+                    k = n/40, mu log-uniform in [1e-5, 1e-2], 8 right-hand
+                    sides each, one randrand_solve_batch per step.
+  serving           Poisson arrivals (200 req/s) of kernel (n log-uniform in
+                    [1000, 32000], mu = 1e-3) and CSR diffusion (grid side in
+                    128..512, mu = 1e-6) requests, k = n/50, 1 right-hand
+                    side, rtol 1e-6, HBM budget 120 GB; p50/p99 latency.
 """
 from __future__ import annotations
 
@@ -46,6 +58,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--workload", default="kernel_ridge",
+                    choices=["kernel_ridge", "sparse_diffusion", "batched", "serving"])
+    ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
+    ap.add_argument("--workers", type=int, default=0, help="batched/serving: 0 = autotune")
     return ap.parse_args()
 
 
@@ -296,6 +313,8 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(rr, torch, op, o, ws, ws_bytes, stream, X, B, seed, args, world, flush)
 
+    plain = None if args.no_plain else run_plain(rr, torch, op, m, k, seed, Bc)
+
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -308,7 +327,7 @@ def run_ours(args):
         "solve": {"inner_iters_max": iters, "rel_residual_max": rel_res},
         "kernels_ms_per_step": {kk: v[1] / args.steps for kk, v in cats.items()},
         "roofline": roof, "roofline_other": others, "clocks": clocks,
-        "gpu_launches": gpu_launches, "e2e": e2e,
+        "gpu_launches": gpu_launches, "e2e": e2e, "plain_form": plain,
         "wall_s": wall,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -321,6 +340,29 @@ def run_ours(args):
                        f"products per solve")}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_plain(rr, torch, op, m, k, seed, Bc, maxit=4000):
+    """The plain form: float32 sketch on the float32 cores, float32 PCG and
+    float32 residuals, direct launches on the legacy stream (no graphs), one
+    system.  Reported with its own residual; it may stop short of rtol."""
+    n = WORKLOAD["n"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = rr.Handle(op, WORKLOAD["mu"], k, WORKLOAD["sketch"], seed=seed, precision="fp32",
+                  max_rhs=m, kernel_impl=1, stream=torch.cuda.default_stream())
+    Xc = torch.zeros_like(Bc)
+    s, infos = rr.randrand_solve(h.h, Bc.data_ptr(), m, n, Xc.data_ptr(), n, 0, WORKLOAD["rtol"], maxit)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h.close()
+    conv = s == rr.RR_OK
+    return {"value": (1.0 / dt) if conv else None, "unit": "solves/s", "seconds": dt,
+            "converged": conv, "status": rr.randrand_status_str(s),
+            "inner_iters_max": max(i["inner_iters"] for i in infos),
+            "rel_residual_max": max(i["rel_residual"] for i in infos),
+            "config": "fp32 sketch on float32 cores, fp32 iterations and residuals, no graphs, "
+                      f"maxit {maxit}"}
 
 
 def estimate_launches(prof):
@@ -408,9 +450,321 @@ def ctypes_copy(dst, src):
         setattr(dst, f, getattr(src, f))
 
 
+# ------------------------------------------------------------ other workloads
+SPARSE = dict(workload="sparse_diffusion", side=512, n=262144, mu=1e-6, k=256, l_sk=1024,
+              gamma=8, gamma_sk=8, nrhs=1, rtol=1e-6, precision="mixed",
+              orth="rand_cholqr (basis-less)", seed=0x52523)
+BATCHED = dict(workload="batched_kernel_ridge", systems=64, n_min=2000, n_max=16000,
+               k="n/40", mu="10^U(-5,-2)", nrhs=8, rtol=1e-6, precision="mixed", seed=0x52524)
+SERVING = dict(workload="serving_mix", rate_per_s=200.0, kernel_share=0.5, kernel_n=[1000, 32000],
+               csr_side=[128, 512], k="n/50", nrhs=1, rtol=1e-6, budget_gb=120.0,
+               precision="mixed", seed=0x52525)
+
+
+def _line(args, world, metric, value, unit, ms_per_step, config, **extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config}
+    line.update(extra)
+    return line
+
+
+def run_other(args):
+    if args.impl == "reference":
+        rank, world, _ = dist_init(args)
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "workload": args.workload,
+                              "unavailable": "the oracle arm times the kernel ridge workload only"}))
+        return
+    {"sparse_diffusion": run_sparse, "batched": run_batched, "serving": run_serving}[args.workload](args)
+
+
+def run_sparse(args):
+    import torch
+    rank, world, local = dist_init(args)
+    torch.cuda.set_device(local)
+    import paper_2509_19747_gb300 as rr
+    from workloads import generators as W
+    cfg = SPARSE
+    seed = cfg["seed"] + 1000 * rank
+    C = W.diffusion_csr(side=cfg["side"], seed=cfg["seed"])
+    b = W.gaussian_rhs(C.n, 1, seed)
+    stream = torch.cuda.Stream()
+    rp, ci, va = (torch.from_numpy(a).cuda() for a in (C.rowptr, C.colidx, C.vals))
+    op = rr.Operator.csr(rp, ci, va)
+    o = rr.rr_build_opts_default()
+    o.precision = rr.RR_PREC_MIXED
+    o.orth = rr.RR_ORTH_RAND_CHOLQR
+    o.l_sk = cfg["l_sk"]
+    o.gamma = cfg["gamma"]
+    o.gamma_sk = cfg["gamma_sk"]
+    o.profile = 1
+    ws_bytes = rr.randrand_workspace_bytes(op.c, cfg["k"], o)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    bd = torch.from_numpy(np.ascontiguousarray(b[:, 0])).cuda()
+    xd = torch.zeros_like(bd)
+
+    def one(collect=None):
+        h = rr.randrand_build(op.c, cfg["mu"], cfg["k"], rr.RR_SKETCH_SPARSE_SIGN, seed, o,
+                              ws.data_ptr(), ws_bytes, stream.cuda_stream)
+        st, infos = rr.randrand_solve(h, bd.data_ptr(), 1, C.n, xd.data_ptr(), C.n, 0, cfg["rtol"],
+                                      100000)
+        if st != rr.RR_OK:
+            raise RuntimeError(f"sparse solve failed: {rr.randrand_status_str(st)} {infos}")
+        if collect is not None:
+            collect.append((rr.randrand_profile(h), infos))
+        rr.randrand_free(h)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one()
+        torch.cuda.synchronize()
+        smi = ClockSampler()
+        barrier(world)
+        smi.start()
+        step_ms, prof = [], []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one(prof)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        barrier(world)
+        clocks = smi.stop()
+    ms = max_over_ranks(sum(step_ms), world) / args.steps
+    infos = [i for _, inf in prof for i in inf]
+    mv = [p["matvec"] for p, _ in prof]
+    cnt, tot = sum(c for c, _ in mv), sum(t for _, t in mv)
+    iters_total = sum(i["inner_iters"] for i in infos)
+    mp = 2    # one right-hand side, padded to two columns
+    peaks = _peaks()
+    if cnt < iters_total / 2:
+        # persistent launches: the event pair spans whole runs of iterations.
+        # Algorithmic bytes of one basis-less iteration: three products with
+        # A_mu (values + indices, row pointers, one vector read, one written),
+        # Omega and Omega^T as patterns, ~10 vector streams.
+        per_s = tot / 1000.0 / max(iters_total, 1)
+        bytes_ = 3 * (8.0 * len(C.vals) + 4.0 * (C.n + 1) + 2 * 4.0 * C.n * mp) \
+            + 2 * 5.0 * cfg["gamma"] * C.n + 10 * 4.0 * C.n * mp
+        kern, unit_note = "k_pcg_implicit (per iteration)", "iterations"
+    else:
+        per_s = tot / 1000.0 / max(cnt, 1)
+        bytes_ = 8.0 * len(C.vals) + 4.0 * (C.n + 1) + 2 * 4.0 * C.n * mp
+        kern, unit_note = "k_csr_mv_add", "launches"
+    roof = {"kernel": kern, "bound": "hbm", "achieved": bytes_ / per_s / 1e9,
+            "peak": peaks["hbm"], "unit": "GB/s", "frac": bytes_ / per_s / 1e9 / peaks["hbm"],
+            "traffic": None, "launches": cnt, "avg_us": per_s * 1e6, "per": unit_note,
+            "algorithmic_bytes": bytes_,
+            "note": "the working set of one iteration stays in L2 between iterations"}
+    line = _line(args, world, "RandRAND-PCG solves/s to rtol 1e-6 (sparse diffusion 512^2)",
+                 world * 1000.0 / ms, "solves/s", ms,
+                 {**{kk: cfg[kk] for kk in ("workload", "side", "n", "k", "l_sk", "mu", "rtol",
+                                            "precision", "orth")},
+                  "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
+                 latency_ms={"p50": float(np.percentile(step_ms, 50)),
+                             "p99": float(np.percentile(step_ms, 99))},
+                 solve={"inner_iters_max": max(i["inner_iters"] for i in infos),
+                        "rel_residual_max": max(i["rel_residual"] for i in infos),
+                        "ms_per_iteration": ms / max(i["inner_iters"] for i in infos)},
+                 kernels_ms_per_step={kk: sum(p[kk][1] for p, _ in prof) / args.steps
+                                      for kk in prof[0][0]},
+                 roofline=roof, clocks=clocks)
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import randrand as O
+        cop = O.CsrOp(C.rowptr, C.colidx, C.vals, C.n)
+        v = np.asarray(b, dtype=np.float64)
+        reps = 200
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            O.shifted(cop, cfg["mu"])(v)
+        t_mv = (time.perf_counter() - t0) / reps
+        iters = max(i["inner_iters"] for i in infos)
+        pps = 3 * iters + 5 * 20 + cfg["k"] + 4
+        line["cpu_baseline"] = {"value": 1.0 / (pps * t_mv), "unit": "solves/s",
+                                "cores": cpu_threads(), "kind": "oracle",
+                                "sample": f"{reps} float64 CSR products (scipy) at n=262144, "
+                                          f"{t_mv * 1e3:.2f} ms each, scaled by {pps} products "
+                                          f"per solve (3 per basis-less iteration)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm": d.get("hbm_gbs", 6800.0), "bf16": d.get("bf16_tflops", 1900.0)}
+    return {"hbm": 6800.0, "bf16": 1900.0}
+
+
+def batched_systems(rr, torch, rank):
+    from workloads import generators as W
+    cfg = BATCHED
+    rng = np.random.default_rng([cfg["seed"], 7, rank])
+    reqs, meta = [], []
+    for i in range(cfg["systems"]):
+        n = int(rng.integers(cfg["n_min"], cfg["n_max"] + 1))
+        mu = float(10.0 ** rng.uniform(-5, -2))
+        sd = cfg["seed"] * 1000 + 64 * rank + i
+        X = torch.from_numpy(W.mixture_points(n, seed=sd)).cuda()
+        B = torch.from_numpy(W.gaussian_rhs(n, cfg["nrhs"], sd)).cuda()
+        op = rr.Operator.gauss_kernel(X)
+        reqs.append(rr.Request(op, mu, n // 40, B, cfg["rtol"], seed=sd, precision="mixed"))
+        meta.append((n, mu))
+    return reqs, meta
+
+
+def run_batched(args):
+    import torch
+    rank, world, local = dist_init(args)
+    torch.cuda.set_device(local)
+    import paper_2509_19747_gb300 as rr
+    reqs, meta = batched_systems(rr, torch, rank)
+    arena = sum((q.workspace_bytes() + 255) // 256 * 256 for q in reqs)
+    # worker count: the best of a few on an untimed pass (autotune), or as given
+    cands = [args.workers] if args.workers > 0 else [4, 8, 16]
+    tune = {}
+    for w in cands:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, _ = rr.solve_batch(reqs, workers=w, arena_bytes=arena)
+        torch.cuda.synchronize()
+        tune[w] = time.perf_counter() - t0
+        if st != rr.RR_OK:
+            raise RuntimeError(f"batch failed: {rr.randrand_status_str(st)}")
+    workers = min(tune, key=tune.get)
+    for _ in range(max(args.warmup - 1, 0)):
+        rr.solve_batch(reqs, workers=workers, arena_bytes=arena)
+    smi = ClockSampler()
+    torch.cuda.synchronize()
+    barrier(world)
+    smi.start()
+    step_ms, lat = [], []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        t0 = time.perf_counter()
+        st, res = rr.solve_batch(reqs, workers=workers, arena_bytes=arena)
+        torch.cuda.synchronize()
+        e1.record()
+        e1.synchronize()
+        step_ms.append(max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3))
+        if st != rr.RR_OK:
+            raise RuntimeError(f"batch failed: {rr.randrand_status_str(st)}")
+        lat += [r["end_ms"] - r["submit_ms"] for r in res]
+    barrier(world)
+    clocks = smi.stop()
+    ms = max_over_ranks(sum(step_ms), world) / args.steps
+    # one system after another on one stream: the same systems, one worker
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rr.solve_batch(reqs, workers=1, arena_bytes=arena)
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    iters = [i["inner_iters"] for r in res for i in r["info"]]
+    line = _line(args, world, "RandRAND-PCG solves/s to rtol 1e-6 (64 batched kernel ridge systems)",
+                 world * BATCHED["systems"] * 1000.0 / ms, "solves/s", ms,
+                 {**BATCHED, "workers": workers, "parallelism": f"replicas x{world}",
+                  "l2": "inputs of the batch exceed L2"},
+                 latency_ms={"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                 one_after_another={"value": BATCHED["systems"] / seq_s, "unit": "solves/s",
+                                    "seconds": seq_s},
+                 autotune_s={str(k): v for k, v in tune.items()},
+                 solve={"inner_iters_max": max(iters), "inner_iters_median": float(np.median(iters))},
+                 roofline=None, clocks=clocks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serving_requests(rr, torch, count, rank):
+    from workloads import generators as W
+    cfg = SERVING
+    rng = np.random.default_rng([cfg["seed"], 11, rank])
+    arrivals = np.cumsum(rng.exponential(1.0 / cfg["rate_per_s"], size=count))
+    csr_ops = {}
+    reqs = []
+    for i in range(count):
+        sd = cfg["seed"] * 10000 + i
+        if rng.random() < cfg["kernel_share"]:
+            n = int(round(np.exp(rng.uniform(np.log(cfg["kernel_n"][0]), np.log(cfg["kernel_n"][1])))))
+            X = torch.from_numpy(W.mixture_points(n, seed=sd)).cuda()
+            b = torch.from_numpy(W.gaussian_rhs(n, 1, sd)[:, 0].copy()).cuda()
+            reqs.append(("kernel", n, rr.Request(rr.Operator.gauss_kernel(X), 1e-3, n // 50, b,
+                                                 cfg["rtol"], seed=sd, precision="mixed")))
+        else:
+            # grid sides on a 64-cell lattice in [128, 512]; one operator per side
+            side = int(rng.integers(2, 9)) * 64
+            if side not in csr_ops:
+                C = W.diffusion_csr(side=side, seed=cfg["seed"] + side)
+                csr_ops[side] = (C.n, rr.Operator.csr(*(torch.from_numpy(a).cuda()
+                                                        for a in (C.rowptr, C.colidx, C.vals))))
+            n, op = csr_ops[side]
+            b = torch.from_numpy(W.gaussian_rhs(n, 1, sd)[:, 0].copy()).cuda()
+            reqs.append(("csr", n, rr.Request(op, 1e-6, n // 50, b, cfg["rtol"], sketch="sparse_sign",
+                                              seed=sd, precision="mixed", orth="rand_cholqr",
+                                              maxit=100000)))
+    return arrivals, reqs
+
+
+def run_serving(args):
+    import torch
+    rank, world, local = dist_init(args)
+    torch.cuda.set_device(local)
+    import paper_2509_19747_gb300 as rr
+    arrivals, reqs = serving_requests(rr, torch, args.requests, rank)
+    budget = int(SERVING["budget_gb"] * 1e9)
+    workers = args.workers if args.workers > 0 else 16
+    srv = rr.Server(budget, workers=workers)
+    # warm-up: a few requests of each kind, untimed
+    warm = [q for _, _, q in reqs[: max(args.warmup, 1) * 2]]
+    for q in warm:
+        srv.submit(q)
+    srv.drain()
+    smi = ClockSampler()
+    barrier(world)
+    smi.start()
+    t0 = time.perf_counter()
+    tickets = []
+    for (kind, n, q), ta in zip(reqs, arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append((kind, n, srv.submit(q)))
+    srv.drain()
+    makespan = time.perf_counter() - t0
+    clocks = smi.stop()
+    res = [(kind, n, srv.poll(t)) for kind, n, t in tickets]
+    stats = srv.stats()
+    srv.close()
+    ok = [r for _, _, r in res if r["status"] == rr.RR_OK]
+    lat = [r["end_ms"] - r["submit_ms"] for _, _, r in res]
+    by_kind = {}
+    for kind, n, r in res:
+        by_kind.setdefault(kind, []).append(r["end_ms"] - r["submit_ms"])
+    value = world * len(ok) / max_over_ranks(makespan, world)
+    line = _line(args, world, "RandRAND-PCG solves/s to rtol 1e-6 (serving mix)", value, "solves/s",
+                 1000.0 * makespan / len(res),
+                 {**SERVING, "requests": len(res), "workers": workers,
+                  "parallelism": f"replicas x{world}"},
+                 latency_ms={"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                             **{f"p50_{k}": float(np.percentile(v, 50)) for k, v in by_kind.items()}},
+                 completed=len(ok), failed=len(res) - len(ok), makespan_s=makespan,
+                 offered_s=float(arrivals[-1]),
+                 overloaded=bool(makespan > 1.5 * float(arrivals[-1])),
+                 peak_arena_gb=stats["peak_bytes"] / 1e9, roofline=None, clocks=clocks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.workload != "kernel_ridge":
+        run_other(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -132,6 +132,9 @@ typedef struct {
   int32_t kernel_impl;   /* Gaussian-kernel sketch (RR_PREC_MIXED) and float32
                             products (FP32 / MIXED), dim == 8: 0 auto (tensor
                             cores), 1 float32 cores only, 2 tensor cores required */
+  int32_t iter_impl;     /* variant C with a basis: 0 auto (one persistent
+                            cooperative launch per iteration for everything
+                            after the operator product), 1 separate kernels */
   double rho;            /* C variant: <= 0 -> eq:optimal_rho with F = 1/mu     */
   double restart_eta;    /* restart after this residual reduction, default 1e-2 */
 } rr_build_opts;

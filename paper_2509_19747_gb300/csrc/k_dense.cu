@@ -266,12 +266,16 @@ void gram_upper(const double* Tm, int k, double* part, double* out, cudaStream_t
 constexpr int kNb = 32;
 
 // Factor the diagonal block A[j0:j0+jb, j0:j0+jb] and write its inverse to
-// winv (jb x jb, row-major, upper).
+// winv (jb x jb, row-major, upper).  Float64 division and square root are
+// long instruction sequences on this part, so each pivot takes one rsqrt and
+// the row is scaled by multiplication; the inverse reuses the reciprocal
+// diagonal.
 __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int k, int j0,
                                                     double* __restrict__ winv,
                                                     int* __restrict__ status) {
   __shared__ double S[kNb][kNb + 1];
   __shared__ double Wi[kNb][kNb + 1];
+  __shared__ double rd[kNb];   // 1 / R[p][p]
   const int jb = (k - j0 < kNb) ? (k - j0) : kNb;
   const int tid = threadIdx.x;
   for (int e = tid; e < jb * jb; e += blockDim.x) {
@@ -280,16 +284,16 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int 
   }
   __syncthreads();
   for (int p = 0; p < jb; ++p) {
-    // pivot
     const double app = S[p][p];
     const bool bad = !(app > 0.0) || !isfinite(app);
-    const double d = bad ? 1.0 : sqrt(app);
+    const double r = bad ? 1.0 : rsqrt(app);
     __syncthreads();
     if (tid == 0) {
       if (bad) atomicCAS(status, 0, j0 + p + 1);
-      S[p][p] = d;
+      S[p][p] = bad ? 1.0 : app * r;
+      rd[p] = r;
     }
-    for (int q = p + 1 + tid; q < jb; q += blockDim.x) S[p][q] /= d;
+    for (int q = p + 1 + tid; q < jb; q += blockDim.x) S[p][q] *= r;
     __syncthreads();
     // trailing update of the upper part: S[i][q] -= S[p][i] S[p][q], p < i <= q
     const int rem = jb - p - 1;
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int 
     for (int r = c; r >= 0; --r) {
       double s = (r == c) ? 1.0 : 0.0;
       for (int q = r + 1; q <= c; ++q) s -= S[r][q] * Wi[q][c];
-      Wi[r][c] = s / S[r][r];
+      Wi[r][c] = s * rd[r];
     }
   }
   __syncthreads();
@@ -400,15 +404,19 @@ void potrf_upper(double* A, int k, double* work, int* status, cudaStream_t st) {
 // Upper-triangular inverse, column-parallel back substitution.
 // Rt = R^T (row p of Rt = column p of R, contiguous).
 // ======================================================================
+// The reciprocal diagonal (j + 1 entries) is formed up front in shared
+// memory, so the serial chain of the substitution holds no division.
 __global__ void __launch_bounds__(128) k_trtri_cols(const double* __restrict__ Rt, int k,
                                                     double* __restrict__ Rinv) {
-  extern __shared__ double b[];  // k entries
+  extern __shared__ double b[];  // k entries, then k reciprocals
+  double* rd = b + k;
   const int j = blockIdx.x;      // column of Rinv
   const int tid = threadIdx.x;
   for (int i = tid; i < k; i += blockDim.x) b[i] = (i == j) ? 1.0 : 0.0;
+  for (int i = tid; i <= j; i += blockDim.x) rd[i] = 1.0 / Rt[(int64_t)i * k + i];
   __syncthreads();
   for (int p = j; p >= 0; --p) {
-    const double xp = b[p] / Rt[(int64_t)p * k + p];
+    const double xp = b[p] * rd[p];
     __syncthreads();
     if (tid == 0) b[p] = xp;
     // b[i] -= R[i][p] x_p for i < p; R[i][p] = Rt[p][i]
@@ -440,7 +448,10 @@ void transpose_kxk(const double* in, double* out, int k, cudaStream_t st) {
 
 void trtri_upper_with(const double* R, int k, double* Rt, double* Rinv, cudaStream_t st) {
   transpose_kxk(R, Rt, k, st);
-  k_trtri_cols<<<(unsigned)k, 128, (size_t)k * sizeof(double), st>>>(Rt, k, Rinv);
+  const size_t smem = 2 * (size_t)k * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_trtri_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_trtri_cols<<<(unsigned)k, 128, smem, st>>>(Rt, k, Rinv);
 }
 
 // ======================================================================

@@ -862,4 +862,565 @@ template void axpby<double, double, float>(const double*, Coefs8, const double*,
 template void axpby<float, float, float>(const float*, Coefs8, const float*, Coefs8, float*, int64_t, int, cudaStream_t);
 template void axpby<double, float, float>(const double*, Coefs8, const float*, Coefs8, float*, int64_t, int, cudaStream_t);
 
+// ======================================================================
+// Persistent fused PCG step (variant C with a basis), one cooperative launch
+// per iteration after the operator product w = A_mu p.  Every CTA owns a
+// contiguous block of rows and runs all of Alg. 7 steps 6-9 for them, with
+// five grid-wide barriers in place of seven kernel boundaries:
+//   A  p^T w partials                                      | barrier
+//   B  alpha; e += alpha p; r -= alpha w; |r|^2 and Q^T r   | barrier
+//      partials over the CTA's rows
+//   C  convergence decision; t = Q^T r reduced (entries     | barrier
+//      spread over the CTAs)
+//   D  s = H t (rows of H spread over the CTAs)             | barrier
+//   E  z = r + Q s for the CTA's rows; r^T z partials       | barrier
+//   F  beta; p = z + beta p
+// Every CTA reduces the per-CTA partials of a scalar itself, in the same
+// fixed order, so all CTAs take identical decisions and the results are
+// deterministic.  Reads of data written by other CTAs bypass L1 (ld.cg).
+// The barrier waits are bounded by the global timer (an error flag and an
+// early exit instead of a hang).
+// ======================================================================
+constexpr int kFT = 256;                 // threads of the fused step
+constexpr int kFusedChunk = 256;         // rows of r staged in shared memory at a time
+constexpr int kTPiece = 256;             // entries of t staged at a time in step D
+constexpr unsigned long long kBarTimeoutNs = 10ull * 1000 * 1000 * 1000;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_barrier(GridBar* gb, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned g = ld_acquire_u32(&gb->gen);
+    __threadfence();
+    const unsigned prev = atomicAdd(&gb->count, 1u);
+    if (prev == gridDim.x - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_u32(&gb->gen) == g) {
+        if (*(volatile int*)&gb->abort || global_ns() - t0 > kBarTimeoutNs) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+      if (!ok) {
+        atomicExch(&gb->abort, 1);
+        atomicExch(err, 1);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// fixed-order sum of part[g * 8 + c] over g < G by one warp (same result in every CTA)
+__device__ __forceinline__ double warp_sum_parts(const double* part, int G, int c) {
+  const int lane = threadIdx.x & 31;
+  double v = 0.0;
+  for (int g = lane; g < G; g += 32) v += __ldcg(part + (int64_t)g * 8 + c);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+struct TailArgs {
+  T* E;
+  T* R;
+  T* P;
+  T* Z;
+  const T* W;
+  const T* Q;
+  const double* H;
+  int64_t n;
+  int k;
+  int rpc;
+  double* part_pw;
+  double* part_rr;
+  double* part_rz;
+  double* part_t;
+  double* tglob;
+  double* sglob;
+  ColState* cs;
+  GridBar* bar;
+  int* err;
+};
+
+// Q^T r over the CTA's rows [r0, r0 + cnt) -> out[j][c] (float64)
+template <typename T, int MP>
+__device__ void tail_qtr(const T* __restrict__ Q, const T* __restrict__ R, int64_t r0, int cnt,
+                         int k, double* __restrict__ out, T* Rs, float* red) {
+  const int t = threadIdx.x;
+  if (sizeof(T) == 4 && (k % 4) == 0 && k / 4 <= kFT) {
+    const int nq = k >> 2, rph = kFT / nq;
+    const int q = t % nq, ph = t / nq;
+    float acc[4][MP];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < MP; ++c) acc[a][c] = 0.f;
+    for (int c0 = 0; c0 < cnt; c0 += kFusedChunk) {
+      const int cc = min(kFusedChunk, cnt - c0);
+      __syncthreads();
+      for (int e = t; e < cc * MP; e += kFT) Rs[e] = R[(r0 + c0) * MP + e];
+      __syncthreads();
+      if (ph < rph) {
+        const float4* qb = reinterpret_cast<const float4*>(Q + (r0 + c0) * k) + q;
+        const float* Rf = reinterpret_cast<const float*>(Rs);
+        int i = ph;
+        // eight rows of Q in flight per thread (memory-level parallelism with
+        // one CTA per SM)
+#pragma unroll 1
+        for (; i + 7 * rph < cc; i += 8 * rph) {
+          float4 v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = qb[(int64_t)(i + u * rph) * nq];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int c = 0; c < MP; ++c) {
+              const float r = Rf[(i + u * rph) * MP + c];
+              acc[0][c] = fmaf(v[u].x, r, acc[0][c]);
+              acc[1][c] = fmaf(v[u].y, r, acc[1][c]);
+              acc[2][c] = fmaf(v[u].z, r, acc[2][c]);
+              acc[3][c] = fmaf(v[u].w, r, acc[3][c]);
+            }
+        }
+        for (; i < cc; i += rph) {
+          const float4 v = qb[(int64_t)i * nq];
+#pragma unroll
+          for (int c = 0; c < MP; ++c) {
+            const float r = Rf[i * MP + c];
+            acc[0][c] = fmaf(v.x, r, acc[0][c]);
+            acc[1][c] = fmaf(v.y, r, acc[1][c]);
+            acc[2][c] = fmaf(v.z, r, acc[2][c]);
+            acc[3][c] = fmaf(v.w, r, acc[3][c]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (rph > 1 && ph < rph && ph > 0) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < MP; ++c) red[((ph - 1) * nq + q) * 4 * MP + a * MP + c] = acc[a][c];
+    }
+    __syncthreads();
+    if (ph == 0) {
+      for (int p2 = 1; p2 < rph; ++p2)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < MP; ++c) acc[a][c] += red[((p2 - 1) * nq + q) * 4 * MP + a * MP + c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < MP; ++c) out[(int64_t)(4 * q + a) * MP + c] = (double)acc[a][c];
+    }
+    return;
+  }
+  // general shape: one column of Q per thread
+  for (int j0 = 0; j0 < k; j0 += kFT) {
+    const int j = j0 + t;
+    T acc[MP];
+#pragma unroll
+    for (int c = 0; c < MP; ++c) acc[c] = (T)0;
+    for (int c0 = 0; c0 < cnt; c0 += kFusedChunk) {
+      const int cc = min(kFusedChunk, cnt - c0);
+      __syncthreads();
+      for (int e = t; e < cc * MP; e += kFT) Rs[e] = R[(r0 + c0) * MP + e];
+      __syncthreads();
+      if (j < k) {
+        const T* q = Q + (r0 + c0) * k + j;
+#pragma unroll 4
+        for (int i = 0; i < cc; ++i) {
+          const T qij = q[(int64_t)i * k];
+#pragma unroll
+          for (int c = 0; c < MP; ++c) acc[c] = fma(qij, Rs[i * MP + c], acc[c]);
+        }
+      }
+    }
+    if (j < k)
+#pragma unroll
+      for (int c = 0; c < MP; ++c) out[(int64_t)j * MP + c] = (double)acc[c];
+  }
+}
+
+template <typename T, int MP>
+__global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sT = reinterpret_cast<T*>(smem_raw);                         // s, column-major [MP][k]
+  T* Rs = sT + (size_t)a.k * MP;                                   // kFusedChunk x MP
+  float* red = reinterpret_cast<float*>(Rs + (size_t)kFusedChunk * MP);
+  __shared__ ColState snap[8];
+  __shared__ double sh_alpha[8], sh_beta[8];
+  __shared__ int sh_act0[8], sh_actA[8], sh_actC[8], sh_actF[8];
+  __shared__ double sh_pw[8], sh_rr[8], sh_rz[8];
+  __shared__ double redd[kFT / 32 * 8];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int G = gridDim.x, cta = blockIdx.x;
+  const int k = a.k;
+  const int64_t r0 = (int64_t)cta * a.rpc;
+  const int cnt = (int)(r0 >= a.n ? 0 : (a.n - r0 < a.rpc ? a.n - r0 : a.rpc));
+
+  if (tid < 8) {
+    if (tid < MP) snap[tid] = a.cs[tid];
+    sh_act0[tid] = (tid < MP) ? a.cs[tid].active : 0;
+  }
+  __syncthreads();
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < MP; ++c) any |= sh_act0[c] != 0;
+  if (!any) return;    // the same decision in every CTA
+
+  // ---- A: p^T w
+  double v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = 0.0;
+  for (int e = tid; e < cnt * MP; e += kFT) {
+    const int64_t g = r0 * MP + e;
+    const int c = e % MP;
+    const double x = (double)a.P[g] * (double)a.W[g];
+#pragma unroll
+    for (int cc = 0; cc < MP; ++cc)
+      if (cc == c) v[cc] += x;
+  }
+  block_sum_cols<kFT>(v, MP, redd);
+  if (tid == 0)
+    for (int c = 0; c < MP; ++c) a.part_pw[(int64_t)cta * 8 + c] = v[c];
+  if (!grid_barrier(a.bar, a.err)) return;
+
+  // ---- B: alpha, e and r, |r|^2 and Q^T r partials
+  if (wid < MP) {
+    const double pw = warp_sum_parts(a.part_pw, G, wid);
+    if (lane == 0) {
+      const int c = wid;
+      sh_pw[c] = pw;
+      int act = sh_act0[c];
+      double al = 0.0;
+      if (act) {
+        if (!(pw > 0.0 && isfinite(pw))) act = 0;
+        else al = snap[c].rho / pw;
+      }
+      sh_alpha[c] = al;
+      sh_actA[c] = act;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = 0.0;
+  for (int e = tid; e < cnt * MP; e += kFT) {
+    const int64_t g = r0 * MP + e;
+    const int c = e % MP;
+    const T al = (T)sh_alpha[c];
+    a.E[g] = fma(al, a.P[g], a.E[g]);
+    const T r = fma(-al, a.W[g], a.R[g]);
+    a.R[g] = r;
+#pragma unroll
+    for (int cc = 0; cc < MP; ++cc)
+      if (cc == c) v[cc] += (double)r * (double)r;
+  }
+  block_sum_cols<kFT>(v, MP, redd);
+  if (tid == 0)
+    for (int c = 0; c < MP; ++c) a.part_rr[(int64_t)cta * 8 + c] = v[c];
+  __syncthreads();
+  tail_qtr<T, MP>(a.Q, a.R, r0, cnt, k, a.part_t + (int64_t)cta * k * MP, Rs, red);
+  if (!grid_barrier(a.bar, a.err)) return;
+
+  // ---- C: convergence decision; t = sum of the Q^T r partials
+  if (wid < MP) {
+    const double rr = warp_sum_parts(a.part_rr, G, wid);
+    if (lane == 0) {
+      const int c = wid;
+      sh_rr[c] = rr;
+      int act = sh_actA[c];
+      if (act) {
+        const int it = snap[c].iters + 1;
+        if (!isfinite(rr) || rr <= snap[c].stop2 || it >= snap[c].budget) act = 0;
+      }
+      sh_actC[c] = act;
+    }
+  }
+  {
+    const int len = k * MP;
+    for (int e = cta * (kFT / 32) + wid; e < len; e += G * (kFT / 32)) {
+      double s = 0.0;
+      for (int g = lane; g < G; g += 32) s += __ldcg(a.part_t + (int64_t)g * len + e);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) a.tglob[e] = s;
+    }
+  }
+  if (!grid_barrier(a.bar, a.err)) return;
+
+  // ---- D: s = H t; the CTA's rows of H (j = cta, cta + G, ...), one warp per
+  // row, with t staged in shared memory in pieces of kTPiece entries
+  {
+    double* tsh = reinterpret_cast<double*>(red);   // the Q^T r scratch is free now
+    const int nrows = (k - cta + G - 1) / G;         // rows of this CTA
+    for (int rb = 0; rb < nrows; rb += kFT / 32) {
+      const int jr = rb + wid;
+      const int j = cta + jr * G;
+      double acc[MP];
+#pragma unroll
+      for (int c = 0; c < MP; ++c) acc[c] = 0.0;
+      for (int l0 = 0; l0 < k; l0 += kTPiece) {
+        const int ll = min(kTPiece, k - l0);
+        __syncthreads();
+        for (int e = tid; e < ll * MP; e += kFT) tsh[e] = __ldcg(a.tglob + (int64_t)l0 * MP + e);
+        __syncthreads();
+        if (jr < nrows) {
+          const double* hj = a.H + (int64_t)j * k + l0;
+          for (int l = lane; l < ll; l += 32) {
+            const double h = hj[l];
+#pragma unroll
+            for (int c = 0; c < MP; ++c) acc[c] = fma(h, tsh[l * MP + c], acc[c]);
+          }
+        }
+      }
+      if (jr < nrows) {
+#pragma unroll
+        for (int c = 0; c < MP; ++c) {
+          double x = acc[c];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+          if (lane == 0) a.sglob[(int64_t)j * MP + c] = x;
+        }
+      }
+    }
+  }
+  if (!grid_barrier(a.bar, a.err)) return;
+
+  // ---- E: z = r + Q s over the CTA's rows, r^T z partials
+  for (int e = tid; e < k * MP; e += kFT) {
+    const int j = e / MP, c = e % MP;
+    sT[c * k + j] = (T)__ldcg(a.sglob + e);
+  }
+  __syncthreads();
+  const int col = tr_col<MP>(lane);
+  const bool writer = tr_writer<MP>(lane);
+  double dacc = 0.0;
+  if (sizeof(T) == 4 && (k % 4) == 0) {
+    // two rows per warp step; each lane loads its quads of both rows before
+    // any arithmetic (eight 16-byte loads in flight for k <= 512)
+    const int nq = k >> 2;
+    const float4* s4 = reinterpret_cast<const float4*>(sT);
+    for (int i = 2 * wid; i < cnt; i += 2 * (kFT / 32)) {
+      const bool two = i + 1 < cnt;
+      const int64_t row0 = r0 + i, row1 = two ? row0 + 1 : row0;
+      float acc0[MP], acc1[MP];
+#pragma unroll
+      for (int c = 0; c < MP; ++c) { acc0[c] = 0.f; acc1[c] = 0.f; }
+      const float4* qa = reinterpret_cast<const float4*>(a.Q + row0 * k);
+      const float4* qb = reinterpret_cast<const float4*>(a.Q + row1 * k);
+      for (int jq0 = 0; jq0 < nq; jq0 += 128) {
+        float4 va[4], vb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int jq = jq0 + lane + 32 * u;
+          va[u] = jq < nq ? qa[jq] : make_float4(0.f, 0.f, 0.f, 0.f);
+          vb[u] = jq < nq ? qb[jq] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int jq = jq0 + lane + 32 * u;
+          if (jq < nq) {
+#pragma unroll
+            for (int c = 0; c < MP; ++c) {
+              const float4 sv = s4[c * nq + jq];
+              acc0[c] = fmaf(va[u].x, sv.x, fmaf(va[u].y, sv.y, fmaf(va[u].z, sv.z, fmaf(va[u].w, sv.w, acc0[c]))));
+              acc1[c] = fmaf(vb[u].x, sv.x, fmaf(vb[u].y, sv.y, fmaf(vb[u].z, sv.z, fmaf(vb[u].w, sv.w, acc1[c]))));
+            }
+          }
+        }
+      }
+      const float sum0 = warp_transpose_reduce<MP>(acc0, lane);
+      const float sum1 = warp_transpose_reduce<MP>(acc1, lane);
+      if (writer) {
+        const int64_t i0 = row0 * MP + col;
+        const T r = a.R[i0];
+        const T z = r + (T)sum0;
+        a.Z[i0] = z;
+        dacc += (double)r * (double)z;
+        if (two) {
+          const int64_t i1 = row1 * MP + col;
+          const T r1 = a.R[i1];
+          const T z1 = r1 + (T)sum1;
+          a.Z[i1] = z1;
+          dacc += (double)r1 * (double)z1;
+        }
+      }
+    }
+  } else {
+    for (int i = wid; i < cnt; i += kFT / 32) {
+      const int64_t row = r0 + i;
+      T acc[MP];
+#pragma unroll
+      for (int c = 0; c < MP; ++c) acc[c] = (T)0;
+      const T* q = a.Q + row * k;
+      for (int j = lane; j < k; j += 32) {
+        const T qj = q[j];
+#pragma unroll
+        for (int c = 0; c < MP; ++c) acc[c] = fma(qj, sT[c * k + j], acc[c]);
+      }
+      const T sum = warp_transpose_reduce<MP>(acc, lane);
+      if (writer) {
+        const int64_t idx = row * MP + col;
+        const T r = a.R[idx];
+        const T z = r + sum;
+        a.Z[idx] = z;
+        dacc += (double)r * (double)z;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = (c == col && writer) ? dacc : 0.0;
+  block_sum_cols<kFT>(v, MP, redd);
+  if (tid == 0)
+    for (int c = 0; c < MP; ++c) a.part_rz[(int64_t)cta * 8 + c] = v[c];
+  if (!grid_barrier(a.bar, a.err)) return;
+
+  // ---- F: beta, p = z + beta p
+  if (wid < MP) {
+    const double rz = warp_sum_parts(a.part_rz, G, wid);
+    if (lane == 0) {
+      const int c = wid;
+      sh_rz[c] = rz;
+      int act = sh_actC[c];
+      double be = snap[c].beta;
+      if (act) {
+        if (!(rz > 0.0 && isfinite(rz))) { act = 0; be = 0.0; }
+        else be = rz / snap[c].rho;
+      }
+      sh_beta[c] = be;
+      sh_actF[c] = act;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < cnt * MP; e += kFT) {
+    const int64_t g = r0 * MP + e;
+    const int c = e % MP;
+    if (sh_actF[c]) a.P[g] = fma((T)sh_beta[c], a.P[g], a.Z[g]);
+  }
+  // the new column state (nobody reads cs during this launch after the start)
+  if (cta == 0 && tid < MP) {
+    const int c = tid;
+    ColState st = snap[c];
+    st.pw = sh_pw[c];
+    st.rr = sh_rr[c];
+    if (sh_act0[c]) {
+      if (!sh_actA[c]) { st.status = RR_ERR_BREAKDOWN; st.alpha = 0.0; }
+      else st.alpha = sh_alpha[c];
+    } else {
+      st.alpha = 0.0;
+    }
+    if (sh_actA[c]) {
+      st.iters += 1;
+      if (!isfinite(sh_rr[c])) st.status = RR_ERR_BREAKDOWN;
+    }
+    if (sh_actC[c]) {
+      if (!sh_actF[c]) { st.status = RR_ERR_BREAKDOWN; st.beta = 0.0; }
+      else { st.beta = sh_beta[c]; st.rho = sh_rz[c]; }
+    }
+    st.active = sh_actF[c];
+    a.cs[c] = st;
+  }
+}
+
+template <typename T>
+size_t pcg_tail_smem(int k, int mp) {
+  size_t red = slab_red_floats(k, mp) * sizeof(float);
+  if (red < (size_t)kTPiece * mp * sizeof(double)) red = (size_t)kTPiece * mp * sizeof(double);
+  return (size_t)k * mp * sizeof(T) + (size_t)kFusedChunk * mp * sizeof(T) + red + 16;
+}
+
+// CTAs of the fused step: one per SM (at most n), or 0 when it cannot run
+template <typename T>
+int pcg_tail_ctas(int64_t n, int k, int mp) {
+  int dev = 0, sms = 0, coop = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+  if (pcg_tail_smem<T>(k, mp) + 4096 > (size_t)optin) return 0;
+  int64_t g = sms;
+  if (g > n) g = n;
+  if (g > kFusedMaxCtas) g = kFusedMaxCtas;
+  return (int)g;
+}
+
+template <typename T, int MP>
+static cudaError_t launch_tail(const TailArgs<T>& a, int G, size_t smem, cudaStream_t st) {
+  auto kern = k_pcg_tail<T, MP>;
+  if (smem > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3(kFT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <typename T>
+cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const double* H, int64_t n,
+                     int k, int mp, int G, double* scratch, ColState* cs, GridBar* bar, int* err,
+                     cudaStream_t st) {
+  TailArgs<T> a;
+  a.E = E; a.R = R; a.P = P; a.Z = Z; a.W = W; a.Q = Q; a.H = H;
+  a.n = n; a.k = k; a.rpc = (int)cdiv(n, G);
+  a.part_pw = scratch;
+  a.part_rr = a.part_pw + (size_t)kFusedMaxCtas * 8;
+  a.part_rz = a.part_rr + (size_t)kFusedMaxCtas * 8;
+  a.tglob = a.part_rz + (size_t)kFusedMaxCtas * 8;
+  a.sglob = a.tglob + (size_t)k * 8;
+  a.part_t = a.sglob + (size_t)k * 8;
+  a.cs = cs; a.bar = bar; a.err = err;
+  const size_t smem = pcg_tail_smem<T>(k, mp);
+  switch (mp) {
+    case 1: return launch_tail<T, 1>(a, G, smem, st);
+    case 2: return launch_tail<T, 2>(a, G, smem, st);
+    case 4: return launch_tail<T, 4>(a, G, smem, st);
+    default: return launch_tail<T, 8>(a, G, smem, st);
+  }
+}
+
+size_t pcg_tail_scratch_doubles(int k, int mp) {
+  return (size_t)kFusedMaxCtas * 8 * 3 + 2 * (size_t)k * 8 + (size_t)kFusedMaxCtas * k * mp;
+}
+
+template int pcg_tail_ctas<float>(int64_t, int, int);
+template int pcg_tail_ctas<double>(int64_t, int, int);
+template cudaError_t pcg_tail<float>(float*, float*, float*, float*, const float*, const float*,
+                                     const double*, int64_t, int, int, int, double*, ColState*,
+                                     GridBar*, int*, cudaStream_t);
+template cudaError_t pcg_tail<double>(double*, double*, double*, double*, const double*,
+                                      const double*, const double*, int64_t, int, int, int,
+                                      double*, ColState*, GridBar*, int*, cudaStream_t);
+
 }  // namespace rr

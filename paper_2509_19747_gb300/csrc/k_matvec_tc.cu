@@ -3,21 +3,23 @@
 //
 // K_ij = 2^(a_ij), a_ij = xs_i . xs_j + cn_i + cn_j (the exp2 form of
 // exp(-|x_i - x_j|^2 / (2 h^2)), see prepare_kernel_points).  Writing
-// u_i = [xs_i, cn_i, 1, 0...] and w_j = [xs_j, 1, cn_j, 0...] (16 floats),
-// a_ij = u_i . w_j is a K = 16 contraction.  Each vector is split into a
-// TF32 head and a TF32 tail (x = hi + lo); the three-term product
-// hi.hi + hi.lo + lo.hi (the published "3xTF32" split) gives ~float32
-// accuracy, so the CTA contracts augmented rows [u_hi u_hi u_lo] with
-// [w_hi w_lo w_hi]: K = 48, six tcgen05.mma kind::tf32 instructions.
+// u_i = [xs_i, cn_i, 1] and w_j = [xs_j, 1, cn_j] (10 floats for d = 8),
+// a_ij = u_i . w_j.  Each vector is split into a TF32 head and a TF32 tail
+// (x = hi + lo); the three-term product hi.hi + hi.lo + lo.hi (the published
+// "3xTF32" split) gives ~float32 accuracy, so the CTA contracts augmented
+// rows [u_hi u_hi u_lo 0 0] with [w_hi w_lo w_hi 0 0]: K = 32 (one 128-byte
+// swizzle atom per row), four tcgen05.mma kind::tf32 instructions.
 //
 // CTA: two blocks of 128 rows (TMEM lanes) x a range of points, in tiles of
 // 128 points; per tile the MMA writes 128 x 128 exponent arguments per row
 // block into TMEM (double-buffered: 2 row blocks x 2 buffers x 128 columns =
-// all 512 columns), and 16 epilogue warps read them with tcgen05.ld (thread =
-// row, each warp one half of the columns), apply ex2 (MUFU) and accumulate
-// w_i += K_ij v_j in registers with v_j broadcast from shared memory (LDS);
-// the two column halves of a row are merged once at the end.
-//   warp 0   TMA: augmented row blocks (once), point tiles (3 stages), and
+// all 512 columns), and 16 epilogue warps read them with tcgen05.ld.  A warp
+// serves its TMEM lane quarter in both row blocks (two rows per thread) for
+// one quarter of the tile's columns, so each v_j it loads from shared memory
+// (LDS broadcast) feeds two kernel entries; it applies ex2 (MUFU) and
+// accumulates w_i += K_ij v_j in registers.  The four column quarters of a
+// row are merged once at the end.
+//   warp 0   TMA: augmented row blocks (once), point tiles (4 stages), and
 //            the matching rows of v (bulk copy, 4 stages);
 //   warp 1   TMEM allocation; one thread issues the MMAs and commits;
 //   warps 2-17 epilogue.
@@ -36,22 +38,23 @@ using namespace tc;
 constexpr int kRows = 128;           // rows per row block (TMEM lanes)
 constexpr int kRB = 2;               // row blocks per CTA
 constexpr int kPts = 128;            // points per tile (MMA N)
-constexpr int kKf = 64;              // floats per augmented vector (48 used)
-constexpr int kKSteps = 6;           // 48 / 8 tf32 MMAs
-constexpr int kStagesB = 3;
+constexpr int kKf = kAugFloats;      // floats per augmented vector (30 used)
+static_assert(kKf == 32, "one 128-byte swizzle atom per augmented row");
+constexpr int kKSteps = kKf / 8;     // tf32 MMAs of K = 8
+constexpr int kStagesB = 4;
 constexpr int kStagesV = 4;
 constexpr int kEpiWarps = 16;          // 4 per SM sub-partition
 constexpr int kThreadsMv = 32 * (2 + kEpiWarps);
-constexpr int kAtomA = kRows * 128;  // one 32-float K atom of a row block (16 KB)
-constexpr int kAtomB = kPts * 128;   // one 32-float K atom of a point tile (16 KB)
-constexpr int kABytes = kRB * 2 * kAtomA;    // 64 KB
-constexpr int kBBytes = 2 * kAtomB;          // 32 KB per stage
+constexpr int kAtomA = kRows * 128;  // a row block (16 KB)
+constexpr int kAtomB = kPts * 128;   // a point tile (16 KB)
+constexpr int kABytes = kRB * kAtomA;        // 32 KB
+constexpr int kBBytes = kAtomB;              // 16 KB per stage
 constexpr uint32_t kTmemCols = 512;
 
 template <int MP>
 struct MvSmem {
   float v[kStagesV][kPts * MP];
-  float half[kRB * kRows][MP];   // column-half partial sums merged at the end
+  float quarter[3][kRB * kRows][MP];   // column-quarter partial sums merged at the end
   unsigned long long a_full;
   unsigned long long b_full[kStagesB], b_empty[kStagesB];
   unsigned long long v_full[kStagesV], v_empty[kStagesV];
@@ -69,7 +72,14 @@ template <int MP>
 __global__ void __launch_bounds__(kThreadsMv, 1)
     k_kernel_mv_tc(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
                    int64_t n, int64_t pts_per_split, const float* __restrict__ V,
-                   float* __restrict__ part, int* __restrict__ err) {
+                   float* __restrict__ part, int* __restrict__ err,
+                   const ColState* __restrict__ gate, int gate_mp) {
+  if (gate) {
+    // inside the Krylov iterations: nothing to do once every column is done
+    bool any = false;
+    for (int c = 0; c < gate_mp; ++c) any |= gate[c].active != 0;
+    if (!any) return;
+  }
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = base;
@@ -108,27 +118,33 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = sm->tmem_base;
-  float acc[MP];                               // epilogue warps: row partial sums
+  float acc[MP], acc1[MP];                     // epilogue warps: partial sums of two rows
+  constexpr int kP2 = MP >= 2 ? MP / 2 : 1;
+  unsigned long long acc2[kP2], acc12[kP2];     // the same as packed column pairs (MP >= 2)
 #pragma unroll
-  for (int c = 0; c < MP; ++c) acc[c] = 0.f;
+  for (int c = 0; c < MP; ++c) {
+    acc[c] = 0.f;
+    acc1[c] = 0.f;
+  }
+#pragma unroll
+  for (int c = 0; c < kP2; ++c) {
+    acc2[c] = 0ull;
+    acc12[c] = 0ull;
+  }
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0 && ntiles > 0) {
       mbar_arrive_tx(&sm->a_full, kABytes);
       for (int b = 0; b < kRB; ++b)
-        for (int a = 0; a < 2; ++a)
-          tma_load_2d(sA + (size_t)(b * 2 + a) * kAtomA, &amap, 32 * a, (int)(row0 + b * kRows),
-                      &sm->a_full);
+        tma_load_2d(sA + (size_t)b * kAtomA, &amap, 0, (int)(row0 + b * kRows), &sm->a_full);
       int issued_b = 0, issued_v = 0;
       for (int t = 0; t < ntiles; ++t) {
         const int sb = t % kStagesB, sv = t % kStagesV;
         const int64_t jt = j0 + (int64_t)t * kPts;
         if (t >= kStagesB && !mbar_wait(&sm->b_empty[sb], ((t / kStagesB) - 1) & 1, err, abort)) break;
         mbar_arrive_tx(&sm->b_full[sb], kBBytes);
-        for (int a = 0; a < 2; ++a)
-          tma_load_2d(sB + (size_t)sb * kBBytes + (size_t)a * kAtomB, &bmap, 32 * a, (int)jt,
-                      &sm->b_full[sb]);
+        tma_load_2d(sB + (size_t)sb * kBBytes, &bmap, 0, (int)jt, &sm->b_full[sb]);
         ++issued_b;
         if (t >= kStagesV && !mbar_wait(&sm->v_empty[sv], ((t / kStagesV) - 1) & 1, err, abort)) break;
         mbar_arrive_tx(&sm->v_full[sv], kVBytes);
@@ -154,13 +170,13 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
         fence_after();
         const uint32_t bbase = smem_u32(sB + (size_t)sb * kBBytes);
         for (int b = 0; b < kRB; ++b) {
-          const uint32_t abase = smem_u32(sA + (size_t)b * 2 * kAtomA);
+          const uint32_t abase = smem_u32(sA + (size_t)b * kAtomA);
           const uint32_t d = tmem + (uint32_t)(b * 256 + buf * kPts);
 #pragma unroll
           for (int kk = 0; kk < kKSteps; ++kk) {
-            const uint32_t off = (uint32_t)(kk & 3) * 32;
-            const uint64_t ad = umma_desc_sw128(abase + (kk >> 2) * kAtomA + off);
-            const uint64_t bd = umma_desc_sw128(bbase + (kk >> 2) * kAtomB + off);
+            const uint32_t off = (uint32_t)kk * 32;   // 8 tf32 values inside the atom row
+            const uint64_t ad = umma_desc_sw128(abase + off);
+            const uint64_t bd = umma_desc_sw128(bbase + off);
             mma_tf32(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
           }
         }
@@ -172,9 +188,7 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
     // ------------------------------------------------------------ epilogue
     const int e = warp - 2;                     // 0 .. 15
     const int q = warp & 3;                     // TMEM lane quarter of this warp
-    const int b = (e >> 2) & 1;                 // row block
-    const int hh = e >> 3;                      // column half of each tile
-    const int rloc = b * kRows + q * 32 + lane; // row within the CTA
+    const int cq = e >> 2;                      // column quarter of each tile
     bool ok = true;
     for (int t = 0; t < ntiles; ++t) {
       const int buf = t & 1, sv = t % kStagesV;
@@ -183,39 +197,47 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
       ok = __all_sync(0xffffffffu, ok);            // tcgen05.ld is warp-collective
       if (!ok) break;
       fence_after();
-      const uint32_t vs = smem_u32(sm->v[sv]) + (uint32_t)(hh * (kPts / 2) * MP * 4);
-      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) +
-                             (uint32_t)(b * 256 + buf * kPts + hh * (kPts / 2));
-#pragma unroll 1
-      for (int ch = 0; ch < kPts / 2 / 16; ++ch) {
-        uint32_t a[16];
-        tmem_ld16(tbase + (uint32_t)(ch * 16), a);
+      const uint32_t vs = smem_u32(sm->v[sv]) + (uint32_t)(cq * (kPts / 4) * MP * 4);
+      const uint32_t tb0 = tmem + ((uint32_t)(q * 32) << 16) +
+                           (uint32_t)(buf * kPts + cq * (kPts / 4));
+#pragma unroll
+      for (int ch = 0; ch < kPts / 4 / 16; ++ch) {
+        uint32_t ra[16], rb[16];
+        tmem_ld16_nowait(tb0 + (uint32_t)(ch * 16), ra);          // row block 0
+        tmem_ld16_nowait(tb0 + 256u + (uint32_t)(ch * 16), rb);   // row block 1
+        tmem_wait_ld();
+        reg_fence16(ra);
+        reg_fence16(rb);
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
-          const float kij = ex2_approx(__uint_as_float(a[u]));
+          const float k0 = ex2_approx(__uint_as_float(ra[u]));
+          const float k1 = ex2_approx(__uint_as_float(rb[u]));
           const uint32_t vj = vs + (uint32_t)((ch * 16 + u) * MP * 4);
-          if (MP == 4) {
-            const float4 v4 = lds128(vj);
-            acc[0] = fmaf(kij, v4.x, acc[0]);
-            acc[1 % MP] = fmaf(kij, v4.y, acc[1 % MP]);
-            acc[2 % MP] = fmaf(kij, v4.z, acc[2 % MP]);
-            acc[3 % MP] = fmaf(kij, v4.w, acc[3 % MP]);
-          } else if (MP == 8) {
-            const float4 v4 = lds128(vj), w4 = lds128(vj + 16);
-            acc[0] = fmaf(kij, v4.x, acc[0]);
-            acc[1 % MP] = fmaf(kij, v4.y, acc[1 % MP]);
-            acc[2 % MP] = fmaf(kij, v4.z, acc[2 % MP]);
-            acc[3 % MP] = fmaf(kij, v4.w, acc[3 % MP]);
-            acc[4 % MP] = fmaf(kij, w4.x, acc[4 % MP]);
-            acc[5 % MP] = fmaf(kij, w4.y, acc[5 % MP]);
-            acc[6 % MP] = fmaf(kij, w4.z, acc[6 % MP]);
-            acc[7 % MP] = fmaf(kij, w4.w, acc[7 % MP]);
-          } else if (MP == 2) {
-            const float2 v2 = lds64(vj);
-            acc[0] = fmaf(kij, v2.x, acc[0]);
-            acc[1 % MP] = fmaf(kij, v2.y, acc[1 % MP]);
+          if (MP >= 2) {
+            // packed pair FMAs: the accumulators of columns (2c, 2c+1) share
+            // one fma.rn.f32x2 with the entry broadcast to both halves
+            const unsigned long long kk0 = pk2(k0, k0), kk1 = pk2(k1, k1);
+#pragma unroll
+            for (int c2 = 0; c2 < MP / 2; c2 += 2) {
+              unsigned long long va, vb = 0;
+              if (MP == 2) {
+                va = lds64u(vj);
+              } else {
+                const ulonglong2 v = lds128u(vj + (uint32_t)(c2 * 8));
+                va = v.x;
+                vb = v.y;
+              }
+              ffma2(acc2[c2], kk0, va);
+              ffma2(acc12[c2], kk1, va);
+              if (MP > 2) {
+                ffma2(acc2[c2 + 1], kk0, vb);
+                ffma2(acc12[c2 + 1], kk1, vb);
+              }
+            }
           } else {
-            acc[0] = fmaf(kij, lds32(vj), acc[0]);
+            const float v1 = lds32(vj);
+            acc[0] = fmaf(k0, v1, acc[0]);
+            acc1[0] = fmaf(k1, v1, acc1[0]);
           }
         }
       }
@@ -226,9 +248,23 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
         mbar_arrive(&sm->v_empty[sv]);
       }
     }
-    if (hh == 1) {
+    if (MP >= 2) {
 #pragma unroll
-      for (int c = 0; c < MP; ++c) sm->half[rloc][c] = ok ? acc[c] : 0.f;
+      for (int c = 0; c < kP2; ++c) {
+        const float2 a0 = upk2(acc2[c]), a1 = upk2(acc12[c]);
+        acc[(2 * c) % MP] = a0.x;
+        acc[(2 * c + 1) % MP] = a0.y;
+        acc1[(2 * c) % MP] = a1.x;
+        acc1[(2 * c + 1) % MP] = a1.y;
+      }
+    }
+    if (cq > 0) {
+      const int r = q * 32 + lane;
+#pragma unroll
+      for (int c = 0; c < MP; ++c) {
+        sm->quarter[cq - 1][r][c] = ok ? acc[c] : 0.f;
+        sm->quarter[cq - 1][kRows + r][c] = ok ? acc1[c] : 0.f;
+      }
     }
   }
   fence_before();
@@ -237,20 +273,24 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
     fence_after();
     tmem_dealloc(tmem, kTmemCols);
   }
-  // merge the two column halves of every row and write the split's partial
-  if (warp >= 2 && ((warp - 2) >> 3) == 0 && !*abort) {
-    const int e = warp - 2;
-    const int rloc = ((e >> 2) & 1) * kRows + (warp & 3) * 32 + lane;
-    const int64_t gi = row0 + rloc;
-    if (gi < n) {
-      float* out = part + ((int64_t)blockIdx.y * n + gi) * MP;
+  // merge the four column quarters of every row and write the split's partial
+  if (warp >= 2 && ((warp - 2) >> 2) == 0 && !*abort) {
+    const int r = (warp & 3) * 32 + lane;
 #pragma unroll
-      for (int c = 0; c < MP; ++c) out[c] = acc[c] + sm->half[rloc][c];
+    for (int b = 0; b < kRB; ++b) {
+      const int64_t gi = row0 + b * kRows + r;
+      if (gi < n) {
+        float* out = part + ((int64_t)blockIdx.y * n + gi) * MP;
+#pragma unroll
+        for (int c = 0; c < MP; ++c)
+          out[c] = (b == 0 ? acc[c] : acc1[c]) + sm->quarter[0][b * kRows + r][c] +
+                   sm->quarter[1][b * kRows + r][c] + sm->quarter[2][b * kRows + r][c];
+      }
     }
   }
 }
 
-// augmented TF32-split vectors: A rows [u_hi u_hi u_lo 0], B rows [w_hi w_lo w_hi 0]
+// augmented TF32-split vectors: A rows [u_hi u_hi u_lo 0 0], B rows [w_hi w_lo w_hi 0 0]
 __device__ __forceinline__ float tf32_head(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -261,9 +301,10 @@ __global__ void k_prep_aug(const float* __restrict__ xs, const float* __restrict
                            int64_t npad, float* __restrict__ A, float* __restrict__ B) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npad) return;
-  float u[16], w[16];
+  constexpr int kU = 10;            // 8 coordinates, cn, 1
+  float u[kU], w[kU];
 #pragma unroll
-  for (int d = 0; d < 16; ++d) { u[d] = 0.f; w[d] = 0.f; }
+  for (int d = 0; d < kU; ++d) { u[d] = 0.f; w[d] = 0.f; }
   if (i < n) {
 #pragma unroll
     for (int d = 0; d < 8; ++d) { u[d] = xs[i * 8 + d]; w[d] = u[d]; }
@@ -278,12 +319,14 @@ __global__ void k_prep_aug(const float* __restrict__ xs, const float* __restrict
   float* ar = A + i * kKf;
   float* br = B + i * kKf;
 #pragma unroll
-  for (int d = 0; d < 16; ++d) {
+  for (int d = 0; d < kU; ++d) {
     const float uh = tf32_head(u[d]), ul = u[d] - uh;
     const float wh = tf32_head(w[d]), wl = w[d] - wh;
-    ar[d] = uh; ar[16 + d] = uh; ar[32 + d] = ul; ar[48 + d] = 0.f;
-    br[d] = wh; br[16 + d] = wl; br[32 + d] = wh; br[48 + d] = 0.f;
+    ar[d] = uh; ar[kU + d] = uh; ar[2 * kU + d] = ul;
+    br[d] = wh; br[kU + d] = wl; br[2 * kU + d] = wh;
   }
+#pragma unroll
+  for (int d = 3 * kU; d < kKf; ++d) { ar[d] = 0.f; br[d] = 0.f; }
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -355,7 +398,8 @@ int mv_tc_nsplit(int64_t n) {
 // part[s][i][c] = sum_{j in split s} K_ij V[j][c]; V must have mv_tc_pad(n)
 // rows (zero beyond n).  Returns false if the kernel cannot be launched.
 bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const float* V,
-                  float* part, int nsplit, int* err, cudaStream_t st) {
+                  float* part, int nsplit, int* err, const ColState* gate, int gate_mp,
+                  cudaStream_t st) {
   const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
   const int64_t tiles = cdiv(n, kPts);
   const int64_t pps = cdiv(tiles, nsplit) * kPts;
@@ -365,19 +409,19 @@ bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const f
   switch (mp) {
     case 1:
       if (!set_attr<1>()) return false;
-      k_kernel_mv_tc<1><<<grid, kThreadsMv, mv_smem_bytes<1>(), st>>>(am, bm, n, pps, V, part, err);
+      k_kernel_mv_tc<1><<<grid, kThreadsMv, mv_smem_bytes<1>(), st>>>(am, bm, n, pps, V, part, err, gate, gate_mp);
       break;
     case 2:
       if (!set_attr<2>()) return false;
-      k_kernel_mv_tc<2><<<grid, kThreadsMv, mv_smem_bytes<2>(), st>>>(am, bm, n, pps, V, part, err);
+      k_kernel_mv_tc<2><<<grid, kThreadsMv, mv_smem_bytes<2>(), st>>>(am, bm, n, pps, V, part, err, gate, gate_mp);
       break;
     case 4:
       if (!set_attr<4>()) return false;
-      k_kernel_mv_tc<4><<<grid, kThreadsMv, mv_smem_bytes<4>(), st>>>(am, bm, n, pps, V, part, err);
+      k_kernel_mv_tc<4><<<grid, kThreadsMv, mv_smem_bytes<4>(), st>>>(am, bm, n, pps, V, part, err, gate, gate_mp);
       break;
     default:
       if (!set_attr<8>()) return false;
-      k_kernel_mv_tc<8><<<grid, kThreadsMv, mv_smem_bytes<8>(), st>>>(am, bm, n, pps, V, part, err);
+      k_kernel_mv_tc<8><<<grid, kThreadsMv, mv_smem_bytes<8>(), st>>>(am, bm, n, pps, V, part, err, gate, gate_mp);
       break;
   }
   return cudaGetLastError() == cudaSuccess;

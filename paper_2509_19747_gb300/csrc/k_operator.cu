@@ -428,7 +428,13 @@ __global__ void k_point_norms(const float* __restrict__ x, int64_t n, int dim,
 
 template <typename T>
 __global__ void k_sum_splits(const T* __restrict__ part, int nsplit, int64_t n, int mp,
-                             double mu, const T* __restrict__ V, T* __restrict__ W) {
+                             double mu, const T* __restrict__ V, T* __restrict__ W,
+                             const ColState* __restrict__ gate = nullptr, int gate_mp = 0) {
+  if (gate) {
+    bool any = false;
+    for (int c = 0; c < gate_mp; ++c) any |= gate[c].active != 0;
+    if (!any) return;
+  }
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * mp) return;
   T acc = (T)0;
@@ -464,9 +470,10 @@ void kernel_mv<float>(const OpDev& op, double mu, const float* V, float* W, int 
   if (op.use_tc) {
     const int nt = mv_tc_nsplit(op.n);
     rec(ev, 0, st);
-    if (kernel_mv_tc(op.amap, op.bmap, op.n, mp, V, part, nt, op.tc_err, st)) {
+    if (kernel_mv_tc(op.amap, op.bmap, op.n, mp, V, part, nt, op.tc_err, op.gate, op.gate_mp, st)) {
       rec(ev, 1, st);
-      k_sum_splits<float><<<(unsigned)cdiv(op.n * mp, 256), 256, 0, st>>>(part, nt, op.n, mp, mu, V, W);
+      k_sum_splits<float><<<(unsigned)cdiv(op.n * mp, 256), 256, 0, st>>>(part, nt, op.n, mp, mu, V, W,
+                                                                          op.gate, op.gate_mp);
       return;
     }
   }

@@ -22,12 +22,14 @@ namespace {
 constexpr int kKK = 16;           // k x k float64 work matrices
 constexpr int kMaxGammaHost = 16; // sparse-sign nonzeros per row, at most
 constexpr int kChunk = 8;         // Krylov iterations per captured graph
+constexpr int kImplicitChunk = 256;  // iterations per persistent basis-less launch
+                                     // (it stops by itself once every column is done)
 constexpr int kMaxRestarts = 400;
 
 enum Region {
   R_OM, R_OMB, R_SSC, R_SSS, R_THC, R_THS, R_SK, R_Y, R_Q, R_KK, R_KKT, R_GPART, R_CHOLW,
   R_STATUS, R_XS, R_CN, R_PN, R_AUG, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT,
-  R_CS, R_NORMS, R_NREG
+  R_CS, R_NORMS, R_FUSED, R_NREG
 };
 
 struct Layout {
@@ -85,9 +87,10 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_XS] = (A.kind == RR_OP_GAUSS_KERNEL) ? npts * (size_t)A.dim * 4 : 0;
   L.size[R_CN] = (A.kind == RR_OP_GAUSS_KERNEL) ? npts * 4 : 0;
   L.size[R_PN] = (A.kind == RR_OP_GAUSS_KERNEL) ? n * 8 : 0;
-  // tensor-core product: two augmented arrays of 64 floats per (padded) point
+  // tensor-core product: two augmented arrays of kAugFloats floats per (padded) point
   const size_t npad_tc = (size_t)mv_tc_pad(A.n);
-  L.size[R_AUG] = (A.kind == RR_OP_GAUSS_KERNEL && A.dim == 8 && !uses_f64(o)) ? 2 * npad_tc * 64 * 4 : 0;
+  L.size[R_AUG] = (A.kind == RR_OP_GAUSS_KERNEL && A.dim == 8 && !uses_f64(o))
+                      ? 2 * npad_tc * kAugFloats * 4 : 0;
   L.size[R_MVS] = op_matvec_scratch_elems(od, mp) * 8;
   // Krylov vectors carry zero rows up to the tensor-core tile multiple
   L.size[R_VT] = 7 * (size_t)mv_tc_pad(A.n) * (size_t)mp * ts;
@@ -99,6 +102,11 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_CNT] = 64 * 4;
   L.size[R_CS] = 8 * sizeof(ColState);
   L.size[R_NORMS] = 64 * 8;
+  // persistent fused steps of variant C: barrier + partials
+  L.size[R_FUSED] = (o.variant == RR_VARIANT_C)
+                        ? 256 + std::max(pcg_tail_scratch_doubles(k, mp),
+                                         pcg_implicit_scratch_doubles(k, mp)) * 8
+                        : 0;
   size_t off = 0;
   for (int r = 0; r < R_NREG; ++r) {
     L.off[r] = off;
@@ -112,6 +120,8 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
   if (!A) return RR_ERR_INVALID_ARG;
   if (A->n < 1 || A->n > (int64_t)INT32_MAX) return RR_ERR_INVALID_ARG;
   if (k < 1 || (int64_t)k > A->n) return RR_ERR_INVALID_ARG;
+  // the triangular inverse stages 2 k float64 values per CTA in shared memory
+  if (k > 14000) return RR_ERR_UNSUPPORTED;
   if (o.max_rhs < 1 || o.max_rhs > 8) return RR_ERR_INVALID_ARG;
   if (o.variant != RR_VARIANT_C && o.variant != RR_VARIANT_R) return RR_ERR_INVALID_ARG;
   if (o.precision < RR_PREC_FP64 || o.precision > RR_PREC_MIXED) return RR_ERR_INVALID_ARG;
@@ -130,6 +140,7 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
     }
   }
   if (o.power_iters < 1 || o.power_iters > 1000) return RR_ERR_INVALID_ARG;
+  if (o.iter_impl < 0 || o.iter_impl > 1) return RR_ERR_INVALID_ARG;
   if (!(o.restart_eta > 0.0 && o.restart_eta < 1.0)) return RR_ERR_INVALID_ARG;
   switch (A->kind) {
     case RR_OP_DENSE:
@@ -209,6 +220,10 @@ struct rr_handle {
   double* S2;
   int lsk;
   bool implicit;      // basis-less: Q applied through A_mu, Omega and R^-1
+  int fusedG;         // CTAs of the persistent fused step (0: separate kernels)
+  GridBar* bar;
+  double* fscratch;
+  bool graph_failed;  // capture not possible: direct launches
   void* Y;
   void* Q;
   void* QH;
@@ -298,7 +313,7 @@ void carve(rr_handle* h) {
   for (int i = 0; i < 7; ++i) h->V[i] = vb + i * vecp * ts;
   float* aug = (float*)at(R_AUG);
   h->op.aug_a = aug;
-  h->op.aug_b = aug ? aug + (size_t)mv_tc_pad(h->n) * 64 : nullptr;
+  h->op.aug_b = aug ? aug + (size_t)mv_tc_pad(h->n) * kAugFloats : nullptr;
   double* v64 = (double*)at(R_V64);
   for (int i = 0; i < 4; ++i) h->v64[i] = v64 + i * vec;
   double* stg = (double*)at(R_STAGE);
@@ -311,6 +326,9 @@ void carve(rr_handle* h) {
   h->cnt = (unsigned*)at(R_CNT);
   h->cs = (ColState*)at(R_CS);
   h->norms = (double*)at(R_NORMS);
+  unsigned char* fz = (unsigned char*)at(R_FUSED);
+  h->bar = (GridBar*)fz;
+  h->fscratch = fz ? (double*)(fz + 256) : nullptr;
 }
 
 // a pair of timing events for one launch of category `cat` (nullptr when the
@@ -852,16 +870,46 @@ rr_status build_impl(rr_handle* h) {
     // Hb = R^-1 (tau G - I) R^-T = tau Gb - Cinv
     axpby<double, double, double>(h->kk[kGb], coefs_all(h->tau), h->kk[kCinv], coefs_all(-1.0),
                                   h->kk[kHb], (int64_t)k * k, 1, st);
+    h->fusedG = (h->o.iter_impl == 0 && h->sketch == RR_SKETCH_SPARSE_SIGN)
+                    ? pcg_implicit_ctas<T>(n, k, h->mp) : 0;
+    if (h->fusedG > 0) RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), st));
   } else if (h->o.variant == RR_VARIANT_C) {
-    // P = I + Q (tau G - I) Q^T; keep QH = Q H so that z = r + QH (Q^T r)
+    // P = I + Q (tau G - I) Q^T = I + Q H Q^T
     form_H(h->kk[kG], h->tau, h->kk[kH], k, st);
-    h->QH = h->Y;
-    right_mult<T>(h, (const T*)h->Q, h->kk[kH], (T*)h->QH);
+    h->fusedG = (h->o.iter_impl == 0) ? pcg_tail_ctas<T>(n, k, h->mp) : 0;
+    if (h->fusedG > 0) {
+      // the fused step applies H to the k x m vector Q^T r and reads Q twice
+      // per iteration (one n x k matrix stays resident in L2)
+      RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), st));
+      h->QH = nullptr;
+    } else {
+      // separate kernels: keep QH = Q H so that z = r + QH (Q^T r)
+      h->QH = h->Y;
+      right_mult<T>(h, (const T*)h->Q, h->kk[kH], (T*)h->QH);
+    }
   }
   return sync_status(h);
 }
 
 // ------------------------------------------------------------------ solve
+// z = P r = r + Q (H (Q^T r)) (variant C with a basis), last block applies
+// `mode` to r^T z.  With QH = Q H formed at build the k x k product is folded
+// into the basis.
+template <typename T>
+void precond_C(rr_handle* h, const T* Rv, T* Zv, int mode) {
+  const int64_t n = h->n;
+  const int mp = h->mp, k = h->k;
+  qt<T>(h, Rv, h->t[0], false);
+  if (h->QH) {
+    qcomb<T>((const T*)h->QH, n, k, mp, h->t[0], coefs_all(1.0), Rv, Zv, Rv, mode, h->rpart,
+             h->cnt, h->cs, false, h->st);
+  } else {
+    kxk_apply(h->kk[kH], h->t[0], k, mp, coefs_all(0.0), coefs_all(1.0), h->t[1], h->st);
+    qcomb<T>((const T*)h->Q, n, k, mp, h->t[1], coefs_all(1.0), Rv, Zv, Rv, mode, h->rpart,
+             h->cnt, h->cs, false, h->st);
+  }
+}
+
 template <typename T>
 void iter_C(rr_handle* h, const cudaEvent_t* ev) {
   const int64_t n = h->n;
@@ -869,6 +917,12 @@ void iter_C(rr_handle* h, const cudaEvent_t* ev) {
   T *Rv = vt<T>(h, kR), *Pv = vt<T>(h, kP), *Wv = vt<T>(h, kW), *Zv = vt<T>(h, kZ),
     *Ev = vt<T>(h, kE);
   matvec<T>(h, Pv, Wv, ev);                                               // w = A_mu p
+  if (h->fusedG > 0) {
+    // Alg. 7 steps 6-9 in one persistent cooperative launch
+    pcg_tail<T>(Ev, Rv, Pv, Zv, Wv, (const T*)h->Q, h->kk[kH], n, k, mp, h->fusedG, h->fscratch,
+                h->cs, h->bar, h->dstatus + 3, h->st);
+    return;
+  }
   dot_cols<T>(Pv, Wv, n, mp, kModeAlpha, h->rpart, h->cnt, h->cs, true, nullptr, h->st);
   update_qt<T>(Ev, Rv, Pv, Wv, (const T*)h->Q, n, k, mp, h->tpart, h->rpart, h->cnt, h->cs, h->st);
   reduce_slabs_gated(h->tpart, qt_nslab(n), k * mp, h->t[0], h->cs, mp, h->st);  // t = Q^T r
@@ -897,9 +951,13 @@ void iter_R(rr_handle* h, const cudaEvent_t* ev);
 
 template <typename T>
 void iter_any(rr_handle* h, const cudaEvent_t* ev) {
+  // the kernel-operator products skip their work once every column is done
+  h->op.gate = h->cs;
+  h->op.gate_mp = h->mp;
   if (h->implicit) iter_C_implicit<T>(h, ev);
   else if (h->o.variant == RR_VARIANT_C) iter_C<T>(h, ev);
   else iter_R<T>(h, ev);
+  h->op.gate = nullptr;
 }
 
 template <typename T>
@@ -930,12 +988,24 @@ void iter_R(rr_handle* h, const cudaEvent_t* ev) {
 
 template <typename T>
 rr_status run_chunk(rr_handle* h) {
+  if (h->implicit && h->fusedG > 0) {
+    // one persistent launch iterates until every column is done (or the chunk ends)
+    const cudaEvent_t* ev = ev_take(h, RR_PROF_MATVEC);
+    if (ev) RR_CUDA_TRY(cudaEventRecord(ev[0], h->st));
+    RR_CUDA_TRY(pcg_implicit<T>(h->op, h->mu, h->ss_cols, h->ss_sgn, h->o.gamma, h->kk[kHb],
+                                vt<T>(h, kE), vt<T>(h, kR), vt<T>(h, kP), vt<T>(h, kW),
+                                vt<T>(h, kZ), vt<T>(h, kU), h->k, h->mp, h->fusedG, kImplicitChunk,
+                                h->fscratch,
+                                h->cs, h->bar, h->dstatus + 3, h->st));
+    if (ev) RR_CUDA_TRY(cudaEventRecord(ev[1], h->st));
+    return RR_OK;
+  }
   // the legacy default stream cannot be captured; a profiled handle whose
-  // captured event records gave no timings launches directly as well
-  if (h->st == nullptr || h->st == cudaStreamLegacy || (h->prof && h->graph_prof_broken)) {
-    for (int i = 0; i < kChunk; ++i) {
-      iter_any<T>(h, ev_take(h, RR_PROF_MATVEC));
-    }
+  // captured event records gave no timings, or a handle whose capture failed,
+  // launches directly as well
+  if (h->st == nullptr || h->st == cudaStreamLegacy || (h->prof && h->graph_prof_broken) ||
+      h->graph_failed) {
+    for (int i = 0; i < kChunk; ++i) iter_any<T>(h, ev_take(h, RR_PROF_MATVEC));
     RR_CUDA_TRY(cudaGetLastError());
     return RR_OK;
   }
@@ -944,14 +1014,18 @@ rr_status run_chunk(rr_handle* h) {
     // pointers and scalars (tau is fixed at build)
     cudaGraph_t g = nullptr;
     RR_CUDA_TRY(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < kChunk; ++i) {
-      iter_any<T>(h, h->prof ? h->ev_graph[i].e : nullptr);
-    }
+    for (int i = 0; i < kChunk; ++i) iter_any<T>(h, h->prof ? h->ev_graph[i].e : nullptr);
     cudaError_t e = cudaStreamEndCapture(h->st, &g);
-    if (e != cudaSuccess || !g) return RR_ERR_CUDA;
-    e = cudaGraphInstantiate(&h->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return RR_ERR_CUDA;
+    if (e == cudaSuccess && g) {
+      e = cudaGraphInstantiate(&h->graph, g, 0);
+      cudaGraphDestroy(g);
+    }
+    if (e != cudaSuccess || !g) {
+      // nothing of the failed capture ran; iterate with direct launches
+      cudaGetLastError();
+      h->graph_failed = true;
+      return run_chunk<T>(h);
+    }
     h->graph_ok = true;
   }
   RR_CUDA_TRY(cudaGraphLaunch(h->graph, h->st));
@@ -1071,9 +1145,7 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
       p_update<T>(vt<T>(h, kP), vt<T>(h, kZ), n, mp, h->cs, true, st);
     } else if (h->o.variant == RR_VARIANT_C) {
       // z = P r, p = z, rho = r^T z
-      qt<T>(h, Rv, h->t[0], false);
-      qcomb<T>((const T*)h->QH, n, h->k, mp, h->t[0], coefs_all(1.0), Rv, vt<T>(h, kZ), Rv,
-               kModeRhoInit, h->rpart, h->cnt, h->cs, false, st);
+      precond_C<T>(h, Rv, vt<T>(h, kZ), kModeRhoInit);
       p_update<T>(vt<T>(h, kP), vt<T>(h, kZ), n, mp, h->cs, true, st);
     } else {
       p_update<T>(vt<T>(h, kP), Rv, n, mp, h->cs, true, st);
@@ -1099,10 +1171,12 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
     axpby<double, T, double>(X, coefs_all(1.0), Ev, coefs_all(1.0), X, n, mp, st);
   }
   RR_TRY(sync_status(h));
-  if (h->op.use_tc) {
-    int err = 0;
-    RR_TRY(read_int(h, h->dstatus + 2, &err));
-    if (err) return RR_ERR_TIMEOUT;
+  if (h->op.use_tc || h->fusedG > 0) {
+    int err[2] = {0, 0};
+    RR_CUDA_TRY(cudaMemcpyAsync(h->norms_host, h->dstatus + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    RR_TRY(sync_status(h));
+    memcpy(err, h->norms_host, sizeof(err));
+    if (err[0] || err[1]) return RR_ERR_TIMEOUT;
   }
   rr_status worst = RR_OK;
   for (int c = 0; c < m; ++c) {
@@ -1143,9 +1217,7 @@ void apply_impl(rr_handle* h) {
   if (h->implicit) {
     precond_implicit<T>(h, Rv, Zv, false, nullptr);
   } else if (h->o.variant == RR_VARIANT_C) {
-    qt<T>(h, Rv, h->t[0], false);
-    qcomb<T>((const T*)h->QH, n, k, mp, h->t[0], coefs_all(1.0), Rv, Zv, nullptr, kModeNone,
-             h->rpart, h->cnt, h->cs, false, h->st);
+    precond_C<T>(h, Rv, Zv, kModeNone);
   } else {
     const T* Q = (const T*)h->Q;
     qt<T>(h, Rv, h->t[0], false);
@@ -1185,6 +1257,7 @@ void rr_build_opts_default(rr_build_opts* o) {
   o->restart_eta = 1e-2;
   o->profile = 0;
   o->kernel_impl = 0;
+  o->iter_impl = 0;
 }
 
 const char* randrand_status_str(rr_status s) {
@@ -1257,6 +1330,8 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
   h->gsplit = gram_nsplit(A->n, k, k);
   h->lsk = uses_alg3(o) ? sketch_rows(k, o) : 0;
   h->implicit = basis_less(*A, o);
+  h->fusedG = 0;
+  h->graph_failed = false;
   h->graph_ok = false;
   h->graph = nullptr;
   h->prof = o.profile != 0;

@@ -29,6 +29,22 @@ constexpr int kSmSlabs = 304;      // row slabs of the tall-skinny reductions (2
 
 // ---------------------------------------------------------------- operator
 // Device view of the operator plus the preprocessed kernel points.
+// Per right-hand-side Krylov scalars, device resident.
+struct ColState {
+  double rho;     // r^T z (C) or r^T r (R)
+  double alpha;
+  double beta;
+  double rr;      // |r|^2 of the recursive residual
+  double stop2;   // inner stop threshold squared
+  double pw;      // p^T A p (C) or p^T B p (R)
+  double lam;     // power-iteration norm
+  double pad;
+  int active;     // 1 while the inner solve runs on this column
+  int iters;      // inner iterations of the current restart
+  int budget;     // iteration budget of the current restart
+  int status;     // RR_OK or RR_ERR_BREAKDOWN
+};
+
 struct OpDev {
   int kind;
   int dtype;          // 0 f64, 1 f32 (dense / csr values)
@@ -58,6 +74,10 @@ struct OpDev {
   const void* amap;
   const void* bmap;
   int* tc_err;
+  // when set (inside the Krylov iterations), the product kernels of the
+  // kernel operator return at once if no column of gate[0..gate_mp) is active
+  const ColState* gate;
+  int gate_mp;
 };
 
 // One-time host setup per device (function attributes): bit d of `mask` is
@@ -79,21 +99,6 @@ struct Coefs8s {
   double v[8];
 };
 
-// Per right-hand-side Krylov scalars, device resident.
-struct ColState {
-  double rho;     // r^T z (C) or r^T r (R)
-  double alpha;
-  double beta;
-  double rr;      // |r|^2 of the recursive residual
-  double stop2;   // inner stop threshold squared
-  double pw;      // p^T A p (C) or p^T B p (R)
-  double lam;     // power-iteration norm
-  double pad;
-  int active;     // 1 while the inner solve runs on this column
-  int iters;      // inner iterations of the current restart
-  int budget;     // iteration budget of the current restart
-  int status;     // RR_OK or RR_ERR_BREAKDOWN
-};
 
 // ------------------------------------------------------------ launchers
 // k_rng.cu
@@ -168,11 +173,14 @@ void csr_sketch_sparse(const OpDev& op, double mu, const int32_t* cols, const in
 
 // k_matvec_tc.cu -- tensor-core float32 Gaussian-kernel product
 int64_t mv_tc_pad(int64_t n);
+// floats per point in each augmented TF32-split array (k_matvec_tc.cu)
+constexpr int kAugFloats = 32;
 void prepare_mv_tc(const OpDev& op, float* Aaug, float* Baug, cudaStream_t st);
 bool encode_mv_tc(const float* Aaug, const float* Baug, int64_t n, void* amap, void* bmap);
 int mv_tc_nsplit(int64_t n);
 bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const float* V,
-                  float* part, int nsplit, int* err, cudaStream_t st);
+                  float* part, int nsplit, int* err, const ColState* gate, int gate_mp,
+                  cudaStream_t st);
 
 // k_sketch_tc.cu -- tensor-core sketch of the Gaussian-kernel operator
 size_t sketch_tc_smem_bytes();

@@ -64,4 +64,31 @@ void restart_init(ColState* cs, int mp, const RestartParams& p, cudaStream_t st)
 
 constexpr int kMaxReduceBlocks = 8 * 152;  // upper bound on CTAs of the fused reductions
 
+// grid-wide barrier state of the persistent fused step (zero-initialised)
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+  int abort;
+  int pad;
+};
+constexpr int kFusedMaxCtas = 2 * 152;
+// Persistent fused PCG step (variant C with a basis): see k_krylov.cu.
+template <typename T>
+int pcg_tail_ctas(int64_t n, int k, int mp);
+size_t pcg_tail_scratch_doubles(int k, int mp);
+template <typename T>
+cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const double* H, int64_t n,
+                     int k, int mp, int G, double* scratch, ColState* cs, GridBar* bar, int* err,
+                     cudaStream_t st);
+// Persistent basis-less PCG for CSR operators with a sparse-sign Omega
+// (k_implicit_fused.cu): `iters` iterations in one cooperative launch.
+size_t pcg_implicit_scratch_doubles(int k, int mp);
+template <typename T>
+int pcg_implicit_ctas(int64_t n, int k, int mp);
+template <typename T>
+cudaError_t pcg_implicit(const OpDev& op, double mu, const int32_t* om_cols, const int8_t* om_sgn,
+                         int gamma, const double* Hb, T* E, T* R, T* P, T* W, T* Z, T* U, int k,
+                         int mp, int G, int iters, double* scratch, ColState* cs, GridBar* bar,
+                         int* err, cudaStream_t st);
+
 }  // namespace rr

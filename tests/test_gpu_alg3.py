@@ -169,3 +169,28 @@ def test_sparse_operator_full_size(cuda_lib):
     res = O.true_rel_residual(op, mu, x.cpu().numpy(), b)
     assert res[0] <= 1e-6
     assert infos[0]["rel_residual"] == pytest.approx(res[0], rel=1e-3)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_persistent_basis_less_matches_separate_kernels(cuda_lib, precision):
+    """The persistent basis-less iteration (iter_impl 0) and the separate
+    kernels (iter_impl 1) agree: float64 iterates to 1e-10 at a fixed budget,
+    and both solve to rtol with the float64 residual as the judge."""
+    rr = cuda_lib
+    C, op, vals = csr_problem(40, 46, fp64=(precision == "fp64"))
+    mu, k = 1e-6, 32
+    B = W.gaussian_rhs(C.n, 3, 46)
+    res = []
+    for impl in (0, 1):
+        h = csr_handle(rr, C, vals, mu, k, "sparse_sign", 46, precision=precision, max_rhs=3,
+                       iter_impl=impl)
+        if precision == "fp64":
+            x, status, infos = h.solve(dev(B), rtol=1e-14, maxit=25)
+            assert status == rr.RR_ERR_MAXIT
+            res.append(x.cpu().numpy())
+        x, status, infos = h.solve(dev(B), rtol=1e-6, maxit=20000)
+        assert status == rr.RR_OK
+        assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), B) <= 1e-6)
+        h.close()
+    if precision == "fp64":
+        assert rel(res[0], res[1]) <= 1e-10

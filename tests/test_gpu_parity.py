@@ -346,3 +346,52 @@ def test_tensor_core_kernel_product(cuda_lib, n, m):
                       precision="mixed", max_rhs=m, kernel_impl=impl)
         w = h.apply_operator(dev(V)).cpu().numpy().reshape(n, m)[idx]
         assert np.max(np.abs(w - ref) / scale) <= (2e-5 if impl == 1 else 1e-4), impl
+
+
+# ------------------------------------------- persistent fused PCG step
+@pytest.mark.parametrize("m", [1, 3, 8])
+def test_fused_step_matches_separate_kernels_fp64(cuda_lib, m):
+    """The persistent cooperative PCG step (iter_impl 0) and the separate
+    kernels (iter_impl 1) take the same iterations and reach the same iterate
+    (their reductions group sums differently: rounding-level differences)."""
+    rr = cuda_lib
+    n, k, mu = 1025, 100, 1e-4
+    P, op = dense_problem(n)
+    B = W.gaussian_rhs(n, m, 61)
+    out = []
+    for impl in (0, 1):
+        h = rr.Handle(rr.Operator.dense(dev(P.A)), mu, k, "gaussian", seed=61, max_rhs=m,
+                      iter_impl=impl)
+        for budget in (5, 40):
+            x, status, infos = h.solve(dev(B), rtol=1e-13, maxit=budget)
+            out.append((budget, x.cpu().numpy(), [i["inner_iters"] for i in infos]))
+        h.close()
+    for (b0, x0, i0), (b1, x1, i1) in zip(out[:2], out[2:]):
+        assert i0 == i1
+        assert rel(x0, x1) <= 1e-12
+    bd = O.build(op, mu, k, "gaussian", seed=61)
+    xo, _ = O.solve(bd, B, rtol=1e-13, maxit=40)
+    assert rel(out[1][1], xo) <= 1e-10
+
+
+@pytest.mark.parametrize("m", [1, 4])
+def test_fused_step_kernel_operator_mixed(cuda_lib, m):
+    """Float32 iterations with the fused step on the Gaussian-kernel operator:
+    same iteration counts as the separate kernels within a few, and the float64
+    residual meets rtol."""
+    rr = cuda_lib
+    n, k, mu = 3001, 80, 1e-3
+    X = W.mixture_points(n, seed=62)
+    op = O.GaussKernelOp(X)
+    B = W.gaussian_rhs(n, m, 62)
+    its = []
+    for impl in (0, 1):
+        h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=62,
+                      precision="mixed", max_rhs=m, iter_impl=impl)
+        x, status, infos = h.solve(dev(B), rtol=1e-6)
+        assert status == rr.RR_OK
+        assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), B) <= 1e-6)
+        its.append([i["inner_iters"] for i in infos])
+        h.close()
+    for a, b in zip(*its):
+        assert abs(a - b) <= max(3, 0.05 * b)
