@@ -413,6 +413,139 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df(const float* __restri
   }
 }
 
+// The double-float product above with two columns j, j + 1 per step in the
+// lanes of packed float32 pair instructions (about half the instructions).
+// Every lane performs exactly the scalar kernel's operations; entries below
+// 2^-100 contribute zero (their scale factor is set to zero instead of
+// skipping them), and the two lanes keep separate double-float partial sums
+// that are added at the end.  An odd last column is paired with itself and
+// a zero coefficient.
+template <int MP>
+__global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df2(const float* __restrict__ x,
+                                                          const float2* __restrict__ pn,
+                                                          int64_t n, int dim, float sch, float scl,
+                                                          int64_t cols_per_split,
+                                                          const double* __restrict__ V,
+                                                          double* __restrict__ part) {
+  __shared__ __align__(16) float sx[kKmvTile * kMaxDim];
+  __shared__ float2 spn[kKmvTile];
+  __shared__ float2 sv[kKmvTile * MP];
+  __shared__ float2 tab[65];
+  if (threadIdx.x < 65) {
+    const double t = exp2((double)((int)threadIdx.x - 32) / 64.0);
+    const float h = (float)t;
+    tab[threadIdx.x] = make_float2(h, (float)(t - (double)h));
+  }
+  const int64_t i = (int64_t)blockIdx.x * kKmvRows + threadIdx.x;
+  const bool live = i < n;
+  p2 xi[kMaxDim];
+#pragma unroll
+  for (int d = 0; d < kMaxDim; ++d) {
+    const float v = (live && d < dim) ? x[i * dim + d] : 0.f;
+    xi[d] = mk2(v, v);
+  }
+  const float2 pni = live ? pn[i] : make_float2(0.f, 0.f);
+  const p2 pnih = mk2(pni.x, pni.x), pnil = mk2(pni.y, pni.y);
+  df2 acc[MP];
+#pragma unroll
+  for (int c = 0; c < MP; ++c) acc[c] = {mk2(0.f, 0.f), mk2(0.f, 0.f)};
+  const p2 ln2h = mk2(0.693147182464599609375f, 0.693147182464599609375f);
+  const p2 ln2l = mk2(-1.904654323148236e-09f, -1.904654323148236e-09f);
+  const p2 sch2 = mk2(sch, sch), scl2 = mk2(scl, scl);
+  const p2 m2 = mk2(-2.f, -2.f), two = mk2(2.f, 2.f), half = mk2(0.5f, 0.5f), one = mk2(1.f, 1.f);
+  const p2 c3 = mk2(0.16666667f, 0.16666667f), c4 = mk2(0.041666668f, 0.041666668f),
+           c5 = mk2(0.0083333338f, 0.0083333338f), s64 = mk2(64.f, 64.f),
+           i64 = mk2(0.015625f, 0.015625f);
+  const int64_t j0 = (int64_t)blockIdx.y * cols_per_split;
+  int64_t j1 = j0 + cols_per_split;
+  if (j1 > n) j1 = n;
+  for (int64_t jt = j0; jt < j1; jt += kKmvTile) {
+    const int cnt = (int)((j1 - jt < kKmvTile) ? (j1 - jt) : kKmvTile);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * dim; e += kKmvRows) sx[(e / dim) * kMaxDim + e % dim] = x[jt * dim + e];
+    for (int e = threadIdx.x; e < cnt; e += kKmvRows) spn[e] = pn[jt + e];
+    for (int e = threadIdx.x; e < cnt * MP; e += kKmvRows) {
+      const df v = df_from_double(V[jt * MP + e]);
+      sv[e] = make_float2(v.h, v.l);
+    }
+    __syncthreads();
+    for (int jj = 0; jj < cnt; jj += 2) {
+      const bool pair = jj + 1 < cnt;
+      const int jb = pair ? jj + 1 : jj;
+      const float* xa = sx + jj * kMaxDim;
+      const float* xb = sx + jb * kMaxDim;
+      // p_i . p_j in double-float
+      df2 c = two_prod2(xi[0], mk2(xa[0], xb[0]));
+#pragma unroll
+      for (int d = 1; d < kMaxDim; ++d) {
+        if (d < dim) {
+          const df2 t = two_prod2(xi[d], mk2(xa[d], xb[d]));
+          const df2 s2 = two_sum2(c.h, t.h);
+          c = {s2.h, add2(add2(c.l, t.l), s2.l)};
+        }
+      }
+      const float2 pa = spn[jj], pb = spn[jb];
+      df2 a = two_sum2(pnih, mk2(pa.x, pb.x));
+      a.l = add2(a.l, add2(pnil, mk2(pa.y, pb.y)));
+      df2 b = two_sum2(a.h, mul2(m2, c.h));
+      b.l = add2(b.l, sub2(a.l, mul2(two, c.l)));
+      const df2 d2 = fast_two_sum2(b.h, b.l);
+      // t = -d2 * s  (s = log2(e) / (2 h^2) as sch + scl)
+      p2 th = neg2(mul2(d2.h, sch2));
+      p2 tl = neg2(fma2(d2.h, sch2, th));            // exact low part of -d2.h * sch
+      tl = fma2(neg2(d2.h), scl2, tl);
+      tl = fma2(neg2(d2.l), sch2, tl);
+      float2 thf = un2(th);
+      const bool va = thf.x > -100.f, vb = thf.y > -100.f && pair;
+      thf.x = va ? thf.x : -100.f;                     // keep the exponent in range
+      thf.y = vb ? thf.y : -100.f;
+      th = mk2(thf.x, thf.y);
+      const float kfa = rintf(thf.x), kfb = rintf(thf.y);
+      const p2 f = sub2(th, mk2(kfa, kfb));           // exact, |f| <= 1/2
+      const float2 f64 = un2(mul2(f, s64));
+      const float jfa = rintf(f64.x), jfb = rintf(f64.y);
+      const p2 r = sub2(f, mul2(mk2(jfa, jfb), i64));  // exact, |r| <= 1/128
+      const df2 rr = two_sum2(r, tl);
+      const df2 z = df_mul2(rr, df2{ln2h, ln2l});
+      const p2 zh = z.h;
+      const p2 p3 = mul2(mul2(mul2(zh, zh), zh), fma2(zh, fma2(zh, c5, c4), c3));
+      df2 q = two_prod2(zh, zh);
+      q.h = mul2(q.h, half);
+      q.l = fma2(zh, z.l, mul2(q.l, half));
+      const df2 ah = fast_two_sum2(one, zh);
+      const df2 bh = two_sum2(ah.h, q.h);
+      const p2 low = add2(add2(add2(ah.l, bh.l), add2(z.l, q.l)), p3);
+      const df2 E = fast_two_sum2(bh.h, low);
+      const float2 ta = tab[(int)jfa + 32], tb = tab[(int)jfb + 32];
+      df2 K = df_mul2(df2{mk2(ta.x, tb.x), mk2(ta.y, tb.y)}, E);
+      const float sca = va ? __int_as_float(((int)kfa + 127) << 23) : 0.f;   // 2^k or 0
+      const float scb = vb ? __int_as_float(((int)kfb + 127) << 23) : 0.f;
+      const p2 sc = mk2(sca, scb);
+      K.h = mul2(K.h, sc);
+      K.l = mul2(K.l, sc);
+#pragma unroll
+      for (int cc = 0; cc < MP; ++cc) {
+        const float2 wa = sv[jj * MP + cc], wb = sv[jb * MP + cc];
+        const p2 vh = mk2(wa.x, wb.x), vl = mk2(wa.y, wb.y);
+        df2 pr = two_prod2(K.h, vh);
+        pr.l = fma2(K.h, vl, pr.l);
+        pr.l = fma2(K.l, vh, pr.l);
+        const df2 s2 = two_sum2(acc[cc].h, pr.h);
+        acc[cc] = {s2.h, add2(acc[cc].l, add2(s2.l, pr.l))};
+      }
+    }
+  }
+  if (live) {
+    double* out = part + ((int64_t)blockIdx.y * n + i) * MP;
+#pragma unroll
+    for (int cc = 0; cc < MP; ++cc) {
+      const float2 h = un2(acc[cc].h), l = un2(acc[cc].l);
+      out[cc] = df_to_double(df_add(df{h.x, l.x}, df{h.y, l.y}));
+    }
+  }
+}
+
+
 __global__ void k_point_norms(const float* __restrict__ x, int64_t n, int dim,
                               float2* __restrict__ pn) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -509,10 +642,10 @@ void kernel_mv<double>(const OpDev& op, double mu, const double* V, double* W, i
     const float sch = (float)s64;
     const float scl = (float)(s64 - (double)sch);
     switch (mp) {
-      case 1: k_kernel_mv_df<1><<<grid, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, cps, V, part); break;
-      case 2: k_kernel_mv_df<2><<<grid, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, cps, V, part); break;
-      case 4: k_kernel_mv_df<4><<<grid, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, cps, V, part); break;
-      default: k_kernel_mv_df<8><<<grid, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, cps, V, part); break;
+      case 1: k_kernel_mv_df2<1><<<grid, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, cps, V, part); break;
+      case 2: k_kernel_mv_df2<2><<<grid, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, cps, V, part); break;
+      case 4: k_kernel_mv_df2<4><<<grid, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, cps, V, part); break;
+      default: k_kernel_mv_df2<8><<<grid, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, cps, V, part); break;
     }
     rec(ev, 1, st);
     k_sum_splits<double><<<(unsigned)cdiv(op.n * mp, 256), 256, 0, st>>>(part, ns, op.n, mp, mu, V, W);

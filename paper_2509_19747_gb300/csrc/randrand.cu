@@ -104,7 +104,7 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_NORMS] = 64 * 8;
   // persistent fused steps of variant C: barrier + partials
   L.size[R_FUSED] = (o.variant == RR_VARIANT_C)
-                        ? 256 + std::max(pcg_tail_scratch_doubles(k, mp),
+                        ? sizeof(GridBar) + std::max(pcg_tail_scratch_doubles(k, mp),
                                          pcg_implicit_scratch_doubles(k, mp)) * 8
                         : 0;
   size_t off = 0;
@@ -328,7 +328,7 @@ void carve(rr_handle* h) {
   h->norms = (double*)at(R_NORMS);
   unsigned char* fz = (unsigned char*)at(R_FUSED);
   h->bar = (GridBar*)fz;
-  h->fscratch = fz ? (double*)(fz + 256) : nullptr;
+  h->fscratch = fz ? (double*)(fz + sizeof(GridBar)) : nullptr;
 }
 
 // a pair of timing events for one launch of category `cat` (nullptr when the

@@ -64,13 +64,17 @@ void restart_init(ColState* cs, int mp, const RestartParams& p, cudaStream_t st)
 
 constexpr int kMaxReduceBlocks = 8 * 152;  // upper bound on CTAs of the fused reductions
 
-// grid-wide barrier state of the persistent fused step (zero-initialised)
+// grid-wide barrier state of the persistent fused steps (zero-initialised);
+// the arrival counter and the generation word sit on separate 128-byte
+// lines, so that arrivals do not contend with the waiters' polling
 struct GridBar {
   unsigned count;
+  unsigned pad0[31];
   unsigned gen;
   int abort;
-  int pad;
+  unsigned pad1[30];
 };
+static_assert(sizeof(GridBar) == 256, "GridBar layout");
 constexpr int kFusedMaxCtas = 2 * 152;
 // Persistent fused PCG step (variant C with a basis): see k_krylov.cu.
 template <typename T>
