@@ -601,7 +601,7 @@ def _peaks():
     return {"hbm": 6800.0, "bf16": 1900.0}
 
 
-def batched_systems(rr, torch, rank):
+def batched_systems(rr, torch, rank, iter_impl=0):
     from workloads import generators as W
     cfg = BATCHED
     rng = np.random.default_rng([cfg["seed"], 7, rank])
@@ -613,7 +613,8 @@ def batched_systems(rr, torch, rank):
         X = torch.from_numpy(W.mixture_points(n, seed=sd)).cuda()
         B = torch.from_numpy(W.gaussian_rhs(n, cfg["nrhs"], sd)).cuda()
         op = rr.Operator.gauss_kernel(X)
-        reqs.append(rr.Request(op, mu, n // 40, B, cfg["rtol"], seed=sd, precision="mixed"))
+        reqs.append(rr.Request(op, mu, n // 40, B, cfg["rtol"], seed=sd, precision="mixed",
+                               iter_impl=iter_impl))
         meta.append((n, mu))
     return reqs, meta
 
@@ -623,20 +624,23 @@ def run_batched(args):
     rank, world, local = dist_init(args)
     torch.cuda.set_device(local)
     import paper_2509_19747_gb300 as rr
-    reqs, meta = batched_systems(rr, torch, rank)
-    arena = sum((q.workspace_bytes() + 255) // 256 * 256 for q in reqs)
-    # worker count: the best of a few on an untimed pass (autotune), or as given
-    cands = [args.workers] if args.workers > 0 else [4, 8, 16]
+    sets = {impl: batched_systems(rr, torch, rank, iter_impl=impl)[0] for impl in (0, 1)}
+    arena = sum((q.workspace_bytes() + 255) // 256 * 256 for q in sets[0])
+    # worker count and iteration form (persistent cooperative step or separate
+    # kernels): the best of a few on untimed passes (autotune), or as given
+    cands = [(w, impl) for w in ([args.workers] if args.workers > 0 else [4, 8, 16])
+             for impl in (0, 1)]
     tune = {}
-    for w in cands:
+    for w, impl in cands:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, _ = rr.solve_batch(reqs, workers=w, arena_bytes=arena)
+        st, _ = rr.solve_batch(sets[impl], workers=w, arena_bytes=arena)
         torch.cuda.synchronize()
-        tune[w] = time.perf_counter() - t0
+        tune[(w, impl)] = time.perf_counter() - t0
         if st != rr.RR_OK:
             raise RuntimeError(f"batch failed: {rr.randrand_status_str(st)}")
-    workers = min(tune, key=tune.get)
+    workers, impl = min(tune, key=tune.get)
+    reqs = sets[impl]
     for _ in range(max(args.warmup - 1, 0)):
         rr.solve_batch(reqs, workers=workers, arena_bytes=arena)
     smi = ClockSampler()
@@ -668,12 +672,12 @@ def run_batched(args):
     iters = [i["inner_iters"] for r in res for i in r["info"]]
     line = _line(args, world, "RandRAND-PCG solves/s to rtol 1e-6 (64 batched kernel ridge systems)",
                  world * BATCHED["systems"] * 1000.0 / ms, "solves/s", ms,
-                 {**BATCHED, "workers": workers, "parallelism": f"replicas x{world}",
+                 {**BATCHED, "workers": workers, "iter_impl": impl, "parallelism": f"replicas x{world}",
                   "l2": "inputs of the batch exceed L2"},
                  latency_ms={"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
                  one_after_another={"value": BATCHED["systems"] / seq_s, "unit": "solves/s",
                                     "seconds": seq_s},
-                 autotune_s={str(k): v for k, v in tune.items()},
+                 autotune_s={f"workers={k[0]},iter_impl={k[1]}": v for k, v in tune.items()},
                  solve={"inner_iters_max": max(iters), "inner_iters_median": float(np.median(iters))},
                  roofline=None, clocks=clocks)
     if rank == 0:

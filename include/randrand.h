@@ -135,6 +135,10 @@ typedef struct {
   int32_t iter_impl;     /* variant C with a basis: 0 auto (one persistent
                             cooperative launch per iteration for everything
                             after the operator product), 1 separate kernels */
+  int32_t q;             /* power of the test matrix Omega = A^q X^T
+                            (eq:testmatrix), 0..4, default 0; q >= 1 costs q
+                            more sketch products and is not available with the
+                            basis-less CSR form */
   double rho;            /* C variant: <= 0 -> eq:optimal_rho with F = 1/mu     */
   double restart_eta;    /* restart after this residual reduction, default 1e-2 */
 } rr_build_opts;

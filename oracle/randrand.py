@@ -214,15 +214,24 @@ class Build:
 
 
 def make_omega(n: int, k: int, sketch: str, seed: int, gamma: int = 8,
-               precision: str = "fp64") -> np.ndarray:
-    """Test matrix Omega = X^T (eq:testmatrix with q = 0), rounded to the
-    working precision of the sketch (float64, float32 or bfloat16)."""
+               precision: str = "fp64", q: int = 0, op=None) -> np.ndarray:
+    """Test matrix Omega = A^q X^T (eq:testmatrix, A symmetric), rounded to the
+    working precision of the sketch (float64, float32 or bfloat16).  X^T is
+    the Gaussian or sparse-sign draw; with q >= 1 it is multiplied by A (not
+    A_mu: Omega does not depend on the shift) q times before the rounding."""
     if sketch == "gaussian":
         Om = philox.gaussian_omega(n, k, seed)
     elif sketch == "sparse_sign":
         Om = philox.sparse_sign_omega_dense(n, k, gamma, seed)
     else:
         raise ValueError(sketch)
+    if q > 0:
+        if precision == "bf16":
+            Om = philox.round_bf16(Om)
+        elif precision == "fp32":
+            Om = philox.round_f32(Om)
+        for _ in range(q):
+            Om = op.matmat(Om)
     if precision == "bf16":
         Om = philox.round_bf16(Om)
     elif precision == "fp32":
@@ -262,12 +271,17 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
           omega_precision: str = "fp64", orth: str = "householder",
           gamma: int = 8, l_sk: int | None = None, gamma_sk: int = 8,
           power_iters: int = 20, rho: float | None = None,
-          tau: float | None = None) -> Build:
+          tau: float | None = None, q: int = 0) -> Build:
     n = op.n
     if not (1 <= k <= n):
         raise ValueError("need 1 <= k <= n")
-    Om = make_omega(n, k, sketch, seed, gamma, omega_precision) if omega is None \
-        else np.asarray(omega, dtype=np.float64)
+    if omega is None:
+        Om = make_omega(n, k, sketch, seed, gamma, omega_precision, q=q, op=op)
+    else:
+        # a given X^T: Omega = A^q X^T (eq:testmatrix)
+        Om = np.asarray(omega, dtype=np.float64)
+        for _ in range(q):
+            Om = op.matmat(Om)
     # Alg. 7 step 1 / Alg. 4 step 1: Y_mu = A Omega + mu Omega
     Ymu = op.matmat(Om) + mu * Om
     if orth == "householder":

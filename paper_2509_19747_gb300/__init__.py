@@ -55,7 +55,8 @@ class rr_build_opts(ctypes.Structure):
         ("variant", ctypes.c_int32), ("precision", ctypes.c_int32), ("orth", ctypes.c_int32),
         ("gamma", ctypes.c_int32), ("l_sk", ctypes.c_int32), ("gamma_sk", ctypes.c_int32),
         ("power_iters", ctypes.c_int32), ("max_rhs", ctypes.c_int32), ("profile", ctypes.c_int32),
-        ("kernel_impl", ctypes.c_int32), ("iter_impl", ctypes.c_int32), ("rho", ctypes.c_double),
+        ("kernel_impl", ctypes.c_int32), ("iter_impl", ctypes.c_int32), ("q", ctypes.c_int32),
+        ("rho", ctypes.c_double),
         ("restart_eta", ctypes.c_double),
     ]
 
@@ -337,7 +338,8 @@ class Handle:
                  variant: str = "C", precision: str = "fp64", max_rhs: int = 1,
                  power_iters: int = 20, rho: float = 0.0, restart_eta: float = 1e-2,
                  gamma: int = 8, profile: bool = False, kernel_impl: int = 0, stream=None,
-                 orth: str = "cholqr2", l_sk: int = 0, gamma_sk: int = 8, iter_impl: int = 0):
+                 orth: str = "cholqr2", l_sk: int = 0, gamma_sk: int = 8, iter_impl: int = 0,
+                 q: int = 0):
         import torch
         self.op = op
         self.n = op.n
@@ -356,6 +358,7 @@ class Handle:
         o.profile = 1 if profile else 0
         o.kernel_impl = kernel_impl
         o.iter_impl = iter_impl
+        o.q = q
         self.opts = o
         self.ws_bytes = randrand_workspace_bytes(op.c, k, o)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
@@ -488,7 +491,7 @@ class Request:
     def __init__(self, op: Operator, mu: float, k: int, b, rtol: float, sketch: str = "gaussian",
                  seed: int = 0, maxit: int = 20000, variant: str = "C", precision: str = "mixed",
                  orth: str = "cholqr2", power_iters: int = 20, gamma: int = 8, l_sk: int = 0,
-                 gamma_sk: int = 8, kernel_impl: int = 0):
+                 gamma_sk: int = 8, kernel_impl: int = 0, iter_impl: int = 0, q: int = 0):
         import torch
         B = b.reshape(op.n, -1)
         m = B.shape[1]
@@ -505,6 +508,8 @@ class Request:
         o.l_sk = l_sk
         o.gamma_sk = gamma_sk
         o.kernel_impl = kernel_impl
+        o.iter_impl = iter_impl
+        o.q = q
         self.op = op
         self.c = rr_request(op=op.c, mu=float(mu), k=int(k), sketch=SKETCHES[sketch],
                             seed=int(seed) & 0xFFFFFFFFFFFFFFFF, opts=o, b=self.bc.data_ptr(),

@@ -4,18 +4,21 @@
 // With Q = A_mu Omega R^-1 never formed and Hb = R^-1 (tau G - I) R^-T,
 //   z = P r = r + A_mu Omega Hb Omega^T A_mu r.
 // Per iteration, for the CTA's rows (Omega is a sparse-sign pattern):
-//   1  w = A_mu p, p^T w partials                           | barrier
-//   2  alpha; e += alpha p; r -= alpha w; |r|^2 partials     | barrier
-//   3  convergence decision; u = A_mu r; g partials of      | barrier
-//      Omega^T u (shared-memory scatter, then global)
-//   4  g reduced (entries spread over the CTAs)             | barrier
+//   1  w = A_mu p; p^T w accumulated                        | barrier
+//   2  alpha; e += alpha p; r -= alpha w; |r|^2 accumulated  | barrier
+//   3  convergence decision; u = A_mu r; g += Omega^T u     | barrier
+//      (shared-memory scatter per CTA, then float64 atomic adds)
 //   5  s = Hb g (rows of Hb spread over the CTAs)           | barrier
 //   6  v = Omega s                                          | barrier
-//   7  z = r + A_mu v; r^T z partials                       | barrier
+//   7  z = r + A_mu v; r^T z accumulated                    | barrier
 //   8  beta; p = z + beta p                                 | barrier (next step)
-// Scalars are reduced by every CTA itself in a fixed order; vectors written
-// in this launch by other CTAs are read through L2 (ld.cg).  The barrier
-// waits are bounded by the global timer.
+// Scalars and g are summed over the CTAs with float64 atomic adds (arrival
+// order: rounding-level differences between runs); CTA 0 clears each
+// accumulator in a step after its last reader and before its next writer.
+// Each thread advances several rows of a CSR product at once so that their
+// index and vector loads are in flight together.  Vectors written in this
+// launch by other CTAs are read through L2 (ld.cg).  The barrier waits are
+// bounded by the global timer.
 #include "rr_common.cuh"
 #include "rr_krylov.cuh"
 
@@ -88,16 +91,6 @@ __device__ __forceinline__ void block_sum(double (&v)[8], double* sh) {
   __syncthreads();
 }
 
-// fixed-order sum of part[g * 8 + c] over g < G by one warp
-__device__ __forceinline__ double warp_parts(const double* part, int G, int c) {
-  const int lane = threadIdx.x & 31;
-  double v = 0.0;
-  for (int g = lane; g < G; g += 32) v += __ldcg(part + (int64_t)g * 8 + c);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 template <typename T>
 struct ImpArgs {
   const int32_t* rowptr;
@@ -119,11 +112,7 @@ struct ImpArgs {
   int k;
   int rpc;
   int iters;            // iterations in this launch
-  double* part_pw;      // [G][8]
-  double* part_rr;
-  double* part_rz;
-  double* part_g;       // [G][k][MP]
-  double* gglob;        // [k][MP]
+  double* acc;          // [pw 8 | rr 8 | rz 8 | g k x 8]
   double* sglob;        // [k][MP]
   ColState* cs;
   GridBar* bar;
@@ -133,6 +122,57 @@ struct ImpArgs {
 template <typename T>
 __device__ __forceinline__ T aval(const ImpArgs<T>& a, int32_t p) {
   return a.vals_f64 ? (T)((const double*)a.vals)[p] : (T)((const float*)a.vals)[p];
+}
+
+constexpr int kRPT = 2;   // rows a thread advances together
+constexpr int kNz = 6;    // nonzeros per row whose indices are loaded in one batch
+
+// out[m] = (A_mu X)_{row m} for the rows i0 + m kIT (m < kRPT) of the CTA.
+// All column indices and values of a batch are loaded before any gather, and
+// all gathers of a batch are issued before any use, so a thread has up to
+// kRPT x kNz independent loads in flight.
+template <typename T, int MP>
+__device__ __forceinline__ void csr_rows(const ImpArgs<T>& a, const T* X, int64_t r0, int cnt,
+                                         int i0, T mu, T (&out)[kRPT][MP], bool (&live)[kRPT]) {
+  int32_t beg[kRPT], end[kRPT];
+  int len = 0;
+#pragma unroll
+  for (int m = 0; m < kRPT; ++m) {
+    const int idx = i0 + m * kIT;
+    live[m] = idx < cnt;
+    const int64_t row = r0 + (live[m] ? idx : 0);
+    beg[m] = live[m] ? a.rowptr[row] : 0;
+    end[m] = live[m] ? a.rowptr[row + 1] : 0;
+#pragma unroll
+    for (int c = 0; c < MP; ++c) out[m][c] = live[m] ? mu * __ldcg(X + row * MP + c) : (T)0;
+    len = max(len, end[m] - beg[m]);
+  }
+  for (int qb = 0; qb < len; qb += kNz) {
+    int32_t j[kRPT][kNz];
+    T av[kRPT][kNz];
+#pragma unroll
+    for (int m = 0; m < kRPT; ++m)
+#pragma unroll
+      for (int q = 0; q < kNz; ++q) {
+        const int p = beg[m] + qb + q;
+        const bool ok = p < end[m];
+        j[m][q] = ok ? a.colidx[p] : -1;
+        av[m][q] = ok ? aval(a, p) : (T)0;
+      }
+#pragma unroll
+    for (int m = 0; m < kRPT; ++m) {
+      T xv[kNz][MP];
+#pragma unroll
+      for (int q = 0; q < kNz; ++q)
+#pragma unroll
+        for (int c = 0; c < MP; ++c)
+          xv[q][c] = j[m][q] >= 0 ? __ldcg(X + (int64_t)j[m][q] * MP + c) : (T)0;
+#pragma unroll
+      for (int q = 0; q < kNz; ++q)
+#pragma unroll
+        for (int c = 0; c < MP; ++c) out[m][c] = fma(av[m][q], xv[q][c], out[m][c]);
+    }
+  }
 }
 
 template <typename T, int MP>
@@ -163,135 +203,142 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit(ImpArgs<T> a) {
     if (it > 0 && !barrier_all(a.bar, a.err)) return;   // p of the last step complete
 
     // ---- 1: w = A_mu p, p^T w
+    double* acc_pw = a.acc;
+    double* acc_rr = a.acc + 8;
+    double* acc_rz = a.acc + 16;
+    double* gacc = a.acc + 24;
     double v[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) v[c] = 0.0;
-    for (int i = tid; i < cnt; i += kIT) {
-      const int64_t row = r0 + i;
-      T acc[MP];
+    for (int i0 = tid; i0 < cnt; i0 += kIT * kRPT) {
+      T w[kRPT][MP];
+      bool live[kRPT];
+      csr_rows<T, MP>(a, a.P, r0, cnt, i0, mu, w, live);
 #pragma unroll
-      for (int c = 0; c < MP; ++c) acc[c] = mu * __ldcg(a.P + row * MP + c);
-      for (int32_t p = a.rowptr[row]; p < a.rowptr[row + 1]; ++p) {
-        const T av = aval(a, p);
-        const int64_t j = a.colidx[p];
+      for (int m = 0; m < kRPT; ++m)
+        if (live[m]) {
+          const int64_t row = r0 + i0 + m * kIT;
 #pragma unroll
-        for (int c = 0; c < MP; ++c) acc[c] = fma(av, __ldcg(a.P + j * MP + c), acc[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < MP; ++c) {
-        a.W[row * MP + c] = acc[c];
-        v[c] += (double)__ldcg(a.P + row * MP + c) * (double)acc[c];
-      }
+          for (int c = 0; c < MP; ++c) {
+            a.W[row * MP + c] = w[m][c];
+            v[c] += (double)__ldcg(a.P + row * MP + c) * (double)w[m][c];
+          }
+        }
     }
+    if (cta == 0 && tid < 8) acc_rz[tid] = 0.0;
     block_sum<MP>(v, redd);
-    if (tid == 0)
-      for (int c = 0; c < MP; ++c) a.part_pw[(int64_t)cta * 8 + c] = v[c];
+    if (tid == 0 && cnt > 0)
+      for (int c = 0; c < MP; ++c) atomicAdd(acc_pw + c, v[c]);
     if (!barrier_all(a.bar, a.err)) return;
 
     // ---- 2: alpha, e, r, |r|^2
-    if (wid < MP) {
-      const double pw = warp_parts(a.part_pw, G, wid);
-      if (lane == 0) {
-        const int c = wid;
-        sh_pw[c] = pw;
-        int act = st[c].active;
-        double al = 0.0;
-        if (act) {
-          if (!(pw > 0.0 && isfinite(pw))) act = -1;       // breakdown
-          else al = st[c].rho / pw;
-        }
-        sh_alpha[c] = al;
-        sh_act[c] = act;
+    if (tid < MP) {
+      const int c = tid;
+      const double pw = __ldcg(acc_pw + c);
+      sh_pw[c] = pw;
+      int act = st[c].active;
+      double al = 0.0;
+      if (act) {
+        if (!(pw > 0.0 && isfinite(pw))) act = -1;       // breakdown
+        else al = st[c].rho / pw;
       }
+      sh_alpha[c] = al;
+      sh_act[c] = act;
     }
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < 8; ++c) v[c] = 0.0;
-    for (int i = tid; i < cnt; i += kIT) {
-      const int64_t row = r0 + i;
+    for (int i0 = tid; i0 < cnt; i0 += kIT * kRPT) {
+      // loads of all rows first, then the arithmetic and the stores
+      T pe[kRPT][MP], ee[kRPT][MP], we[kRPT][MP], re[kRPT][MP];
 #pragma unroll
-      for (int c = 0; c < MP; ++c) {
-        const T al = (T)sh_alpha[c];
-        const int64_t g = row * MP + c;
-        a.E[g] = fma(al, __ldcg(a.P + g), a.E[g]);
-        const T r = fma(-al, a.W[g], a.R[g]);
-        a.R[g] = r;
-        v[c] += (double)r * (double)r;
+      for (int m = 0; m < kRPT; ++m) {
+        const int idx = i0 + m * kIT;
+        const int64_t row = r0 + (idx < cnt ? idx : 0);
+#pragma unroll
+        for (int c = 0; c < MP; ++c) {
+          const int64_t g = row * MP + c;
+          pe[m][c] = __ldcg(a.P + g);
+          ee[m][c] = a.E[g];
+          we[m][c] = a.W[g];
+          re[m][c] = a.R[g];
+        }
       }
-    }
-    block_sum<MP>(v, redd);
-    if (tid == 0)
-      for (int c = 0; c < MP; ++c) a.part_rr[(int64_t)cta * 8 + c] = v[c];
-    if (!barrier_all(a.bar, a.err)) return;
-
-    // ---- 3: convergence decision; u = A_mu r; g partials of Omega^T u
-    if (wid < MP) {
-      const double rr = warp_parts(a.part_rr, G, wid);
-      if (lane == 0) {
-        const int c = wid;
-        sh_rr[c] = rr;
-        ColState& s = st[c];
-        s.pw = sh_pw[c];
-        s.rr = rr;
-        if (sh_act[c] < 0) {
-          s.status = RR_ERR_BREAKDOWN;
-          s.alpha = 0.0;
-          s.active = 0;
-        } else if (sh_act[c] > 0) {
-          s.alpha = sh_alpha[c];
-          s.iters += 1;
-          if (!isfinite(rr)) { s.status = RR_ERR_BREAKDOWN; s.active = 0; }
-          else if (rr <= s.stop2 || s.iters >= s.budget) s.active = 0;
-        } else {
-          s.alpha = 0.0;
+#pragma unroll
+      for (int m = 0; m < kRPT; ++m) {
+        const int idx = i0 + m * kIT;
+        if (idx >= cnt) continue;
+        const int64_t row = r0 + idx;
+#pragma unroll
+        for (int c = 0; c < MP; ++c) {
+          const T al = (T)sh_alpha[c];
+          const int64_t g = row * MP + c;
+          a.E[g] = fma(al, pe[m][c], ee[m][c]);
+          const T r = fma(-al, we[m][c], re[m][c]);
+          a.R[g] = r;
+          v[c] += (double)r * (double)r;
         }
       }
     }
-    for (int e = tid; e < k * MP; e += kIT) acc_g[e] = (T)0;
-    __syncthreads();
-    for (int i = tid; i < cnt; i += kIT) {
-      const int64_t row = r0 + i;
-      T u[MP];
-#pragma unroll
-      for (int c = 0; c < MP; ++c) u[c] = mu * __ldcg(a.R + row * MP + c);
-      for (int32_t p = a.rowptr[row]; p < a.rowptr[row + 1]; ++p) {
-        const T av = aval(a, p);
-        const int64_t j = a.colidx[p];
-#pragma unroll
-        for (int c = 0; c < MP; ++c) u[c] = fma(av, __ldcg(a.R + j * MP + c), u[c]);
-      }
-      for (int t = 0; t < a.gamma; ++t) {
-        const int cc = a.om_cols[row * a.gamma + t];
-        const T sg = a.om_sgn[row * a.gamma + t] > 0 ? om : -om;
-#pragma unroll
-        for (int c = 0; c < MP; ++c) atomicAdd(&acc_g[cc * MP + c], sg * u[c]);
-      }
-    }
-    __syncthreads();
-    {
-      double* out = a.part_g + (int64_t)cta * k * MP;
-      for (int e = tid; e < k * MP; e += kIT) out[e] = (double)acc_g[e];
-    }
+    block_sum<MP>(v, redd);
+    if (tid == 0 && cnt > 0)
+      for (int c = 0; c < MP; ++c) atomicAdd(acc_rr + c, v[c]);
     if (!barrier_all(a.bar, a.err)) return;
 
-    // ---- 4: g reduced
-    {
-      const int len = k * MP;
-      for (int e = cta * (kIT / 32) + wid; e < len; e += G * (kIT / 32)) {
-        double sum = 0.0;
-        for (int g = lane; g < G; g += 32) sum += __ldcg(a.part_g + (int64_t)g * len + e);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) a.gglob[e] = sum;
+    // ---- 3: convergence decision; u = A_mu r; g += Omega^T u
+    if (tid < MP) {
+      const int c = tid;
+      const double rr = __ldcg(acc_rr + c);
+      sh_rr[c] = rr;
+      ColState& s = st[c];
+      s.pw = sh_pw[c];
+      s.rr = rr;
+      if (sh_act[c] < 0) {
+        s.status = RR_ERR_BREAKDOWN;
+        s.alpha = 0.0;
+        s.active = 0;
+      } else if (sh_act[c] > 0) {
+        s.alpha = sh_alpha[c];
+        s.iters += 1;
+        if (!isfinite(rr)) { s.status = RR_ERR_BREAKDOWN; s.active = 0; }
+        else if (rr <= s.stop2 || s.iters >= s.budget) s.active = 0;
+      } else {
+        s.alpha = 0.0;
       }
     }
+    if (cta == 0 && tid < 8) acc_pw[tid] = 0.0;
+    for (int e = tid; e < k * MP; e += kIT) acc_g[e] = (T)0;
+    __syncthreads();
+    for (int i0 = tid; i0 < cnt; i0 += kIT * kRPT) {
+      T u[kRPT][MP];
+      bool live[kRPT];
+      csr_rows<T, MP>(a, a.R, r0, cnt, i0, mu, u, live);
+#pragma unroll
+      for (int m = 0; m < kRPT; ++m)
+        if (live[m]) {
+          const int64_t row = r0 + i0 + m * kIT;
+          for (int t = 0; t < a.gamma; ++t) {
+            const int cc = a.om_cols[row * a.gamma + t];
+            const T sg = a.om_sgn[row * a.gamma + t] > 0 ? om : -om;
+#pragma unroll
+            for (int c = 0; c < MP; ++c) atomicAdd(&acc_g[cc * MP + c], sg * u[m][c]);
+          }
+        }
+    }
+    __syncthreads();
+    if (cnt > 0)
+      for (int e = tid; e < k * MP; e += kIT) {
+        const T x = acc_g[e];
+        if (x != (T)0) atomicAdd(gacc + (e / MP) * 8 + (e % MP), (double)x);
+      }
     if (!barrier_all(a.bar, a.err)) return;
 
     // ---- 5: s = Hb g; the CTA's rows of Hb (j = cta, cta + G, ...), g staged
     // in shared memory
     {
       T* gsh = s_sh;   // free until step 6
-      for (int e = tid; e < k * MP; e += kIT) gsh[e] = (T)__ldcg(a.gglob + e);
+      for (int e = tid; e < k * MP; e += kIT) gsh[e] = (T)__ldcg(gacc + (e / MP) * 8 + (e % MP));
+      if (cta == 0 && tid < 8) acc_rr[tid] = 0.0;
       __syncthreads();
       for (int j = cta + wid * G; j < k; j += G * (kIT / 32)) {
         double acc[MP];
@@ -316,56 +363,78 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit(ImpArgs<T> a) {
 
     // ---- 6: v = Omega s
     for (int e = tid; e < k * MP; e += kIT) s_sh[e] = (T)__ldcg(a.sglob + e);
+    if (cta == 0)
+      for (int e = tid; e < k * 8; e += kIT) gacc[e] = 0.0;
     __syncthreads();
-    for (int i = tid; i < cnt; i += kIT) {
-      const int64_t row = r0 + i;
-      T acc[MP];
+    for (int i0 = tid; i0 < cnt; i0 += kIT * kRPT) {
+      int32_t cc[kRPT][8];
+      T sg[kRPT][8];
+      const int gm = a.gamma < 8 ? a.gamma : 8;
 #pragma unroll
-      for (int c = 0; c < MP; ++c) acc[c] = (T)0;
-      for (int t = 0; t < a.gamma; ++t) {
-        const int cc = a.om_cols[row * a.gamma + t];
-        const T sg = a.om_sgn[row * a.gamma + t] > 0 ? om : -om;
+      for (int m = 0; m < kRPT; ++m) {
+        const int idx = i0 + m * kIT;
+        const int64_t row = r0 + (idx < cnt ? idx : 0);
 #pragma unroll
-        for (int c = 0; c < MP; ++c) acc[c] = fma(sg, s_sh[cc * MP + c], acc[c]);
+        for (int t = 0; t < 8; ++t) {
+          cc[m][t] = t < gm ? a.om_cols[row * a.gamma + t] : 0;
+          sg[m][t] = t < gm ? (a.om_sgn[row * a.gamma + t] > 0 ? om : -om) : (T)0;
+        }
       }
 #pragma unroll
-      for (int c = 0; c < MP; ++c) a.U[row * MP + c] = acc[c];
+      for (int m = 0; m < kRPT; ++m) {
+        const int idx = i0 + m * kIT;
+        if (idx >= cnt) continue;
+        const int64_t row = r0 + idx;
+        T acc[MP];
+#pragma unroll
+        for (int c = 0; c < MP; ++c) acc[c] = (T)0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+#pragma unroll
+          for (int c = 0; c < MP; ++c) acc[c] = fma(sg[m][t], s_sh[cc[m][t] * MP + c], acc[c]);
+        for (int t = 8; t < a.gamma; ++t) {
+          const int c2 = a.om_cols[row * a.gamma + t];
+          const T s2 = a.om_sgn[row * a.gamma + t] > 0 ? om : -om;
+#pragma unroll
+          for (int c = 0; c < MP; ++c) acc[c] = fma(s2, s_sh[c2 * MP + c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < MP; ++c) a.U[row * MP + c] = acc[c];
+      }
     }
     if (!barrier_all(a.bar, a.err)) return;
 
     // ---- 7: z = r + A_mu v, r^T z
 #pragma unroll
     for (int c = 0; c < 8; ++c) v[c] = 0.0;
-    for (int i = tid; i < cnt; i += kIT) {
-      const int64_t row = r0 + i;
-      T acc[MP];
+    for (int i0 = tid; i0 < cnt; i0 += kIT * kRPT) {
+      T zv[kRPT][MP];
+      bool live[kRPT];
+      csr_rows<T, MP>(a, a.U, r0, cnt, i0, mu, zv, live);
 #pragma unroll
-      for (int c = 0; c < MP; ++c) acc[c] = mu * __ldcg(a.U + row * MP + c);
-      for (int32_t p = a.rowptr[row]; p < a.rowptr[row + 1]; ++p) {
-        const T av = aval(a, p);
-        const int64_t j = a.colidx[p];
+      for (int m = 0; m < kRPT; ++m)
+        if (live[m]) {
+          const int64_t row = r0 + i0 + m * kIT;
 #pragma unroll
-        for (int c = 0; c < MP; ++c) acc[c] = fma(av, __ldcg(a.U + j * MP + c), acc[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < MP; ++c) {
-        const int64_t g = row * MP + c;
-        const T r = a.R[g];
-        const T z = r + acc[c];
-        a.Z[g] = z;
-        v[c] += (double)r * (double)z;
-      }
+          for (int c = 0; c < MP; ++c) {
+            const int64_t g = row * MP + c;
+            const T r = a.R[g];
+            const T z = r + zv[m][c];
+            a.Z[g] = z;
+            v[c] += (double)r * (double)z;
+          }
+        }
     }
     block_sum<MP>(v, redd);
-    if (tid == 0)
-      for (int c = 0; c < MP; ++c) a.part_rz[(int64_t)cta * 8 + c] = v[c];
+    if (tid == 0 && cnt > 0)
+      for (int c = 0; c < MP; ++c) atomicAdd(acc_rz + c, v[c]);
     if (!barrier_all(a.bar, a.err)) return;
 
     // ---- 8: beta, p = z + beta p
-    if (wid < MP) {
-      const double rz = warp_parts(a.part_rz, G, wid);
-      if (lane == 0) {
-        const int c = wid;
+    if (tid < MP) {
+      const double rz = __ldcg(a.acc + 16 + tid);
+      {
+        const int c = tid;
         ColState& s = st[c];
         sh_rz[c] = rz;
         double be = 0.0;
@@ -403,15 +472,36 @@ size_t imp_smem(int k, int mp) {
   return 2 * (size_t)k * mp * sizeof(T);
 }
 
+// raise the kernel's dynamic shared-memory limit to the device maximum once
+// per device (outside any stream capture: called first from the build)
+template <typename T, int MP>
+bool imp_attr() {
+  static std::atomic<uint64_t> done{0};
+  return once_per_device(done, [] {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return false;
+    // the dynamic limit is the opt-in maximum less the kernel's static shared memory
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_pcg_implicit<T, MP>) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (cudaFuncSetAttribute(k_pcg_implicit<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  });
+}
+
 template <typename T, int MP>
 cudaError_t launch_imp(const ImpArgs<T>& a, int G, cudaStream_t st) {
   auto kern = k_pcg_implicit<T, MP>;
   const size_t smem = imp_smem<T>(a.k, MP);
-  if (smem > 48 * 1024) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  if (!imp_attr<T, MP>()) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
   cfg.blockDim = dim3(kIT);
@@ -428,7 +518,8 @@ cudaError_t launch_imp(const ImpArgs<T>& a, int G, cudaStream_t st) {
 }  // namespace
 
 size_t pcg_implicit_scratch_doubles(int k, int mp) {
-  return (size_t)kFusedMaxCtas * 8 * 3 + 2 * (size_t)k * 8 + (size_t)kFusedMaxCtas * k * mp;
+  (void)mp;
+  return 24 + 2 * (size_t)k * 8;
 }
 
 template <typename T>
@@ -439,6 +530,14 @@ int pcg_implicit_ctas(int64_t n, int k, int mp) {
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
   if (imp_smem<T>(k, mp) + 8192 > (size_t)optin) return 0;
+  bool attr = false;
+  switch (mp) {
+    case 1: attr = imp_attr<T, 1>(); break;
+    case 2: attr = imp_attr<T, 2>(); break;
+    case 4: attr = imp_attr<T, 4>(); break;
+    default: attr = imp_attr<T, 8>(); break;
+  }
+  if (!attr) return 0;
   int64_t g = sms;
   if (g > n) g = n;
   if (g > kFusedMaxCtas) g = kFusedMaxCtas;
@@ -465,12 +564,8 @@ cudaError_t pcg_implicit(const OpDev& op, double mu, const int32_t* om_cols, con
   a.k = k;
   a.rpc = (int)cdiv(op.n, G);
   a.iters = iters;
-  a.part_pw = scratch;
-  a.part_rr = a.part_pw + (size_t)kFusedMaxCtas * 8;
-  a.part_rz = a.part_rr + (size_t)kFusedMaxCtas * 8;
-  a.gglob = a.part_rz + (size_t)kFusedMaxCtas * 8;
-  a.sglob = a.gglob + (size_t)k * 8;
-  a.part_g = a.sglob + (size_t)k * 8;
+  a.acc = scratch;
+  a.sglob = scratch + 24 + (size_t)k * 8;
   a.cs = cs;
   a.bar = bar;
   a.err = err;

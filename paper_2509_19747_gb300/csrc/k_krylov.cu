@@ -865,25 +865,22 @@ template void axpby<double, float, float>(const double*, Coefs8, const float*, C
 // ======================================================================
 // Persistent fused PCG step (variant C with a basis), one cooperative launch
 // per iteration after the operator product w = A_mu p.  Every CTA owns a
-// contiguous block of rows and runs all of Alg. 7 steps 6-9 for them, with
-// five grid-wide barriers in place of seven kernel boundaries:
-//   A  p^T w partials                                      | barrier
-//   B  alpha; e += alpha p; r -= alpha w; |r|^2 and Q^T r   | barrier
-//      partials over the CTA's rows
-//   C  convergence decision; t = Q^T r reduced (entries     | barrier
-//      spread over the CTAs)
-//   D  s = H t (rows of H spread over the CTAs)             | barrier
-//   E  z = r + Q s for the CTA's rows; r^T z partials       | barrier
+// contiguous block of rows and runs Alg. 7 steps 6-9 for them:
+//   A  p^T w (unless the product kernel already formed alpha)  | barrier
+//   B  alpha; e += alpha p; r -= alpha w; |r|^2 and Q^T r       | barrier
+//      accumulated over the CTAs (float64 atomic adds)
+//   E  convergence decision; z = r + (Q H) t, t = Q^T r;        | barrier
+//      r^T z accumulated
 //   F  beta; p = z + beta p
-// Every CTA reduces the per-CTA partials of a scalar itself, in the same
-// fixed order, so all CTAs take identical decisions and the results are
-// deterministic.  Reads of data written by other CTAs bypass L1 (ld.cg).
-// The barrier waits are bounded by the global timer (an error flag and an
-// early exit instead of a hang).
+// The accumulators come in two sets used by alternate launches (the parity
+// of a launch counter kept beside the barrier); CTA 0 clears the other set
+// while the current one is in use, so no clearing races a reader.  Sums over
+// CTAs thus run in arrival order (rounding-level differences between runs).
+// Reads of data written by other CTAs bypass L1 (ld.cg).  The barrier waits
+// are bounded by the global timer.
 // ======================================================================
 constexpr int kFT = 256;                 // threads of the fused step
 constexpr int kFusedChunk = 256;         // rows of r staged in shared memory at a time
-constexpr int kTPiece = 256;             // entries of t staged at a time in step D
 constexpr unsigned long long kBarTimeoutNs = 10ull * 1000 * 1000 * 1000;
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -929,16 +926,6 @@ __device__ bool grid_barrier(GridBar* gb, int* err) {
   return ok != 0;
 }
 
-// fixed-order sum of part[g * 8 + c] over g < G by one warp (same result in every CTA)
-__device__ __forceinline__ double warp_sum_parts(const double* part, int G, int c) {
-  const int lane = threadIdx.x & 31;
-  double v = 0.0;
-  for (int g = lane; g < G; g += 32) v += __ldcg(part + (int64_t)g * 8 + c);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 template <typename T>
 struct TailArgs {
   T* E;
@@ -947,22 +934,20 @@ struct TailArgs {
   T* Z;
   const T* W;
   const T* Q;
-  const double* H;
+  const T* QH;
   int64_t n;
   int k;
   int rpc;
-  double* part_pw;
-  double* part_rr;
-  double* part_rz;
-  double* part_t;
-  double* tglob;
-  double* sglob;
+  int alpha_ready;    // the product kernel has applied alpha to cs
+  double* acc;        // two sets of [pw 8 | rr 8 | rz 8 | t k x 8]
   ColState* cs;
   GridBar* bar;
   int* err;
 };
 
-// Q^T r over the CTA's rows [r0, r0 + cnt) -> out[j][c] (float64)
+__host__ __device__ inline size_t tail_set_doubles(int k) { return 24 + (size_t)k * 8; }
+
+// Q^T r over the CTA's rows [r0, r0 + cnt), added into out[j][c] (float64 atomics)
 template <typename T, int MP>
 __device__ void tail_qtr(const T* __restrict__ Q, const T* __restrict__ R, int64_t r0, int cnt,
                          int k, double* __restrict__ out, T* Rs, float* red) {
@@ -1029,10 +1014,12 @@ __device__ void tail_qtr(const T* __restrict__ Q, const T* __restrict__ R, int64
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int c = 0; c < MP; ++c) acc[a][c] += red[((p2 - 1) * nq + q) * 4 * MP + a * MP + c];
+      if (cnt > 0) {
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < MP; ++c) out[(int64_t)(4 * q + a) * MP + c] = (double)acc[a][c];
+          for (int c = 0; c < MP; ++c) atomicAdd(out + (int64_t)(4 * q + a) * MP + c, (double)acc[a][c]);
+      }
     }
     return;
   }
@@ -1057,25 +1044,25 @@ __device__ void tail_qtr(const T* __restrict__ Q, const T* __restrict__ R, int64
         }
       }
     }
-    if (j < k)
+    if (j < k && cnt > 0)
 #pragma unroll
-      for (int c = 0; c < MP; ++c) out[(int64_t)j * MP + c] = (double)acc[c];
+      for (int c = 0; c < MP; ++c) atomicAdd(out + (int64_t)j * MP + c, (double)acc[c]);
   }
 }
 
 template <typename T, int MP>
 __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
   extern __shared__ unsigned char smem_raw[];
-  T* sT = reinterpret_cast<T*>(smem_raw);                         // s, column-major [MP][k]
+  T* sT = reinterpret_cast<T*>(smem_raw);                         // t, column-major [MP][k]
   T* Rs = sT + (size_t)a.k * MP;                                   // kFusedChunk x MP
   float* red = reinterpret_cast<float*>(Rs + (size_t)kFusedChunk * MP);
   __shared__ ColState snap[8];
-  __shared__ double sh_alpha[8], sh_beta[8];
+  __shared__ double sh_alpha[8], sh_beta[8], sh_pw[8], sh_rr[8], sh_rz[8];
   __shared__ int sh_act0[8], sh_actA[8], sh_actC[8], sh_actF[8];
-  __shared__ double sh_pw[8], sh_rr[8], sh_rz[8];
   __shared__ double redd[kFT / 32 * 8];
+  __shared__ unsigned sh_parity;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int G = gridDim.x, cta = blockIdx.x;
+  const int cta = blockIdx.x;
   const int k = a.k;
   const int64_t r0 = (int64_t)cta * a.rpc;
   const int cnt = (int)(r0 >= a.n ? 0 : (a.n - r0 < a.rpc ? a.n - r0 : a.rpc));
@@ -1084,34 +1071,37 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
     if (tid < MP) snap[tid] = a.cs[tid];
     sh_act0[tid] = (tid < MP) ? a.cs[tid].active : 0;
   }
+  if (tid == 0) sh_parity = *(volatile unsigned*)&a.bar->launches & 1u;
   __syncthreads();
   bool any = false;
 #pragma unroll
   for (int c = 0; c < MP; ++c) any |= sh_act0[c] != 0;
   if (!any) return;    // the same decision in every CTA
+  const size_t set = tail_set_doubles(k);
+  double* acc = a.acc + sh_parity * set;             // this launch's accumulators
+  double* nxt = a.acc + (sh_parity ^ 1u) * set;      // cleared here for the next launch
+  double* tacc = acc + 24;
 
-  // ---- A: p^T w
   double v[8];
+  // ---- A: p^T w
+  if (!a.alpha_ready) {
 #pragma unroll
-  for (int c = 0; c < 8; ++c) v[c] = 0.0;
-  for (int e = tid; e < cnt * MP; e += kFT) {
-    const int64_t g = r0 * MP + e;
-    const int c = e % MP;
-    const double x = (double)a.P[g] * (double)a.W[g];
+    for (int c = 0; c < 8; ++c) v[c] = 0.0;
+    for (int e = tid; e < cnt * MP; e += kFT) {
+      const int64_t g = r0 * MP + e;
+      const int c = e % MP;
+      const double x = (double)a.P[g] * (double)a.W[g];
 #pragma unroll
-    for (int cc = 0; cc < MP; ++cc)
-      if (cc == c) v[cc] += x;
-  }
-  block_sum_cols<kFT>(v, MP, redd);
-  if (tid == 0)
-    for (int c = 0; c < MP; ++c) a.part_pw[(int64_t)cta * 8 + c] = v[c];
-  if (!grid_barrier(a.bar, a.err)) return;
-
-  // ---- B: alpha, e and r, |r|^2 and Q^T r partials
-  if (wid < MP) {
-    const double pw = warp_sum_parts(a.part_pw, G, wid);
-    if (lane == 0) {
-      const int c = wid;
+      for (int cc = 0; cc < MP; ++cc)
+        if (cc == c) v[cc] += x;
+    }
+    block_sum_cols<kFT>(v, MP, redd);
+    if (tid == 0 && cnt > 0)
+      for (int c = 0; c < MP; ++c) atomicAdd(acc + c, v[c]);
+    if (!grid_barrier(a.bar, a.err)) return;
+    if (tid < MP) {
+      const int c = tid;
+      const double pw = __ldcg(acc + c);
       sh_pw[c] = pw;
       int act = sh_act0[c];
       double al = 0.0;
@@ -1122,8 +1112,17 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
       sh_alpha[c] = al;
       sh_actA[c] = act;
     }
+  } else if (tid < MP) {
+    // the product kernel formed alpha (and flagged a breakdown) already
+    sh_pw[tid] = snap[tid].pw;
+    sh_alpha[tid] = snap[tid].active ? snap[tid].alpha : 0.0;
+    sh_actA[tid] = snap[tid].active;
   }
+  if (cta == 0)
+    for (int e = tid; e < (int)set; e += kFT) nxt[e] = 0.0;
   __syncthreads();
+
+  // ---- B: e and r, |r|^2 and Q^T r
 #pragma unroll
   for (int c = 0; c < 8; ++c) v[c] = 0.0;
   for (int e = tid; e < cnt * MP; e += kFT) {
@@ -1138,80 +1137,37 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
       if (cc == c) v[cc] += (double)r * (double)r;
   }
   block_sum_cols<kFT>(v, MP, redd);
-  if (tid == 0)
-    for (int c = 0; c < MP; ++c) a.part_rr[(int64_t)cta * 8 + c] = v[c];
+  if (tid == 0 && cnt > 0)
+    for (int c = 0; c < MP; ++c) atomicAdd(acc + 8 + c, v[c]);
   __syncthreads();
-  tail_qtr<T, MP>(a.Q, a.R, r0, cnt, k, a.part_t + (int64_t)cta * k * MP, Rs, red);
+  tail_qtr<T, MP>(a.Q, a.R, r0, cnt, k, tacc, Rs, red);
   if (!grid_barrier(a.bar, a.err)) return;
 
-  // ---- C: convergence decision; t = sum of the Q^T r partials
-  if (wid < MP) {
-    const double rr = warp_sum_parts(a.part_rr, G, wid);
-    if (lane == 0) {
-      const int c = wid;
-      sh_rr[c] = rr;
-      int act = sh_actA[c];
-      if (act) {
-        const int it = snap[c].iters + 1;
-        if (!isfinite(rr) || rr <= snap[c].stop2 || it >= snap[c].budget) act = 0;
-      }
-      sh_actC[c] = act;
+  // ---- E: convergence decision; z = r + (Q H) t; r^T z
+  if (tid < MP) {
+    const int c = tid;
+    const double rr = __ldcg(acc + 8 + c);
+    sh_rr[c] = rr;
+    int act = sh_actA[c];
+    if (act) {
+      const int it = snap[c].iters + 1;
+      if (!isfinite(rr) || rr <= snap[c].stop2 || it >= snap[c].budget) act = 0;
     }
+    sh_actC[c] = act;
   }
-  {
-    const int len = k * MP;
-    for (int e = cta * (kFT / 32) + wid; e < len; e += G * (kFT / 32)) {
-      double s = 0.0;
-      for (int g = lane; g < G; g += 32) s += __ldcg(a.part_t + (int64_t)g * len + e);
+  for (int e0 = tid; e0 < k * MP; e0 += 8 * kFT) {
+    // eight loads in flight per thread, then the stores
+    double tv[8];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) a.tglob[e] = s;
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * kFT;
+      tv[u] = e < k * MP ? __ldcg(tacc + e) : 0.0;
     }
-  }
-  if (!grid_barrier(a.bar, a.err)) return;
-
-  // ---- D: s = H t; the CTA's rows of H (j = cta, cta + G, ...), one warp per
-  // row, with t staged in shared memory in pieces of kTPiece entries
-  {
-    double* tsh = reinterpret_cast<double*>(red);   // the Q^T r scratch is free now
-    const int nrows = (k - cta + G - 1) / G;         // rows of this CTA
-    for (int rb = 0; rb < nrows; rb += kFT / 32) {
-      const int jr = rb + wid;
-      const int j = cta + jr * G;
-      double acc[MP];
 #pragma unroll
-      for (int c = 0; c < MP; ++c) acc[c] = 0.0;
-      for (int l0 = 0; l0 < k; l0 += kTPiece) {
-        const int ll = min(kTPiece, k - l0);
-        __syncthreads();
-        for (int e = tid; e < ll * MP; e += kFT) tsh[e] = __ldcg(a.tglob + (int64_t)l0 * MP + e);
-        __syncthreads();
-        if (jr < nrows) {
-          const double* hj = a.H + (int64_t)j * k + l0;
-          for (int l = lane; l < ll; l += 32) {
-            const double h = hj[l];
-#pragma unroll
-            for (int c = 0; c < MP; ++c) acc[c] = fma(h, tsh[l * MP + c], acc[c]);
-          }
-        }
-      }
-      if (jr < nrows) {
-#pragma unroll
-        for (int c = 0; c < MP; ++c) {
-          double x = acc[c];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-          if (lane == 0) a.sglob[(int64_t)j * MP + c] = x;
-        }
-      }
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * kFT;
+      if (e < k * MP) sT[(e % MP) * k + e / MP] = (T)tv[u];
     }
-  }
-  if (!grid_barrier(a.bar, a.err)) return;
-
-  // ---- E: z = r + Q s over the CTA's rows, r^T z partials
-  for (int e = tid; e < k * MP; e += kFT) {
-    const int j = e / MP, c = e % MP;
-    sT[c * k + j] = (T)__ldcg(a.sglob + e);
   }
   __syncthreads();
   const int col = tr_col<MP>(lane);
@@ -1222,14 +1178,25 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
     // any arithmetic (eight 16-byte loads in flight for k <= 512)
     const int nq = k >> 2;
     const float4* s4 = reinterpret_cast<const float4*>(sT);
+    // with k <= 512 and MP <= 4 every lane keeps its quads of t in registers
+    constexpr int kTq = MP <= 4 ? MP : 1;
+    const bool treg = nq <= 128 && MP <= 4;
+    float4 tq[4][kTq];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int c = 0; c < kTq; ++c) {
+        const int jq = lane + 32 * u;
+        tq[u][c] = (treg && jq < nq) ? s4[c * nq + jq] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     for (int i = 2 * wid; i < cnt; i += 2 * (kFT / 32)) {
       const bool two = i + 1 < cnt;
       const int64_t row0 = r0 + i, row1 = two ? row0 + 1 : row0;
       float acc0[MP], acc1[MP];
 #pragma unroll
       for (int c = 0; c < MP; ++c) { acc0[c] = 0.f; acc1[c] = 0.f; }
-      const float4* qa = reinterpret_cast<const float4*>(a.Q + row0 * k);
-      const float4* qb = reinterpret_cast<const float4*>(a.Q + row1 * k);
+      const float4* qa = reinterpret_cast<const float4*>(a.QH + row0 * k);
+      const float4* qb = reinterpret_cast<const float4*>(a.QH + row1 * k);
       for (int jq0 = 0; jq0 < nq; jq0 += 128) {
         float4 va[4], vb[4];
 #pragma unroll
@@ -1244,7 +1211,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
           if (jq < nq) {
 #pragma unroll
             for (int c = 0; c < MP; ++c) {
-              const float4 sv = s4[c * nq + jq];
+              const float4 sv = treg ? tq[u][c % kTq] : s4[c * nq + jq];
               acc0[c] = fmaf(va[u].x, sv.x, fmaf(va[u].y, sv.y, fmaf(va[u].z, sv.z, fmaf(va[u].w, sv.w, acc0[c]))));
               acc1[c] = fmaf(vb[u].x, sv.x, fmaf(vb[u].y, sv.y, fmaf(vb[u].z, sv.z, fmaf(vb[u].w, sv.w, acc1[c]))));
             }
@@ -1271,16 +1238,16 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
   } else {
     for (int i = wid; i < cnt; i += kFT / 32) {
       const int64_t row = r0 + i;
-      T acc[MP];
+      T accr[MP];
 #pragma unroll
-      for (int c = 0; c < MP; ++c) acc[c] = (T)0;
-      const T* q = a.Q + row * k;
+      for (int c = 0; c < MP; ++c) accr[c] = (T)0;
+      const T* q = a.QH + row * k;
       for (int j = lane; j < k; j += 32) {
         const T qj = q[j];
 #pragma unroll
-        for (int c = 0; c < MP; ++c) acc[c] = fma(qj, sT[c * k + j], acc[c]);
+        for (int c = 0; c < MP; ++c) accr[c] = fma(qj, sT[c * k + j], accr[c]);
       }
-      const T sum = warp_transpose_reduce<MP>(acc, lane);
+      const T sum = warp_transpose_reduce<MP>(accr, lane);
       if (writer) {
         const int64_t idx = row * MP + col;
         const T r = a.R[idx];
@@ -1293,25 +1260,23 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) v[c] = (c == col && writer) ? dacc : 0.0;
   block_sum_cols<kFT>(v, MP, redd);
-  if (tid == 0)
-    for (int c = 0; c < MP; ++c) a.part_rz[(int64_t)cta * 8 + c] = v[c];
+  if (tid == 0 && cnt > 0)
+    for (int c = 0; c < MP; ++c) atomicAdd(acc + 16 + c, v[c]);
   if (!grid_barrier(a.bar, a.err)) return;
 
   // ---- F: beta, p = z + beta p
-  if (wid < MP) {
-    const double rz = warp_sum_parts(a.part_rz, G, wid);
-    if (lane == 0) {
-      const int c = wid;
-      sh_rz[c] = rz;
-      int act = sh_actC[c];
-      double be = snap[c].beta;
-      if (act) {
-        if (!(rz > 0.0 && isfinite(rz))) { act = 0; be = 0.0; }
-        else be = rz / snap[c].rho;
-      }
-      sh_beta[c] = be;
-      sh_actF[c] = act;
+  if (tid < MP) {
+    const int c = tid;
+    const double rz = __ldcg(acc + 16 + c);
+    sh_rz[c] = rz;
+    int act = sh_actC[c];
+    double be = snap[c].beta;
+    if (act) {
+      if (!(rz > 0.0 && isfinite(rz))) { act = 0; be = 0.0; }
+      else be = rz / snap[c].rho;
     }
+    sh_beta[c] = be;
+    sh_actF[c] = act;
   }
   __syncthreads();
   for (int e = tid; e < cnt * MP; e += kFT) {
@@ -1323,13 +1288,15 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
   if (cta == 0 && tid < MP) {
     const int c = tid;
     ColState st = snap[c];
-    st.pw = sh_pw[c];
     st.rr = sh_rr[c];
-    if (sh_act0[c]) {
-      if (!sh_actA[c]) { st.status = RR_ERR_BREAKDOWN; st.alpha = 0.0; }
-      else st.alpha = sh_alpha[c];
-    } else {
-      st.alpha = 0.0;
+    if (!a.alpha_ready) {
+      st.pw = sh_pw[c];
+      if (sh_act0[c]) {
+        if (!sh_actA[c]) { st.status = RR_ERR_BREAKDOWN; st.alpha = 0.0; }
+        else st.alpha = sh_alpha[c];
+      } else {
+        st.alpha = 0.0;
+      }
     }
     if (sh_actA[c]) {
       st.iters += 1;
@@ -1342,13 +1309,38 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
     st.active = sh_actF[c];
     a.cs[c] = st;
   }
+  if (cta == 0 && tid == 0) atomicAdd(&a.bar->launches, 1u);
 }
 
 template <typename T>
 size_t pcg_tail_smem(int k, int mp) {
-  size_t red = slab_red_floats(k, mp) * sizeof(float);
-  if (red < (size_t)kTPiece * mp * sizeof(double)) red = (size_t)kTPiece * mp * sizeof(double);
-  return (size_t)k * mp * sizeof(T) + (size_t)kFusedChunk * mp * sizeof(T) + red + 16;
+  return (size_t)k * mp * sizeof(T) + (size_t)kFusedChunk * mp * sizeof(T) +
+         slab_red_floats(k, mp) * sizeof(float) + 16;
+}
+
+// raise the kernel's dynamic shared-memory limit to the device maximum once
+// per device (outside any stream capture: called first from the build)
+template <typename T, int MP>
+static bool tail_attr() {
+  static std::atomic<uint64_t> done{0};
+  return once_per_device(done, [] {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return false;
+    // the dynamic limit is the opt-in maximum less the kernel's static shared memory
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_pcg_tail<T, MP>) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (cudaFuncSetAttribute(k_pcg_tail<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  });
 }
 
 // CTAs of the fused step: one per SM (at most n), or 0 when it cannot run
@@ -1360,6 +1352,14 @@ int pcg_tail_ctas(int64_t n, int k, int mp) {
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
   if (pcg_tail_smem<T>(k, mp) + 4096 > (size_t)optin) return 0;
+  bool attr = false;
+  switch (mp) {
+    case 1: attr = tail_attr<T, 1>(); break;
+    case 2: attr = tail_attr<T, 2>(); break;
+    case 4: attr = tail_attr<T, 4>(); break;
+    default: attr = tail_attr<T, 8>(); break;
+  }
+  if (!attr) return 0;
   int64_t g = sms;
   if (g > n) g = n;
   if (g > kFusedMaxCtas) g = kFusedMaxCtas;
@@ -1369,11 +1369,7 @@ int pcg_tail_ctas(int64_t n, int k, int mp) {
 template <typename T, int MP>
 static cudaError_t launch_tail(const TailArgs<T>& a, int G, size_t smem, cudaStream_t st) {
   auto kern = k_pcg_tail<T, MP>;
-  if (smem > 48 * 1024) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  if (!tail_attr<T, MP>()) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
   cfg.blockDim = dim3(kFT);
@@ -1388,18 +1384,14 @@ static cudaError_t launch_tail(const TailArgs<T>& a, int G, size_t smem, cudaStr
 }
 
 template <typename T>
-cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const double* H, int64_t n,
-                     int k, int mp, int G, double* scratch, ColState* cs, GridBar* bar, int* err,
-                     cudaStream_t st) {
+cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const T* QH, int64_t n,
+                     int k, int mp, int G, bool alpha_ready, double* scratch, ColState* cs,
+                     GridBar* bar, int* err, cudaStream_t st) {
   TailArgs<T> a;
-  a.E = E; a.R = R; a.P = P; a.Z = Z; a.W = W; a.Q = Q; a.H = H;
+  a.E = E; a.R = R; a.P = P; a.Z = Z; a.W = W; a.Q = Q; a.QH = QH;
   a.n = n; a.k = k; a.rpc = (int)cdiv(n, G);
-  a.part_pw = scratch;
-  a.part_rr = a.part_pw + (size_t)kFusedMaxCtas * 8;
-  a.part_rz = a.part_rr + (size_t)kFusedMaxCtas * 8;
-  a.tglob = a.part_rz + (size_t)kFusedMaxCtas * 8;
-  a.sglob = a.tglob + (size_t)k * 8;
-  a.part_t = a.sglob + (size_t)k * 8;
+  a.alpha_ready = alpha_ready ? 1 : 0;
+  a.acc = scratch;
   a.cs = cs; a.bar = bar; a.err = err;
   const size_t smem = pcg_tail_smem<T>(k, mp);
   switch (mp) {
@@ -1411,16 +1403,65 @@ cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const doubl
 }
 
 size_t pcg_tail_scratch_doubles(int k, int mp) {
-  return (size_t)kFusedMaxCtas * 8 * 3 + 2 * (size_t)k * 8 + (size_t)kFusedMaxCtas * k * mp;
+  (void)mp;
+  return 2 * tail_set_doubles(k);
+}
+
+// W = sum of the split partials + mu V (the kernel product's last step) with
+// the p^T w reduction of variant C fused in: alpha = rho / (p^T w), applied by
+// the last block (fixed order).  Skipped when no column is active.
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_sum_splits_alpha(const T* __restrict__ part, int nsplit,
+                                                          int64_t n, int mp, double mu,
+                                                          const T* __restrict__ V,
+                                                          T* __restrict__ W,
+                                                          double* __restrict__ rpart,
+                                                          unsigned* __restrict__ counter,
+                                                          ColState* __restrict__ cs) {
+  if (!any_active(cs, mp)) return;
+  __shared__ double red[kNT / 32 * 8];
+  double v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = 0.0;
+  const int64_t total = n * mp;
+  const int64_t stride = (int64_t)gridDim.x * kNT;
+  for (int64_t e = (int64_t)blockIdx.x * kNT + threadIdx.x; e < total; e += stride) {
+    T acc = (T)0;
+    for (int s = 0; s < nsplit; ++s) acc += part[(int64_t)s * total + e];
+    const T w = acc + (T)mu * V[e];
+    W[e] = w;
+    const int c = (int)(e % mp);
+    const double x = (double)V[e] * (double)w;
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc)
+      if (cc == c) v[cc] += x;
+  }
+  block_sum_cols<kNT>(v, mp, red);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < mp; ++c) rpart[(int64_t)blockIdx.x * mp + c] = v[c];
+  if (!last_block(counter)) return;
+  double tot[8];
+  sum_parts_block<kNT>(rpart, gridDim.x, mp, tot, red);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < mp; ++c) finish_mode(cs[c], kModeAlpha, tot[c]);
+}
+
+template <typename T>
+void sum_splits_alpha(const T* part, int nsplit, int64_t n, int mp, double mu, const T* V, T* W,
+                      double* rpart, unsigned* counter, ColState* cs, cudaStream_t st) {
+  const unsigned blocks = grid_rows(n * mp, kNT * 4);
+  k_sum_splits_alpha<T><<<blocks, kNT, 0, st>>>(part, nsplit, n, mp, mu, V, W, rpart, counter, cs);
 }
 
 template int pcg_tail_ctas<float>(int64_t, int, int);
 template int pcg_tail_ctas<double>(int64_t, int, int);
 template cudaError_t pcg_tail<float>(float*, float*, float*, float*, const float*, const float*,
-                                     const double*, int64_t, int, int, int, double*, ColState*,
-                                     GridBar*, int*, cudaStream_t);
+                                     const float*, int64_t, int, int, int, bool, double*,
+                                     ColState*, GridBar*, int*, cudaStream_t);
 template cudaError_t pcg_tail<double>(double*, double*, double*, double*, const double*,
-                                      const double*, const double*, int64_t, int, int, int,
+                                      const double*, const double*, int64_t, int, int, int, bool,
                                       double*, ColState*, GridBar*, int*, cudaStream_t);
+template void sum_splits_alpha<float>(const float*, int, int64_t, int, double, const float*,
+                                      float*, double*, unsigned*, ColState*, cudaStream_t);
 
 }  // namespace rr

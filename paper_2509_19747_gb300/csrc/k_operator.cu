@@ -11,6 +11,7 @@
 
 #include "df.cuh"
 #include "rr_common.cuh"
+#include "rr_krylov.cuh"
 
 namespace rr {
 
@@ -605,8 +606,12 @@ void kernel_mv<float>(const OpDev& op, double mu, const float* V, float* W, int 
     rec(ev, 0, st);
     if (kernel_mv_tc(op.amap, op.bmap, op.n, mp, V, part, nt, op.tc_err, op.gate, op.gate_mp, st)) {
       rec(ev, 1, st);
-      k_sum_splits<float><<<(unsigned)cdiv(op.n * mp, 256), 256, 0, st>>>(part, nt, op.n, mp, mu, V, W,
-                                                                          op.gate, op.gate_mp);
+      if (op.alpha_cs)
+        sum_splits_alpha<float>(part, nt, op.n, mp, mu, V, W, op.alpha_rpart, op.alpha_cnt,
+                                op.alpha_cs, st);
+      else
+        k_sum_splits<float><<<(unsigned)cdiv(op.n * mp, 256), 256, 0, st>>>(part, nt, op.n, mp, mu, V,
+                                                                            W, op.gate, op.gate_mp);
       return;
     }
   }
@@ -626,7 +631,11 @@ void kernel_mv<float>(const OpDev& op, double mu, const float* V, float* W, int 
   }
 #undef RR_KMV
   rec(ev, 1, st);
-  k_sum_splits<float><<<(unsigned)cdiv(op.n * mp, 256), 256, 0, st>>>(part, ns, op.n, mp, mu, V, W);
+  if (op.alpha_cs)
+    sum_splits_alpha<float>(part, ns, op.n, mp, mu, V, W, op.alpha_rpart, op.alpha_cnt, op.alpha_cs,
+                            st);
+  else
+    k_sum_splits<float><<<(unsigned)cdiv(op.n * mp, 256), 256, 0, st>>>(part, ns, op.n, mp, mu, V, W);
 }
 
 template <>

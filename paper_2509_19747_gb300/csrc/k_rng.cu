@@ -94,6 +94,37 @@ void gen_power_start(T* V, int64_t n, int mp, int col, int which, uint64_t seed,
   k_power_start<T><<<(unsigned)cdiv(n, 256), 256, 0, st>>>(V, n, mp, col, which, seed);
 }
 
+// Omega <- the product A X^T of a power step (eq:testmatrix), rounded like
+// the drawn test matrix: bf16 values (and the K-major bf16 copy) in the mixed
+// path, the working type otherwise
+template <typename T>
+__global__ void k_set_omega(const T* __restrict__ src, T* __restrict__ Om,
+                            __nv_bfloat16* __restrict__ Ob, int64_t n, int k, int round_bf16,
+                            int64_t ldo) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  const int64_t i = e / k;
+  const int j = (int)(e - i * k);
+  T v = src[e];
+  if (round_bf16) {
+    const __nv_bfloat16 b = __float2bfloat16_rn((float)v);
+    v = (T)__bfloat162float(b);
+    if (Ob) Ob[(int64_t)j * ldo + i] = b;
+  }
+  Om[e] = v;
+}
+
+template <typename T>
+void set_omega(const T* src, T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, int k,
+               bool round_bf16, cudaStream_t st) {
+  k_set_omega<T><<<(unsigned)cdiv(n * k, 256), 256, 0, st>>>(src, Om, OmT_bf16, n, k,
+                                                             round_bf16 ? 1 : 0, ldo);
+}
+template void set_omega<float>(const float*, float*, __nv_bfloat16*, int64_t, int64_t, int, bool,
+                               cudaStream_t);
+template void set_omega<double>(const double*, double*, __nv_bfloat16*, int64_t, int64_t, int,
+                                bool, cudaStream_t);
+
 template void gen_gaussian_omega<float>(float*, __nv_bfloat16*, int64_t, int64_t, int, uint64_t,
                                         bool, cudaStream_t);
 template void gen_gaussian_omega<double>(double*, __nv_bfloat16*, int64_t, int64_t, int, uint64_t,

@@ -135,12 +135,15 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
       // the preconditioner of Alg. 4 needs Q^T p, Q t and Pi p per step: not
       // provided without a basis
       if (o.variant != RR_VARIANT_C) return RR_ERR_UNSUPPORTED;
+      // the implicit Q applies Omega from its sparse pattern (q = 0 only)
+      if (o.q != 0) return RR_ERR_UNSUPPORTED;
       // Omega^T v partials and Omega s stage k x m values in shared memory
       if ((size_t)k * pad_mp(o.max_rhs) * (uses_f64(o) ? 8 : 4) > 200 * 1024) return RR_ERR_UNSUPPORTED;
     }
   }
   if (o.power_iters < 1 || o.power_iters > 1000) return RR_ERR_INVALID_ARG;
   if (o.iter_impl < 0 || o.iter_impl > 1) return RR_ERR_INVALID_ARG;
+  if (o.q < 0 || o.q > 4) return RR_ERR_INVALID_ARG;
   if (!(o.restart_eta > 0.0 && o.restart_eta < 1.0)) return RR_ERR_INVALID_ARG;
   switch (A->kind) {
     case RR_OP_DENSE:
@@ -787,6 +790,39 @@ void choose_tau(rr_handle* h) {
   }
 }
 
+// Y = A Omega + shift Omega (Alg. 7 step 1 with shift = mu; a power step of
+// eq:testmatrix with shift = 0), on the tensor cores where they apply
+template <typename T>
+rr_status sketch_product(rr_handle* h, double shift, bool tc, int64_t ldo) {
+  const int64_t n = h->n;
+  const int k = h->k;
+  cudaStream_t st = h->st;
+  const bool mixed = h->o.precision == RR_PREC_MIXED;
+  if (tc) {
+    RR_CUDA_TRY(cudaMemsetAsync(h->dstatus + 1, 0, sizeof(int), st));
+    const cudaEvent_t* ev = ev_take(h, RR_PROF_SKETCH);
+    if (ev) cudaEventRecord(ev[0], st);
+    const rr_status s = sketch_kernel_tc(h->op, shift, h->Omb, ldo, (const float*)h->Om,
+                                         (float*)h->Y, k, h->dstatus + 1, st);
+    if (ev) cudaEventRecord(ev[1], st);
+    if (s == RR_OK) {
+      int err = 0;
+      RR_TRY(read_int(h, h->dstatus + 1, &err));
+      if (err) return RR_ERR_TIMEOUT;
+      return RR_OK;
+    }
+    if (s != RR_ERR_UNSUPPORTED || h->o.kernel_impl == 2) return s;
+  }
+  (void)n;
+  if (h->op.kind == RR_OP_CSR && h->sketch == RR_SKETCH_SPARSE_SIGN && h->o.q == 0)
+    csr_sketch_sparse<T>(h->op, shift, h->ss_cols, h->ss_sgn, h->o.gamma, (T*)h->Y, k, st,
+                         ev_take(h, RR_PROF_SKETCH));
+  else
+    op_sketch<T>(h->op, shift, (const T*)h->Om, (T*)h->Y, k,
+                 mixed && h->op.kind == RR_OP_GAUSS_KERNEL, st, ev_take(h, RR_PROF_SKETCH));
+  return RR_OK;
+}
+
 template <typename T>
 rr_status build_impl(rr_handle* h) {
   const int64_t n = h->n;
@@ -822,30 +858,13 @@ rr_status build_impl(rr_handle* h) {
   // tensor cores for the mixed-precision Gaussian-kernel sketch (bf16 operands)
   const bool tc = mixed && h->op.kind == RR_OP_GAUSS_KERNEL && h->sketch == RR_SKETCH_GAUSSIAN &&
                   h->op.dim == 8 && h->o.kernel_impl != 1 && sizeof(T) == 4;
-  bool done_tc = false;
-  if (tc) {
-    RR_CUDA_TRY(cudaMemsetAsync(h->dstatus + 1, 0, sizeof(int), st));
-    const cudaEvent_t* ev = ev_take(h, RR_PROF_SKETCH);
-    if (ev) cudaEventRecord(ev[0], st);
-    const rr_status s = sketch_kernel_tc(h->op, h->mu, h->Omb, ldo, (const float*)h->Om,
-                                         (float*)h->Y, k, h->dstatus + 1, st);
-    if (ev) cudaEventRecord(ev[1], st);
-    if (s == RR_OK) {
-      int err = 0;
-      RR_TRY(read_int(h, h->dstatus + 1, &err));
-      if (err) return RR_ERR_TIMEOUT;
-      done_tc = true;
-    } else if (s != RR_ERR_UNSUPPORTED || h->o.kernel_impl == 2) {
-      return s;
-    }
+  // eq:testmatrix with q >= 1: Omega <- A Omega, q times (A, not A_mu), each
+  // product rounded like the drawn test matrix
+  for (int p = 0; p < h->o.q; ++p) {
+    RR_TRY(sketch_product<T>(h, 0.0, tc, ldo));
+    set_omega<T>((const T*)h->Y, (T*)h->Om, h->Omb, ldo, n, k, mixed, st);
   }
-  if (done_tc) {
-  } else if (h->op.kind == RR_OP_CSR && h->sketch == RR_SKETCH_SPARSE_SIGN)
-    csr_sketch_sparse<T>(h->op, h->mu, h->ss_cols, h->ss_sgn, h->o.gamma, (T*)h->Y, k, st,
-                         ev_take(h, RR_PROF_SKETCH));
-  else
-    op_sketch<T>(h->op, h->mu, (const T*)h->Om, (T*)h->Y, k,
-                 mixed && h->op.kind == RR_OP_GAUSS_KERNEL, st, ev_take(h, RR_PROF_SKETCH));
+  RR_TRY(sketch_product<T>(h, h->mu, tc, ldo));
   // M = sym(Omega^T Y_mu) = Omega^T A_mu Omega (C variant), before Y is reused
   if (h->o.variant == RR_VARIANT_C) {
     gram_partial<T>((const T*)h->Om, k, (const T*)h->Y, k, n, k, k, false, h->gsplit, h->gpart, st);
@@ -872,21 +891,16 @@ rr_status build_impl(rr_handle* h) {
                                   h->kk[kHb], (int64_t)k * k, 1, st);
     h->fusedG = (h->o.iter_impl == 0 && h->sketch == RR_SKETCH_SPARSE_SIGN)
                     ? pcg_implicit_ctas<T>(n, k, h->mp) : 0;
-    if (h->fusedG > 0) RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), st));
+    if (h->fusedG > 0) RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
   } else if (h->o.variant == RR_VARIANT_C) {
     // P = I + Q (tau G - I) Q^T = I + Q H Q^T
     form_H(h->kk[kG], h->tau, h->kk[kH], k, st);
     h->fusedG = (h->o.iter_impl == 0) ? pcg_tail_ctas<T>(n, k, h->mp) : 0;
-    if (h->fusedG > 0) {
-      // the fused step applies H to the k x m vector Q^T r and reads Q twice
-      // per iteration (one n x k matrix stays resident in L2)
-      RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), st));
-      h->QH = nullptr;
-    } else {
-      // separate kernels: keep QH = Q H so that z = r + QH (Q^T r)
-      h->QH = h->Y;
-      right_mult<T>(h, (const T*)h->Q, h->kk[kH], (T*)h->QH);
-    }
+    // keep QH = Q H so that z = r + QH (Q^T r)
+    h->QH = h->Y;
+    right_mult<T>(h, (const T*)h->Q, h->kk[kH], (T*)h->QH);
+    if (h->fusedG > 0)   // barrier and both accumulator sets start at zero
+      RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
   }
   return sync_status(h);
 }
@@ -916,13 +930,22 @@ void iter_C(rr_handle* h, const cudaEvent_t* ev) {
   const int mp = h->mp, k = h->k;
   T *Rv = vt<T>(h, kR), *Pv = vt<T>(h, kP), *Wv = vt<T>(h, kW), *Zv = vt<T>(h, kZ),
     *Ev = vt<T>(h, kE);
-  matvec<T>(h, Pv, Wv, ev);                                               // w = A_mu p
   if (h->fusedG > 0) {
-    // Alg. 7 steps 6-9 in one persistent cooperative launch
-    pcg_tail<T>(Ev, Rv, Pv, Zv, Wv, (const T*)h->Q, h->kk[kH], n, k, mp, h->fusedG, h->fscratch,
-                h->cs, h->bar, h->dstatus + 3, h->st);
+    // w = A_mu p (with alpha formed by the kernel-operator product where it
+    // can), then Alg. 7 steps 6-9 in one persistent cooperative launch
+    const bool alpha_ready = h->op.kind == RR_OP_GAUSS_KERNEL && sizeof(T) == 4;
+    if (alpha_ready) {
+      h->op.alpha_cs = h->cs;
+      h->op.alpha_rpart = h->rpart;
+      h->op.alpha_cnt = h->cnt;
+    }
+    matvec<T>(h, Pv, Wv, ev);
+    h->op.alpha_cs = nullptr;
+    pcg_tail<T>(Ev, Rv, Pv, Zv, Wv, (const T*)h->Q, (const T*)h->QH, n, k, mp, h->fusedG,
+                alpha_ready, h->fscratch, h->cs, h->bar, h->dstatus + 3, h->st);
     return;
   }
+  matvec<T>(h, Pv, Wv, ev);                                               // w = A_mu p
   dot_cols<T>(Pv, Wv, n, mp, kModeAlpha, h->rpart, h->cnt, h->cs, true, nullptr, h->st);
   update_qt<T>(Ev, Rv, Pv, Wv, (const T*)h->Q, n, k, mp, h->tpart, h->rpart, h->cnt, h->cs, h->st);
   reduce_slabs_gated(h->tpart, qt_nslab(n), k * mp, h->t[0], h->cs, mp, h->st);  // t = Q^T r
@@ -1258,6 +1281,7 @@ void rr_build_opts_default(rr_build_opts* o) {
   o->profile = 0;
   o->kernel_impl = 0;
   o->iter_impl = 0;
+  o->q = 0;
 }
 
 const char* randrand_status_str(rr_status s) {

@@ -78,6 +78,11 @@ struct OpDev {
   // kernel operator return at once if no column of gate[0..gate_mp) is active
   const ColState* gate;
   int gate_mp;
+  // when set (variant C with the persistent step), the float32 kernel-operator
+  // product also forms alpha = rho / (p^T w) into alpha_cs (V = p)
+  ColState* alpha_cs;
+  double* alpha_rpart;
+  unsigned* alpha_cnt;
 };
 
 // One-time host setup per device (function attributes): bit d of `mask` is
@@ -106,6 +111,10 @@ struct Coefs8s {
 template <typename T>
 void gen_gaussian_omega(T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, int k,
                         uint64_t seed, bool round_bf16, cudaStream_t st);
+// Omega <- src (a power step A X^T), bf16-rounded with its K-major copy if asked
+template <typename T>
+void set_omega(const T* src, T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, int k,
+               bool round_bf16, cudaStream_t st);
 void gen_sparse_sign(int32_t* cols, int8_t* sgn, int64_t nlines, int ncols, int gamma,
                      uint64_t seed, uint32_t stream_id, cudaStream_t st);
 template <typename T>

@@ -72,7 +72,8 @@ struct GridBar {
   unsigned pad0[31];
   unsigned gen;
   int abort;
-  unsigned pad1[30];
+  unsigned launches;   // launches of the fused step so far (accumulator parity)
+  unsigned pad1[29];
 };
 static_assert(sizeof(GridBar) == 256, "GridBar layout");
 constexpr int kFusedMaxCtas = 2 * 152;
@@ -81,9 +82,14 @@ template <typename T>
 int pcg_tail_ctas(int64_t n, int k, int mp);
 size_t pcg_tail_scratch_doubles(int k, int mp);
 template <typename T>
-cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const double* H, int64_t n,
-                     int k, int mp, int G, double* scratch, ColState* cs, GridBar* bar, int* err,
-                     cudaStream_t st);
+cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const T* QH, int64_t n,
+                     int k, int mp, int G, bool alpha_ready, double* scratch, ColState* cs,
+                     GridBar* bar, int* err, cudaStream_t st);
+// W = sum of split partials + mu V with alpha = rho / (p^T w) applied to cs
+// (variant C with the persistent step; V = p)
+template <typename T>
+void sum_splits_alpha(const T* part, int nsplit, int64_t n, int mp, double mu, const T* V, T* W,
+                      double* rpart, unsigned* counter, ColState* cs, cudaStream_t st);
 // Persistent basis-less PCG for CSR operators with a sparse-sign Omega
 // (k_implicit_fused.cu): `iters` iterations in one cooperative launch.
 size_t pcg_implicit_scratch_doubles(int k, int mp);

@@ -395,3 +395,55 @@ def test_fused_step_kernel_operator_mixed(cuda_lib, m):
         h.close()
     for a, b in zip(*its):
         assert abs(a - b) <= max(3, 0.05 * b)
+
+
+# ------------------------------------------- test matrix with power q = 1
+def test_power_q1_factors_fp64(cuda_lib):
+    """eq:testmatrix with q = 1 (Omega = A X^T): Omega, R, G, tau and the
+    power-iteration estimates equal the oracle's."""
+    rr = cuda_lib
+    n, k, mu = 700, 40, 1e-4
+    P, op = dense_problem(n)
+    h = rr.Handle(rr.Operator.dense(dev(P.A)), mu, k, "gaussian", seed=71, q=1, max_rhs=2)
+    bd = O.build(op, mu, k, "gaussian", seed=71, q=1)
+    assert rel(h.export("omega").cpu().numpy(), bd.Omega) <= 1e-13
+    cond = np.linalg.cond(bd.R)
+    assert rel(h.export("R").cpu().numpy(), bd.R) <= max(1e-12, 1e-15 * cond) * 100
+    tau, nE, lmax = h.scalars()
+    assert nE == pytest.approx(bd.normE, rel=1e-8)
+    # lambda_max (hence tau) goes through G = (R_M R^-1)^T (R_M R^-1): with q = 1
+    # cond(R) ~ 7e6 here, so the tolerance scales with u cond(R)
+    assert tau == pytest.approx(bd.tau, rel=max(1e-8, 1e-15 * cond) * 100)
+    B = W.gaussian_rhs(n, 2, 71)
+    x, status, infos = h.solve(dev(B), rtol=1e-12)
+    assert status == rr.RR_OK
+    assert rel(x.cpu().numpy(), O.exact_solve(op, mu, B)) <= 1e-8
+
+
+def test_power_q1_kernel_mixed(cuda_lib):
+    """q = 1 on the Gaussian-kernel operator (bf16 sketch products): the solve
+    meets rtol in the float64 residual and takes no more iterations than q = 0."""
+    rr = cuda_lib
+    n, k, mu = 3001, 60, 1e-3
+    X = W.mixture_points(n, seed=72)
+    op = O.GaussKernelOp(X)
+    B = W.gaussian_rhs(n, 2, 72)
+    its = {}
+    for q in (0, 1):
+        h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=72,
+                      precision="mixed", max_rhs=2, q=q)
+        x, status, infos = h.solve(dev(B), rtol=1e-6)
+        assert status == rr.RR_OK
+        assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), B) <= 1e-6)
+        its[q] = max(i["inner_iters"] for i in infos)
+        h.close()
+    assert its[1] <= its[0]
+
+
+def test_power_q_with_basis_less_unsupported(cuda_lib):
+    rr = cuda_lib
+    C = W.diffusion_csr(side=16, seed=73, corr_len=4.0)
+    op = rr.Operator.csr(dev(C.rowptr), dev(C.colidx), dev(C.vals.astype(np.float64)))
+    with pytest.raises(rr.RandRandError) as e:
+        rr.Handle(op, 1e-4, 8, "sparse_sign", seed=73, orth="rand_cholqr", q=1)
+    assert e.value.status == rr.RR_ERR_UNSUPPORTED

@@ -213,14 +213,16 @@ def test_core_matrix_G_equals_QT_Ainv_Q():
 # --------------------------------------------------------------------------
 # Special cases with closed-form spectra
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("q", [0, 1])
 @pytest.mark.parametrize("variant", ["C", "R"])
-def test_exact_eigenvector_deflation_spectrum(variant):
-    # Omega = U_k (exact top-k eigenvectors): Pi = U_k U_k^T and both the
-    # R-RandRAND operator B (eq:APdef2) and the C-RandRAND P A_mu have
-    # spectrum {tau (k times)} U {lambda_i + mu, i > k}
+def test_exact_eigenvector_deflation_spectrum(variant, q):
+    # X^T = U_k (exact top-k eigenvectors), Omega = A^q X^T spans the same
+    # space: Pi = U_k U_k^T and both the R-RandRAND operator B (eq:APdef2)
+    # and the C-RandRAND P A_mu have spectrum {tau (k times)} U
+    # {lambda_i + mu, i > k}
     P, op = small_dense(n=120)
     k, mu = 10, 1e-3
-    bd = O.build(op, mu, k, omega=P.U[:, :k], variant=variant)
+    bd = O.build(op, mu, k, omega=P.U[:, :k], variant=variant, q=q)
     I = np.eye(op.n)
     if variant == "C":
         M = bd.apply_P(I) @ (op.A + mu * I)
@@ -237,6 +239,27 @@ def test_exact_eigenvector_deflation_spectrum(variant):
     # |E| = lambda_{k+1} + mu is approached from below by the power iteration
     assert bd.normE <= (P.lam[k] + mu) * (1 + 1e-12)
     assert bd.normE >= 0.5 * (P.lam[k] + mu)
+
+
+def test_subspace_iteration_test_matrix():
+    # eq:testmatrix with q = 1: Omega = A X^T (A, not A_mu), and the basis
+    # A_mu Omega deflates the spectrum closer to the optimum lambda_{k+1} + mu
+    # than q = 0 (range approximation of Sec. 4 with one power; power-law
+    # spectra, same X)
+    for power in (1.0, 2.0):
+        P, op = small_dense(n=400, power=power)
+        k, mu = 20, 1e-4
+        X = O.make_omega(op.n, k, "gaussian", seed=8)
+        assert np.allclose(O.make_omega(op.n, k, "gaussian", seed=8, q=1, op=op), op.A @ X,
+                           rtol=0, atol=1e-14)
+        ratios = []
+        for q in (0, 1):
+            bd = O.build(op, mu, k, "gaussian", seed=8, q=q)
+            I = np.eye(op.n)
+            E = (I - bd.Pi(I)) @ (op.A + mu * I) @ (I - bd.Pi(I))
+            ratios.append(np.linalg.norm(E, 2) / (P.lam[k] + mu))
+        assert 1.0 <= ratios[1] < ratios[0]
+        assert ratios[1] <= 1.8
 
 
 @pytest.mark.parametrize("variant", ["C", "R"])
