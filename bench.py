@@ -47,6 +47,11 @@ WORKLOAD = dict(workload="gaussian_kernel_ridge", n=20000, d=8, components=10, m
                 nrhs=4, rtol=1e-6, bandwidth=1.0, sketch="gaussian", precision="mixed",
                 variant="C", seed=0x52522)
 METRIC = "RandRAND-PCG solves/s to rtol 1e-6 vs plain form on 1 GB300; p50/p99 latency"
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
+# stands (summaries in profiles/: k_kernel_mv_tc_kernel_ridge_n20000.md,
+# k_pcg_implicit_sparse_diffusion_512.md, the latter per iteration of a
+# 256-iteration launch)
+TRAFFIC = {"k_kernel_mv_tc": 5.512192e6, "k_pcg_implicit": (28.928768e6 + 1.673472e6) / 256}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -391,7 +396,8 @@ def roofline(name, stat, clocks):
         peak = 152 * 16 * f
         return {"kernel": "k_kernel_mv_tc", "bound": "alu", "achieved": ops / avg_s / 1e9,
                 "peak": peak / 1e9, "unit": "G ex2/s (MUFU)", "frac": ops / avg_s / peak,
-                "traffic": None, "launches": cnt, "avg_us": avg_s * 1e6}
+                "traffic": TRAFFIC["k_kernel_mv_tc"], "launches": cnt, "avg_us": avg_s * 1e6,
+                "peak_note": "derived: 152 SMs x 16 ex2 per clock x sampled max SM clock"}
     if name == "residual":
         # double-float restart residual: ~190 float32-pipe ops per entry
         ops = float(n) * n * 190
@@ -551,13 +557,15 @@ def run_sparse(args):
         bytes_ = 3 * (8.0 * len(C.vals) + 4.0 * (C.n + 1) + 2 * 4.0 * C.n * mp) \
             + 2 * 5.0 * cfg["gamma"] * C.n + 10 * 4.0 * C.n * mp
         kern, unit_note = "k_pcg_implicit (per iteration)", "iterations"
+        traffic = TRAFFIC["k_pcg_implicit"]
     else:
         per_s = tot / 1000.0 / max(cnt, 1)
         bytes_ = 8.0 * len(C.vals) + 4.0 * (C.n + 1) + 2 * 4.0 * C.n * mp
         kern, unit_note = "k_csr_mv_add", "launches"
+        traffic = None
     roof = {"kernel": kern, "bound": "hbm", "achieved": bytes_ / per_s / 1e9,
             "peak": peaks["hbm"], "unit": "GB/s", "frac": bytes_ / per_s / 1e9 / peaks["hbm"],
-            "traffic": None, "launches": cnt, "avg_us": per_s * 1e6, "per": unit_note,
+            "traffic": traffic, "launches": cnt, "avg_us": per_s * 1e6, "per": unit_note,
             "algorithmic_bytes": bytes_,
             "note": "the working set of one iteration stays in L2 between iterations"}
     line = _line(args, world, "RandRAND-PCG solves/s to rtol 1e-6 (sparse diffusion 512^2)",
