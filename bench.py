@@ -391,13 +391,14 @@ def roofline(name, stat, clocks):
     if name in ("matvec", "power"):
         # tensor-core float32 kernel product: the exponent arguments come from
         # the tensor cores, so each of the n^2 entries needs exactly one ex2 on
-        # the special-function units (MUFU): peak 152 SMs x 16 ex2/clk x clock
+        # the special-function units (MUFU): peak 152 SMs x 32 ex2/clk x clock
+        # (a throughput probe measured 30.2 ex2 per SM per clock on this part)
         ops = float(n) * n
-        peak = 152 * 16 * f
+        peak = 152 * 32 * f
         return {"kernel": "k_kernel_mv_tc", "bound": "alu", "achieved": ops / avg_s / 1e9,
                 "peak": peak / 1e9, "unit": "G ex2/s (MUFU)", "frac": ops / avg_s / peak,
                 "traffic": TRAFFIC["k_kernel_mv_tc"], "launches": cnt, "avg_us": avg_s * 1e6,
-                "peak_note": "derived: 152 SMs x 16 ex2 per clock x sampled max SM clock"}
+                "peak_note": "derived: 152 SMs x 32 ex2 per clock x sampled max SM clock"}
     if name == "residual":
         # double-float restart residual: ~190 float32-pipe ops per entry
         ops = float(n) * n * 190

@@ -1426,8 +1426,14 @@ __global__ void __launch_bounds__(kNT) k_sum_splits_alpha(const T* __restrict__ 
   const int64_t total = n * mp;
   const int64_t stride = (int64_t)gridDim.x * kNT;
   for (int64_t e = (int64_t)blockIdx.x * kNT + threadIdx.x; e < total; e += stride) {
+    // the split partials of one entry, all loads in flight together
+    T pv[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) pv[s] = s < nsplit ? part[(int64_t)s * total + e] : (T)0;
     T acc = (T)0;
-    for (int s = 0; s < nsplit; ++s) acc += part[(int64_t)s * total + e];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) acc += pv[s];
+    for (int s = 16; s < nsplit; ++s) acc += part[(int64_t)s * total + e];
     const T w = acc + (T)mu * V[e];
     W[e] = w;
     const int c = (int)(e % mp);
@@ -1449,7 +1455,7 @@ __global__ void __launch_bounds__(kNT) k_sum_splits_alpha(const T* __restrict__ 
 template <typename T>
 void sum_splits_alpha(const T* part, int nsplit, int64_t n, int mp, double mu, const T* V, T* W,
                       double* rpart, unsigned* counter, ColState* cs, cudaStream_t st) {
-  const unsigned blocks = grid_rows(n * mp, kNT * 4);
+  const unsigned blocks = grid_rows(n * mp, kNT);   // one entry per thread
   k_sum_splits_alpha<T><<<blocks, kNT, 0, st>>>(part, nsplit, n, mp, mu, V, W, rpart, counter, cs);
 }
 

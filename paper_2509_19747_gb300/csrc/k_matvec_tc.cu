@@ -200,14 +200,26 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
       const uint32_t vs = smem_u32(sm->v[sv]) + (uint32_t)(cq * (kPts / 4) * MP * 4);
       const uint32_t tb0 = tmem + ((uint32_t)(q * 32) << 16) +
                            (uint32_t)(buf * kPts + cq * (kPts / 4));
+      // the TMEM loads of the second chunk are in flight while the first is
+      // consumed
+      uint32_t ra0[16], rb0[16], ra1[16], rb1[16];
+      tmem_ld16_nowait(tb0, ra0);                       // row block 0, chunk 0
+      tmem_ld16_nowait(tb0 + 256u, rb0);                // row block 1, chunk 0
+      tmem_wait_ld();
+      reg_fence16(ra0);
+      reg_fence16(rb0);
+      tmem_ld16_nowait(tb0 + 16u, ra1);
+      tmem_ld16_nowait(tb0 + 256u + 16u, rb1);
 #pragma unroll
-      for (int ch = 0; ch < kPts / 4 / 16; ++ch) {
-        uint32_t ra[16], rb[16];
-        tmem_ld16_nowait(tb0 + (uint32_t)(ch * 16), ra);          // row block 0
-        tmem_ld16_nowait(tb0 + 256u + (uint32_t)(ch * 16), rb);   // row block 1
-        tmem_wait_ld();
-        reg_fence16(ra);
-        reg_fence16(rb);
+      for (int ch = 0; ch < 2; ++ch) {
+        static_assert(kPts / 4 / 16 == 2, "two 16-column chunks per warp and tile");
+        if (ch == 1) {
+          tmem_wait_ld();
+          reg_fence16(ra1);
+          reg_fence16(rb1);
+        }
+        uint32_t(&ra)[16] = ch ? ra1 : ra0;
+        uint32_t(&rb)[16] = ch ? rb1 : rb0;
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
           const float k0 = ex2_approx(__uint_as_float(ra[u]));
