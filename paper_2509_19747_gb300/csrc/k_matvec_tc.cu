@@ -10,7 +10,8 @@
 // rows [u_hi u_hi u_lo 0 0] with [w_hi w_lo w_hi 0 0]: K = 32 (one 128-byte
 // swizzle atom per row), four tcgen05.mma kind::tf32 instructions.
 //
-// CTA: two blocks of 128 rows (TMEM lanes) x a range of points, in tiles of
+// Persistent CTAs (one per SM) take work units round-robin: a unit is two
+// blocks of 128 rows (TMEM lanes) x a range of points, in tiles of
 // 128 points; per tile the MMA writes 128 x 128 exponent arguments per row
 // block into TMEM (double-buffered: 2 row blocks x 2 buffers x 128 columns =
 // all 512 columns), and 16 epilogue warps read them with tcgen05.ld.  A warp
@@ -18,9 +19,10 @@
 // one quarter of the tile's columns, so each v_j it loads from shared memory
 // (LDS broadcast) feeds two kernel entries; it applies ex2 (MUFU) and
 // accumulates w_i += K_ij v_j in registers.  The four column quarters of a
-// row are merged once at the end.
-//   warp 0   TMA: augmented row blocks (once), point tiles (4 stages), and
-//            the matching rows of v (bulk copy, 4 stages);
+// row are merged at the end of each unit through shared memory.
+//   warp 0   TMA: augmented row blocks (double-buffered across units),
+//            point tiles (4 stages), and the matching rows of v (bulk copy,
+//            4 stages);
 //   warp 1   TMEM allocation; one thread issues the MMAs and commits;
 //   warps 2-17 epilogue.
 // All waits are bounded (error flag instead of a hang).
@@ -47,32 +49,49 @@ constexpr int kEpiWarps = 16;          // 4 per SM sub-partition
 constexpr int kThreadsMv = 32 * (2 + kEpiWarps);
 constexpr int kAtomA = kRows * 128;  // a row block (16 KB)
 constexpr int kAtomB = kPts * 128;   // a point tile (16 KB)
-constexpr int kABytes = kRB * kAtomA;        // 32 KB
+constexpr int kABytes = kRB * kAtomA;        // 32 KB per unit (two buffers)
 constexpr int kBBytes = kAtomB;              // 16 KB per stage
 constexpr uint32_t kTmemCols = 512;
 
 template <int MP>
 struct MvSmem {
   float v[kStagesV][kPts * MP];
-  float quarter[3][kRB * kRows][MP];   // column-quarter partial sums merged at the end
-  unsigned long long a_full;
+  float quarter[3][kRB * kRows][MP];   // column-quarter partial sums merged per unit
+  unsigned long long a_full[2], a_empty[2];
   unsigned long long b_full[kStagesB], b_empty[kStagesB];
   unsigned long long v_full[kStagesV], v_empty[kStagesV];
   unsigned long long t_full[2], t_empty[2];
+  unsigned long long q_full, q_empty;  // the quarters of a unit written / read
   uint32_t tmem_base;
   int abort;
 };
 
 template <int MP>
 constexpr size_t mv_smem_bytes() {
-  return 1024 + (size_t)kABytes + (size_t)kStagesB * kBBytes + sizeof(MvSmem<MP>);
+  return 1024 + 2 * (size_t)kABytes + (size_t)kStagesB * kBBytes + sizeof(MvSmem<MP>);
+}
+
+// unit u of a launch: row pair u / nsplit, point range (split) u % nsplit
+struct MvUnit {
+  int64_t row0, j0, j1;
+  int split, ntiles;
+};
+__device__ __forceinline__ MvUnit mv_unit(int64_t u, int nsplit, int64_t pts_per_split, int64_t n) {
+  MvUnit w;
+  w.split = (int)(u % nsplit);
+  w.row0 = (u / nsplit) * (kRows * kRB);
+  w.j0 = (int64_t)w.split * pts_per_split;
+  w.j1 = w.j0 + pts_per_split;
+  if (w.j1 > n) w.j1 = n;
+  w.ntiles = (w.j1 > w.j0) ? (int)((w.j1 - w.j0 + kPts - 1) / kPts) : 0;
+  return w;
 }
 
 template <int MP>
 __global__ void __launch_bounds__(kThreadsMv, 1)
     k_kernel_mv_tc(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
-                   int64_t n, int64_t pts_per_split, const float* __restrict__ V,
-                   float* __restrict__ part, int* __restrict__ err,
+                   int64_t n, int64_t pts_per_split, int nsplit, int64_t nunits,
+                   const float* __restrict__ V, float* __restrict__ part, int* __restrict__ err,
                    const ColState* __restrict__ gate, int gate_mp) {
   if (gate) {
     // inside the Krylov iterations: nothing to do once every column is done
@@ -82,22 +101,20 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
   }
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = base;
-  unsigned char* sB = base + kABytes;
+  unsigned char* sA = base;                                   // two unit buffers
+  unsigned char* sB = base + 2 * (size_t)kABytes;
   MvSmem<MP>* sm = (MvSmem<MP>*)(sB + (size_t)kStagesB * kBBytes);
   volatile int* abort = &sm->abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t row0 = (int64_t)blockIdx.x * (kRows * kRB);
-  const int64_t j0 = (int64_t)blockIdx.y * pts_per_split;
-  int64_t j1 = j0 + pts_per_split;
-  if (j1 > n) j1 = n;
-  const int ntiles = (j1 > j0) ? (int)((j1 - j0 + kPts - 1) / kPts) : 0;
   constexpr uint32_t kVBytes = kPts * MP * 4;
   constexpr uint32_t idesc = make_idesc(kFmtTF32, kRows, kPts);
 
   if (threadIdx.x == 0) {
-    mbar_init(&sm->a_full, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&sm->a_full[s], 1);
+      mbar_init(&sm->a_empty[s], 1);
+    }
     for (int s = 0; s < kStagesB; ++s) {
       mbar_init(&sm->b_full[s], 1);
       mbar_init(&sm->b_empty[s], 1);
@@ -110,6 +127,8 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
       mbar_init(&sm->t_full[s], 1);
       mbar_init(&sm->t_empty[s], kEpiWarps);
     }
+    mbar_init(&sm->q_full, kEpiWarps - 4);
+    mbar_init(&sm->q_empty, 4);
     sm->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -118,41 +137,46 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = sm->tmem_base;
-  float acc[MP], acc1[MP];                     // epilogue warps: partial sums of two rows
-  constexpr int kP2 = MP >= 2 ? MP / 2 : 1;
-  unsigned long long acc2[kP2], acc12[kP2];     // the same as packed column pairs (MP >= 2)
-#pragma unroll
-  for (int c = 0; c < MP; ++c) {
-    acc[c] = 0.f;
-    acc1[c] = 0.f;
-  }
-#pragma unroll
-  for (int c = 0; c < kP2; ++c) {
-    acc2[c] = 0ull;
-    acc12[c] = 0ull;
-  }
 
+  // every role walks the same units (u = blockIdx.x, + gridDim.x, ...) and
+  // counts this CTA's units (k) and tiles (T) for stage indices and parities
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    if (lane == 0 && ntiles > 0) {
-      mbar_arrive_tx(&sm->a_full, kABytes);
-      for (int b = 0; b < kRB; ++b)
-        tma_load_2d(sA + (size_t)b * kAtomA, &amap, 0, (int)(row0 + b * kRows), &sm->a_full);
-      int issued_b = 0, issued_v = 0;
-      for (int t = 0; t < ntiles; ++t) {
-        const int sb = t % kStagesB, sv = t % kStagesV;
-        const int64_t jt = j0 + (int64_t)t * kPts;
-        if (t >= kStagesB && !mbar_wait(&sm->b_empty[sb], ((t / kStagesB) - 1) & 1, err, abort)) break;
-        mbar_arrive_tx(&sm->b_full[sb], kBBytes);
-        tma_load_2d(sB + (size_t)sb * kBBytes, &bmap, 0, (int)jt, &sm->b_full[sb]);
-        ++issued_b;
-        if (t >= kStagesV && !mbar_wait(&sm->v_empty[sv], ((t / kStagesV) - 1) & 1, err, abort)) break;
-        mbar_arrive_tx(&sm->v_full[sv], kVBytes);
-        bulk_load(sm->v[sv], V + jt * MP, kVBytes, &sm->v_full[sv]);
-        ++issued_v;
+    if (lane == 0) {
+      int issued_a = 0, issued_b = 0, issued_v = 0;
+      int T = 0, k = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++k) {
+        const MvUnit w = mv_unit(u, nsplit, pts_per_split, n);
+        const int ab = k & 1;
+        if (k >= 2 && !mbar_wait(&sm->a_empty[ab], ((k >> 1) - 1) & 1, err, abort)) break;
+        mbar_arrive_tx(&sm->a_full[ab], kABytes);
+        for (int b = 0; b < kRB; ++b)
+          tma_load_2d(sA + (size_t)ab * kABytes + (size_t)b * kAtomA, &amap, 0,
+                      (int)(w.row0 + b * kRows), &sm->a_full[ab]);
+        ++issued_a;
+        for (int t = 0; t < w.ntiles; ++t, ++T) {
+          const int sb = T % kStagesB, sv = T % kStagesV;
+          const int64_t jt = w.j0 + (int64_t)t * kPts;
+          if (T >= kStagesB && !mbar_wait(&sm->b_empty[sb], ((T / kStagesB) - 1) & 1, err, abort)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_tx(&sm->b_full[sb], kBBytes);
+          tma_load_2d(sB + (size_t)sb * kBBytes, &bmap, 0, (int)jt, &sm->b_full[sb]);
+          ++issued_b;
+          if (T >= kStagesV && !mbar_wait(&sm->v_empty[sv], ((T / kStagesV) - 1) & 1, err, abort)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_tx(&sm->v_full[sv], kVBytes);
+          bulk_load(sm->v[sv], V + jt * MP, kVBytes, &sm->v_full[sv]);
+          ++issued_v;
+        }
       }
       // no bulk copy may still be writing shared memory when the CTA exits
-      mbar_wait(&sm->a_full, 0, err, abort);
+      for (int a = (issued_a > 2 ? issued_a - 2 : 0); a < issued_a; ++a)
+        mbar_wait(&sm->a_full[a & 1], (a >> 1) & 1, err, abort);
       for (int t = (issued_b > kStagesB ? issued_b - kStagesB : 0); t < issued_b; ++t)
         mbar_wait(&sm->b_full[t % kStagesB], (t / kStagesB) & 1, err, abort);
       for (int t = (issued_v > kStagesV ? issued_v - kStagesV : 0); t < issued_v; ++t)
@@ -160,28 +184,35 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
     }
   } else if (warp == 1) {
     // ----------------------------------------------------------------- MMA
-    if (lane == 0 && ntiles > 0) {
-      bool ok = mbar_wait(&sm->a_full, 0, err, abort);
-      for (int t = 0; t < ntiles && ok; ++t) {
-        const int sb = t % kStagesB, buf = t & 1;
-        ok = mbar_wait(&sm->b_full[sb], (t / kStagesB) & 1, err, abort);
-        if (ok && t >= 2) ok = mbar_wait(&sm->t_empty[buf], ((t >> 1) - 1) & 1, err, abort);
-        if (!ok) break;
-        fence_after();
-        const uint32_t bbase = smem_u32(sB + (size_t)sb * kBBytes);
-        for (int b = 0; b < kRB; ++b) {
-          const uint32_t abase = smem_u32(sA + (size_t)b * kAtomA);
-          const uint32_t d = tmem + (uint32_t)(b * 256 + buf * kPts);
+    if (lane == 0) {
+      bool ok = true;
+      int T = 0, k = 0;
+      for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++k) {
+        const MvUnit w = mv_unit(u, nsplit, pts_per_split, n);
+        const int ab = k & 1;
+        ok = mbar_wait(&sm->a_full[ab], (k >> 1) & 1, err, abort);
+        for (int t = 0; t < w.ntiles && ok; ++t, ++T) {
+          const int sb = T % kStagesB, buf = T & 1;
+          ok = mbar_wait(&sm->b_full[sb], (T / kStagesB) & 1, err, abort);
+          if (ok && T >= 2) ok = mbar_wait(&sm->t_empty[buf], ((T >> 1) - 1) & 1, err, abort);
+          if (!ok) break;
+          fence_after();
+          const uint32_t bbase = smem_u32(sB + (size_t)sb * kBBytes);
+          for (int b = 0; b < kRB; ++b) {
+            const uint32_t abase = smem_u32(sA + (size_t)ab * kABytes + (size_t)b * kAtomA);
+            const uint32_t d = tmem + (uint32_t)(b * 256 + buf * kPts);
 #pragma unroll
-          for (int kk = 0; kk < kKSteps; ++kk) {
-            const uint32_t off = (uint32_t)kk * 32;   // 8 tf32 values inside the atom row
-            const uint64_t ad = umma_desc_sw128(abase + off);
-            const uint64_t bd = umma_desc_sw128(bbase + off);
-            mma_tf32(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+            for (int kk = 0; kk < kKSteps; ++kk) {
+              const uint32_t off = (uint32_t)kk * 32;   // 8 tf32 values inside the atom row
+              const uint64_t ad = umma_desc_sw128(abase + off);
+              const uint64_t bd = umma_desc_sw128(bbase + off);
+              mma_tf32(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+            }
           }
+          mma_commit(&sm->b_empty[sb]);
+          mma_commit(&sm->t_full[buf]);
         }
-        mma_commit(&sm->b_empty[sb]);
-        mma_commit(&sm->t_full[buf]);
+        if (ok) mma_commit(&sm->a_empty[ab]);    // the unit's row blocks are free once its MMAs end
       }
     }
   } else {
@@ -189,93 +220,136 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
     const int e = warp - 2;                     // 0 .. 15
     const int q = warp & 3;                     // TMEM lane quarter of this warp
     const int cq = e >> 2;                      // column quarter of each tile
+    const int r = q * 32 + lane;                // row within each row block
+    constexpr int kP2 = MP >= 2 ? MP / 2 : 1;
     bool ok = true;
-    for (int t = 0; t < ntiles; ++t) {
-      const int buf = t & 1, sv = t % kStagesV;
-      ok = ok && mbar_wait(&sm->t_full[buf], (t >> 1) & 1, err, abort);
-      ok = ok && mbar_wait(&sm->v_full[sv], (t / kStagesV) & 1, err, abort);
-      ok = __all_sync(0xffffffffu, ok);            // tcgen05.ld is warp-collective
-      if (!ok) break;
-      fence_after();
-      const uint32_t vs = smem_u32(sm->v[sv]) + (uint32_t)(cq * (kPts / 4) * MP * 4);
-      const uint32_t tb0 = tmem + ((uint32_t)(q * 32) << 16) +
-                           (uint32_t)(buf * kPts + cq * (kPts / 4));
-      // the TMEM loads of the second chunk are in flight while the first is
-      // consumed
-      uint32_t ra0[16], rb0[16], ra1[16], rb1[16];
-      tmem_ld16_nowait(tb0, ra0);                       // row block 0, chunk 0
-      tmem_ld16_nowait(tb0 + 256u, rb0);                // row block 1, chunk 0
-      tmem_wait_ld();
-      reg_fence16(ra0);
-      reg_fence16(rb0);
-      tmem_ld16_nowait(tb0 + 16u, ra1);
-      tmem_ld16_nowait(tb0 + 256u + 16u, rb1);
-#pragma unroll
-      for (int ch = 0; ch < 2; ++ch) {
-        static_assert(kPts / 4 / 16 == 2, "two 16-column chunks per warp and tile");
-        if (ch == 1) {
-          tmem_wait_ld();
-          reg_fence16(ra1);
-          reg_fence16(rb1);
-        }
-        uint32_t(&ra)[16] = ch ? ra1 : ra0;
-        uint32_t(&rb)[16] = ch ? rb1 : rb0;
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const float k0 = ex2_approx(__uint_as_float(ra[u]));
-          const float k1 = ex2_approx(__uint_as_float(rb[u]));
-          const uint32_t vj = vs + (uint32_t)((ch * 16 + u) * MP * 4);
-          if (MP >= 2) {
-            // packed pair FMAs: the accumulators of columns (2c, 2c+1) share
-            // one fma.rn.f32x2 with the entry broadcast to both halves
-            const unsigned long long kk0 = pk2(k0, k0), kk1 = pk2(k1, k1);
-#pragma unroll
-            for (int c2 = 0; c2 < MP / 2; c2 += 2) {
-              unsigned long long va, vb = 0;
-              if (MP == 2) {
-                va = lds64u(vj);
-              } else {
-                const ulonglong2 v = lds128u(vj + (uint32_t)(c2 * 8));
-                va = v.x;
-                vb = v.y;
-              }
-              ffma2(acc2[c2], kk0, va);
-              ffma2(acc12[c2], kk1, va);
-              if (MP > 2) {
-                ffma2(acc2[c2 + 1], kk0, vb);
-                ffma2(acc12[c2 + 1], kk1, vb);
-              }
-            }
-          } else {
-            const float v1 = lds32(vj);
-            acc[0] = fmaf(k0, v1, acc[0]);
-            acc1[0] = fmaf(k1, v1, acc1[0]);
-          }
-        }
-      }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&sm->t_empty[buf]);
-        mbar_arrive(&sm->v_empty[sv]);
-      }
-    }
-    if (MP >= 2) {
-#pragma unroll
-      for (int c = 0; c < kP2; ++c) {
-        const float2 a0 = upk2(acc2[c]), a1 = upk2(acc12[c]);
-        acc[(2 * c) % MP] = a0.x;
-        acc[(2 * c + 1) % MP] = a0.y;
-        acc1[(2 * c) % MP] = a1.x;
-        acc1[(2 * c + 1) % MP] = a1.y;
-      }
-    }
-    if (cq > 0) {
-      const int r = q * 32 + lane;
+    int T = 0, k = 0;
+    for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++k) {
+      const MvUnit w = mv_unit(u, nsplit, pts_per_split, n);
+      float acc[MP], acc1[MP];                  // partial sums of this thread's two rows
+      unsigned long long acc2[kP2], acc12[kP2]; // the same as packed column pairs (MP >= 2)
 #pragma unroll
       for (int c = 0; c < MP; ++c) {
-        sm->quarter[cq - 1][r][c] = ok ? acc[c] : 0.f;
-        sm->quarter[cq - 1][kRows + r][c] = ok ? acc1[c] : 0.f;
+        acc[c] = 0.f;
+        acc1[c] = 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < kP2; ++c) {
+        acc2[c] = 0ull;
+        acc12[c] = 0ull;
+      }
+      for (int t = 0; t < w.ntiles; ++t, ++T) {
+        const int buf = T & 1, sv = T % kStagesV;
+        ok = ok && mbar_wait(&sm->t_full[buf], (T >> 1) & 1, err, abort);
+        ok = ok && mbar_wait(&sm->v_full[sv], (T / kStagesV) & 1, err, abort);
+        ok = __all_sync(0xffffffffu, ok);            // tcgen05.ld is warp-collective
+        if (!ok) break;
+        fence_after();
+        const uint32_t vs = smem_u32(sm->v[sv]) + (uint32_t)(cq * (kPts / 4) * MP * 4);
+        const uint32_t tb0 = tmem + ((uint32_t)(q * 32) << 16) +
+                             (uint32_t)(buf * kPts + cq * (kPts / 4));
+        // the TMEM loads of the second chunk are in flight while the first is
+        // consumed
+        uint32_t ra0[16], rb0[16], ra1[16], rb1[16];
+        tmem_ld16_nowait(tb0, ra0);                       // row block 0, chunk 0
+        tmem_ld16_nowait(tb0 + 256u, rb0);                // row block 1, chunk 0
+        tmem_wait_ld();
+        reg_fence16(ra0);
+        reg_fence16(rb0);
+        tmem_ld16_nowait(tb0 + 16u, ra1);
+        tmem_ld16_nowait(tb0 + 256u + 16u, rb1);
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+          static_assert(kPts / 4 / 16 == 2, "two 16-column chunks per warp and tile");
+          if (ch == 1) {
+            tmem_wait_ld();
+            reg_fence16(ra1);
+            reg_fence16(rb1);
+          }
+          uint32_t(&ra)[16] = ch ? ra1 : ra0;
+          uint32_t(&rb)[16] = ch ? rb1 : rb0;
+#pragma unroll
+          for (int uu = 0; uu < 16; ++uu) {
+            const float k0 = ex2_approx(__uint_as_float(ra[uu]));
+            const float k1 = ex2_approx(__uint_as_float(rb[uu]));
+            const uint32_t vj = vs + (uint32_t)((ch * 16 + uu) * MP * 4);
+            if (MP >= 2) {
+              // packed pair FMAs: the accumulators of columns (2c, 2c+1) share
+              // one fma.rn.f32x2 with the entry broadcast to both halves
+              const unsigned long long kk0 = pk2(k0, k0), kk1 = pk2(k1, k1);
+#pragma unroll
+              for (int c2 = 0; c2 < MP / 2; c2 += 2) {
+                unsigned long long va, vb = 0;
+                if (MP == 2) {
+                  va = lds64u(vj);
+                } else {
+                  const ulonglong2 v = lds128u(vj + (uint32_t)(c2 * 8));
+                  va = v.x;
+                  vb = v.y;
+                }
+                ffma2(acc2[c2], kk0, va);
+                ffma2(acc12[c2], kk1, va);
+                if (MP > 2) {
+                  ffma2(acc2[c2 + 1], kk0, vb);
+                  ffma2(acc12[c2 + 1], kk1, vb);
+                }
+              }
+            } else {
+              const float v1 = lds32(vj);
+              acc[0] = fmaf(k0, v1, acc[0]);
+              acc1[0] = fmaf(k1, v1, acc1[0]);
+            }
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&sm->t_empty[buf]);
+          mbar_arrive(&sm->v_empty[sv]);
+        }
+      }
+      if (!ok) break;
+      if (MP >= 2) {
+#pragma unroll
+        for (int c = 0; c < kP2; ++c) {
+          const float2 a0 = upk2(acc2[c]), a1 = upk2(acc12[c]);
+          acc[(2 * c) % MP] = a0.x;
+          acc[(2 * c + 1) % MP] = a0.y;
+          acc1[(2 * c) % MP] = a1.x;
+          acc1[(2 * c + 1) % MP] = a1.y;
+        }
+      }
+      // merge the four column quarters of every row of the unit: the warps of
+      // quarters 1-3 leave their sums in shared memory, quarter 0 adds them
+      // and writes the split's partial
+      if (cq > 0) {
+        if (k >= 1) ok = mbar_wait(&sm->q_empty, (k - 1) & 1, err, abort);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+#pragma unroll
+        for (int c = 0; c < MP; ++c) {
+          sm->quarter[cq - 1][r][c] = acc[c];
+          sm->quarter[cq - 1][kRows + r][c] = acc1[c];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm->q_full);
+      } else {
+        ok = mbar_wait(&sm->q_full, k & 1, err, abort);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+#pragma unroll
+        for (int b = 0; b < kRB; ++b) {
+          const int64_t gi = w.row0 + b * kRows + r;
+          if (gi < n) {
+            float* out = part + ((int64_t)w.split * n + gi) * MP;
+#pragma unroll
+            for (int c = 0; c < MP; ++c)
+              out[c] = (b == 0 ? acc[c] : acc1[c]) + sm->quarter[0][b * kRows + r][c] +
+                       sm->quarter[1][b * kRows + r][c] + sm->quarter[2][b * kRows + r][c];
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm->q_empty);
       }
     }
   }
@@ -284,21 +358,6 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
   if (warp == 1) {
     fence_after();
     tmem_dealloc(tmem, kTmemCols);
-  }
-  // merge the four column quarters of every row and write the split's partial
-  if (warp >= 2 && ((warp - 2) >> 2) == 0 && !*abort) {
-    const int r = (warp & 3) * 32 + lane;
-#pragma unroll
-    for (int b = 0; b < kRB; ++b) {
-      const int64_t gi = row0 + b * kRows + r;
-      if (gi < n) {
-        float* out = part + ((int64_t)blockIdx.y * n + gi) * MP;
-#pragma unroll
-        for (int c = 0; c < MP; ++c)
-          out[c] = (b == 0 ? acc[c] : acc1[c]) + sm->quarter[0][b * kRows + r][c] +
-                   sm->quarter[1][b * kRows + r][c] + sm->quarter[2][b * kRows + r][c];
-      }
-    }
   }
 }
 
@@ -398,13 +457,26 @@ bool encode_mv_tc(const float* Aaug, const float* Baug, int64_t n, void* amap, v
   return encode_aug((CUtensorMap*)amap, Aaug, npad) && encode_aug((CUtensorMap*)bmap, Baug, npad);
 }
 
+// point ranges per row pair: the persistent CTAs (one per SM) take units
+// round-robin, so choose the split that minimises the largest per-CTA work
+// (whole units times tiles per unit, plus about half a tile per unit for its
+// row-block load and the merge)
 int mv_tc_nsplit(int64_t n) {
   const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
-  int64_t s = cdiv(4 * 152, pairs);     // about 4 waves of one CTA per SM
   const int64_t tiles = cdiv(n, kPts);
-  if (s > tiles / 8) s = tiles / 8;     // at least ~8 tiles per CTA
-  if (s < 1) s = 1;
-  return (int)s;
+  const int64_t ctas = 152;
+  int best = 1;
+  double best_cost = 1e300;
+  for (int64_t s = 1; s <= tiles && s <= 64; ++s) {
+    const int64_t tpu = cdiv(tiles, s);
+    const int64_t units = pairs * cdiv(tiles, tpu);
+    const double cost = (double)cdiv(units, ctas) * ((double)tpu + 0.5);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = (int)cdiv(tiles, tpu);
+    }
+  }
+  return best;
 }
 
 // part[s][i][c] = sum_{j in split s} K_ij V[j][c]; V must have mv_tc_pad(n)
@@ -415,27 +487,31 @@ bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const f
   const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
   const int64_t tiles = cdiv(n, kPts);
   const int64_t pps = cdiv(tiles, nsplit) * kPts;
-  dim3 grid((unsigned)pairs, (unsigned)nsplit);
+  const int64_t nunits = pairs * nsplit;
+  static std::atomic<int> sms_cached{0};
+  int sms = sms_cached.load();
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return false;
+    sms_cached.store(sms);
+  }
+  const unsigned grid = (unsigned)(nunits < sms ? nunits : sms);
   const CUtensorMap& am = *(const CUtensorMap*)amap;
   const CUtensorMap& bm = *(const CUtensorMap*)bmap;
+#define RR_MVTC(MPV)                                                                             \
+  if (!set_attr<MPV>()) return false;                                                            \
+  k_kernel_mv_tc<MPV><<<grid, kThreadsMv, mv_smem_bytes<MPV>(), st>>>(am, bm, n, pps, nsplit,     \
+                                                                      nunits, V, part, err, gate, \
+                                                                      gate_mp);
   switch (mp) {
-    case 1:
-      if (!set_attr<1>()) return false;
-      k_kernel_mv_tc<1><<<grid, kThreadsMv, mv_smem_bytes<1>(), st>>>(am, bm, n, pps, V, part, err, gate, gate_mp);
-      break;
-    case 2:
-      if (!set_attr<2>()) return false;
-      k_kernel_mv_tc<2><<<grid, kThreadsMv, mv_smem_bytes<2>(), st>>>(am, bm, n, pps, V, part, err, gate, gate_mp);
-      break;
-    case 4:
-      if (!set_attr<4>()) return false;
-      k_kernel_mv_tc<4><<<grid, kThreadsMv, mv_smem_bytes<4>(), st>>>(am, bm, n, pps, V, part, err, gate, gate_mp);
-      break;
-    default:
-      if (!set_attr<8>()) return false;
-      k_kernel_mv_tc<8><<<grid, kThreadsMv, mv_smem_bytes<8>(), st>>>(am, bm, n, pps, V, part, err, gate, gate_mp);
-      break;
+    case 1: RR_MVTC(1) break;
+    case 2: RR_MVTC(2) break;
+    case 4: RR_MVTC(4) break;
+    default: RR_MVTC(8) break;
   }
+#undef RR_MVTC
   return cudaGetLastError() == cudaSuccess;
 }
 

@@ -316,7 +316,7 @@ def test_tensor_core_sketch_matches_float_cores(cuda_lib, n, k):
     assert O.true_rel_residual(O.GaussKernelOp(X), mu, x.cpu().numpy(), b)[0] <= 1e-8
 
 
-@pytest.mark.parametrize("n,m", [(20000, 4), (3001, 4), (777, 1), (1000, 2), (515, 8)])
+@pytest.mark.parametrize("n,m", [(20000, 4), (12345, 2), (3001, 4), (777, 1), (1000, 2), (515, 8)])
 def test_tensor_core_kernel_product(cuda_lib, n, m):
     """Float32 Gaussian-kernel product with the exponent arguments contracted
     on the tensor cores (augmented 3xTF32 split) against the float64 oracle,
@@ -331,11 +331,18 @@ def test_tensor_core_kernel_product(cuda_lib, n, m):
     mu = 1e-3
     V = np.random.default_rng(3).standard_normal((n, m))
     if n > 5000:
-        idx = np.random.default_rng(4).choice(n, 64, replace=False)
-        op_rows = O.GaussKernelOp(X)
-        K = np.exp(-((X[idx, None, :].astype(np.float64) - X[None, :, :].astype(np.float64)) ** 2).sum(-1) / 2)
-        ref = K @ V + mu * V[idx]
-        scale = np.abs(K) @ np.abs(V) + mu * np.abs(V[idx])
+        # sampled rows, including the last (ragged) row block, computed a few
+        # rows at a time from the definition K_ij = exp(-|x_i - x_j|^2 / 2)
+        idx = np.concatenate([np.random.default_rng(4).choice(n - 300, 192, replace=False),
+                              np.arange(n - 64, n)])
+        X64 = X.astype(np.float64)
+        ref, scale = [], []
+        for c in range(0, len(idx), 32):
+            ii = idx[c:c + 32]
+            K = np.exp(-((X64[ii, None, :] - X64[None, :, :]) ** 2).sum(-1) / 2)
+            ref.append(K @ V + mu * V[ii])
+            scale.append(np.abs(K) @ np.abs(V) + mu * np.abs(V[ii]))
+        ref, scale = np.concatenate(ref), np.concatenate(scale)
     else:
         op = O.GaussKernelOp(X)
         ref = op.matmat(V) + mu * V
