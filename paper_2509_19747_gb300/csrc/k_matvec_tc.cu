@@ -10,17 +10,21 @@
 // rows [u_hi u_hi u_lo 0 0] with [w_hi w_lo w_hi 0 0]: K = 32 (one 128-byte
 // swizzle atom per row), four tcgen05.mma kind::tf32 instructions.
 //
-// Persistent CTAs (one per SM) take work units round-robin: a unit is two
-// blocks of 128 rows (TMEM lanes) x a range of points, in tiles of
-// 128 points; per tile the MMA writes 128 x 128 exponent arguments per row
+// Persistent CTAs (one per SM), stream-K order: the (row pair, point tile)
+// work items, row pair major, are cut into one contiguous range per CTA
+// (equal to one tile); a CTA's range falls into segments, one per row pair
+// it touches, and a segment is two blocks of 128 rows (TMEM lanes) x a run of
+// tiles of 128 points; per tile the MMA writes 128 x 128 exponent arguments per row
 // block into TMEM (double-buffered: 2 row blocks x 2 buffers x 128 columns =
 // all 512 columns), and 16 epilogue warps read them with tcgen05.ld.  A warp
 // serves its TMEM lane quarter in both row blocks (two rows per thread) for
 // one quarter of the tile's columns, so each v_j it loads from shared memory
 // (LDS broadcast) feeds two kernel entries; it applies ex2 (MUFU) and
 // accumulates w_i += K_ij v_j in registers.  The four column quarters of a
-// row are merged at the end of each unit through shared memory.
-//   warp 0   TMA: augmented row blocks (double-buffered across units),
+// row are merged at the end of each segment through shared memory and
+// written as the segment's partial sums (slot = this CTA's rank among the
+// CTAs that touch the row pair).
+//   warp 0   TMA: augmented row blocks (double-buffered across segments),
 //            point tiles (4 stages), and the matching rows of v (bulk copy,
 //            4 stages);
 //   warp 1   TMEM allocation; one thread issues the MMAs and commits;
@@ -71,26 +75,36 @@ constexpr size_t mv_smem_bytes() {
   return 1024 + 2 * (size_t)kABytes + (size_t)kStagesB * kBBytes + sizeof(MvSmem<MP>);
 }
 
-// unit u of a launch: row pair u / nsplit, point range (split) u % nsplit
-struct MvUnit {
-  int64_t row0, j0, j1;
-  int split, ntiles;
+// the CTA (of g over total work items) whose range holds item x: CTA c owns
+// [floor(c total / g), floor((c + 1) total / g))
+__host__ __device__ __forceinline__ int64_t mv_cta_of(int64_t x, int64_t total, int64_t g) {
+  return ((x + 1) * g + total - 1) / total - 1;
+}
+
+// the segment of CTA c starting at work item x (its range ends at xend)
+struct MvSeg {
+  int64_t row0, j0;
+  int ntiles, slot;
+  bool last;                         // the segment ends the row pair
 };
-__device__ __forceinline__ MvUnit mv_unit(int64_t u, int nsplit, int64_t pts_per_split, int64_t n) {
-  MvUnit w;
-  w.split = (int)(u % nsplit);
-  w.row0 = (u / nsplit) * (kRows * kRB);
-  w.j0 = (int64_t)w.split * pts_per_split;
-  w.j1 = w.j0 + pts_per_split;
-  if (w.j1 > n) w.j1 = n;
-  w.ntiles = (w.j1 > w.j0) ? (int)((w.j1 - w.j0 + kPts - 1) / kPts) : 0;
+__device__ __forceinline__ MvSeg mv_seg(int64_t x, int64_t xend, int64_t tiles, int64_t total,
+                                        int64_t g, int64_t c) {
+  MvSeg w;
+  const int64_t p = x / tiles;
+  const int64_t pend = (p + 1) * tiles;
+  const int64_t e = xend < pend ? xend : pend;
+  w.row0 = p * (kRows * kRB);
+  w.j0 = (x - p * tiles) * kPts;
+  w.ntiles = (int)(e - x);
+  w.slot = (int)(c - mv_cta_of(p * tiles, total, g));
+  w.last = e == pend;
   return w;
 }
 
 template <int MP>
 __global__ void __launch_bounds__(kThreadsMv, 1)
     k_kernel_mv_tc(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
-                   int64_t n, int64_t pts_per_split, int nsplit, int64_t nunits,
+                   int64_t n, int64_t tiles, int64_t total, int nslots,
                    const float* __restrict__ V, float* __restrict__ part, int* __restrict__ err,
                    const ColState* __restrict__ gate, int gate_mp) {
   if (gate) {
@@ -138,16 +152,19 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
   fence_after();
   const uint32_t tmem = sm->tmem_base;
 
-  // every role walks the same units (u = blockIdx.x, + gridDim.x, ...) and
-  // counts this CTA's units (k) and tiles (T) for stage indices and parities
+  // every role walks the same segments of this CTA's range and counts them
+  // (k) and its tiles (T) for stage indices and parities
+  const int64_t xbeg = (int64_t)blockIdx.x * total / gridDim.x;
+  const int64_t xend = ((int64_t)blockIdx.x + 1) * total / gridDim.x;
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       int issued_a = 0, issued_b = 0, issued_v = 0;
       int T = 0, k = 0;
       bool ok = true;
-      for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++k) {
-        const MvUnit w = mv_unit(u, nsplit, pts_per_split, n);
+      for (int64_t x = xbeg; x < xend && ok; ++k) {
+        const MvSeg w = mv_seg(x, xend, tiles, total, gridDim.x, blockIdx.x);
+        x += w.ntiles;
         const int ab = k & 1;
         if (k >= 2 && !mbar_wait(&sm->a_empty[ab], ((k >> 1) - 1) & 1, err, abort)) break;
         mbar_arrive_tx(&sm->a_full[ab], kABytes);
@@ -187,8 +204,9 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
     if (lane == 0) {
       bool ok = true;
       int T = 0, k = 0;
-      for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++k) {
-        const MvUnit w = mv_unit(u, nsplit, pts_per_split, n);
+      for (int64_t x = xbeg; x < xend && ok; ++k) {
+        const MvSeg w = mv_seg(x, xend, tiles, total, gridDim.x, blockIdx.x);
+        x += w.ntiles;
         const int ab = k & 1;
         ok = mbar_wait(&sm->a_full[ab], (k >> 1) & 1, err, abort);
         for (int t = 0; t < w.ntiles && ok; ++t, ++T) {
@@ -224,8 +242,9 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
     constexpr int kP2 = MP >= 2 ? MP / 2 : 1;
     bool ok = true;
     int T = 0, k = 0;
-    for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++k) {
-      const MvUnit w = mv_unit(u, nsplit, pts_per_split, n);
+    for (int64_t x = xbeg; x < xend && ok; ++k) {
+      const MvSeg w = mv_seg(x, xend, tiles, total, gridDim.x, blockIdx.x);
+      x += w.ntiles;
       float acc[MP], acc1[MP];                  // partial sums of this thread's two rows
       unsigned long long acc2[kP2], acc12[kP2]; // the same as packed column pairs (MP >= 2)
 #pragma unroll
@@ -341,11 +360,16 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
         for (int b = 0; b < kRB; ++b) {
           const int64_t gi = w.row0 + b * kRows + r;
           if (gi < n) {
-            float* out = part + ((int64_t)w.split * n + gi) * MP;
+            float* out = part + ((int64_t)w.slot * n + gi) * MP;
 #pragma unroll
             for (int c = 0; c < MP; ++c)
               out[c] = (b == 0 ? acc[c] : acc1[c]) + sm->quarter[0][b * kRows + r][c] +
                        sm->quarter[1][b * kRows + r][c] + sm->quarter[2][b * kRows + r][c];
+            // the CTA that ends the row pair clears the slots no CTA uses
+            if (w.last)
+              for (int sl = w.slot + 1; sl < nslots; ++sl)
+#pragma unroll
+                for (int c = 0; c < MP; ++c) part[((int64_t)sl * n + gi) * MP + c] = 0.f;
           }
         }
         __syncwarp();
@@ -457,53 +481,54 @@ bool encode_mv_tc(const float* Aaug, const float* Baug, int64_t n, void* amap, v
   return encode_aug((CUtensorMap*)amap, Aaug, npad) && encode_aug((CUtensorMap*)bmap, Baug, npad);
 }
 
-// point ranges per row pair: the persistent CTAs (one per SM) take units
-// round-robin, so choose the split that minimises the largest per-CTA work
-// (whole units times tiles per unit, plus about half a tile per unit for its
-// row-block load and the merge)
-int mv_tc_nsplit(int64_t n) {
-  const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
-  const int64_t tiles = cdiv(n, kPts);
-  const int64_t ctas = 152;
-  int best = 1;
-  double best_cost = 1e300;
-  for (int64_t s = 1; s <= tiles && s <= 64; ++s) {
-    const int64_t tpu = cdiv(tiles, s);
-    const int64_t units = pairs * cdiv(tiles, tpu);
-    const double cost = (double)cdiv(units, ctas) * ((double)tpu + 0.5);
-    if (cost < best_cost - 1e-9) {
-      best_cost = cost;
-      best = (int)cdiv(tiles, tpu);
-    }
-  }
-  return best;
-}
-
-// part[s][i][c] = sum_{j in split s} K_ij V[j][c]; V must have mv_tc_pad(n)
-// rows (zero beyond n).  Returns false if the kernel cannot be launched.
-bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const float* V,
-                  float* part, int nsplit, int* err, const ColState* gate, int gate_mp,
-                  cudaStream_t st) {
-  const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
-  const int64_t tiles = cdiv(n, kPts);
-  const int64_t pps = cdiv(tiles, nsplit) * kPts;
-  const int64_t nunits = pairs * nsplit;
+namespace {
+// the launch's CTA count: one per SM (at most one per work item)
+int64_t mv_tc_ctas(int64_t total) {
   static std::atomic<int> sms_cached{0};
   int sms = sms_cached.load();
   if (sms == 0) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      return false;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+      sms = 152;
     sms_cached.store(sms);
   }
-  const unsigned grid = (unsigned)(nunits < sms ? nunits : sms);
+  return total < sms ? total : sms;
+}
+}  // namespace
+
+// partial-sum slots per row: the most CTAs whose ranges touch one row pair
+int mv_tc_nsplit(int64_t n) {
+  const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
+  const int64_t tiles = cdiv(n, kPts);
+  const int64_t total = pairs * tiles;
+  const int64_t g = mv_tc_ctas(total);
+  int64_t most = 1;
+  for (int64_t p = 0; p < pairs; ++p) {
+    const int64_t s = mv_cta_of((p + 1) * tiles - 1, total, g) - mv_cta_of(p * tiles, total, g) + 1;
+    if (s > most) most = s;
+  }
+  return (int)most;
+}
+
+// part[s][i][c] = sum over the points of the s-th CTA touching row i's pair of
+// K_ij V[j][c] (zero for the slots beyond that pair's CTAs); nslots =
+// mv_tc_nsplit(n).  V must have mv_tc_pad(n) rows (zero beyond n).  Returns
+// false if the kernel cannot be launched.
+bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const float* V,
+                  float* part, int nslots, int* err, const ColState* gate, int gate_mp,
+                  cudaStream_t st) {
+  const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
+  const int64_t tiles = cdiv(n, kPts);
+  const int64_t total = pairs * tiles;
+  const unsigned grid = (unsigned)mv_tc_ctas(total);
   const CUtensorMap& am = *(const CUtensorMap*)amap;
   const CUtensorMap& bm = *(const CUtensorMap*)bmap;
 #define RR_MVTC(MPV)                                                                             \
   if (!set_attr<MPV>()) return false;                                                            \
-  k_kernel_mv_tc<MPV><<<grid, kThreadsMv, mv_smem_bytes<MPV>(), st>>>(am, bm, n, pps, nsplit,     \
-                                                                      nunits, V, part, err, gate, \
+  k_kernel_mv_tc<MPV><<<grid, kThreadsMv, mv_smem_bytes<MPV>(), st>>>(am, bm, n, tiles, total,    \
+                                                                      nslots, V, part, err, gate, \
                                                                       gate_mp);
   switch (mp) {
     case 1: RR_MVTC(1) break;
