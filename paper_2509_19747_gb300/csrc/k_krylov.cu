@@ -33,27 +33,82 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
   return s_last;
 }
 
-// Block-wide sum of per-thread values v[0..mp) into sh[0..mp) (thread 0 holds them).
-template <int NT>
-__device__ __forceinline__ void block_sum_cols(double* v, int mp, double* sh /*[NT/32][8]*/) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// Warp sum of per-lane values v[0..MP) by halving exchanges: at the level of
+// lane bit b the lower half of each lane pair keeps the lower half of its
+// columns and receives the partner's, the upper half the upper ones, so a
+// level costs MP/2^(l+1) float64 adds (float64 runs at a small fraction of
+// the float32 rate).  Afterwards lane L holds the warp's sum of column
+// tr_col-order ((L >> 4) & 1) * MP/2 + ((L >> 3) & 1) * MP/4 + ..., and the
+// sum is complete in every lane with the same high bits.
+template <int MP>
+__device__ __forceinline__ double warp_halving_sum(const double* v, int lane) {
+  double x[MP];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    if (c >= mp) break;
-    double x = v[c];
+  for (int c = 0; c < MP; ++c) x[c] = v[c];
+  int w = MP;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) sh[wid * 8 + c] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < mp; ++c) {
-      double s = 0.0;
-      for (int w = 0; w < NT / 32; ++w) s += sh[w * 8 + c];
-      v[c] = s;
+  for (int o = 16; o > 0; o >>= 1) {
+    if (w > 1) {
+      const bool hi = (lane & o) != 0;
+      const int h = w >> 1;
+#pragma unroll
+      for (int i = 0; i < MP / 2; ++i) {
+        if (i < h) {
+          const double keep = hi ? x[h + i] : x[i];
+          const double send = hi ? x[i] : x[h + i];
+          x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+      w = h;
+    } else {
+      x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
     }
   }
+  return x[0];
+}
+
+template <int NT, int MP>
+__device__ __forceinline__ void block_sum_cols_t(double* v, double* sh) {
+  __shared__ double res[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double x = warp_halving_sum<MP>(v, lane);
+  // the lane that holds column c's warp sum: high bits = c, low bits zero
+  if ((lane & (32 / MP - 1)) == 0) {
+    int c = 0;
+#pragma unroll
+    for (int b = 4, m = MP / 2; m > 0; --b, m >>= 1) c += ((lane >> b) & 1) * m;
+    sh[wid * 8 + c] = x;
+  }
   __syncthreads();
+  if (threadIdx.x < MP) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += sh[w * 8 + threadIdx.x];
+    res[threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int c = 0; c < MP; ++c) v[c] = res[c];
+}
+
+// Block-wide sum of per-thread values v[0..mp) into v[0..mp) of thread 0
+// (mp in {1, 2, 4, 8}; fixed order, so the result does not depend on timing).
+template <int NT>
+__device__ __forceinline__ void block_sum_cols(double* v, int mp, double* sh /*[NT/32][8]*/) {
+  switch (mp) {
+    case 1: block_sum_cols_t<NT, 1>(v, sh); break;
+    case 2: block_sum_cols_t<NT, 2>(v, sh); break;
+    case 4: block_sum_cols_t<NT, 4>(v, sh); break;
+    default: block_sum_cols_t<NT, 8>(v, sh); break;
+  }
+}
+
+// v = s in column c, zero elsewhere (selects, no float64 arithmetic): a
+// thread whose elements e = e0 + j * stride all fall in one column (stride a
+// multiple of the column count) accumulates them in one scalar
+__device__ __forceinline__ void place_col(double* v, double s, int c) {
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) v[cc] = (cc == c) ? s : 0.0;
 }
 
 // sum over blocks of part[b][c], by thread 0 of the last block (small nb)
@@ -600,8 +655,7 @@ __global__ void __launch_bounds__(kNT) k_update_qt(T* __restrict__ E, T* __restr
   const int64_t r0 = (int64_t)blockIdx.x * rps;
   const int cnt = (int)((n - r0 < rps) ? (n - r0) : rps);
   double v[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) v[c] = 0.0;
+  double vs = 0.0;
   for (int e = threadIdx.x; e < cnt * MP; e += kNT) {
     const int64_t g = r0 * MP + e;
     const int c = e % MP;
@@ -610,10 +664,9 @@ __global__ void __launch_bounds__(kNT) k_update_qt(T* __restrict__ E, T* __restr
     const T r = fma(-a, W[g], R[g]);
     R[g] = r;
     Rs[e] = r;
-#pragma unroll
-    for (int cc = 0; cc < MP; ++cc)
-      if (cc == c) v[cc] += (double)r * (double)r;
+    vs += (double)r * (double)r;
   }
+  place_col(v, vs, (int)threadIdx.x % MP);
   __syncthreads();
   if (tpart && sizeof(T) == 4 && vec4_ok(k)) {
     slab_qt_vec4<MP>((const float*)Q, r0, cnt, k, (const float*)Rs,
@@ -683,8 +736,7 @@ __global__ void __launch_bounds__(kNT) k_update_cg(T* __restrict__ Yv, T* __rest
   if (threadIdx.x < 8) al[threadIdx.x] = (threadIdx.x < mp && cs[threadIdx.x].active) ? (T)cs[threadIdx.x].alpha : (T)0;
   __syncthreads();
   double v[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) v[c] = 0.0;
+  double vs = 0.0;
   const int64_t total = n * mp;
   const int64_t stride = (int64_t)gridDim.x * kNT;
   for (int64_t g = (int64_t)blockIdx.x * kNT + threadIdx.x; g < total; g += stride) {
@@ -693,10 +745,9 @@ __global__ void __launch_bounds__(kNT) k_update_cg(T* __restrict__ Yv, T* __rest
     Yv[g] = fma(a, P[g], Yv[g]);
     const T r = fma(-a, Bp[g], R[g]);
     R[g] = r;
-#pragma unroll
-    for (int cc = 0; cc < 8; ++cc)
-      if (cc == c) v[cc] += (double)r * (double)r;
+    vs += (double)r * (double)r;
   }
+  place_col(v, vs, (int)threadIdx.x % mp);
   block_sum_cols<kNT>(v, mp, red);
   if (threadIdx.x == 0)
     for (int c = 0; c < mp; ++c) part[(int64_t)blockIdx.x * mp + c] = v[c];
@@ -879,7 +930,7 @@ template void axpby<double, float, float>(const double*, Coefs8, const float*, C
 // Reads of data written by other CTAs bypass L1 (ld.cg).  The barrier waits
 // are bounded by the global timer.
 // ======================================================================
-constexpr int kFT = 256;                 // threads of the fused step
+constexpr int kFT = 512;                 // threads of the fused step
 constexpr int kFusedChunk = 256;         // rows of r staged in shared memory at a time
 constexpr unsigned long long kBarTimeoutNs = 10ull * 1000 * 1000 * 1000;
 
@@ -1085,16 +1136,12 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
   double v[8];
   // ---- A: p^T w
   if (!a.alpha_ready) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) v[c] = 0.0;
+    double vs = 0.0;
     for (int e = tid; e < cnt * MP; e += kFT) {
       const int64_t g = r0 * MP + e;
-      const int c = e % MP;
-      const double x = (double)a.P[g] * (double)a.W[g];
-#pragma unroll
-      for (int cc = 0; cc < MP; ++cc)
-        if (cc == c) v[cc] += x;
+      vs += (double)a.P[g] * (double)a.W[g];
     }
+    place_col(v, vs, tid % MP);
     block_sum_cols<kFT>(v, MP, redd);
     if (tid == 0 && cnt > 0)
       for (int c = 0; c < MP; ++c) atomicAdd(acc + c, v[c]);
@@ -1123,18 +1170,18 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
   __syncthreads();
 
   // ---- B: e and r, |r|^2 and Q^T r
-#pragma unroll
-  for (int c = 0; c < 8; ++c) v[c] = 0.0;
-  for (int e = tid; e < cnt * MP; e += kFT) {
-    const int64_t g = r0 * MP + e;
-    const int c = e % MP;
-    const T al = (T)sh_alpha[c];
-    a.E[g] = fma(al, a.P[g], a.E[g]);
-    const T r = fma(-al, a.W[g], a.R[g]);
-    a.R[g] = r;
-#pragma unroll
-    for (int cc = 0; cc < MP; ++cc)
-      if (cc == c) v[cc] += (double)r * (double)r;
+  {
+    double vs = 0.0;
+    for (int e = tid; e < cnt * MP; e += kFT) {
+      const int64_t g = r0 * MP + e;
+      const int c = e % MP;
+      const T al = (T)sh_alpha[c];
+      a.E[g] = fma(al, a.P[g], a.E[g]);
+      const T r = fma(-al, a.W[g], a.R[g]);
+      a.R[g] = r;
+      vs += (double)r * (double)r;
+    }
+    place_col(v, vs, tid % MP);
   }
   block_sum_cols<kFT>(v, MP, redd);
   if (tid == 0 && cnt > 0)
@@ -1312,10 +1359,17 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
   if (cta == 0 && tid == 0) atomicAdd(&a.bar->launches, 1u);
 }
 
+// row-phase partials of the fused step's Q^T r (kFT threads over k / 4 quads)
+inline size_t tail_red_floats(int k, int mp) {
+  const int nq = k / 4;
+  const int rph = nq > 0 ? kFT / nq : 1;
+  return (size_t)(rph > 1 ? rph - 1 : 0) * nq * 4 * mp;
+}
+
 template <typename T>
 size_t pcg_tail_smem(int k, int mp) {
   return (size_t)k * mp * sizeof(T) + (size_t)kFusedChunk * mp * sizeof(T) +
-         slab_red_floats(k, mp) * sizeof(float) + 16;
+         tail_red_floats(k, mp) * sizeof(float) + 16;
 }
 
 // raise the kernel's dynamic shared-memory limit to the device maximum once
@@ -1421,8 +1475,7 @@ __global__ void __launch_bounds__(kNT) k_sum_splits_alpha(const T* __restrict__ 
   if (!any_active(cs, mp)) return;
   __shared__ double red[kNT / 32 * 8];
   double v[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) v[c] = 0.0;
+  double vs = 0.0;
   const int64_t total = n * mp;
   const int64_t stride = (int64_t)gridDim.x * kNT;
   for (int64_t e = (int64_t)blockIdx.x * kNT + threadIdx.x; e < total; e += stride) {
@@ -1436,12 +1489,9 @@ __global__ void __launch_bounds__(kNT) k_sum_splits_alpha(const T* __restrict__ 
     for (int s = 16; s < nsplit; ++s) acc += part[(int64_t)s * total + e];
     const T w = acc + (T)mu * V[e];
     W[e] = w;
-    const int c = (int)(e % mp);
-    const double x = (double)V[e] * (double)w;
-#pragma unroll
-    for (int cc = 0; cc < 8; ++cc)
-      if (cc == c) v[cc] += x;
+    vs += (double)V[e] * (double)w;
   }
+  place_col(v, vs, (int)threadIdx.x % mp);
   block_sum_cols<kNT>(v, mp, red);
   if (threadIdx.x == 0)
     for (int c = 0; c < mp; ++c) rpart[(int64_t)blockIdx.x * mp + c] = v[c];
