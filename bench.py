@@ -68,6 +68,8 @@ def parse():
                     choices=["kernel_ridge", "sparse_diffusion", "batched", "serving"])
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
     ap.add_argument("--workers", type=int, default=0, help="batched/serving: 0 = autotune")
+    ap.add_argument("--kernel-impl", type=int, default=0,
+                    help="kernel ridge: Gaussian-kernel product form (rr_build_opts.kernel_impl)")
     return ap.parse_args()
 
 
@@ -250,6 +252,7 @@ def run_ours(args):
     o.precision = rr.PRECISIONS[WORKLOAD["precision"]]
     o.max_rhs = m
     o.profile = 1
+    o.kernel_impl = args.kernel_impl
     ws_bytes = rr.randrand_workspace_bytes(op.c, k, o)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")

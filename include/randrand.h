@@ -131,7 +131,11 @@ typedef struct {
   int32_t profile;       /* 1: time the hot kernels with CUDA events (rr_profile) */
   int32_t kernel_impl;   /* Gaussian-kernel sketch (RR_PREC_MIXED) and float32
                             products (FP32 / MIXED), dim == 8: 0 auto (tensor
-                            cores), 1 float32 cores only, 2 tensor cores required */
+                            cores), 1 float32 cores only, 2 tensor cores required
+                            (exponent arguments on the tensor cores, K v on the
+                            float32 cores), 3 tensor cores for both (K split into
+                            two bf16 parts, K v by a second tcgen05 product);
+                            other values: RR_ERR_INVALID_ARG */
   int32_t iter_impl;     /* variant C with a basis: 0 auto (one persistent
                             cooperative launch per iteration for everything
                             after the operator product), 1 separate kernels */

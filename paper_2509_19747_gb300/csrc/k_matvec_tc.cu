@@ -75,12 +75,6 @@ constexpr size_t mv_smem_bytes() {
   return 1024 + 2 * (size_t)kABytes + (size_t)kStagesB * kBBytes + sizeof(MvSmem<MP>);
 }
 
-// the CTA (of g over total work items) whose range holds item x: CTA c owns
-// [floor(c total / g), floor((c + 1) total / g))
-__host__ __device__ __forceinline__ int64_t mv_cta_of(int64_t x, int64_t total, int64_t g) {
-  return ((x + 1) * g + total - 1) / total - 1;
-}
-
 // the segment of CTA c starting at work item x (its range ends at xend)
 struct MvSeg {
   int64_t row0, j0;
@@ -89,15 +83,13 @@ struct MvSeg {
 };
 __device__ __forceinline__ MvSeg mv_seg(int64_t x, int64_t xend, int64_t tiles, int64_t total,
                                         int64_t g, int64_t c) {
+  const SkSeg k = sk_seg(x, xend, tiles, total, g, c);
   MvSeg w;
-  const int64_t p = x / tiles;
-  const int64_t pend = (p + 1) * tiles;
-  const int64_t e = xend < pend ? xend : pend;
-  w.row0 = p * (kRows * kRB);
-  w.j0 = (x - p * tiles) * kPts;
-  w.ntiles = (int)(e - x);
-  w.slot = (int)(c - mv_cta_of(p * tiles, total, g));
-  w.last = e == pend;
+  w.row0 = k.pair * (kRows * kRB);
+  w.j0 = k.t0 * kPts;
+  w.ntiles = k.ntiles;
+  w.slot = k.slot;
+  w.last = k.last;
   return w;
 }
 
@@ -481,9 +473,8 @@ bool encode_mv_tc(const float* Aaug, const float* Baug, int64_t n, void* amap, v
   return encode_aug((CUtensorMap*)amap, Aaug, npad) && encode_aug((CUtensorMap*)bmap, Baug, npad);
 }
 
-namespace {
-// the launch's CTA count: one per SM (at most one per work item)
-int64_t mv_tc_ctas(int64_t total) {
+// persistent tensor-core kernels: one CTA per SM (at most one per work item)
+int64_t tc_persistent_ctas(int64_t total) {
   static std::atomic<int> sms_cached{0};
   int sms = sms_cached.load();
   if (sms == 0) {
@@ -496,20 +487,30 @@ int64_t mv_tc_ctas(int64_t total) {
   }
   return total < sms ? total : sms;
 }
-}  // namespace
+
+// a 2-d tensor map (row-major, inner extent `inner` elements, `outer` rows,
+// 128-byte swizzle) of float32 or bf16 elements
+bool tc_encode_2d(void* map, bool bf16, const void* base, uint64_t inner, uint64_t outer,
+                  uint32_t box_inner, uint32_t box_outer) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const uint64_t esz = bf16 ? 2 : 4;
+  const cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t gstride[1] = {(cuuint64_t)(inner * esz)};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estride[2] = {1, 1};
+  return enc((CUtensorMap*)map,
+             bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+             (void*)base, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // partial-sum slots per row: the most CTAs whose ranges touch one row pair
 int mv_tc_nsplit(int64_t n) {
   const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
   const int64_t tiles = cdiv(n, kPts);
-  const int64_t total = pairs * tiles;
-  const int64_t g = mv_tc_ctas(total);
-  int64_t most = 1;
-  for (int64_t p = 0; p < pairs; ++p) {
-    const int64_t s = mv_cta_of((p + 1) * tiles - 1, total, g) - mv_cta_of(p * tiles, total, g) + 1;
-    if (s > most) most = s;
-  }
-  return (int)most;
+  return sk_nslots(pairs, tiles, tc_persistent_ctas(pairs * tiles));
 }
 
 // part[s][i][c] = sum over the points of the s-th CTA touching row i's pair of
@@ -522,7 +523,7 @@ bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const f
   const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
   const int64_t tiles = cdiv(n, kPts);
   const int64_t total = pairs * tiles;
-  const unsigned grid = (unsigned)mv_tc_ctas(total);
+  const unsigned grid = (unsigned)tc_persistent_ctas(total);
   const CUtensorMap& am = *(const CUtensorMap*)amap;
   const CUtensorMap& bm = *(const CUtensorMap*)bmap;
 #define RR_MVTC(MPV)                                                                             \

@@ -589,8 +589,9 @@ static int kernel_nsplit(int64_t n) {
 size_t op_matvec_scratch_elems(const OpDev& op, int mp) {
   if (op.kind != RR_OP_GAUSS_KERNEL) return 0;
   int ns = kernel_nsplit(op.n);
-  const int nt = mv_tc_nsplit(op.n);
+  const int nt = mv_tc_nsplit(op.n), nt2 = mv_tc2_nsplit(op.n);
   if (nt > ns) ns = nt;
+  if (nt2 > ns) ns = nt2;
   return (size_t)ns * (size_t)op.n * (size_t)mp;
 }
 
@@ -602,9 +603,14 @@ template <>
 void kernel_mv<float>(const OpDev& op, double mu, const float* V, float* W, int mp, float* part,
                       cudaStream_t st, const cudaEvent_t* ev) {
   if (op.use_tc) {
-    const int nt = mv_tc_nsplit(op.n);
+    const int nt = op.tc2 ? mv_tc2_nsplit(op.n) : mv_tc_nsplit(op.n);
     rec(ev, 0, st);
-    if (kernel_mv_tc(op.amap, op.bmap, op.n, mp, V, part, nt, op.tc_err, op.gate, op.gate_mp, st)) {
+    const bool launched =
+        op.tc2 ? kernel_mv_tc2(op.amap, op.bmap64, op.vmap, op.n, mp, V, op.vsplit, part, nt,
+                               op.tc_err, op.gate, op.gate_mp, st)
+               : kernel_mv_tc(op.amap, op.bmap, op.n, mp, V, part, nt, op.tc_err, op.gate,
+                              op.gate_mp, st);
+    if (launched) {
       rec(ev, 1, st);
       if (op.alpha_cs)
         sum_splits_alpha<float>(part, nt, op.n, mp, mu, V, W, op.alpha_rpart, op.alpha_cnt,

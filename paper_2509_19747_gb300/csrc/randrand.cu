@@ -89,8 +89,9 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_PN] = (A.kind == RR_OP_GAUSS_KERNEL) ? n * 8 : 0;
   // tensor-core product: two augmented arrays of kAugFloats floats per (padded) point
   const size_t npad_tc = (size_t)mv_tc_pad(A.n);
+  // (then the bf16 split vector array of the two-contraction product)
   L.size[R_AUG] = (A.kind == RR_OP_GAUSS_KERNEL && A.dim == 8 && !uses_f64(o))
-                      ? 2 * npad_tc * kAugFloats * 4 : 0;
+                      ? 2 * npad_tc * kAugFloats * 4 + mv_tc2_vsplit_elems(A.n) * 2 : 0;
   L.size[R_MVS] = op_matvec_scratch_elems(od, mp) * 8;
   // Krylov vectors carry zero rows up to the tensor-core tile multiple
   L.size[R_VT] = 7 * (size_t)mv_tc_pad(A.n) * (size_t)mp * ts;
@@ -143,6 +144,7 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
   }
   if (o.power_iters < 1 || o.power_iters > 1000) return RR_ERR_INVALID_ARG;
   if (o.iter_impl < 0 || o.iter_impl > 1) return RR_ERR_INVALID_ARG;
+  if (o.kernel_impl < 0 || o.kernel_impl > 3) return RR_ERR_INVALID_ARG;
   if (o.q < 0 || o.q > 4) return RR_ERR_INVALID_ARG;
   if (!(o.restart_eta > 0.0 && o.restart_eta < 1.0)) return RR_ERR_INVALID_ARG;
   switch (A->kind) {
@@ -267,6 +269,8 @@ struct rr_handle {
   bool graph_prof_broken;        // captured event records gave no timings
   alignas(64) unsigned char amap[128];  // tensor maps of the augmented point arrays
   alignas(64) unsigned char bmap[128];
+  alignas(64) unsigned char bmap64[128];  // 64-point tiles, and the split vector array
+  alignas(64) unsigned char vmap[128];
 };
 
 namespace {
@@ -317,6 +321,7 @@ void carve(rr_handle* h) {
   float* aug = (float*)at(R_AUG);
   h->op.aug_a = aug;
   h->op.aug_b = aug ? aug + (size_t)mv_tc_pad(h->n) * kAugFloats : nullptr;
+  h->op.vsplit = aug ? (uint16_t*)(aug + 2 * (size_t)mv_tc_pad(h->n) * kAugFloats) : nullptr;
   double* v64 = (double*)at(R_V64);
   for (int i = 0; i < 4; ++i) h->v64[i] = v64 + i * vec;
   double* stg = (double*)at(R_STAGE);
@@ -811,7 +816,7 @@ rr_status sketch_product(rr_handle* h, double shift, bool tc, int64_t ldo) {
       if (err) return RR_ERR_TIMEOUT;
       return RR_OK;
     }
-    if (s != RR_ERR_UNSUPPORTED || h->o.kernel_impl == 2) return s;
+    if (s != RR_ERR_UNSUPPORTED || h->o.kernel_impl >= 2) return s;
   }
   (void)n;
   if (h->op.kind == RR_OP_CSR && h->sketch == RR_SKETCH_SPARSE_SIGN && h->o.q == 0)
@@ -833,8 +838,10 @@ rr_status build_impl(rr_handle* h) {
   RR_CUDA_TRY(cudaMemsetAsync(h->dstatus, 0, h->L.size[R_STATUS], st));
   RR_CUDA_TRY(cudaMemsetAsync(h->V[0], 0, h->L.size[R_VT], st));   // zero pad rows
   if (h->op.kind == RR_OP_GAUSS_KERNEL) prepare_kernel_points(h->op, st);
-  // float32 kernel products on the tensor cores (kernel_impl 0 = auto, 2 = on)
+  // float32 kernel products on the tensor cores (kernel_impl 0 = auto, 2 =
+  // exponents on the tensor cores, 3 = K v on them too)
   h->op.use_tc = 0;
+  h->op.tc2 = 0;
   if (h->op.aug_a && h->o.kernel_impl != 1) {
     prepare_mv_tc(h->op, h->op.aug_a, h->op.aug_b, st);
     if (encode_mv_tc(h->op.aug_a, h->op.aug_b, n, h->amap, h->bmap)) {
@@ -842,7 +849,14 @@ rr_status build_impl(rr_handle* h) {
       h->op.bmap = h->bmap;
       h->op.tc_err = h->dstatus + 2;
       h->op.use_tc = 1;
-    } else if (h->o.kernel_impl == 2) {
+      if (h->o.kernel_impl == 3) {
+        if (!encode_mv_tc2(h->op.aug_b, h->op.vsplit, n, h->bmap64, h->vmap))
+          return RR_ERR_UNSUPPORTED;
+        h->op.bmap64 = h->bmap64;
+        h->op.vmap = h->vmap;
+        h->op.tc2 = 1;
+      }
+    } else if (h->o.kernel_impl >= 2) {
       return RR_ERR_UNSUPPORTED;
     }
   }

@@ -74,6 +74,12 @@ struct OpDev {
   const void* amap;
   const void* bmap;
   int* tc_err;
+  // both contractions on the tensor cores (k_matvec_tc2.cu): bf16 split
+  // vector scratch and the maps of 64-point tiles and of that scratch
+  int tc2;
+  uint16_t* vsplit;
+  const void* bmap64;
+  const void* vmap;
   // when set (inside the Krylov iterations), the product kernels of the
   // kernel operator return at once if no column of gate[0..gate_mp) is active
   const ColState* gate;
@@ -187,9 +193,19 @@ constexpr int kAugFloats = 32;
 void prepare_mv_tc(const OpDev& op, float* Aaug, float* Baug, cudaStream_t st);
 bool encode_mv_tc(const float* Aaug, const float* Baug, int64_t n, void* amap, void* bmap);
 int mv_tc_nsplit(int64_t n);
+int64_t tc_persistent_ctas(int64_t total);
+bool tc_encode_2d(void* map, bool bf16, const void* base, uint64_t inner, uint64_t outer,
+                  uint32_t box_inner, uint32_t box_outer);
 bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const float* V,
                   float* part, int nsplit, int* err, const ColState* gate, int gate_mp,
                   cudaStream_t st);
+// k_matvec_tc2.cu -- the same product with K v also on the tensor cores
+size_t mv_tc2_vsplit_elems(int64_t n);
+bool encode_mv_tc2(const float* Baug, const uint16_t* vsplit, int64_t n, void* bmap64, void* vmap);
+int mv_tc2_nsplit(int64_t n);
+bool kernel_mv_tc2(const void* amap, const void* bmap64, const void* vmap, int64_t n, int mp,
+                   const float* V, uint16_t* vsplit, float* part, int nslots, int* err,
+                   const ColState* gate, int gate_mp, cudaStream_t st);
 
 // k_sketch_tc.cu -- tensor-core sketch of the Gaussian-kernel operator
 size_t sketch_tc_smem_bytes();

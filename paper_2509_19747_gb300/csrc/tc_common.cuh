@@ -223,6 +223,70 @@ __device__ __forceinline__ float lds32(uint32_t saddr) {
   return v;
 }
 
+// tcgen05.st of 16 consecutive 32-bit columns of this warp's lane quarter;
+// complete (visible to tcgen05.mma after a thread-sync fence) only after
+// tmem_wait_st()
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// tcgen05.mma kind::f16 with the A operand in tensor memory (M = 128: row i
+// in lane i, K along the columns, two 16-bit elements per column, the lower
+// K index in the lower half)
+__device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                           uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// ------------------------------------------------ stream-K work ranges
+// Work items (row pair, point tile), row pair major, are cut into one
+// contiguous range per CTA: CTA c of g owns [floor(c total / g),
+// floor((c + 1) total / g)).  A range falls into segments, one per row pair it
+// touches; the partial sums of a segment go to slot "c - first CTA touching
+// the pair".
+__host__ __device__ __forceinline__ int64_t sk_cta_of(int64_t x, int64_t total, int64_t g) {
+  return ((x + 1) * g + total - 1) / total - 1;
+}
+struct SkSeg {
+  int64_t pair, t0;                  // row pair, first tile within the pair
+  int ntiles, slot;
+  bool last;                         // the segment ends the row pair
+};
+__device__ __forceinline__ SkSeg sk_seg(int64_t x, int64_t xend, int64_t tiles, int64_t total,
+                                        int64_t g, int64_t c) {
+  SkSeg w;
+  w.pair = x / tiles;
+  const int64_t pend = (w.pair + 1) * tiles;
+  const int64_t e = xend < pend ? xend : pend;
+  w.t0 = x - w.pair * tiles;
+  w.ntiles = (int)(e - x);
+  w.slot = (int)(c - sk_cta_of(w.pair * tiles, total, g));
+  w.last = e == pend;
+  return w;
+}
+// the most CTAs whose ranges touch one row pair (partial-sum slots per row)
+inline int sk_nslots(int64_t pairs, int64_t tiles, int64_t g) {
+  const int64_t total = pairs * tiles;
+  int64_t most = 1;
+  for (int64_t p = 0; p < pairs; ++p) {
+    const int64_t s = sk_cta_of((p + 1) * tiles - 1, total, g) - sk_cta_of(p * tiles, total, g) + 1;
+    if (s > most) most = s;
+  }
+  return (int)most;
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                    smem_u32(dst_smem)),

@@ -348,11 +348,47 @@ def test_tensor_core_kernel_product(cuda_lib, n, m):
         ref = op.matmat(V) + mu * V
         scale = op.matmat(np.abs(V)) + mu * np.abs(V)
         idx = slice(None)
-    for impl in (1, 2):
+    # impl 3 also contracts K v on the tensor cores with K and v each split
+    # into two bf16 parts (hi = RN(x), lo = RN(x - hi): relative error
+    # <= 2^-16 each), so an entry's product is off by <= 2^-15 more: with the
+    # exponent error (ln2 x 4e-5) still within 1e-4
+    for impl in (1, 2, 3):
         h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, 16, "gaussian", seed=26,
                       precision="mixed", max_rhs=m, kernel_impl=impl)
         w = h.apply_operator(dev(V)).cpu().numpy().reshape(n, m)[idx]
         assert np.max(np.abs(w - ref) / scale) <= (2e-5 if impl == 1 else 1e-4), impl
+
+
+@pytest.mark.parametrize("m", [1, 4])
+def test_two_contraction_product_solve(cuda_lib, m):
+    """Mixed-precision solves with K v on the tensor cores (kernel_impl 3):
+    the float64 residual meets rtol and the inner iteration counts stay within
+    a few of those with K v on the float32 cores (kernel_impl 2)."""
+    rr = cuda_lib
+    n, k, mu = 3001, 80, 1e-3
+    X = W.mixture_points(n, seed=63)
+    op = O.GaussKernelOp(X)
+    B = W.gaussian_rhs(n, m, 63)
+    its = []
+    for impl in (2, 3):
+        h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=63,
+                      precision="mixed", max_rhs=m, kernel_impl=impl)
+        for _ in range(2):     # the split scratch is rewritten by every product
+            x, status, infos = h.solve(dev(B), rtol=1e-6)
+            assert status == rr.RR_OK
+            assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), B) <= 1e-6)
+        its.append([i["inner_iters"] for i in infos])
+        h.close()
+    for a, b in zip(*its):
+        assert abs(a - b) <= max(3, 0.05 * b)
+
+
+def test_kernel_impl_out_of_range(cuda_lib):
+    rr = cuda_lib
+    X = W.mixture_points(300, seed=64)
+    with pytest.raises(rr.RandRandError):
+        rr.Handle(rr.Operator.gauss_kernel(dev(X)), 1e-3, 16, "gaussian", seed=64,
+                  precision="mixed", kernel_impl=4)
 
 
 # ------------------------------------------- persistent fused PCG step
