@@ -428,9 +428,13 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df2(const float* __restr
                                                           int64_t cols_per_split,
                                                           const double* __restrict__ V,
                                                           double* __restrict__ part) {
-  __shared__ __align__(16) float sx[kKmvTile * kMaxDim];
-  __shared__ float2 spn[kKmvTile];
-  __shared__ float2 sv[kKmvTile * MP];
+  // the tile is staged as column pairs (2P, 2P + 1) so that every packed
+  // operand is one 64- or 128-bit shared load: coordinates (x_a[d], x_b[d]),
+  // norms (hi_a, hi_b, lo_a, lo_b), vector entries (hi_a, hi_b, lo_a, lo_b)
+  constexpr int kPairs = kKmvTile / 2;
+  __shared__ __align__(16) float2 sx2[kPairs * kMaxDim];
+  __shared__ __align__(16) float4 spn2[kPairs];
+  __shared__ __align__(16) float4 sv2[kPairs * MP];
   __shared__ float2 tab[65];
   if (threadIdx.x < 65) {
     const double t = exp2((double)((int)threadIdx.x - 32) / 64.0);
@@ -462,32 +466,43 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df2(const float* __restr
   if (j1 > n) j1 = n;
   for (int64_t jt = j0; jt < j1; jt += kKmvTile) {
     const int cnt = (int)((j1 - jt < kKmvTile) ? (j1 - jt) : kKmvTile);
+    const int npairs = (cnt + 1) >> 1;      // an odd last column is paired with itself
     __syncthreads();
-    for (int e = threadIdx.x; e < cnt * dim; e += kKmvRows) sx[(e / dim) * kMaxDim + e % dim] = x[jt * dim + e];
-    for (int e = threadIdx.x; e < cnt; e += kKmvRows) spn[e] = pn[jt + e];
-    for (int e = threadIdx.x; e < cnt * MP; e += kKmvRows) {
-      const df v = df_from_double(V[jt * MP + e]);
-      sv[e] = make_float2(v.h, v.l);
+    for (int e = threadIdx.x; e < npairs * dim; e += kKmvRows) {
+      const int P = e / dim, d = e % dim;
+      const int ja = 2 * P, jb = (2 * P + 1 < cnt) ? 2 * P + 1 : 2 * P;
+      sx2[P * kMaxDim + d] = make_float2(x[(jt + ja) * dim + d], x[(jt + jb) * dim + d]);
+    }
+    for (int P = threadIdx.x; P < npairs; P += kKmvRows) {
+      const int ja = 2 * P, jb = (2 * P + 1 < cnt) ? 2 * P + 1 : 2 * P;
+      const float2 pa = pn[jt + ja], pb = pn[jt + jb];
+      spn2[P] = make_float4(pa.x, pb.x, pa.y, pb.y);
+    }
+    for (int e = threadIdx.x; e < npairs * MP; e += kKmvRows) {
+      const int P = e / MP, cc = e % MP;
+      const int ja = 2 * P, jb = (2 * P + 1 < cnt) ? 2 * P + 1 : 2 * P;
+      const df va = df_from_double(V[(jt + ja) * MP + cc]);
+      const df vb = df_from_double(V[(jt + jb) * MP + cc]);
+      sv2[e] = make_float4(va.h, vb.h, va.l, vb.l);
     }
     __syncthreads();
-    for (int jj = 0; jj < cnt; jj += 2) {
+    for (int P = 0; P < npairs; ++P) {
+      const int jj = 2 * P;
       const bool pair = jj + 1 < cnt;
-      const int jb = pair ? jj + 1 : jj;
-      const float* xa = sx + jj * kMaxDim;
-      const float* xb = sx + jb * kMaxDim;
+      const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(sx2 + P * kMaxDim);
       // p_i . p_j in double-float
-      df2 c = two_prod2(xi[0], mk2(xa[0], xb[0]));
+      df2 c = two_prod2(xi[0], p2{xp[0]});
 #pragma unroll
       for (int d = 1; d < kMaxDim; ++d) {
         if (d < dim) {
-          const df2 t = two_prod2(xi[d], mk2(xa[d], xb[d]));
+          const df2 t = two_prod2(xi[d], p2{xp[d]});
           const df2 s2 = two_sum2(c.h, t.h);
           c = {s2.h, add2(add2(c.l, t.l), s2.l)};
         }
       }
-      const float2 pa = spn[jj], pb = spn[jb];
-      df2 a = two_sum2(pnih, mk2(pa.x, pb.x));
-      a.l = add2(a.l, add2(pnil, mk2(pa.y, pb.y)));
+      const ulonglong2 pp = *reinterpret_cast<const ulonglong2*>(spn2 + P);
+      df2 a = two_sum2(pnih, p2{pp.x});
+      a.l = add2(a.l, add2(pnil, p2{pp.y}));
       df2 b = two_sum2(a.h, mul2(m2, c.h));
       b.l = add2(b.l, sub2(a.l, mul2(two, c.l)));
       const df2 d2 = fast_two_sum2(b.h, b.l);
@@ -526,8 +541,8 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df2(const float* __restr
       K.l = mul2(K.l, sc);
 #pragma unroll
       for (int cc = 0; cc < MP; ++cc) {
-        const float2 wa = sv[jj * MP + cc], wb = sv[jb * MP + cc];
-        const p2 vh = mk2(wa.x, wb.x), vl = mk2(wa.y, wb.y);
+        const ulonglong2 vv = *reinterpret_cast<const ulonglong2*>(sv2 + P * MP + cc);
+        const p2 vh = p2{vv.x}, vl = p2{vv.y};
         df2 pr = two_prod2(K.h, vh);
         pr.l = fma2(K.h, vl, pr.l);
         pr.l = fma2(K.l, vh, pr.l);
