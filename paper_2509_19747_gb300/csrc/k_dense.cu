@@ -8,6 +8,7 @@
 // triangular inverse, tile-parallel trailing updates) instead of one CTA.
 #include <cmath>
 
+#include "df.cuh"
 #include "rr_common.cuh"
 
 namespace rr {
@@ -80,6 +81,191 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int64_t M, int64_t N, int64_t K
   }
 }
 
+// ======================================================================
+// Float32 tiles for the n x k products of the basis construction (Y R^-1,
+// Y^T Y, Omega^T Y): CTA tile 64 x 128, 256 threads with 4 x 8 outputs each
+// (rows 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3 and 64 + 4 tx ..), K steps
+// of 16 staged k-major in shared memory so that a step costs three 128-bit
+// shared loads per 32 FMAs, the next step's global loads held in registers
+// while the current one is computed.  Used when the leading dimensions and
+// the widths are multiples of 4 (16-byte vectors).
+// ======================================================================
+constexpr int kSgM = 64, kSgN = 128, kSgK = 16;
+constexpr int kSgFold = 256;   // rows summed in float32 before a fold
+
+__device__ __forceinline__ void sg_step(const float (*As)[kSgM], const float (*Bs)[kSgN], int ty,
+                                        int tx, float (&acc)[4][8]) {
+#pragma unroll
+  for (int kk = 0; kk < kSgK; ++kk) {
+    const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+  }
+}
+
+__device__ __forceinline__ float4 ld4_or_zero(const float* p, bool ok) {
+  return ok ? *reinterpret_cast<const float4*>(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// C = alpha A B + beta D (A: M x K, B: K x N, row-major)
+__global__ void __launch_bounds__(256) k_sgemm_nn(int64_t M, int64_t N, int64_t K, float alpha,
+                                                  const float* __restrict__ A, int64_t lda,
+                                                  const float* __restrict__ B, int64_t ldb,
+                                                  float beta, const float* __restrict__ D,
+                                                  int64_t ldd, float* __restrict__ C, int64_t ldc) {
+  __shared__ __align__(16) float As[2][kSgK][kSgM];
+  __shared__ __align__(16) float Bs[2][kSgK][kSgN];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int64_t m0 = (int64_t)blockIdx.y * kSgM, n0 = (int64_t)blockIdx.x * kSgN;
+  // loads of one step: A rows m0 + tid / 4, columns k0 + 4 (tid % 4) (stored
+  // transposed); B rows k0 + tid / 32 and k0 + 8 + tid / 32, columns 4 (tid % 32)
+  const int ar = tid / 4, ac = (tid % 4) * 4;
+  const int br = tid / 32, bc = (tid % 32) * 4;
+  float4 ra, rb0, rb1;
+  auto load = [&](int64_t k0) {
+    ra = ld4_or_zero(A + (m0 + ar) * lda + k0 + ac, m0 + ar < M && k0 + ac < K);
+    rb0 = ld4_or_zero(B + (k0 + br) * ldb + n0 + bc, k0 + br < K && n0 + bc < N);
+    rb1 = ld4_or_zero(B + (k0 + 8 + br) * ldb + n0 + bc, k0 + 8 + br < K && n0 + bc < N);
+  };
+  auto store = [&](int buf) {
+    As[buf][ac + 0][ar] = ra.x;
+    As[buf][ac + 1][ar] = ra.y;
+    As[buf][ac + 2][ar] = ra.z;
+    As[buf][ac + 3][ar] = ra.w;
+    *reinterpret_cast<float4*>(&Bs[buf][br][bc]) = rb0;
+    *reinterpret_cast<float4*>(&Bs[buf][8 + br][bc]) = rb1;
+  };
+  float acc[4][8];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int64_t k0 = 0; k0 < K; k0 += kSgK) {
+    const bool more = k0 + kSgK < K;
+    if (more) load(k0 + kSgK);
+    sg_step(As[buf], Bs[buf], ty, tx, acc);
+    if (more) store(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int64_t gi = m0 + ty * 4 + x;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t gj = n0 + h * 64 + tx * 4;
+      if (gj >= N) continue;
+      float4 v = make_float4(alpha * acc[x][4 * h], alpha * acc[x][4 * h + 1],
+                             alpha * acc[x][4 * h + 2], alpha * acc[x][4 * h + 3]);
+      if (D) {
+        const float4 d = *reinterpret_cast<const float4*>(D + gi * ldd + gj);
+        v.x = fmaf(beta, d.x, v.x);
+        v.y = fmaf(beta, d.y, v.y);
+        v.z = fmaf(beta, d.z, v.z);
+        v.w = fmaf(beta, d.w, v.w);
+      }
+      *reinterpret_cast<float4*>(C + gi * ldc + gj) = v;
+    }
+  }
+}
+
+// part[s] = A[rows_s]^T B[rows_s] (A: rows x k1, B: rows x k2, row-major):
+// products summed in float32 over blocks of 256 rows, each block folded into
+// double-float accumulators (float32 two-sums; float64 adds run at a small
+// fraction of the float32 rate here), written as float64
+__global__ void __launch_bounds__(256) k_sgram(const float* __restrict__ A, int64_t lda,
+                                               const float* __restrict__ B, int64_t ldb,
+                                               int64_t nrows, int k1, int k2, int symmetric,
+                                               int64_t rows_per_split, double* __restrict__ part) {
+  const int64_t i0 = (int64_t)blockIdx.y * kSgM, j0 = (int64_t)blockIdx.x * kSgN;
+  if (symmetric && i0 >= j0 + kSgN) return;      // only i > j in this tile
+  __shared__ __align__(16) float As[2][kSgK][kSgM];
+  __shared__ __align__(16) float Bs[2][kSgK][kSgN];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int64_t r0 = (int64_t)blockIdx.z * rows_per_split;
+  const int64_t r1 = (r0 + rows_per_split < nrows) ? r0 + rows_per_split : nrows;
+  // loads of one step: A rows r + tid / 16, columns i0 + 4 (tid % 16); B rows
+  // r + tid / 32 and r + 8 + tid / 32, columns j0 + 4 (tid % 32)
+  const int ar = tid / 16, ac = (tid % 16) * 4;
+  const int br = tid / 32, bc = (tid % 32) * 4;
+  float4 ra, rb0, rb1;
+  auto load = [&](int64_t r) {
+    ra = ld4_or_zero(A + (r + ar) * lda + i0 + ac, r + ar < r1 && i0 + ac < k1);
+    rb0 = ld4_or_zero(B + (r + br) * ldb + j0 + bc, r + br < r1 && j0 + bc < k2);
+    rb1 = ld4_or_zero(B + (r + 8 + br) * ldb + j0 + bc, r + 8 + br < r1 && j0 + bc < k2);
+  };
+  auto store = [&](int buf) {
+    *reinterpret_cast<float4*>(&As[buf][ar][ac]) = ra;
+    *reinterpret_cast<float4*>(&Bs[buf][br][bc]) = rb0;
+    *reinterpret_cast<float4*>(&Bs[buf][8 + br][bc]) = rb1;
+  };
+  float acc[4][8], hi[4][8], lo[4][8];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+      acc[x][y] = 0.f;
+      hi[x][y] = 0.f;
+      lo[x][y] = 0.f;
+    }
+  auto fold = [&]() {
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        const df s = two_sum(hi[x][y], acc[x][y]);
+        hi[x][y] = s.h;
+        lo[x][y] += s.l;
+        acc[x][y] = 0.f;
+      }
+  };
+  if (r0 < r1) {
+    load(r0);
+    store(0);
+  }
+  __syncthreads();
+  int buf = 0, steps = 0;
+  for (int64_t r = r0; r < r1; r += kSgK) {
+    const bool more = r + kSgK < r1;
+    if (more) load(r + kSgK);
+    sg_step(As[buf], Bs[buf], ty, tx, acc);
+    if (more) store(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+    if (++steps == kSgFold / kSgK) {
+      fold();
+      steps = 0;
+    }
+  }
+  fold();
+  double* out = part + (int64_t)blockIdx.z * k1 * k2;
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int64_t gi = i0 + ty * 4 + x;
+    if (gi >= k1) continue;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+      const int64_t gj = j0 + (y < 4 ? tx * 4 + y : 64 + tx * 4 + y - 4);
+      if (gj < k2) out[gi * k2 + gj] = (double)hi[x][y] + (double)lo[x][y];
+    }
+  }
+}
+
+static bool sg_aligned(const void* p, int64_t ld, int64_t width) {
+  return ((uintptr_t)p % 16) == 0 && ld % 4 == 0 && width % 4 == 0;
+}
+
 template <typename T>
 static void gemm_launch(int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t lda,
                         const T* B, int64_t ldb, double beta, const T* D, int64_t ldd, T* C,
@@ -100,6 +286,13 @@ template <typename T>
 void gemm_nn(int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t lda,
              const T* B, int64_t ldb, double beta, const T* D, int64_t ldd, T* C,
              int64_t ldc, cudaStream_t st) {
+  if (sizeof(T) == 4 && sg_aligned(A, lda, K) && sg_aligned(B, ldb, N) && sg_aligned(C, ldc, N) &&
+      (!D || sg_aligned(D, ldd, N))) {
+    dim3 grid((unsigned)cdiv(N, kSgN), (unsigned)cdiv(M, kSgM));
+    k_sgemm_nn<<<grid, 256, 0, st>>>(M, N, K, (float)alpha, (const float*)A, lda, (const float*)B,
+                                     ldb, (float)beta, (const float*)D, ldd, (float*)C, ldc);
+    return;
+  }
   gemm_launch<T>(M, N, K, alpha, A, lda, B, ldb, beta, D, ldd, C, ldc, 0, 0, st);
 }
 
@@ -205,9 +398,10 @@ __global__ void __launch_bounds__(256) k_gram_partial(const T* __restrict__ A, i
 }
 
 int gram_nsplit(int64_t nrows, int k1, int k2) {
-  const int64_t tiles = cdiv(k1, 32) * cdiv(k2, 32);
-  int64_t ns = cdiv(4 * 152, tiles);
-  const int64_t maxs = cdiv(nrows, 64);  // at least 64 rows per split
+  // about two CTAs of the float32 64 x 128 tiles per SM
+  const int64_t tiles = cdiv(k1, kSgM) * cdiv(k2, kSgN);
+  int64_t ns = cdiv(2 * 152, tiles);
+  const int64_t maxs = cdiv(nrows, 256);  // at least one 256-row block per split
   if (ns > maxs) ns = maxs;
   if (ns < 1) ns = 1;
   if (ns > 64) ns = 64;
@@ -227,6 +421,13 @@ static void gram_launch(const T* A, int64_t lda, const T* B, int64_t ldb, int64_
 template <typename T>
 void gram_partial(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t nrows, int k1,
                   int k2, bool symmetric, int nsplit, double* part, cudaStream_t st) {
+  if (sizeof(T) == 4 && sg_aligned(A, lda, k1) && sg_aligned(B, ldb, k2)) {
+    const int64_t rps = cdiv(cdiv(nrows, nsplit), kSgK) * kSgK;
+    dim3 grid((unsigned)cdiv(k2, kSgN), (unsigned)cdiv(k1, kSgM), (unsigned)nsplit);
+    k_sgram<<<grid, 256, 0, st>>>((const float*)A, lda, (const float*)B, ldb, nrows, k1, k2,
+                                  symmetric ? 1 : 0, rps, part);
+    return;
+  }
   gram_launch<T>(A, lda, B, ldb, nrows, k1, k2, symmetric, nsplit, 0, part, st);
 }
 
