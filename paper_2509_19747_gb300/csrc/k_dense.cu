@@ -485,34 +485,53 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int 
   }
   __syncthreads();
   for (int p = 0; p < jb; ++p) {
-    const double app = S[p][p];
-    const bool bad = !(app > 0.0) || !isfinite(app);
-    const double r = bad ? 1.0 : rsqrt(app);
-    __syncthreads();
+    // the pivot (one float64 reciprocal square root, by one thread)
     if (tid == 0) {
+      const double app = S[p][p];
+      const bool bad = !(app > 0.0) || !isfinite(app);
+      const double r = bad ? 1.0 : rsqrt(app);
       if (bad) atomicCAS(status, 0, j0 + p + 1);
       S[p][p] = bad ? 1.0 : app * r;
       rd[p] = r;
     }
+    __syncthreads();
+    const double r = rd[p];
     for (int q = p + 1 + tid; q < jb; q += blockDim.x) S[p][q] *= r;
     __syncthreads();
-    // trailing update of the upper part: S[i][q] -= S[p][i] S[p][q], p < i <= q
+    // trailing update of the upper part: S[i][q] -= S[p][i] S[p][q] for
+    // p < i <= q, enumerated over the upper triangle only (e -> (i, q))
     const int rem = jb - p - 1;
-    for (int e = tid; e < rem * rem; e += blockDim.x) {
-      const int i = p + 1 + e / rem, q = p + 1 + e % rem;
-      if (q >= i) S[i][q] -= S[p][i] * S[p][q];
+    const int tri = rem * (rem + 1) / 2;
+    for (int e = tid; e < tri; e += blockDim.x) {
+      // row-major upper-triangle index: row a has rem - a entries
+      int a = (int)((2.0f * rem + 1.0f - sqrtf((2.0f * rem + 1.0f) * (2.0f * rem + 1.0f) - 8.0f * e)) * 0.5f);
+      if (a < 0) a = 0;
+      while (a > 0 && a * (2 * rem - a + 1) / 2 > e) --a;
+      while ((a + 1) * (2 * rem - a) / 2 <= e) ++a;
+      const int b = e - a * (2 * rem - a + 1) / 2 + a;
+      const int i = p + 1 + a, q = p + 1 + b;
+      S[i][q] -= S[p][i] * S[p][q];
     }
     __syncthreads();
   }
-  // inverse of the upper factor: column-oriented back substitution, one
-  // thread per column c of Wi (jb <= 32)
-  if (tid < jb) {
-    const int c = tid;
-    for (int r = 0; r < jb; ++r) Wi[r][c] = 0.0;
-    for (int r = c; r >= 0; --r) {
-      double s = (r == c) ? 1.0 : 0.0;
-      for (int q = r + 1; q <= c; ++q) s -= S[r][q] * Wi[q][c];
-      Wi[r][c] = s * rd[r];
+  // inverse of the upper factor: column-oriented back substitution with
+  // eight threads per column c of Wi (jb <= 32); each step r sums
+  // S[r][q] Wi[q][c] over q = r+1..c in eight strided parts and a shuffle tree
+  {
+    const int c = tid >> 3, part = tid & 7;
+    const bool col = c < jb;
+    if (col && part == 0)
+      for (int r = 0; r < jb; ++r) Wi[r][c] = 0.0;
+    __syncwarp();
+    for (int r = jb - 1; r >= 0; --r) {
+      double s = 0.0;
+      if (col && r <= c)
+        for (int q = r + 1 + part; q <= c; q += 8) s += S[r][q] * Wi[q][c];
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      if (col && r <= c && part == 0) Wi[r][c] = (((r == c) ? 1.0 : 0.0) - s) * rd[r];
+      __syncwarp();
     }
   }
   __syncthreads();
