@@ -406,7 +406,7 @@ def roofline(name, stat, clocks):
         # double-float restart residual: ~190 float32-pipe ops per entry
         ops = float(n) * n * 190
         peak = 152 * 128 * f
-        return {"kernel": "k_kernel_mv_df", "bound": "alu", "achieved": ops / avg_s / 1e9,
+        return {"kernel": "k_kernel_mv_df2", "bound": "alu", "achieved": ops / avg_s / 1e9,
                 "peak": peak / 1e9, "unit": "G f32-op/s", "frac": ops / avg_s / peak,
                 "traffic": None, "launches": cnt, "avg_us": avg_s * 1e6}
     # sketch: 2 n^2 k flops on the tensor cores (bf16, dense)
