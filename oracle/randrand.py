@@ -28,7 +28,11 @@ arXiv 2509.19747):
 * PCG / CG with restarts after each residual reduction by eta = 1e-2
   (Sec. 7 experimental setup; Alg. 4 step 9, Alg. 7 step 10), the restart
   residual b - A_mu x recomputed in float64;
-* the exact solution x* = A_mu^-1 b by a dense Cholesky solve.
+* the exact solution x* = A_mu^-1 b by a dense Cholesky solve;
+* several shifts from one sketch (Sec. 5.1): A Omega computed once, Y_mu =
+  A Omega + mu Omega per shift, and the Gram separation (A Omega + mu
+  Omega)^T (A Omega + mu Omega) = Omega^T A^T A Omega + 2 mu Omega^T A Omega
+  + mu^2 Omega^T Omega of the parameter-free projections.
 
 Readings where the paper is silent: 20 power iterations from seeded start
 vectors, estimate = |w_20| (norm of the last image of a unit vector); the
@@ -271,7 +275,11 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
           omega_precision: str = "fp64", orth: str = "householder",
           gamma: int = 8, l_sk: int | None = None, gamma_sk: int = 8,
           power_iters: int = 20, rho: float | None = None,
-          tau: float | None = None, q: int = 0) -> Build:
+          tau: float | None = None, q: int = 0,
+          a_omega: np.ndarray | None = None) -> Build:
+    """a_omega: A Omega computed once for several shifts (Sec. 5.1): then
+    omega must be the Omega it was computed from, and Y_mu = a_omega + mu
+    Omega replaces the product."""
     n = op.n
     if not (1 <= k <= n):
         raise ValueError("need 1 <= k <= n")
@@ -282,8 +290,14 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
         Om = np.asarray(omega, dtype=np.float64)
         for _ in range(q):
             Om = op.matmat(Om)
-    # Alg. 7 step 1 / Alg. 4 step 1: Y_mu = A Omega + mu Omega
-    Ymu = op.matmat(Om) + mu * Om
+    # Alg. 7 step 1 / Alg. 4 step 1: Y_mu = A Omega + mu Omega (A Omega
+    # recycled across shifts when given, Sec. 5.1)
+    if a_omega is not None:
+        if omega is None:
+            raise ValueError("a_omega needs the omega it was computed from")
+        Ymu = np.asarray(a_omega, dtype=np.float64) + mu * Om
+    else:
+        Ymu = op.matmat(Om) + mu * Om
     if orth == "householder":
         Q, R = orthogonalize_householder(Ymu)
     elif orth == "qless":
@@ -339,6 +353,36 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
     else:
         raise ValueError(variant)
     return b
+
+
+# ==========================================================================
+# Multiple shifts (Sec. 5.1): the parameter-free pieces of one sketch
+# ==========================================================================
+@dataclasses.dataclass
+class ShiftSketch:
+    """Omega, A Omega and the parameter-free Gram matrices of Sec. 5.1:
+    P2 = (A Omega)^T (A Omega), M0 = Omega^T A Omega (symmetrized), S0 =
+    Omega^T Omega."""
+    Omega: np.ndarray
+    AOmega: np.ndarray
+    P2: np.ndarray
+    M0: np.ndarray
+    S0: np.ndarray
+
+
+def shift_sketch(op, k: int, sketch: str = "gaussian", seed: int = 0, gamma: int = 8,
+                 omega_precision: str = "fp64") -> ShiftSketch:
+    Om = make_omega(op.n, k, sketch, seed, gamma, omega_precision)
+    AOm = op.matmat(Om)
+    M0 = Om.T @ AOm
+    return ShiftSketch(Omega=Om, AOmega=AOm, P2=AOm.T @ AOm, M0=0.5 * (M0 + M0.T),
+                       S0=Om.T @ Om)
+
+
+def shifted_gram(sk: ShiftSketch, mu: float) -> np.ndarray:
+    """(A Omega + mu Omega)^T (A Omega + mu Omega) from the parameter-free
+    projections (the Gram separation of Sec. 5.1; A symmetric)."""
+    return sk.P2 + 2.0 * mu * sk.M0 + mu * mu * sk.S0
 
 
 # ==========================================================================

@@ -457,3 +457,39 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     bad = O.build(op, -mu, k, "gaussian", seed=1)
     assert np.linalg.norm((op.A + mu * I) @ bad.Omega - bad.Q @ bad.R) > 1e-8
     assert orig is O.shifted
+
+
+# ------------------------------------------------ multiple shifts (Sec. 5.1)
+def test_shift_gram_separation_matches_direct_gram():
+    """The Gram separation of the parameter-free projections equals the Gram
+    of Y_mu formed directly, for several shifts (A symmetric)."""
+    P = W.dense_power_spectrum(300, seed=81, power=2.0)
+    op = O.DenseOp(P.A)
+    sk = O.shift_sketch(op, 24, "gaussian", seed=81)
+    for mu in (0.0, 1e-4, 0.3, 5.0):
+        Ymu = P.A @ sk.Omega + mu * sk.Omega
+        direct = Ymu.T @ Ymu
+        sep = O.shifted_gram(sk, mu)
+        assert np.linalg.norm(sep - direct) <= 1e-12 * np.linalg.norm(direct)
+        # its Cholesky factor is the R of Y_mu = Q R (unique with a positive
+        # diagonal), as the Householder QR of Y_mu gives it
+        R = np.linalg.cholesky(sep).T
+        _, Rh = O.householder_qr(Ymu)
+        assert np.allclose(R, Rh, rtol=0, atol=1e-9 * np.abs(Rh).max())
+
+
+def test_recycled_sketch_build_equals_fresh_build():
+    """A build from the recycled A Omega (Sec. 5.1) equals a fresh build at
+    the same shift with the same Omega: R, G, tau and the solution."""
+    P = W.dense_power_spectrum(300, seed=82, power=2.0)
+    op = O.DenseOp(P.A)
+    sk = O.shift_sketch(op, 24, "gaussian", seed=82)
+    B = W.gaussian_rhs(300, 2, 82)
+    for mu in (1e-3, 0.2):
+        fresh = O.build(op, mu, 24, "gaussian", seed=82, omega=sk.Omega)
+        rec = O.build(op, mu, 24, "gaussian", seed=82, omega=sk.Omega, a_omega=sk.AOmega)
+        assert np.allclose(rec.R, fresh.R, rtol=1e-12, atol=1e-12 * np.abs(fresh.R).max())
+        assert np.allclose(rec.G, fresh.G, rtol=1e-10, atol=1e-10 * np.abs(fresh.G).max())
+        assert rec.tau == pytest.approx(fresh.tau, rel=1e-10)
+        x, info = O.solve(rec, B, rtol=1e-12)
+        assert np.linalg.norm(x - O.exact_solve(op, mu, B)) <= 1e-8 * np.linalg.norm(x)
