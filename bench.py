@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--workload", default="kernel_ridge",
-                    choices=["kernel_ridge", "sparse_diffusion", "batched", "serving"])
+                    choices=["kernel_ridge", "sparse_diffusion", "batched", "serving", "shift_path"])
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
     ap.add_argument("--workers", type=int, default=0, help="batched/serving: 0 = autotune")
     ap.add_argument("--kernel-impl", type=int, default=0,
@@ -466,6 +466,8 @@ SPARSE = dict(workload="sparse_diffusion", side=512, n=262144, mu=1e-6, k=256, l
               orth="rand_cholqr (basis-less)", seed=0x52523)
 BATCHED = dict(workload="batched_kernel_ridge", systems=64, n_min=2000, n_max=16000,
                k="n/40", mu="10^U(-5,-2)", nrhs=8, rtol=1e-6, precision="mixed", seed=0x52524)
+SHIFTS = dict(workload="kernel_ridge_shift_path", n=20000, d=8, k=500, nrhs=4, rtol=1e-6,
+              precision="mixed", mus=[1e-1, 3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 3e-5])
 SERVING = dict(workload="serving_mix", rate_per_s=200.0, kernel_share=0.5, kernel_n=[1000, 32000],
                csr_side=[128, 512], k="n/50", nrhs=1, rtol=1e-6, budget_gb=120.0,
                precision="mixed", seed=0x52525)
@@ -487,7 +489,8 @@ def run_other(args):
             print(json.dumps({"impl": "reference", "workload": args.workload,
                               "unavailable": "the oracle arm times the kernel ridge workload only"}))
         return
-    {"sparse_diffusion": run_sparse, "batched": run_batched, "serving": run_serving}[args.workload](args)
+    {"sparse_diffusion": run_sparse, "batched": run_batched, "serving": run_serving,
+     "shift_path": run_shift_path}[args.workload](args)
 
 
 def run_sparse(args):
@@ -691,6 +694,82 @@ def run_batched(args):
                                     "seconds": seq_s},
                  autotune_s={f"workers={k[0]},iter_impl={k[1]}": v for k, v in tune.items()},
                  solve={"inner_iters_max": max(iters), "inner_iters_median": float(np.median(iters))},
+                 roofline=None, clocks=clocks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_shift_path(args):
+    """A regularization path (Sec. 5.1): the kernel ridge system of the main
+    workload solved for 8 shifts.  One step = the whole path with the sketch
+    kept (one build with keep_sketch, then randrand_set_mu + solve per shift);
+    the same path with a fresh build per shift is timed beside it."""
+    import torch
+    rank, world, local = dist_init(args)
+    torch.cuda.set_device(local)
+    import paper_2509_19747_gb300 as rr
+    cfg = SHIFTS
+    seed = WORKLOAD["seed"] + 1000 * rank
+    X, B = make_inputs(seed)
+    Xd = torch.from_numpy(X).cuda()
+    Bd = torch.from_numpy(B).cuda()
+    op = rr.Operator.gauss_kernel(Xd, WORKLOAD["bandwidth"])
+    mus = cfg["mus"]
+
+    def kept():
+        h = rr.Handle(op, mus[0], cfg["k"], "gaussian", seed=seed, precision=cfg["precision"],
+                      max_rhs=cfg["nrhs"], keep_sketch=True)
+        its = []
+        for i, mu in enumerate(mus):
+            if i > 0:
+                h.set_mu(mu)
+            _, st, infos = h.solve(Bd, rtol=cfg["rtol"])
+            if st != rr.RR_OK:
+                raise RuntimeError(f"shift {mu}: {rr.randrand_status_str(st)}")
+            its.append(max(j["inner_iters"] for j in infos))
+        h.close()
+        return its
+
+    def fresh():
+        its = []
+        for mu in mus:
+            h = rr.Handle(op, mu, cfg["k"], "gaussian", seed=seed, precision=cfg["precision"],
+                          max_rhs=cfg["nrhs"])
+            _, st, infos = h.solve(Bd, rtol=cfg["rtol"])
+            if st != rr.RR_OK:
+                raise RuntimeError(f"shift {mu}: {rr.randrand_status_str(st)}")
+            its.append(max(j["inner_iters"] for j in infos))
+            h.close()
+        return its
+
+    def timed(fn, steps):
+        ms = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = fn()
+            torch.cuda.synchronize()
+            ms.append((time.perf_counter() - t0) * 1e3)
+        return ms, its
+
+    for _ in range(args.warmup):
+        kept()
+    fresh()
+    smi = ClockSampler()
+    barrier(world)
+    smi.start()
+    ms_kept, its = timed(kept, args.steps)
+    barrier(world)
+    clocks = smi.stop()
+    ms_fresh, its_fresh = timed(fresh, max(1, args.steps // 2))
+    ms = max_over_ranks(sum(ms_kept), world) / args.steps
+    line = _line(args, world, "RandRAND-PCG shifts solved/s along a regularization path (sketch kept)",
+                 world * len(mus) * 1000.0 / ms, "solves/s", ms,
+                 {**cfg, "parallelism": f"replicas x{world}", "l2": "inputs of a path exceed L2"},
+                 fresh_builds={"value": len(mus) * 1000.0 / (sum(ms_fresh) / len(ms_fresh)),
+                               "unit": "solves/s", "ms_per_path": sum(ms_fresh) / len(ms_fresh)},
+                 solve={"inner_iters_max_per_shift": its, "fresh_inner_iters_max_per_shift": its_fresh},
+                 timing="host wall clock around each path with the device synchronised",
                  roofline=None, clocks=clocks)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -145,6 +145,13 @@ typedef struct {
                             basis-less CSR form */
   double rho;            /* C variant: <= 0 -> eq:optimal_rho with F = 1/mu     */
   double restart_eta;    /* restart after this residual reduction, default 1e-2 */
+  int32_t keep_sketch;   /* 1: keep A Omega and the shift-free projections
+                            Omega^T A^T A Omega, Omega^T A Omega, Omega^T Omega
+                            (Sec. 5.1) so that randrand_set_mu can rebuild the
+                            preconditioner for another shift without a new
+                            sketch product; costs one more n x k array.  Variant
+                            C with an explicit basis (orth CHOLQR2) and q = 0
+                            only (else RR_ERR_UNSUPPORTED).  Default 0 */
 } rr_build_opts;
 
 typedef struct {
@@ -248,6 +255,24 @@ rr_status randrand_solve_host(rr_handle* h, const double* b_host, int32_t nrhs,
 /* Release a handle (host memory only; the workspace stays the caller's).
  * NULL is accepted.  Never fails.  Synchronises the handle's stream. */
 void randrand_free(rr_handle* h);
+
+/*
+ * Rebuild the preconditioner of h for the shift mu (Sec. 5.1, multiple
+ * shifting parameters): Y_mu = A Omega + mu Omega from the kept A Omega; the
+ * first Cholesky QR pass takes its Gram from the shift-free projections,
+ * (A Omega + mu Omega)^T (A Omega + mu Omega) = Omega^T A^T A Omega +
+ * 2 mu Omega^T A Omega + mu^2 Omega^T Omega, the second pass orthogonalizes
+ * the result as in the build; then Omega^T A_mu Omega = Omega^T A Omega + mu
+ * Omega^T Omega for G, the power iterations for tau, and Q H.  Later solves
+ * use mu.  Synchronous on the handle stream.
+ *   h   a handle built with opts.keep_sketch = 1.
+ *   mu  new shift, >= 0 and finite.
+ * Errors: RR_ERR_INVALID_ARG (h NULL, mu < 0 or not finite),
+ * RR_ERR_UNSUPPORTED (handle built without keep_sketch), RR_ERR_NOT_SPD,
+ * RR_ERR_TIMEOUT, RR_ERR_CUDA.  On an error the handle must not be used
+ * for solves until a successful randrand_set_mu.
+ */
+rr_status randrand_set_mu(rr_handle* h, double mu);
 
 /*
  * Test and inspection hooks (used by the parity tests): copy device-resident

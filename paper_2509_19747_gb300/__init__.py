@@ -58,6 +58,7 @@ class rr_build_opts(ctypes.Structure):
         ("kernel_impl", ctypes.c_int32), ("iter_impl", ctypes.c_int32), ("q", ctypes.c_int32),
         ("rho", ctypes.c_double),
         ("restart_eta", ctypes.c_double),
+        ("keep_sketch", ctypes.c_int32),
     ]
 
 
@@ -131,6 +132,7 @@ _SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
       ctypes.c_int64, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(rr_solve_info)]),
     ("randrand_free", None, [ctypes.c_void_p]),
+    ("randrand_set_mu", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double]),
     ("randrand_export", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     ("randrand_scalars", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -251,6 +253,12 @@ def randrand_export(h, what: int, dst_ptr: int) -> None:
         raise RandRandError(s, "randrand_export")
 
 
+def randrand_set_mu(h, mu: float) -> None:
+    s = _lib().randrand_set_mu(h, float(mu))
+    if s != RR_OK:
+        raise RandRandError(s, "randrand_set_mu")
+
+
 def randrand_scalars(h) -> tuple[float, float, float]:
     t, e, l = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     s = _lib().randrand_scalars(h, ctypes.byref(t), ctypes.byref(e), ctypes.byref(l))
@@ -339,7 +347,7 @@ class Handle:
                  power_iters: int = 20, rho: float = 0.0, restart_eta: float = 1e-2,
                  gamma: int = 8, profile: bool = False, kernel_impl: int = 0, stream=None,
                  orth: str = "cholqr2", l_sk: int = 0, gamma_sk: int = 8, iter_impl: int = 0,
-                 q: int = 0):
+                 q: int = 0, keep_sketch: bool = False):
         import torch
         self.op = op
         self.n = op.n
@@ -359,6 +367,7 @@ class Handle:
         o.kernel_impl = kernel_impl
         o.iter_impl = iter_impl
         o.q = q
+        o.keep_sketch = 1 if keep_sketch else 0
         self.opts = o
         self.ws_bytes = randrand_workspace_bytes(op.c, k, o)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
@@ -396,6 +405,10 @@ class Handle:
 
     def scalars(self):
         return randrand_scalars(self.h)
+
+    def set_mu(self, mu: float):
+        """Rebuild for another shift from the kept sketch (keep_sketch=True)."""
+        randrand_set_mu(self.h, mu)
 
     def profile(self) -> dict:
         return randrand_profile(self.h)

@@ -19,7 +19,7 @@ using namespace rr;
 
 namespace {
 
-constexpr int kKK = 16;           // k x k float64 work matrices
+constexpr int kKK = 19;           // k x k float64 work matrices
 constexpr int kMaxGammaHost = 16; // sparse-sign nonzeros per row, at most
 constexpr int kChunk = 8;         // Krylov iterations per captured graph
 constexpr int kImplicitChunk = 256;  // iterations per persistent basis-less launch
@@ -27,7 +27,7 @@ constexpr int kImplicitChunk = 256;  // iterations per persistent basis-less lau
 constexpr int kMaxRestarts = 400;
 
 enum Region {
-  R_OM, R_OMB, R_SSC, R_SSS, R_THC, R_THS, R_SK, R_Y, R_Q, R_KK, R_KKT, R_GPART, R_CHOLW,
+  R_OM, R_OMB, R_SSC, R_SSS, R_THC, R_THS, R_SK, R_Y, R_Q, R_Y0, R_KK, R_KKT, R_GPART, R_CHOLW,
   R_STATUS, R_XS, R_CN, R_PN, R_AUG, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT,
   R_CS, R_NORMS, R_FUSED, R_NREG
 };
@@ -78,6 +78,7 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_SK] = 2 * lsk * kk * 8;   // S = Theta Y_mu and one copy for CholeskyQR passes
   L.size[R_Y] = n * kk * ts;
   L.size[R_Q] = n * kk * ts;
+  L.size[R_Y0] = o.keep_sketch ? n * kk * ts : 0;   // A Omega kept for other shifts
   L.size[R_KK] = (size_t)kKK * kk * kk * 8;
   L.size[R_KKT] = kk * kk * ts;
   L.size[R_GPART] = (size_t)gs_max * kk * kk * 8;
@@ -145,6 +146,10 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
   if (o.power_iters < 1 || o.power_iters > 1000) return RR_ERR_INVALID_ARG;
   if (o.iter_impl < 0 || o.iter_impl > 1) return RR_ERR_INVALID_ARG;
   if (o.kernel_impl < 0 || o.kernel_impl > 3) return RR_ERR_INVALID_ARG;
+  if (o.keep_sketch != 0 && o.keep_sketch != 1) return RR_ERR_INVALID_ARG;
+  if (o.keep_sketch &&
+      (o.variant != RR_VARIANT_C || uses_alg3(o) || o.q != 0 || basis_less(*A, o)))
+    return RR_ERR_UNSUPPORTED;
   if (o.q < 0 || o.q > 4) return RR_ERR_INVALID_ARG;
   if (!(o.restart_eta > 0.0 && o.restart_eta < 1.0)) return RR_ERR_INVALID_ARG;
   switch (A->kind) {
@@ -232,6 +237,7 @@ struct rr_handle {
   void* Y;
   void* Q;
   void* QH;
+  void* Y0;           // A Omega (opts.keep_sketch)
   double* kk[kKK];
   void* kkT;
   double* gpart;
@@ -281,7 +287,9 @@ enum { kB64 = 0, kX64 = 1, kR64 = 2, kW64 = 3 };
 enum { kR1 = 0, kR2 = 1, kRinvA = 2, kRinvB = 3, kRinv = 4, kRfull = 5, kM = 6, kG = 7, kH = 8,
        kTm = 9, kScA = 10, kScB = 11,
        // basis-less: R_sk, R^-1 H R^-T, R^-1 R^-T, R^-1 G R^-T
-       kRsk = 12, kHb = 13, kCinv = 14, kGb = 15 };
+       kRsk = 12, kHb = 13, kCinv = 14, kGb = 15,
+       // kept sketch (Sec. 5.1): (A Omega)^T A Omega, sym(Omega^T A Omega), Omega^T Omega
+       kP2 = 16, kM0 = 17, kS0 = 18 };
 
 template <typename T>
 T* vt(rr_handle* h, int i) {
@@ -301,6 +309,7 @@ void carve(rr_handle* h) {
   h->Y = at(R_Y);
   h->Q = at(R_Q);
   h->QH = nullptr;
+  h->Y0 = h->L.size[R_Y0] ? at(R_Y0) : nullptr;
   double* kkbase = (double*)at(R_KK);
   for (int i = 0; i < kKK; ++i) h->kk[i] = kkbase + (size_t)i * h->k * h->k;
   h->kkT = at(R_KKT);
@@ -455,7 +464,7 @@ __global__ void k_maxdiag(const double* A, int k, double* out) {
 // shifted first pass (shifted CholeskyQR, Fukaya et al. 2020, the shift of
 // Sec. 5.1) is followed by two plain passes.
 template <typename T>
-rr_status orthogonalize(rr_handle* h) {
+rr_status orthogonalize(rr_handle* h, const double* G1given = nullptr) {
   const int k = h->k;
   double* G1 = h->kk[kScA];
   double* Rp = h->kk[kR1];
@@ -466,7 +475,10 @@ rr_status orthogonalize(rr_handle* h) {
   T* dst = (T*)h->Q;
   int passes = 2;
   bool shifted = false;
-  gram<T>(h, src, G1);
+  if (G1given)   // the Gram of Y_mu from the shift-free projections (Sec. 5.1)
+    RR_CUDA_TRY(cudaMemcpyAsync(G1, G1given, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
+  else
+    gram<T>(h, src, G1);
   RR_CUDA_TRY(cudaMemcpyAsync(Rp, G1, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
   rr_status s = chol(h, Rp);
   if (s == RR_ERR_NOT_SPD) {
@@ -829,6 +841,11 @@ rr_status sketch_product(rr_handle* h, double shift, bool tc, int64_t ldo) {
 }
 
 template <typename T>
+rr_status finish_build(rr_handle* h, const double* G1given);
+template <typename T>
+rr_status shift_finish(rr_handle* h);
+
+template <typename T>
 rr_status build_impl(rr_handle* h) {
   const int64_t n = h->n;
   const int k = h->k;
@@ -878,14 +895,36 @@ rr_status build_impl(rr_handle* h) {
     RR_TRY(sketch_product<T>(h, 0.0, tc, ldo));
     set_omega<T>((const T*)h->Y, (T*)h->Om, h->Omb, ldo, n, k, mixed, st);
   }
+  if (h->o.keep_sketch) {
+    // Sec. 5.1: A Omega once, then the shift-free projections
+    RR_TRY(sketch_product<T>(h, 0.0, tc, ldo));
+    RR_CUDA_TRY(cudaMemcpyAsync(h->Y0, h->Y, (size_t)n * k * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    gram<T>(h, (const T*)h->Y0, h->kk[kP2]);
+    gram_partial<T>((const T*)h->Om, k, (const T*)h->Y0, k, n, k, k, false, h->gsplit, h->gpart, st);
+    reduce_gram(h->gpart, h->gsplit, k, k, false, true, h->kk[kM0], st);
+    gram<T>(h, (const T*)h->Om, h->kk[kS0]);
+    return shift_finish<T>(h);
+  }
   RR_TRY(sketch_product<T>(h, h->mu, tc, ldo));
   // M = sym(Omega^T Y_mu) = Omega^T A_mu Omega (C variant), before Y is reused
   if (h->o.variant == RR_VARIANT_C) {
     gram_partial<T>((const T*)h->Om, k, (const T*)h->Y, k, n, k, k, false, h->gsplit, h->gpart, st);
     reduce_gram(h->gpart, h->gsplit, k, k, false, true, h->kk[kM], st);
   }
+  return finish_build<T>(h, nullptr);
+}
+
+// Alg. 7 steps 2-4 after the sketch: orthogonalization (its first Gram
+// given when the shift-free projections provide it), core matrix, power
+// iterations, tau, H and Q H
+template <typename T>
+rr_status finish_build(rr_handle* h, const double* G1given) {
+  const int64_t n = h->n;
+  const int k = h->k;
+  cudaStream_t st = h->st;
+  (void)n;
   if (uses_alg3(h->o)) RR_TRY(rand_qless_qr<T>(h));
-  else RR_TRY(orthogonalize<T>(h));
+  else RR_TRY(orthogonalize<T>(h, G1given));
   if (h->o.variant == RR_VARIANT_C) RR_TRY(core_matrix(h));
   if (h->implicit) {
     implicit_core(h);
@@ -917,6 +956,28 @@ rr_status build_impl(rr_handle* h) {
       RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
   }
   return sync_status(h);
+}
+
+// Sec. 5.1 for the kept sketch: Y_mu = A Omega + mu Omega, the first Gram
+// P2 + 2 mu M0 + mu^2 S0 and Omega^T A_mu Omega = M0 + mu S0 from the
+// shift-free projections, then the rest of the build
+template <typename T>
+rr_status shift_finish(rr_handle* h) {
+  const int64_t n = h->n;
+  const int k = h->k;
+  const double mu = h->mu;
+  cudaStream_t st = h->st;
+  axpby<T, T, T>((const T*)h->Y0, coefs_all(1.0), (const T*)h->Om, coefs_all(mu), (T*)h->Y,
+                 n * k, 1, st);
+  const int64_t kk2 = (int64_t)k * k;
+  double* G1 = h->kk[kH];   // free until H is formed
+  axpby<double, double, double>(h->kk[kP2], coefs_all(1.0), h->kk[kM0], coefs_all(2.0 * mu), G1,
+                                kk2, 1, st);
+  axpby<double, double, double>(G1, coefs_all(1.0), h->kk[kS0], coefs_all(mu * mu), G1, kk2, 1,
+                                st);
+  axpby<double, double, double>(h->kk[kM0], coefs_all(1.0), h->kk[kS0], coefs_all(mu), h->kk[kM],
+                                kk2, 1, st);
+  return finish_build<T>(h, G1);
 }
 
 // ------------------------------------------------------------------ solve
@@ -1296,6 +1357,7 @@ void rr_build_opts_default(rr_build_opts* o) {
   o->kernel_impl = 0;
   o->iter_impl = 0;
   o->q = 0;
+  o->keep_sketch = 0;
 }
 
 const char* randrand_status_str(rr_status s) {
@@ -1445,6 +1507,23 @@ void randrand_free(rr_handle* h) {
       cudaEventDestroy(p.e[1]);
     }
   delete h;
+}
+
+rr_status randrand_set_mu(rr_handle* h, double mu) {
+  if (!h || !(mu >= 0.0) || !std::isfinite(mu)) return RR_ERR_INVALID_ARG;
+  if (!h->o.keep_sketch || !h->Y0) return RR_ERR_UNSUPPORTED;
+  // captured iteration graphs carry the shift as a kernel argument
+  RR_CUDA_TRY(cudaStreamSynchronize(h->st));
+  if (h->graph_ok) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_ok = false;
+  }
+  h->mu = mu;
+  RR_CUDA_TRY(cudaMemsetAsync(h->cnt, 0, h->L.size[R_CNT], h->st));
+  RR_CUDA_TRY(cudaMemsetAsync(h->cs, 0, h->L.size[R_CS], h->st));
+  RR_CUDA_TRY(cudaMemsetAsync(h->dstatus, 0, h->L.size[R_STATUS], h->st));
+  return h->f64 ? shift_finish<double>(h) : shift_finish<float>(h);
 }
 
 rr_status randrand_profile(rr_handle* h, rr_profile* out) {
