@@ -27,12 +27,22 @@ Stream layout (counter = (c0, c1, c2, c3), key = (seed lo 32, seed hi 32)):
   with column i of Theta in place of row i of Omega and l_sk in place of k.
 * Power-iteration start vectors, stream 4: counter (i, 0, 4, 0), word c
   gives entry i of start vector c (c = 0, 1) as N(0,1) numbers.
+* SRHT (Sec. 2, fast randomized transforms): X = l^-1/2 S H D, first n of s
+  columns (s the smallest power of two >= n).  Sign d_i (stream 5): negative
+  iff the top bit of word 0 of counter (i, 0, 5, 0) is set.  H: Sylvester
+  Walsh-Hadamard, H[r][i] = (-1)^popcount(r & i).  S (uniform subsampling
+  without replacement): row j of X is row pi(j) of H, pi a keyed permutation
+  of [0, s): four balanced Feistel rounds on b bits (b = log2 s; b + 1 when
+  odd, then cycle-walking back into [0, s)), round r mapping (L, R) to
+  (R, L xor (word 0 of counter (R, r, 6, 0)) mod 2^(b/2)).
 
 Uniforms use 24 bits so that they are exact in float32 and float64:
 u = ((w >> 8) + 0.5) * 2^-24 in (0, 1).  Box-Muller pairs:
 (z0, z1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1), likewise (z2, z3).
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -46,6 +56,8 @@ PHILOX_ROUNDS = 10
 STREAM_OMEGA = 2
 STREAM_THETA = 3
 STREAM_POWER = 4
+STREAM_SRHT_SIGN = 5
+STREAM_SRHT_PERM = 6
 
 _MASK32 = np.uint64(0xFFFFFFFF)
 
@@ -185,3 +197,56 @@ def round_bf16(a: np.ndarray) -> np.ndarray:
 
 def round_f32(a: np.ndarray) -> np.ndarray:
     return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def srht_size(n: int) -> int:
+    """The smallest power of two s >= n."""
+    s = 1
+    while s < n:
+        s <<= 1
+    return s
+
+
+def _feistel(x: np.ndarray, bits: int, seed: int) -> np.ndarray:
+    h = bits // 2
+    mask = np.uint64((1 << h) - 1)
+    x = np.asarray(x, dtype=np.uint64)
+    L, R = x >> np.uint64(h), x & mask
+    for r in range(4):
+        ctr = np.zeros((x.size, 4), dtype=np.uint32)
+        ctr[:, 0] = R.astype(np.uint32)
+        ctr[:, 1] = r
+        ctr[:, 2] = STREAM_SRHT_PERM
+        f = philox4x32_10(ctr, seed_key(seed))[:, 0].astype(np.uint64) & mask
+        L, R = R, L ^ f
+    return (L << np.uint64(h)) | R
+
+
+def srht_rows(k: int, s: int, seed: int) -> np.ndarray:
+    """pi(0), ..., pi(k-1): the rows of H that S keeps (distinct)."""
+    b = s.bit_length() - 1
+    if b == 0:
+        return np.zeros(k, dtype=np.int64)
+    bits = b if b % 2 == 0 else b + 1
+    x = _feistel(np.arange(k, dtype=np.uint64), bits, seed)
+    while np.any(x >= np.uint64(s)):          # cycle-walking (bits = b + 1)
+        out = x >= np.uint64(s)
+        x[out] = _feistel(x[out], bits, seed)
+    return x.astype(np.int64)
+
+
+def srht_signs(n: int, seed: int) -> np.ndarray:
+    ctr = np.zeros((n, 4), dtype=np.uint32)
+    ctr[:, 0] = np.arange(n, dtype=np.uint32)
+    ctr[:, 2] = STREAM_SRHT_SIGN
+    w = philox4x32_10(ctr, seed_key(seed))[:, 0]
+    return np.where(w >> np.uint32(31), -1.0, 1.0)
+
+
+def srht_omega(n: int, k: int, seed: int) -> np.ndarray:
+    """Omega = X^T (n x k): Omega_ij = d_i H[pi(j)][i] / sqrt(k)."""
+    s = srht_size(n)
+    rows = srht_rows(k, s, seed)
+    i = np.arange(n, dtype=np.int64)
+    par = np.bitwise_count(i[:, None] & rows[None, :]) & 1
+    return srht_signs(n, seed)[:, None] * np.where(par, -1.0, 1.0) * (1.0 / math.sqrt(k))

@@ -222,11 +222,14 @@ def make_omega(n: int, k: int, sketch: str, seed: int, gamma: int = 8,
     """Test matrix Omega = A^q X^T (eq:testmatrix, A symmetric), rounded to the
     working precision of the sketch (float64, float32 or bfloat16).  X^T is
     the Gaussian or sparse-sign draw; with q >= 1 it is multiplied by A (not
-    A_mu: Omega does not depend on the shift) q times before the rounding."""
+    A_mu: Omega does not depend on the shift) q times before the rounding.
+    X^T may also be an SRHT (Sec. 2, fast randomized transforms)."""
     if sketch == "gaussian":
         Om = philox.gaussian_omega(n, k, seed)
     elif sketch == "sparse_sign":
         Om = philox.sparse_sign_omega_dense(n, k, gamma, seed)
+    elif sketch == "srht":
+        Om = philox.srht_omega(n, k, seed)
     else:
         raise ValueError(sketch)
     if q > 0:

@@ -493,3 +493,45 @@ def test_recycled_sketch_build_equals_fresh_build():
         assert rec.tau == pytest.approx(fresh.tau, rel=1e-10)
         x, info = O.solve(rec, B, rtol=1e-12)
         assert np.linalg.norm(x - O.exact_solve(op, mu, B)) <= 1e-8 * np.linalg.norm(x)
+
+
+# ------------------------------------------------------------ SRHT (Sec. 2)
+def test_srht_subsampling_is_a_permutation():
+    """The keyed Feistel permutation (with cycle-walking for odd log2 s) maps
+    0..s-1 onto 0..s-1, so the k kept rows are distinct."""
+    for s in (1, 2, 4, 8, 16, 32, 64, 256, 512, 2048):
+        rows = philox.srht_rows(s, s, seed=17)
+        assert np.array_equal(np.sort(rows), np.arange(s))
+    assert philox.srht_size(20000) == 32768 and philox.srht_size(256) == 256
+
+
+def test_srht_hadamard_entries_match_library():
+    """H[r][i] = (-1)^popcount(r & i) is the Sylvester Walsh-Hadamard matrix
+    of the library routine."""
+    sp = pytest.importorskip("scipy.linalg")
+    s = 64
+    H = sp.hadamard(s)
+    r = np.arange(s)[:, None]
+    i = np.arange(s)[None, :]
+    assert np.array_equal(np.where(np.bitwise_count(r & i) & 1, -1, 1), H)
+
+
+def test_srht_columns_orthogonal_for_power_of_two():
+    """With n = s the k columns of Omega are distinct rows of D H / sqrt(k)
+    (H^T H = s I): Omega^T Omega = (s / k) I, off-diagonal entries exactly 0."""
+    n, k = 256, 32
+    Om = philox.srht_omega(n, k, seed=23)
+    assert np.all(np.abs(Om) == 1.0 / math.sqrt(k))
+    S = np.rint(Om * math.sqrt(k)).astype(np.int64)     # the +-1 pattern, exactly
+    assert np.array_equal(S.T @ S, n * np.eye(k, dtype=np.int64))
+
+
+def test_srht_build_solves():
+    """An SRHT test matrix gives a working preconditioner: the PCG solution
+    reaches the exact solution."""
+    P = W.dense_power_spectrum(300, seed=84, power=2.0)
+    op = O.DenseOp(P.A)
+    B = W.gaussian_rhs(300, 1, 84)
+    bd = O.build(op, 1e-4, 40, "srht", seed=84)
+    x, info = O.solve(bd, B, rtol=1e-12)
+    assert np.linalg.norm(x - O.exact_solve(op, 1e-4, B)) <= 1e-8 * np.linalg.norm(x)
