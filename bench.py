@@ -68,6 +68,8 @@ def parse():
                     choices=["kernel_ridge", "sparse_diffusion", "batched", "serving", "shift_path"])
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
     ap.add_argument("--workers", type=int, default=0, help="batched/serving: 0 = autotune")
+    ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "srht"],
+                    help="kernel ridge: test matrix (Gaussian or SRHT)")
     ap.add_argument("--kernel-impl", type=int, default=0,
                     help="kernel ridge: Gaussian-kernel product form (rr_build_opts.kernel_impl)")
     return ap.parse_args()
@@ -234,6 +236,7 @@ def run_reference(args):
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
+    WORKLOAD["sketch"] = args.sketch
 
     rank, world, local = dist_init(args)
     torch.cuda.set_device(local)
@@ -329,7 +332,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {**{kk: WORKLOAD[kk] for kk in ("workload", "n", "d", "k", "nrhs", "mu", "rtol",
-                                                  "precision", "variant")},
+                                                  "precision", "variant", "sketch")},
                    "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "solve": {"inner_iters_max": iters, "rel_residual_max": rel_res},

@@ -60,8 +60,11 @@ enum {
 
 /* Test matrices Omega = X^T (Sec. 2) */
 enum {
-  RR_SKETCH_GAUSSIAN = 0,   /* entries N(0, 1/k) */
-  RR_SKETCH_SPARSE_SIGN = 1 /* gamma entries +-1/sqrt(gamma) per row of Omega */
+  RR_SKETCH_GAUSSIAN = 0,    /* entries N(0, 1/k) */
+  RR_SKETCH_SPARSE_SIGN = 1, /* gamma entries +-1/sqrt(gamma) per row of Omega */
+  RR_SKETCH_SRHT = 2         /* subsampled randomized Hadamard transform (Sec. 2):
+                                Omega = X^T, X = k^-1/2 S H D, the first n of
+                                s = 2^ceil(log2 n) columns; entries +-1/sqrt(k) */
 };
 
 /* Arithmetic of the path */
@@ -203,7 +206,7 @@ rr_status randrand_workspace_bytes(const rr_operator* A, int32_t k,
  *   A          operator (see rr_operator); borrowed.
  *   mu         shift, >= 0 and finite.
  *   k          sketch dimension l of the paper, 1 <= k <= n.
- *   sketch     RR_SKETCH_GAUSSIAN or RR_SKETCH_SPARSE_SIGN.
+ *   sketch     RR_SKETCH_GAUSSIAN, RR_SKETCH_SPARSE_SIGN or RR_SKETCH_SRHT.
  *   seed       64-bit key of the counter-based generator that draws Omega,
  *              Theta and the power-iteration start vectors.
  *   opts       NULL for defaults.

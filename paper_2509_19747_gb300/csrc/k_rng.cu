@@ -39,6 +39,46 @@ void gen_gaussian_omega(T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, 
                                                                    round_bf16 ? 1 : 0, ldo);
 }
 
+// SRHT test matrix Omega = X^T (Sec. 2, fast randomized transforms):
+// Omega_ij = d_i (-1)^popcount(pi(j) & i) / sqrt(k); the k kept rows pi(j)
+// and the n signs are drawn first into small scratch arrays
+__global__ void k_srht_draw(int32_t* __restrict__ rows, int8_t* __restrict__ sgn, int64_t n,
+                            int k, int64_t s, uint64_t seed) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < k) rows[g] = (int32_t)srht_row(g, s, seed);
+  if (g < n) sgn[g] = (philox_draw(seed, (uint32_t)g, 0u, kStreamSrhtSign).v[0] >> 31) ? -1 : 1;
+}
+
+template <typename T>
+__global__ void k_srht_omega(T* __restrict__ Om, __nv_bfloat16* __restrict__ Ob, int64_t n,
+                             int k, const int32_t* __restrict__ rows,
+                             const int8_t* __restrict__ sgn, int round_bf16, int64_t ldo) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * k) return;
+  const int64_t i = g / k;
+  const int j = (int)(g - i * k);
+  const T scale = (T)(1.0 / sqrt((double)k));
+  const bool neg = ((__popcll((unsigned long long)(rows[j] & i)) & 1) != 0) != (sgn[i] < 0);
+  T v = neg ? -scale : scale;
+  if (round_bf16) {
+    const __nv_bfloat16 b = __float2bfloat16_rn((float)v);
+    v = (T)__bfloat162float(b);
+    if (Ob) Ob[(int64_t)j * ldo + i] = b;   // Omega^T, K-major operand of the sketch MMA
+  }
+  Om[i * k + j] = v;
+}
+
+template <typename T>
+void gen_srht_omega(T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, int k,
+                    uint64_t seed, bool round_bf16, int32_t* rows, int8_t* sgn, cudaStream_t st) {
+  int64_t s = 1;
+  while (s < n) s <<= 1;
+  const int64_t m = n > k ? n : k;
+  k_srht_draw<<<(unsigned)cdiv(m, 256), 256, 0, st>>>(rows, sgn, n, k, s, seed);
+  k_srht_omega<T><<<(unsigned)cdiv(n * k, 256), 256, 0, st>>>(Om, OmT_bf16, n, k, rows, sgn,
+                                                               round_bf16 ? 1 : 0, ldo);
+}
+
 __global__ void k_sparse_sign(int32_t* __restrict__ cols, int8_t* __restrict__ sgn,
                               int64_t nlines, int ncols, int gamma, uint64_t seed,
                               uint32_t stream_id) {
@@ -125,6 +165,10 @@ template void set_omega<float>(const float*, float*, __nv_bfloat16*, int64_t, in
 template void set_omega<double>(const double*, double*, __nv_bfloat16*, int64_t, int64_t, int,
                                 bool, cudaStream_t);
 
+template void gen_srht_omega<float>(float*, __nv_bfloat16*, int64_t, int64_t, int, uint64_t,
+                                    bool, int32_t*, int8_t*, cudaStream_t);
+template void gen_srht_omega<double>(double*, __nv_bfloat16*, int64_t, int64_t, int, uint64_t,
+                                     bool, int32_t*, int8_t*, cudaStream_t);
 template void gen_gaussian_omega<float>(float*, __nv_bfloat16*, int64_t, int64_t, int, uint64_t,
                                         bool, cudaStream_t);
 template void gen_gaussian_omega<double>(double*, __nv_bfloat16*, int64_t, int64_t, int, uint64_t,

@@ -10,7 +10,13 @@
 //     counters (line, t, stream, 0), t = 0, 1, ..., two candidates per draw
 //     (column = mulhi(w_even, ncols), sign = top bit of w_odd), duplicates
 //     within a line skipped, gamma accepted per line;
-//   power-iteration start vectors (stream 4): counter (i, 0, 4, 0).
+//   power-iteration start vectors (stream 4): counter (i, 0, 4, 0);
+//   SRHT (X = l^-1/2 S H D, the first n of s columns, s = 2^ceil(log2 n)):
+//     sign d_i negative iff the top bit of word 0 of counter (i, 0, 5, 0) is
+//     set; row j of X is row pi(j) of the Sylvester Walsh-Hadamard matrix,
+//     pi a keyed permutation of [0, s): four balanced Feistel rounds on b
+//     bits (b = log2 s, or b + 1 with cycle-walking when b is odd), round r
+//     mapping (L, R) to (R, L ^ (word 0 of counter (R, r, 6, 0) mod 2^(b/2))).
 // Uniforms carry 24 bits, u = ((w >> 8) + 0.5) 2^-24, exact in float32.
 #pragma once
 #include <cstdint>
@@ -25,6 +31,8 @@ constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 constexpr uint32_t kStreamOmega = 2;
 constexpr uint32_t kStreamTheta = 3;
 constexpr uint32_t kStreamPower = 4;
+constexpr uint32_t kStreamSrhtSign = 5;
+constexpr uint32_t kStreamSrhtPerm = 6;
 
 struct U32x4 {
   uint32_t v[4];
@@ -55,6 +63,32 @@ __host__ __device__ inline U32x4 philox_draw(uint64_t seed, uint32_t c0, uint32_
                                              uint32_t c2) {
   U32x4 c = {{c0, c1, c2, 0u}};
   return philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// one pass of the SRHT row permutation on `bits` bits (bits even, > 0)
+__host__ __device__ inline uint64_t srht_feistel(uint64_t x, int bits, uint64_t seed) {
+  const int h = bits / 2;
+  const uint64_t mask = (1ull << h) - 1;
+  uint64_t L = x >> h, R = x & mask;
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t f = philox_draw(seed, (uint32_t)R, (uint32_t)r, kStreamSrhtPerm).v[0] & mask;
+    const uint64_t t = L ^ f;
+    L = R;
+    R = t;
+  }
+  return (L << h) | R;
+}
+
+// pi(j) for the SRHT of width s = 2^b (j < s); the cycle-walk ends within s
+// steps because pi restricted to a cycle returns to [0, s)
+__host__ __device__ inline int64_t srht_row(int64_t j, int64_t s, uint64_t seed) {
+  int b = 0;
+  while ((1ll << b) < s) ++b;
+  if (b == 0) return 0;
+  const int bits = (b % 2 == 0) ? b : b + 1;
+  uint64_t x = srht_feistel((uint64_t)j, bits, seed);
+  for (int64_t it = 0; x >= (uint64_t)s && it < 2 * s; ++it) x = srht_feistel(x, bits, seed);
+  return (int64_t)x;
 }
 
 // 24-bit uniform in (0,1), exact in float and double.

@@ -882,12 +882,14 @@ rr_status build_impl(rr_handle* h) {
   const int64_t ldo = cdiv(n, 8) * 8;
   if (h->sketch == RR_SKETCH_GAUSSIAN) {
     gen_gaussian_omega<T>((T*)h->Om, h->Omb, ldo, n, k, h->seed, mixed, st);
+  } else if (h->sketch == RR_SKETCH_SRHT) {
+    gen_srht_omega<T>((T*)h->Om, h->Omb, ldo, n, k, h->seed, mixed, h->ss_cols, h->ss_sgn, st);
   } else {
     gen_sparse_sign(h->ss_cols, h->ss_sgn, n, k, h->o.gamma, h->seed, 2u, st);
     sparse_to_dense_omega<T>((T*)h->Om, h->ss_cols, h->ss_sgn, n, k, h->o.gamma, st);
   }
   // tensor cores for the mixed-precision Gaussian-kernel sketch (bf16 operands)
-  const bool tc = mixed && h->op.kind == RR_OP_GAUSS_KERNEL && h->sketch == RR_SKETCH_GAUSSIAN &&
+  const bool tc = mixed && h->op.kind == RR_OP_GAUSS_KERNEL && h->sketch != RR_SKETCH_SPARSE_SIGN &&
                   h->op.dim == 8 && h->o.kernel_impl != 1 && sizeof(T) == 4;
   // eq:testmatrix with q >= 1: Omega <- A Omega, q times (A, not A_mu), each
   // product rounded like the drawn test matrix
@@ -1396,7 +1398,8 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
   else rr_build_opts_default(&o);
   RR_TRY(validate(A, k, o));
   if (!(mu >= 0.0) || !std::isfinite(mu)) return RR_ERR_INVALID_ARG;
-  if (sketch != RR_SKETCH_GAUSSIAN && sketch != RR_SKETCH_SPARSE_SIGN) return RR_ERR_INVALID_ARG;
+  if (sketch != RR_SKETCH_GAUSSIAN && sketch != RR_SKETCH_SPARSE_SIGN && sketch != RR_SKETCH_SRHT)
+    return RR_ERR_INVALID_ARG;
   if (sketch == RR_SKETCH_SPARSE_SIGN && o.gamma > k) return RR_ERR_INVALID_ARG;
   if (!workspace || ((uintptr_t)workspace & 255)) return RR_ERR_INVALID_ARG;
   const Layout L = make_layout(*A, k, o);

@@ -117,6 +117,9 @@ struct Coefs8s {
 template <typename T>
 void gen_gaussian_omega(T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, int k,
                         uint64_t seed, bool round_bf16, cudaStream_t st);
+template <typename T>
+void gen_srht_omega(T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, int k,
+                    uint64_t seed, bool round_bf16, int32_t* rows, int8_t* sgn, cudaStream_t st);
 // Omega <- src (a power step A X^T), bf16-rounded with its K-major copy if asked
 template <typename T>
 void set_omega(const T* src, T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, int k,
