@@ -29,12 +29,22 @@ arXiv 2509.19747):
   (Sec. 7 experimental setup; Alg. 4 step 9, Alg. 7 step 10), the restart
   residual b - A_mu x recomputed in float64;
 * the exact solution x* = A_mu^-1 b by a dense Cholesky solve;
+* G-RandRAND (Sec. 3.3 eq:g_randrand): P = (I - Pi) + tau Q G Q^T with
+  G = (R^-T Omega^T Omega R^-1)^(1/2), tau = rho^(1/2) |(I - Pi) A_mu| /
+  |Pi~ A_mu| (eq:g_randrand_tau, the Sec. 6.3 estimates), and restarted
+  preconditioned MINRES (Paige and Saunders), also for indefinite A_mu
+  (mu < 0);
 * several shifts from one sketch (Sec. 5.1): A Omega computed once, Y_mu =
   A Omega + mu Omega per shift, and the Gram separation (A Omega + mu
   Omega)^T (A Omega + mu Omega) = Omega^T A^T A Omega + 2 mu Omega^T A Omega
   + mu^2 Omega^T Omega of the parameter-free projections.
 
-Readings where the paper is silent: 20 power iterations from seeded start
+Readings where the paper is silent: for G-RandRAND rho = 0.5 a priori (the
+optimal rho of eq:rho_g_rand_rand needs |A_mu^-1|), the norms as square
+roots of power-iteration estimates of the largest eigenvalues of A_mu (I -
+Pi) A_mu and A_mu Pi~^2 A_mu, and the MINRES inner stop as the same
+relative reduction of |r|_P = sqrt(r^T P r), the norm MINRES tracks.  Also:
+20 power iterations from seeded start
 vectors, estimate = |w_20| (norm of the last image of a unit vector); the
 inner stop max(eta |r_0|, 0.5 rtol |b|); R = R_chol R_sk as the product
 order in Alg. 3 (the only order with R^T R = Y_mu^T Y_mu); l_sk = 4k and
@@ -51,6 +61,8 @@ from . import philox
 
 VARIANT_C = "C"
 VARIANT_R = "R"
+VARIANT_G = "G"
+MAX_RESTARTS = 400      # restarts per column, as in the library
 
 
 # ==========================================================================
@@ -319,7 +331,8 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
         u = v - b.Pi(v)
         w = Amu(u)
         return w - b.Pi(w)
-    b.normE = power_iteration(E_apply, philox.power_start(n, 0, seed), power_iters)
+    if variant != VARIANT_G:
+        b.normE = power_iteration(E_apply, philox.power_start(n, 0, seed), power_iters)
     # For k < n, interlacing gives |E| >= lambda_min(A_mu) >= mu (the
     # eigenvalues of E on the complement of range(Y_mu) are not below those
     # of A_mu).  Clamping the estimate at mu changes nothing then, and keeps
@@ -348,6 +361,29 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
             b.tau = b.rho * nE / b.lam_max           # eq:c_randrand_tau
             if b.tau <= 0.0:                         # mu = 0 and k = n
                 b.tau = 1.0 / b.lam_max
+    elif variant == VARIANT_G:
+        # G-RandRAND (Sec. 3.3 eq:g_randrand): P = (I - Pi) + tau Pi~ with
+        # Pi~ = Q G Q^T, G = (R^-T (Omega^T Omega) R^-1)^(1/2) (the symmetric
+        # square root, by an eigendecomposition)
+        Ri = solve_upper(R, np.eye(k))
+        MG = Ri.T @ (Om.T @ Om) @ Ri
+        MG = 0.5 * (MG + MG.T)
+        wv, V = np.linalg.eigh(MG)
+        b.G = (V * np.sqrt(np.maximum(wv, 0.0))) @ V.T
+        Pt = lambda v: b.Q @ (b.G @ (b.Q.T @ v))
+        # |(I - Pi) A_mu| and |Pi~ A_mu| as square roots of the largest
+        # eigenvalues of A_mu (I - Pi) A_mu and A_mu Pi~^2 A_mu (the G-RandRAND
+        # MINRES estimates of Sec. 6.3)
+        def EA(v):                       # A_mu (I - Pi) A_mu v
+            u = Amu(v)
+            return Amu(u - b.Pi(u))
+        b.normE = math.sqrt(power_iteration(EA, philox.power_start(n, 0, seed), power_iters))
+        b.lam_max = math.sqrt(power_iteration(lambda v: Amu(Pt(Pt(Amu(v)))),
+                                              philox.power_start(n, 1, seed), power_iters))
+        # eq:g_randrand_tau; rho = 0.5 a priori (the optimal rho of
+        # eq:rho_g_rand_rand needs |A_mu^-1|, unknown for an indefinite A_mu)
+        b.rho = float(rho) if (rho is not None and rho > 0) else 0.5
+        b.tau = math.sqrt(b.rho) * b.normE / b.lam_max if tau is None else float(tau)
     elif variant == VARIANT_R:
         b.rho = 1.0
         b.tau = nE if tau is None else float(tau)        # Alg. 4 step 2
@@ -426,6 +462,59 @@ def pcg(Aop, b, Pop, stop: float, maxit: int):
     return x, it
 
 
+def minres(Aop, b, Pop, stop_rel: float, maxit: int):
+    """Preconditioned MINRES (Paige and Saunders 1975, in the Lanczos /
+    Givens form with an SPD preconditioner P ~ A^-1), x0 = 0.  Works with the
+    unnormalised Lanczos vectors v_j and z_j = P v_j; eta carries the
+    P-norm of the residual, |r_j|_P = sqrt(r_j^T P r_j).  Stops when |eta| <=
+    stop_rel |eta_0| or after maxit steps."""
+    x = np.zeros_like(b)
+    v_prev = np.zeros_like(b)
+    v = b.copy()
+    z = Pop(v)
+    zv = float(z @ v)
+    it = 0
+    if not (zv > 0.0 and math.isfinite(zv)):     # r = 0, or P not SPD in rounding
+        return x, it
+    gamma = math.sqrt(zv)
+    eta = eta0 = gamma
+    gamma_prev = 1.0
+    c_prev = c = 1.0
+    s_prev = s = 0.0
+    w_prev = np.zeros_like(b)
+    w = np.zeros_like(b)
+    while it < maxit:
+        z = z / gamma
+        Az = Aop(z)
+        delta = float(Az @ z)
+        v_next = Az - (delta / gamma) * v - (gamma / gamma_prev) * v_prev
+        z_next = Pop(v_next)
+        zv = float(z_next @ v_next)
+        if not (math.isfinite(zv) and math.isfinite(delta)):
+            break                                  # breakdown: keep the iterate so far
+        gamma_next = math.sqrt(max(zv, 0.0))
+        # the new column of the tridiagonal matrix through the previous
+        # rotations, then the rotation that annihilates gamma_next
+        a0 = c * delta - c_prev * s * gamma
+        a1 = math.hypot(a0, gamma_next)
+        a2 = s * delta + c_prev * c * gamma
+        a3 = s_prev * gamma
+        c_next, s_next = a0 / a1, gamma_next / a1
+        w_next = (z - a3 * w_prev - a2 * w) / a1
+        x += c_next * eta * w_next
+        eta = -s_next * eta
+        it += 1
+        v_prev, v = v, v_next
+        z = z_next
+        gamma_prev, gamma = gamma, gamma_next
+        c_prev, c = c, c_next
+        s_prev, s = s, s_next
+        w_prev, w = w, w_next
+        if abs(eta) <= stop_rel * eta0 or gamma == 0.0:
+            break
+    return x, it
+
+
 def solve(b_: Build, B: np.ndarray, rtol: float, maxit: int = 20000,
           eta: float = 1e-2, x0: np.ndarray | None = None,
           fixed_inner: int | None = None):
@@ -433,8 +522,10 @@ def solve(b_: Build, B: np.ndarray, rtol: float, maxit: int = 20000,
 
     Outer loop = the paper's restarting (Alg. 7 step 10 / Alg. 4 step 9):
     r = b - A_mu x in float64; stop when |r| <= rtol |b| or when the inner
-    iterations reach maxit; otherwise run PCG (C) or CG on B (R) to the inner
-    target max(eta |r|, 0.5 rtol |b|) and add the correction to x.
+    iterations reach maxit; otherwise run PCG (C), CG on B (R) or MINRES with
+    the G-RandRAND preconditioner (G, Sec. 6.3) to the inner target
+    max(eta |r|, 0.5 rtol |b|) (for MINRES the same reduction of the P-norm of
+    the residual) and add the correction to x.
 
     fixed_inner: if set, run exactly that many inner iterations once (no
     restart), for iteration-level comparisons.
@@ -472,12 +563,19 @@ def solve(b_: Build, B: np.ndarray, rtol: float, maxit: int = 20000,
             stop = max(eta * rel * nb, 0.5 * rtol * nb) if fixed_inner is None else 0.0
             if b_.variant == VARIANT_C:
                 e, it = pcg(Amu, r, b_.apply_P, stop, budget)
+            elif b_.variant == VARIANT_G:
+                # the same inner target relative to |r|, in the P-norm
+                # MINRES tracks: |r_j|_P <= max(eta, 0.5 rtol |b| / |r|) |r_0|_P
+                srel = max(eta, 0.5 * rtol * nb / (rel * nb)) if fixed_inner is None else 0.0
+                e, it = minres(Amu, r, b_.apply_P, srel, budget)
             else:
                 y, it = pcg(b_.apply_B, r, lambda v: v, stop, budget)
                 e = b_.recover_R(y)
             x += e
             info.inner_iters += it
             info.outer_iters += 1
+            if it == 0 or info.outer_iters >= MAX_RESTARTS:
+                break                              # no progress (breakdown) or too many restarts
         infos.append(info)
     return (X[:, 0] if one else X), infos
 

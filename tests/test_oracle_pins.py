@@ -535,3 +535,81 @@ def test_srht_build_solves():
     bd = O.build(op, 1e-4, 40, "srht", seed=84)
     x, info = O.solve(bd, B, rtol=1e-12)
     assert np.linalg.norm(x - O.exact_solve(op, 1e-4, B)) <= 1e-8 * np.linalg.norm(x)
+
+
+# ------------------------------------------ G-RandRAND and MINRES (Sec. 3.3, 6.3)
+def _indefinite(n=200, seed=86, after=20):
+    P = W.dense_power_spectrum(n, seed=seed, power=2.0)
+    ev = np.sort(np.linalg.eigvalsh(P.A))[::-1]
+    mu = -0.5 * (ev[after] + ev[after + 1])      # a shift between two eigenvalues
+    return P.A, mu
+
+
+def test_minres_matches_library_minres():
+    """The oracle's preconditioned MINRES takes the library routine's iterates
+    (same Krylov method, same SPD preconditioner) on an indefinite system."""
+    spl = pytest.importorskip("scipy.sparse.linalg")
+    A, mu = _indefinite()
+    n = A.shape[0]
+    Amu = A + mu * np.eye(n)
+    rng = np.random.default_rng(3)
+    Mh = rng.standard_normal((n, n))
+    Pm = np.eye(n) + 0.1 * Mh @ Mh.T / n        # an SPD preconditioner
+    b = rng.standard_normal(n)
+    # iterates to rounding over the first steps; later the Lanczos recurrences
+    # of the two formulations drift apart by rounding on this ill-conditioned
+    # system, so the residual norms are compared there
+    for m in (1, 2, 3, 12):
+        x, it = O.minres(lambda v: Amu @ v, b, lambda v: Pm @ v, 0.0, m)
+        assert it == m
+        xs, _ = spl.minres(Amu, b, M=spl.aslinearoperator(Pm), maxiter=m, rtol=1e-300)
+        if m <= 3:
+            assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs)
+        else:
+            r, rs = np.linalg.norm(b - Amu @ x), np.linalg.norm(b - Amu @ xs)
+            assert abs(r - rs) <= 1e-6 * rs
+
+
+def test_g_randrand_core_and_eigenvalue_bounds():
+    """G^2 = R^-T Omega^T Omega R^-1; P is SPD although A_mu is indefinite; with
+    tau from eq:g_randrand_tau on the exact norms, the singular values of P A_mu
+    obey eq:c_randrand_eigenvalues2."""
+    A, mu = _indefinite()
+    n = A.shape[0]
+    op = O.DenseOp(A)
+    Amu = A + mu * np.eye(n)
+    assert np.linalg.eigvalsh(Amu).min() < 0 < np.linalg.eigvalsh(Amu).max()
+    bd = O.build(op, mu, 40, "gaussian", seed=86, variant="G", q=1)
+    Ri = np.linalg.inv(bd.R)
+    MG = Ri.T @ (bd.Omega.T @ bd.Omega) @ Ri
+    assert np.linalg.norm(bd.G @ bd.G - MG) <= 1e-10 * np.linalg.norm(MG)
+    I = np.eye(n)
+    Pi = bd.Q @ bd.Q.T
+    Pt = bd.Q @ bd.G @ bd.Q.T
+    n1 = np.linalg.norm((I - Pi) @ Amu, 2)
+    n2 = np.linalg.norm(Pt @ Amu, 2)
+    rho = 0.5
+    tau = math.sqrt(rho) * n1 / n2
+    bt = O.build(op, mu, 40, "gaussian", seed=86, variant="G", q=1, tau=tau)
+    Pm = bt.apply_P(I)
+    assert np.allclose(Pm, Pm.T, atol=1e-12)
+    assert np.linalg.eigvalsh(0.5 * (Pm + Pm.T)).min() > 0.0
+    s = np.linalg.svd(Pm @ Amu, compute_uv=False)
+    lo = 1.0 / (np.linalg.norm((I - Pi) @ np.linalg.inv(Amu), 2) ** 2 + tau ** -2)
+    assert s.min() ** 2 >= lo * (1 - 1e-8)
+    assert s.max() ** 2 <= (1 + rho) * n1 ** 2 * (1 + 1e-8)
+
+
+def test_g_randrand_minres_solves_indefinite():
+    """Restarted MINRES with the G-RandRAND preconditioner (q = 1) reaches the
+    exact solution of an indefinite system, in fewer iterations than plain
+    MINRES."""
+    A, mu = _indefinite(n=300, seed=87)
+    op = O.DenseOp(A)
+    B = W.gaussian_rhs(300, 2, 87)
+    bd = O.build(op, mu, 60, "gaussian", seed=87, variant="G", q=1)
+    x, infos = O.solve(bd, B, rtol=1e-10)
+    xs = np.linalg.solve(A + mu * np.eye(300), B)
+    assert np.linalg.norm(x - xs) <= 1e-7 * np.linalg.norm(xs)
+    _, plain = O.minres(lambda v: A @ v + mu * v, B[:, 0], lambda v: v, 1e-10, 5000)
+    assert infos[0].inner_iters < plain
