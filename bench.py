@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--workload", default="kernel_ridge",
-                    choices=["kernel_ridge", "sparse_diffusion", "batched", "serving", "shift_path"])
+                    choices=["kernel_ridge", "sparse_diffusion", "batched", "serving", "shift_path",
+                             "indefinite"])
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
     ap.add_argument("--workers", type=int, default=0, help="batched/serving: 0 = autotune")
     ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "srht"],
@@ -469,6 +470,8 @@ SPARSE = dict(workload="sparse_diffusion", side=512, n=262144, mu=1e-6, k=256, l
               orth="rand_cholqr (basis-less)", seed=0x52523)
 BATCHED = dict(workload="batched_kernel_ridge", systems=64, n_min=2000, n_max=16000,
                k="n/40", mu="10^U(-5,-2)", nrhs=8, rtol=1e-6, precision="mixed", seed=0x52524)
+INDEF = dict(workload="kernel_shift_invert", n=20000, d=8, k=500, nrhs=4, mu=-20.0, rtol=1e-6,
+             precision="mixed", variant="G", q=1, solver="MINRES")
 SHIFTS = dict(workload="kernel_ridge_shift_path", n=20000, d=8, k=500, nrhs=4, rtol=1e-6,
               precision="mixed", mus=[1e-1, 3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 3e-5])
 SERVING = dict(workload="serving_mix", rate_per_s=200.0, kernel_share=0.5, kernel_n=[1000, 32000],
@@ -493,7 +496,7 @@ def run_other(args):
                               "unavailable": "the oracle arm times the kernel ridge workload only"}))
         return
     {"sparse_diffusion": run_sparse, "batched": run_batched, "serving": run_serving,
-     "shift_path": run_shift_path}[args.workload](args)
+     "shift_path": run_shift_path, "indefinite": run_indefinite}[args.workload](args)
 
 
 def run_sparse(args):
@@ -697,6 +700,59 @@ def run_batched(args):
                                     "seconds": seq_s},
                  autotune_s={f"workers={k[0]},iter_impl={k[1]}": v for k, v in tune.items()},
                  solve={"inner_iters_max": max(iters), "inner_iters_median": float(np.median(iters))},
+                 roofline=None, clocks=clocks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_indefinite(args):
+    """Shift-and-invert on the Gaussian kernel system of the main workload: A_mu
+    = K - 20 I is indefinite (about a hundred eigenvalues of K lie above 20), solved with
+    G-RandRAND MINRES (Sec. 3.3, 6.3; q = 1).  One step = build + solve."""
+    import torch
+    rank, world, local = dist_init(args)
+    torch.cuda.set_device(local)
+    import paper_2509_19747_gb300 as rr
+    cfg = INDEF
+    seed = WORKLOAD["seed"] + 1000 * rank
+    X, B = make_inputs(seed)
+    Xd = torch.from_numpy(X).cuda()
+    Bd = torch.from_numpy(B).cuda()
+    op = rr.Operator.gauss_kernel(Xd, WORKLOAD["bandwidth"])
+
+    def step():
+        h = rr.Handle(op, cfg["mu"], cfg["k"], "gaussian", seed=seed, variant=cfg["variant"],
+                      q=cfg["q"], precision=cfg["precision"], max_rhs=cfg["nrhs"])
+        _, st, infos = h.solve(Bd, rtol=cfg["rtol"])
+        h.close()
+        if st != rr.RR_OK:
+            raise RuntimeError(f"indefinite solve: {rr.randrand_status_str(st)}")
+        return infos
+
+    for _ in range(args.warmup):
+        step()
+    smi = ClockSampler()
+    barrier(world)
+    smi.start()
+    ms = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = step()
+        torch.cuda.synchronize()
+        ms.append((time.perf_counter() - t0) * 1e3)
+    barrier(world)
+    clocks = smi.stop()
+    mean = max_over_ranks(sum(ms), world) / args.steps
+    line = _line(args, world, "G-RandRAND MINRES solves/s to rtol 1e-6 (kernel shift-and-invert, mu = -20)",
+                 world * 1000.0 / mean, "solves/s", mean,
+                 {**cfg, "parallelism": f"replicas x{world}", "l2": "inputs of a solve exceed L2"},
+                 solve={"inner_iters_max": max(i["inner_iters"] for i in infos),
+                        "outer_iters_max": max(i["outer_iters"] for i in infos),
+                        "rel_residual_max": max(i["rel_residual"] for i in infos),
+                        "tau": infos[0]["tau"], "norm_I_minus_Pi_A": infos[0]["normE"],
+                        "norm_Pit_A": infos[0]["lam_max"]},
+                 timing="host wall clock around build + solve with the device synchronised",
                  roofline=None, clocks=clocks)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -78,7 +78,12 @@ enum {
 /* Preconditioner variants */
 enum {
   RR_VARIANT_C = 0,         /* C-RandRAND PCG (Sec. 3.2, Alg. 7) */
-  RR_VARIANT_R = 1          /* R-RandRAND CG on B y = b, x = P y (Sec. 3.1, Alg. 4) */
+  RR_VARIANT_R = 1,         /* R-RandRAND CG on B y = b, x = P y (Sec. 3.1, Alg. 4) */
+  RR_VARIANT_G = 2          /* G-RandRAND MINRES (Sec. 3.3 eq:g_randrand, Sec. 6.3):
+                               P = (I - Pi) + tau Q G Q^T, G = (R^-T Omega^T Omega
+                               R^-1)^(1/2), for symmetric A_mu that may be
+                               indefinite (mu < 0 allowed); explicit basis only
+                               (orth CHOLQR2) */
 };
 
 /* Orthogonalisation of Y_mu = A_mu Omega */

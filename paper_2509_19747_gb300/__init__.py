@@ -21,7 +21,7 @@ __all__ = [
     "RR_ERR_MAXIT", "RR_ERR_TIMEOUT", "RR_ERR_CUDA", "RR_ERR_UNSUPPORTED", "RR_PENDING",
     "RR_OP_DENSE", "RR_OP_CSR", "RR_OP_GAUSS_KERNEL", "RR_SKETCH_GAUSSIAN",
     "RR_SKETCH_SPARSE_SIGN", "RR_SKETCH_SRHT", "RR_PREC_FP64", "RR_PREC_FP32", "RR_PREC_MIXED", "RR_VARIANT_C",
-    "RR_VARIANT_R", "rr_operator", "rr_build_opts", "rr_solve_info", "rr_profile", "RandRandError",
+    "RR_VARIANT_R", "RR_VARIANT_G", "rr_operator", "rr_build_opts", "rr_solve_info", "rr_profile", "RandRandError",
     "load_library", "Operator", "Handle", "rr_request", "rr_result", "Arena", "Server",
     "Request", "solve_batch",
 ]
@@ -31,13 +31,13 @@ RR_ERR_MAXIT, RR_ERR_TIMEOUT, RR_ERR_CUDA, RR_ERR_UNSUPPORTED, RR_PENDING = 5, 6
 RR_OP_DENSE, RR_OP_CSR, RR_OP_GAUSS_KERNEL = 0, 1, 2
 RR_SKETCH_GAUSSIAN, RR_SKETCH_SPARSE_SIGN, RR_SKETCH_SRHT = 0, 1, 2
 RR_PREC_FP64, RR_PREC_FP32, RR_PREC_MIXED = 0, 1, 2
-RR_VARIANT_C, RR_VARIANT_R = 0, 1
+RR_VARIANT_C, RR_VARIANT_R, RR_VARIANT_G = 0, 1, 2
 RR_ORTH_CHOLQR2, RR_ORTH_RAND_CHOLQR = 0, 1
 
 SKETCHES = {"gaussian": RR_SKETCH_GAUSSIAN, "sparse_sign": RR_SKETCH_SPARSE_SIGN,
             "srht": RR_SKETCH_SRHT}
 PRECISIONS = {"fp64": RR_PREC_FP64, "fp32": RR_PREC_FP32, "mixed": RR_PREC_MIXED}
-VARIANTS = {"C": RR_VARIANT_C, "R": RR_VARIANT_R}
+VARIANTS = {"C": RR_VARIANT_C, "R": RR_VARIANT_R, "G": RR_VARIANT_G}
 ORTHS = {"cholqr2": RR_ORTH_CHOLQR2, "rand_cholqr": RR_ORTH_RAND_CHOLQR}
 
 

@@ -695,6 +695,43 @@ void form_H(const double* G, double tau, double* H, int k, cudaStream_t st) {
   k_form_H<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(G, tau, H, k);
 }
 
+// out = a A + b I (k x k)
+__global__ void k_scale_add_identity(const double* __restrict__ A, double a, double b,
+                                     double* __restrict__ out, int k) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)k * k) return;
+  const int i = (int)(e / k), j = (int)(e % k);
+  out[e] = a * A[e] + (i == j ? b : 0.0);
+}
+void kxk_scale_add_identity(const double* A, double a, double b, double* out, int k,
+                            cudaStream_t st) {
+  k_scale_add_identity<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(A, a, b, out, k);
+}
+
+// out[0] = |A - c I|_F (one block, fixed order)
+__global__ void k_frob_minus_identity(const double* __restrict__ A, double c, int k,
+                                      double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  const int64_t total = (int64_t)k * k;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e % k);
+    const double d = A[e] - (i == j ? c : 0.0);
+    s = fma(d, d, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[0] = sqrt(t);
+  }
+}
+void kxk_frob_minus_identity(const double* A, double c, int k, double* out, cudaStream_t st) {
+  k_frob_minus_identity<<<1, 1024, 0, st>>>(A, c, k, out);
+}
+
 template <typename Tin, typename Tout>
 __global__ void k_convert(const Tin* __restrict__ in, Tout* __restrict__ out, int64_t count) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

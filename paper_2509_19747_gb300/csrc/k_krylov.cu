@@ -467,6 +467,58 @@ __device__ __forceinline__ void finish_mode(ColState& st, int mode, double s) {
     }
   } else if (mode == kModeNorm) {      // lam = |out|
     st.lam = sqrt(s);
+  } else if (mode == kModeMrInit) {    // gamma_1 = sqrt(r^T P r): start of MINRES
+    st.rr = s;
+    st.mupd = 0;
+    if (st.active) {
+      if (!(s > 0.0 && isfinite(s))) {
+        if (s == 0.0) st.active = 0;
+        else { st.status = RR_ERR_BREAKDOWN; st.active = 0; }
+      } else {
+        st.mg = sqrt(s);
+        st.mgp = 1.0;
+        st.meta = st.meta0 = st.mg;
+        st.mc = st.mcp = 1.0;
+        st.ms = st.msp = 0.0;
+      }
+    }
+  } else if (mode == kModeMrDelta) {   // delta_j = (A z_j)^T z_j
+    if (st.active) st.mdelta = s;
+  } else if (mode == kModeMrGamma) {   // gamma_{j+1}, the rotation, eta, the stop
+    st.mupd = 0;
+    if (st.active) {
+      const double g = st.mg, d = st.mdelta;
+      if (!(isfinite(s) && isfinite(d))) {
+        st.status = RR_ERR_BREAKDOWN;
+        st.active = 0;
+      } else {
+        const double gn = sqrt(fmax(s, 0.0));
+        const double a0 = st.mc * d - st.mcp * st.ms * g;
+        const double a1 = hypot(a0, gn);
+        if (!(a1 > 0.0)) {
+          st.status = RR_ERR_BREAKDOWN;
+          st.active = 0;
+        } else {
+          st.ma1 = a1;
+          st.ma2 = st.ms * d + st.mcp * st.mc * g;
+          st.ma3 = st.msp * g;
+          const double cn = a0 / a1, sn = gn / a1;
+          st.mxc = cn * st.meta;
+          st.meta = -sn * st.meta;
+          st.mgp = g;
+          st.mg = gn;
+          st.mcp = st.mc;
+          st.mc = cn;
+          st.msp = st.ms;
+          st.ms = sn;
+          st.mupd = 1;
+          st.iters += 1;
+          // stop2 holds the relative target of the P-norm of the residual
+          if (fabs(st.meta) <= st.stop2 * st.meta0 || gn == 0.0 || st.iters >= st.budget)
+            st.active = 0;
+        }
+      }
+    }
   }
 }
 
@@ -845,6 +897,67 @@ void scale_cols(const T* X, T* out, int64_t n, int mp, const ColState* cs, cudaS
   k_scale_cols<T><<<grid_rows(n * mp, 256 * 4), 256, 0, st>>>(X, out, n, mp, cs);
 }
 
+// ------------------------------------------------------ MINRES (variant G)
+template <typename T>
+__global__ void k_minres_v(const T* __restrict__ Az, T* __restrict__ V, T* __restrict__ Vp,
+                           int64_t n, int mp, const ColState* __restrict__ cs) {
+  const int64_t total = n * mp;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const int c = (int)(g % mp);
+    if (!cs[c].active) continue;
+    const T a = (T)(cs[c].mdelta / cs[c].mg), b = (T)(cs[c].mg / cs[c].mgp);
+    const T v = V[g];
+    const T vn = Az[g] - a * v - b * Vp[g];
+    Vp[g] = v;
+    V[g] = vn;
+  }
+}
+
+template <typename T>
+__global__ void k_minres_w(T* __restrict__ Zs, const T* __restrict__ Z, T* __restrict__ W,
+                           T* __restrict__ Wp, T* __restrict__ E, int64_t n, int mp,
+                           const ColState* __restrict__ cs) {
+  const int64_t total = n * mp;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const int c = (int)(g % mp);
+    const ColState& st = cs[c];
+    if (!st.mupd) continue;
+    const T w = W[g];
+    const T wn = (Zs[g] - (T)st.ma3 * Wp[g] - (T)st.ma2 * w) / (T)st.ma1;
+    E[g] += (T)st.mxc * wn;
+    Wp[g] = w;
+    W[g] = wn;
+    if (st.mg > 0.0) Zs[g] = (T)((double)Z[g] / st.mg);
+  }
+}
+
+template <typename T>
+__global__ void k_minres_zs(const T* __restrict__ Z, T* __restrict__ Zs, int64_t n, int mp,
+                            const ColState* __restrict__ cs) {
+  const int64_t total = n * mp;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const int c = (int)(g % mp);
+    Zs[g] = (cs[c].active && cs[c].mg > 0.0) ? (T)((double)Z[g] / cs[c].mg) : (T)0;
+  }
+}
+
+template <typename T>
+void minres_v(const T* Az, T* V, T* Vp, int64_t n, int mp, const ColState* cs, cudaStream_t st) {
+  k_minres_v<T><<<grid_rows(n * mp, 256 * 4), 256, 0, st>>>(Az, V, Vp, n, mp, cs);
+}
+template <typename T>
+void minres_w(T* Zs, const T* Z, T* W, T* Wp, T* E, int64_t n, int mp, const ColState* cs,
+              cudaStream_t st) {
+  k_minres_w<T><<<grid_rows(n * mp, 256 * 4), 256, 0, st>>>(Zs, Z, W, Wp, E, n, mp, cs);
+}
+template <typename T>
+void minres_zs(const T* Z, T* Zs, int64_t n, int mp, const ColState* cs, cudaStream_t st) {
+  k_minres_zs<T><<<grid_rows(n * mp, 256 * 4), 256, 0, st>>>(Z, Zs, n, mp, cs);
+}
+
 // column-major (ld) <-> interleaved n x mp
 __global__ void k_gather_cols(const double* __restrict__ B, int64_t ld, int m, int64_t n, int mp,
                               double* __restrict__ out) {
@@ -884,6 +997,7 @@ __global__ void k_restart_init(ColState* cs, int mp, RestartParams p) {
   s.beta = 0.0;
   s.rho = 0.0;
   s.status = RR_OK;
+  s.mupd = 0;
 }
 void restart_init(ColState* cs, int mp, const RestartParams& p, cudaStream_t st) {
   k_restart_init<<<1, 32, 0, st>>>(cs, mp, p);
@@ -903,7 +1017,11 @@ void restart_init(ColState* cs, int mp, const RestartParams& p, cudaStream_t st)
   template void update_cg<T>(T*, T*, const T*, const T*, int64_t, int, double*, unsigned*,       \
                              ColState*, cudaStream_t);                                           \
   template void p_update<T>(T*, const T*, int64_t, int, const ColState*, bool, cudaStream_t);    \
-  template void scale_cols<T>(const T*, T*, int64_t, int, const ColState*, cudaStream_t);
+  template void scale_cols<T>(const T*, T*, int64_t, int, const ColState*, cudaStream_t);      \
+  template void minres_v<T>(const T*, T*, T*, int64_t, int, const ColState*, cudaStream_t);      \
+  template void minres_w<T>(T*, const T*, T*, T*, T*, int64_t, int, const ColState*,             \
+                            cudaStream_t);                                                       \
+  template void minres_zs<T>(const T*, T*, int64_t, int, const ColState*, cudaStream_t);
 
 RR_INST(float)
 RR_INST(double)

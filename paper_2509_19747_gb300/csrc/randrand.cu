@@ -20,6 +20,7 @@ using namespace rr;
 namespace {
 
 constexpr int kKK = 19;           // k x k float64 work matrices
+constexpr int kNumVec = 8;        // Krylov vectors of n x mp (MINRES uses all eight)
 constexpr int kMaxGammaHost = 16; // sparse-sign nonzeros per row, at most
 constexpr int kChunk = 8;         // Krylov iterations per captured graph
 constexpr int kImplicitChunk = 256;  // iterations per persistent basis-less launch
@@ -95,7 +96,7 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
                       ? 2 * npad_tc * kAugFloats * 4 + mv_tc2_vsplit_elems(A.n) * 2 : 0;
   L.size[R_MVS] = op_matvec_scratch_elems(od, mp) * 8;
   // Krylov vectors carry zero rows up to the tensor-core tile multiple
-  L.size[R_VT] = 7 * (size_t)mv_tc_pad(A.n) * (size_t)mp * ts;
+  L.size[R_VT] = (size_t)kNumVec * (size_t)mv_tc_pad(A.n) * (size_t)mp * ts;
   L.size[R_V64] = 4 * n * (size_t)mp * 8;
   L.size[R_STAGE] = 2 * n * (size_t)mp * 8;
   L.size[R_TPART] = (size_t)qt_nslab(A.n) * kk * (size_t)mp * 8;
@@ -125,7 +126,10 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
   // the triangular inverse stages 2 k float64 values per CTA in shared memory
   if (k > 14000) return RR_ERR_UNSUPPORTED;
   if (o.max_rhs < 1 || o.max_rhs > 8) return RR_ERR_INVALID_ARG;
-  if (o.variant != RR_VARIANT_C && o.variant != RR_VARIANT_R) return RR_ERR_INVALID_ARG;
+  if (o.variant != RR_VARIANT_C && o.variant != RR_VARIANT_R && o.variant != RR_VARIANT_G)
+    return RR_ERR_INVALID_ARG;
+  // G-RandRAND works with an explicit basis (its Pi~ needs Q)
+  if (o.variant == RR_VARIANT_G && uses_alg3(o)) return RR_ERR_UNSUPPORTED;
   if (o.precision < RR_PREC_FP64 || o.precision > RR_PREC_MIXED) return RR_ERR_INVALID_ARG;
   if (o.orth != RR_ORTH_CHOLQR2 && o.orth != RR_ORTH_RAND_CHOLQR) return RR_ERR_INVALID_ARG;
   if (o.gamma < 1 || o.gamma > kMaxGammaHost) return RR_ERR_INVALID_ARG;
@@ -246,7 +250,7 @@ struct rr_handle {
   int* dstatus;
   void* mvs;
   // solve state
-  void* V[7];  // R P W Z E U V
+  void* V[8];  // R P W Z E U V S
   double* v64[4];  // B X R W
   double* stage[2];
   double* tpart;
@@ -281,7 +285,7 @@ struct rr_handle {
 
 namespace {
 
-enum { kR = 0, kP = 1, kW = 2, kZ = 3, kE = 4, kU = 5, kV = 6 };
+enum { kR = 0, kP = 1, kW = 2, kZ = 3, kE = 4, kU = 5, kV = 6, kS = 7 };
 enum { kB64 = 0, kX64 = 1, kR64 = 2, kW64 = 3 };
 // k x k slots
 enum { kR1 = 0, kR2 = 1, kRinvA = 2, kRinvB = 3, kRinv = 4, kRfull = 5, kM = 6, kG = 7, kH = 8,
@@ -326,7 +330,7 @@ void carve(rr_handle* h) {
   const size_t vec = (size_t)h->n * h->mp;
   const size_t vecp = (size_t)mv_tc_pad(h->n) * h->mp;
   unsigned char* vb = (unsigned char*)at(R_VT);
-  for (int i = 0; i < 7; ++i) h->V[i] = vb + i * vecp * ts;
+  for (int i = 0; i < kNumVec; ++i) h->V[i] = vb + i * vecp * ts;
   float* aug = (float*)at(R_AUG);
   h->op.aug_a = aug;
   h->op.aug_b = aug ? aug + (size_t)mv_tc_pad(h->n) * kAugFloats : nullptr;
@@ -790,11 +794,99 @@ void implicit_core(rr_handle* h) {
                   h->st);
 }
 
+// Square root of the SPD k x k matrix M, in place: the coupled Newton-Schulz
+// iteration (Higham, Functions of Matrices, Sec. 6.3: Y <- Y T, Z <- T Z,
+// T = (3 I - Z Y) / 2 from Y = M / c, Z = I with c = |M|_F, so that the
+// spectrum of Y lies in (0, 1]; Y -> (M / c)^(1/2)), float64 k x k products.
+// Stops when |Z Y - I|_F <= 1e-13 sqrt(k) (checked every 4 steps), at most
+// 120 steps (the eigenvalues of Z Y grow by ~9/4 per step while small).
+rr_status sqrtm_spd(rr_handle* h, double* M) {
+  const int k = h->k;
+  cudaStream_t st = h->st;
+  double* Y = h->kk[kR1];
+  double* Z = h->kk[kR2];
+  double* T = h->kk[kTm];
+  double* S1 = h->kk[kScA];
+  double* S2 = h->kk[kScB];
+  double fro = 0.0;
+  kxk_frob_minus_identity(M, 0.0, k, h->norms, st);
+  RR_TRY(read_doubles(h, h->norms, 1, &fro));
+  if (!(fro > 0.0) || !std::isfinite(fro)) return RR_ERR_NOT_SPD;
+  kxk_scale_add_identity(M, 1.0 / fro, 0.0, Y, k, st);
+  kxk_scale_add_identity(M, 0.0, 1.0, Z, k, st);
+  const int64_t kk2 = (int64_t)k * k;
+  bool done = false;
+  for (int it = 0; it < 120 && !done; ++it) {
+    gemm_nn<double>(k, k, k, 1.0, Z, k, Y, k, 0.0, nullptr, 0, S1, k, st);   // Z Y
+    if (it % 4 == 3) {
+      double d = 0.0;
+      kxk_frob_minus_identity(S1, 1.0, k, h->norms, st);
+      RR_TRY(read_doubles(h, h->norms, 1, &d));
+      if (!std::isfinite(d)) return RR_ERR_NOT_SPD;
+      if (d <= 1e-13 * std::sqrt((double)k)) done = true;
+    }
+    kxk_scale_add_identity(S1, -0.5, 1.5, T, k, st);                          // (3I - ZY)/2
+    gemm_nn<double>(k, k, k, 1.0, Y, k, T, k, 0.0, nullptr, 0, S2, k, st);    // Y T
+    gemm_nn<double>(k, k, k, 1.0, T, k, Z, k, 0.0, nullptr, 0, S1, k, st);    // T Z
+    RR_CUDA_TRY(cudaMemcpyAsync(Y, S2, (size_t)kk2 * 8, cudaMemcpyDeviceToDevice, st));
+    RR_CUDA_TRY(cudaMemcpyAsync(Z, S1, (size_t)kk2 * 8, cudaMemcpyDeviceToDevice, st));
+  }
+  // M^(1/2) = c^(1/2) Y, symmetrized against rounding
+  kxk_scale_add_identity(Y, std::sqrt(fro), 0.0, S1, k, st);
+  transpose_kxk(S1, S2, k, st);
+  axpby<double, double, double>(S1, coefs_all(0.5), S2, coefs_all(0.5), M, kk2, 1, st);
+  return RR_OK;
+}
+
+// G-RandRAND norms (Sec. 6.3): |(I - Pi) A_mu| (column 0) and |Pi~ A_mu|
+// (column 1, Pi~ = Q G Q^T), each the square root of a power-iteration
+// estimate of the largest eigenvalue of B^T B: A_mu (I - Pi) A_mu and
+// A_mu Pi~^2 A_mu (two products with A_mu per step)
+template <typename T>
+rr_status power_iterations_G(rr_handle* h) {
+  const int64_t n = h->n;
+  const int mp = h->mp, k = h->k;
+  T* Vv = vt<T>(h, kV);
+  T* Uv = vt<T>(h, kU);
+  T* Wv = vt<T>(h, kW);
+  T* Zv = vt<T>(h, kZ);
+  RR_CUDA_TRY(cudaMemsetAsync(Vv, 0, (size_t)n * mp * sizeof(T), h->st));
+  gen_power_start<T>(Vv, n, mp, 0, 0, h->seed, h->st);
+  gen_power_start<T>(Vv, n, mp, 1, 1, h->seed, h->st);
+  dot_cols<T>(Vv, Vv, n, mp, kModeNorm, h->rpart, h->cnt, h->cs, false, nullptr, h->st);
+  scale_cols<T>(Vv, Vv, n, mp, h->cs, h->st);
+  for (int it = 0; it < h->o.power_iters; ++it) {
+    matvec<T>(h, Vv, Wv, ev_take(h, RR_PROF_POWER));                 // u = A_mu v
+    qt<T>(h, Wv, h->t[0], false);
+    // column 0: -Q^T u (-> (I - Pi) u); column 1: G (G Q^T u) (-> Pi~^2 u)
+    kxk_apply(h->kk[kG], h->t[0], k, mp, coefs(-1.0, 0.0), coefs(0.0, 1.0), h->t[1], h->st);
+    kxk_apply(h->kk[kG], h->t[1], k, mp, coefs(1.0, 0.0), coefs(0.0, 1.0), h->t[2], h->st);
+    qcomb<T>((const T*)h->Q, n, k, mp, h->t[2], coefs(1.0, 0.0), Wv, Uv, nullptr, kModeNone,
+             h->rpart, h->cnt, h->cs, false, h->st);
+    matvec<T>(h, Uv, Zv, ev_take(h, RR_PROF_POWER));                 // A_mu (...)
+    dot_cols<T>(Zv, Zv, n, mp, kModeNorm, h->rpart, h->cnt, h->cs, false, nullptr, h->st);
+    scale_cols<T>(Zv, Vv, n, mp, h->cs, h->st);
+  }
+  RR_TRY(read_cs(h));
+  h->normE = std::sqrt(h->cs_host[0].lam);
+  h->lam_max = std::sqrt(h->cs_host[1].lam);
+  return RR_OK;
+}
+
 // tau: eq:c_randrand_tau with rho from eq:optimal_rho (F = 1/mu) for C;
 // tau = |E| (Alg. 4 step 2) for R.  |E| is clamped below at mu: for k < n
 // interlacing gives |E| >= lambda_min(A_mu) >= mu, and the clamp keeps tau
 // positive in the degenerate case k = n (E = 0).
 void choose_tau(rr_handle* h) {
+  if (h->o.variant == RR_VARIANT_G) {
+    // eq:g_randrand_tau with the Sec. 6.3 estimates |(I - Pi) A_mu| (normE)
+    // and |Pi~ A_mu| (lam_max); rho = 0.5 a priori (eq:rho_g_rand_rand needs
+    // |A_mu^-1|, unknown for an indefinite A_mu)
+    const double rho = h->o.rho > 0.0 ? h->o.rho : 0.5;
+    h->tau = (h->lam_max > 0.0) ? std::sqrt(rho) * h->normE / h->lam_max : 1.0;
+    if (!(h->tau > 0.0)) h->tau = 1.0;
+    return;
+  }
   const double nE = std::max(h->normE, h->mu);
   if (h->o.variant == RR_VARIANT_C) {
     double rho;
@@ -928,9 +1020,18 @@ rr_status finish_build(rr_handle* h, const double* G1given) {
   if (uses_alg3(h->o)) RR_TRY(rand_qless_qr<T>(h));
   else RR_TRY(orthogonalize<T>(h, G1given));
   if (h->o.variant == RR_VARIANT_C) RR_TRY(core_matrix(h));
+  if (h->o.variant == RR_VARIANT_G) {
+    // Sec. 3.3: G = (R^-T (Omega^T Omega) R^-1)^(1/2); core_matrix forms
+    // R^-T M R^-1 in its SPD-preserving form for M = Omega^T Omega
+    gram<T>(h, (const T*)h->Om, h->kk[kM]);
+    RR_TRY(core_matrix(h));
+    RR_TRY(sqrtm_spd(h, h->kk[kG]));
+  }
   if (h->implicit) {
     implicit_core(h);
     RR_TRY(power_iterations_implicit<T>(h));
+  } else if (h->o.variant == RR_VARIANT_G) {
+    RR_TRY(power_iterations_G<T>(h));
   } else {
     RR_TRY(power_iterations<T>(h));
   }
@@ -947,10 +1048,12 @@ rr_status finish_build(rr_handle* h, const double* G1given) {
     h->fusedG = (h->o.iter_impl == 0 && h->sketch == RR_SKETCH_SPARSE_SIGN)
                     ? pcg_implicit_ctas<T>(n, k, h->mp) : 0;
     if (h->fusedG > 0) RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
-  } else if (h->o.variant == RR_VARIANT_C) {
-    // P = I + Q (tau G - I) Q^T = I + Q H Q^T
+  } else if (h->o.variant == RR_VARIANT_C || h->o.variant == RR_VARIANT_G) {
+    // P = I + Q (tau G - I) Q^T = I + Q H Q^T (C; for G, (I - Pi) + tau Q G Q^T
+    // is the same expression)
     form_H(h->kk[kG], h->tau, h->kk[kH], k, st);
-    h->fusedG = (h->o.iter_impl == 0) ? pcg_tail_ctas<T>(n, k, h->mp) : 0;
+    h->fusedG = (h->o.iter_impl == 0 && h->o.variant == RR_VARIANT_C)
+                    ? pcg_tail_ctas<T>(n, k, h->mp) : 0;
     // keep QH = Q H so that z = r + QH (Q^T r)
     h->QH = h->Y;
     right_mult<T>(h, (const T*)h->Q, h->kk[kH], (T*)h->QH);
@@ -1049,6 +1152,31 @@ void iter_C_implicit(rr_handle* h, const cudaEvent_t* ev) {
 template <typename T>
 void iter_R(rr_handle* h, const cudaEvent_t* ev);
 
+// One preconditioned MINRES step (variant G; the Lanczos / Givens form of
+// the oracle): Az = A_mu zs, delta = Az^T zs, v_next = Az - (delta / gamma) v
+// - (gamma / gamma_prev) v_prev, z = P v_next and gamma_next = (v^T z)^(1/2)
+// with the rotation in the last block, then the direction and x updates and
+// zs = z / gamma_next.  All vectors keep their buffers (shifts are in place).
+template <typename T>
+void iter_G(rr_handle* h, const cudaEvent_t* ev) {
+  const int64_t n = h->n;
+  const int mp = h->mp;
+  cudaStream_t st = h->st;
+  T* Vv = vt<T>(h, kR);
+  T* Vp = vt<T>(h, kP);
+  T* Az = vt<T>(h, kW);
+  T* Zv = vt<T>(h, kZ);
+  T* Ev = vt<T>(h, kE);
+  T* Wv = vt<T>(h, kU);
+  T* Wp = vt<T>(h, kV);
+  T* Zs = vt<T>(h, kS);
+  matvec<T>(h, Zs, Az, ev);
+  dot_cols<T>(Az, Zs, n, mp, kModeMrDelta, h->rpart, h->cnt, h->cs, true, nullptr, st);
+  minres_v<T>(Az, Vv, Vp, n, mp, h->cs, st);
+  precond_C<T>(h, Vv, Zv, kModeMrGamma);
+  minres_w<T>(Zs, Zv, Wv, Wp, Ev, n, mp, h->cs, st);
+}
+
 template <typename T>
 void iter_any(rr_handle* h, const cudaEvent_t* ev) {
   // the kernel-operator products skip their work once every column is done
@@ -1056,6 +1184,7 @@ void iter_any(rr_handle* h, const cudaEvent_t* ev) {
   h->op.gate_mp = h->mp;
   if (h->implicit) iter_C_implicit<T>(h, ev);
   else if (h->o.variant == RR_VARIANT_C) iter_C<T>(h, ev);
+  else if (h->o.variant == RR_VARIANT_G) iter_G<T>(h, ev);
   else iter_R<T>(h, ev);
   h->op.gate = nullptr;
 }
@@ -1227,7 +1356,8 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
       if (rel[c] <= rtol) { done[c] = true; stat[c] = RR_OK; continue; }
       if (used[c] >= maxit || restart == kMaxRestarts) { done[c] = true; stat[c] = RR_ERR_MAXIT; continue; }
       const double stop = std::max(h->o.restart_eta * rel[c] * bn, 0.5 * rtol * bn);
-      rp.stop2[c] = stop * stop;
+      // MINRES tracks |r|_P: the same reduction relative to the start
+      rp.stop2[c] = (h->o.variant == RR_VARIANT_G) ? stop / (rel[c] * bn) : stop * stop;
       rp.budget[c] = maxit - used[c];
       rp.active[c] = 1;
       any = true;
@@ -1247,6 +1377,15 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
       // z = P r, p = z, rho = r^T z
       precond_C<T>(h, Rv, vt<T>(h, kZ), kModeRhoInit);
       p_update<T>(vt<T>(h, kP), vt<T>(h, kZ), n, mp, h->cs, true, st);
+    } else if (h->o.variant == RR_VARIANT_G) {
+      // MINRES: v = r, v_prev = w = w_prev = 0, z = P v, gamma_1 = sqrt(v^T z),
+      // zs = z / gamma_1
+      const size_t vb = (size_t)n * mp * sizeof(T);
+      RR_CUDA_TRY(cudaMemsetAsync(vt<T>(h, kP), 0, vb, st));
+      RR_CUDA_TRY(cudaMemsetAsync(vt<T>(h, kU), 0, vb, st));
+      RR_CUDA_TRY(cudaMemsetAsync(vt<T>(h, kV), 0, vb, st));
+      precond_C<T>(h, Rv, vt<T>(h, kZ), kModeMrInit);
+      minres_zs<T>(vt<T>(h, kZ), vt<T>(h, kS), n, mp, h->cs, st);
     } else {
       p_update<T>(vt<T>(h, kP), Rv, n, mp, h->cs, true, st);
       dot_cols<T>(Rv, Rv, n, mp, kModeRhoInit, h->rpart, h->cnt, h->cs, false, nullptr, st);
@@ -1316,7 +1455,7 @@ void apply_impl(rr_handle* h) {
   axpby<double, double, T>(h->v64[kR64], coefs_all(1.0), nullptr, coefs_all(0.0), Rv, n, mp, h->st);
   if (h->implicit) {
     precond_implicit<T>(h, Rv, Zv, false, nullptr);
-  } else if (h->o.variant == RR_VARIANT_C) {
+  } else if (h->o.variant == RR_VARIANT_C || h->o.variant == RR_VARIANT_G) {
     precond_C<T>(h, Rv, Zv, kModeNone);
   } else {
     const T* Q = (const T*)h->Q;
@@ -1397,7 +1536,8 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
   if (opts) o = *opts;
   else rr_build_opts_default(&o);
   RR_TRY(validate(A, k, o));
-  if (!(mu >= 0.0) || !std::isfinite(mu)) return RR_ERR_INVALID_ARG;
+  // variants C and R need A_mu SPD (mu >= 0); G also takes an indefinite A_mu
+  if (!std::isfinite(mu) || (o.variant != RR_VARIANT_G && !(mu >= 0.0))) return RR_ERR_INVALID_ARG;
   if (sketch != RR_SKETCH_GAUSSIAN && sketch != RR_SKETCH_SPARSE_SIGN && sketch != RR_SKETCH_SRHT)
     return RR_ERR_INVALID_ARG;
   if (sketch == RR_SKETCH_SPARSE_SIGN && o.gamma > k) return RR_ERR_INVALID_ARG;
@@ -1550,7 +1690,7 @@ rr_status randrand_export(rr_handle* h, int32_t what, double* dst) {
       src = h->Q; count = nk; is_t = true; break;
     case 2: src = h->kk[kRfull]; count = kk; break;
     case 3:
-      if (h->o.variant != RR_VARIANT_C) return RR_ERR_INVALID_ARG;
+      if (h->o.variant != RR_VARIANT_C && h->o.variant != RR_VARIANT_G) return RR_ERR_INVALID_ARG;
       src = h->kk[kG]; count = kk; break;
     default: return RR_ERR_INVALID_ARG;
   }

@@ -43,6 +43,12 @@ struct ColState {
   int iters;      // inner iterations of the current restart
   int budget;     // iteration budget of the current restart
   int status;     // RR_OK or RR_ERR_BREAKDOWN
+  // MINRES (variant G): Lanczos norms gamma_j, gamma_{j-1}, delta_j, the
+  // last two Givens rotations (c, s), the residual P-norm eta and its start,
+  // and this step's direction coefficients a1, a2, a3 and x coefficient
+  double mg, mgp, mdelta, mc, mcp, ms, msp, meta, meta0, ma1, ma2, ma3, mxc;
+  int mupd;       // the direction / x update of this step applies
+  int mpad;
 };
 
 struct OpDev {
@@ -158,6 +164,10 @@ void gram_upper(const double* Tm, int k, double* part, double* out, cudaStream_t
 void add_diag(double* A, int k, double alpha, cudaStream_t st);
 // H = tau G - I
 void form_H(const double* G, double tau, double* H, int k, cudaStream_t st);
+// out = a A + b I; out[0] = |A - c I|_F (k x k float64)
+void kxk_scale_add_identity(const double* A, double a, double b, double* out, int k,
+                            cudaStream_t st);
+void kxk_frob_minus_identity(const double* A, double c, int k, double* out, cudaStream_t st);
 template <typename Tin, typename Tout>
 void convert(const Tin* in, Tout* out, int64_t count, cudaStream_t st);
 void transpose_kxk(const double* in, double* out, int k, cudaStream_t st);

@@ -22,7 +22,9 @@ struct RestartParams {
 };
 
 // what the last block of a fused reduction does with the per-column sums
-enum { kModeNone = 0, kModeAlpha = 1, kModeBeta = 2, kModeRhoInit = 3, kModeNorm = 4 };
+enum { kModeNone = 0, kModeAlpha = 1, kModeBeta = 2, kModeRhoInit = 3, kModeNorm = 4,
+       // MINRES (variant G): gamma_1 from r^T P r; delta_j; gamma_{j+1} and the rotation
+       kModeMrInit = 5, kModeMrDelta = 6, kModeMrGamma = 7 };
 
 int qt_rows_per_slab(int64_t n);
 
@@ -61,6 +63,18 @@ void gather_cols(const double* B, int64_t ld, int m, int64_t n, int mp, double* 
 void scatter_cols(const double* X, int64_t n, int mp, int m, double* out, int64_t ld,
                   cudaStream_t st);
 void restart_init(ColState* cs, int mp, const RestartParams& p, cudaStream_t st);
+// MINRES (variant G) vector steps, columns gated by their state:
+//   v_prev <- v, v <- Az - (delta/gamma) v - (gamma/gamma_prev) v_prev
+template <typename T>
+void minres_v(const T* Az, T* V, T* Vp, int64_t n, int mp, const ColState* cs, cudaStream_t st);
+//   w_new = (zs - a3 w_prev - a2 w) / a1, e += xc w_new, w_prev <- w, w <- w_new,
+//   zs <- z / gamma (the next normalized Lanczos vector)
+template <typename T>
+void minres_w(T* Zs, const T* Z, T* W, T* Wp, T* E, int64_t n, int mp, const ColState* cs,
+              cudaStream_t st);
+//   zs <- z / gamma for the active columns (after kModeMrInit)
+template <typename T>
+void minres_zs(const T* Z, T* Zs, int64_t n, int mp, const ColState* cs, cudaStream_t st);
 
 constexpr int kMaxReduceBlocks = 8 * 152;  // upper bound on CTAs of the fused reductions
 
