@@ -35,6 +35,11 @@ Stream layout (counter = (c0, c1, c2, c3), key = (seed lo 32, seed hi 32)):
   of [0, s): four balanced Feistel rounds on b bits (b = log2 s; b + 1 when
   odd, then cycle-walking back into [0, s)), round r mapping (L, R) to
   (R, L xor (word 0 of counter (R, r, 6, 0)) mod 2^(b/2)).
+* Multi-level embedding X = X2 X1 (Sec. 2 eq:multilevelose): X1 (l1 x n,
+  gamma1 nonzeros +-1/sqrt(gamma1) per column) by the sparse-sign recipe on
+  stream 7 with column i of X1 as line i and l1 candidates; X2 (l x l1)
+  Gaussian with entries N(0, 1/l), X2[j][r] from the Gaussian recipe of
+  Omega on stream 8 with (r, j) in place of (i, j).  Omega = X^T = X1^T X2^T.
 
 Uniforms use 24 bits so that they are exact in float32 and float64:
 u = ((w >> 8) + 0.5) * 2^-24 in (0, 1).  Box-Muller pairs:
@@ -58,6 +63,8 @@ STREAM_THETA = 3
 STREAM_POWER = 4
 STREAM_SRHT_SIGN = 5
 STREAM_SRHT_PERM = 6
+STREAM_ML_SPARSE = 7
+STREAM_ML_GAUSS = 8
 
 _MASK32 = np.uint64(0xFFFFFFFF)
 
@@ -250,3 +257,40 @@ def srht_omega(n: int, k: int, seed: int) -> np.ndarray:
     i = np.arange(n, dtype=np.int64)
     par = np.bitwise_count(i[:, None] & rows[None, :]) & 1
     return srht_signs(n, seed)[:, None] * np.where(par, -1.0, 1.0) * (1.0 / math.sqrt(k))
+
+
+def multilevel_defaults(n: int, k: int) -> tuple[int, int]:
+    """(l1, gamma1) of the multi-level embedding: the paper's experiment with
+    sparse + Gaussian embeddings takes density gamma1 = log n and l1 = l log n
+    (Sec. 7, inverse-PDE example).  Reading: natural logarithm rounded up,
+    gamma1 at most 16 and at most l1."""
+    g = max(1, math.ceil(math.log(n)))
+    g = min(g, 16)
+    return g * k, g
+
+
+def multilevel_parts(n: int, k: int, l1: int, gamma1: int, seed: int):
+    """The two factors of X = X2 X1: the sparse pattern of X1 (for each
+    column i, gamma1 distinct rows in [0, l1) and their signs) and the dense
+    X2^T (l1 x k), entries N(0, 1/k)."""
+    cols, sgn = sparse_sign_pattern(n, l1, gamma1, seed, STREAM_ML_SPARSE)
+    X2T = gaussian_normals(l1, k, seed, STREAM_ML_GAUSS) / math.sqrt(k)
+    return cols, sgn, X2T
+
+
+def multilevel_x1(n: int, l1: int, gamma1: int, cols: np.ndarray, sgn: np.ndarray):
+    """X1 (l1 x n) as a scipy sparse matrix."""
+    import scipy.sparse as sp
+    rows = cols.ravel()
+    colidx = np.repeat(np.arange(n), gamma1)
+    return sp.csr_matrix((sgn.ravel() / math.sqrt(gamma1), (rows, colidx)), shape=(l1, n))
+
+
+def multilevel_omega(n: int, k: int, seed: int, l1: int = 0, gamma1: int = 0) -> np.ndarray:
+    """Omega = X^T = X1^T X2^T (n x k) of the multi-level embedding
+    (Sec. 2 eq:multilevelose); l1 = gamma1 = 0 take multilevel_defaults."""
+    if l1 <= 0 or gamma1 <= 0:
+        l1, gamma1 = multilevel_defaults(n, k)
+    cols, sgn, X2T = multilevel_parts(n, k, l1, gamma1, seed)
+    X1 = multilevel_x1(n, l1, gamma1, cols, sgn)
+    return np.asarray(X1.T @ X2T)

@@ -9,8 +9,8 @@ What it computes (paper: Balabanov, Derezinski, Mahoney et al., "RandRAND",
 arXiv 2509.19747):
 
 * the shifted system (A + mu I) x = b, A symmetric PSD (Sec. 1, eq:initsys);
-* the test matrix Omega = X^T (q = 0 in eq:testmatrix), Gaussian or sparse
-  sign (Sec. 2), drawn by ``oracle.philox``;
+* the test matrix Omega = A^q X^T (eq:testmatrix), X Gaussian, sparse sign,
+  SRHT or the multi-level embedding X2 X1 (Sec. 2), drawn by ``oracle.philox``;
 * the basis Y_mu = A_mu Omega and its orthogonalisation A_mu Omega = Q R
   (Sec. 4.1 eq:Rdef) by Householder QR (library ``numpy.linalg.qr``), or
   the randomised Q-less preconditioned Cholesky QR (Sec. 4.2, Alg. 3);
@@ -230,18 +230,24 @@ class Build:
 
 
 def make_omega(n: int, k: int, sketch: str, seed: int, gamma: int = 8,
-               precision: str = "fp64", q: int = 0, op=None) -> np.ndarray:
+               precision: str = "fp64", q: int = 0, op=None, ml_l1: int = 0,
+               ml_gamma: int = 0) -> np.ndarray:
     """Test matrix Omega = A^q X^T (eq:testmatrix, A symmetric), rounded to the
     working precision of the sketch (float64, float32 or bfloat16).  X^T is
     the Gaussian or sparse-sign draw; with q >= 1 it is multiplied by A (not
     A_mu: Omega does not depend on the shift) q times before the rounding.
-    X^T may also be an SRHT (Sec. 2, fast randomized transforms)."""
+    X^T may also be an SRHT (Sec. 2, fast randomized transforms) or the
+    multi-level embedding X = X2 X1 of eq:multilevelose (sparse X1 with
+    ml_l1 rows and ml_gamma nonzeros per column, Gaussian X2), whose float64
+    product is rounded once."""
     if sketch == "gaussian":
         Om = philox.gaussian_omega(n, k, seed)
     elif sketch == "sparse_sign":
         Om = philox.sparse_sign_omega_dense(n, k, gamma, seed)
     elif sketch == "srht":
         Om = philox.srht_omega(n, k, seed)
+    elif sketch == "multilevel":
+        Om = philox.multilevel_omega(n, k, seed, ml_l1, ml_gamma)
     else:
         raise ValueError(sketch)
     if q > 0:
@@ -291,7 +297,7 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
           gamma: int = 8, l_sk: int | None = None, gamma_sk: int = 8,
           power_iters: int = 20, rho: float | None = None,
           tau: float | None = None, q: int = 0,
-          a_omega: np.ndarray | None = None) -> Build:
+          a_omega: np.ndarray | None = None, ml_l1: int = 0, ml_gamma: int = 0) -> Build:
     """a_omega: A Omega computed once for several shifts (Sec. 5.1): then
     omega must be the Omega it was computed from, and Y_mu = a_omega + mu
     Omega replaces the product."""
@@ -299,7 +305,8 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
     if not (1 <= k <= n):
         raise ValueError("need 1 <= k <= n")
     if omega is None:
-        Om = make_omega(n, k, sketch, seed, gamma, omega_precision, q=q, op=op)
+        Om = make_omega(n, k, sketch, seed, gamma, omega_precision, q=q, op=op, ml_l1=ml_l1,
+                        ml_gamma=ml_gamma)
     else:
         # a given X^T: Omega = A^q X^T (eq:testmatrix)
         Om = np.asarray(omega, dtype=np.float64)

@@ -537,6 +537,79 @@ def test_srht_build_solves():
     assert np.linalg.norm(x - O.exact_solve(op, 1e-4, B)) <= 1e-8 * np.linalg.norm(x)
 
 
+# ------------------------------------------ multi-level embedding (Sec. 2 eq:multilevelose)
+def test_multilevel_x1_is_a_sparse_random_operator():
+    """X1 has exactly gamma1 nonzeros +-1/sqrt(gamma1) in each column, in
+    distinct rows, so every column has unit norm (Sec. 2 definition of a
+    sparse random operator); rows of X1 are hit about n gamma1 / l1 times."""
+    n, k = 3000, 40
+    l1, g1 = philox.multilevel_defaults(n, k)
+    assert (l1, g1) == (9 * 40, 9)
+    cols, sgn, X2T = philox.multilevel_parts(n, k, l1, g1, seed=31)
+    X1 = philox.multilevel_x1(n, l1, g1, cols, sgn).toarray()
+    assert X1.shape == (l1, n) and X2T.shape == (l1, k)
+    assert np.all((X1 != 0).sum(axis=0) == g1)
+    assert np.allclose(np.abs(X1[X1 != 0]), 1.0 / math.sqrt(g1), rtol=0, atol=1e-15)
+    assert np.allclose((X1 * X1).sum(axis=0), 1.0, rtol=0, atol=1e-14)
+    hits = (X1 != 0).sum(axis=1)
+    assert abs(hits.mean() - n * g1 / l1) < 1e-9 and hits.min() > 0
+    # the signs are balanced
+    assert abs(np.mean(sgn)) < 0.05
+
+
+def test_multilevel_omega_rows_are_signed_sums_of_x2_columns():
+    """Row i of Omega = X1^T X2^T, taken the other way round: the signed sum
+    of the gamma1 rows of X2^T that column i of X1 selects, and the dense
+    product (X2 X1)^T."""
+    n, k, l1, g1 = 500, 24, 120, 5
+    Om = philox.multilevel_omega(n, k, seed=32, l1=l1, gamma1=g1)
+    cols, sgn, X2T = philox.multilevel_parts(n, k, l1, g1, seed=32)
+    for i in (0, 1, 77, 499):
+        row = np.zeros(k)
+        for t in range(g1):
+            row += sgn[i, t] * X2T[cols[i, t]]
+        assert np.allclose(Om[i], row / math.sqrt(g1), rtol=0, atol=1e-14)
+    X1 = philox.multilevel_x1(n, l1, g1, cols, sgn).toarray()
+    assert np.allclose(Om, (X2T.T @ X1).T, rtol=0, atol=1e-13)
+
+
+def test_multilevel_embedding_is_isotropic_and_embeds_subspaces():
+    """E[X^T X] = I_n (E[X2^T X2] = I_l1 and the columns of X1 have unit
+    norm), so the mean squared row norm of Omega is 1; and X embeds a fixed
+    d-dimensional subspace: the singular values of X U lie near 1."""
+    n, k = 4000, 200
+    Om = philox.multilevel_omega(n, k, seed=33)
+    assert abs(np.mean(np.sum(Om * Om, axis=1)) - 1.0) < 0.02
+    U, _ = np.linalg.qr(np.random.default_rng(5).standard_normal((n, 4)))
+    sv = np.linalg.svd(Om.T @ U, compute_uv=False)
+    assert sv.min() > 0.7 and sv.max() < 1.3
+
+
+def test_multilevel_build_solves_like_gaussian():
+    """A multi-level test matrix gives a working preconditioner: PCG reaches
+    the exact solution, in about the iterations of the Gaussian sketch of
+    the same size (the range guarantees are alike)."""
+    P = W.dense_power_spectrum(400, seed=85, power=2.0)
+    op = O.DenseOp(P.A)
+    B = W.gaussian_rhs(400, 1, 85)
+    its = {}
+    for sk in ("multilevel", "gaussian"):
+        bd = O.build(op, 1e-4, 40, sk, seed=85)
+        x, info = O.solve(bd, B, rtol=1e-12)
+        assert np.linalg.norm(x - O.exact_solve(op, 1e-4, B)) <= 1e-8 * np.linalg.norm(x)
+        its[sk] = info[0].inner_iters
+    assert its["multilevel"] <= 1.5 * its["gaussian"] + 3
+
+
+def test_multilevel_full_sketch_converges_in_one_iteration():
+    # k = n: Omega square and nonsingular, Pi = I, P = tau A_mu^-1
+    P, op = small_dense(n=40)
+    bd = O.build(op, 1e-2, 40, "multilevel", seed=7)
+    b = W.gaussian_rhs(40, 1, 7)[:, 0]
+    x, info = O.solve(bd, b, rtol=1e-10, fixed_inner=1)
+    assert O.true_rel_residual(op, 1e-2, x, b)[0] < 1e-9
+
+
 # ------------------------------------------ G-RandRAND and MINRES (Sec. 3.3, 6.3)
 def _indefinite(n=200, seed=86, after=20):
     P = W.dense_power_spectrum(n, seed=seed, power=2.0)
