@@ -69,8 +69,10 @@ def parse():
                              "indefinite"])
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
     ap.add_argument("--workers", type=int, default=0, help="batched/serving: 0 = autotune")
-    ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "srht"],
-                    help="kernel ridge: test matrix (Gaussian or SRHT)")
+    ap.add_argument("--sketch", default=None,
+                    choices=["gaussian", "srht", "multilevel", "sparse_sign"],
+                    help="test matrix (default: Gaussian for the kernel ridge workload, "
+                         "sparse sign for the sparse diffusion workload)")
     ap.add_argument("--kernel-impl", type=int, default=0,
                     help="kernel ridge: Gaussian-kernel product form (rr_build_opts.kernel_impl)")
     return ap.parse_args()
@@ -237,7 +239,7 @@ def run_reference(args):
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
-    WORKLOAD["sketch"] = args.sketch
+    WORKLOAD["sketch"] = args.sketch or "gaussian"
 
     rank, world, local = dist_init(args)
     torch.cuda.set_device(local)
@@ -257,6 +259,7 @@ def run_ours(args):
     o.max_rhs = m
     o.profile = 1
     o.kernel_impl = args.kernel_impl
+    rr.set_multilevel(o, WORKLOAD["sketch"], n, k)
     ws_bytes = rr.randrand_workspace_bytes(op.c, k, o)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -519,6 +522,8 @@ def run_sparse(args):
     o.gamma = cfg["gamma"]
     o.gamma_sk = cfg["gamma_sk"]
     o.profile = 1
+    sketch = args.sketch or "sparse_sign"
+    rr.set_multilevel(o, sketch, C.n, cfg["k"])
     ws_bytes = rr.randrand_workspace_bytes(op.c, cfg["k"], o)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -526,7 +531,7 @@ def run_sparse(args):
     xd = torch.zeros_like(bd)
 
     def one(collect=None):
-        h = rr.randrand_build(op.c, cfg["mu"], cfg["k"], rr.RR_SKETCH_SPARSE_SIGN, seed, o,
+        h = rr.randrand_build(op.c, cfg["mu"], cfg["k"], rr.SKETCHES[sketch], seed, o,
                               ws.data_ptr(), ws_bytes, stream.cuda_stream)
         st, infos = rr.randrand_solve(h, bd.data_ptr(), 1, C.n, xd.data_ptr(), C.n, 0, cfg["rtol"],
                                       100000)
@@ -585,6 +590,8 @@ def run_sparse(args):
                  world * 1000.0 / ms, "solves/s", ms,
                  {**{kk: cfg[kk] for kk in ("workload", "side", "n", "k", "l_sk", "mu", "rtol",
                                             "precision", "orth")},
+                  "sketch": sketch if sketch != "multilevel"
+                  else f"multilevel (l1 = {o.ml_l1}, gamma1 = {o.ml_gamma})",
                   "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
                  latency_ms={"p50": float(np.percentile(step_ms, 50)),
                              "p99": float(np.percentile(step_ms, 99))},

@@ -62,9 +62,17 @@ enum {
 enum {
   RR_SKETCH_GAUSSIAN = 0,    /* entries N(0, 1/k) */
   RR_SKETCH_SPARSE_SIGN = 1, /* gamma entries +-1/sqrt(gamma) per row of Omega */
-  RR_SKETCH_SRHT = 2         /* subsampled randomized Hadamard transform (Sec. 2):
+  RR_SKETCH_SRHT = 2,        /* subsampled randomized Hadamard transform (Sec. 2):
                                 Omega = X^T, X = k^-1/2 S H D, the first n of
                                 s = 2^ceil(log2 n) columns; entries +-1/sqrt(k) */
+  RR_SKETCH_MULTILEVEL = 3   /* multi-level embedding X = X2 X1 (Sec. 2
+                                eq:multilevelose): X1 a sparse random operator
+                                (opts.ml_l1 x n, opts.ml_gamma entries
+                                +-1/sqrt(ml_gamma) per column), X2 Gaussian
+                                (k x ml_l1, entries N(0, 1/k)); Omega = X1^T X2^T.
+                                Needs opts.ml_gamma >= 1 (see
+                                rr_multilevel_defaults).  In the basis-less CSR
+                                form Omega is applied as the two factors */
 };
 
 /* Arithmetic of the path */
@@ -160,6 +168,12 @@ typedef struct {
                             sketch product; costs one more n x k array.  Variant
                             C with an explicit basis (orth CHOLQR2) and q = 0
                             only (else RR_ERR_UNSUPPORTED).  Default 0 */
+  int32_t ml_l1;         /* RR_SKETCH_MULTILEVEL: rows l1 of X1, k <= l1 <= 2^24 */
+  int32_t ml_gamma;      /* RR_SKETCH_MULTILEVEL: nonzeros per column of X1,
+                            1..16, <= ml_l1.  0 (the default) reserves no
+                            workspace for the multi-level factors, and a
+                            multi-level build then fails with
+                            RR_ERR_INVALID_ARG */
 } rr_build_opts;
 
 typedef struct {
@@ -193,6 +207,12 @@ typedef struct rr_handle rr_handle;
 /* Fill *o with the defaults listed in rr_build_opts. */
 void rr_build_opts_default(rr_build_opts* o);
 
+/* Set o->ml_gamma and o->ml_l1 to the multi-level embedding of the paper's
+ * sparse + Gaussian experiment (Sec. 7): gamma1 = ceil(ln n) (at most 16)
+ * nonzeros per column of X1 and l1 = gamma1 k rows.  Other fields are left
+ * as they are.  No-op when o is NULL, n < 1 or k < 1. */
+void rr_multilevel_defaults(int64_t n, int32_t k, rr_build_opts* o);
+
 /* Human-readable name of a status code (static string, never NULL). */
 const char* randrand_status_str(rr_status s);
 
@@ -211,7 +231,8 @@ rr_status randrand_workspace_bytes(const rr_operator* A, int32_t k,
  *   A          operator (see rr_operator); borrowed.
  *   mu         shift, >= 0 and finite.
  *   k          sketch dimension l of the paper, 1 <= k <= n.
- *   sketch     RR_SKETCH_GAUSSIAN, RR_SKETCH_SPARSE_SIGN or RR_SKETCH_SRHT.
+ *   sketch     RR_SKETCH_GAUSSIAN, RR_SKETCH_SPARSE_SIGN, RR_SKETCH_SRHT or
+ *              RR_SKETCH_MULTILEVEL.
  *   seed       64-bit key of the counter-based generator that draws Omega,
  *              Theta and the power-iteration start vectors.
  *   opts       NULL for defaults.

@@ -20,7 +20,7 @@ __all__ = [
     "RR_OK", "RR_ERR_INVALID_ARG", "RR_ERR_WORKSPACE", "RR_ERR_NOT_SPD", "RR_ERR_BREAKDOWN",
     "RR_ERR_MAXIT", "RR_ERR_TIMEOUT", "RR_ERR_CUDA", "RR_ERR_UNSUPPORTED", "RR_PENDING",
     "RR_OP_DENSE", "RR_OP_CSR", "RR_OP_GAUSS_KERNEL", "RR_SKETCH_GAUSSIAN",
-    "RR_SKETCH_SPARSE_SIGN", "RR_SKETCH_SRHT", "RR_PREC_FP64", "RR_PREC_FP32", "RR_PREC_MIXED", "RR_VARIANT_C",
+    "RR_SKETCH_SPARSE_SIGN", "RR_SKETCH_SRHT", "RR_SKETCH_MULTILEVEL", "RR_PREC_FP64", "RR_PREC_FP32", "RR_PREC_MIXED", "RR_VARIANT_C",
     "RR_VARIANT_R", "RR_VARIANT_G", "rr_operator", "rr_build_opts", "rr_solve_info", "rr_profile", "RandRandError",
     "load_library", "Operator", "Handle", "rr_request", "rr_result", "Arena", "Server",
     "Request", "solve_batch",
@@ -29,13 +29,13 @@ __all__ = [
 RR_OK, RR_ERR_INVALID_ARG, RR_ERR_WORKSPACE, RR_ERR_NOT_SPD, RR_ERR_BREAKDOWN = 0, 1, 2, 3, 4
 RR_ERR_MAXIT, RR_ERR_TIMEOUT, RR_ERR_CUDA, RR_ERR_UNSUPPORTED, RR_PENDING = 5, 6, 7, 8, 9
 RR_OP_DENSE, RR_OP_CSR, RR_OP_GAUSS_KERNEL = 0, 1, 2
-RR_SKETCH_GAUSSIAN, RR_SKETCH_SPARSE_SIGN, RR_SKETCH_SRHT = 0, 1, 2
+RR_SKETCH_GAUSSIAN, RR_SKETCH_SPARSE_SIGN, RR_SKETCH_SRHT, RR_SKETCH_MULTILEVEL = 0, 1, 2, 3
 RR_PREC_FP64, RR_PREC_FP32, RR_PREC_MIXED = 0, 1, 2
 RR_VARIANT_C, RR_VARIANT_R, RR_VARIANT_G = 0, 1, 2
 RR_ORTH_CHOLQR2, RR_ORTH_RAND_CHOLQR = 0, 1
 
 SKETCHES = {"gaussian": RR_SKETCH_GAUSSIAN, "sparse_sign": RR_SKETCH_SPARSE_SIGN,
-            "srht": RR_SKETCH_SRHT}
+            "srht": RR_SKETCH_SRHT, "multilevel": RR_SKETCH_MULTILEVEL}
 PRECISIONS = {"fp64": RR_PREC_FP64, "fp32": RR_PREC_FP32, "mixed": RR_PREC_MIXED}
 VARIANTS = {"C": RR_VARIANT_C, "R": RR_VARIANT_R, "G": RR_VARIANT_G}
 ORTHS = {"cholqr2": RR_ORTH_CHOLQR2, "rand_cholqr": RR_ORTH_RAND_CHOLQR}
@@ -60,6 +60,7 @@ class rr_build_opts(ctypes.Structure):
         ("rho", ctypes.c_double),
         ("restart_eta", ctypes.c_double),
         ("keep_sketch", ctypes.c_int32),
+        ("ml_l1", ctypes.c_int32), ("ml_gamma", ctypes.c_int32),
     ]
 
 
@@ -117,6 +118,7 @@ _LIB = None
 # (name, restype, argtypes) of every exported entry point
 _SIGNATURES = [
     ("rr_build_opts_default", None, [ctypes.POINTER(rr_build_opts)]),
+    ("rr_multilevel_defaults", None, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(rr_build_opts)]),
     ("randrand_status_str", ctypes.c_char_p, [ctypes.c_int32]),
     ("randrand_workspace_bytes", ctypes.c_int32,
      [ctypes.POINTER(rr_operator), ctypes.c_int32, ctypes.POINTER(rr_build_opts),
@@ -196,6 +198,19 @@ def _lib() -> ctypes.CDLL:
 
 
 # ------------------------------------------------------------ C entry points
+def set_multilevel(o: rr_build_opts, sketch: str, n: int, k: int, ml_l1: int = 0,
+                   ml_gamma: int = 0) -> None:
+    """Reserve the multi-level factors in o when the sketch is "multilevel":
+    the given sizes, else rr_multilevel_defaults (argument marshalling)."""
+    if sketch != "multilevel":
+        return
+    _lib().rr_multilevel_defaults(int(n), int(k), ctypes.byref(o))
+    if ml_gamma:
+        o.ml_gamma = int(ml_gamma)
+    if ml_l1:
+        o.ml_l1 = int(ml_l1)
+
+
 def rr_build_opts_default() -> rr_build_opts:
     o = rr_build_opts()
     _lib().rr_build_opts_default(ctypes.byref(o))
@@ -348,7 +363,9 @@ class Handle:
                  power_iters: int = 20, rho: float = 0.0, restart_eta: float = 1e-2,
                  gamma: int = 8, profile: bool = False, kernel_impl: int = 0, stream=None,
                  orth: str = "cholqr2", l_sk: int = 0, gamma_sk: int = 8, iter_impl: int = 0,
-                 q: int = 0, keep_sketch: bool = False):
+                 q: int = 0, keep_sketch: bool = False, ml_l1: int = 0, ml_gamma: int = 0):
+        """sketch "multilevel": ml_l1 / ml_gamma give X1's rows and nonzeros per
+        column; 0 takes rr_multilevel_defaults."""
         import torch
         self.op = op
         self.n = op.n
@@ -369,6 +386,7 @@ class Handle:
         o.iter_impl = iter_impl
         o.q = q
         o.keep_sketch = 1 if keep_sketch else 0
+        set_multilevel(o, sketch, op.n, k, ml_l1, ml_gamma)
         self.opts = o
         self.ws_bytes = randrand_workspace_bytes(op.c, k, o)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
@@ -505,7 +523,8 @@ class Request:
     def __init__(self, op: Operator, mu: float, k: int, b, rtol: float, sketch: str = "gaussian",
                  seed: int = 0, maxit: int = 20000, variant: str = "C", precision: str = "mixed",
                  orth: str = "cholqr2", power_iters: int = 20, gamma: int = 8, l_sk: int = 0,
-                 gamma_sk: int = 8, kernel_impl: int = 0, iter_impl: int = 0, q: int = 0):
+                 gamma_sk: int = 8, kernel_impl: int = 0, iter_impl: int = 0, q: int = 0,
+                 ml_l1: int = 0, ml_gamma: int = 0):
         import torch
         B = b.reshape(op.n, -1)
         m = B.shape[1]
@@ -524,6 +543,7 @@ class Request:
         o.kernel_impl = kernel_impl
         o.iter_impl = iter_impl
         o.q = q
+        set_multilevel(o, sketch, op.n, k, ml_l1, ml_gamma)
         self.op = op
         self.c = rr_request(op=op.c, mu=float(mu), k=int(k), sketch=SKETCHES[sketch],
                             seed=int(seed) & 0xFFFFFFFFFFFFFFFF, opts=o, b=self.bc.data_ptr(),

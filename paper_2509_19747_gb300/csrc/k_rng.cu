@@ -117,6 +117,160 @@ void sparse_to_dense_omega(T* Om, const int32_t* cols, const int8_t* sgn, int64_
   k_sparse_to_dense<T><<<(unsigned)cdiv(n, 128), 128, 0, st>>>(Om, cols, sgn, n, k, gamma, val);
 }
 
+// X2^T (l1 x k) of the multi-level embedding, entries N(0, 1/k) in float64;
+// X2 (k x l1) too when asked (the basis-less form applies both)
+__global__ void k_ml_x2(double* __restrict__ X2T, double* __restrict__ X2, int l1, int k,
+                        uint64_t seed) {
+  const int q4 = (k + 3) >> 2;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (int64_t)l1 * q4) return;
+  const int r = (int)(g / q4);
+  const int q = (int)(g - (int64_t)r * q4);
+  double z[4];
+  box_muller4(philox_draw(seed, (uint32_t)r, (uint32_t)q, kStreamMlGauss), z);
+  const double scale = 1.0 / sqrt((double)k);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int j = 4 * q + t;
+    if (j >= k) break;
+    const double v = z[t] * scale;
+    X2T[(int64_t)r * k + j] = v;
+    if (X2) X2[(int64_t)j * l1 + r] = v;
+  }
+}
+
+// Omega_ij = sum_t s_it X2T[c_it][j] / sqrt(gamma1), summed in float64 and
+// rounded once to the working type (and to bf16 with its K-major copy)
+template <typename T>
+__global__ void k_ml_omega(T* __restrict__ Om, __nv_bfloat16* __restrict__ Ob, int64_t n, int k,
+                           const int32_t* __restrict__ cols, const int8_t* __restrict__ sgn,
+                           int gamma1, const double* __restrict__ X2T, int round_bf16,
+                           int64_t ldo) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * k) return;
+  const int64_t i = g / k;
+  const int j = (int)(g - i * k);
+  double acc = 0.0;
+  for (int t = 0; t < gamma1; ++t) {
+    const double x = X2T[(int64_t)cols[i * gamma1 + t] * k + j];
+    acc += sgn[i * gamma1 + t] > 0 ? x : -x;
+  }
+  T v = (T)(acc / sqrt((double)gamma1));
+  if (round_bf16) {
+    const __nv_bfloat16 b = __float2bfloat16_rn((float)v);
+    v = (T)__bfloat162float(b);
+    if (Ob) Ob[(int64_t)j * ldo + i] = b;   // Omega^T, K-major operand of the sketch MMA
+  }
+  Om[g] = v;
+}
+
+template <typename T>
+void gen_multilevel_omega(T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, int k, int l1,
+                          int gamma1, uint64_t seed, bool round_bf16, int32_t* cols, int8_t* sgn,
+                          double* X2T, double* X2, cudaStream_t st) {
+  gen_sparse_sign(cols, sgn, n, l1, gamma1, seed, kStreamMlSparse, st);
+  const int64_t nq = (int64_t)l1 * ((k + 3) / 4);
+  k_ml_x2<<<(unsigned)cdiv(nq, 256), 256, 0, st>>>(X2T, X2, l1, k, seed);
+  k_ml_omega<T><<<(unsigned)cdiv(n * k, 256), 256, 0, st>>>(Om, OmT_bf16, n, k, cols, sgn, gamma1,
+                                                            X2T, round_bf16 ? 1 : 0, ldo);
+}
+
+// y = M x: one warp per row of M, lanes striding along the row (coalesced)
+template <int MP>
+__global__ void __launch_bounds__(256) k_rowmajor_gemv(const double* __restrict__ M, int rows,
+                                                       int cols, const double* __restrict__ x,
+                                                       double* __restrict__ y,
+                                                       const ColState* __restrict__ cs) {
+  if (cs) {
+    bool any = false;
+    for (int c = 0; c < MP; ++c) any |= cs[c].active != 0;
+    if (!any) return;
+  }
+  const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const double* m = M + (int64_t)row * cols;
+  double acc[MP];
+#pragma unroll
+  for (int c = 0; c < MP; ++c) acc[c] = 0.0;
+  for (int e = lane; e < cols; e += 32) {
+    const double a = m[e];
+#pragma unroll
+    for (int c = 0; c < MP; ++c) acc[c] = fma(a, x[(int64_t)e * MP + c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < MP; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    acc[c] = v;
+  }
+  if (lane < MP) {
+    double v = acc[0];
+#pragma unroll
+    for (int c = 1; c < MP; ++c)
+      if (lane == c) v = acc[c];
+    y[(int64_t)row * MP + lane] = v;
+  }
+}
+
+// y = M x with one CTA per row (long rows: a warp per row would leave most
+// SMs idle and serialise the row's loads)
+template <int MP>
+__global__ void __launch_bounds__(256) k_rowmajor_gemv_cta(const double* __restrict__ M, int cols,
+                                                           const double* __restrict__ x,
+                                                           double* __restrict__ y,
+                                                           const ColState* __restrict__ cs) {
+  if (cs) {
+    bool any = false;
+    for (int c = 0; c < MP; ++c) any |= cs[c].active != 0;
+    if (!any) return;
+  }
+  __shared__ double red[8][MP];
+  const double* m = M + (int64_t)blockIdx.x * cols;
+  double acc[MP];
+#pragma unroll
+  for (int c = 0; c < MP; ++c) acc[c] = 0.0;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < cols; e += 256) {
+    const double a = m[e];
+#pragma unroll
+    for (int c = 0; c < MP; ++c) acc[c] = fma(a, x[(int64_t)e * MP + c], acc[c]);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < MP; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < MP) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
+    y[(int64_t)blockIdx.x * MP + threadIdx.x] = v;
+  }
+}
+
+void rowmajor_gemv(const double* M, int rows, int cols, const double* x, int mp, double* y,
+                   const ColState* cs, cudaStream_t st) {
+  if (cols >= 1024) {
+    switch (mp) {
+      case 1: k_rowmajor_gemv_cta<1><<<rows, 256, 0, st>>>(M, cols, x, y, cs); break;
+      case 2: k_rowmajor_gemv_cta<2><<<rows, 256, 0, st>>>(M, cols, x, y, cs); break;
+      case 4: k_rowmajor_gemv_cta<4><<<rows, 256, 0, st>>>(M, cols, x, y, cs); break;
+      default: k_rowmajor_gemv_cta<8><<<rows, 256, 0, st>>>(M, cols, x, y, cs); break;
+    }
+    return;
+  }
+  const unsigned blocks = (unsigned)cdiv((int64_t)rows * 32, 256);
+  switch (mp) {
+    case 1: k_rowmajor_gemv<1><<<blocks, 256, 0, st>>>(M, rows, cols, x, y, cs); break;
+    case 2: k_rowmajor_gemv<2><<<blocks, 256, 0, st>>>(M, rows, cols, x, y, cs); break;
+    case 4: k_rowmajor_gemv<4><<<blocks, 256, 0, st>>>(M, rows, cols, x, y, cs); break;
+    default: k_rowmajor_gemv<8><<<blocks, 256, 0, st>>>(M, rows, cols, x, y, cs); break;
+  }
+}
+
 template <typename T>
 __global__ void k_power_start(T* __restrict__ V, int64_t n, int mp, int col, int which,
                               uint64_t seed) {
@@ -165,6 +319,12 @@ template void set_omega<float>(const float*, float*, __nv_bfloat16*, int64_t, in
 template void set_omega<double>(const double*, double*, __nv_bfloat16*, int64_t, int64_t, int,
                                 bool, cudaStream_t);
 
+template void gen_multilevel_omega<float>(float*, __nv_bfloat16*, int64_t, int64_t, int, int, int,
+                                          uint64_t, bool, int32_t*, int8_t*, double*, double*,
+                                          cudaStream_t);
+template void gen_multilevel_omega<double>(double*, __nv_bfloat16*, int64_t, int64_t, int, int,
+                                           int, uint64_t, bool, int32_t*, int8_t*, double*,
+                                           double*, cudaStream_t);
 template void gen_srht_omega<float>(float*, __nv_bfloat16*, int64_t, int64_t, int, uint64_t,
                                     bool, int32_t*, int8_t*, cudaStream_t);
 template void gen_srht_omega<double>(double*, __nv_bfloat16*, int64_t, int64_t, int, uint64_t,

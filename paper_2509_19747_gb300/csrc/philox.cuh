@@ -16,7 +16,11 @@
 //     set; row j of X is row pi(j) of the Sylvester Walsh-Hadamard matrix,
 //     pi a keyed permutation of [0, s): four balanced Feistel rounds on b
 //     bits (b = log2 s, or b + 1 with cycle-walking when b is odd), round r
-//     mapping (L, R) to (R, L ^ (word 0 of counter (R, r, 6, 0) mod 2^(b/2))).
+//     mapping (L, R) to (R, L ^ (word 0 of counter (R, r, 6, 0) mod 2^(b/2)));
+//   multi-level embedding X = X2 X1 (Sec. 2 eq:multilevelose): column i of
+//     X1 (l1 x n) by the sparse-sign recipe on stream 7 with l1 candidates;
+//     X2^T (l1 x k) by the Gaussian recipe on stream 8, counter (r, j>>2, 8,
+//     0) for row r, scaled by 1/sqrt(k).
 // Uniforms carry 24 bits, u = ((w >> 8) + 0.5) 2^-24, exact in float32.
 #pragma once
 #include <cstdint>
@@ -33,6 +37,8 @@ constexpr uint32_t kStreamTheta = 3;
 constexpr uint32_t kStreamPower = 4;
 constexpr uint32_t kStreamSrhtSign = 5;
 constexpr uint32_t kStreamSrhtPerm = 6;
+constexpr uint32_t kStreamMlSparse = 7;
+constexpr uint32_t kStreamMlGauss = 8;
 
 struct U32x4 {
   uint32_t v[4];

@@ -30,7 +30,7 @@ constexpr int kMaxRestarts = 400;
 enum Region {
   R_OM, R_OMB, R_SSC, R_SSS, R_THC, R_THS, R_SK, R_Y, R_Q, R_Y0, R_KK, R_KKT, R_GPART, R_CHOLW,
   R_STATUS, R_XS, R_CN, R_PN, R_AUG, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT,
-  R_CS, R_NORMS, R_FUSED, R_NREG
+  R_CS, R_NORMS, R_FUSED, R_ML, R_NREG
 };
 
 struct Layout {
@@ -57,6 +57,13 @@ bool basis_less(const rr_operator& A, const rr_build_opts& o) {
   return uses_alg3(o) && A.kind == RR_OP_CSR;
 }
 int sketch_rows(int k, const rr_build_opts& o) { return o.l_sk > 0 ? o.l_sk : 4 * k; }
+// multi-level embedding (Sec. 2 eq:multilevelose): storage reserved when
+// opts.ml_gamma > 0; the basis-less form keeps X2, X2^T and an l1 x mp buffer
+bool ml_reserved(const rr_build_opts& o) { return o.ml_gamma > 0; }
+// slabs of the X1 V partial sums: four per SM (the scatter into l1 bins is
+// latency-bound; more slabs would multiply the l1 x mp partials)
+int ml_rows_per_slab(int64_t n) { return (int)std::max<int64_t>(64, cdiv(n, 4 * 152)); }
+int ml_nslab(int64_t n) { return (int)cdiv(n, ml_rows_per_slab(n)); }
 
 Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   Layout L;
@@ -71,8 +78,12 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   const int gs_max = std::max(gram_nsplit(A.n, k, k), 1);
   L.size[R_OM] = n * kk * ts;
   L.size[R_OMB] = (o.precision == RR_PREC_MIXED) ? kk * (size_t)cdiv(A.n, 8) * 8 * 2 : 0;
-  L.size[R_SSC] = n * (size_t)o.gamma * 4;
-  L.size[R_SSS] = n * (size_t)o.gamma;
+  const size_t gmax = (size_t)std::max(o.gamma, ml_reserved(o) ? o.ml_gamma : 0);
+  L.size[R_SSC] = n * gmax * 4;
+  L.size[R_SSS] = n * gmax;
+  const bool ml_bl = ml_reserved(o) && basis_less(A, o);
+  const size_t l1 = ml_reserved(o) ? (size_t)o.ml_l1 : 0;
+  L.size[R_ML] = ml_reserved(o) ? (l1 * kk + (ml_bl ? kk * l1 + l1 * (size_t)mp : 0)) * 8 : 0;
   const size_t lsk = uses_alg3(o) ? (size_t)sketch_rows(k, o) : 0;
   L.size[R_THC] = uses_alg3(o) ? n * (size_t)o.gamma_sk * 4 : 0;
   L.size[R_THS] = uses_alg3(o) ? n * (size_t)o.gamma_sk : 0;
@@ -99,7 +110,8 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_VT] = (size_t)kNumVec * (size_t)mv_tc_pad(A.n) * (size_t)mp * ts;
   L.size[R_V64] = 4 * n * (size_t)mp * 8;
   L.size[R_STAGE] = 2 * n * (size_t)mp * 8;
-  L.size[R_TPART] = (size_t)qt_nslab(A.n) * kk * (size_t)mp * 8;
+  L.size[R_TPART] = std::max((size_t)qt_nslab(A.n) * kk,
+                             ml_bl ? (size_t)ml_nslab(A.n) * l1 : (size_t)0) * (size_t)mp * 8;
   L.size[R_TVEC] = 3 * kk * (size_t)mp * 8;
   L.size[R_RPART] = (size_t)kMaxReduceBlocks * 8 * 8;
   L.size[R_CNT] = 64 * 4;
@@ -156,6 +168,15 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
     return RR_ERR_UNSUPPORTED;
   if (o.q < 0 || o.q > 4) return RR_ERR_INVALID_ARG;
   if (!(o.restart_eta > 0.0 && o.restart_eta < 1.0)) return RR_ERR_INVALID_ARG;
+  if (o.ml_gamma != 0 || o.ml_l1 != 0) {
+    if (o.ml_gamma < 1 || o.ml_gamma > kMaxGammaHost || o.ml_l1 < k || o.ml_l1 < o.ml_gamma ||
+        o.ml_l1 > (1 << 24))
+      return RR_ERR_INVALID_ARG;
+    // X1 V partials and X2^T s stage l1 x m values in shared memory
+    if (basis_less(*A, o) &&
+        (size_t)o.ml_l1 * pad_mp(o.max_rhs) * (uses_f64(o) ? 8 : 4) > 200 * 1024)
+      return RR_ERR_UNSUPPORTED;
+  }
   switch (A->kind) {
     case RR_OP_DENSE:
       if (!A->dense || A->ld < A->n || (A->dtype != 0 && A->dtype != 1)) return RR_ERR_INVALID_ARG;
@@ -233,6 +254,10 @@ struct rr_handle {
   double* S;          // S = Theta Y_mu (l_sk x k) and a second l_sk x k buffer
   double* S2;
   int lsk;
+  int ml_l1, ml_g;    // multi-level embedding: rows of X1, nonzeros per column
+  double* ml_x2t;     // X2^T (l1 x k)
+  double* ml_x2;      // X2 (k x l1), basis-less form only
+  double* ml_tmp;     // l1 x mp, basis-less form only
   bool implicit;      // basis-less: Q applied through A_mu, Omega and R^-1
   int fusedG;         // CTAs of the persistent fused step (0: separate kernels)
   GridBar* bar;
@@ -341,6 +366,10 @@ void carve(rr_handle* h) {
   h->stage[0] = stg;
   h->stage[1] = stg + vec;
   h->tpart = (double*)at(R_TPART);
+  double* ml = (double*)at(R_ML);
+  h->ml_x2t = ml;
+  h->ml_x2 = (ml && h->implicit) ? ml + (size_t)h->ml_l1 * h->k : nullptr;
+  h->ml_tmp = (ml && h->implicit) ? h->ml_x2 + (size_t)h->ml_l1 * h->k : nullptr;
   double* tv = (double*)at(R_TVEC);
   for (int i = 0; i < 3; ++i) h->t[i] = tv + (size_t)i * h->k * h->mp;
   h->rpart = (double*)at(R_RPART);
@@ -693,6 +722,17 @@ rr_status power_iterations(rr_handle* h) {
 // g = Omega^T V  (k x mp, float64)
 template <typename T>
 void omega_t(rr_handle* h, const T* V, double* out, bool gated) {
+  if (h->sketch == RR_SKETCH_MULTILEVEL) {
+    // Omega^T V = X2 (X1 V): the sparse X1 gathers V into l1 bins, then the
+    // dense k x l1 X2
+    const int ns = ml_nslab(h->n);
+    omega_t_partial<T>(V, h->n, h->ml_l1, h->mp, h->ss_cols, h->ss_sgn, h->ml_g, ns,
+                       ml_rows_per_slab(h->n), h->tpart, gated ? h->cs : nullptr, h->st);
+    if (gated) reduce_slabs_gated(h->tpart, ns, h->ml_l1 * h->mp, h->ml_tmp, h->cs, h->mp, h->st);
+    else reduce_slabs(h->tpart, ns, h->ml_l1 * h->mp, h->ml_tmp, h->st);
+    rowmajor_gemv(h->ml_x2, h->k, h->ml_l1, h->ml_tmp, h->mp, out, gated ? h->cs : nullptr, h->st);
+    return;
+  }
   const int nslab = qt_nslab(h->n);
   if (h->sketch == RR_SKETCH_SPARSE_SIGN)
     omega_t_partial<T>(V, h->n, h->k, h->mp, h->ss_cols, h->ss_sgn, h->o.gamma, nslab,
@@ -708,6 +748,13 @@ void omega_t(rr_handle* h, const T* V, double* out, bool gated) {
 // U = Omega s
 template <typename T>
 void omega_mul(rr_handle* h, const double* s, T* U, bool gated) {
+  if (h->sketch == RR_SKETCH_MULTILEVEL) {
+    // Omega s = X1^T (X2^T s)
+    rowmajor_gemv(h->ml_x2t, h->ml_l1, h->k, s, h->mp, h->ml_tmp, gated ? h->cs : nullptr, h->st);
+    omega_expand<T>(h->ml_tmp, h->n, h->ml_l1, h->mp, h->ss_cols, h->ss_sgn, h->ml_g, U,
+                    gated ? h->cs : nullptr, h->st);
+    return;
+  }
   if (h->sketch == RR_SKETCH_SPARSE_SIGN)
     omega_expand<T>(s, h->n, h->k, h->mp, h->ss_cols, h->ss_sgn, h->o.gamma, U,
                     gated ? h->cs : nullptr, h->st);
@@ -976,6 +1023,12 @@ rr_status build_impl(rr_handle* h) {
     gen_gaussian_omega<T>((T*)h->Om, h->Omb, ldo, n, k, h->seed, mixed, st);
   } else if (h->sketch == RR_SKETCH_SRHT) {
     gen_srht_omega<T>((T*)h->Om, h->Omb, ldo, n, k, h->seed, mixed, h->ss_cols, h->ss_sgn, st);
+  } else if (h->sketch == RR_SKETCH_MULTILEVEL) {
+    // the basis-less form applies Omega as its two factors in every
+    // iteration, so the build must see that same Omega: no bf16 rounding there
+    // (the bf16 copy only feeds the tensor-core kernel sketch)
+    gen_multilevel_omega<T>((T*)h->Om, h->Omb, ldo, n, k, h->ml_l1, h->ml_g, h->seed,
+                            mixed && !h->implicit, h->ss_cols, h->ss_sgn, h->ml_x2t, h->ml_x2, st);
   } else {
     gen_sparse_sign(h->ss_cols, h->ss_sgn, n, k, h->o.gamma, h->seed, 2u, st);
     sparse_to_dense_omega<T>((T*)h->Om, h->ss_cols, h->ss_sgn, n, k, h->o.gamma, st);
@@ -1501,6 +1554,14 @@ void rr_build_opts_default(rr_build_opts* o) {
   o->keep_sketch = 0;
 }
 
+void rr_multilevel_defaults(int64_t n, int32_t k, rr_build_opts* o) {
+  if (!o || n < 1 || k < 1) return;
+  int g = (int)std::ceil(std::log((double)n));
+  g = std::min(std::max(g, 1), kMaxGammaHost);
+  o->ml_gamma = g;
+  o->ml_l1 = (int32_t)std::min<int64_t>((int64_t)g * k, INT32_MAX);
+}
+
 const char* randrand_status_str(rr_status s) {
   switch (s) {
     case RR_OK: return "ok";
@@ -1538,8 +1599,11 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
   RR_TRY(validate(A, k, o));
   // variants C and R need A_mu SPD (mu >= 0); G also takes an indefinite A_mu
   if (!std::isfinite(mu) || (o.variant != RR_VARIANT_G && !(mu >= 0.0))) return RR_ERR_INVALID_ARG;
-  if (sketch != RR_SKETCH_GAUSSIAN && sketch != RR_SKETCH_SPARSE_SIGN && sketch != RR_SKETCH_SRHT)
+  if (sketch != RR_SKETCH_GAUSSIAN && sketch != RR_SKETCH_SPARSE_SIGN &&
+      sketch != RR_SKETCH_SRHT && sketch != RR_SKETCH_MULTILEVEL)
     return RR_ERR_INVALID_ARG;
+  // the multi-level factors need their workspace (opts.ml_gamma > 0)
+  if (sketch == RR_SKETCH_MULTILEVEL && !ml_reserved(o)) return RR_ERR_INVALID_ARG;
   if (sketch == RR_SKETCH_SPARSE_SIGN && o.gamma > k) return RR_ERR_INVALID_ARG;
   if (!workspace || ((uintptr_t)workspace & 255)) return RR_ERR_INVALID_ARG;
   const Layout L = make_layout(*A, k, o);
@@ -1572,6 +1636,8 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
   h->ws = (unsigned char*)workspace;
   h->gsplit = gram_nsplit(A->n, k, k);
   h->lsk = uses_alg3(o) ? sketch_rows(k, o) : 0;
+  h->ml_l1 = ml_reserved(o) ? o.ml_l1 : 0;
+  h->ml_g = ml_reserved(o) ? o.ml_gamma : 0;
   h->implicit = basis_less(*A, o);
   h->fusedG = 0;
   h->graph_failed = false;

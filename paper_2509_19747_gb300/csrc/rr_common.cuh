@@ -132,6 +132,17 @@ void set_omega(const T* src, T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_
                bool round_bf16, cudaStream_t st);
 void gen_sparse_sign(int32_t* cols, int8_t* sgn, int64_t nlines, int ncols, int gamma,
                      uint64_t seed, uint32_t stream_id, cudaStream_t st);
+// multi-level Omega = X1^T X2^T (Sec. 2 eq:multilevelose): draws the pattern
+// of X1 into cols/sgn (n x gamma1), X2^T (l1 x k, float64) into X2T and, when
+// X2 is given, X2 (k x l1) as well, then Omega row by row
+template <typename T>
+void gen_multilevel_omega(T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, int k, int l1,
+                          int gamma1, uint64_t seed, bool round_bf16, int32_t* cols, int8_t* sgn,
+                          double* X2T, double* X2, cudaStream_t st);
+// y = M x for a row-major rows x cols float64 matrix M and x of mp columns
+// (row-major cols x mp); skipped once no column is active when cs is given
+void rowmajor_gemv(const double* M, int rows, int cols, const double* x, int mp, double* y,
+                   const ColState* cs, cudaStream_t st);
 template <typename T>
 void sparse_to_dense_omega(T* Om, const int32_t* cols, const int8_t* sgn, int64_t n, int k,
                            int gamma, cudaStream_t st);

@@ -123,6 +123,36 @@ def test_build_rejects_bad_arguments_before_any_launch(lib):
     assert e.value.status == lib.RR_ERR_INVALID_ARG
 
 
+def test_multilevel_options_on_the_host(lib):
+    """rr_multilevel_defaults gives the paper's sparse + Gaussian sizes (the
+    same reading as the oracle); the factors enlarge the workspace; a
+    multi-level build without them, or with sizes out of range, is rejected
+    before any launch."""
+    from oracle import philox
+    op = lib.rr_operator(kind=lib.RR_OP_GAUSS_KERNEL, dtype=1, n=20000, points=0x1000, dim=8,
+                         bandwidth=1.0)
+    o = lib.rr_build_opts_default()
+    o.precision = lib.RR_PREC_MIXED
+    assert (o.ml_l1, o.ml_gamma) == (0, 0)
+    base = lib.randrand_workspace_bytes(op, 500, o)
+    for n, k in ((20000, 500), (3001, 80), (262144, 256), (2, 1), (10 ** 9, 100)):
+        lib.set_multilevel(o, "multilevel", n, k)
+        assert (o.ml_l1, o.ml_gamma) == philox.multilevel_defaults(n, k)
+    lib.set_multilevel(o, "multilevel", 20000, 500)
+    assert lib.randrand_workspace_bytes(op, 500, o) >= base + 5000 * 500 * 8
+    plain = lib.rr_build_opts_default()
+    dense = lib.rr_operator(kind=lib.RR_OP_DENSE, dtype=0, n=100, dense=0x1000, ld=100)
+    with pytest.raises(lib.RandRandError) as e:      # nothing reserved for the factors
+        lib.randrand_build(dense, 0.0, 10, lib.RR_SKETCH_MULTILEVEL, 1, plain, 0x100000, 1 << 30, 0)
+    assert e.value.status == lib.RR_ERR_INVALID_ARG
+    for l1, g in ((5, 2), (100, 0), (100, 17), (8, 9)):   # l1 < k, gamma1 outside 1..16 or > l1
+        bad = lib.rr_build_opts_default()
+        bad.ml_l1, bad.ml_gamma = l1, g
+        with pytest.raises(lib.RandRandError) as e:
+            lib.randrand_workspace_bytes(dense, 8 if l1 == 8 else 10, bad)
+        assert e.value.status == lib.RR_ERR_INVALID_ARG
+
+
 def test_oracle_not_imported_by_product():
     # the product path never imports the oracle
     for dirpath, _, files in os.walk(os.path.join(ROOT, "paper_2509_19747_gb300")):
