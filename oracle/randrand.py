@@ -34,6 +34,9 @@ arXiv 2509.19747):
   |Pi~ A_mu| (eq:g_randrand_tau, the Sec. 6.3 estimates), and restarted
   preconditioned MINRES (Paige and Saunders), also for indefinite A_mu
   (mu < 0);
+* the refined projector of eq:accurate_proj: Pi ~ Q T Q^T with the Neumann
+  T = 2 I - Q^T Q, and Pi A_mu^-1 Pi ~ Q T G T Q^T (the symmetric reading of
+  the re-orthogonalized C-RandRAND, eq:c_randrand_reorth);
 * several shifts from one sketch (Sec. 5.1): A Omega computed once, Y_mu =
   A Omega + mu Omega per shift, and the Gram separation (A Omega + mu
   Omega)^T (A Omega + mu Omega) = Omega^T A^T A Omega + 2 mu Omega^T A Omega
@@ -201,6 +204,7 @@ class Build:
     tau: float
     rho: float
     jitter: float = 0.0
+    Tref: np.ndarray | None = None   # refined projector, eq:accurate_proj (refine=True)
 
     # --- projector and preconditioner applications (Sec. 4.1 eq:projector)
     def Pi(self, V):
@@ -211,8 +215,13 @@ class Build:
         return self.Omega @ solve_upper(self.R, self.Q.T @ V)
 
     def apply_P(self, V):
-        """C-RandRAND: P V = V - Q Q^T V + tau Q G Q^T V (eq:g_randrand_explicit)."""
+        """C-RandRAND: P V = V - Q Q^T V + tau Q G Q^T V (eq:g_randrand_explicit).
+        With the refined projector (eq:accurate_proj) Pi is replaced by
+        Q T Q^T and Pi A_mu^-1 Pi by Q T G T Q^T, T = 2 I - Q^T Q."""
         t = self.Q.T @ V
+        if self.Tref is not None:
+            Tt = self.Tref @ t
+            return V - self.Q @ Tt + self.tau * (self.Q @ (self.Tref @ (self.G @ Tt)))
         return V - self.Q @ t + self.tau * (self.Q @ (self.G @ t))
 
     def apply_B(self, V):
@@ -297,10 +306,12 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
           gamma: int = 8, l_sk: int | None = None, gamma_sk: int = 8,
           power_iters: int = 20, rho: float | None = None,
           tau: float | None = None, q: int = 0,
-          a_omega: np.ndarray | None = None, ml_l1: int = 0, ml_gamma: int = 0) -> Build:
+          a_omega: np.ndarray | None = None, ml_l1: int = 0, ml_gamma: int = 0,
+          refine: bool = False) -> Build:
     """a_omega: A Omega computed once for several shifts (Sec. 5.1): then
     omega must be the Omega it was computed from, and Y_mu = a_omega + mu
-    Omega replaces the product."""
+    Omega replaces the product.  refine: the preconditioner applies the
+    Neumann-refined projector of eq:accurate_proj (variants C and G)."""
     n = op.n
     if not (1 <= k <= n):
         raise ValueError("need 1 <= k <= n")
@@ -392,13 +403,25 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
         b.rho = float(rho) if (rho is not None and rho > 0) else 0.5
         b.tau = math.sqrt(b.rho) * b.normE / b.lam_max if tau is None else float(tau)
     elif variant == VARIANT_R:
+        if refine:
+            raise ValueError("the refined projector is applied to variants C and G")
         b.rho = 1.0
         b.tau = nE if tau is None else float(tau)        # Alg. 4 step 2
         if b.tau <= 0.0:                                  # mu = 0 and k = n
             b.tau = 1.0
     else:
         raise ValueError(variant)
+    if refine:
+        b.Tref = neumann_T(b.Q)
     return b
+
+
+def neumann_T(Q: np.ndarray) -> np.ndarray:
+    """T = 2 I - Q^T Q, the Neumann approximation of (Q^T Q)^-1 for a nearly
+    orthonormal Q (Sec. 4.3 eq:accurate_proj): Q T Q^T u approximates the
+    orthogonal projection Q (Q^T Q)^-1 Q^T u to second order in
+    |I - Q^T Q|."""
+    return 2.0 * np.eye(Q.shape[1]) - Q.T @ Q
 
 
 # ==========================================================================

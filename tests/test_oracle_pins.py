@@ -610,6 +610,93 @@ def test_multilevel_full_sketch_converges_in_one_iteration():
     assert O.true_rel_residual(op, 1e-2, x, b)[0] < 1e-9
 
 
+# ------------------------------------------ refined projector (Sec. 4.3 eq:accurate_proj)
+def _perturbed_basis(n, k, eps, seed):
+    rng = np.random.default_rng(seed)
+    Q0, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    F = rng.standard_normal((k, k))
+    return Q0 @ (np.eye(k) + eps * F)        # a basis of range(Q0), |I - Q^T Q| ~ eps
+
+
+def test_neumann_projector_error_is_second_order():
+    """For a nearly orthonormal Q, Q Q^T is off the orthogonal projector onto
+    range(Q) by O(|I - Q^T Q|) and Q T Q^T by O(|I - Q^T Q|^2) (the claim after
+    eq:accurate_proj).  The exact projector comes from a Householder QR."""
+    n, k = 300, 20
+    errs = {}
+    for eps in (1e-3, 1e-4):
+        Q = _perturbed_basis(n, k, eps, seed=61)
+        U, _ = np.linalg.qr(Q)
+        Pex = U @ U.T
+        plain = np.linalg.norm(Q @ Q.T - Pex, 2)
+        refined = np.linalg.norm(Q @ O.neumann_T(Q) @ Q.T - Pex, 2)
+        errs[eps] = (plain, refined)
+        d = np.linalg.norm(np.eye(k) - Q.T @ Q, 2)
+        assert 0.3 * d <= plain <= 1.5 * d
+        assert refined <= 2.0 * d * d
+    # first order vs second order in eps
+    assert 5 < errs[1e-3][0] / errs[1e-4][0] < 20
+    assert 50 < errs[1e-3][1] / errs[1e-4][1] < 200
+
+
+def test_neumann_T_is_two_refinement_steps():
+    """eq:accurate_proj_2: v_1 = Q^T u, v_(i+1) = v_i + Q^T (u - Q v_i).  Two
+    steps give T Q^T u exactly; many steps reach the least-squares solution
+    Q^+ u of the library solver."""
+    Q = _perturbed_basis(200, 12, 1e-2, seed=62)
+    u = np.random.default_rng(63).standard_normal(200)
+    v = Q.T @ u
+    v2 = v + Q.T @ (u - Q @ v)
+    assert np.allclose(v2, O.neumann_T(Q) @ (Q.T @ u), rtol=0, atol=1e-13)
+    for _ in range(60):
+        v = v + Q.T @ (u - Q @ v)
+    assert np.allclose(v, np.linalg.lstsq(Q, u, rcond=None)[0], rtol=0, atol=1e-12)
+
+
+def test_refined_build_equals_plain_for_orthonormal_basis_and_solves():
+    """With the Householder basis (orthonormal to rounding) T = I to rounding:
+    the refined preconditioner equals the plain one, and the solve is exact."""
+    P, op = small_dense(n=200)
+    mu, k = 1e-4, 24
+    plain = O.build(op, mu, k, "gaussian", seed=64)
+    ref = O.build(op, mu, k, "gaussian", seed=64, refine=True)
+    assert np.linalg.norm(ref.Tref - np.eye(k)) <= 1e-13
+    V = np.random.default_rng(65).standard_normal((200, 3))
+    assert np.allclose(ref.apply_P(V), plain.apply_P(V), rtol=0, atol=1e-10 * np.abs(plain.apply_P(V)).max())
+    b = W.gaussian_rhs(200, 1, 64)
+    x, info = O.solve(ref, b, rtol=1e-12)
+    assert np.linalg.norm(x - O.exact_solve(op, mu, b)) <= 1e-8 * np.linalg.norm(x)
+    with pytest.raises(ValueError):
+        O.build(op, mu, k, "gaussian", seed=64, variant="R", refine=True)
+
+
+def test_refined_preconditioner_restores_the_spectrum():
+    """Exact eigenvector deflation with a non-orthonormal basis of the same
+    range: the plain P = I + Q (tau G - I) Q^T loses the closed-form spectrum
+    {tau (k times), lambda_i + mu (i > k)} of P A_mu at first order in
+    |I - Q^T Q|, the refined one at second order."""
+    P, op = small_dense(n=120)
+    mu, k = 1e-3, 10
+    good = O.build(op, mu, k, omega=P.U[:, :k])
+    expect = np.sort(np.concatenate([np.full(k, good.tau), P.lam[k:] + mu]))
+    Amu = P.A + mu * np.eye(op.n)
+    rng = np.random.default_rng(66)
+    Mp = np.eye(k) + 1e-4 * rng.standard_normal((k, k))
+    Qp = good.Q @ Mp
+    # the core matrix of that basis, G = Q^T A_mu^-1 Q (what the build forms
+    # from its own Q = A_mu Omega R^-1), here from the dense inverse
+    Gp = Qp.T @ np.linalg.solve(Amu, Qp)
+    dev_ = {}
+    for name, Tref in (("plain", None), ("refined", O.neumann_T(Qp))):
+        bd = O.Build(op=op, mu=mu, k=k, variant="C", Omega=good.Omega, Ymu=good.Ymu, Q=Qp,
+                     R=np.linalg.solve(Mp, good.R), G=Gp, normE=good.normE,
+                     lam_max=good.lam_max, tau=good.tau, rho=good.rho, Tref=Tref)
+        ev = np.sort(np.linalg.eigvals(bd.apply_P(np.eye(op.n)) @ Amu).real)
+        dev_[name] = np.max(np.abs(ev - expect) / expect)
+    assert dev_["plain"] > 1e-6
+    assert dev_["refined"] < 1e-2 * dev_["plain"]
+
+
 # ------------------------------------------ G-RandRAND and MINRES (Sec. 3.3, 6.3)
 def _indefinite(n=200, seed=86, after=20):
     P = W.dense_power_spectrum(n, seed=seed, power=2.0)
