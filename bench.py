@@ -73,6 +73,8 @@ def parse():
                     choices=["gaussian", "srht", "multilevel", "sparse_sign"],
                     help="test matrix (default: Gaussian for the kernel ridge workload, "
                          "sparse sign for the sparse diffusion workload)")
+    ap.add_argument("--refine", action="store_true",
+                    help="kernel ridge: refined projector (rr_build_opts.refine)")
     ap.add_argument("--kernel-impl", type=int, default=0,
                     help="kernel ridge: Gaussian-kernel product form (rr_build_opts.kernel_impl)")
     return ap.parse_args()
@@ -259,6 +261,7 @@ def run_ours(args):
     o.max_rhs = m
     o.profile = 1
     o.kernel_impl = args.kernel_impl
+    o.refine = 1 if args.refine else 0
     rr.set_multilevel(o, WORKLOAD["sketch"], n, k)
     ws_bytes = rr.randrand_workspace_bytes(op.c, k, o)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
@@ -337,6 +340,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {**{kk: WORKLOAD[kk] for kk in ("workload", "n", "d", "k", "nrhs", "mu", "rtol",
                                                   "precision", "variant", "sketch")},
+                   **({"refine": "eq:accurate_proj"} if args.refine else {}),
                    "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "solve": {"inner_iters_max": iters, "rel_residual_max": rel_res},

@@ -174,6 +174,13 @@ typedef struct {
                             workspace for the multi-level factors, and a
                             multi-level build then fails with
                             RR_ERR_INVALID_ARG */
+  int32_t refine;        /* 1: refined projector (Sec. 4.3 eq:accurate_proj):
+                            Pi ~ Q T Q^T and Pi A_mu^-1 Pi ~ Q T G T Q^T with
+                            the Neumann T = 2 I - Q^T Q of the stored basis,
+                            so P = I + Q (tau T G T - T) Q^T; one k x k Gram
+                            at build, no cost per iteration.  Variants C and
+                            G with an explicit basis (else
+                            RR_ERR_UNSUPPORTED).  0 (default): plain Q Q^T */
 } rr_build_opts;
 
 typedef struct {
@@ -324,8 +331,9 @@ rr_status randrand_profile(rr_handle* h, rr_profile* out);
 rr_status randrand_scalars(const rr_handle* h, double* tau, double* normE, double* lam_max);
 
 /*
- * Apply the preconditioner (variant C: z = P r, P = I + Q (tau G - I) Q^T,
- * the footnote form of Sec. 7.3) or the operator B of variant R
+ * Apply the preconditioner (variants C and G: z = P r, P = I + Q H Q^T with
+ * H = tau G - I, the footnote form of Sec. 7.3, or H = tau T G T - T with
+ * opts.refine) or the operator B of variant R
  * (z = (I-Pi) A_mu (I-Pi) r + tau Pi r, eq:APdef2) to m <= max_rhs columns.
  *   r, z  device, n x m float64 column-major with leading dimension ld.
  * Enqueued on the handle stream; does not synchronise.

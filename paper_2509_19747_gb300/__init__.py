@@ -60,7 +60,7 @@ class rr_build_opts(ctypes.Structure):
         ("rho", ctypes.c_double),
         ("restart_eta", ctypes.c_double),
         ("keep_sketch", ctypes.c_int32),
-        ("ml_l1", ctypes.c_int32), ("ml_gamma", ctypes.c_int32),
+        ("ml_l1", ctypes.c_int32), ("ml_gamma", ctypes.c_int32), ("refine", ctypes.c_int32),
     ]
 
 
@@ -363,7 +363,8 @@ class Handle:
                  power_iters: int = 20, rho: float = 0.0, restart_eta: float = 1e-2,
                  gamma: int = 8, profile: bool = False, kernel_impl: int = 0, stream=None,
                  orth: str = "cholqr2", l_sk: int = 0, gamma_sk: int = 8, iter_impl: int = 0,
-                 q: int = 0, keep_sketch: bool = False, ml_l1: int = 0, ml_gamma: int = 0):
+                 q: int = 0, keep_sketch: bool = False, ml_l1: int = 0, ml_gamma: int = 0,
+                 refine: bool = False):
         """sketch "multilevel": ml_l1 / ml_gamma give X1's rows and nonzeros per
         column; 0 takes rr_multilevel_defaults."""
         import torch
@@ -386,6 +387,7 @@ class Handle:
         o.iter_impl = iter_impl
         o.q = q
         o.keep_sketch = 1 if keep_sketch else 0
+        o.refine = 1 if refine else 0
         set_multilevel(o, sketch, op.n, k, ml_l1, ml_gamma)
         self.opts = o
         self.ws_bytes = randrand_workspace_bytes(op.c, k, o)

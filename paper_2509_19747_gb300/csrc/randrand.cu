@@ -168,6 +168,9 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
     return RR_ERR_UNSUPPORTED;
   if (o.q < 0 || o.q > 4) return RR_ERR_INVALID_ARG;
   if (!(o.restart_eta > 0.0 && o.restart_eta < 1.0)) return RR_ERR_INVALID_ARG;
+  if (o.refine != 0 && o.refine != 1) return RR_ERR_INVALID_ARG;
+  // the refined projector needs the stored basis (its Gram) and the H form
+  if (o.refine && (o.variant == RR_VARIANT_R || basis_less(*A, o))) return RR_ERR_UNSUPPORTED;
   if (o.ml_gamma != 0 || o.ml_l1 != 0) {
     if (o.ml_gamma < 1 || o.ml_gamma > kMaxGammaHost || o.ml_l1 < k || o.ml_l1 < o.ml_gamma ||
         o.ml_l1 > (1 << 24))
@@ -1104,7 +1107,20 @@ rr_status finish_build(rr_handle* h, const double* G1given) {
   } else if (h->o.variant == RR_VARIANT_C || h->o.variant == RR_VARIANT_G) {
     // P = I + Q (tau G - I) Q^T = I + Q H Q^T (C; for G, (I - Pi) + tau Q G Q^T
     // is the same expression)
-    form_H(h->kk[kG], h->tau, h->kk[kH], k, st);
+    if (h->o.refine) {
+      // Sec. 4.3 eq:accurate_proj: Pi ~ Q T Q^T, Pi A_mu^-1 Pi ~ Q T G T Q^T with
+      // T = 2 I - Q^T Q of the stored basis, so H = tau T G T - T
+      gram<T>(h, (const T*)h->Q, h->kk[kScA]);
+      kxk_scale_add_identity(h->kk[kScA], -1.0, 2.0, h->kk[kScB], k, st);
+      gemm_nn<double>(k, k, k, 1.0, h->kk[kScB], k, h->kk[kG], k, 0.0, nullptr, 0, h->kk[kTm], k,
+                      st);
+      gemm_nn<double>(k, k, k, h->tau, h->kk[kTm], k, h->kk[kScB], k, 0.0, nullptr, 0,
+                      h->kk[kH], k, st);
+      axpby<double, double, double>(h->kk[kH], coefs_all(1.0), h->kk[kScB], coefs_all(-1.0),
+                                    h->kk[kH], (int64_t)k * k, 1, st);
+    } else {
+      form_H(h->kk[kG], h->tau, h->kk[kH], k, st);
+    }
     h->fusedG = (h->o.iter_impl == 0 && h->o.variant == RR_VARIANT_C)
                     ? pcg_tail_ctas<T>(n, k, h->mp) : 0;
     // keep QH = Q H so that z = r + QH (Q^T r)

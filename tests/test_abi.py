@@ -153,6 +153,22 @@ def test_multilevel_options_on_the_host(lib):
         assert e.value.status == lib.RR_ERR_INVALID_ARG
 
 
+def test_refine_option_checks(lib):
+    dense = lib.rr_operator(kind=lib.RR_OP_DENSE, dtype=0, n=100, dense=0x1000, ld=100)
+    o = lib.rr_build_opts_default()
+    assert o.refine == 0
+    o.refine = 1
+    assert lib.randrand_workspace_bytes(dense, 10, o) > 0
+    o.refine = 2
+    with pytest.raises(lib.RandRandError) as e:
+        lib.randrand_workspace_bytes(dense, 10, o)
+    assert e.value.status == lib.RR_ERR_INVALID_ARG
+    o.refine, o.variant = 1, lib.RR_VARIANT_R
+    with pytest.raises(lib.RandRandError) as e:
+        lib.randrand_workspace_bytes(dense, 10, o)
+    assert e.value.status == lib.RR_ERR_UNSUPPORTED
+
+
 def test_oracle_not_imported_by_product():
     # the product path never imports the oracle
     for dirpath, _, files in os.walk(os.path.join(ROOT, "paper_2509_19747_gb300")):
