@@ -30,7 +30,7 @@ constexpr int kMaxRestarts = 400;
 enum Region {
   R_OM, R_OMB, R_SSC, R_SSS, R_THC, R_THS, R_SK, R_Y, R_Q, R_Y0, R_KK, R_KKT, R_GPART, R_CHOLW,
   R_STATUS, R_XS, R_CN, R_PN, R_AUG, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT,
-  R_CS, R_NORMS, R_FUSED, R_ML, R_NREG
+  R_CS, R_NORMS, R_FUSED, R_ML, R_FWHT, R_NREG
 };
 
 struct Layout {
@@ -84,6 +84,13 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   const bool ml_bl = ml_reserved(o) && basis_less(A, o);
   const size_t l1 = ml_reserved(o) ? (size_t)o.ml_l1 : 0;
   L.size[R_ML] = ml_reserved(o) ? (l1 * kk + (ml_bl ? kk * l1 + l1 * (size_t)mp : 0)) * 8 : 0;
+  // basis-less form: the SRHT applied by fast Walsh-Hadamard transforms needs
+  // the inverse row map (s int32) and an s x mp pass buffer
+  {
+    int64_t sp = 1;
+    while (sp < A.n) sp <<= 1;
+    L.size[R_FWHT] = basis_less(A, o) ? align256((size_t)sp * 4) + (size_t)sp * mp * ts : 0;
+  }
   const size_t lsk = uses_alg3(o) ? (size_t)sketch_rows(k, o) : 0;
   L.size[R_THC] = uses_alg3(o) ? n * (size_t)o.gamma_sk * 4 : 0;
   L.size[R_THS] = uses_alg3(o) ? n * (size_t)o.gamma_sk : 0;
@@ -261,6 +268,10 @@ struct rr_handle {
   double* ml_x2t;     // X2^T (l1 x k)
   double* ml_x2;      // X2 (k x l1), basis-less form only
   double* ml_tmp;     // l1 x mp, basis-less form only
+  int32_t* srht_inv;  // SRHT, basis-less: inverse of the row selection (s entries)
+  void* fwht_buf;     // SRHT, basis-less: s x mp buffer between the two passes
+  int64_t srht_s;     // SRHT points s = 2^ceil(log2 n)
+  int fwht_B;         // rows per pass-A block; 0: Omega applied as a dense matrix
   bool implicit;      // basis-less: Q applied through A_mu, Omega and R^-1
   int fusedG;         // CTAs of the persistent fused step (0: separate kernels)
   GridBar* bar;
@@ -373,6 +384,13 @@ void carve(rr_handle* h) {
   h->ml_x2t = ml;
   h->ml_x2 = (ml && h->implicit) ? ml + (size_t)h->ml_l1 * h->k : nullptr;
   h->ml_tmp = (ml && h->implicit) ? h->ml_x2 + (size_t)h->ml_l1 * h->k : nullptr;
+  {
+    unsigned char* fw = (unsigned char*)at(R_FWHT);
+    h->srht_s = 1;
+    while (h->srht_s < h->n) h->srht_s <<= 1;
+    h->srht_inv = (int32_t*)fw;
+    h->fwht_buf = fw ? fw + align256((size_t)h->srht_s * 4) : nullptr;
+  }
   double* tv = (double*)at(R_TVEC);
   for (int i = 0; i < 3; ++i) h->t[i] = tv + (size_t)i * h->k * h->mp;
   h->rpart = (double*)at(R_RPART);
@@ -725,6 +743,12 @@ rr_status power_iterations(rr_handle* h) {
 // g = Omega^T V  (k x mp, float64)
 template <typename T>
 void omega_t(rr_handle* h, const T* V, double* out, bool gated) {
+  if (h->sketch == RR_SKETCH_SRHT && h->fwht_B > 0) {
+    // Omega^T V = k^-1/2 S H (D V) by fast Walsh-Hadamard transforms
+    srht_apply_t<T>(V, h->n, h->k, h->mp, h->ss_sgn, h->srht_inv, h->srht_s, h->fwht_B,
+                    (T*)h->fwht_buf, out, gated ? h->cs : nullptr, h->st);
+    return;
+  }
   if (h->sketch == RR_SKETCH_MULTILEVEL) {
     // Omega^T V = X2 (X1 V): the sparse X1 gathers V into l1 bins, then the
     // dense k x l1 X2
@@ -751,6 +775,12 @@ void omega_t(rr_handle* h, const T* V, double* out, bool gated) {
 // U = Omega s
 template <typename T>
 void omega_mul(rr_handle* h, const double* s, T* U, bool gated) {
+  if (h->sketch == RR_SKETCH_SRHT && h->fwht_B > 0) {
+    // Omega s = k^-1/2 D H (S^T s)
+    srht_apply<T>(s, h->n, h->k, h->mp, h->ss_sgn, h->srht_inv, h->srht_s, h->fwht_B,
+                  (T*)h->fwht_buf, U, gated ? h->cs : nullptr, h->st);
+    return;
+  }
   if (h->sketch == RR_SKETCH_MULTILEVEL) {
     // Omega s = X1^T (X2^T s)
     rowmajor_gemv(h->ml_x2t, h->ml_l1, h->k, s, h->mp, h->ml_tmp, gated ? h->cs : nullptr, h->st);
@@ -1025,7 +1055,12 @@ rr_status build_impl(rr_handle* h) {
   if (h->sketch == RR_SKETCH_GAUSSIAN) {
     gen_gaussian_omega<T>((T*)h->Om, h->Omb, ldo, n, k, h->seed, mixed, st);
   } else if (h->sketch == RR_SKETCH_SRHT) {
-    gen_srht_omega<T>((T*)h->Om, h->Omb, ldo, n, k, h->seed, mixed, h->ss_cols, h->ss_sgn, st);
+    // basis-less: the iterations apply Omega by fast Walsh-Hadamard
+    // transforms, so the build uses that same (unrounded) Omega
+    gen_srht_omega<T>((T*)h->Om, h->Omb, ldo, n, k, h->seed, mixed && !h->implicit, h->ss_cols,
+                      h->ss_sgn, st);
+    h->fwht_B = h->implicit ? srht_fwht_block(h->srht_s, h->mp, sizeof(T)) : 0;
+    if (h->fwht_B > 0) srht_inverse_map(h->ss_cols, k, h->srht_s, h->srht_inv, st);
   } else if (h->sketch == RR_SKETCH_MULTILEVEL) {
     // the basis-less form applies Omega as its two factors in every
     // iteration, so the build must see that same Omega: no bf16 rounding there
@@ -1652,6 +1687,7 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
   h->ws = (unsigned char*)workspace;
   h->gsplit = gram_nsplit(A->n, k, k);
   h->lsk = uses_alg3(o) ? sketch_rows(k, o) : 0;
+  h->fwht_B = 0;
   h->ml_l1 = ml_reserved(o) ? o.ml_l1 : 0;
   h->ml_g = ml_reserved(o) ? o.ml_gamma : 0;
   h->implicit = basis_less(*A, o);

@@ -139,6 +139,19 @@ template <typename T>
 void gen_multilevel_omega(T* Om, __nv_bfloat16* OmT_bf16, int64_t ldo, int64_t n, int k, int l1,
                           int gamma1, uint64_t seed, bool round_bf16, int32_t* cols, int8_t* sgn,
                           double* X2T, double* X2, cudaStream_t st);
+// k_fwht.cu: the SRHT test matrix applied by fast Walsh-Hadamard transforms
+// (basis-less form).  srht_fwht_block: rows per shared-memory block for s
+// points and mp columns of elem bytes, 0 when two passes do not cover s.
+int srht_fwht_block(int64_t s, int mp, size_t elem);
+void srht_inverse_map(const int32_t* rows, int k, int64_t s, int32_t* inv, cudaStream_t st);
+// out = Omega^T V (k x mp, float64); F: s x mp scratch
+template <typename T>
+void srht_apply_t(const T* V, int64_t n, int k, int mp, const int8_t* sgn, const int32_t* inv,
+                  int64_t s, int B, T* F, double* out, const ColState* cs, cudaStream_t st);
+// U = Omega t (n x mp) for t (k x mp, float64)
+template <typename T>
+void srht_apply(const double* t, int64_t n, int k, int mp, const int8_t* sgn, const int32_t* inv,
+                int64_t s, int B, T* F, T* U, const ColState* cs, cudaStream_t st);
 // y = M x for a row-major rows x cols float64 matrix M and x of mp columns
 // (row-major cols x mp); skipped once no column is active when cs is given
 void rowmajor_gemv(const double* M, int rows, int cols, const double* x, int mp, double* y,

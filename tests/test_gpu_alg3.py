@@ -41,7 +41,7 @@ def csr_handle(rr, C, vals, mu, k, sketch, seed, **kw):
 
 
 # ------------------------------------------------------------ Alg. 3 factors
-@pytest.mark.parametrize("sketch", ["sparse_sign", "gaussian", "multilevel"])
+@pytest.mark.parametrize("sketch", ["sparse_sign", "gaussian", "multilevel", "srht"])
 @pytest.mark.parametrize("side,k,l_sk", [(24, 40, 0), (30, 17, 50)])
 def test_alg3_basis_less_factors_fp64(cuda_lib, sketch, side, k, l_sk):
     """Basis-less build on a CSR operator: R, G, tau and the power-iteration
@@ -83,7 +83,7 @@ def test_alg3_explicit_basis_dense_fp64(cuda_lib):
 
 
 # ------------------------------------------------------- preconditioner apply
-@pytest.mark.parametrize("sketch", ["sparse_sign", "gaussian", "multilevel"])
+@pytest.mark.parametrize("sketch", ["sparse_sign", "gaussian", "multilevel", "srht"])
 def test_basis_less_apply_fp64(cuda_lib, sketch):
     """z = P r with Q applied through A_mu, Omega and R^-1 equals the oracle's
     P r = r - Q Q^T r + tau Q G Q^T r with its explicit Q."""
@@ -99,7 +99,7 @@ def test_basis_less_apply_fp64(cuda_lib, sketch):
 
 
 # ---------------------------------------------------------------- solves
-@pytest.mark.parametrize("sketch", ["sparse_sign", "gaussian", "multilevel"])
+@pytest.mark.parametrize("sketch", ["sparse_sign", "gaussian", "multilevel", "srht"])
 @pytest.mark.parametrize("m", [1, 3])
 def test_basis_less_iteration_level_fp64(cuda_lib, sketch, m):
     """After a fixed inner budget the GPU iterate equals the oracle iterate."""

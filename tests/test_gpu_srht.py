@@ -1,7 +1,9 @@
 """GPU parity of the SRHT test matrix (Sec. 2, fast randomized transforms):
 Omega bit for bit against the oracle's draw (same Philox streams, same keyed
-Feistel subsampling), float64 factors against the oracle build, and a mixed
-precision kernel solve judged by the float64 residual."""
+Feistel subsampling), float64 factors against the oracle build, a mixed
+precision kernel solve judged by the float64 residual, and the basis-less CSR
+form, which applies Omega and Omega^T by fast Walsh-Hadamard transforms (one
+shared-memory pass, or two when s exceeds the block)."""
 import numpy as np
 import pytest
 
@@ -70,5 +72,34 @@ def test_srht_kernel_mixed_solve(cuda_lib):
     h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "srht", seed=98, precision="mixed",
                   max_rhs=4)
     x, status, infos = h.solve(dev(B), rtol=1e-6)
+    assert status == rr.RR_OK
+    assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), B) <= 1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_srht_basis_less_fwht(cuda_lib, precision):
+    """n = 9216 (s = 16384: two transform passes, zero padding): the float64
+    preconditioner apply and fixed-budget iterates equal the oracle's (which
+    applies the dense Omega); the mixed solve meets rtol by the float64
+    residual."""
+    rr = cuda_lib
+    C = W.diffusion_csr(side=96, seed=99, corr_len=4.0)
+    op = O.CsrOp(C.rowptr, C.colidx, C.vals, C.n)
+    fp64 = precision == "fp64"
+    vals = dev(C.vals.astype(np.float64)) if fp64 else dev(C.vals)
+    mu, k = 1e-6, 48
+    h = rr.Handle(rr.Operator.csr(dev(C.rowptr), dev(C.colidx), vals), mu, k, "srht", seed=99,
+                  orth="rand_cholqr", precision=precision, max_rhs=2)
+    B = W.gaussian_rhs(C.n, 2, 99)
+    if fp64:
+        bd = O.build(op, mu, k, "srht", seed=99, orth="qless")
+        r = np.random.default_rng(5).standard_normal((C.n, 2))
+        cond = np.linalg.cond(bd.R)
+        assert rel(h.apply(dev(r)).cpu().numpy(), bd.apply_P(r)) <= max(1e-12, 1e-15 * cond ** 2) * 100
+        x, status, infos = h.solve(dev(B), rtol=1e-14, maxit=6)
+        xo, oinfo = O.solve(bd, B, rtol=1e-14, maxit=6)
+        assert [i["inner_iters"] for i in infos] == [i.inner_iters for i in oinfo]
+        assert rel(x.cpu().numpy(), xo) <= 1e-9
+    x, status, infos = h.solve(dev(B), rtol=1e-6, maxit=20000)
     assert status == rr.RR_OK
     assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), B) <= 1e-6)
