@@ -732,6 +732,48 @@ void kxk_frob_minus_identity(const double* A, double c, int k, double* out, cuda
   k_frob_minus_identity<<<1, 1024, 0, st>>>(A, c, k, out);
 }
 
+// First-order Cholesky factor of a Gram G = I + E that is the identity up to
+// a small E (the last CholeskyQR pass): G = R^T R with R = I + Phi(E) +
+// O(|E|^2) and R^-1 = I - Phi(E) + O(|E|^2), Phi(E) the strict upper part of
+// E plus half its diagonal (from (I + U)^T (I + U) = I + U + U^T + U^T U).
+// Reads the upper triangle of G; out[0] = |E|_F, accumulated in float (a
+// size test only).  One block, fixed order.
+__global__ void k_chol_near_identity(const double* __restrict__ G, int k, double* __restrict__ R,
+                                     double* __restrict__ Rinv, double* __restrict__ out) {
+  __shared__ float red[32];
+  float s = 0.f;
+  const int64_t total = (int64_t)k * k;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e % k);
+    double r = 0.0, ri = 0.0;
+    if (j > i) {
+      const double v = G[e];
+      r = v;
+      ri = -v;
+      s += 2.f * (float)v * (float)v;
+    } else if (j == i) {
+      const double d = G[e] - 1.0;
+      r = 1.0 + 0.5 * d;
+      ri = 1.0 - 0.5 * d;
+      s += (float)d * (float)d;
+    }
+    R[e] = r;
+    Rinv[e] = ri;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[0] = sqrt((double)t);
+  }
+}
+void chol_near_identity(const double* G, int k, double* R, double* Rinv, double* nrm,
+                        cudaStream_t st) {
+  k_chol_near_identity<<<1, 1024, 0, st>>>(G, k, R, Rinv, nrm);
+}
+
 template <typename Tin, typename Tout>
 __global__ void k_convert(const Tin* __restrict__ in, Tout* __restrict__ out, int64_t count) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -551,11 +551,24 @@ rr_status orthogonalize(rr_handle* h, const double* G1given = nullptr) {
   }
   (void)shifted;
   for (int p = 0; p < passes; ++p) {
+    bool series = false;
     if (p > 0) {
       gram<T>(h, src, Rp);
-      RR_TRY(chol(h, Rp));
+      if (p == passes - 1) {
+        // the last pass factors a Gram I + E with E at rounding level: the
+        // first-order factor and inverse are exact to O(|E|^2), below the
+        // working precision once |E| <= sqrt(u) (1e-8 float64, 1e-4 float32)
+        chol_near_identity(Rp, k, h->kk[kScB], Rip, h->norms, h->st);
+        double e = 0.0;
+        RR_TRY(read_doubles(h, h->norms, 1, &e));
+        series = e <= (h->f64 ? 1e-8 : 1e-4);
+        if (series)
+          RR_CUDA_TRY(cudaMemcpyAsync(Rp, h->kk[kScB], (size_t)k * k * 8, cudaMemcpyDeviceToDevice,
+                                      h->st));
+      }
+      if (!series) RR_TRY(chol(h, Rp));
     }
-    trtri_upper_with(Rp, k, h->kk[kScB], Rip, h->st);
+    if (!series) trtri_upper_with(Rp, k, h->kk[kScB], Rip, h->st);
     right_mult<T>(h, src, Rip, dst);
     if (p == 0) {
       RR_CUDA_TRY(cudaMemcpyAsync(RinvAcc, Rip, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));

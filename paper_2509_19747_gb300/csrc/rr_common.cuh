@@ -192,6 +192,10 @@ void form_H(const double* G, double tau, double* H, int k, cudaStream_t st);
 void kxk_scale_add_identity(const double* A, double a, double b, double* out, int k,
                             cudaStream_t st);
 void kxk_frob_minus_identity(const double* A, double c, int k, double* out, cudaStream_t st);
+// first-order Cholesky factor (R) and inverse (Rinv) of a Gram G = I + E,
+// nrm[0] = |E|_F (device)
+void chol_near_identity(const double* G, int k, double* R, double* Rinv, double* nrm,
+                        cudaStream_t st);
 template <typename Tin, typename Tout>
 void convert(const Tin* in, Tout* out, int64_t count, cudaStream_t st);
 void transpose_kxk(const double* in, double* out, int k, cudaStream_t st);

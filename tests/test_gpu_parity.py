@@ -72,6 +72,26 @@ def test_sparse_sign_omega_bitwise(cuda_lib):
 
 
 # ------------------------------------------------------- build products
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+def test_float32_basis_orthonormal_and_factorizes(cuda_lib, precision):
+    """Float32 paths (the last Cholesky QR pass taken to first order in
+    |I - Q1^T Q1|): the stored basis is orthonormal to float32 rounding and
+    Q R reproduces Y_mu = A_mu Omega of the oracle (same Omega)."""
+    rr = cuda_lib
+    n, k, mu = 3001, 120, 1e-3
+    X = W.mixture_points(n, seed=121)
+    op = O.GaussKernelOp(X)
+    h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=121,
+                  precision=precision)
+    Q = h.export("Q").cpu().numpy().astype(np.float64)
+    R = h.export("R").cpu().numpy()
+    assert np.linalg.norm(Q.T @ Q - np.eye(k), 2) <= 2e-5
+    Om = h.export("omega").cpu().numpy().astype(np.float64)
+    Ymu = op.matmat(Om) + mu * Om
+    # the mixed path forms Y_mu on the tensor cores with bf16 operands
+    assert rel(Q @ R, Ymu) <= (1e-2 if precision == "mixed" else 1e-5)
+
+
 @pytest.mark.parametrize("n,k,variant", [(300, 30, "C"), (517, 37, "C"), (517, 37, "R"),
                                          (129, 1, "C"), (64, 64, "C")])
 def test_build_factors_fp64(cuda_lib, n, k, variant):
