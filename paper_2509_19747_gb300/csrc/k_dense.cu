@@ -736,14 +736,20 @@ void kxk_frob_minus_identity(const double* A, double c, int k, double* out, cuda
 // a small E (the last CholeskyQR pass): G = R^T R with R = I + Phi(E) +
 // O(|E|^2) and R^-1 = I - Phi(E) + O(|E|^2), Phi(E) the strict upper part of
 // E plus half its diagonal (from (I + U)^T (I + U) = I + U + U^T + U^T U).
-// Reads the upper triangle of G; out[0] = |E|_F, accumulated in float (a
-// size test only).  One block, fixed order.
-__global__ void k_chol_near_identity(const double* __restrict__ G, int k, double* __restrict__ R,
-                                     double* __restrict__ Rinv, double* __restrict__ out) {
-  __shared__ float red[32];
+// Reads the upper triangle of G.  out[0] = |E|_F (a size test only): block
+// partials in float, summed in fixed order by the last block.
+__global__ void __launch_bounds__(256) k_chol_near_identity(const double* __restrict__ G, int k,
+                                                            double* __restrict__ R,
+                                                            double* __restrict__ Rinv,
+                                                            double* __restrict__ part,
+                                                            unsigned* __restrict__ counter,
+                                                            double* __restrict__ out) {
+  __shared__ float red[8];
+  __shared__ bool s_last;
   float s = 0.f;
   const int64_t total = (int64_t)k * k;
-  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
     const int i = (int)(e / k), j = (int)(e % k);
     double r = 0.0, ri = 0.0;
     if (j > i) {
@@ -765,13 +771,26 @@ __global__ void k_chol_near_identity(const double* __restrict__ G, int k, double
   __syncthreads();
   if (threadIdx.x == 0) {
     float t = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    out[0] = sqrt((double)t);
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[blockIdx.x] = (double)t;
+    __threadfence();
+    s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    double t = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(part + b);
+    out[0] = sqrt(t);
+    *counter = 0u;
   }
 }
-void chol_near_identity(const double* G, int k, double* R, double* Rinv, double* nrm,
-                        cudaStream_t st) {
-  k_chol_near_identity<<<1, 1024, 0, st>>>(G, k, R, Rinv, nrm);
+void chol_near_identity(const double* G, int k, double* R, double* Rinv, double* part,
+                        unsigned* counter, double* nrm, cudaStream_t st) {
+  int64_t blocks = cdiv((int64_t)k * k, 256 * 4);
+  if (blocks > 256) blocks = 256;
+  if (blocks < 1) blocks = 1;
+  k_chol_near_identity<<<(unsigned)blocks, 256, 0, st>>>(G, k, R, Rinv, part, counter, nrm);
 }
 
 template <typename Tin, typename Tout>

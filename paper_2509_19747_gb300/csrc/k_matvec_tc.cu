@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
     k_kernel_mv_tc(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
                    int64_t n, int64_t tiles, int64_t total, int nslots,
                    const float* __restrict__ V, float* __restrict__ part, int* __restrict__ err,
-                   const ColState* __restrict__ gate, int gate_mp) {
+                   const ColState* __restrict__ gate, int gate_mp, float* __restrict__ W,
+                   float mu, unsigned* __restrict__ pair_cnt) {
   if (gate) {
     // inside the Krylov iterations: nothing to do once every column is done
     bool any = false;
@@ -358,7 +359,7 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
               out[c] = (b == 0 ? acc[c] : acc1[c]) + sm->quarter[0][b * kRows + r][c] +
                        sm->quarter[1][b * kRows + r][c] + sm->quarter[2][b * kRows + r][c];
             // the CTA that ends the row pair clears the slots no CTA uses
-            if (w.last)
+            if (w.last && !W)
               for (int sl = w.slot + 1; sl < nslots; ++sl)
 #pragma unroll
                 for (int c = 0; c < MP; ++c) part[((int64_t)sl * n + gi) * MP + c] = 0.f;
@@ -366,6 +367,51 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm->q_empty);
+        if (W) {
+          // split sum in the kernel: each quarter-0 warp (rows q*32 + lane of
+          // both row blocks) arrives on its quarter's counter of the pair once
+          // its partials are visible; the last of the pair's nseg arrivals
+          // sums that quarter's slots (fixed order) into W = sum + mu V and
+          // resets the counter.  No warp waits.
+          const int64_t pair = w.row0 / (kRows * kRB);
+          const int nseg = (int)(sk_cta_of((pair + 1) * tiles - 1, total, gridDim.x) -
+                                 sk_cta_of(pair * tiles, total, gridDim.x) + 1);
+          __threadfence();
+          __syncwarp();
+          unsigned lastw = 0u;
+          unsigned* ctr = pair_cnt + pair * 4 + q;
+          if (lane == 0) {
+            lastw = atomicAdd(ctr, 1u) == (unsigned)nseg - 1u ? 1u : 0u;
+            if (lastw) *ctr = 0u;
+          }
+          lastw = __shfl_sync(0xffffffffu, lastw, 0);
+          if (lastw) {
+            __threadfence();
+            float sum[kRB][MP];
+#pragma unroll
+            for (int b = 0; b < kRB; ++b)
+#pragma unroll
+              for (int c = 0; c < MP; ++c) sum[b][c] = 0.f;
+#pragma unroll 2
+            for (int sl = 0; sl < nseg; ++sl)
+#pragma unroll
+              for (int b = 0; b < kRB; ++b) {
+                const int64_t gi = w.row0 + b * kRows + r;
+                if (gi < n) {
+                  const float* src = part + ((int64_t)sl * n + gi) * MP;
+#pragma unroll
+                  for (int c = 0; c < MP; ++c) sum[b][c] += __ldcg(src + c);
+                }
+              }
+#pragma unroll
+            for (int b = 0; b < kRB; ++b) {
+              const int64_t gi = w.row0 + b * kRows + r;
+              if (gi < n)
+#pragma unroll
+                for (int c = 0; c < MP; ++c) W[gi * MP + c] = sum[b][c] + mu * V[gi * MP + c];
+            }
+          }
+        }
       }
     }
   }
@@ -517,9 +563,11 @@ int mv_tc_nsplit(int64_t n) {
 // K_ij V[j][c] (zero for the slots beyond that pair's CTAs); nslots =
 // mv_tc_nsplit(n).  V must have mv_tc_pad(n) rows (zero beyond n).  Returns
 // false if the kernel cannot be launched.
+int64_t mv_tc_pairs(int64_t n) { return mv_tc_pad(n) / (kRows * kRB); }
+
 bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const float* V,
                   float* part, int nslots, int* err, const ColState* gate, int gate_mp,
-                  cudaStream_t st) {
+                  float* W, float mu, unsigned* pair_cnt, cudaStream_t st) {
   const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
   const int64_t tiles = cdiv(n, kPts);
   const int64_t total = pairs * tiles;
@@ -530,7 +578,7 @@ bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const f
   if (!set_attr<MPV>()) return false;                                                            \
   k_kernel_mv_tc<MPV><<<grid, kThreadsMv, mv_smem_bytes<MPV>(), st>>>(am, bm, n, tiles, total,    \
                                                                       nslots, V, part, err, gate, \
-                                                                      gate_mp);
+                                                                      gate_mp, W, mu, pair_cnt);
   switch (mp) {
     case 1: RR_MVTC(1) break;
     case 2: RR_MVTC(2) break;

@@ -30,7 +30,7 @@ constexpr int kMaxRestarts = 400;
 enum Region {
   R_OM, R_OMB, R_SSC, R_SSS, R_THC, R_THS, R_SK, R_Y, R_Q, R_Y0, R_KK, R_KKT, R_GPART, R_CHOLW,
   R_STATUS, R_XS, R_CN, R_PN, R_AUG, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT,
-  R_CS, R_NORMS, R_FUSED, R_ML, R_FWHT, R_NREG
+  R_CS, R_NORMS, R_FUSED, R_ML, R_FWHT, R_PCNT, R_NREG
 };
 
 struct Layout {
@@ -113,6 +113,9 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_AUG] = (A.kind == RR_OP_GAUSS_KERNEL && A.dim == 8 && !uses_f64(o))
                       ? 2 * npad_tc * kAugFloats * 4 + mv_tc2_vsplit_elems(A.n) * 2 : 0;
   L.size[R_MVS] = op_matvec_scratch_elems(od, mp) * 8;
+  // arrival counters of the tensor-core product's row pairs
+  L.size[R_PCNT] = (A.kind == RR_OP_GAUSS_KERNEL && A.dim == 8 && !uses_f64(o))
+                       ? (size_t)mv_tc_pairs(A.n) * 4 * 4 : 0;
   // Krylov vectors carry zero rows up to the tensor-core tile multiple
   L.size[R_VT] = (size_t)kNumVec * (size_t)mv_tc_pad(A.n) * (size_t)mp * ts;
   L.size[R_V64] = 4 * n * (size_t)mp * 8;
@@ -370,6 +373,7 @@ void carve(rr_handle* h) {
   const size_t vecp = (size_t)mv_tc_pad(h->n) * h->mp;
   unsigned char* vb = (unsigned char*)at(R_VT);
   for (int i = 0; i < kNumVec; ++i) h->V[i] = vb + i * vecp * ts;
+  h->op.pair_cnt = (unsigned*)at(R_PCNT);
   float* aug = (float*)at(R_AUG);
   h->op.aug_a = aug;
   h->op.aug_b = aug ? aug + (size_t)mv_tc_pad(h->n) * kAugFloats : nullptr;
@@ -558,7 +562,7 @@ rr_status orthogonalize(rr_handle* h, const double* G1given = nullptr) {
         // the last pass factors a Gram I + E with E at rounding level: the
         // first-order factor and inverse are exact to O(|E|^2), below the
         // working precision once |E| <= sqrt(u) (1e-8 float64, 1e-4 float32)
-        chol_near_identity(Rp, k, h->kk[kScB], Rip, h->norms, h->st);
+        chol_near_identity(Rp, k, h->kk[kScB], Rip, h->rpart, h->cnt, h->norms, h->st);
         double e = 0.0;
         RR_TRY(read_doubles(h, h->norms, 1, &e));
         series = e <= (h->f64 ? 1e-8 : 1e-4);
@@ -1039,6 +1043,7 @@ rr_status build_impl(rr_handle* h) {
   RR_CUDA_TRY(cudaMemsetAsync(h->cs, 0, h->L.size[R_CS], st));
   RR_CUDA_TRY(cudaMemsetAsync(h->dstatus, 0, h->L.size[R_STATUS], st));
   RR_CUDA_TRY(cudaMemsetAsync(h->V[0], 0, h->L.size[R_VT], st));   // zero pad rows
+  if (h->op.pair_cnt) RR_CUDA_TRY(cudaMemsetAsync(h->op.pair_cnt, 0, h->L.size[R_PCNT], st));
   if (h->op.kind == RR_OP_GAUSS_KERNEL) prepare_kernel_points(h->op, st);
   // float32 kernel products on the tensor cores (kernel_impl 0 = auto, 2 =
   // exponents on the tensor cores, 3 = K v on them too)
@@ -1230,7 +1235,8 @@ void iter_C(rr_handle* h, const cudaEvent_t* ev) {
   if (h->fusedG > 0) {
     // w = A_mu p (with alpha formed by the kernel-operator product where it
     // can), then Alg. 7 steps 6-9 in one persistent cooperative launch
-    const bool alpha_ready = h->op.kind == RR_OP_GAUSS_KERNEL && sizeof(T) == 4;
+    const bool alpha_ready = h->op.kind == RR_OP_GAUSS_KERNEL && sizeof(T) == 4 &&
+                             kernel_product_forms_alpha(h->op);
     if (alpha_ready) {
       h->op.alpha_cs = h->cs;
       h->op.alpha_rpart = h->rpart;
@@ -1431,6 +1437,10 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
   double* X = h->v64[kX64];
   double* R64 = h->v64[kR64];
   double bn2[8] = {0}, rn2[8] = {0};
+  // the product's pair counters are zero between launches; a launch that gave
+  // up on a wait (error flag) may have left some set
+  if (h->op.pair_cnt)
+    RR_CUDA_TRY(cudaMemsetAsync(h->op.pair_cnt, 0, h->L.size[R_PCNT], st));
   dot_cols<double>(B, B, n, mp, kModeNone, h->rpart, h->cnt, nullptr, false, h->norms, st);
   RR_TRY(read_doubles(h, h->norms, mp, bn2));
   int used[8] = {0}, outer[8] = {0}, mv[8] = {0}, stat[8] = {0};

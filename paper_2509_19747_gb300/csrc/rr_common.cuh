@@ -95,7 +95,16 @@ struct OpDev {
   ColState* alpha_cs;
   double* alpha_rpart;
   unsigned* alpha_cnt;
+  // tensor-core product (k_matvec_tc.cu): one arrival counter per row pair
+  // (zero between launches); the CTA whose segment arrives last sums the
+  // pair's split partials into W itself
+  unsigned* pair_cnt;
 };
+
+// the kernel-operator product forms alpha = rho / (p^T w) itself (in its split
+// sum); the tensor-core product writes W from the CTAs and leaves alpha to
+// the persistent step
+inline bool kernel_product_forms_alpha(const OpDev& op) { return !(op.use_tc && !op.tc2); }
 
 // One-time host setup per device (function attributes): bit d of `mask` is
 // set once fn() has succeeded with device d current.  Safe to call from
@@ -193,9 +202,10 @@ void kxk_scale_add_identity(const double* A, double a, double b, double* out, in
                             cudaStream_t st);
 void kxk_frob_minus_identity(const double* A, double c, int k, double* out, cudaStream_t st);
 // first-order Cholesky factor (R) and inverse (Rinv) of a Gram G = I + E,
-// nrm[0] = |E|_F (device)
-void chol_near_identity(const double* G, int k, double* R, double* Rinv, double* nrm,
-                        cudaStream_t st);
+// nrm[0] = |E|_F (device); part: >= 256 doubles, counter: zero on entry
+// (left zero)
+void chol_near_identity(const double* G, int k, double* R, double* Rinv, double* part,
+                        unsigned* counter, double* nrm, cudaStream_t st);
 template <typename Tin, typename Tout>
 void convert(const Tin* in, Tout* out, int64_t count, cudaStream_t st);
 void transpose_kxk(const double* in, double* out, int k, cudaStream_t st);
@@ -237,9 +247,13 @@ int mv_tc_nsplit(int64_t n);
 int64_t tc_persistent_ctas(int64_t total);
 bool tc_encode_2d(void* map, bool bf16, const void* base, uint64_t inner, uint64_t outer,
                   uint32_t box_inner, uint32_t box_outer);
+// W = K V + mu V (n x mp) when W is given: the partials go to `part` and the
+// last CTA of each row pair sums them (pair_cnt: 4 mv_tc_pad(n) / 256
+// counters, one per TMEM lane quarter of a pair, zero on entry and on return)
 bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const float* V,
                   float* part, int nsplit, int* err, const ColState* gate, int gate_mp,
-                  cudaStream_t st);
+                  float* W, float mu, unsigned* pair_cnt, cudaStream_t st);
+int64_t mv_tc_pairs(int64_t n);
 // k_matvec_tc2.cu -- the same product with K v also on the tensor cores
 size_t mv_tc2_vsplit_elems(int64_t n);
 bool encode_mv_tc2(const float* Baug, const uint16_t* vsplit, int64_t n, void* bmap64, void* vmap);
