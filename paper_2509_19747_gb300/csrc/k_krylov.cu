@@ -1107,7 +1107,8 @@ struct TailArgs {
   int64_t n;
   int k;
   int rpc;
-  int alpha_ready;    // the product kernel has applied alpha to cs
+  int alpha_mode;     // 0: p^T w here; 1: the product kernel applied alpha to cs;
+                      // 2: the product kernel accumulated p^T w into this launch's set
   double* acc;        // two sets of [pw 8 | rr 8 | rz 8 | t k x 8]
   ColState* cs;
   GridBar* bar;
@@ -1253,7 +1254,22 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
 
   double v[8];
   // ---- A: p^T w
-  if (!a.alpha_ready) {
+  if (a.alpha_mode == 2) {
+    // accumulated by the product kernel before this launch (stream order)
+    if (tid < MP) {
+      const int c = tid;
+      const double pw = __ldcg(acc + c);
+      sh_pw[c] = pw;
+      int act = sh_act0[c];
+      double al = 0.0;
+      if (act) {
+        if (!(pw > 0.0 && isfinite(pw))) act = 0;
+        else al = snap[c].rho / pw;
+      }
+      sh_alpha[c] = al;
+      sh_actA[c] = act;
+    }
+  } else if (a.alpha_mode == 0) {
     double vs = 0.0;
     for (int e = tid; e < cnt * MP; e += kFT) {
       const int64_t g = r0 * MP + e;
@@ -1454,7 +1470,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
     const int c = tid;
     ColState st = snap[c];
     st.rr = sh_rr[c];
-    if (!a.alpha_ready) {
+    if (a.alpha_mode != 1) {
       st.pw = sh_pw[c];
       if (sh_act0[c]) {
         if (!sh_actA[c]) { st.status = RR_ERR_BREAKDOWN; st.alpha = 0.0; }
@@ -1557,12 +1573,12 @@ static cudaError_t launch_tail(const TailArgs<T>& a, int G, size_t smem, cudaStr
 
 template <typename T>
 cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const T* QH, int64_t n,
-                     int k, int mp, int G, bool alpha_ready, double* scratch, ColState* cs,
+                     int k, int mp, int G, int alpha_mode, double* scratch, ColState* cs,
                      GridBar* bar, int* err, cudaStream_t st) {
   TailArgs<T> a;
   a.E = E; a.R = R; a.P = P; a.Z = Z; a.W = W; a.Q = Q; a.QH = QH;
   a.n = n; a.k = k; a.rpc = (int)cdiv(n, G);
-  a.alpha_ready = alpha_ready ? 1 : 0;
+  a.alpha_mode = alpha_mode;
   a.acc = scratch;
   a.cs = cs; a.bar = bar; a.err = err;
   const size_t smem = pcg_tail_smem<T>(k, mp);
@@ -1630,10 +1646,10 @@ void sum_splits_alpha(const T* part, int nsplit, int64_t n, int mp, double mu, c
 template int pcg_tail_ctas<float>(int64_t, int, int);
 template int pcg_tail_ctas<double>(int64_t, int, int);
 template cudaError_t pcg_tail<float>(float*, float*, float*, float*, const float*, const float*,
-                                     const float*, int64_t, int, int, int, bool, double*,
+                                     const float*, int64_t, int, int, int, int, double*,
                                      ColState*, GridBar*, int*, cudaStream_t);
 template cudaError_t pcg_tail<double>(double*, double*, double*, double*, const double*,
-                                      const double*, const double*, int64_t, int, int, int, bool,
+                                      const double*, const double*, int64_t, int, int, int, int,
                                       double*, ColState*, GridBar*, int*, cudaStream_t);
 template void sum_splits_alpha<float>(const float*, int, int64_t, int, double, const float*,
                                       float*, double*, unsigned*, ColState*, cudaStream_t);

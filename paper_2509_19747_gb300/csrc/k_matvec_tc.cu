@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
                    int64_t n, int64_t tiles, int64_t total, int nslots,
                    const float* __restrict__ V, float* __restrict__ part, int* __restrict__ err,
                    const ColState* __restrict__ gate, int gate_mp, float* __restrict__ W,
-                   float mu, unsigned* __restrict__ pair_cnt) {
+                   float mu, unsigned* __restrict__ pair_cnt, double* __restrict__ pw_acc,
+                   int64_t pw_set, const unsigned* __restrict__ pw_launches) {
   if (gate) {
     // inside the Krylov iterations: nothing to do once every column is done
     bool any = false;
@@ -403,12 +404,31 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
                   for (int c = 0; c < MP; ++c) sum[b][c] += __ldcg(src + c);
                 }
               }
+            double pw[MP];
+#pragma unroll
+            for (int c = 0; c < MP; ++c) pw[c] = 0.0;
 #pragma unroll
             for (int b = 0; b < kRB; ++b) {
               const int64_t gi = w.row0 + b * kRows + r;
               if (gi < n)
 #pragma unroll
-                for (int c = 0; c < MP; ++c) W[gi * MP + c] = sum[b][c] + mu * V[gi * MP + c];
+                for (int c = 0; c < MP; ++c) {
+                  const float vv = V[gi * MP + c];
+                  const float ww = sum[b][c] + mu * vv;
+                  W[gi * MP + c] = ww;
+                  pw[c] = fma((double)vv, (double)ww, pw[c]);
+                }
+            }
+            if (pw_acc) {
+              // p^T w of these rows into the persistent step's next accumulator set
+#pragma unroll
+              for (int c = 0; c < MP; ++c)
+                for (int o = 16; o > 0; o >>= 1) pw[c] += __shfl_xor_sync(0xffffffffu, pw[c], o);
+              if (lane == 0) {
+                double* dst = pw_acc + (int64_t)(*(volatile const unsigned*)pw_launches & 1u) * pw_set;
+#pragma unroll
+                for (int c = 0; c < MP; ++c) atomicAdd(dst + c, pw[c]);
+              }
             }
           }
         }
@@ -567,7 +587,8 @@ int64_t mv_tc_pairs(int64_t n) { return mv_tc_pad(n) / (kRows * kRB); }
 
 bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const float* V,
                   float* part, int nslots, int* err, const ColState* gate, int gate_mp,
-                  float* W, float mu, unsigned* pair_cnt, cudaStream_t st) {
+                  float* W, float mu, unsigned* pair_cnt, double* pw_acc, int64_t pw_set,
+                  const unsigned* pw_launches, cudaStream_t st) {
   const int64_t pairs = mv_tc_pad(n) / (kRows * kRB);
   const int64_t tiles = cdiv(n, kPts);
   const int64_t total = pairs * tiles;
@@ -578,7 +599,8 @@ bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const f
   if (!set_attr<MPV>()) return false;                                                            \
   k_kernel_mv_tc<MPV><<<grid, kThreadsMv, mv_smem_bytes<MPV>(), st>>>(am, bm, n, tiles, total,    \
                                                                       nslots, V, part, err, gate, \
-                                                                      gate_mp, W, mu, pair_cnt);
+                                                                      gate_mp, W, mu, pair_cnt,   \
+                                                                      pw_acc, pw_set, pw_launches);
   switch (mp) {
     case 1: RR_MVTC(1) break;
     case 2: RR_MVTC(2) break;

@@ -624,7 +624,8 @@ void kernel_mv<float>(const OpDev& op, double mu, const float* V, float* W, int 
         op.tc2 ? kernel_mv_tc2(op.amap, op.bmap64, op.vmap, op.n, mp, V, op.vsplit, part, nt,
                                op.tc_err, op.gate, op.gate_mp, st)
                : kernel_mv_tc(op.amap, op.bmap, op.n, mp, V, part, nt, op.tc_err, op.gate,
-                              op.gate_mp, W, (float)mu, op.pair_cnt, st);
+                              op.gate_mp, W, (float)mu, op.pair_cnt, op.pw_acc, op.pw_set,
+                              op.pw_launches, st);
     if (launched) {
       rec(ev, 1, st);
       if (!op.tc2) return;    // the product kernel wrote W (its CTAs sum the splits)

@@ -1233,19 +1233,25 @@ void iter_C(rr_handle* h, const cudaEvent_t* ev) {
   T *Rv = vt<T>(h, kR), *Pv = vt<T>(h, kP), *Wv = vt<T>(h, kW), *Zv = vt<T>(h, kZ),
     *Ev = vt<T>(h, kE);
   if (h->fusedG > 0) {
-    // w = A_mu p (with alpha formed by the kernel-operator product where it
-    // can), then Alg. 7 steps 6-9 in one persistent cooperative launch
-    const bool alpha_ready = h->op.kind == RR_OP_GAUSS_KERNEL && sizeof(T) == 4 &&
-                             kernel_product_forms_alpha(h->op);
-    if (alpha_ready) {
+    // w = A_mu p (the float32 kernel-operator product also forms alpha, or,
+    // on the tensor cores, p^T w into the step's next accumulator set), then
+    // Alg. 7 steps 6-9 in one persistent cooperative launch
+    const bool kf = h->op.kind == RR_OP_GAUSS_KERNEL && sizeof(T) == 4;
+    const int alpha_mode = !kf ? 0 : (kernel_product_forms_alpha(h->op) ? 1 : 2);
+    if (alpha_mode == 1) {
       h->op.alpha_cs = h->cs;
       h->op.alpha_rpart = h->rpart;
       h->op.alpha_cnt = h->cnt;
+    } else if (alpha_mode == 2) {
+      h->op.pw_acc = h->fscratch;
+      h->op.pw_set = (int64_t)(pcg_tail_scratch_doubles(k, mp) / 2);
+      h->op.pw_launches = &h->bar->launches;
     }
     matvec<T>(h, Pv, Wv, ev);
     h->op.alpha_cs = nullptr;
+    h->op.pw_acc = nullptr;
     pcg_tail<T>(Ev, Rv, Pv, Zv, Wv, (const T*)h->Q, (const T*)h->QH, n, k, mp, h->fusedG,
-                alpha_ready, h->fscratch, h->cs, h->bar, h->dstatus + 3, h->st);
+                alpha_mode, h->fscratch, h->cs, h->bar, h->dstatus + 3, h->st);
     return;
   }
   matvec<T>(h, Pv, Wv, ev);                                               // w = A_mu p

@@ -99,6 +99,12 @@ struct OpDev {
   // (zero between launches); the CTA whose segment arrives last sums the
   // pair's split partials into W itself
   unsigned* pair_cnt;
+  // when set (variant C with the persistent step and the tensor-core
+  // product), the split-sum warps also add their rows' p^T w into pw_acc +
+  // (launches & 1) pw_set, the accumulator set of the step's next launch
+  double* pw_acc;
+  int64_t pw_set;
+  const unsigned* pw_launches;
 };
 
 // the kernel-operator product forms alpha = rho / (p^T w) itself (in its split
@@ -252,7 +258,8 @@ bool tc_encode_2d(void* map, bool bf16, const void* base, uint64_t inner, uint64
 // counters, one per TMEM lane quarter of a pair, zero on entry and on return)
 bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const float* V,
                   float* part, int nsplit, int* err, const ColState* gate, int gate_mp,
-                  float* W, float mu, unsigned* pair_cnt, cudaStream_t st);
+                  float* W, float mu, unsigned* pair_cnt, double* pw_acc, int64_t pw_set,
+                  const unsigned* pw_launches, cudaStream_t st);
 int64_t mv_tc_pairs(int64_t n);
 // k_matvec_tc2.cu -- the same product with K v also on the tensor cores
 size_t mv_tc2_vsplit_elems(int64_t n);

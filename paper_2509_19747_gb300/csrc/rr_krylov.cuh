@@ -97,7 +97,7 @@ int pcg_tail_ctas(int64_t n, int k, int mp);
 size_t pcg_tail_scratch_doubles(int k, int mp);
 template <typename T>
 cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const T* QH, int64_t n,
-                     int k, int mp, int G, bool alpha_ready, double* scratch, ColState* cs,
+                     int k, int mp, int G, int alpha_mode, double* scratch, ColState* cs,
                      GridBar* bar, int* err, cudaStream_t st);
 // W = sum of split partials + mu V with alpha = rho / (p^T w) applied to cs
 // (variant C with the persistent step; V = p)
