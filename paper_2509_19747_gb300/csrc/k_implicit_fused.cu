@@ -28,9 +28,9 @@ namespace {
 constexpr int kIT = 512;   // threads per CTA
 constexpr unsigned long long kTimeoutNs = 10ull * 1000 * 1000 * 1000;
 
-__device__ __forceinline__ unsigned ld_acq(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acq64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -44,15 +44,13 @@ __device__ bool barrier_all(GridBar* gb, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    const unsigned g = ld_acq(&gb->gen);
     __threadfence();
-    if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else {
+    const unsigned long long g = gridDim.x;
+    const unsigned long long old = atomicAdd(&gb->arrivals, 1ull);
+    const unsigned long long target = (old / g + 1) * g;
+    if (old + 1 != target) {
       const unsigned long long t0 = gtimer();
-      while (ld_acq(&gb->gen) == g) {
+      while (ld_acq64(&gb->arrivals) < target) {
         if (*(volatile int*)&gb->abort || gtimer() - t0 > kTimeoutNs) {
           ok = 0;
           break;

@@ -1052,9 +1052,9 @@ constexpr int kFT = 512;                 // threads of the fused step
 constexpr int kFusedChunk = 256;         // rows of r staged in shared memory at a time
 constexpr unsigned long long kBarTimeoutNs = 10ull * 1000 * 1000 * 1000;
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -1068,16 +1068,13 @@ __device__ bool grid_barrier(GridBar* gb, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    const unsigned g = ld_acquire_u32(&gb->gen);
     __threadfence();
-    const unsigned prev = atomicAdd(&gb->count, 1u);
-    if (prev == gridDim.x - 1) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else {
+    const unsigned long long g = gridDim.x;
+    const unsigned long long old = atomicAdd(&gb->arrivals, 1ull);
+    const unsigned long long target = (old / g + 1) * g;
+    if (old + 1 != target) {
       const unsigned long long t0 = global_ns();
-      while (ld_acquire_u32(&gb->gen) == g) {
+      while (ld_acquire_u64(&gb->arrivals) < target) {
         if (*(volatile int*)&gb->abort || global_ns() - t0 > kBarTimeoutNs) {
           ok = 0;
           break;

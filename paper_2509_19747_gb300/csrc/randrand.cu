@@ -1447,6 +1447,9 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
   // up on a wait (error flag) may have left some set
   if (h->op.pair_cnt)
     RR_CUDA_TRY(cudaMemsetAsync(h->op.pair_cnt, 0, h->L.size[R_PCNT], st));
+  // likewise the grid barrier's arrival count of a persistent step (with both
+  // accumulator sets and the launch parity)
+  if (h->fusedG > 0) RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
   dot_cols<double>(B, B, n, mp, kModeNone, h->rpart, h->cnt, nullptr, false, h->norms, st);
   RR_TRY(read_doubles(h, h->norms, mp, bn2));
   int used[8] = {0}, outer[8] = {0}, mv[8] = {0}, stat[8] = {0};

@@ -82,9 +82,12 @@ constexpr int kMaxReduceBlocks = 8 * 152;  // upper bound on CTAs of the fused r
 // the arrival counter and the generation word sit on separate 128-byte
 // lines, so that arrivals do not contend with the waiters' polling
 struct GridBar {
-  unsigned count;
-  unsigned pad0[31];
-  unsigned gen;
+  // arrivals at grid barriers since the last reset, never decremented: a CTA
+  // arriving as number a waits until the count reaches the next multiple of
+  // the grid size (64 bits: no wrap)
+  unsigned long long arrivals;
+  unsigned pad0[30];
+  unsigned spare;
   int abort;
   unsigned launches;   // launches of the fused step so far (accumulator parity)
   unsigned pad1[29];
