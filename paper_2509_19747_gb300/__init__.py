@@ -526,7 +526,7 @@ class Request:
                  seed: int = 0, maxit: int = 20000, variant: str = "C", precision: str = "mixed",
                  orth: str = "cholqr2", power_iters: int = 20, gamma: int = 8, l_sk: int = 0,
                  gamma_sk: int = 8, kernel_impl: int = 0, iter_impl: int = 0, q: int = 0,
-                 ml_l1: int = 0, ml_gamma: int = 0):
+                 ml_l1: int = 0, ml_gamma: int = 0, refine: bool = False):
         import torch
         B = b.reshape(op.n, -1)
         m = B.shape[1]
@@ -545,6 +545,7 @@ class Request:
         o.kernel_impl = kernel_impl
         o.iter_impl = iter_impl
         o.q = q
+        o.refine = 1 if refine else 0
         set_multilevel(o, sketch, op.n, k, ml_l1, ml_gamma)
         self.op = op
         self.c = rr_request(op=op.c, mu=float(mu), k=int(k), sketch=SKETCHES[sketch],

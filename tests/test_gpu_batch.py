@@ -95,6 +95,43 @@ def test_batch_mixed_operator_kinds(cuda_lib):
     assert rel(xd, xa.cpu().numpy()) <= 1e-12
 
 
+def test_batch_new_test_matrices_and_options(cuda_lib):
+    """Multi-level and SRHT test matrices (the SRHT applied by fast
+    Walsh-Hadamard transforms in the basis-less CSR form) and the refined
+    projector inside one batch: every system meets rtol by the float64
+    residual, in the iterations it takes alone."""
+    rr = cuda_lib
+    rtol = 1e-6
+    C = W.diffusion_csr(side=40, seed=54, corr_len=4.0)
+    csr_op = rr.Operator.csr(dev(C.rowptr), dev(C.colidx), dev(C.vals))
+    bc = W.gaussian_rhs(C.n, 1, 54)
+    k1 = kernel_system(rr, 11, 1500, m=2)
+    k2 = kernel_system(rr, 12, 1300, m=2)
+    specs = [
+        (k1["op"], k1["mu"], k1["k"], k1["B"], dict(sketch="multilevel", seed=k1["seed"])),
+        (k2["op"], k2["mu"], k2["k"], k2["B"], dict(sketch="srht", seed=k2["seed"], refine=True)),
+        (csr_op, 1e-6, 32, bc, dict(sketch="srht", seed=54, orth="rand_cholqr")),
+        (csr_op, 1e-6, 32, bc, dict(sketch="multilevel", seed=55, orth="rand_cholqr")),
+    ]
+    reqs = [rr.Request(op, mu, k, dev(B), rtol, **kw) for op, mu, k, B, kw in specs]
+    st, res = rr.solve_batch(reqs, workers=4)
+    assert st == rr.RR_OK, res
+    oracles = [k1["oracle"], k2["oracle"], O.CsrOp(C.rowptr, C.colidx, C.vals, C.n),
+               O.CsrOp(C.rowptr, C.colidx, C.vals, C.n)]
+    for (op, mu, k, B, kw), q, r, orc in zip(specs, reqs, res, oracles):
+        assert r["status"] == rr.RR_OK
+        x = q.x.cpu().numpy()
+        assert np.all(O.true_rel_residual(orc, mu, x, B) <= rtol)
+        h = rr.Handle(op, mu, k, kw["sketch"], seed=kw["seed"], precision="mixed",
+                      max_rhs=B.shape[1], orth=kw.get("orth", "cholqr2"),
+                      refine=kw.get("refine", False))
+        _, sa, ia = h.solve(dev(B), rtol=rtol)
+        h.close()
+        assert sa == rr.RR_OK
+        for a, b in zip([i["inner_iters"] for i in r["info"]], [i["inner_iters"] for i in ia]):
+            assert abs(a - b) <= 2
+
+
 def test_server_alone_vs_mix_and_admission(cuda_lib):
     """Requests submitted while others run complete with the results they
     have alone; a budget that holds one workspace at a time serialises them
