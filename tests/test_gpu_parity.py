@@ -510,3 +510,51 @@ def test_power_q_with_basis_less_unsupported(cuda_lib):
     with pytest.raises(rr.RandRandError) as e:
         rr.Handle(op, 1e-4, 8, "sparse_sign", seed=73, orth="rand_cholqr", q=1)
     assert e.value.status == rr.RR_ERR_UNSUPPORTED
+
+
+# ------------------------------------ the benchmark's configuration, full size
+def _kernel_rows(X64, rows, V, mu):
+    """(K + mu I) V and sum_j |K_ij V_j| on the given rows, from the definition
+    K_ij = exp(-|x_i - x_j|^2 / 2), float64, a few rows at a time."""
+    out, scale = [], []
+    for c in range(0, len(rows), 32):
+        ii = rows[c:c + 32]
+        K = np.exp(-((X64[ii, None, :] - X64[None, :, :]) ** 2).sum(-1) / 2)
+        out.append(K @ V + mu * V[ii])
+        scale.append(np.abs(K) @ np.abs(V) + mu * np.abs(V[ii]))
+    return np.concatenate(out), np.concatenate(scale)
+
+
+def test_kernel_ridge_full_size(cuda_lib):
+    """n = 20000, d = 8, k = 500, 4 right-hand sides, mu = 1e-3, mixed
+    precision, rtol 1e-6 (the timed configuration, same launch path): the
+    double-float restart product matches the float64 definition on sampled
+    rows (including the ragged last block) to ~1e-11 of the row magnitudes,
+    the solve converges, and the float64 residual on sampled rows is
+    consistent with the reported |b - A_mu x| / |b| <= rtol."""
+    rr = cuda_lib
+    n, m, k, mu, rtol = 20000, 4, 500, 1e-3, 1e-6
+    X = W.mixture_points(n, 8, 10, seed=W.SEED_KERNEL)
+    B = W.gaussian_rhs(n, m, W.SEED_KERNEL)
+    X64 = X.astype(np.float64)
+    rows = np.concatenate([np.random.default_rng(7).choice(n - 300, 160, replace=False),
+                           np.arange(n - 96, n)])
+    h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=W.SEED_KERNEL,
+                  precision="mixed", max_rhs=m)
+    V = np.random.default_rng(8).standard_normal((n, m))
+    w = h.matvec(dev(V)).cpu().numpy().reshape(n, m)[rows]
+    ref, scale = _kernel_rows(X64, rows, V, mu)
+    assert np.max(np.abs(w - ref) / scale) <= 1e-11
+    x, status, infos = h.solve(dev(B), rtol=rtol)
+    assert status == rr.RR_OK
+    assert all(i["rel_residual"] <= rtol for i in infos)
+    x = x.cpu().numpy()
+    Ax, _ = _kernel_rows(X64, rows, x, mu)
+    r = B[rows] - Ax
+    # sampled rows estimate |r|^2 / n per column; the reported residual is the
+    # full float64-accurate |r| / |b|
+    est = np.sqrt((r ** 2).mean(axis=0) * n) / np.linalg.norm(B, axis=0)
+    rep = np.array([i["rel_residual"] for i in infos])
+    assert np.all(est <= 3 * rtol)
+    assert np.all(est <= 4 * rep + 1e-9) and np.all(rep <= 4 * est + 1e-9)
+    h.close()
