@@ -227,7 +227,10 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {k: WORKLOAD[k] for k in ("workload", "n", "d", "k", "nrhs", "mu", "rtol")},
+        # the same workload description as the GPU arm's line
+        "config": {**{k: WORKLOAD[k] for k in ("workload", "n", "d", "k", "nrhs", "mu", "rtol",
+                                               "precision", "variant", "sketch")},
+                   "parallelism": f"replicas x{world}", "l2": "host cores (no GPU cache)"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_threads(),
                          "kind": "oracle",
                          "sample": f"per step: one float64 (K+mu I)V product with 4 columns at "
