@@ -1640,6 +1640,227 @@ void sum_splits_alpha(const T* part, int nsplit, int64_t n, int mp, double mu, c
   k_sum_splits_alpha<T><<<blocks, kNT, 0, st>>>(part, nsplit, n, mp, mu, V, W, rpart, counter, cs);
 }
 
+// ======================================================================
+// Power iterations of variant C (Alg. 7 step 3) as two persistent cooperative
+// launches per iteration around the operator product (one CTA per SM):
+//   pre  (mode 0): t = Q^T V | barrier | s0 = -t0, s1 = G t1 (the rows of G
+//                  spread over the CTAs, a warp per row) | barrier |
+//                  U = (V0, 0) + Q s
+//   post (mode 1): t = Q^T W | barrier | Z = (W0, 0) + Q (-t0, t1) and |Z|^2 |
+//                  barrier | V = Z / |Z|, lam = |Z| into the column states
+// Column 0 iterates v -> (I - Pi) A_mu (I - Pi) v, column 1 v -> Pi A_mu Q G
+// Q^T v; further columns stay zero.  Accumulators: two sets [|Z|^2 8 | t k x
+// MP | s k x MP], set 0 for pre and set 1 for post, each launch clearing the
+// other's (launches alternate).  Q^T X uses the persistent step's row-phase
+// partials and float64 atomics (arrival order: rounding-level differences).
+// ======================================================================
+template <typename T>
+struct PowArgs {
+  const T* X;        // pre: V; post: W
+  T* Out;            // pre: U; post: V
+  const T* Q;
+  const double* G;   // k x k row-major
+  int64_t n;
+  int k;
+  int rpc;
+  int mode;
+  double* acc;
+  ColState* cs;
+  GridBar* bar;
+  int* err;
+};
+
+__host__ __device__ inline size_t pow_set_doubles(int k) { return 8 + 16 * (size_t)k; }
+
+// Out rows = (X column 0, zero columns) + Q rows s (s staged [MP][k] in shared
+// memory); four rows per warp in flight; v[c] += Out^2 when v is given
+template <typename T, int MP>
+__device__ void pow_combine(const T* __restrict__ Q, const T* __restrict__ X, T* __restrict__ Out,
+                            int64_t r0, int cnt, int k, const T* sT, double* v) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int kW = kFT / 32;
+  for (int i0 = wid; i0 < cnt; i0 += 4 * kW) {
+    T acc[4][MP];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < MP; ++c) acc[b][c] = (T)0;
+    for (int j0 = 0; j0 < k; j0 += 128) {
+      T qv[4][4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = i0 + b * kW;
+        const T* q = Q + (r0 + (i < cnt ? i : 0)) * k;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + lane + 32 * u;
+          qv[b][u] = (i < cnt && j < k) ? q[j] : (T)0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + lane + 32 * u;
+        if (j < k)
+#pragma unroll
+          for (int c = 0; c < MP; ++c) {
+            const T sv = sT[(size_t)c * k + j];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[b][c] = fma(qv[b][u], sv, acc[b][c]);
+          }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + b * kW;
+#pragma unroll
+      for (int c = 0; c < MP; ++c) {
+        T x = acc[b][c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == c && i < cnt) {
+          const int64_t g = (r0 + i) * MP + c;
+          const T o = (c == 0 ? X[g] : (T)0) + x;
+          Out[g] = o;
+          if (v) v[c] += (double)o * (double)o;
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int MP>
+__global__ void __launch_bounds__(kFT, 1) k_power_proj(PowArgs<T> a) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sT = reinterpret_cast<T*>(smem_raw);                         // s, [MP][k]
+  T* Rs = sT + (size_t)a.k * MP;                                   // kFusedChunk x MP
+  float* red = reinterpret_cast<float*>(Rs + (size_t)kFusedChunk * MP);
+  __shared__ double redd[kFT / 32 * 8];
+  __shared__ double sh_inv[8];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int cta = blockIdx.x, G = gridDim.x, k = a.k;
+  const int64_t r0 = (int64_t)cta * a.rpc;
+  const int cnt = (int)(r0 >= a.n ? 0 : (a.n - r0 < a.rpc ? a.n - r0 : a.rpc));
+  const size_t set = pow_set_doubles(k);
+  double* acc = a.acc + (size_t)a.mode * set;
+  double* other = a.acc + (size_t)(a.mode ^ 1) * set;
+  double* nrm = acc;
+  double* tacc = acc + 8;
+  double* sg = acc + 8 + (size_t)k * MP;
+  // t = Q^T X
+  tail_qtr<T, MP>(a.Q, a.X, r0, cnt, k, tacc, Rs, red);
+  if (cta == 0)
+    for (size_t e = tid; e < set; e += kFT) other[e] = 0.0;
+  if (!grid_barrier(a.bar, a.err)) return;
+  if (a.mode == 0) {
+    // s0 = -t0, s1 = G t1: a warp per row of G, rows spread over the CTAs
+    for (int j = cta + wid * G; j < k; j += G * (kFT / 32)) {
+      double x = 0.0;
+      if (MP > 1) {
+        const double* gj = a.G + (int64_t)j * k;
+        for (int l = lane; l < k; l += 32) x = fma(gj[l], __ldcg(tacc + (size_t)l * MP + 1), x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      }
+      if (lane == 0) {
+        sg[(size_t)j * MP] = -__ldcg(tacc + (size_t)j * MP);
+        if (MP > 1) sg[(size_t)j * MP + 1] = x;
+        for (int c = 2; c < MP; ++c) sg[(size_t)j * MP + c] = 0.0;
+      }
+    }
+    if (!grid_barrier(a.bar, a.err)) return;
+    for (int e = tid; e < k * MP; e += kFT)
+      sT[(size_t)(e % MP) * k + e / MP] = (T)__ldcg(sg + e);
+  } else {
+    // s = (-t0, t1, 0, ...): (I - Pi) w and Pi w
+    for (int e = tid; e < k * MP; e += kFT) {
+      const int c = e % MP;
+      const double t = __ldcg(tacc + e);
+      sT[(size_t)c * k + e / MP] = (T)(c == 0 ? -t : (c == 1 ? t : 0.0));
+    }
+  }
+  __syncthreads();
+  double v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = 0.0;
+  pow_combine<T, MP>(a.Q, a.X, a.Out, r0, cnt, k, sT, a.mode == 1 ? v : nullptr);
+  if (a.mode == 0) return;
+  block_sum_cols<kFT>(v, MP, redd);
+  if (tid == 0 && cnt > 0)
+    for (int c = 0; c < MP; ++c) atomicAdd(nrm + c, v[c]);
+  if (!grid_barrier(a.bar, a.err)) return;
+  if (tid < MP) {
+    const double l = sqrt(__ldcg(nrm + tid));
+    sh_inv[tid] = l > 0.0 ? 1.0 / l : 0.0;
+    if (cta == 0) a.cs[tid].lam = l;
+  }
+  __syncthreads();
+  for (int e = tid; e < cnt * MP; e += kFT) {
+    const int64_t g = r0 * MP + e;
+    a.Out[g] = (T)((double)a.Out[g] * sh_inv[e % MP]);
+  }
+}
+
+template <typename T, int MP>
+static bool pow_attr() {
+  static std::atomic<uint64_t> done{0};
+  return once_per_device(done, [] {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return false;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_power_proj<T, MP>) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (cudaFuncSetAttribute(k_power_proj<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  });
+}
+
+size_t power_proj_scratch_doubles(int k) { return 2 * pow_set_doubles(k); }
+
+template <typename T>
+cudaError_t power_proj(int mode, const T* X, T* Out, const T* Q, const double* Gm, int64_t n, int k,
+                       int mp, int G, double* scratch, ColState* cs, GridBar* bar, int* err,
+                       cudaStream_t st) {
+  PowArgs<T> a;
+  a.X = X; a.Out = Out; a.Q = Q; a.G = Gm;
+  a.n = n; a.k = k; a.rpc = (int)cdiv(n, G); a.mode = mode;
+  a.acc = scratch; a.cs = cs; a.bar = bar; a.err = err;
+  const size_t smem = pcg_tail_smem<T>(k, mp);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3(kFT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+#define RR_POW(MPV)                                                  \
+  if (!pow_attr<T, MPV>()) return cudaErrorInvalidValue;             \
+  return cudaLaunchKernelEx(&cfg, k_power_proj<T, MPV>, a);
+  switch (mp) {
+    case 2: { RR_POW(2) }
+    case 4: { RR_POW(4) }
+    default: { RR_POW(8) }
+  }
+#undef RR_POW
+}
+
+template cudaError_t power_proj<float>(int, const float*, float*, const float*, const double*,
+                                       int64_t, int, int, int, double*, ColState*, GridBar*, int*,
+                                       cudaStream_t);
+template cudaError_t power_proj<double>(int, const double*, double*, const double*, const double*,
+                                        int64_t, int, int, int, double*, ColState*, GridBar*,
+                                        int*, cudaStream_t);
+
 template int pcg_tail_ctas<float>(int64_t, int, int);
 template int pcg_tail_ctas<double>(int64_t, int, int);
 template cudaError_t pcg_tail<float>(float*, float*, float*, float*, const float*, const float*,

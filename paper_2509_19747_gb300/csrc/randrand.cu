@@ -129,8 +129,9 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_NORMS] = 64 * 8;
   // persistent fused steps of variant C: barrier + partials
   L.size[R_FUSED] = (o.variant == RR_VARIANT_C)
-                        ? sizeof(GridBar) + std::max(pcg_tail_scratch_doubles(k, mp),
-                                         pcg_implicit_scratch_doubles(k, mp)) * 8
+                        ? sizeof(GridBar) + std::max({pcg_tail_scratch_doubles(k, mp),
+                                          pcg_implicit_scratch_doubles(k, mp),
+                                          power_proj_scratch_doubles(k)}) * 8
                         : 0;
   size_t off = 0;
   for (int r = 0; r < R_NREG; ++r) {
@@ -734,6 +735,26 @@ rr_status power_iterations(rr_handle* h) {
   dot_cols<T>(Vv, Vv, n, mp, kModeNorm, h->rpart, h->cnt, h->cs, false, nullptr, h->st);
   scale_cols<T>(Vv, Vv, n, mp, h->cs, h->st);
   const Coefs8 a = coefs(1.0, 0.0);
+  // variant C with the persistent step: the projections of an iteration in two
+  // persistent launches around the product
+  const int Gp = (isC && h->o.iter_impl == 0) ? pcg_tail_ctas<T>(n, h->k, mp) : 0;
+  if (Gp > 0) {
+    RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], h->st));
+    for (int it = 0; it < h->o.power_iters; ++it) {
+      RR_CUDA_TRY(power_proj<T>(0, Vv, Uv, (const T*)h->Q, h->kk[kG], n, h->k, mp, Gp,
+                                h->fscratch, h->cs, h->bar, h->dstatus + 3, h->st));
+      matvec<T>(h, Uv, Wv, ev_take(h, RR_PROF_POWER));
+      RR_CUDA_TRY(power_proj<T>(1, Wv, Vv, (const T*)h->Q, h->kk[kG], n, h->k, mp, Gp,
+                                h->fscratch, h->cs, h->bar, h->dstatus + 3, h->st));
+    }
+    int err = 0;
+    RR_TRY(read_int(h, h->dstatus + 3, &err));
+    if (err) return RR_ERR_TIMEOUT;
+    RR_TRY(read_cs(h));
+    h->normE = h->cs_host[0].lam;
+    h->lam_max = h->cs_host[1].lam;
+    return RR_OK;
+  }
   for (int it = 0; it < h->o.power_iters; ++it) {
     qt<T>(h, Vv, h->t[0], false);
     // column 0: -Q^T v (-> (I - Pi) v); column 1: G Q^T v (-> Q G Q^T v)

@@ -102,6 +102,15 @@ template <typename T>
 cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const T* QH, int64_t n,
                      int k, int mp, int G, int alpha_mode, double* scratch, ColState* cs,
                      GridBar* bar, int* err, cudaStream_t st);
+// power iterations of variant C in two persistent launches per iteration
+// (mode 0: U = (I - Pi) V | Q G Q^T V; mode 1: V = normalised (I - Pi) W | Pi W
+// with lam = the norms in cs); scratch: power_proj_scratch_doubles(k), zero
+// before the first launch
+size_t power_proj_scratch_doubles(int k);
+template <typename T>
+cudaError_t power_proj(int mode, const T* X, T* Out, const T* Q, const double* Gm, int64_t n, int k,
+                       int mp, int G, double* scratch, ColState* cs, GridBar* bar, int* err,
+                       cudaStream_t st);
 // W = sum of split partials + mu V with alpha = rho / (p^T w) applied to cs
 // (variant C with the persistent step; V = p)
 template <typename T>
