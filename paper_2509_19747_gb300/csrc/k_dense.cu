@@ -465,6 +465,7 @@ void gram_upper(const double* Tm, int k, double* part, double* out, cudaStream_t
 // Blocked upper Cholesky  A = R^T R  (k x k float64, row-major, in place)
 // ======================================================================
 constexpr int kNb = 32;
+constexpr int kTriPerThread = 3;   // ceil(32 * 33 / 2 / 256)
 
 // Factor the diagonal block A[j0:j0+jb, j0:j0+jb] and write its inverse to
 // winv (jb x jb, row-major, upper).  Float64 division and square root are
@@ -483,6 +484,17 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int 
     const int r = e / jb, c = e % jb;
     S[r][c] = A[(int64_t)(j0 + r) * k + j0 + c];
   }
+  // this thread's elements (i, q), i <= q, of the 32 x 32 upper triangle,
+  // numbered row by row (528 elements over 256 threads)
+  int ti[kTriPerThread], tq[kTriPerThread];
+#pragma unroll
+  for (int u = 0; u < kTriPerThread; ++u) {
+    const int e = tid + u * 256;
+    int i = 0, rest = e;
+    while (i < kNb && rest >= kNb - i) { rest -= kNb - i; ++i; }
+    ti[u] = i < kNb ? i : kNb;          // kNb: no element
+    tq[u] = i < kNb ? i + rest : kNb;
+  }
   __syncthreads();
   for (int p = 0; p < jb; ++p) {
     // the pivot (one float64 reciprocal square root, by one thread)
@@ -499,18 +511,11 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int 
     for (int q = p + 1 + tid; q < jb; q += blockDim.x) S[p][q] *= r;
     __syncthreads();
     // trailing update of the upper part: S[i][q] -= S[p][i] S[p][q] for
-    // p < i <= q, enumerated over the upper triangle only (e -> (i, q))
-    const int rem = jb - p - 1;
-    const int tri = rem * (rem + 1) / 2;
-    for (int e = tid; e < tri; e += blockDim.x) {
-      // row-major upper-triangle index: row a has rem - a entries
-      int a = (int)((2.0f * rem + 1.0f - sqrtf((2.0f * rem + 1.0f) * (2.0f * rem + 1.0f) - 8.0f * e)) * 0.5f);
-      if (a < 0) a = 0;
-      while (a > 0 && a * (2 * rem - a + 1) / 2 > e) --a;
-      while ((a + 1) * (2 * rem - a) / 2 <= e) ++a;
-      const int b = e - a * (2 * rem - a + 1) / 2 + a;
-      const int i = p + 1 + a, q = p + 1 + b;
-      S[i][q] -= S[p][i] * S[p][q];
+    // p < i <= q, each thread keeping its fixed elements of the triangle
+#pragma unroll
+    for (int u = 0; u < kTriPerThread; ++u) {
+      const int i = ti[u], q = tq[u];
+      if (i > p && i < jb && q < jb) S[i][q] -= S[p][i] * S[p][q];
     }
     __syncthreads();
   }
