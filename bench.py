@@ -73,6 +73,8 @@ def parse():
                     choices=["gaussian", "srht", "multilevel", "sparse_sign"],
                     help="test matrix (default: Gaussian for the kernel ridge workload, "
                          "sparse sign for the sparse diffusion workload)")
+    ap.add_argument("--variant", default="C", choices=["C", "R"],
+                    help="sparse diffusion: preconditioner variant (basis-less C or R)")
     ap.add_argument("--refine", action="store_true",
                     help="kernel ridge: refined projector (rr_build_opts.refine)")
     ap.add_argument("--kernel-impl", type=int, default=0,
@@ -530,6 +532,7 @@ def run_sparse(args):
     o.gamma_sk = cfg["gamma_sk"]
     o.profile = 1
     sketch = args.sketch or "sparse_sign"
+    o.variant = rr.VARIANTS[args.variant]
     rr.set_multilevel(o, sketch, C.n, cfg["k"])
     ws_bytes = rr.randrand_workspace_bytes(op.c, cfg["k"], o)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
@@ -597,6 +600,7 @@ def run_sparse(args):
                  world * 1000.0 / ms, "solves/s", ms,
                  {**{kk: cfg[kk] for kk in ("workload", "side", "n", "k", "l_sk", "mu", "rtol",
                                             "precision", "orth")},
+                  "variant": args.variant,
                   "sketch": sketch if sketch != "multilevel"
                   else f"multilevel (l1 = {o.ml_l1}, gamma1 = {o.ml_gamma})",
                   "parallelism": f"replicas x{world}", "l2": "flushed between steps"},

@@ -102,9 +102,11 @@ enum {
                                Cholesky QR of S, W = Y_mu R_sk^-1, R = chol(W^T W) R_sk.
                                With a CSR operator no basis is kept (Sec. 4.2
                                basis-less form: Q^T v = R^-T Omega^T A_mu v and
-                               Q s = A_mu Omega R^-1 s; C variant only, three
-                               products with A_mu per iteration); other operators
-                               form Q = W chol(W^T W)^-1. */
+                               Q s = A_mu Omega R^-1 s; variant C with three
+                               products with A_mu per iteration, variant R with
+                               five and four for the recovery; variant G:
+                               RR_ERR_UNSUPPORTED); other operators form
+                               Q = W chol(W^T W)^-1. */
 };
 
 /*

@@ -161,9 +161,9 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
     const int64_t l = o.l_sk > 0 ? o.l_sk : 4 * (int64_t)k;
     if (l < k || l > (int64_t)INT32_MAX / 2 || o.gamma_sk > l) return RR_ERR_INVALID_ARG;
     if (basis_less(*A, o)) {
-      // the preconditioner of Alg. 4 needs Q^T p, Q t and Pi p per step: not
-      // provided without a basis
-      if (o.variant != RR_VARIANT_C) return RR_ERR_UNSUPPORTED;
+      // variants C and R: Q^T x = R^-T Omega^T A_mu x and Q s = A_mu Omega
+      // R^-1 s; G-RandRAND's estimates use the basis itself
+      if (o.variant == RR_VARIANT_G) return RR_ERR_UNSUPPORTED;
       // the implicit Q applies Omega from its sparse pattern (q = 0 only)
       if (o.q != 0) return RR_ERR_UNSUPPORTED;
       // Omega^T v partials and Omega s stage k x m values in shared memory
@@ -900,6 +900,61 @@ rr_status power_iterations_implicit(rr_handle* h) {
   return RR_OK;
 }
 
+// Variant R without a basis (Sec. 4.2 with Alg. 4): with Q^T x = R^-T g_x,
+// g_x = Omega^T A_mu x, and Q s = A_mu Omega R^-1 s, Pi x = A_mu Omega Cinv g_x
+// (Cinv = R^-1 R^-T), so B x = (I - Pi) A_mu (I - Pi) x + tau Pi x =
+// w + A_mu Omega Cinv (tau g_x - g_w) with u = x + A_mu Omega (-Cinv g_x),
+// w = A_mu u: five products with A_mu.
+template <typename T>
+void apply_B_implicit(rr_handle* h, const T* X, T* Out, bool gated, const cudaEvent_t* ev) {
+  const int k = h->k, mp = h->mp;
+  T* S = vt<T>(h, kS);
+  T* V = vt<T>(h, kV);
+  T* U = vt<T>(h, kU);
+  T* Wv = vt<T>(h, kW);
+  const Coefs8 one = coefs_all(1.0);
+  amul<T>(h, X, nullptr, nullptr, S, gated, ev);
+  omega_t<T>(h, S, h->t[0], gated);                                           // g_x
+  kxk_apply(h->kk[kCinv], h->t[0], k, mp, coefs_all(0.0), coefs_all(-1.0), h->t[1], h->st);
+  omega_mul<T>(h, h->t[1], V, gated);
+  amul<T>(h, V, X, one.v, U, gated);                                          // u = (I - Pi) x
+  amul<T>(h, U, nullptr, nullptr, Wv, gated);                                 // w = A_mu u
+  amul<T>(h, Wv, nullptr, nullptr, S, gated);
+  omega_t<T>(h, S, h->t[2], gated);                                           // g_w
+  axpby<double, double, double>(h->t[0], coefs_all(h->tau), h->t[2], coefs_all(-1.0), h->t[1], k,
+                                mp, h->st);
+  kxk_apply(h->kk[kCinv], h->t[1], k, mp, coefs_all(0.0), one, h->t[2], h->st);
+  omega_mul<T>(h, h->t[2], V, gated);
+  amul<T>(h, V, Wv, one.v, Out, gated);                                       // B x
+}
+
+// x = P y = Omega R^-1 Q^T (tau y - A_mu (I - Pi) y) + (I - Pi) y (eq:APdef3)
+// without a basis: R^-1 Q^T z = Cinv Omega^T A_mu z; four products with A_mu
+template <typename T>
+void recover_R_implicit(rr_handle* h) {
+  const int64_t n = h->n;
+  const int k = h->k, mp = h->mp;
+  T* Ev = vt<T>(h, kE);
+  T* S = vt<T>(h, kS);
+  T* V = vt<T>(h, kV);
+  T* U = vt<T>(h, kU);
+  T* Wv = vt<T>(h, kW);
+  T* Zv = vt<T>(h, kZ);
+  const Coefs8 one = coefs_all(1.0);
+  amul<T>(h, Ev, nullptr, nullptr, S, false, ev_take(h, RR_PROF_MATVEC));
+  omega_t<T>(h, S, h->t[0], false);
+  kxk_apply(h->kk[kCinv], h->t[0], k, mp, coefs_all(0.0), coefs_all(-1.0), h->t[1], h->st);
+  omega_mul<T>(h, h->t[1], V, false);
+  amul<T>(h, V, Ev, one.v, U, false);                                         // u = (I - Pi) y
+  amul<T>(h, U, nullptr, nullptr, Wv, false);                                 // w = A_mu u
+  axpby<T, T, T>(Ev, coefs_all(h->tau), Wv, coefs_all(-1.0), Zv, n, mp, h->st);   // tau y - w
+  amul<T>(h, Zv, nullptr, nullptr, S, false);
+  omega_t<T>(h, S, h->t[0], false);
+  kxk_apply(h->kk[kCinv], h->t[0], k, mp, coefs_all(0.0), one, h->t[1], h->st);
+  omega_mul<T>(h, h->t[1], V, false);
+  axpby<T, T, T>(V, one, U, one, Ev, n, mp, h->st);                           // e = Omega s + u
+}
+
 // Cinv = R^-1 R^-T and Gb = R^-1 G R^-T (k x k float64)
 void implicit_core(rr_handle* h) {
   const int k = h->k;
@@ -1158,6 +1213,10 @@ rr_status finish_build(rr_handle* h, const double* G1given) {
     RR_TRY(sqrtm_spd(h, h->kk[kG]));
   }
   if (h->implicit) {
+    // variant R has no core matrix: G = 0 makes the lambda_max column of the
+    // shared power iterations a zero vector (only |E| is used)
+    if (h->o.variant == RR_VARIANT_R)
+      RR_CUDA_TRY(cudaMemsetAsync(h->kk[kG], 0, (size_t)k * k * 8, st));
     implicit_core(h);
     RR_TRY(power_iterations_implicit<T>(h));
   } else if (h->o.variant == RR_VARIANT_G) {
@@ -1175,7 +1234,8 @@ rr_status finish_build(rr_handle* h, const double* G1given) {
     // Hb = R^-1 (tau G - I) R^-T = tau Gb - Cinv
     axpby<double, double, double>(h->kk[kGb], coefs_all(h->tau), h->kk[kCinv], coefs_all(-1.0),
                                   h->kk[kHb], (int64_t)k * k, 1, st);
-    h->fusedG = (h->o.iter_impl == 0 && h->sketch == RR_SKETCH_SPARSE_SIGN)
+    h->fusedG = (h->o.iter_impl == 0 && h->sketch == RR_SKETCH_SPARSE_SIGN &&
+                 h->o.variant == RR_VARIANT_C)
                     ? pcg_implicit_ctas<T>(n, k, h->mp) : 0;
     if (h->fusedG > 0) RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
   } else if (h->o.variant == RR_VARIANT_C || h->o.variant == RR_VARIANT_G) {
@@ -1302,6 +1362,18 @@ void iter_C_implicit(rr_handle* h, const cudaEvent_t* ev) {
 template <typename T>
 void iter_R(rr_handle* h, const cudaEvent_t* ev);
 
+// CG on B y = r (Alg. 4) with the basis-less B
+template <typename T>
+void iter_R_implicit(rr_handle* h, const cudaEvent_t* ev) {
+  const int64_t n = h->n;
+  const int mp = h->mp;
+  T *Rv = vt<T>(h, kR), *Pv = vt<T>(h, kP), *Zv = vt<T>(h, kZ), *Ev = vt<T>(h, kE);
+  apply_B_implicit<T>(h, Pv, Zv, true, ev);                                   // B p
+  dot_cols<T>(Pv, Zv, n, mp, kModeAlpha, h->rpart, h->cnt, h->cs, true, nullptr, h->st);
+  update_cg<T>(Ev, Rv, Pv, Zv, n, mp, h->rpart, h->cnt, h->cs, h->st);        // y, r, beta
+  p_update<T>(Pv, Rv, n, mp, h->cs, false, h->st);                            // p = r + beta p
+}
+
 // One preconditioned MINRES step (variant G; the Lanczos / Givens form of
 // the oracle): Az = A_mu zs, delta = Az^T zs, v_next = Az - (delta / gamma) v
 // - (gamma / gamma_prev) v_prev, z = P v_next and gamma_next = (v^T z)^(1/2)
@@ -1332,7 +1404,8 @@ void iter_any(rr_handle* h, const cudaEvent_t* ev) {
   // the kernel-operator products skip their work once every column is done
   h->op.gate = h->cs;
   h->op.gate_mp = h->mp;
-  if (h->implicit) iter_C_implicit<T>(h, ev);
+  if (h->implicit && h->o.variant == RR_VARIANT_R) iter_R_implicit<T>(h, ev);
+  else if (h->implicit) iter_C_implicit<T>(h, ev);
   else if (h->o.variant == RR_VARIANT_C) iter_C<T>(h, ev);
   else if (h->o.variant == RR_VARIANT_G) iter_G<T>(h, ev);
   else iter_R<T>(h, ev);
@@ -1490,7 +1563,8 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
       }
     if (any_zero) axpby<double, double, double>(X, keep, nullptr, coefs_all(0.0), X, n, mp, st);
   }
-  const int mv_per_iter = h->implicit ? 3 : 1;
+  const bool isR = h->o.variant == RR_VARIANT_R;
+  const int mv_per_iter = h->implicit ? (isR ? 5 : 3) : 1;
   for (int restart = 0; restart <= kMaxRestarts; ++restart) {
     if (restart == 0 && !x_guess) {
       RR_CUDA_TRY(cudaMemcpyAsync(R64, B, (size_t)n * mp * 8, cudaMemcpyDeviceToDevice, st));
@@ -1526,7 +1600,7 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
     T* Ev = vt<T>(h, kE);
     axpby<double, double, T>(R64, coefs_all(1.0), nullptr, coefs_all(0.0), Rv, n, mp, st);
     RR_CUDA_TRY(cudaMemsetAsync(Ev, 0, (size_t)n * mp * sizeof(T), st));
-    if (h->implicit) {
+    if (h->implicit && h->o.variant == RR_VARIANT_C) {
       precond_implicit<T>(h, Rv, vt<T>(h, kZ), false, nullptr);
       dot_cols<T>(Rv, vt<T>(h, kZ), n, mp, kModeRhoInit, h->rpart, h->cnt, h->cs, false, nullptr, st);
       p_update<T>(vt<T>(h, kP), vt<T>(h, kZ), n, mp, h->cs, true, st);
@@ -1558,11 +1632,15 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
       if (done[c] || !rp.active[c]) continue;
       const ColState& s = h->cs_host[c];
       used[c] += s.iters;
-      mv[c] += s.iters * mv_per_iter + (h->o.variant == RR_VARIANT_R ? 1 : 0) + (h->implicit ? 2 : 0);
+      mv[c] += s.iters * mv_per_iter + (isR ? (h->implicit ? 4 : 1) : 0) +
+               (h->implicit && !isR ? 2 : 0);
       outer[c] += 1;
       if (s.status == RR_ERR_BREAKDOWN && s.iters == 0) { done[c] = true; stat[c] = RR_ERR_BREAKDOWN; }
     }
-    if (h->o.variant == RR_VARIANT_R) recover_R<T>(h);
+    if (h->o.variant == RR_VARIANT_R) {
+      if (h->implicit) recover_R_implicit<T>(h);
+      else recover_R<T>(h);
+    }
     // x += e for the columns that ran (e = 0 elsewhere)
     axpby<double, T, double>(X, coefs_all(1.0), Ev, coefs_all(1.0), X, n, mp, st);
   }
@@ -1610,7 +1688,9 @@ void apply_impl(rr_handle* h) {
   const int mp = h->mp, k = h->k;
   T *Rv = vt<T>(h, kR), *Zv = vt<T>(h, kZ), *Uv = vt<T>(h, kU), *Wv = vt<T>(h, kW);
   axpby<double, double, T>(h->v64[kR64], coefs_all(1.0), nullptr, coefs_all(0.0), Rv, n, mp, h->st);
-  if (h->implicit) {
+  if (h->implicit && h->o.variant == RR_VARIANT_R) {
+    apply_B_implicit<T>(h, Rv, Zv, false, nullptr);
+  } else if (h->implicit) {
     precond_implicit<T>(h, Rv, Zv, false, nullptr);
   } else if (h->o.variant == RR_VARIANT_C || h->o.variant == RR_VARIANT_G) {
     precond_C<T>(h, Rv, Zv, kModeNone);

@@ -142,11 +142,53 @@ def test_basis_less_solve(cuda_lib, precision):
         assert rel(x.cpu().numpy(), xs) <= 1e-7
 
 
-def test_basis_less_variant_R_unsupported(cuda_lib):
+@pytest.mark.parametrize("sketch", ["sparse_sign", "gaussian"])
+def test_basis_less_variant_R_fp64(cuda_lib, sketch):
+    """Variant R (Alg. 4) without a basis: tau = |E| and R equal the oracle's
+    Alg. 3 build; B p (five products with A_mu) equals the oracle's
+    (I - Pi) A_mu (I - Pi) p + tau Pi p; after fixed inner budgets the
+    recovered iterate equals the oracle's."""
+    rr = cuda_lib
+    C, op, vals = csr_problem(24, 45)
+    mu, k = 1e-4, 40
+    h = csr_handle(rr, C, vals, mu, k, sketch, 45, variant="R", max_rhs=3)
+    bd = O.build(op, mu, k, sketch, seed=45, orth="qless", variant="R")
+    cond = np.linalg.cond(bd.R)
+    assert rel(h.export("R").cpu().numpy(), bd.R) <= max(1e-12, 1e-15 * cond) * 100
+    tau, nE, _ = h.scalars()
+    assert nE == pytest.approx(bd.normE, rel=1e-8)
+    assert tau == pytest.approx(bd.tau, rel=1e-8)
+    r = np.random.default_rng(6).standard_normal((C.n, 3))
+    assert rel(h.apply(dev(r)).cpu().numpy(), bd.apply_B(r)) <= max(1e-12, 1e-15 * cond ** 2) * 100
+    B = W.gaussian_rhs(C.n, 3, 45)
+    for budget in (3, 12):
+        x, status, infos = h.solve(dev(B), rtol=1e-14, maxit=budget)
+        xo, oinfo = O.solve(bd, B, rtol=1e-14, maxit=budget)
+        assert [i["inner_iters"] for i in infos] == [i.inner_iters for i in oinfo]
+        assert rel(x.cpu().numpy(), xo) <= 1e-9
+    x, status, infos = h.solve(dev(B), rtol=1e-12, maxit=20000)
+    assert status == rr.RR_OK
+    assert rel(x.cpu().numpy(), O.exact_solve(op, mu, B)) <= 1e-7
+    assert all(i["matvecs"] >= 5 * i["inner_iters"] for i in infos)
+
+
+def test_basis_less_variant_R_mixed(cuda_lib):
+    rr = cuda_lib
+    C, op, vals = csr_problem(40, 46, fp64=False)
+    mu, k = 1e-6, 32
+    b = W.gaussian_rhs(C.n, 2, 46)
+    h = csr_handle(rr, C, vals, mu, k, "sparse_sign", 46, variant="R", precision="mixed",
+                   max_rhs=2)
+    x, status, infos = h.solve(dev(b), rtol=1e-6, maxit=20000)
+    assert status == rr.RR_OK
+    assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), b) <= 1e-6)
+
+
+def test_basis_less_variant_G_unsupported(cuda_lib):
     rr = cuda_lib
     C, op, vals = csr_problem(16, 45)
     with pytest.raises(rr.RandRandError):
-        csr_handle(rr, C, vals, 1e-4, 8, "sparse_sign", 45, variant="R")
+        csr_handle(rr, C, vals, 1e-4, 8, "sparse_sign", 45, variant="G")
 
 
 def test_sparse_operator_full_size(cuda_lib):
