@@ -74,7 +74,7 @@ def parse():
                     help="test matrix (default: Gaussian for the kernel ridge workload, "
                          "sparse sign for the sparse diffusion workload)")
     ap.add_argument("--variant", default="C", choices=["C", "R"],
-                    help="sparse diffusion: preconditioner variant (basis-less C or R)")
+                    help="kernel ridge and sparse diffusion: preconditioner variant")
     ap.add_argument("--refine", action="store_true",
                     help="kernel ridge: refined projector (rr_build_opts.refine)")
     ap.add_argument("--kernel-impl", type=int, default=0,
@@ -247,6 +247,7 @@ def run_reference(args):
 def run_ours(args):
     import torch
     WORKLOAD["sketch"] = args.sketch or "gaussian"
+    WORKLOAD["variant"] = args.variant
 
     rank, world, local = dist_init(args)
     torch.cuda.set_device(local)
