@@ -391,14 +391,16 @@ def run_plain(rr, torch, op, m, k, seed, Bc, maxit=4000):
 
 
 def estimate_launches(prof):
-    # our kernels per solve, counted from the profile's launch counts: the
-    # product kernels plus the fixed per-iteration companions (8 per PCG
-    # iteration with the kernel operator, ~10 per power iteration, ~60 for the
-    # build's factorisations)
+    # our kernels per solve, counted from the profile's launch counts: each
+    # PCG product with the persistent step after it (2), each power-iteration
+    # product with its two projection launches (3), each restart residual with
+    # its split sum and updates (4), and ~150 for the rest of the build
+    # (sketch, Cholesky QR panels, core matrix); the one-step launch list of
+    # this workload (profiles/launches_kernel_ridge_n20000_k500.md) counts 623
     total = 0
     for p, infos in prof:
-        mv = p["matvec"][0]
-        total += mv * 8 + p["power"][0] * 10 + p["residual"][0] * 4 + 60 + p["sketch"][0]
+        total += (p["matvec"][0] * 2 + p["power"][0] * 3 + p["residual"][0] * 4 + 150 +
+                  p["sketch"][0])
     return total
 
 
