@@ -51,7 +51,7 @@ METRIC = "RandRAND-PCG solves/s to rtol 1e-6 vs plain form on 1 GB300; p50/p99 l
 # stands (summaries in profiles/: k_kernel_mv_tc_kernel_ridge_n20000.md,
 # k_pcg_implicit_sparse_diffusion_512.md, the latter per iteration of a
 # 256-iteration launch)
-TRAFFIC = {"k_kernel_mv_tc": 5.534464e6, "k_pcg_implicit": (28.928768e6 + 1.673472e6) / 256}
+TRAFFIC = {"k_kernel_mv_tc": 5.542656e6, "k_pcg_implicit": (28.929024e6 + 1.674240e6) / 256}
 L2_FLUSH_BYTES = 512 << 20
 
 
