@@ -47,13 +47,15 @@ def test_tiny_basis_less_csr(cuda_lib, side, variant, sketch):
     rr = cuda_lib
     C = W.diffusion_csr(side=side, seed=140 + side, corr_len=1.0)
     op = O.CsrOp(C.rowptr, C.colidx, C.vals, C.n)
-    # k = n - 1, except for the zero-padded SRHT (n = 9, 16 rows of H: rows r
-    # and r ^ 8 differ in one of the nine coordinates), which draws n / 2
-    k = max(1, C.n // 2) if sketch == "srht" else max(1, C.n - 1)
+    # k = n / 2: with k close to n the test matrices are nearly singular on
+    # these few points (a dense sign Omega when gamma = k; the zero-padded
+    # SRHT at n = 9, whose rows r and r ^ 8 differ in one coordinate), and the
+    # build's float64 Cholesky then fails or not at rounding level
+    k = max(1, C.n // 2)
     b = W.gaussian_rhs(C.n, 1, 140)
     h = rr.Handle(rr.Operator.csr(dev(C.rowptr), dev(C.colidx), dev(C.vals.astype(np.float64))),
                   1e-3, k, sketch, seed=140 + side, orth="rand_cholqr", variant=variant,
-                  gamma=min(8, k), l_sk=max(k, 4), gamma_sk=min(8, max(k, 4)))
+                  gamma=min(8, k), gamma_sk=min(8, 4 * k))
     x, status, infos = h.solve(dev(b), rtol=1e-10)
     assert status == rr.RR_OK
     assert O.true_rel_residual(op, 1e-3, x.cpu().numpy(), b)[0] <= 1e-10
