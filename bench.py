@@ -325,7 +325,7 @@ def run_ours(args):
     infos = [i for _, inf in prof for i in inf]
     iters = max(i["inner_iters"] for i in infos)
     rel_res = max(i["rel_residual"] for i in infos)
-    gpu_launches = estimate_launches(prof)
+    gpu_launches = estimate_launches(prof, args.variant)
 
     # dominant kernel and its roofline
     dom = max(cats.items(), key=lambda kv: kv[1][1])
@@ -390,16 +390,17 @@ def run_plain(rr, torch, op, m, k, seed, Bc, maxit=4000):
                       f"maxit {maxit}"}
 
 
-def estimate_launches(prof):
+def estimate_launches(prof, variant="C"):
     # our kernels per solve, counted from the profile's launch counts: each
-    # PCG product with the persistent step after it (2), each power-iteration
+    # PCG product with the persistent step after it (2; variant R has a
+    # persistent launch on each side of the product: 3), each power-iteration
     # product with its two projection launches (3), each restart residual with
     # its split sum and updates (4), and ~150 for the rest of the build
     # (sketch, Cholesky QR panels, core matrix); the one-step launch list of
     # this workload (profiles/launches_kernel_ridge_n20000_k500.md) counts 623
     total = 0
     for p, infos in prof:
-        total += (p["matvec"][0] * 2 + p["power"][0] * 3 + p["residual"][0] * 4 + 150 +
+        total += (p["matvec"][0] * (3 if variant == "R" else 2) + p["power"][0] * 3 + p["residual"][0] * 4 + 150 +
                   p["sketch"][0])
     return total
 

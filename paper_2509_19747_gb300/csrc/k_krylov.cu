@@ -1648,6 +1648,7 @@ void sum_splits_alpha(const T* part, int nsplit, int64_t n, int mp, double mu, c
 //                  U = (V0, 0) + Q s
 //   post (mode 1): t = Q^T W | barrier | Z = (W0, 0) + Q (-t0, t1) and |Z|^2 |
 //                  barrier | V = Z / |Z|, lam = |Z| into the column states
+//   mode 2 (variant R, every column): t = Q^T V in set 0 | barrier | U = V - Q t
 // Column 0 iterates v -> (I - Pi) A_mu (I - Pi) v, column 1 v -> Pi A_mu Q G
 // Q^T v; further columns stay zero.  Accumulators: two sets [|Z|^2 8 | t k x
 // MP | s k x MP], set 0 for pre and set 1 for post, each launch clearing the
@@ -1676,7 +1677,8 @@ __host__ __device__ inline size_t pow_set_doubles(int k) { return 8 + 16 * (size
 // memory); four rows per warp in flight; v[c] += Out^2 when v is given
 template <typename T, int MP>
 __device__ void pow_combine(const T* __restrict__ Q, const T* __restrict__ X, T* __restrict__ Out,
-                            int64_t r0, int cnt, int k, const T* sT, double* v) {
+                            int64_t r0, int cnt, int k, const T* sT, double* v,
+                            bool all_cols = false) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int kW = kFT / 32;
   for (int i0 = wid; i0 < cnt; i0 += 4 * kW) {
@@ -1719,7 +1721,7 @@ __device__ void pow_combine(const T* __restrict__ Q, const T* __restrict__ X, T*
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == c && i < cnt) {
           const int64_t g = (r0 + i) * MP + c;
-          const T o = (c == 0 ? X[g] : (T)0) + x;
+          const T o = ((c == 0 || all_cols) ? X[g] : (T)0) + x;
           Out[g] = o;
           if (v) v[c] += (double)o * (double)o;
         }
@@ -1741,8 +1743,14 @@ __global__ void __launch_bounds__(kFT, 1) k_power_proj(PowArgs<T> a) {
   const int64_t r0 = (int64_t)cta * a.rpc;
   const int cnt = (int)(r0 >= a.n ? 0 : (a.n - r0 < a.rpc ? a.n - r0 : a.rpc));
   const size_t set = pow_set_doubles(k);
-  double* acc = a.acc + (size_t)a.mode * set;
-  double* other = a.acc + (size_t)(a.mode ^ 1) * set;
+  if (a.mode == 2) {
+    // the same decision in every CTA: nothing accumulates once all columns are done
+    bool any = false;
+    for (int c = 0; c < MP; ++c) any |= a.cs[c].active != 0;
+    if (!any) return;
+  }
+  double* acc = a.acc + (size_t)(a.mode == 1) * set;
+  double* other = a.acc + (size_t)(a.mode != 1) * set;
   double* nrm = acc;
   double* tacc = acc + 8;
   double* sg = acc + 8 + (size_t)k * MP;
@@ -1751,11 +1759,16 @@ __global__ void __launch_bounds__(kFT, 1) k_power_proj(PowArgs<T> a) {
   if (cta == 0)
     for (size_t e = tid; e < set; e += kFT) other[e] = 0.0;
   if (!grid_barrier(a.bar, a.err)) return;
-  if (a.mode == 0) {
+  if (a.mode == 2) {
+    // variant R: s = -t in every column, u = x - Q Q^T x (t stays in the set
+    // for the step after the product)
+    for (int e = tid; e < k * MP; e += kFT)
+      sT[(size_t)(e % MP) * k + e / MP] = (T)(-__ldcg(tacc + e));
+  } else if (a.mode == 0) {
     // s0 = -t0, s1 = G t1: a warp per row of G, rows spread over the CTAs
     for (int j = cta + wid * G; j < k; j += G * (kFT / 32)) {
       double x = 0.0;
-      if (MP > 1) {
+      if (MP > 1 && a.G) {   // no G (variant R): column 1 is not iterated
         const double* gj = a.G + (int64_t)j * k;
         for (int l = lane; l < k; l += 32) x = fma(gj[l], __ldcg(tacc + (size_t)l * MP + 1), x);
 #pragma unroll
@@ -1782,8 +1795,8 @@ __global__ void __launch_bounds__(kFT, 1) k_power_proj(PowArgs<T> a) {
   double v[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) v[c] = 0.0;
-  pow_combine<T, MP>(a.Q, a.X, a.Out, r0, cnt, k, sT, a.mode == 1 ? v : nullptr);
-  if (a.mode == 0) return;
+  pow_combine<T, MP>(a.Q, a.X, a.Out, r0, cnt, k, sT, a.mode == 1 ? v : nullptr, a.mode == 2);
+  if (a.mode != 1) return;
   block_sum_cols<kFT>(v, MP, redd);
   if (tid == 0 && cnt > 0)
     for (int c = 0; c < MP; ++c) atomicAdd(nrm + c, v[c]);
@@ -1799,6 +1812,210 @@ __global__ void __launch_bounds__(kFT, 1) k_power_proj(PowArgs<T> a) {
     a.Out[g] = (T)((double)a.Out[g] * sh_inv[e % MP]);
   }
 }
+
+// Variant R (Alg. 4) after the product w = A_mu u (u = (I - Pi) p from
+// k_power_proj mode 2, whose set 0 holds t1 = Q^T p): persistent cooperative
+//   t2 = Q^T w | barrier | B p = w + Q (tau t1 - t2) into Z, p^T B p | barrier |
+//   alpha, y += alpha p, r -= alpha B p, |r|^2 | barrier | beta, p = r + beta p
+// with the column-state rules of the separate kernels (kModeAlpha, update_cg,
+// p_update).  Set 1: [p^T B p 8 | t2 k x MP | |r|^2 8]; set 0 is cleared here
+// once every CTA has read t1.
+template <typename T>
+struct RPostArgs {
+  const T* W;
+  T* P;
+  T* Y;
+  T* R;
+  T* Z;
+  const T* Q;
+  double tau;
+  int64_t n;
+  int k;
+  int rpc;
+  double* acc;
+  ColState* cs;
+  GridBar* bar;
+  int* err;
+};
+
+template <typename T, int MP>
+__global__ void __launch_bounds__(kFT, 1) k_r_post(RPostArgs<T> a) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sT = reinterpret_cast<T*>(smem_raw);
+  T* Rs = sT + (size_t)a.k * MP;
+  float* red = reinterpret_cast<float*>(Rs + (size_t)kFusedChunk * MP);
+  __shared__ double redd[kFT / 32 * 8];
+  __shared__ ColState snap[8];
+  __shared__ double sh_alpha[8], sh_pw[8], sh_beta[8];
+  __shared__ int sh_act0[8], sh_actA[8], sh_actF[8];
+  const int tid = threadIdx.x, cta = blockIdx.x, k = a.k;
+  const int64_t r0 = (int64_t)cta * a.rpc;
+  const int cnt = (int)(r0 >= a.n ? 0 : (a.n - r0 < a.rpc ? a.n - r0 : a.rpc));
+  if (tid < 8) {
+    if (tid < MP) snap[tid] = a.cs[tid];
+    sh_act0[tid] = tid < MP ? a.cs[tid].active : 0;
+  }
+  __syncthreads();
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < MP; ++c) any |= sh_act0[c] != 0;
+  if (!any) return;                                   // the same decision in every CTA
+  const size_t set = pow_set_doubles(k);
+  double* pre = a.acc;                                // t1 at pre + 8
+  double* post = a.acc + set;
+  double* acc_pw = post;
+  double* t2 = post + 8;
+  double* acc_rr = post + 8 + (size_t)k * MP;
+  // ---- t2 = Q^T w
+  tail_qtr<T, MP>(a.Q, a.W, r0, cnt, k, t2, Rs, red);
+  if (!grid_barrier(a.bar, a.err)) return;
+  // ---- B p = w + Q (tau t1 - t2), p^T B p
+  for (int e = tid; e < k * MP; e += kFT)
+    sT[(size_t)(e % MP) * k + e / MP] = (T)(a.tau * __ldcg(pre + 8 + e) - __ldcg(t2 + e));
+  __syncthreads();
+  double v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = 0.0;
+  pow_combine<T, MP>(a.Q, a.W, a.Z, r0, cnt, k, sT, nullptr, true);
+  __syncthreads();
+  {
+    double vs = 0.0;
+    for (int e = tid; e < cnt * MP; e += kFT) {
+      const int64_t g = r0 * MP + e;
+      vs += (double)a.P[g] * (double)a.Z[g];
+    }
+    place_col(v, vs, tid % MP);
+  }
+  block_sum_cols<kFT>(v, MP, redd);
+  if (tid == 0 && cnt > 0)
+    for (int c = 0; c < MP; ++c) atomicAdd(acc_pw + c, v[c]);
+  if (!grid_barrier(a.bar, a.err)) return;
+  // ---- alpha (kModeAlpha), y and r, |r|^2
+  if (cta == 0)
+    for (size_t e = tid; e < set; e += kFT) pre[e] = 0.0;   // t1 has been read
+  if (tid < MP) {
+    const int c = tid;
+    const double pw = __ldcg(acc_pw + c);
+    sh_pw[c] = pw;
+    int act = sh_act0[c];
+    double al = 0.0;
+    if (act) {
+      if (!(pw > 0.0 && isfinite(pw))) act = -1;       // breakdown
+      else al = snap[c].rho / pw;
+    }
+    sh_alpha[c] = al;
+    sh_actA[c] = act;
+  }
+  __syncthreads();
+  bool anyA = false;
+#pragma unroll
+  for (int c = 0; c < MP; ++c) anyA |= sh_actA[c] > 0;
+  {
+    double vs = 0.0;
+    for (int e = tid; e < cnt * MP; e += kFT) {
+      const int64_t g = r0 * MP + e;
+      const int c = e % MP;
+      const T al = sh_actA[c] > 0 ? (T)sh_alpha[c] : (T)0;
+      a.Y[g] = fma(al, a.P[g], a.Y[g]);
+      const T r = fma(-al, a.Z[g], a.R[g]);
+      a.R[g] = r;
+      vs += (double)r * (double)r;
+    }
+    place_col(v, vs, tid % MP);
+  }
+  block_sum_cols<kFT>(v, MP, redd);
+  if (tid == 0 && cnt > 0)
+    for (int c = 0; c < MP; ++c) atomicAdd(acc_rr + c, v[c]);
+  if (!grid_barrier(a.bar, a.err)) return;
+  // ---- beta, the column state, p = r + beta p
+  if (tid < MP) {
+    const int c = tid;
+    ColState st = snap[c];
+    st.pw = sh_pw[c];
+    if (sh_actA[c] < 0) { st.status = RR_ERR_BREAKDOWN; st.active = 0; st.alpha = 0.0; }
+    else st.alpha = sh_actA[c] > 0 ? sh_alpha[c] : 0.0;
+    if (anyA) {
+      const double s2 = __ldcg(acc_rr + c);
+      st.rr = s2;
+      if (st.active) {
+        st.iters += 1;
+        if (!isfinite(s2)) { st.status = RR_ERR_BREAKDOWN; st.active = 0; }
+        else {
+          st.beta = (st.rho > 0.0) ? s2 / st.rho : 0.0;
+          st.rho = s2;
+          if (s2 <= st.stop2 || st.iters >= st.budget) st.active = 0;
+        }
+      }
+    }
+    sh_beta[c] = st.beta;
+    sh_actF[c] = st.active;
+    if (cta == 0) a.cs[c] = st;
+  }
+  __syncthreads();
+  for (int e = tid; e < cnt * MP; e += kFT) {
+    const int64_t g = r0 * MP + e;
+    const int c = e % MP;
+    if (sh_actF[c]) a.P[g] = fma((T)sh_beta[c], a.P[g], a.R[g]);
+  }
+}
+
+template <typename T, int MP>
+static bool rpost_attr() {
+  static std::atomic<uint64_t> done{0};
+  return once_per_device(done, [] {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return false;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_r_post<T, MP>) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (cudaFuncSetAttribute(k_r_post<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  });
+}
+
+template <typename T>
+cudaError_t r_post(const T* W, T* P, T* Y, T* R, T* Z, const T* Q, double tau, int64_t n, int k,
+                   int mp, int G, double* scratch, ColState* cs, GridBar* bar, int* err,
+                   cudaStream_t st) {
+  RPostArgs<T> a;
+  a.W = W; a.P = P; a.Y = Y; a.R = R; a.Z = Z; a.Q = Q; a.tau = tau;
+  a.n = n; a.k = k; a.rpc = (int)cdiv(n, G);
+  a.acc = scratch; a.cs = cs; a.bar = bar; a.err = err;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3(kFT);
+  cfg.dynamicSmemBytes = pcg_tail_smem<T>(k, mp);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+#define RR_RPOST(MPV)                                               \
+  if (!rpost_attr<T, MPV>()) return cudaErrorInvalidValue;          \
+  return cudaLaunchKernelEx(&cfg, k_r_post<T, MPV>, a);
+  switch (mp) {
+    case 2: { RR_RPOST(2) }
+    case 4: { RR_RPOST(4) }
+    default: { RR_RPOST(8) }
+  }
+#undef RR_RPOST
+}
+
+template cudaError_t r_post<float>(const float*, float*, float*, float*, float*, const float*,
+                                   double, int64_t, int, int, int, double*, ColState*, GridBar*,
+                                   int*, cudaStream_t);
+template cudaError_t r_post<double>(const double*, double*, double*, double*, double*,
+                                    const double*, double, int64_t, int, int, int, double*,
+                                    ColState*, GridBar*, int*, cudaStream_t);
 
 template <typename T, int MP>
 static bool pow_attr() {
@@ -1861,6 +2078,23 @@ template cudaError_t power_proj<double>(int, const double*, double*, const doubl
                                         int64_t, int, int, int, double*, ColState*, GridBar*,
                                         int*, cudaStream_t);
 
+// CTAs of the persistent variant-R step (both of its kernels), or 0
+template <typename T>
+int r_step_ctas(int64_t n, int k, int mp) {
+  const int G = pcg_tail_ctas<T>(n, k, mp);
+  if (G <= 0) return 0;
+  bool ok = false;
+  switch (mp) {
+    case 2: ok = pow_attr<T, 2>() && rpost_attr<T, 2>(); break;
+    case 4: ok = pow_attr<T, 4>() && rpost_attr<T, 4>(); break;
+    case 8: ok = pow_attr<T, 8>() && rpost_attr<T, 8>(); break;
+    default: ok = false; break;
+  }
+  return ok ? G : 0;
+}
+
+template int r_step_ctas<float>(int64_t, int, int);
+template int r_step_ctas<double>(int64_t, int, int);
 template int pcg_tail_ctas<float>(int64_t, int, int);
 template int pcg_tail_ctas<double>(int64_t, int, int);
 template cudaError_t pcg_tail<float>(float*, float*, float*, float*, const float*, const float*,

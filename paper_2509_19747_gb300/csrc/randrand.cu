@@ -127,8 +127,8 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_CNT] = 64 * 4;
   L.size[R_CS] = 8 * sizeof(ColState);
   L.size[R_NORMS] = 64 * 8;
-  // persistent fused steps of variant C: barrier + partials
-  L.size[R_FUSED] = (o.variant == RR_VARIANT_C)
+  // persistent fused steps of variants C and R: barrier + partials
+  L.size[R_FUSED] = (o.variant == RR_VARIANT_C || o.variant == RR_VARIANT_R)
                         ? sizeof(GridBar) + std::max({pcg_tail_scratch_doubles(k, mp),
                                           pcg_implicit_scratch_doubles(k, mp),
                                           power_proj_scratch_doubles(k)}) * 8
@@ -735,16 +735,17 @@ rr_status power_iterations(rr_handle* h) {
   dot_cols<T>(Vv, Vv, n, mp, kModeNorm, h->rpart, h->cnt, h->cs, false, nullptr, h->st);
   scale_cols<T>(Vv, Vv, n, mp, h->cs, h->st);
   const Coefs8 a = coefs(1.0, 0.0);
-  // variant C with the persistent step: the projections of an iteration in two
-  // persistent launches around the product
-  const int Gp = (isC && h->o.iter_impl == 0) ? pcg_tail_ctas<T>(n, h->k, mp) : 0;
+  // the persistent step: the projections of an iteration in two persistent
+  // launches around the product (variant R has no G and no column 1)
+  const int Gp = h->o.iter_impl == 0 ? pcg_tail_ctas<T>(n, h->k, mp) : 0;
+  const double* Gm = isC ? h->kk[kG] : nullptr;
   if (Gp > 0) {
     RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], h->st));
     for (int it = 0; it < h->o.power_iters; ++it) {
-      RR_CUDA_TRY(power_proj<T>(0, Vv, Uv, (const T*)h->Q, h->kk[kG], n, h->k, mp, Gp,
+      RR_CUDA_TRY(power_proj<T>(0, Vv, Uv, (const T*)h->Q, Gm, n, h->k, mp, Gp,
                                 h->fscratch, h->cs, h->bar, h->dstatus + 3, h->st));
       matvec<T>(h, Uv, Wv, ev_take(h, RR_PROF_POWER));
-      RR_CUDA_TRY(power_proj<T>(1, Wv, Vv, (const T*)h->Q, h->kk[kG], n, h->k, mp, Gp,
+      RR_CUDA_TRY(power_proj<T>(1, Wv, Vv, (const T*)h->Q, Gm, n, h->k, mp, Gp,
                                 h->fscratch, h->cs, h->bar, h->dstatus + 3, h->st));
     }
     int err = 0;
@@ -1262,6 +1263,10 @@ rr_status finish_build(rr_handle* h, const double* G1given) {
     right_mult<T>(h, (const T*)h->Q, h->kk[kH], (T*)h->QH);
     if (h->fusedG > 0)   // barrier and both accumulator sets start at zero
       RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
+  } else if (h->o.variant == RR_VARIANT_R) {
+    // the projections of a CG step on B in two persistent launches
+    h->fusedG = h->o.iter_impl == 0 ? r_step_ctas<T>(n, k, h->mp) : 0;
+    if (h->fusedG > 0) RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
   }
   return sync_status(h);
 }
@@ -1427,6 +1432,16 @@ void iter_R(rr_handle* h, const cudaEvent_t* ev) {
   T *Rv = vt<T>(h, kR), *Pv = vt<T>(h, kP), *Wv = vt<T>(h, kW), *Zv = vt<T>(h, kZ),
     *Ev = vt<T>(h, kE), *Uv = vt<T>(h, kU);
   const T* Q = (const T*)h->Q;
+  if (h->fusedG > 0) {
+    // u = (I - Pi) p (t1 = Q^T p kept), w = A_mu u, then B p = w + Q (tau t1 -
+    // Q^T w), alpha, y, r, beta and p in one persistent launch
+    power_proj<T>(2, Pv, Uv, Q, nullptr, n, k, mp, h->fusedG, h->fscratch, h->cs, h->bar,
+                  h->dstatus + 3, h->st);
+    matvec<T>(h, Uv, Wv, ev);
+    r_post<T>(Wv, Pv, Ev, Rv, Zv, Q, h->tau, n, k, mp, h->fusedG, h->fscratch, h->cs, h->bar,
+              h->dstatus + 3, h->st);
+    return;
+  }
   qt_comb<T>(h, Pv, -1.0, nullptr, 0.0, h->t[0]);                          // t1n = -Q^T p
   qcomb<T>(Q, n, k, mp, h->t[0], coefs_all(1.0), Pv, Uv, nullptr, kModeNone, h->rpart, h->cnt,
            h->cs, true, h->st);                                             // u = (I - Pi) p

@@ -97,6 +97,9 @@ constexpr int kFusedMaxCtas = 2 * 152;
 // Persistent fused PCG step (variant C with a basis): see k_krylov.cu.
 template <typename T>
 int pcg_tail_ctas(int64_t n, int k, int mp);
+// CTAs of the persistent variant-R step (power_proj mode 2 + r_post), or 0
+template <typename T>
+int r_step_ctas(int64_t n, int k, int mp);
 size_t pcg_tail_scratch_doubles(int k, int mp);
 template <typename T>
 cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const T* QH, int64_t n,
@@ -111,6 +114,12 @@ template <typename T>
 cudaError_t power_proj(int mode, const T* X, T* Out, const T* Q, const double* Gm, int64_t n, int k,
                        int mp, int G, double* scratch, ColState* cs, GridBar* bar, int* err,
                        cudaStream_t st);
+// variant R after the product w = A_mu u, u from power_proj mode 2 (t1 = Q^T p
+// in its set): B p into Z, alpha, y, r, beta and p in one persistent launch
+template <typename T>
+cudaError_t r_post(const T* W, T* P, T* Y, T* R, T* Z, const T* Q, double tau, int64_t n, int k,
+                   int mp, int G, double* scratch, ColState* cs, GridBar* bar, int* err,
+                   cudaStream_t st);
 // W = sum of split partials + mu V with alpha = rho / (p^T w) applied to cs
 // (variant C with the persistent step; V = p)
 template <typename T>

@@ -412,11 +412,18 @@ def test_kernel_impl_out_of_range(cuda_lib):
 
 
 # ------------------------------------------- persistent fused PCG step
+@pytest.mark.parametrize("variant", ["C", "R"])
 @pytest.mark.parametrize("m", [1, 3, 8])
-def test_fused_step_matches_separate_kernels_fp64(cuda_lib, m):
-    """The persistent cooperative PCG step (iter_impl 0) and the separate
-    kernels (iter_impl 1) take the same iterations and reach the same iterate
-    (their reductions group sums differently: rounding-level differences)."""
+def test_fused_step_matches_separate_kernels_fp64(cuda_lib, m, variant):
+    """The persistent cooperative step (iter_impl 0: the fused PCG step of
+    variant C; for variant R the two launches around the product) and the
+    separate kernels (iter_impl 1) take the same iterations and reach the same
+    iterate (their reductions group sums differently: rounding-level
+    differences), and both match the oracle's iterate.  Variant R stops on
+    |r| of plain CG on B, which is not monotone: near rtol 1e-13 a reordered
+    sum can move a crossing (of the restart threshold or of rtol) by a step,
+    and an extra restart adds a few; there the counts agree within 10 % and
+    the converged iterates to 1e-10."""
     rr = cuda_lib
     n, k, mu = 1025, 100, 1e-4
     P, op = dense_problem(n)
@@ -424,21 +431,26 @@ def test_fused_step_matches_separate_kernels_fp64(cuda_lib, m):
     out = []
     for impl in (0, 1):
         h = rr.Handle(rr.Operator.dense(dev(P.A)), mu, k, "gaussian", seed=61, max_rhs=m,
-                      iter_impl=impl)
+                      variant=variant, iter_impl=impl)
         for budget in (5, 40):
             x, status, infos = h.solve(dev(B), rtol=1e-13, maxit=budget)
             out.append((budget, x.cpu().numpy(), [i["inner_iters"] for i in infos]))
         h.close()
     for (b0, x0, i0), (b1, x1, i1) in zip(out[:2], out[2:]):
-        assert i0 == i1
-        assert rel(x0, x1) <= 1e-12
-    bd = O.build(op, mu, k, "gaussian", seed=61)
+        if variant == "C" or b0 == 5:
+            assert i0 == i1
+            assert rel(x0, x1) <= 1e-12
+        else:
+            assert all(abs(a - b) <= max(2, 0.1 * b) for a, b in zip(i0, i1)), (i0, i1)
+            assert rel(x0, x1) <= 1e-10
+    bd = O.build(op, mu, k, "gaussian", seed=61, variant=variant)
     xo, _ = O.solve(bd, B, rtol=1e-13, maxit=40)
     assert rel(out[1][1], xo) <= 1e-10
 
 
+@pytest.mark.parametrize("variant", ["C", "R"])
 @pytest.mark.parametrize("m", [1, 4])
-def test_fused_step_kernel_operator_mixed(cuda_lib, m):
+def test_fused_step_kernel_operator_mixed(cuda_lib, m, variant):
     """Float32 iterations with the fused step on the Gaussian-kernel operator:
     same iteration counts as the separate kernels within a few, and the float64
     residual meets rtol."""
@@ -450,7 +462,7 @@ def test_fused_step_kernel_operator_mixed(cuda_lib, m):
     its = []
     for impl in (0, 1):
         h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=62,
-                      precision="mixed", max_rhs=m, iter_impl=impl)
+                      precision="mixed", max_rhs=m, variant=variant, iter_impl=impl)
         x, status, infos = h.solve(dev(B), rtol=1e-6)
         assert status == rr.RR_OK
         assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), B) <= 1e-6)
