@@ -449,7 +449,7 @@ def test_fused_step_matches_separate_kernels_fp64(cuda_lib, m, variant):
 
 
 @pytest.mark.parametrize("variant", ["C", "R"])
-@pytest.mark.parametrize("m", [1, 4])
+@pytest.mark.parametrize("m", [1, 4, 8])
 def test_fused_step_kernel_operator_mixed(cuda_lib, m, variant):
     """Float32 iterations with the fused step on the Gaussian-kernel operator:
     same iteration counts as the separate kernels within a few, and the float64
@@ -570,3 +570,30 @@ def test_kernel_ridge_full_size(cuda_lib):
     assert np.all(est <= 3 * rtol)
     assert np.all(est <= 4 * rep + 1e-9) and np.all(rep <= 4 * est + 1e-9)
     h.close()
+
+
+@pytest.mark.parametrize("m", [2, 5])
+def test_variant_r_persistent_step_fp32_dense(cuda_lib, m):
+    """Variant R in float32 on a dense operator: the persistent launches
+    around the product and the separate kernels reach the same float32
+    iterate at a fixed budget (sums in another order: float32 rounding), and
+    plain float32 solve reaches a float32-level residual."""
+    rr = cuda_lib
+    n, k, mu = 1500, 120, 1e-3
+    P, op = dense_problem(n)
+    B = W.gaussian_rhs(n, m, 63)
+    A32 = P.A.astype(np.float32)
+    op32 = O.DenseOp(A32.astype(np.float64))
+    xs, its = [], []
+    for impl in (0, 1):
+        h = rr.Handle(rr.Operator.dense(dev(A32)), mu, k, "gaussian", seed=63,
+                      precision="fp32", variant="R", max_rhs=m, iter_impl=impl)
+        x, status, infos = h.solve(dev(B), rtol=1e-14, maxit=6)
+        xs.append(x.cpu().numpy())
+        its.append([i["inner_iters"] for i in infos])
+        x, status, infos = h.solve(dev(B), rtol=1e-4)
+        assert status == rr.RR_OK
+        assert np.all(O.true_rel_residual(op32, mu, x.cpu().numpy(), B) <= 2e-4)
+        h.close()
+    assert its[0] == its[1]
+    assert rel(xs[0], xs[1]) <= 1e-4
