@@ -592,13 +592,24 @@ __global__ void k_sum_splits(const T* __restrict__ part, int nsplit, int64_t n, 
 }
 
 static int kernel_nsplit(int64_t n) {
-  const int64_t rb = cdiv(n, kKmvRows);
-  int64_t s = cdiv(8 * 152, rb);  // ~8 CTAs of 128 threads per SM
-  if (s < 1) s = 1;
-  if (s > 64) s = 64;
-  const int64_t maxs = cdiv(n, kKmvTile);
-  if (s > maxs) s = maxs;
-  return (int)s;
+  // column splits s for the rb x s CTAs (~8 of 128 threads resident per SM):
+  // the fewest waves x columns per CTA, so that a last, nearly empty wave of
+  // CTAs does not double the time (n = 20000: 157 x 23 CTAs in 3 full waves
+  // instead of 157 x 8 in one full wave and 40 CTAs after it)
+  const int64_t rb = cdiv(n, kKmvRows), slots = 8 * 152;
+  int64_t maxs = cdiv(n, kKmvTile);
+  if (maxs > 64) maxs = 64;
+  int64_t best = 1, best_cost = -1;
+  for (int64_t s = 1; s <= maxs; ++s) {
+    const int64_t cps = cdiv(cdiv(n, s), kKmvTile) * kKmvTile;
+    if ((s - 1) * cps >= n) continue;          // an empty split
+    const int64_t cost = cdiv(rb * s, slots) * cps;
+    if (best_cost < 0 || cost < best_cost) {
+      best = s;
+      best_cost = cost;
+    }
+  }
+  return (int)best;
 }
 
 size_t op_matvec_scratch_elems(const OpDev& op, int mp) {
