@@ -422,18 +422,20 @@ def test_fused_step_matches_separate_kernels_fp64(cuda_lib, m, variant):
     differences), and both match the oracle's iterate.  Variant R stops on
     |r| of plain CG on B, which is not monotone: near rtol 1e-13 a reordered
     sum can move a crossing (of the restart threshold or of rtol) by a step,
-    and an extra restart adds a few; there the counts agree within 10 % and
-    the converged iterates to 1e-10."""
+    and an extra restart adds a few; near 1e-13 its recursive residual can
+    also stall at float64 rounding.  So variant R stops at rtol 1e-11, and
+    there the counts agree within 10 % and the converged iterates to 1e-10."""
     rr = cuda_lib
     n, k, mu = 1025, 100, 1e-4
     P, op = dense_problem(n)
     B = W.gaussian_rhs(n, m, 61)
+    rt = 1e-13 if variant == "C" else 1e-11
     out = []
     for impl in (0, 1):
         h = rr.Handle(rr.Operator.dense(dev(P.A)), mu, k, "gaussian", seed=61, max_rhs=m,
                       variant=variant, iter_impl=impl)
         for budget in (5, 40):
-            x, status, infos = h.solve(dev(B), rtol=1e-13, maxit=budget)
+            x, status, infos = h.solve(dev(B), rtol=rt, maxit=budget)
             out.append((budget, x.cpu().numpy(), [i["inner_iters"] for i in infos]))
         h.close()
     for (b0, x0, i0), (b1, x1, i1) in zip(out[:2], out[2:]):
@@ -444,7 +446,7 @@ def test_fused_step_matches_separate_kernels_fp64(cuda_lib, m, variant):
             assert all(abs(a - b) <= max(2, 0.1 * b) for a, b in zip(i0, i1)), (i0, i1)
             assert rel(x0, x1) <= 1e-10
     bd = O.build(op, mu, k, "gaussian", seed=61, variant=variant)
-    xo, _ = O.solve(bd, B, rtol=1e-13, maxit=40)
+    xo, _ = O.solve(bd, B, rtol=rt, maxit=40)
     assert rel(out[1][1], xo) <= 1e-10
 
 
