@@ -333,6 +333,16 @@ rr_status randrand_profile(rr_handle* h, rr_profile* out);
 rr_status randrand_scalars(const rr_handle* h, double* tau, double* normE, double* lam_max);
 
 /*
+ * Jitter of the last core-matrix factorization (variant C, remark after
+ * Alg. 7; App. C): 0 when M = sym(Omega^T A_mu Omega) factored as it is,
+ * else the alpha of the ladder, the smallest of 10^-14 |M|, ..., 10^-1 |M|
+ * for which M + alpha I factors, |M| the spectral norm of M (estimated by
+ * 30 power iterations on the k x k M).  Host only; *alpha is written.
+ * Errors: RR_ERR_INVALID_ARG (h or alpha NULL).
+ */
+rr_status randrand_core_jitter(const rr_handle* h, double* alpha);
+
+/*
  * Apply the preconditioner (variants C and G: z = P r, P = I + Q H Q^T with
  * H = tau G - I, the footnote form of Sec. 7.3, or H = tau T G T - T with
  * opts.refine) or the operator B of variant R

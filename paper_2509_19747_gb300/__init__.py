@@ -140,6 +140,7 @@ _SIGNATURES = [
     ("randrand_scalars", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
       ctypes.POINTER(ctypes.c_double)]),
+    ("randrand_core_jitter", ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("randrand_apply", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     ("randrand_profile", ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rr_profile)]),
@@ -281,6 +282,14 @@ def randrand_scalars(h) -> tuple[float, float, float]:
     if s != RR_OK:
         raise RandRandError(s, "randrand_scalars")
     return t.value, e.value, l.value
+
+
+def randrand_core_jitter(h) -> float:
+    a = ctypes.c_double()
+    s = _lib().randrand_core_jitter(h, ctypes.byref(a))
+    if s != RR_OK:
+        raise RandRandError(s, "randrand_core_jitter")
+    return a.value
 
 
 def randrand_apply(h, r_ptr, z_ptr, m, ld) -> None:
@@ -426,6 +435,9 @@ class Handle:
 
     def scalars(self):
         return randrand_scalars(self.h)
+
+    def core_jitter(self) -> float:
+        return randrand_core_jitter(self.h)
 
     def set_mu(self, mu: float):
         """Rebuild for another shift from the kept sketch (keep_sketch=True)."""

@@ -306,6 +306,7 @@ struct rr_handle {
   double* norms_host; // pinned
   // scalars
   double tau, normE, lam_max;
+  double jitter;      // alpha of the App. C ladder in the last core matrix (0: none)
   // captured iteration graphs (per mp width)
   cudaGraphExec_t graph;
   bool graph_ok;
@@ -511,12 +512,6 @@ __global__ void k_trace(const double* A, int k, double* out) {
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (threadIdx.x == 0) *out = s;
 }
-__global__ void k_maxdiag(const double* A, int k, double* out) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) s = fmax(s, fabs(A[(int64_t)i * k + i]));
-  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-  if (threadIdx.x == 0) *out = s;
-}
 
 // CholeskyQR2 of Y_mu (Sec. 4.2 Alg. 2 applied twice): Q = Y R^-1, R upper
 // with positive diagonal.  If the first Gram is numerically singular, a
@@ -676,24 +671,120 @@ rr_status rand_qless_qr(rr_handle* h) {
   return RR_OK;
 }
 
+// Spectral norm of a symmetric k x k float64 matrix by power iteration:
+// x_0 a fixed pseudo-random vector, x_t = M x_{t-1} / |x_{t-1}|, estimate =
+// |x_T| (the norm of the image of a unit vector; a lower bound that
+// converges to |M|_2 = max |lambda_i(M)|).  One warp per row of M (rows are
+// contiguous, so the warp's loads coalesce); each block writes the sum of
+// squares of its rows of x_t, and the next step sums those partials in a
+// fixed order, so the estimate does not depend on scheduling.
+constexpr int kSymRowsPerBlock = 8;
+
+__global__ void __launch_bounds__(256) k_sym_power_start(double* x, double* xpart, int k) {
+  // x_j = u_j - 1/2 with u_j from a 32-bit integer hash of j (no zero entry
+  // pattern tied to the rows of M); one block
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    uint32_t z = (uint32_t)j * 0x9E3779B1u + 0x7F4A7C15u;
+    z ^= z >> 15; z *= 0x2C1B3C6Du; z ^= z >> 12; z *= 0x297A2D39u; z ^= z >> 15;
+    const double v = ((double)z + 0.5) * 0x1p-32 - 0.5;
+    x[j] = v;
+    s += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    xpart[0] = t;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_sym_power_step(const double* __restrict__ M, int k,
+                                                        const double* __restrict__ x,
+                                                        const double* __restrict__ xpart, int nxpart,
+                                                        double* __restrict__ y,
+                                                        double* __restrict__ ypart) {
+  __shared__ double s_scale;
+  __shared__ double red[kSymRowsPerBlock];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    double s = 0.0;
+    for (int i = lane; i < nxpart; i += 32) s += xpart[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) s_scale = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * kSymRowsPerBlock + warp;
+  double yi = 0.0;
+  if (i < k) {
+    const double* row = M + (int64_t)i * k;
+    for (int j = lane; j < k; j += 32) yi = fma(row[j], x[j], yi);
+    for (int o = 16; o > 0; o >>= 1) yi += __shfl_xor_sync(0xffffffffu, yi, o);
+    yi *= s_scale;
+    if (lane == 0) y[i] = yi;
+  }
+  if (lane == 0) red[warp] = yi * yi;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kSymRowsPerBlock; ++w) t += red[w];
+    ypart[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sum_parts_sqrt(const double* __restrict__ part, int np, double* out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += 32) s += part[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+constexpr int kSymNormIters = 30;
+
+// |M|_2 of the symmetric k x k M (device) by kSymNormIters power steps;
+// scratch: xbuf of >= 2k doubles, pbuf of >= 2 ceil(k / 8) doubles.
+rr_status sym_norm2(rr_handle* h, const double* M, int k, double* xbuf, double* pbuf, double* out) {
+  const int nb = (k + kSymRowsPerBlock - 1) / kSymRowsPerBlock;
+  double* x[2] = {xbuf, xbuf + k};
+  double* p[2] = {pbuf, pbuf + nb};
+  k_sym_power_start<<<1, 256, 0, h->st>>>(x[0], p[0], k);
+  int np = 1;
+  for (int t = 0; t < kSymNormIters; ++t) {
+    const int a = t & 1, b = a ^ 1;
+    k_sym_power_step<<<nb, 32 * kSymRowsPerBlock, 0, h->st>>>(M, k, x[a], p[a], np, x[b], p[b]);
+    np = nb;
+  }
+  k_sum_parts_sqrt<<<1, 32, 0, h->st>>>(p[kSymNormIters & 1], nb, h->norms);
+  return read_doubles(h, h->norms, 1, out);
+}
+
 // C-RandRAND core matrix G = (R_M R^-1)^T (R_M R^-1), R_M^T R_M = sym(Omega^T
-// Y_mu) (remark after Alg. 7).  M is in kk[kM].  Jitter ladder of App. C
-// (alpha = 10^-14 .. 10^-1 times the largest diagonal entry) on failure.
+// Y_mu) (remark after Alg. 7).  M is in kk[kM].  On a failed factorization,
+// the jitter ladder of App. C: R_M = chol(M + alpha I) with alpha the
+// smallest of 10^-14 |M|, 10^-13 |M|, ..., 10^-1 |M| that factors, |M| the
+// spectral norm (the paper's |.| for matrices), estimated by power iteration.
 rr_status core_matrix(rr_handle* h) {
   const int k = h->k;
   double* RM = h->kk[kScA];
   RR_CUDA_TRY(cudaMemcpyAsync(RM, h->kk[kM], (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
   rr_status s = chol(h, RM);
+  h->jitter = 0.0;
   if (s == RR_ERR_NOT_SPD) {
-    double md = 0.0;
-    k_maxdiag<<<1, 32, 0, h->st>>>(h->kk[kM], k, h->norms);
-    RR_TRY(read_doubles(h, h->norms, 1, &md));
+    // the Krylov coefficient vectors t[0] (k mp >= 2k doubles) and t[1] are
+    // free during the build
+    double nrm = 0.0;
+    RR_TRY(sym_norm2(h, h->kk[kM], k, h->t[0], h->t[1], &nrm));
     s = RR_ERR_NOT_SPD;
     for (int e = -14; e <= -1 && s == RR_ERR_NOT_SPD; ++e) {
       RR_CUDA_TRY(cudaMemcpyAsync(RM, h->kk[kM], (size_t)k * k * 8, cudaMemcpyDeviceToDevice, h->st));
-      add_diag(RM, k, std::pow(10.0, e) * md, h->st);
+      h->jitter = std::pow(10.0, e) * nrm;
+      add_diag(RM, k, h->jitter, h->st);
       s = chol(h, RM);
     }
+    if (s != RR_OK) h->jitter = 0.0;
   }
   if (s != RR_OK) return s;
   gemm_upper_upper(k, RM, h->kk[kRinv], h->kk[kTm], h->st);   // T = R_M R^-1
@@ -1971,6 +2062,12 @@ rr_status randrand_scalars(const rr_handle* h, double* tau, double* normE, doubl
   if (tau) *tau = h->tau;
   if (normE) *normE = h->normE;
   if (lam_max) *lam_max = h->lam_max;
+  return RR_OK;
+}
+
+rr_status randrand_core_jitter(const rr_handle* h, double* alpha) {
+  if (!h || !alpha) return RR_ERR_INVALID_ARG;
+  *alpha = h->jitter;
   return RR_OK;
 }
 

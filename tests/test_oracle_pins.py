@@ -773,3 +773,56 @@ def test_g_randrand_minres_solves_indefinite():
     assert np.linalg.norm(x - xs) <= 1e-7 * np.linalg.norm(xs)
     _, plain = O.minres(lambda v: A @ v + mu * v, B[:, 0], lambda v: v, 1e-10, 5000)
     assert infos[0].inner_iters < plain
+
+
+# --------------------------------------------------------------------------
+# Core-matrix jitter ladder (App. C): alpha = the smallest of 10^-14 |M|,
+# ..., 10^-1 |M| for which M + alpha I factors, |M| the spectral norm
+# --------------------------------------------------------------------------
+def test_jitter_ladder_matches_brute_force_scan():
+    from ladder_cases import ladder_core, ladder_rung
+    k = 40
+    M = ladder_core(k)
+    ev = np.linalg.eigvalsh(M)
+    nrm2 = np.abs(ev).max()
+    assert nrm2 == pytest.approx(np.linalg.svd(M, compute_uv=False)[0], rel=1e-12)
+    expected = ladder_rung(M, nrm2)
+    # the fixture decides every rung far from rounding: the rung below fails
+    # and the chosen one succeeds by margins well above k u |M|
+    assert expected is not None and expected > 0
+    margin = 1e4 * k * np.finfo(float).eps * nrm2
+    assert ev.min() + expected > margin
+    assert ev.min() + expected / 10 < -margin
+    RM, alpha = O.chol_upper_jitter(M)
+    assert alpha == pytest.approx(expected, rel=1e-12)
+    assert np.allclose(RM.T @ RM, M + alpha * np.eye(k), rtol=0, atol=1e-13 * nrm2)
+    assert np.all(np.diag(RM) > 0) and np.allclose(RM, np.triu(RM))
+    # the largest-diagonal reading of |M| lands on another rung here, so a
+    # ladder scaled by that reading fails this test
+    alt = ladder_rung(M, np.abs(np.diag(M)).max())
+    assert alt is not None and not np.isclose(alt, expected, rtol=0.5)
+    # an SPD matrix factors without jitter; one far from SPD exhausts the ladder
+    _, a0 = O.chol_upper_jitter(M + 1e-6 * nrm2 * np.eye(k))
+    assert a0 == 0.0
+    with pytest.raises(np.linalg.LinAlgError):
+        O.chol_upper_jitter(M - 0.5 * nrm2 * np.eye(k))
+
+
+def test_build_takes_the_jitter_ladder_for_an_indefinite_core():
+    """A dense A with Omega^T A_mu Omega = M (one slightly negative eigenvalue)
+    sends the C build through the ladder: G = R^-T (M + alpha I) R^-1 with the
+    brute-force alpha, and A_mu Omega = Q R stays well conditioned."""
+    from ladder_cases import ladder_core, ladder_rung, operator_with_core
+    n, k, mu, seed = 400, 40, 1e-3, 21
+    Om = O.make_omega(n, k, "sparse_sign", seed, gamma=8)
+    M = ladder_core(k)
+    A = operator_with_core(Om, M, mu)
+    assert np.allclose(A, A.T)
+    assert np.allclose(Om.T @ (A + mu * np.eye(n)) @ Om, M, rtol=0, atol=1e-11)
+    b = O.build(O.DenseOp(A), mu, k, "sparse_sign", seed, gamma=8)
+    assert np.linalg.cond(b.Ymu) < 1e4
+    expected = ladder_rung(M, np.abs(np.linalg.eigvalsh(M)).max())
+    assert b.jitter == pytest.approx(expected, rel=1e-9)
+    Rinv = np.linalg.inv(b.R)
+    G_def = Rinv.T @ (M + b.jitter * np.eye(k)) @ Rinv
+    assert np.allclose(b.G, G_def, rtol=0, atol=1e-10 * np.abs(G_def).max())
