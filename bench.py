@@ -170,24 +170,28 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- CPU oracle
-def oracle_sample(X, B, products_per_solve, reps=1):
-    """Float64 CPU oracle, as it stands, on a bounded sample of the workload:
-    `reps` full-size products (K + mu I) V with the 4 right-hand sides and one
-    Householder QR of an n x k basis; scaled to one solve by the number of
-    such products the solve performs.  Returns (solves/s, seconds of sample)."""
+def oracle_solve_timed(X, B, seed, sketch="gaussian", ml_l1=0, ml_gamma=0):
+    """The float64 CPU oracle, as it stands, on the whole workload, end to end
+    from the points: the dense K materialized once (the oracle's own
+    materialize option), the build (the test matrix rounded to bf16 like the
+    mixed path's, Householder QR, core matrix, 20 + 20 power iterations) and
+    restarted PCG to rtol.  Returns (seconds, X, infos, operator)."""
     from oracle import randrand as O
-    op = O.GaussKernelOp(X, WORKLOAD["bandwidth"])
-    V = np.asarray(B, dtype=np.float64)
     t0 = time.perf_counter()
-    for _ in range(reps):
-        O.shifted(op, WORKLOAD["mu"])(V)
-    t_mv = (time.perf_counter() - t0) / reps
-    Y = np.random.default_rng(0).standard_normal((WORKLOAD["n"], WORKLOAD["k"]))
-    t1 = time.perf_counter()
-    O.householder_qr(Y)
-    t_qr = time.perf_counter() - t1
-    per_solve = products_per_solve * t_mv + 2 * t_qr
-    return 1.0 / per_solve, time.perf_counter() - t0, t_mv, t_qr
+    op = O.GaussKernelOp(X, WORKLOAD["bandwidth"], materialize=True)
+    bd = O.build(op, WORKLOAD["mu"], WORKLOAD["k"], sketch, seed, omega_precision="bf16",
+                 ml_l1=ml_l1, ml_gamma=ml_gamma)
+    Xo, infos = O.solve(bd, np.asarray(B, dtype=np.float64), rtol=WORKLOAD["rtol"])
+    return time.perf_counter() - t0, Xo, infos, op
+
+
+def forward_error(Xg, op, mu, B):
+    """|x - x*| / |x*| per column, x* = A_mu^-1 b by the oracle's dense
+    Cholesky solve (float64)."""
+    from oracle import randrand as O
+    Xs = O.exact_solve(op, mu, np.asarray(B, dtype=np.float64))
+    return [float(np.linalg.norm(Xg[:, j] - Xs[:, j]) / np.linalg.norm(Xs[:, j]))
+            for j in range(Xs.shape[1])], Xs
 
 
 def cpu_threads():
@@ -199,45 +203,57 @@ def cpu_threads():
         return os.cpu_count() or 1
 
 
-def products_per_solve(iters, k, nrhs, power_iters=20, restarts=3):
-    # sketch: k columns = k / nrhs products of nrhs columns; power: 2 x 20 single
-    # columns (= 40 / nrhs products); iterations: one product each; restarts.
-    return k / nrhs + 2 * power_iters / nrhs + iters + restarts
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 # ------------------------------------------------------------- reference arm
+REFERENCE_BUDGET_S = 150.0
+
+
 def run_reference(args):
+    """The oracle timed on the host cores: whole solves of the workload, as
+    many of the requested steps as fit in REFERENCE_BUDGET_S (at least one),
+    after at most one untimed warm-up solve.  The line reports the steps it
+    actually ran and their measured time."""
     rank, world, _ = dist_init(args)
     if rank != 0:
         return
     X, B = make_inputs(WORKLOAD["seed"])
-    # iteration count of the oracle's own solve of this workload (committed
-    # fixture written by tests/golden/make_golden.py from the oracle)
-    gpath = os.path.join(ROOT, "tests", "golden", "kernel_ridge_oracle_iters.json")
-    iters = json.load(open(gpath))["inner_iters_max"] if os.path.exists(gpath) else 250
-    pps = products_per_solve(iters, WORKLOAD["k"], WORKLOAD["nrhs"])
-    for _ in range(args.warmup):
-        oracle_sample(X, B, pps)
-    vals, secs = [], 0.0
-    for _ in range(args.steps):
-        v, s, _, _ = oracle_sample(X, B, pps)
-        vals.append(v)
-        secs += s
-    value = statistics.median(vals)
+    warm = min(args.warmup, 1)
+    for _ in range(warm):
+        oracle_solve_timed(X, B, WORKLOAD["seed"])
+    times, iters = [], 0
+    t_start = time.perf_counter()
+    while len(times) < args.steps:
+        t, _, infos, _ = oracle_solve_timed(X, B, WORKLOAD["seed"])
+        times.append(t)
+        iters = max(i.inner_iters for i in infos)
+        if time.perf_counter() - t_start + t > REFERENCE_BUDGET_S:
+            break
+    steps = len(times)
+    value = steps / sum(times)
+    sample = (f"{steps} whole float64 oracle solve(s) of the workload (n=20000, k=500, 4 right-hand "
+              f"sides, rtol 1e-6; dense K materialized from the points, Householder QR, PCG with "
+              f"restarts; {iters} iterations), {', '.join(f'{t:.1f}' for t in times)} s each; "
+              f"{warm} untimed warm-up solve")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+        "n_gpus": args.gpus, "steps": steps, "steps_requested": args.steps, "warmup": warm,
+        "ms_per_step": 1000.0 * sum(times) / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         # the same workload description as the GPU arm's line
         "config": {**{k: WORKLOAD[k] for k in ("workload", "n", "d", "k", "nrhs", "mu", "rtol",
                                                "precision", "variant", "sketch")},
                    "parallelism": f"replicas x{world}", "l2": "host cores (no GPU cache)"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_threads(),
-                         "kind": "oracle",
-                         "sample": f"per step: one float64 (K+mu I)V product with 4 columns at "
-                                   f"n=20000 and one 20000x500 Householder QR, scaled by "
-                                   f"{pps:.0f} products per solve (oracle iteration count {iters})"},
+                         "cpu": cpu_model(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -265,17 +281,20 @@ def run_ours(args):
     o.variant = rr.VARIANTS[WORKLOAD["variant"]]
     o.precision = rr.PRECISIONS[WORKLOAD["precision"]]
     o.max_rhs = m
-    o.profile = 1
+    o.profile = 0                 # the headline steps run without profiling events
     o.kernel_impl = args.kernel_impl
     o.refine = 1 if args.refine else 0
     rr.set_multilevel(o, WORKLOAD["sketch"], n, k)
-    ws_bytes = rr.randrand_workspace_bytes(op.c, k, o)
+    op_prof = rr.rr_build_opts()
+    ctypes_copy(op_prof, o)
+    op_prof.profile = 1
+    ws_bytes = rr.randrand_workspace_bytes(op.c, k, op_prof)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sk = rr.SKETCHES[WORKLOAD["sketch"]]
 
-    def one_solve(collect=None):
-        h = rr.randrand_build(op.c, WORKLOAD["mu"], k, sk, seed, o, ws.data_ptr(), ws_bytes,
+    def one_solve(opts, collect=None):
+        h = rr.randrand_build(op.c, WORKLOAD["mu"], k, sk, seed, opts, ws.data_ptr(), ws_bytes,
                               stream.cuda_stream)
         Xc.zero_()
         s, infos = rr.randrand_solve(h, Bc.data_ptr(), m, n, Xc.data_ptr(), n, 0,
@@ -283,13 +302,26 @@ def run_ours(args):
         if s != rr.RR_OK:
             raise RuntimeError(f"solve failed: {rr.randrand_status_str(s)} {infos}")
         if collect is not None:
-            collect.append((rr.randrand_profile(h), infos))
+            collect.append((rr.randrand_profile(h) if opts.profile else None, infos))
         rr.randrand_free(h)
         return infos
 
+    def timed_pass(opts, collect):
+        ms = []
+        for _ in range(args.steps):
+            flush.fill_(1)                           # L2 flush between timed steps (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_solve(opts, collect)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            one_solve()
+            one_solve(o)
         torch.cuda.synchronize()
         smi = ClockSampler(getattr(torch.cuda.get_device_properties(local), "uuid", None) and
                            "GPU-" + str(torch.cuda.get_device_properties(local).uuid))
@@ -297,32 +329,30 @@ def run_ours(args):
         torch.cuda.synchronize()
         smi.start()
         wall0 = time.perf_counter()
-        step_ms, prof = [], []
-        for _ in range(args.steps):
-            flush.fill_(1)                           # L2 flush between timed steps (not timed)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            one_solve(prof)
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
+        runs = []
+        step_ms = timed_pass(o, runs)
         torch.cuda.synchronize()
         barrier(world)
         wall = time.perf_counter() - wall0
         clocks = smi.stop()
+        x_gpu = Xc.t().cpu().numpy().copy()        # the last timed solve's x (n x m)
+        # per-kernel split and the roofline: a separate pass of the same steps
+        # with CUDA events around every hot launch (randrand_profile)
+        prof = []
+        prof_ms = timed_pass(op_prof, prof)
+        torch.cuda.synchronize()
     total_ms = max_over_ranks(sum(step_ms), world)
     ms_per_step = total_ms / args.steps
     value = world * 1000.0 / ms_per_step
 
-    # per-kernel profile over the timed region
+    # per-kernel profile over the profiled pass
     cats = {}
     for p, _ in prof:
         for nm, (cnt, ms) in p.items():
             c = cats.setdefault(nm, [0, 0.0])
             c[0] += cnt
             c[1] += ms
-    infos = [i for _, inf in prof for i in inf]
+    infos = [i for _, inf in runs for i in inf]
     iters = max(i["inner_iters"] for i in infos)
     rel_res = max(i["rel_residual"] for i in infos)
     gpu_launches = estimate_launches(prof, args.variant)
@@ -330,6 +360,9 @@ def run_ours(args):
     # dominant kernel and its roofline
     dom = max(cats.items(), key=lambda kv: kv[1][1])
     roof = roofline(dom[0], dom[1], clocks)
+    roof["measured"] = ("CUDA events around each launch in a profiled pass of the same "
+                        f"{args.steps} steps ({sum(prof_ms) / args.steps:.2f} ms per step with "
+                        "the events), after the headline steps")
     others = {kk: roofline(kk, v, clocks) for kk, v in cats.items() if kk != dom[0] and v[0] > 0}
 
     # end-to-end: host buffers through the C ABI, H2D inputs and D2H solution inside
@@ -356,13 +389,21 @@ def run_ours(args):
         "wall_s": wall,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        pps = products_per_solve(iters, k, m)
-        v, secs, t_mv, t_qr = oracle_sample(X, B, pps)
+        t, Xo, oinfos, oop = oracle_solve_timed(X, B, seed, WORKLOAD["sketch"], o.ml_l1, o.ml_gamma)
+        fe, Xs = forward_error(x_gpu, oop, WORKLOAD["mu"], B)
+        fe_o = [float(np.linalg.norm(Xo[:, j] - Xs[:, j]) / np.linalg.norm(Xs[:, j]))
+                for j in range(Xs.shape[1])]
+        line["solve"]["forward_error_vs_oracle"] = fe
+        line["solve"]["forward_error_note"] = (
+            "|x - x*| / |x*| per right-hand side of the last timed solve, x* = (K + mu I)^-1 b "
+            "by the float64 oracle's dense Cholesky solve; the oracle's own rtol-1e-6 solve is at "
+            + ", ".join(f"{e:.2e}" for e in fe_o))
         line["cpu_baseline"] = {
-            "value": v, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
-            "sample": (f"one float64 (K+mu I)V product with 4 columns at n=20000 ({t_mv:.2f} s) and "
-                       f"one 20000x500 Householder QR ({t_qr:.2f} s), scaled by {pps:.0f} "
-                       f"products per solve")}
+            "value": 1.0 / t, "unit": "solves/s", "cores": cpu_threads(), "cpu": cpu_model(),
+            "kind": "oracle",
+            "sample": (f"one whole float64 oracle solve of this workload, timed end to end from the "
+                       f"points ({t:.1f} s: dense K materialized, build, PCG with restarts, "
+                       f"{max(i.inner_iters for i in oinfos)} iterations)")}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -617,21 +658,26 @@ def run_sparse(args):
                                       for kk in prof[0][0]},
                  roofline=roof, clocks=clocks)
     if rank == 0 and not args.no_cpu_baseline:
+        # bounded sample: the oracle's build of this system (sparse-sign Omega,
+        # basis by Householder QR: its Alg. 3 forms Theta as a dense l_sk x n
+        # matrix, 2 GB here) and 50 of its PCG iterations, each timed; the
+        # iteration time is scaled to the GPU solve's iteration count
         from oracle import randrand as O
         cop = O.CsrOp(C.rowptr, C.colidx, C.vals, C.n)
-        v = np.asarray(b, dtype=np.float64)
-        reps = 200
         t0 = time.perf_counter()
-        for _ in range(reps):
-            O.shifted(cop, cfg["mu"])(v)
-        t_mv = (time.perf_counter() - t0) / reps
+        bd = O.build(cop, cfg["mu"], cfg["k"], "sparse_sign", seed, gamma=cfg["gamma"])
+        t_build = time.perf_counter() - t0
+        fixed = 50
+        t1 = time.perf_counter()
+        O.solve(bd, np.asarray(b, dtype=np.float64), rtol=cfg["rtol"], fixed_inner=fixed)
+        t_it = (time.perf_counter() - t1) / fixed
         iters = max(i["inner_iters"] for i in infos)
-        pps = 3 * iters + 5 * 20 + cfg["k"] + 4
-        line["cpu_baseline"] = {"value": 1.0 / (pps * t_mv), "unit": "solves/s",
-                                "cores": cpu_threads(), "kind": "oracle",
-                                "sample": f"{reps} float64 CSR products (scipy) at n=262144, "
-                                          f"{t_mv * 1e3:.2f} ms each, scaled by {pps} products "
-                                          f"per solve (3 per basis-less iteration)"}
+        line["cpu_baseline"] = {
+            "value": 1.0 / (t_build + iters * t_it), "unit": "solves/s", "cores": cpu_threads(),
+            "cpu": cpu_model(), "kind": "oracle",
+            "sample": (f"the float64 oracle's build of this system ({t_build:.1f} s; Householder "
+                       f"basis) and {fixed} of its PCG iterations ({t_it * 1e3:.1f} ms each), "
+                       f"scaled to the GPU solve's {iters} iterations")}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

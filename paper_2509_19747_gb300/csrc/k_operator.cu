@@ -306,6 +306,10 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_f64(const float* __restr
 
 // float64-accurate product on the float32 pipes (double-float arithmetic):
 //   d2_ij = |p_i|^2 + |p_j|^2 - 2 p_i . p_j   (p_i . p_j by TwoProd/TwoSum)
+// and 2^t by the table-driven method of P. T. P. Tang ("Table-driven
+// implementation of the exponential function in IEEE floating-point
+// arithmetic", ACM TOMS 15(2), 1989): reduce the argument by a multiple of
+// 1/64, take 2^(j/64) from a table and a short polynomial for the rest,
 //   t = -d2 log2(e) / (2 h^2) = k + j/64 + r,  |r| <= 1/128
 //   K_ij = 2^k * T[j] * exp(r ln 2),  T[j] = 2^(j/64) from a 65-entry table,
 //   exp(z) = 1 + z + z^2/2 + z^3/6 + z^4/24 + z^5/120 for |z| <= ln2/128

@@ -574,6 +574,41 @@ def test_kernel_ridge_full_size(cuda_lib):
     h.close()
 
 
+def test_kernel_ridge_full_size_error_vs_exact_solution(cuda_lib):
+    """The timed configuration (n = 20000, d = 8, k = 500, 4 right-hand sides,
+    mu = 1e-3, bf16 sketch, float32 iterations, float64-accurate refinement)
+    against the float64 oracle's exact solution x* = (K + mu I)^-1 b, a dense
+    Cholesky solve of the materialized K.  The throughput solve (rtol 1e-6)
+    has a float64 residual, over all rows, within rtol and a forward error
+    within 1e-5; a parity solve to rtol 1e-9 (the refinement loop run to a
+    tighter target on the same inputs) is within 1e-7 of x*."""
+    rr = cuda_lib
+    n, m, k, mu = 20000, 4, 500, 1e-3
+    X = W.mixture_points(n, 8, 10, seed=W.SEED_KERNEL)
+    B = W.gaussian_rhs(n, m, W.SEED_KERNEL)
+    op = O.GaussKernelOp(X, materialize=True)
+    xs = O.exact_solve(op, mu, B)
+    h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=W.SEED_KERNEL,
+                  precision="mixed", max_rhs=m)
+    x, status, infos = h.solve(dev(B), rtol=1e-6)
+    assert status == rr.RR_OK
+    x = x.cpu().numpy()
+    res = O.true_rel_residual(op, mu, x, B)
+    rep = np.array([i["rel_residual"] for i in infos])
+    fe = np.linalg.norm(x - xs, axis=0) / np.linalg.norm(xs, axis=0)
+    print(f"rtol 1e-6: residual {res}, reported {rep}, forward error {fe}")
+    assert np.all(res <= 1e-6)
+    assert np.allclose(res, rep, rtol=1e-3, atol=1e-12)
+    assert np.all(fe <= 1e-5)
+    x, status, infos = h.solve(dev(B), rtol=1e-9)
+    assert status == rr.RR_OK
+    x = x.cpu().numpy()
+    fe = np.linalg.norm(x - xs, axis=0) / np.linalg.norm(xs, axis=0)
+    print(f"rtol 1e-9: residual {O.true_rel_residual(op, mu, x, B)}, forward error {fe}")
+    assert np.all(fe <= 1e-7)
+    h.close()
+
+
 @pytest.mark.parametrize("m", [2, 5])
 def test_variant_r_persistent_step_fp32_dense(cuda_lib, m):
     """Variant R in float32 on a dense operator: the persistent launches
