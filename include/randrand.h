@@ -380,7 +380,9 @@ rr_status randrand_matvec(rr_handle* h, const double* v, double* w, int32_t m, i
  *   points  device, n x dim float32 row-major (dim <= 16); bandwidth h > 0.
  *   v, w    device, n x m float64 column-major, leading dimension ld >= n;
  *           1 <= m <= 8.  Caller-owned.
- *   stream  cudaStream_t (as void*).  Enqueued only; does not synchronise.
+ *   stream  cudaStream_t (as void*) of the current device (a stream of
+ *           another device: RR_ERR_INVALID_ARG).  Enqueued only; does not
+ *           synchronise.
  * Scratch: a fixed 32 MiB static device array inside the library (held on
  * every GPU that loads it until the library is unloaded), nothing else; no
  * cudaMalloc, cudaFree or allocating library call.  Limit: with mp the
@@ -388,9 +390,14 @@ rr_status randrand_matvec(rr_handle* h, const double* v, double* w, int32_t m, i
  * (rounded up to 256-byte blocks) must fit in 32 MiB, else RR_ERR_WORKSPACE
  * and nothing is launched.  All calls share the array: calls that overlap
  * on the GPU race; serialise them.  Nothing in it needs to start at zero.
- * The first call on a device looks up the array's device address (once,
- * with that device current); make that first call before any stream
- * capture.  Errors: RR_ERR_INVALID_ARG, RR_ERR_WORKSPACE, RR_ERR_CUDA.
+ * Each call outside stream capture looks up the array's device address on
+ * the current device (and the first such call loads the library's module
+ * there); a call on a capturing stream reuses the address of the last
+ * uncaptured call on that device, so make the first call on each device
+ * before any stream capture.  An error already pending in the CUDA runtime
+ * when the call starts is left in place and reported as RR_ERR_CUDA with
+ * nothing launched.  Errors: RR_ERR_INVALID_ARG, RR_ERR_WORKSPACE,
+ * RR_ERR_CUDA.
  */
 rr_status randrand_kernel_matvec_noalloc(const float* points, int64_t n, int32_t dim,
                                          double bandwidth, double mu, const double* v, double* w,

@@ -19,10 +19,12 @@
 //   * every scratch element a call reads is written earlier in the same
 //     call, so nothing has to start at zero and the last call's leftovers
 //     are harmless;
-//   * host code cannot use the array's name as a device address: the
-//     address is looked up once per device with cudaGetSymbolAddress on the
-//     first call made with that device current, so make that first call
-//     before any stream capture.
+//   * host code cannot use the array's name as a device address: every
+//     call made outside stream capture looks the address up with
+//     cudaGetSymbolAddress (current device) and remembers it per device; a
+//     call made while its stream is being captured uses the remembered
+//     address, so make the first call on each device before any capture
+//     (that first call also loads the module into the device's context).
 #include <cmath>
 #include <mutex>
 
@@ -39,12 +41,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 std::mutex g_addr_mu;
 void* g_addr[kMaxDevices] = {nullptr};
 
-// device address of the static scratch for the current device
-rr_status scratch_address(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RR_ERR_CUDA;
+// device address of the static scratch for the current device.  Outside
+// stream capture the address is looked up on every call (cheap), so a
+// context re-created after cudaDeviceReset is seen; during capture the
+// address remembered from the last uncaptured call on this device is used.
+rr_status scratch_address(int dev, bool capturing, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return RR_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (!g_addr[dev]) {
+  if (!capturing) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
@@ -52,6 +56,7 @@ rr_status scratch_address(void** out) {
     }
     g_addr[dev] = p;
   }
+  if (!g_addr[dev]) return RR_ERR_CUDA;     // first call on this device under capture
   *out = g_addr[dev];
   return RR_OK;
 }
@@ -79,16 +84,33 @@ extern "C" rr_status randrand_kernel_matvec_noalloc(const float* points, int64_t
   if (fixed + part1 > kNoAllocScratchBytes) return RR_ERR_WORKSPACE;  // n, m beyond the array
   int nsplit = kernel_mv_nsplit(n);
   while (nsplit > 1 && fixed + (size_t)nsplit * part1 > kNoAllocScratchBytes) --nsplit;
+  // an error left pending by earlier, unrelated work is not ours to clear or
+  // to report as a failed launch of this call
+  if (cudaPeekAtLastError() != cudaSuccess) return RR_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = -1, sdev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RR_ERR_CUDA;
+  if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+    cudaGetLastError();
+    return RR_ERR_INVALID_ARG;                // not a stream handle of this process
+  }
+  if (sdev != dev) return RR_ERR_INVALID_ARG;  // the stream belongs to another device
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return RR_ERR_CUDA;
+  }
   void* base = nullptr;
-  RR_TRY(scratch_address(&base));
+  RR_TRY(scratch_address(dev, cap != cudaStreamCaptureStatusNone, &base));
   unsigned char* b = (unsigned char*)base;
   double* Vi = (double*)b;
   double* Wi = (double*)(b + vec);
   float2* pn = (float2*)(b + 2 * vec);
   double* part = (double*)(b + fixed);
-  cudaStream_t st = (cudaStream_t)stream;
   gather_cols(v, ld, m, n, mp, Vi, st);
+  if (cudaGetLastError() != cudaSuccess) return RR_ERR_CUDA;
   kernel_mv_df_raw(points, n, dim, bandwidth, mu, Vi, Wi, mp, pn, part, nsplit, st);
+  if (cudaGetLastError() != cudaSuccess) return RR_ERR_CUDA;
   scatter_cols(Wi, n, mp, m, w, ld, st);
   if (cudaGetLastError() != cudaSuccess) return RR_ERR_CUDA;
   return RR_OK;
