@@ -69,6 +69,8 @@ def parse():
                              "indefinite"])
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
     ap.add_argument("--workers", type=int, default=0, help="batched/serving: 0 = autotune")
+    ap.add_argument("--no-rounds", action="store_true",
+                    help="serving: every request on its worker's stream (no shared rounds)")
     ap.add_argument("--sketch", default=None,
                     choices=["gaussian", "srht", "multilevel", "sparse_sign"],
                     help="test matrix (default: Gaussian for the kernel ridge workload, "
@@ -715,23 +717,30 @@ def run_batched(args):
     import paper_2509_19747_gb300 as rr
     sets = {impl: batched_systems(rr, torch, rank, iter_impl=impl)[0] for impl in (0, 1)}
     arena = sum((q.workspace_bytes() + 255) // 256 * 256 for q in sets[0])
-    # worker count and iteration form (persistent cooperative step or separate
-    # kernels): the best of a few on untimed passes (autotune), or as given
+    ropts = rr.batch_rounds_opts(sets[0])
+    # schedule: shared rounds (every system's iterations in one grouped launch
+    # per round; the library tunes the rounds per graph replay) or one stream
+    # per worker with the persistent step or separate kernels, and the worker
+    # count: the best of a few on untimed passes, or as given
     cands = [(w, impl) for w in ([args.workers] if args.workers > 0 else [4, 8, 16])
-             for impl in (0, 1)]
+             for impl in ("rounds", 0, 1)]
     tune = {}
     for w, impl in cands:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, _ = rr.solve_batch(sets[impl], workers=w, arena_bytes=arena)
+        if impl == "rounds":
+            st, _ = rr.solve_batch(sets[0], workers=w, arena_bytes=arena, rounds=ropts)
+        else:
+            st, _ = rr.solve_batch(sets[impl], workers=w, arena_bytes=arena)
         torch.cuda.synchronize()
         tune[(w, impl)] = time.perf_counter() - t0
         if st != rr.RR_OK:
-            raise RuntimeError(f"batch failed: {rr.randrand_status_str(st)}")
+            raise RuntimeError(f"batch failed ({impl}): {rr.randrand_status_str(st)}")
     workers, impl = min(tune, key=tune.get)
-    reqs = sets[impl]
+    reqs = sets[0] if impl == "rounds" else sets[impl]
+    kw = dict(rounds=ropts) if impl == "rounds" else {}
     for _ in range(max(args.warmup - 1, 0)):
-        rr.solve_batch(reqs, workers=workers, arena_bytes=arena)
+        rr.solve_batch(reqs, workers=workers, arena_bytes=arena, **kw)
     smi = ClockSampler()
     torch.cuda.synchronize()
     barrier(world)
@@ -741,7 +750,7 @@ def run_batched(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         t0 = time.perf_counter()
-        st, res = rr.solve_batch(reqs, workers=workers, arena_bytes=arena)
+        st, res = rr.solve_batch(reqs, workers=workers, arena_bytes=arena, **kw)
         torch.cuda.synchronize()
         e1.record()
         e1.synchronize()
@@ -761,12 +770,14 @@ def run_batched(args):
     iters = [i["inner_iters"] for r in res for i in r["info"]]
     line = _line(args, world, "RandRAND-PCG solves/s to rtol 1e-6 (64 batched kernel ridge systems)",
                  world * BATCHED["systems"] * 1000.0 / ms, "solves/s", ms,
-                 {**BATCHED, "workers": workers, "iter_impl": impl, "parallelism": f"replicas x{world}",
+                 {**BATCHED, "workers": workers, "schedule": "shared rounds" if impl == "rounds"
+                  else f"one stream per worker, iter_impl {impl}", "parallelism": f"replicas x{world}",
                   "l2": "inputs of the batch exceed L2"},
                  latency_ms={"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
                  one_after_another={"value": BATCHED["systems"] / seq_s, "unit": "solves/s",
                                     "seconds": seq_s},
-                 autotune_s={f"workers={k[0]},iter_impl={k[1]}": v for k, v in tune.items()},
+                 autotune_s={f"workers={k[0]},schedule={k[1]}": v for k, v in tune.items()},
+                 in_rounds=sum(r.get("rounds", 0) for r in res),
                  solve={"inner_iters_max": max(iters), "inner_iters_median": float(np.median(iters))},
                  roofline=None, clocks=clocks)
     if rank == 0:
@@ -940,7 +951,10 @@ def run_serving(args):
     arrivals, reqs = serving_requests(rr, torch, args.requests, rank)
     budget = int(SERVING["budget_gb"] * 1e9)
     workers = args.workers if args.workers > 0 else 16
-    srv = rr.Server(budget, workers=workers)
+    # the kernel requests (one right-hand side, k = n / 50 <= 640) iterate in
+    # shared rounds; the CSR requests iterate in their own persistent launches
+    ropts = rr.rounds_opts(2, 640, 152, 2 << 20) if not args.no_rounds else None
+    srv = rr.Server(budget, workers=workers, rounds=ropts)
     # warm-up: a few requests of each kind, untimed
     warm = [q for _, _, q in reqs[: max(args.warmup, 1) * 2]]
     for q in warm:
@@ -971,13 +985,15 @@ def run_serving(args):
     line = _line(args, world, "RandRAND-PCG solves/s to rtol 1e-6 (serving mix)", value, "solves/s",
                  1000.0 * makespan / len(res),
                  {**SERVING, "requests": len(res), "workers": workers,
-                  "parallelism": f"replicas x{world}"},
+                  "schedule": "kernel requests in shared rounds" if ropts is not None
+                  else "one stream per worker", "parallelism": f"replicas x{world}"},
                  latency_ms={"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                              **{f"p50_{k}": float(np.percentile(v, 50)) for k, v in by_kind.items()}},
                  completed=len(ok), failed=len(res) - len(ok), makespan_s=makespan,
                  offered_s=float(arrivals[-1]),
                  overloaded=bool(makespan > 1.5 * float(arrivals[-1])),
-                 peak_arena_gb=stats["peak_bytes"] / 1e9, roofline=None, clocks=clocks)
+                 peak_arena_gb=stats["peak_bytes"] / 1e9,
+                 in_rounds=sum(r.get("rounds", 0) for _, _, r in res), roofline=None, clocks=clocks)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -368,6 +368,54 @@ rr_status randrand_apply_operator(rr_handle* h, const double* v, double* w, int3
 rr_status randrand_matvec(rr_handle* h, const double* v, double* w, int32_t m, int64_t ld);
 
 /*
+ * Several built systems solved together in shared rounds.  Each round
+ * advances every system's Krylov iteration once.  The round is one
+ * persistent launch of the tensor-core kernel product over all systems'
+ * (row pair, point tile) work items, plus one cooperative launch of the
+ * persistent PCG step, in which each system gets a share of the SMs and
+ * its own grid barrier.  A CUDA graph captures R rounds once.  Its kernels
+ * read the group's system tables from device memory, so the same graph
+ * serves the group while systems finish.  Between replays the host reads
+ * every system's column states in one copy.  It runs the restarts
+ * (float64-accurate residual, Alg. 7 step 10) of the systems whose inner
+ * solves ended, and drops the systems that are done.  R, the rounds per
+ * replay, is tuned on the first replays of each (columns, log2 mean n,
+ * log2 mean k) class and then cached for the process.  Results equal
+ * randrand_solve's up to the summation order of the split sums.  The paper
+ * solves one system; this is a scheduling of its iterations for many.
+ *   hs          nsys (1..152) distinct built handles that iterate in float32
+ *               with the tensor-core product and the persistent step:
+ *               RR_OP_GAUSS_KERNEL in d = 8, RR_PREC_FP32 or RR_PREC_MIXED,
+ *               variant C, explicit basis, iter_impl 0, kernel_impl 0 or 2,
+ *               profile 0, all with the same column count (max_rhs rounded
+ *               up to a power of two); else RR_ERR_UNSUPPORTED.
+ *   rhs         per system: b, x (device, column-major, as randrand_solve),
+ *               nrhs <= opts.max_rhs, rtol, maxit.
+ *   workspace   device, >= randrand_group_workspace_bytes(hs, nsys), 256-byte
+ *               aligned, caller-owned: the handles' augmented point arrays
+ *               stacked, the system tables, each system's partial sums.
+ *   stream      cudaStream_t of all group work, not the legacy default
+ *               stream (NULL: RR_ERR_INVALID_ARG).  While it runs each handle
+ *               is moved to this stream, then back to its own.
+ *   info        host, 8 entries per system (info[8 i + c]), may be NULL.
+ * Synchronous.  Returns RR_OK when every system converged, else the first
+ * non-OK status in input order.  Errors: RR_ERR_INVALID_ARG,
+ * RR_ERR_UNSUPPORTED, RR_ERR_WORKSPACE, RR_ERR_CUDA, RR_ERR_TIMEOUT.
+ */
+typedef struct {
+  const double* b;
+  int64_t ldb;
+  double* x;
+  int64_t ldx;
+  int32_t nrhs;
+  int32_t maxit;
+  double rtol;
+} rr_group_rhs;
+rr_status randrand_group_workspace_bytes(rr_handle* const* hs, int32_t nsys, size_t* bytes);
+rr_status randrand_solve_group(rr_handle* const* hs, int32_t nsys, const rr_group_rhs* rhs,
+                               void* workspace, size_t ws_bytes, void* stream, rr_solve_info* info);
+
+/*
  * Allocation-free float64-accurate Gaussian-kernel product
  *     w = (K + mu I) v,   K_ij = exp(-|p_i - p_j|^2 / (2 h^2)),
  * the same double-float arithmetic as the restart residual of
@@ -442,6 +490,8 @@ typedef struct {
   double submit_ms, start_ms, end_ms;
   double queue_ms, build_ms, solve_ms;
   rr_solve_info info[8];   /* per right-hand side                             */
+  int32_t rounds;          /* 1: its iterations ran in the shared rounds      */
+  int32_t pad_;
 } rr_result;
 
 /* First-fit allocator of the serving loop over byte offsets [0, bytes),
@@ -478,6 +528,39 @@ rr_status rr_server_stats(rr_server* s, int32_t* queued, int32_t* running, size_
 void rr_server_destroy(rr_server* s);
 
 /*
+ * Shared rounds in the serving loop and the batch (see randrand_solve_group):
+ * systems whose handles qualify for the rounds (and have mp columns and
+ * k <= kmax) are handed, once built, to one executor thread that joins them
+ * into its running group at the next replay boundary and completes each
+ * request when its system is done; the others are solved by their worker as
+ * before.  Continuous batching: requests that arrive while others iterate
+ * join the same rounds as soon as they are built and the group has room.
+ *   mp           columns of the group: max_rhs rounded up to a power of two,
+ *                at least 2 (2, 4 or 8)
+ *   kmax         largest sketch dimension k of a system in the rounds
+ *   max_systems  systems resident in the rounds at once (1..152)
+ *   max_rows     stacked rows: sum over resident systems of n rounded up to
+ *                a multiple of 256
+ * The group's workspace (rr_rounds_workspace_bytes) is taken from the front
+ * of the arena given to rr_server_create_rounds / randrand_solve_batch_rounds;
+ * the rest is the HBM budget of the handles.  A built system that does not
+ * fit the group now waits for others to leave (or, when the group is empty,
+ * is solved on its own).
+ */
+typedef struct {
+  int32_t mp;
+  int32_t kmax;
+  int32_t max_systems;
+  int32_t pad_;
+  int64_t max_rows;
+} rr_rounds_opts;
+rr_status rr_rounds_workspace_bytes(const rr_rounds_opts* o, size_t* bytes);
+rr_status rr_server_create_rounds(void* arena, size_t arena_bytes, int32_t workers,
+                                  const rr_rounds_opts* rounds, rr_server** out);
+/* Most requests resident at once (admitted and not completed) so far. */
+rr_status rr_server_peak_running(rr_server* s, int32_t* peak);
+
+/*
  * Batched execution of nsys independent systems: a server over `arena` with
  * min(workers, nsys) workers, the systems submitted largest workspace first,
  * drained; results[i] belongs to reqs[i].  Returns RR_OK when every system
@@ -485,6 +568,10 @@ void rr_server_destroy(rr_server* s);
  */
 rr_status randrand_solve_batch(const rr_request* reqs, int32_t nsys, void* arena,
                                size_t arena_bytes, int32_t workers, rr_result* results);
+/* The same with shared rounds (rounds != NULL; see rr_rounds_opts). */
+rr_status randrand_solve_batch_rounds(const rr_request* reqs, int32_t nsys, void* arena,
+                                      size_t arena_bytes, int32_t workers,
+                                      const rr_rounds_opts* rounds, rr_result* results);
 
 #ifdef __cplusplus
 }

@@ -93,16 +93,29 @@ class rr_request(ctypes.Structure):
     ]
 
 
+class rr_group_rhs(ctypes.Structure):
+    _fields_ = [
+        ("b", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("x", ctypes.c_void_p),
+        ("ldx", ctypes.c_int64), ("nrhs", ctypes.c_int32), ("maxit", ctypes.c_int32),
+        ("rtol", ctypes.c_double),
+    ]
+
+
+class rr_rounds_opts(ctypes.Structure):
+    _fields_ = [("mp", ctypes.c_int32), ("kmax", ctypes.c_int32), ("max_systems", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("max_rows", ctypes.c_int64)]
+
+
 class rr_result(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("ws_bytes", ctypes.c_size_t),
         ("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double),
         ("queue_ms", ctypes.c_double), ("build_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
-        ("info", rr_solve_info * 8),
+        ("info", rr_solve_info * 8), ("rounds", ctypes.c_int32), ("pad_", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "info"}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("info", "pad_")}
         d["info"] = [self.info[i].as_dict() for i in range(self.nrhs)]
         return d
 
@@ -141,6 +154,11 @@ _SIGNATURES = [
      [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
       ctypes.POINTER(ctypes.c_double)]),
     ("randrand_core_jitter", ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    ("randrand_group_workspace_bytes", ctypes.c_int32,
+     [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    ("randrand_solve_group", ctypes.c_int32,
+     [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.POINTER(rr_group_rhs),
+      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(rr_solve_info)]),
     ("randrand_apply", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     ("randrand_profile", ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rr_profile)]),
@@ -158,6 +176,15 @@ _SIGNATURES = [
     ("rr_arena_stats", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     ("rr_arena_destroy", None, [ctypes.c_void_p]),
+    ("rr_rounds_workspace_bytes", ctypes.c_int32,
+     [ctypes.POINTER(rr_rounds_opts), ctypes.POINTER(ctypes.c_size_t)]),
+    ("rr_server_create_rounds", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(rr_rounds_opts),
+      ctypes.POINTER(ctypes.c_void_p)]),
+    ("rr_server_peak_running", ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    ("randrand_solve_batch_rounds", ctypes.c_int32,
+     [ctypes.POINTER(rr_request), ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
+      ctypes.POINTER(rr_rounds_opts), ctypes.POINTER(rr_result)]),
     ("rr_server_create", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
     ("rr_server_submit", ctypes.c_int32,
@@ -574,18 +601,45 @@ class Request:
         return randrand_workspace_bytes(self.op.c, self.c.k, self.c.opts)
 
 
-class Server:
-    """Serving loop (rr_server_*) over a device arena of ``budget_bytes``."""
+def rounds_opts(mp: int, kmax: int, max_systems: int, max_rows: int) -> rr_rounds_opts:
+    return rr_rounds_opts(mp=int(mp), kmax=int(kmax), max_systems=int(max_systems),
+                          max_rows=int(max_rows))
 
-    def __init__(self, budget_bytes: int, workers: int = 8):
+
+def rounds_workspace_bytes(o: rr_rounds_opts) -> int:
+    b = ctypes.c_size_t(0)
+    st = _lib().rr_rounds_workspace_bytes(ctypes.byref(o), ctypes.byref(b))
+    if st != RR_OK:
+        raise RandRandError(st, "rr_rounds_workspace_bytes")
+    return int(b.value)
+
+
+class Server:
+    """Serving loop (rr_server_*) over a device arena of ``budget_bytes``;
+    with ``rounds`` (an rr_rounds_opts) the qualifying systems iterate in
+    shared rounds, whose workspace is added to the arena."""
+
+    def __init__(self, budget_bytes: int, workers: int = 8, rounds: rr_rounds_opts | None = None):
         import torch
-        self.arena = torch.empty(int(budget_bytes), dtype=torch.uint8, device="cuda")
+        extra = rounds_workspace_bytes(rounds) if rounds is not None else 0
+        total = int(budget_bytes) + extra
+        self.arena = torch.empty(total, dtype=torch.uint8, device="cuda")
         self.s = ctypes.c_void_p(None)
-        st = _lib().rr_server_create(ctypes.c_void_p(self.arena.data_ptr()), int(budget_bytes),
-                                     int(workers), ctypes.byref(self.s))
+        self.rounds = rounds
+        if rounds is None:
+            st = _lib().rr_server_create(ctypes.c_void_p(self.arena.data_ptr()), total,
+                                         int(workers), ctypes.byref(self.s))
+        else:
+            st = _lib().rr_server_create_rounds(ctypes.c_void_p(self.arena.data_ptr()), total,
+                                                int(workers), ctypes.byref(rounds), ctypes.byref(self.s))
         if st != RR_OK:
             raise RandRandError(st, "rr_server_create")
         self._keep = {}
+
+    def peak_running(self) -> int:
+        p = ctypes.c_int32(0)
+        _lib().rr_server_peak_running(self.s, ctypes.byref(p))
+        return int(p.value)
 
     def submit(self, req: Request) -> int:
         t = ctypes.c_uint64(0)
@@ -628,19 +682,68 @@ class Server:
             pass
 
 
-def solve_batch(reqs: list, workers: int = 8, arena_bytes: int | None = None):
-    """randrand_solve_batch over the requests; returns (status, [result dicts])."""
+def solve_group(handles: list, bs: list, rtol, maxit=20000, stream=None):
+    """randrand_solve_group: the built handles' systems solved together in
+    shared rounds.  bs[i]: (n_i,) or (n_i, m_i) float64 CUDA tensor; rtol and
+    maxit scalars or per-system lists.  Returns (status, [x_i], [[info dicts]])."""
+    import torch
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.h if isinstance(h, Handle) else h for h in handles])
+    rtols = rtol if isinstance(rtol, (list, tuple)) else [rtol] * n
+    maxits = maxit if isinstance(maxit, (list, tuple)) else [maxit] * n
+    keep, rhs = [], (rr_group_rhs * n)()
+    for i, (h, b) in enumerate(zip(handles, bs)):
+        nn = b.shape[0]
+        B = b.reshape(nn, -1)
+        Bc = B.t().contiguous()
+        Xc = torch.zeros_like(Bc)
+        keep.append((Bc, Xc, b.shape))
+        rhs[i] = rr_group_rhs(b=Bc.data_ptr(), ldb=nn, x=Xc.data_ptr(), ldx=nn, nrhs=B.shape[1],
+                              maxit=int(maxits[i]), rtol=float(rtols[i]))
+    ws_bytes = ctypes.c_size_t(0)
+    st = _lib().randrand_group_workspace_bytes(hs, n, ctypes.byref(ws_bytes))
+    if st != RR_OK:
+        raise RandRandError(st, "randrand_group_workspace_bytes")
+    ws = torch.empty(max(int(ws_bytes.value), 256), dtype=torch.uint8, device="cuda")
+    strm = stream if stream is not None else torch.cuda.current_stream()
+    infos = (rr_solve_info * (8 * n))()
+    st = _lib().randrand_solve_group(hs, n, rhs, ctypes.c_void_p(ws.data_ptr()), int(ws_bytes.value),
+                                     ctypes.c_void_p(strm.cuda_stream), infos)
+    xs = [Xc.t().reshape(shape) for _, Xc, shape in keep]
+    out = [[infos[8 * i + c].as_dict() for c in range(rhs[i].nrhs)] for i in range(n)]
+    return st, xs, out
+
+
+def solve_batch(reqs: list, workers: int = 8, arena_bytes: int | None = None,
+                rounds: rr_rounds_opts | None = None):
+    """randrand_solve_batch (or, with ``rounds``, randrand_solve_batch_rounds)
+    over the requests; returns (status, [result dicts])."""
     import torch
     n = len(reqs)
     arr = (rr_request * n)(*[r.c for r in reqs])
     res = (rr_result * n)()
     if arena_bytes is None:
         arena_bytes = sum((r.workspace_bytes() + 255) // 256 * 256 for r in reqs)
+    if rounds is not None:
+        arena_bytes += rounds_workspace_bytes(rounds)
     arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
-    st = _lib().randrand_solve_batch(arr, n, ctypes.c_void_p(arena.data_ptr()), int(arena_bytes),
-                                     int(workers), res)
+    if rounds is None:
+        st = _lib().randrand_solve_batch(arr, n, ctypes.c_void_p(arena.data_ptr()), int(arena_bytes),
+                                         int(workers), res)
+    else:
+        st = _lib().randrand_solve_batch_rounds(arr, n, ctypes.c_void_p(arena.data_ptr()),
+                                                int(arena_bytes), int(workers), ctypes.byref(rounds), res)
     del arena
     return st, [res[i].as_dict() for i in range(n)]
+
+
+def batch_rounds_opts(reqs: list) -> rr_rounds_opts:
+    """Rounds capacity for a batch: every request resident at once."""
+    mp = 2
+    while mp < max(r.c.nrhs for r in reqs):
+        mp *= 2
+    rows = sum((r.op.n + 255) // 256 * 256 for r in reqs)
+    return rounds_opts(mp, max(r.c.k for r in reqs), min(len(reqs), 152), rows)
 
 
 load_library()

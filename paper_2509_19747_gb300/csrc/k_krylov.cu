@@ -8,6 +8,7 @@
 // writes its partial, fences, and takes a ticket; the CTA that draws the
 // last ticket sums the partials in block order (deterministic) and updates
 // the per-column Krylov scalars.  No CTA ever waits for another.
+#include <algorithm>
 #include <cmath>
 
 #include "rr_common.cuh"
@@ -1063,13 +1064,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__device__ bool grid_barrier(GridBar* gb, int* err) {
+// g CTAs (all of the launch, or the CTAs of one system in a grouped launch)
+__device__ bool grid_barrier(GridBar* gb, int* err, unsigned long long g) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
     __threadfence();
-    const unsigned long long g = gridDim.x;
     const unsigned long long old = atomicAdd(&gb->arrivals, 1ull);
     const unsigned long long target = (old / g + 1) * g;
     if (old + 1 != target) {
@@ -1091,26 +1092,7 @@ __device__ bool grid_barrier(GridBar* gb, int* err) {
   __syncthreads();
   return ok != 0;
 }
-
-template <typename T>
-struct TailArgs {
-  T* E;
-  T* R;
-  T* P;
-  T* Z;
-  const T* W;
-  const T* Q;
-  const T* QH;
-  int64_t n;
-  int k;
-  int rpc;
-  int alpha_mode;     // 0: p^T w here; 1: the product kernel applied alpha to cs;
-                      // 2: the product kernel accumulated p^T w into this launch's set
-  double* acc;        // two sets of [pw 8 | rr 8 | rz 8 | t k x 8]
-  ColState* cs;
-  GridBar* bar;
-  int* err;
-};
+__device__ bool grid_barrier(GridBar* gb, int* err) { return grid_barrier(gb, err, gridDim.x); }
 
 __host__ __device__ inline size_t tail_set_doubles(int k) { return 24 + (size_t)k * 8; }
 
@@ -1217,8 +1199,10 @@ __device__ void tail_qtr(const T* __restrict__ Q, const T* __restrict__ R, int64
   }
 }
 
+// Alg. 7 steps 6-9 for the rows of CTA `cta` of the `ncta` CTAs that serve
+// this system (the whole grid, or the system's CTAs of a grouped launch)
 template <typename T, int MP>
-__global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
+__device__ __forceinline__ void pcg_tail_body(const TailArgs<T>& a, const int cta, const int ncta) {
   extern __shared__ unsigned char smem_raw[];
   T* sT = reinterpret_cast<T*>(smem_raw);                         // t, column-major [MP][k]
   T* Rs = sT + (size_t)a.k * MP;                                   // kFusedChunk x MP
@@ -1229,7 +1213,6 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
   __shared__ double redd[kFT / 32 * 8];
   __shared__ unsigned sh_parity;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int cta = blockIdx.x;
   const int k = a.k;
   const int64_t r0 = (int64_t)cta * a.rpc;
   const int cnt = (int)(r0 >= a.n ? 0 : (a.n - r0 < a.rpc ? a.n - r0 : a.rpc));
@@ -1276,7 +1259,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
     block_sum_cols<kFT>(v, MP, redd);
     if (tid == 0 && cnt > 0)
       for (int c = 0; c < MP; ++c) atomicAdd(acc + c, v[c]);
-    if (!grid_barrier(a.bar, a.err)) return;
+    if (!grid_barrier(a.bar, a.err, (unsigned long long)ncta)) return;
     if (tid < MP) {
       const int c = tid;
       const double pw = __ldcg(acc + c);
@@ -1319,7 +1302,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
     for (int c = 0; c < MP; ++c) atomicAdd(acc + 8 + c, v[c]);
   __syncthreads();
   tail_qtr<T, MP>(a.Q, a.R, r0, cnt, k, tacc, Rs, red);
-  if (!grid_barrier(a.bar, a.err)) return;
+  if (!grid_barrier(a.bar, a.err, (unsigned long long)ncta)) return;
 
   // ---- E: convergence decision; z = r + (Q H) t; r^T z
   if (tid < MP) {
@@ -1440,7 +1423,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
   block_sum_cols<kFT>(v, MP, redd);
   if (tid == 0 && cnt > 0)
     for (int c = 0; c < MP; ++c) atomicAdd(acc + 16 + c, v[c]);
-  if (!grid_barrier(a.bar, a.err)) return;
+  if (!grid_barrier(a.bar, a.err, (unsigned long long)ncta)) return;
 
   // ---- F: beta, p = z + beta p
   if (tid < MP) {
@@ -1488,6 +1471,34 @@ __global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
     a.cs[c] = st;
   }
   if (cta == 0 && tid == 0) atomicAdd(&a.bar->launches, 1u);
+}
+
+template <typename T, int MP>
+__global__ void __launch_bounds__(kFT, 1) k_pcg_tail(TailArgs<T> a) {
+  pcg_tail_body<T, MP>(a, blockIdx.x, gridDim.x);
+}
+
+// Several systems' steps in one cooperative launch: system s owns the CTAs
+// [cta0[s], cta0[s + 1]) and synchronises only among them (its own grid
+// barrier).  CTAs beyond the last system's return at once.
+template <typename T, int MP>
+__global__ void __launch_bounds__(kFT, 1) k_pcg_tail_group(const TailGroupHdr* __restrict__ hdr,
+                                                           const TailArgs<T>* __restrict__ tab) {
+  const int nsys = hdr->nsys;
+  const int c = blockIdx.x;
+  if (nsys < 1 || c >= hdr->cta0[nsys]) return;
+  int lo = 0, hi = nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (hdr->cta0[mid] <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  // the system's arguments in shared memory, read where they are used
+  __shared__ TailArgs<T> sa;
+  if (threadIdx.x == 0) sa = tab[lo];
+  __syncthreads();
+  const int c0 = hdr->cta0[lo];
+  pcg_tail_body<T, MP>(sa, c - c0, hdr->cta0[lo + 1] - c0);
 }
 
 // row-phase partials of the fused step's Q^T r (kFT threads over k / 4 quads)
@@ -1584,6 +1595,84 @@ cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const T* QH
     case 2: return launch_tail<T, 2>(a, G, smem, st);
     case 4: return launch_tail<T, 4>(a, G, smem, st);
     default: return launch_tail<T, 8>(a, G, smem, st);
+  }
+}
+
+template <typename T, int MP>
+static bool tail_group_attr() {
+  static std::atomic<uint64_t> done{0};
+  return once_per_device(done, [] {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return false;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_pcg_tail_group<T, MP>) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (cudaFuncSetAttribute(k_pcg_tail_group<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  });
+}
+
+template <typename T, int MP>
+static cudaError_t launch_tail_group(const TailGroupHdr* hdr, const TailArgs<T>* tab, int grid,
+                                     size_t smem, cudaStream_t st) {
+  if (!tail_group_attr<T, MP>()) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kFT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_pcg_tail_group<T, MP>, hdr, tab);
+}
+
+// dynamic shared memory of a grouped step whose systems have k <= kmax (the
+// row-phase partials grow as k shrinks, so the bound is a maximum over k)
+template <typename T>
+static size_t tail_group_smem(int kmax, int mp) {
+  size_t m = 0;
+  for (int k = 1; k <= kmax; ++k) m = std::max(m, pcg_tail_smem<T>(k, mp));
+  return m;
+}
+
+bool pcg_tail_group_fits(int kmax, int mp) {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return false;
+  return tail_group_smem<float>(kmax, mp) + 4096 <= (size_t)optin;
+}
+
+template <typename T>
+cudaError_t pcg_tail_group(const TailGroupHdr* hdr, const TailArgs<T>* tab, int kmax, int mp,
+                           int grid, cudaStream_t st) {
+  if (grid < 1 || grid > kTailGroupMax) return cudaErrorInvalidValue;
+  const size_t smem = tail_group_smem<T>(kmax, mp);
+  switch (mp) {
+    case 1: return launch_tail_group<T, 1>(hdr, tab, grid, smem, st);
+    case 2: return launch_tail_group<T, 2>(hdr, tab, grid, smem, st);
+    case 4: return launch_tail_group<T, 4>(hdr, tab, grid, smem, st);
+    default: return launch_tail_group<T, 8>(hdr, tab, grid, smem, st);
+  }
+}
+
+bool pcg_tail_group_prepare(int mp) {
+  switch (mp) {
+    case 1: return tail_group_attr<float, 1>();
+    case 2: return tail_group_attr<float, 2>();
+    case 4: return tail_group_attr<float, 4>();
+    default: return tail_group_attr<float, 8>();
   }
 }
 
@@ -2097,6 +2186,10 @@ template int r_step_ctas<float>(int64_t, int, int);
 template int r_step_ctas<double>(int64_t, int, int);
 template int pcg_tail_ctas<float>(int64_t, int, int);
 template int pcg_tail_ctas<double>(int64_t, int, int);
+template cudaError_t pcg_tail_group<float>(const TailGroupHdr*, const TailArgs<float>*, int, int,
+                                           int, cudaStream_t);
+template cudaError_t pcg_tail_group<double>(const TailGroupHdr*, const TailArgs<double>*, int, int,
+                                            int, cudaStream_t);
 template cudaError_t pcg_tail<float>(float*, float*, float*, float*, const float*, const float*,
                                      const float*, int64_t, int, int, int, int, double*,
                                      ColState*, GridBar*, int*, cudaStream_t);

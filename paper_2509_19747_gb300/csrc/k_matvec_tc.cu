@@ -33,6 +33,7 @@
 #include <cuda.h>
 
 #include <cmath>
+#include <cstring>
 
 #include "rr_common.cuh"
 #include "tc_common.cuh"
@@ -75,38 +76,73 @@ constexpr size_t mv_smem_bytes() {
   return 1024 + 2 * (size_t)kABytes + (size_t)kStagesB * kBBytes + sizeof(MvSmem<MP>);
 }
 
-// the segment of CTA c starting at work item x (its range ends at xend)
+// the segment of CTA c starting at work item x (its range ends at xend): a
+// run of point tiles of one row pair of system S, whose work items are
+// [S.item0, S.item0 + pairs * tiles) of the launch's total
 struct MvSeg {
-  int64_t row0, j0;
-  int ntiles, slot;
+  int64_t row0, j0;                  // first row of the pair and first point, in the system
+  int64_t grow0, gj0;                // the same as rows of the (stacked) augmented arrays
+  int64_t pair;                      // row pair within the system
+  int ntiles, slot, nseg;            // tiles; rank among the nseg CTAs touching the pair
   bool last;                         // the segment ends the row pair
 };
-__device__ __forceinline__ MvSeg mv_seg(int64_t x, int64_t xend, int64_t tiles, int64_t total,
+__device__ __forceinline__ MvSeg mv_seg(int64_t x, int64_t xend, const MvSys& S, int64_t total,
                                         int64_t g, int64_t c) {
-  const SkSeg k = sk_seg(x, xend, tiles, total, g, c);
+  const int64_t local = x - S.item0;
   MvSeg w;
-  w.row0 = k.pair * (kRows * kRB);
-  w.j0 = k.t0 * kPts;
-  w.ntiles = k.ntiles;
-  w.slot = k.slot;
-  w.last = k.last;
+  w.pair = local / S.tiles;
+  const int64_t a = S.item0 + w.pair * S.tiles, b = a + S.tiles;
+  const int64_t e = xend < b ? xend : b;
+  w.ntiles = (int)(e - x);
+  w.slot = (int)(c - sk_cta_of(a, total, g));
+  w.nseg = (int)(sk_cta_of(b - 1, total, g) - sk_cta_of(a, total, g) + 1);
+  w.last = e == b;
+  w.row0 = w.pair * (kRows * kRB);
+  w.j0 = (local - w.pair * S.tiles) * kPts;
+  w.grow0 = S.row_off + w.row0;
+  w.gj0 = S.row_off + w.j0;
   return w;
 }
 
-template <int MP>
+__device__ __forceinline__ bool mv_live(const ColState* gate, int gate_mp) {
+  if (!gate) return true;
+  bool any = false;
+  for (int c = 0; c < gate_mp; ++c) any |= gate[c].active != 0;
+  return any;
+}
+
+// the system of work item x: the last entry whose first item is <= x
+__device__ __forceinline__ int mv_sys_of(const MvSys* tab, int nsys, int64_t x) {
+  int lo = 0, hi = nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].item0 <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// GROUP = false: one system, given by `one` (item0 = row_off = 0) with
+// total_arg items and its column states as the launch's gate.  GROUP = true:
+// the systems of the device table `tab` (header `hdr`), each skipped while
+// none of its columns is active.
+template <int MP, bool GROUP>
 __global__ void __launch_bounds__(kThreadsMv, 1)
     k_kernel_mv_tc(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
-                   int64_t n, int64_t tiles, int64_t total, int nslots,
-                   const float* __restrict__ V, float* __restrict__ part, int* __restrict__ err,
-                   const ColState* __restrict__ gate, int gate_mp, float* __restrict__ W,
-                   float mu, unsigned* __restrict__ pair_cnt, double* __restrict__ pw_acc,
-                   int64_t pw_set, const unsigned* __restrict__ pw_launches) {
-  if (gate) {
-    // inside the Krylov iterations: nothing to do once every column is done
-    bool any = false;
-    for (int c = 0; c < gate_mp; ++c) any |= gate[c].active != 0;
-    if (!any) return;
-  }
+                   const __grid_constant__ MvSys one, int64_t total_arg, int gate_mp_arg,
+                   const MvGroupHdr* __restrict__ hdr, const MvSys* __restrict__ tab,
+                   int* __restrict__ err) {
+  const int64_t total = GROUP ? hdr->total : total_arg;
+  const int nsys = GROUP ? hdr->nsys : 1;
+  const int gate_mp = GROUP ? hdr->gate_mp : gate_mp_arg;
+  // inside the Krylov iterations: nothing to do once every column is done
+  if (!GROUP && !mv_live(one.gate, gate_mp)) return;
+  if (GROUP && (nsys < 1 || total < 1)) return;
+  // the work items are spread over g = min(grid, total) CTAs, so that no
+  // range is empty (a pair's slots then count the CTAs that touch it); a
+  // grouped launch's grid is fixed when it is captured, the surplus CTAs idle
+  const int64_t g = (int64_t)gridDim.x < total ? (int64_t)gridDim.x : total;
+  if ((int64_t)blockIdx.x >= g) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = base;                                   // two unit buffers
@@ -148,24 +184,35 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
 
   // every role walks the same segments of this CTA's range and counts them
   // (k) and its tiles (T) for stage indices and parities
-  const int64_t xbeg = (int64_t)blockIdx.x * total / gridDim.x;
-  const int64_t xend = ((int64_t)blockIdx.x + 1) * total / gridDim.x;
+  const int64_t xbeg = (int64_t)blockIdx.x * total / g;
+  const int64_t xend = ((int64_t)blockIdx.x + 1) * total / g;
+  const int s0 = GROUP ? mv_sys_of(tab, nsys, xbeg < total ? xbeg : total - 1) : 0;
+  // every role walks the same segments; a segment of a system with no active
+  // column is skipped by all of them (no counter advances)
+#define RR_MV_NEXT_SEG(S, w, s)                                                    \
+  if (GROUP)                                                                       \
+    while (s + 1 < nsys && tab[s + 1].item0 <= x) ++s;                             \
+  const MvSys& S = GROUP ? tab[s] : one;                                           \
+  const MvSeg w = mv_seg(x, xend, S, total, g, blockIdx.x);                        \
+  x += w.ntiles;                                                                   \
+  if (GROUP && !mv_live(S.gate, gate_mp)) continue;
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       int issued_a = 0, issued_b = 0, issued_v = 0;
-      int T = 0, k = 0;
+      int T = 0, k = 0, s = s0;
       bool ok = true;
-      for (int64_t x = xbeg; x < xend && ok; ++k) {
-        const MvSeg w = mv_seg(x, xend, tiles, total, gridDim.x, blockIdx.x);
-        x += w.ntiles;
+      for (int64_t x = xbeg; x < xend && ok;) {
+        RR_MV_NEXT_SEG(S, w, s)
         const int ab = k & 1;
         if (k >= 2 && !mbar_wait(&sm->a_empty[ab], ((k >> 1) - 1) & 1, err, abort)) break;
+        ++k;
         mbar_arrive_tx(&sm->a_full[ab], kABytes);
         for (int b = 0; b < kRB; ++b)
           tma_load_2d(sA + (size_t)ab * kABytes + (size_t)b * kAtomA, &amap, 0,
-                      (int)(w.row0 + b * kRows), &sm->a_full[ab]);
+                      (int)(w.grow0 + b * kRows), &sm->a_full[ab]);
         ++issued_a;
+        const float* Vs = S.V;
         for (int t = 0; t < w.ntiles; ++t, ++T) {
           const int sb = T % kStagesB, sv = T % kStagesV;
           const int64_t jt = w.j0 + (int64_t)t * kPts;
@@ -174,14 +221,15 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
             break;
           }
           mbar_arrive_tx(&sm->b_full[sb], kBBytes);
-          tma_load_2d(sB + (size_t)sb * kBBytes, &bmap, 0, (int)jt, &sm->b_full[sb]);
+          tma_load_2d(sB + (size_t)sb * kBBytes, &bmap, 0, (int)(w.gj0 + (int64_t)t * kPts),
+                      &sm->b_full[sb]);
           ++issued_b;
           if (T >= kStagesV && !mbar_wait(&sm->v_empty[sv], ((T / kStagesV) - 1) & 1, err, abort)) {
             ok = false;
             break;
           }
           mbar_arrive_tx(&sm->v_full[sv], kVBytes);
-          bulk_load(sm->v[sv], V + jt * MP, kVBytes, &sm->v_full[sv]);
+          bulk_load(sm->v[sv], Vs + jt * MP, kVBytes, &sm->v_full[sv]);
           ++issued_v;
         }
       }
@@ -197,12 +245,13 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
     // ----------------------------------------------------------------- MMA
     if (lane == 0) {
       bool ok = true;
-      int T = 0, k = 0;
-      for (int64_t x = xbeg; x < xend && ok; ++k) {
-        const MvSeg w = mv_seg(x, xend, tiles, total, gridDim.x, blockIdx.x);
-        x += w.ntiles;
+      int T = 0, k = 0, s = s0;
+      for (int64_t x = xbeg; x < xend && ok;) {
+        RR_MV_NEXT_SEG(S, w, s)
+        (void)S.n;
         const int ab = k & 1;
         ok = mbar_wait(&sm->a_full[ab], (k >> 1) & 1, err, abort);
+        ++k;
         for (int t = 0; t < w.ntiles && ok; ++t, ++T) {
           const int sb = T % kStagesB, buf = T & 1;
           ok = mbar_wait(&sm->b_full[sb], (T / kStagesB) & 1, err, abort);
@@ -235,10 +284,13 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
     const int r = q * 32 + lane;                // row within each row block
     constexpr int kP2 = MP >= 2 ? MP / 2 : 1;
     bool ok = true;
-    int T = 0, k = 0;
-    for (int64_t x = xbeg; x < xend && ok; ++k) {
-      const MvSeg w = mv_seg(x, xend, tiles, total, gridDim.x, blockIdx.x);
-      x += w.ntiles;
+    int T = 0, k = -1, s = s0;
+    for (int64_t x = xbeg; x < xend && ok;) {
+      RR_MV_NEXT_SEG(S, w, s)
+      ++k;                                      // processed segments, from 0
+      const int64_t n = S.n;
+      float* const part = S.part;
+      float* const W = S.W;
       float acc[MP], acc1[MP];                  // partial sums of this thread's two rows
       unsigned long long acc2[kP2], acc12[kP2]; // the same as packed column pairs (MP >= 2)
 #pragma unroll
@@ -361,7 +413,7 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
                        sm->quarter[1][b * kRows + r][c] + sm->quarter[2][b * kRows + r][c];
             // the CTA that ends the row pair clears the slots no CTA uses
             if (w.last && !W)
-              for (int sl = w.slot + 1; sl < nslots; ++sl)
+              for (int sl = w.slot + 1; sl < S.nslots; ++sl)
 #pragma unroll
                 for (int c = 0; c < MP; ++c) part[((int64_t)sl * n + gi) * MP + c] = 0.f;
           }
@@ -374,13 +426,15 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
           // its partials are visible; the last of the pair's nseg arrivals
           // sums that quarter's slots (fixed order) into W = sum + mu V and
           // resets the counter.  No warp waits.
-          const int64_t pair = w.row0 / (kRows * kRB);
-          const int nseg = (int)(sk_cta_of((pair + 1) * tiles - 1, total, gridDim.x) -
-                                 sk_cta_of(pair * tiles, total, gridDim.x) + 1);
+          const int64_t pair = w.pair;
+          const int nseg = w.nseg;
+          const float* const V = S.V;
+          const float mu = S.mu;
+          double* const pw_acc = S.pw_acc;
           __threadfence();
           __syncwarp();
           unsigned lastw = 0u;
-          unsigned* ctr = pair_cnt + pair * 4 + q;
+          unsigned* ctr = S.pair_cnt + pair * 4 + q;
           if (lane == 0) {
             lastw = atomicAdd(ctr, 1u) == (unsigned)nseg - 1u ? 1u : 0u;
             if (lastw) *ctr = 0u;
@@ -425,7 +479,7 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
               for (int c = 0; c < MP; ++c)
                 for (int o = 16; o > 0; o >>= 1) pw[c] += __shfl_xor_sync(0xffffffffu, pw[c], o);
               if (lane == 0) {
-                double* dst = pw_acc + (int64_t)(*(volatile const unsigned*)pw_launches & 1u) * pw_set;
+                double* dst = pw_acc + (int64_t)(*(volatile const unsigned*)S.pw_launches & 1u) * S.pw_set;
 #pragma unroll
                 for (int c = 0; c < MP; ++c) atomicAdd(dst + c, pw[c]);
               }
@@ -441,6 +495,7 @@ __global__ void __launch_bounds__(kThreadsMv, 1)
     fence_after();
     tmem_dealloc(tmem, kTmemCols);
   }
+#undef RR_MV_NEXT_SEG
 }
 
 // augmented TF32-split vectors: A rows [u_hi u_hi u_lo 0 0], B rows [w_hi w_lo w_hi 0 0]
@@ -515,11 +570,11 @@ bool encode_aug(CUtensorMap* map, const float* base, int64_t npad) {
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int MP>
+template <int MP, bool GROUP>
 bool set_attr() {
   static std::atomic<uint64_t> done{0};
   return once_per_device(done, [] {
-    return cudaFuncSetAttribute(k_kernel_mv_tc<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_kernel_mv_tc<MP, GROUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)mv_smem_bytes<MP>()) == cudaSuccess;
   });
 }
@@ -595,12 +650,26 @@ bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const f
   const unsigned grid = (unsigned)tc_persistent_ctas(total);
   const CUtensorMap& am = *(const CUtensorMap*)amap;
   const CUtensorMap& bm = *(const CUtensorMap*)bmap;
-#define RR_MVTC(MPV)                                                                             \
-  if (!set_attr<MPV>()) return false;                                                            \
-  k_kernel_mv_tc<MPV><<<grid, kThreadsMv, mv_smem_bytes<MPV>(), st>>>(am, bm, n, tiles, total,    \
-                                                                      nslots, V, part, err, gate, \
-                                                                      gate_mp, W, mu, pair_cnt,   \
-                                                                      pw_acc, pw_set, pw_launches);
+  MvSys one;
+  one.n = n;
+  one.tiles = tiles;
+  one.item0 = 0;
+  one.row_off = 0;
+  one.V = V;
+  one.part = part;
+  one.W = W;
+  one.pair_cnt = pair_cnt;
+  one.pw_acc = pw_acc;
+  one.pw_set = pw_set;
+  one.pw_launches = pw_launches;
+  one.gate = gate;
+  one.mu = mu;
+  one.nslots = nslots;
+#define RR_MVTC(MPV)                                                                          \
+  if (!set_attr<MPV, false>()) return false;                                                  \
+  k_kernel_mv_tc<MPV, false><<<grid, kThreadsMv, mv_smem_bytes<MPV>(), st>>>(am, bm, one, total, \
+                                                                             gate_mp, nullptr,   \
+                                                                             nullptr, err);
   switch (mp) {
     case 1: RR_MVTC(1) break;
     case 2: RR_MVTC(2) break;
@@ -608,6 +677,55 @@ bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const f
     default: RR_MVTC(8) break;
   }
 #undef RR_MVTC
+  return cudaGetLastError() == cudaSuccess;
+}
+
+int64_t mv_tc_items(int64_t n) { return (mv_tc_pad(n) / (kRows * kRB)) * cdiv(n, kPts); }
+
+int mv_tc_group_slots(int64_t n, int64_t item0, int64_t total, int64_t g) {
+  if (g > total) g = total;          // the kernel spreads the items over min(grid, total) CTAs
+  const int64_t pairs = mv_tc_pad(n) / (kRows * kRB), tiles = cdiv(n, kPts);
+  int64_t most = 1;
+  for (int64_t p = 0; p < pairs; ++p) {
+    const int64_t a = item0 + p * tiles, b = a + tiles;
+    const int64_t c = sk_cta_of(b - 1, total, g) - sk_cta_of(a, total, g) + 1;
+    if (c > most) most = c;
+  }
+  return (int)most;
+}
+
+bool encode_mv_tc_group(const float* Aaug, const float* Baug, int64_t rows, void* amap, void* bmap) {
+  return encode_aug((CUtensorMap*)amap, Aaug, rows) && encode_aug((CUtensorMap*)bmap, Baug, rows);
+}
+
+bool kernel_mv_tc_group_prepare(int mp) {
+  switch (mp) {
+    case 1: return set_attr<1, true>();
+    case 2: return set_attr<2, true>();
+    case 4: return set_attr<4, true>();
+    default: return set_attr<8, true>();
+  }
+}
+
+// one persistent launch over every system of the table (grid CTAs; the table
+// and its header are read on the device when the launch runs)
+bool kernel_mv_tc_group(const void* amap, const void* bmap, const MvGroupHdr* hdr,
+                        const MvSys* tab, int mp, int grid, int* err, cudaStream_t st) {
+  const CUtensorMap& am = *(const CUtensorMap*)amap;
+  const CUtensorMap& bm = *(const CUtensorMap*)bmap;
+  MvSys none;
+  memset(&none, 0, sizeof(none));
+#define RR_MVTCG(MPV)                                                                         \
+  if (!set_attr<MPV, true>()) return false;                                                   \
+  k_kernel_mv_tc<MPV, true><<<(unsigned)grid, kThreadsMv, mv_smem_bytes<MPV>(), st>>>(          \
+      am, bm, none, 0, 0, hdr, tab, err);
+  switch (mp) {
+    case 1: RR_MVTCG(1) break;
+    case 2: RR_MVTCG(2) break;
+    case 4: RR_MVTCG(4) break;
+    default: RR_MVTCG(8) break;
+  }
+#undef RR_MVTCG
   return cudaGetLastError() == cudaSuccess;
 }
 

@@ -8,11 +8,14 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <chrono>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
 
 #include "rr_common.cuh"
+#include "rr_group.cuh"
 #include "rr_krylov.cuh"
 
 using namespace rr;
@@ -1817,7 +1820,752 @@ void apply_impl(rr_handle* h) {
   axpby<double, T, double>(nullptr, coefs_all(0.0), Zv, coefs_all(1.0), h->v64[kW64], n, mp, h->st);
 }
 
+
+// ======================================================================
+// Shared rounds: the Krylov iterations of several built systems advanced
+// together.  Every round is one grouped tensor-core product (all systems'
+// (row pair, point tile) items in one persistent launch) and one grouped
+// persistent PCG step (each system on its own CTAs and grid barrier); R
+// rounds are captured once in a CUDA graph whose kernels read the group's
+// system tables from device memory, so the same graph serves the group as
+// systems join and leave.  Between replays the host reads every system's
+// column states at once and runs the restarts (the float64-accurate
+// residual, Alg. 7 step 10) of the systems whose inner solves ended.
+// Systems qualify when they iterate in float32 with the tensor-core kernel
+// product and the persistent step (variant C, explicit basis, Gaussian
+// kernel in d = 8).
+// ======================================================================
+constexpr int kGroupMaxSys = kTailGroupMax;
+
+__global__ void k_group_gather_cs(const MvSys* __restrict__ tab, const MvGroupHdr* __restrict__ hdr,
+                                  int mp, ColState* __restrict__ out) {
+  const int s = blockIdx.x;
+  if (s >= hdr->nsys) return;
+  for (int c = threadIdx.x; c < mp; c += blockDim.x) out[s * 8 + c] = tab[s].gate[c];
+}
+
+struct GroupWs {
+  size_t a, b, mvhdr, mvtab, thdr, ttab, csg, err, part, total;
+};
+
+GroupWs group_ws(int mp, int maxsys, int64_t max_rows, size_t part_bytes) {
+  GroupWs L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += align256(bytes);
+    return at;
+  };
+  L.a = take((size_t)max_rows * kAugFloats * 4);
+  L.b = take((size_t)max_rows * kAugFloats * 4);
+  L.mvhdr = take(sizeof(MvGroupHdr));
+  L.mvtab = take((size_t)maxsys * sizeof(MvSys));
+  L.thdr = take(sizeof(TailGroupHdr));
+  L.ttab = take((size_t)maxsys * sizeof(TailArgs<float>));
+  L.csg = take((size_t)maxsys * 8 * sizeof(ColState));
+  L.err = take(sizeof(int) * 4);
+  L.part = take(part_bytes);
+  L.total = o;
+  (void)mp;
+  return L;
+}
+
+// one system in the group: the request and the restart loop's state (the
+// same bookkeeping as solve_impl)
+struct GroupSys {
+  rr_handle* h = nullptr;
+  cudaStream_t st_saved = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  int64_t ldb = 0, ldx = 0;
+  int m = 1;
+  double rtol = 1e-6;
+  int maxit = 1;
+  rr_solve_info* info = nullptr;
+  double bn2[8] = {0}, rel[8] = {0};
+  int used[8] = {0}, outer[8] = {0}, mv[8] = {0}, stat[8] = {0};
+  bool done[8] = {false};
+  bool active[8] = {false};      // columns of the running inner solve
+  int restart = 0;
+  int iters_seen = 0;            // inner iterations read at the last replay (tuner)
+  bool finished = false;
+  rr_status status = RR_OK;
+  size_t row_slot = 0;
+  int64_t row_off = -1;
+  int64_t part_off = -1;         // 256-byte blocks of the group's partial-sum pool
+  int64_t part_blocks = 0;
+  void* user = nullptr;          // the serving loop's job
+};
+
+// first-fit allocator of unit blocks (the stacked rows of a group)
+struct rr_arena_lite {
+  std::map<int64_t, int64_t> free_, used_;
+  void reset(int64_t units) {
+    free_.clear();
+    used_.clear();
+    if (units > 0) free_[0] = units;
+  }
+  bool alloc(int64_t want, int64_t* off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < want) continue;
+      const int64_t o = it->first, rest = it->second - want;
+      free_.erase(it);
+      if (rest) free_[o + want] = rest;
+      used_[o] = want;
+      *off = o;
+      return true;
+    }
+    return false;
+  }
+  void release(int64_t off) {
+    auto u = used_.find(off);
+    if (u == used_.end()) return;
+    int64_t o = off, sz = u->second;
+    used_.erase(u);
+    auto next = free_.lower_bound(o);
+    if (next != free_.end() && next->first == o + sz) {
+      sz += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == o) {
+        o = prev->first;
+        sz += prev->second;
+        free_.erase(prev);
+      }
+    }
+    free_[o] = sz;
+  }
+};
+
+struct GroupExec {
+  int mp = 0, kmax = 0, maxsys = 0;
+  int64_t max_rows = 0;
+  size_t part_bytes = 0;
+  cudaStream_t st = nullptr;
+  GroupWs L;
+  unsigned char* ws = nullptr;
+  float *A = nullptr, *B = nullptr, *part = nullptr;
+  MvGroupHdr* d_mvhdr = nullptr;
+  MvSys* d_mvtab = nullptr;
+  TailGroupHdr* d_thdr = nullptr;
+  TailArgs<float>* d_ttab = nullptr;
+  ColState* d_csg = nullptr;
+  int* d_err = nullptr;
+  ColState* h_csg = nullptr;     // pinned host mirror
+  alignas(64) unsigned char amap[128];
+  alignas(64) unsigned char bmap[128];
+  MvGroupHdr mvhdr;
+  TailGroupHdr thdr;
+  std::vector<MvSys> mvtab;
+  std::vector<TailArgs<float>> ttab;
+  std::vector<GroupSys*> sys;   // systems whose inner solves run in the rounds
+  rr_arena_lite rows;           // 256-row blocks of the stacked arrays
+  rr_arena_lite parts;          // 256-byte blocks of the partial-sum pool
+  int grid = 0;
+  std::vector<std::pair<int, cudaGraphExec_t>> graphs;
+  int R = 0;                    // rounds per replay (tuner)
+  int replays = 0;
+  std::vector<std::pair<int, double>> trials;   // (R, seconds per unit of progress)
+  uint64_t tune_key = 0;
+};
+
+
+// tuner: rounds per graph replay, cached per (mp, log2 mean n, log2 mean k)
+std::mutex g_tune_mu;
+std::map<uint64_t, int> g_tune_R;
+constexpr int kTuneR[4] = {2, 4, 8, 16};
+
+uint64_t group_tune_key(int mp, double mean_n, double mean_k) {
+  const uint64_t bn = (uint64_t)std::max(0.0, std::floor(std::log2(std::max(mean_n, 1.0))));
+  const uint64_t bk = (uint64_t)std::max(0.0, std::floor(std::log2(std::max(mean_k, 1.0))));
+  return ((uint64_t)mp << 32) | (bn << 16) | bk;
+}
+
+// partial-sum bytes of one system in any grouped layout over g CTAs: CTA
+// ranges hold at least floor(total / g) >= floor(items / g) items, so the
+// tiles of a row pair meet at most ceil(tiles / that) + 1 of them
+size_t group_part_bound(int64_t n, int mp, int g) {
+  const int64_t items = mv_tc_items(n), tiles = items / (mv_tc_pad(n) / 256);
+  const int64_t r = std::max<int64_t>(1, items / g);
+  const int64_t slots = std::min<int64_t>(cdiv(tiles, r) + 1, tiles);
+  return align256((size_t)slots * n * mp * 4);
+}
+
+bool group_qualifies(const rr_handle* h) {
+  return h && !h->f64 && h->op.kind == RR_OP_GAUSS_KERNEL && h->op.use_tc && !h->op.tc2 &&
+         h->o.variant == RR_VARIANT_C && !h->implicit && h->fusedG > 0 && h->o.iter_impl == 0 &&
+         h->Q && h->QH && h->op.pair_cnt && !h->prof;
+}
+
+// rebuild the device tables for the systems now in the rounds
+rr_status group_rebuild(GroupExec& g) {
+  const int ns = (int)g.sys.size();
+  g.mvtab.assign(ns, MvSys());
+  g.ttab.assign(ns, TailArgs<float>());
+  int64_t total = 0;
+  for (GroupSys* q : g.sys) total += mv_tc_items(q->h->n);
+  int64_t item0 = 0;
+  double wsum = 0.0;
+  for (GroupSys* q : g.sys) wsum += (double)q->h->n * (q->h->k + 64);
+  std::vector<int> ncta(ns, 1);
+  int used = 0;
+  for (int i = 0; i < ns; ++i) {
+    const rr_handle* h = g.sys[i]->h;
+    const double w = (double)h->n * (h->k + 64);
+    ncta[i] = std::max(1, (int)std::floor(g.grid * w / std::max(wsum, 1.0)));
+    ncta[i] = (int)std::min<int64_t>(ncta[i], h->n);
+    used += ncta[i];
+  }
+  // hand the remaining CTAs (or take the excess) from the largest systems
+  while (used != g.grid) {
+    int best = -1;
+    for (int i = 0; i < ns; ++i) {
+      const rr_handle* h = g.sys[i]->h;
+      if (used < g.grid && ncta[i] >= h->n) continue;
+      if (used > g.grid && ncta[i] <= 1) continue;
+      if (best < 0 || h->n * (h->k + 64) > g.sys[best]->h->n * (g.sys[best]->h->k + 64)) best = i;
+    }
+    if (best < 0) break;
+    ncta[best] += used < g.grid ? 1 : -1;
+    used += used < g.grid ? 1 : -1;
+  }
+  if (used > g.grid) return RR_ERR_UNSUPPORTED;
+  g.thdr.nsys = ns;
+  g.thdr.kmax = g.kmax;
+  g.thdr.cta0[0] = 0;
+  for (int i = 0; i < ns; ++i) {
+    rr_handle* h = g.sys[i]->h;
+    const int64_t n = h->n;
+    const int64_t items = mv_tc_items(n);
+    const int sl = mv_tc_group_slots(n, item0, total, g.grid);
+    if (align256((size_t)sl * n * g.mp * 4) > (size_t)g.sys[i]->part_blocks * 256) return RR_ERR_WORKSPACE;
+    MvSys& m = g.mvtab[i];
+    m.n = n;
+    m.tiles = items / (mv_tc_pad(n) / 256);
+    m.item0 = item0;
+    m.row_off = g.sys[i]->row_off;
+    m.V = vt<float>(h, kP);
+    m.part = (float*)((unsigned char*)g.part + g.sys[i]->part_off * 256);
+    m.W = vt<float>(h, kW);
+    m.pair_cnt = h->op.pair_cnt;
+    m.pw_acc = h->fscratch;
+    m.pw_set = (int64_t)(pcg_tail_scratch_doubles(h->k, g.mp) / 2);
+    m.pw_launches = &h->bar->launches;
+    m.gate = h->cs;
+    m.mu = (float)h->mu;
+    m.nslots = sl;
+    item0 += items;
+    TailArgs<float>& a = g.ttab[i];
+    a.E = vt<float>(h, kE);
+    a.R = vt<float>(h, kR);
+    a.P = vt<float>(h, kP);
+    a.Z = vt<float>(h, kZ);
+    a.W = vt<float>(h, kW);
+    a.Q = (const float*)h->Q;
+    a.QH = (const float*)h->QH;
+    a.n = n;
+    a.k = h->k;
+    a.rpc = (int)cdiv(n, ncta[i]);
+    a.alpha_mode = 2;
+    a.acc = h->fscratch;
+    a.cs = h->cs;
+    a.bar = h->bar;
+    a.err = h->dstatus + 3;
+    g.thdr.cta0[i + 1] = g.thdr.cta0[i] + ncta[i];
+    // the system's grid barrier counts arrivals in multiples of its CTA
+    // count, which a rebuild may change: restart the count (no launch of the
+    // group is in flight here; the launch parity and accumulators are kept)
+    RR_CUDA_TRY(cudaMemsetAsync(&h->bar->arrivals, 0, sizeof(h->bar->arrivals), g.st));
+  }
+  g.mvhdr.total = total;
+  g.mvhdr.nsys = ns;
+  g.mvhdr.gate_mp = g.mp;
+  if (ns) {
+    RR_CUDA_TRY(cudaMemcpyAsync(g.d_mvtab, g.mvtab.data(), ns * sizeof(MvSys), cudaMemcpyHostToDevice, g.st));
+    RR_CUDA_TRY(cudaMemcpyAsync(g.d_ttab, g.ttab.data(), ns * sizeof(TailArgs<float>),
+                                cudaMemcpyHostToDevice, g.st));
+  }
+  RR_CUDA_TRY(cudaMemcpyAsync(g.d_mvhdr, &g.mvhdr, sizeof(MvGroupHdr), cudaMemcpyHostToDevice, g.st));
+  RR_CUDA_TRY(cudaMemcpyAsync(g.d_thdr, &g.thdr, sizeof(TailGroupHdr), cudaMemcpyHostToDevice, g.st));
+  // the host mirrors change before the next copy is issued only after the
+  // stream has caught up (the replay loop synchronises it)
+  return RR_OK;
+}
+
+rr_status group_init(GroupExec& g, int mp, int kmax, int maxsys, int64_t max_rows,
+                     size_t part_bytes, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (mp < 2 || mp > 8 || (mp & (mp - 1)) || kmax < 1 || maxsys < 1 || maxsys > kGroupMaxSys ||
+      max_rows < 256 || (max_rows % 256))
+    return RR_ERR_INVALID_ARG;
+  g.mp = mp;
+  g.kmax = kmax;
+  g.maxsys = maxsys;
+  g.max_rows = max_rows;
+  g.part_bytes = part_bytes;
+  g.st = st;
+  g.L = group_ws(mp, maxsys, max_rows, part_bytes);
+  if (!ws || ((uintptr_t)ws & 255) || ws_bytes < g.L.total) return RR_ERR_WORKSPACE;
+  g.ws = (unsigned char*)ws;
+  g.A = (float*)(g.ws + g.L.a);
+  g.B = (float*)(g.ws + g.L.b);
+  g.d_mvhdr = (MvGroupHdr*)(g.ws + g.L.mvhdr);
+  g.d_mvtab = (MvSys*)(g.ws + g.L.mvtab);
+  g.d_thdr = (TailGroupHdr*)(g.ws + g.L.thdr);
+  g.d_ttab = (TailArgs<float>*)(g.ws + g.L.ttab);
+  g.d_csg = (ColState*)(g.ws + g.L.csg);
+  g.d_err = (int*)(g.ws + g.L.err);
+  g.part = (float*)(g.ws + g.L.part);
+  if (!pcg_tail_group_fits(kmax, mp)) return RR_ERR_UNSUPPORTED;
+  // function attributes are set here, outside the stream capture of the rounds
+  if (!kernel_mv_tc_group_prepare(mp) || !pcg_tail_group_prepare(mp)) return RR_ERR_UNSUPPORTED;
+  if (!encode_mv_tc_group(g.A, g.B, max_rows, g.amap, g.bmap)) return RR_ERR_UNSUPPORTED;
+  g.rows.reset(max_rows / 256);
+  g.parts.reset((int64_t)(part_bytes / 256));
+  RR_CUDA_TRY(cudaMallocHost(&g.h_csg, (size_t)maxsys * 8 * sizeof(ColState) + 64));
+  g.grid = (int)std::min<int64_t>(tc_persistent_ctas(INT64_MAX / 4), kGroupMaxSys);
+  RR_CUDA_TRY(cudaMemsetAsync(g.d_err, 0, sizeof(int) * 4, st));
+  // padding rows of the stacked arrays are never read for a live point, but
+  // start them at zero
+  RR_CUDA_TRY(cudaMemsetAsync(g.A, 0, (size_t)max_rows * kAugFloats * 4, st));
+  RR_CUDA_TRY(cudaMemsetAsync(g.B, 0, (size_t)max_rows * kAugFloats * 4, st));
+  return group_rebuild(g);
+}
+
+void group_destroy(GroupExec& g) {
+  if (g.st) cudaStreamSynchronize(g.st);
+  for (auto& p : g.graphs) cudaGraphExecDestroy(p.second);
+  g.graphs.clear();
+  if (g.h_csg) cudaFreeHost(g.h_csg);
+  g.h_csg = nullptr;
+}
+
+// the restart decision of solve_impl for one system (rn2 known); returns
+// true when an inner solve starts
+bool group_decide(GroupSys* q, const double* rn2) {
+  rr_handle* h = q->h;
+  RestartParams rp;
+  memset(&rp, 0, sizeof(rp));
+  bool any = false;
+  for (int c = 0; c < h->mp; ++c) {
+    q->active[c] = false;
+    if (c >= q->m) continue;
+    const double bn = std::sqrt(q->bn2[c]);
+    q->rel[c] = bn > 0.0 ? std::sqrt(rn2[c]) / bn : 0.0;
+    if (q->done[c]) continue;
+    if (!std::isfinite(q->rel[c])) { q->done[c] = true; q->stat[c] = RR_ERR_BREAKDOWN; continue; }
+    if (q->rel[c] <= q->rtol) { q->done[c] = true; q->stat[c] = RR_OK; continue; }
+    if (q->used[c] >= q->maxit || q->restart == kMaxRestarts) {
+      q->done[c] = true;
+      q->stat[c] = RR_ERR_MAXIT;
+      continue;
+    }
+    const double stop = std::max(h->o.restart_eta * q->rel[c] * bn, 0.5 * q->rtol * bn);
+    rp.stop2[c] = stop * stop;
+    rp.budget[c] = q->maxit - q->used[c];
+    rp.active[c] = 1;
+    q->active[c] = true;
+    any = true;
+  }
+  if (!any) return false;
+  cudaStream_t st = h->st;
+  restart_init(h->cs, h->mp, rp, st);
+  float* Rv = vt<float>(h, kR);
+  axpby<double, double, float>(h->v64[kR64], coefs_all(1.0), nullptr, coefs_all(0.0), Rv, h->n,
+                               h->mp, st);
+  cudaMemsetAsync(vt<float>(h, kE), 0, (size_t)h->n * h->mp * sizeof(float), st);
+  precond_C<float>(h, Rv, vt<float>(h, kZ), kModeRhoInit);
+  p_update<float>(vt<float>(h, kP), vt<float>(h, kZ), h->n, h->mp, h->cs, true, st);
+  q->iters_seen = 0;
+  return true;
+}
+
+// the restart step after an inner solve (or the first one): residual,
+// decision, inner init; false when the system is done
+rr_status group_restart(GroupSys* q, bool* running) {
+  rr_handle* h = q->h;
+  double rn2[8] = {0};
+  if (q->restart == 0) {
+    RR_CUDA_TRY(cudaMemcpyAsync(h->v64[kR64], h->v64[kB64], (size_t)h->n * h->mp * 8,
+                                cudaMemcpyDeviceToDevice, h->st));
+    for (int c = 0; c < h->mp; ++c) rn2[c] = q->bn2[c];
+  } else {
+    RR_TRY(residual<float>(h));
+    RR_TRY(read_doubles(h, h->norms, h->mp, rn2));
+    for (int c = 0; c < q->m; ++c)
+      if (!q->done[c]) q->mv[c] += 1;
+  }
+  *running = group_decide(q, rn2);
+  return cudaGetLastError() == cudaSuccess ? RR_OK : RR_ERR_CUDA;
+}
+
+// bookkeeping after an inner solve (its column states in cs), x += e
+void group_inner_done(GroupSys* q, const ColState* cs) {
+  rr_handle* h = q->h;
+  for (int c = 0; c < q->m; ++c) {
+    if (q->done[c] || !q->active[c]) continue;
+    const ColState& s = cs[c];
+    q->used[c] += s.iters;
+    q->mv[c] += s.iters;
+    q->outer[c] += 1;
+    if (s.status == RR_ERR_BREAKDOWN && s.iters == 0) {
+      q->done[c] = true;
+      q->stat[c] = RR_ERR_BREAKDOWN;
+    }
+  }
+  axpby<double, float, double>(h->v64[kX64], coefs_all(1.0), vt<float>(h, kE), coefs_all(1.0),
+                               h->v64[kX64], h->n, h->mp, h->st);
+  q->restart += 1;
+}
+
+rr_status group_finish(GroupExec& g, GroupSys* q, int group_err) {
+  rr_handle* h = q->h;
+  rr_status s = sync_status(h);
+  int err[2] = {0, 0};
+  if (s == RR_OK) {
+    RR_CUDA_TRY(cudaMemcpyAsync(h->norms_host, h->dstatus + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    s = sync_status(h);
+    memcpy(err, h->norms_host, sizeof(err));
+  }
+  rr_status worst = RR_OK;
+  for (int c = 0; c < q->m; ++c) {
+    if (q->stat[c] != RR_OK && worst == RR_OK) worst = q->stat[c];
+    if (q->info) {
+      q->info[c].inner_iters = q->used[c];
+      q->info[c].outer_iters = q->outer[c];
+      q->info[c].matvecs = q->mv[c];
+      q->info[c].status = q->stat[c];
+      q->info[c].rel_residual = q->rel[c];
+      q->info[c].tau = h->tau;
+      q->info[c].normE = h->normE;
+      q->info[c].lam_max = h->lam_max;
+    }
+  }
+  if (s == RR_OK && (err[0] || err[1] || group_err)) s = RR_ERR_TIMEOUT;
+  if (s == RR_OK && (worst == RR_OK || worst == RR_ERR_MAXIT || worst == RR_ERR_BREAKDOWN)) {
+    scatter_cols(h->v64[kX64], h->n, h->mp, q->m, q->x, q->ldx, h->st);
+    s = sync_status(h);
+    if (s == RR_OK) s = worst;
+  }
+  h->st = q->st_saved;
+  if (q->row_off >= 0) g.rows.release((int64_t)q->row_slot);
+  if (q->part_off >= 0) g.parts.release(q->part_off);
+  q->row_off = -1;
+  q->part_off = -1;
+  q->finished = true;
+  q->status = s;
+  return s;
+}
+
+rr_status group_join_start(GroupExec& g, GroupSys* q);
+
+// a built system joins the rounds: its augmented points into the stacked
+// arrays, the solve's start (b, x = 0, |b|), the first restart
+rr_status group_join(GroupExec& g, GroupSys* q) {
+  rr_handle* h = q->h;
+  if (!group_qualifies(h) || h->mp != g.mp || h->k > g.kmax) return RR_ERR_UNSUPPORTED;
+  if ((int)g.sys.size() >= g.maxsys) return RR_ERR_WORKSPACE;
+  int64_t off = 0;
+  const int64_t npad = mv_tc_pad(h->n);
+  if (!g.rows.alloc(npad / 256, &off)) return RR_ERR_WORKSPACE;
+  q->row_slot = (size_t)off;
+  q->row_off = off * 256;
+  q->part_blocks = (int64_t)(group_part_bound(h->n, g.mp, g.grid) / 256);
+  if (!g.parts.alloc(q->part_blocks, &q->part_off)) {
+    g.rows.release(off);
+    q->row_off = -1;
+    return RR_ERR_WORKSPACE;
+  }
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) {
+    cudaGetLastError();
+    g.rows.release(off);
+    g.parts.release(q->part_off);
+    q->row_off = q->part_off = -1;
+    return RR_ERR_CUDA;
+  }
+  q->st_saved = h->st;
+  h->st = g.st;
+  cudaStream_t st = g.st;
+  rr_status js = group_join_start(g, q);
+  if (js != RR_OK) {
+    group_finish(g, q, 0);
+    q->status = js;
+    return js;
+  }
+  bool running = false;
+  js = group_restart(q, &running);
+  if (js != RR_OK || !running) {
+    const rr_status f = group_finish(g, q, 0);
+    return js != RR_OK ? js : f;
+  }
+  g.sys.push_back(q);
+  return RR_OK;
+}
+
+// the solve's start on the group stream: stacked points, b, x = 0, |b|
+rr_status group_join_start(GroupExec& g, GroupSys* q) {
+  rr_handle* h = q->h;
+  cudaStream_t st = g.st;
+  const int64_t npad = mv_tc_pad(h->n);
+  RR_CUDA_TRY(cudaMemcpyAsync(g.A + q->row_off * kAugFloats, h->op.aug_a, (size_t)npad * kAugFloats * 4,
+                              cudaMemcpyDeviceToDevice, st));
+  RR_CUDA_TRY(cudaMemcpyAsync(g.B + q->row_off * kAugFloats, h->op.aug_b, (size_t)npad * kAugFloats * 4,
+                              cudaMemcpyDeviceToDevice, st));
+  const int64_t n = h->n;
+  const int mp = h->mp;
+  gather_cols(q->b, q->ldb, q->m, n, mp, h->v64[kB64], st);
+  RR_CUDA_TRY(cudaMemsetAsync(h->v64[kX64], 0, (size_t)n * mp * 8, st));
+  RR_CUDA_TRY(cudaMemsetAsync(h->op.pair_cnt, 0, h->L.size[R_PCNT], st));
+  RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
+  dot_cols<double>(h->v64[kB64], h->v64[kB64], n, mp, kModeNone, h->rpart, h->cnt, nullptr, false,
+                   h->norms, st);
+  RR_TRY(read_doubles(h, h->norms, mp, q->bn2));
+  for (int c = 0; c < 8; ++c) q->done[c] = c >= q->m;
+  Coefs8 keep = coefs_all(1.0);
+  bool any_zero = false;
+  for (int c = 0; c < q->m; ++c)
+    if (q->bn2[c] == 0.0) {
+      keep.v[c] = 0.0;
+      q->done[c] = true;
+      any_zero = true;
+    }
+  if (any_zero) axpby<double, double, double>(h->v64[kX64], keep, nullptr, coefs_all(0.0), h->v64[kX64], n, mp, st);
+  return cudaGetLastError() == cudaSuccess ? RR_OK : RR_ERR_CUDA;
+}
+
+rr_status group_graph(GroupExec& g, int R, cudaGraphExec_t* out) {
+  for (auto& p : g.graphs)
+    if (p.first == R) {
+      *out = p.second;
+      return RR_OK;
+    }
+  cudaGraph_t gr = nullptr;
+  RR_CUDA_TRY(cudaStreamBeginCapture(g.st, cudaStreamCaptureModeThreadLocal));
+  bool ok = true;
+  for (int r = 0; r < R && ok; ++r) {
+    ok = kernel_mv_tc_group(g.amap, g.bmap, g.d_mvhdr, g.d_mvtab, g.mp, g.grid, g.d_err, g.st);
+    ok = ok && pcg_tail_group<float>(g.d_thdr, g.d_ttab, g.kmax, g.mp, g.grid, g.st) == cudaSuccess;
+  }
+  cudaError_t e = cudaStreamEndCapture(g.st, &gr);
+  if (!ok || e != cudaSuccess || !gr) {
+    if (gr) cudaGraphDestroy(gr);
+    cudaGetLastError();
+    return RR_ERR_CUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return RR_ERR_CUDA;
+  g.graphs.push_back({R, ex});
+  *out = ex;
+  return RR_OK;
+}
+
+int group_pick_R(GroupExec& g) {
+  if (g.R > 0) return g.R;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_R.find(g.tune_key);
+    if (it != g_tune_R.end()) return g.R = it->second;
+  }
+  // untuned key: two replays of every candidate, then the fastest per unit
+  // of progress (inner iterations x n^2 of the systems that advanced)
+  if ((int)g.trials.size() >= 8) {
+    double best_t = 1e300;
+    int best = 8;
+    for (int R : kTuneR) {
+      double sum = 0.0;
+      int cnt = 0;
+      for (auto& t : g.trials)
+        if (t.first == R && t.second > 0.0) {
+          sum += t.second;
+          ++cnt;
+        }
+      if (cnt && sum / cnt < best_t) {
+        best_t = sum / cnt;
+        best = R;
+      }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_R[g.tune_key] = best;
+    return g.R = best;
+  }
+  return kTuneR[g.trials.size() % 4];
+}
+
+// one replay of R rounds, then the restarts of the systems whose inner
+// solves ended; returns the systems finished in this step
+rr_status group_step(GroupExec& g, std::vector<GroupSys*>* finished) {
+  if (g.sys.empty()) return RR_OK;
+  const int R = group_pick_R(g);
+  cudaGraphExec_t ex = nullptr;
+  RR_TRY(group_graph(g, R, &ex));
+  const auto t0 = std::chrono::steady_clock::now();
+  RR_CUDA_TRY(cudaGraphLaunch(ex, g.st));
+  const int ns = (int)g.sys.size();
+  k_group_gather_cs<<<ns, 32, 0, g.st>>>(g.d_mvtab, g.d_mvhdr, g.mp, g.d_csg);
+  RR_CUDA_TRY(cudaMemcpyAsync(g.h_csg, g.d_csg, (size_t)ns * 8 * sizeof(ColState), cudaMemcpyDeviceToHost, g.st));
+  // the grouped product's error flag, in the pinned block after the states
+  int* herr = (int*)(g.h_csg + (size_t)g.maxsys * 8);
+  RR_CUDA_TRY(cudaMemcpyAsync(herr, g.d_err, sizeof(int), cudaMemcpyDeviceToHost, g.st));
+  RR_CUDA_TRY(cudaStreamSynchronize(g.st));
+  const int gerr = *herr;
+  const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  double progress = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    GroupSys* q = g.sys[i];
+    int it = 0;
+    for (int c = 0; c < q->m; ++c) it = std::max(it, g.h_csg[i * 8 + c].iters);
+    progress += (double)std::max(0, it - q->iters_seen) * (double)q->h->n * q->h->n;
+    q->iters_seen = it;
+  }
+  if (g.R == 0 && progress > 0.0) g.trials.push_back({R, dt / progress});
+  bool changed = false;
+  std::vector<GroupSys*> keep;
+  for (int i = 0; i < ns; ++i) {
+    GroupSys* q = g.sys[i];
+    bool act = false;
+    for (int c = 0; c < q->m; ++c) act |= g.h_csg[i * 8 + c].active != 0;
+    if (act && !gerr) {
+      keep.push_back(q);
+      continue;
+    }
+    changed = true;
+    bool running = false;
+    if (!gerr) {
+      group_inner_done(q, g.h_csg + i * 8);
+      const rr_status s = group_restart(q, &running);
+      if (s != RR_OK) running = false;
+    }
+    if (running) {
+      keep.push_back(q);
+    } else {
+      group_finish(g, q, gerr);
+      finished->push_back(q);
+    }
+  }
+  if (changed) {
+    g.sys = keep;
+    RR_TRY(group_rebuild(g));
+  }
+  return RR_OK;
+}
+
 }  // namespace
+
+// ---------------------------------------------- internal interface (rr_group.cuh)
+namespace rr {
+
+struct Group {
+  GroupExec g;
+  std::vector<GroupSys*> owned;
+};
+
+bool group_accepts(const rr_handle* h, int mp, int kmax) {
+  return group_qualifies(h) && h->mp == mp && h->k <= kmax;
+}
+
+size_t group_bytes(int mp, int maxsys, int64_t max_rows, size_t part_bytes) {
+  return group_ws(mp, maxsys, max_rows, part_bytes).total;
+}
+
+Group* group_create(int mp, int kmax, int maxsys, int64_t max_rows, size_t part_bytes, void* ws,
+                    size_t ws_bytes, cudaStream_t st, rr_status* s) {
+  Group* G = new (std::nothrow) Group();
+  if (!G) {
+    *s = RR_ERR_INVALID_ARG;
+    return nullptr;
+  }
+  *s = group_init(G->g, mp, kmax, maxsys, max_rows, part_bytes, ws, ws_bytes, st);
+  if (*s != RR_OK) {
+    group_destroy(G->g);
+    delete G;
+    return nullptr;
+  }
+  return G;
+}
+
+static void group_collect(Group* G, std::vector<GroupDone>* done) {
+  std::vector<GroupSys*> keep;
+  for (GroupSys* q : G->owned) {
+    if (q->finished) {
+      done->push_back({q->user, q->status});
+      delete q;
+    } else {
+      keep.push_back(q);
+    }
+  }
+  G->owned = keep;
+}
+
+rr_status group_add(Group* G, const GroupReq& r, std::vector<GroupDone>* done) {
+  if (!group_accepts(r.h, G->g.mp, G->g.kmax)) return RR_ERR_UNSUPPORTED;
+  GroupSys* q = new (std::nothrow) GroupSys();
+  if (!q) return RR_ERR_INVALID_ARG;
+  q->h = r.h;
+  q->b = r.b;
+  q->x = r.x;
+  q->ldb = r.ldb;
+  q->ldx = r.ldx;
+  q->m = r.m;
+  q->rtol = r.rtol;
+  q->maxit = r.maxit;
+  q->info = r.info;
+  q->user = r.user;
+  if (G->g.sys.empty()) {
+    G->g.tune_key = group_tune_key(G->g.mp, (double)r.h->n, (double)r.h->k);
+    G->g.R = 0;
+    G->g.trials.clear();
+  }
+  const rr_status s = group_join(G->g, q);
+  if (s != RR_OK && !q->finished) {
+    // not joined and the handle untouched: the caller decides
+    delete q;
+    return s;
+  }
+  G->owned.push_back(q);
+  if (!q->finished) {
+    const rr_status rb = group_rebuild(G->g);
+    if (rb != RR_OK) {
+      // the tables do not take it: it leaves the rounds with that status
+      // (its handle is never joined twice)
+      std::vector<GroupSys*> keep;
+      for (GroupSys* o : G->g.sys)
+        if (o != q) keep.push_back(o);
+      G->g.sys = keep;
+      group_finish(G->g, q, 0);
+      q->status = rb;
+      group_rebuild(G->g);
+    }
+  }
+  group_collect(G, done);
+  return RR_OK;
+}
+
+rr_status group_step(Group* G, std::vector<GroupDone>* done) {
+  std::vector<GroupSys*> fin;
+  const rr_status s = group_step(G->g, &fin);
+  if (s != RR_OK) {
+    for (GroupSys* q : G->g.sys) group_finish(G->g, q, 1);
+    G->g.sys.clear();
+  }
+  group_collect(G, done);
+  return s;
+}
+
+int group_size(const Group* G) { return (int)G->g.sys.size(); }
+
+void group_destroy(Group* G) {
+  if (!G) return;
+  for (GroupSys* q : G->g.sys) group_finish(G->g, q, 1);
+  G->g.sys.clear();
+  for (GroupSys* q : G->owned) delete q;
+  group_destroy(G->g);
+  delete G;
+}
+
+}  // namespace rr
 
 // ======================================================================
 // C ABI
@@ -2063,6 +2811,97 @@ rr_status randrand_scalars(const rr_handle* h, double* tau, double* normE, doubl
   if (normE) *normE = h->normE;
   if (lam_max) *lam_max = h->lam_max;
   return RR_OK;
+}
+
+// workspace of a shared-round group for these handles (see randrand.h)
+static rr_status group_sizes(rr_handle* const* hs, int32_t nsys, int* mp, int* kmax, int64_t* rows,
+                             size_t* part, size_t* bytes) {
+  if (!hs || nsys < 1 || nsys > kGroupMaxSys) return RR_ERR_INVALID_ARG;
+  const int g = (int)std::min<int64_t>(tc_persistent_ctas(INT64_MAX / 4), kGroupMaxSys);
+  *mp = 0;
+  *kmax = 0;
+  *rows = 0;
+  *part = 0;
+  for (int i = 0; i < nsys; ++i) {
+    const rr_handle* h = hs[i];
+    if (!h) return RR_ERR_INVALID_ARG;
+    if (!group_qualifies(h)) return RR_ERR_UNSUPPORTED;
+    if (*mp && h->mp != *mp) return RR_ERR_UNSUPPORTED;
+    *mp = h->mp;
+    *kmax = std::max(*kmax, h->k);
+    *rows += mv_tc_pad(h->n);
+    *part += group_part_bound(h->n, h->mp, g);
+  }
+  if (!pcg_tail_group_fits(*kmax, *mp)) return RR_ERR_UNSUPPORTED;
+  *bytes = group_ws(*mp, nsys, *rows, *part).total;
+  return RR_OK;
+}
+
+rr_status randrand_group_workspace_bytes(rr_handle* const* hs, int32_t nsys, size_t* bytes) {
+  if (!bytes) return RR_ERR_INVALID_ARG;
+  int mp, kmax;
+  int64_t rows;
+  size_t part;
+  return group_sizes(hs, nsys, &mp, &kmax, &rows, &part, bytes);
+}
+
+rr_status randrand_solve_group(rr_handle* const* hs, int32_t nsys, const rr_group_rhs* rhs,
+                               void* workspace, size_t ws_bytes, void* stream, rr_solve_info* info) {
+  if (!rhs) return RR_ERR_INVALID_ARG;
+  int mp, kmax;
+  int64_t rows;
+  size_t part, need;
+  RR_TRY(group_sizes(hs, nsys, &mp, &kmax, &rows, &part, &need));
+  for (int i = 0; i < nsys; ++i) {
+    const rr_group_rhs& r = rhs[i];
+    if (!r.b || !r.x || r.nrhs < 1 || r.nrhs > hs[i]->o.max_rhs || r.ldb < hs[i]->n ||
+        r.ldx < hs[i]->n || !(r.rtol > 0.0) || !std::isfinite(r.rtol) || r.maxit < 1)
+      return RR_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return RR_ERR_INVALID_ARG;   // a handle solves one system at a time
+  }
+  if (ws_bytes < need) return RR_ERR_WORKSPACE;
+  // the rounds are captured in a graph: not on the legacy default stream
+  if (!stream || (cudaStream_t)stream == cudaStreamLegacy) return RR_ERR_INVALID_ARG;
+  GroupExec g;
+  rr_status s = group_init(g, mp, kmax, nsys, rows, part, workspace, ws_bytes, (cudaStream_t)stream);
+  if (s != RR_OK) {
+    group_destroy(g);
+    return s;
+  }
+  double mn = 0.0, mk = 0.0;
+  for (int i = 0; i < nsys; ++i) {
+    mn += (double)hs[i]->n / nsys;
+    mk += (double)hs[i]->k / nsys;
+  }
+  g.tune_key = group_tune_key(mp, mn, mk);
+  std::vector<GroupSys> qs(nsys);
+  for (int i = 0; i < nsys; ++i) {
+    GroupSys& q = qs[i];
+    q.h = hs[i];
+    q.b = rhs[i].b;
+    q.x = rhs[i].x;
+    q.ldb = rhs[i].ldb;
+    q.ldx = rhs[i].ldx;
+    q.m = rhs[i].nrhs;
+    q.rtol = rhs[i].rtol;
+    q.maxit = rhs[i].maxit;
+    q.info = info ? info + 8 * i : nullptr;
+    const rr_status js = group_join(g, &q);
+    if (js != RR_OK && !q.finished) q.status = js, q.finished = true;
+  }
+  s = group_rebuild(g);
+  std::vector<GroupSys*> fin;
+  while (s == RR_OK && !g.sys.empty()) s = group_step(g, &fin);
+  // a failure of the replay loop ends every system still in the rounds
+  for (GroupSys* q : g.sys) group_finish(g, q, 1);
+  g.sys.clear();
+  group_destroy(g);
+  if (s != RR_OK) return s;
+  rr_status worst = RR_OK;
+  for (int i = 0; i < nsys; ++i)
+    if (qs[i].status != RR_OK && worst == RR_OK) worst = qs[i].status;
+  return worst;
 }
 
 rr_status randrand_core_jitter(const rr_handle* h, double* alpha) {

@@ -260,6 +260,40 @@ bool kernel_mv_tc(const void* amap, const void* bmap, int64_t n, int mp, const f
                   float* part, int nsplit, int* err, const ColState* gate, int gate_mp,
                   float* W, float mu, unsigned* pair_cnt, double* pw_acc, int64_t pw_set,
                   const unsigned* pw_launches, cudaStream_t st);
+
+// One system of a grouped tensor-core product (several systems' W = K V + mu V
+// in one persistent launch): its work items follow the previous system's in a
+// global (row pair, point tile) order; its augmented rows start at row row_off
+// of the group's stacked arrays (a multiple of 256).  The launch reads the
+// header and the table from device memory, so a captured launch serves any
+// group that fits its stacked arrays and grid.
+struct MvSys {
+  int64_t n, tiles, item0, row_off;
+  const float* V;
+  float* part;
+  float* W;
+  unsigned* pair_cnt;
+  double* pw_acc;                   // p^T w accumulators (two sets; see pcg_tail)
+  int64_t pw_set;
+  const unsigned* pw_launches;
+  const ColState* gate;             // the system's column states (skipped when none is active)
+  float mu;
+  int nslots;
+};
+struct MvGroupHdr {
+  int64_t total;                    // work items of all systems
+  int nsys;
+  int gate_mp;
+};
+// items of one system in a grouped product, and the most CTAs of a grid of g
+// that touch one of its row pairs when its items start at item0 of total
+int64_t mv_tc_items(int64_t n);
+int mv_tc_group_slots(int64_t n, int64_t item0, int64_t total, int64_t g);
+bool kernel_mv_tc_group(const void* amap, const void* bmap, const MvGroupHdr* hdr,
+                        const MvSys* tab, int mp, int grid, int* err, cudaStream_t st);
+bool encode_mv_tc_group(const float* Aaug, const float* Baug, int64_t rows, void* amap, void* bmap);
+// the grouped product's function attributes (call outside stream capture)
+bool kernel_mv_tc_group_prepare(int mp);
 int64_t mv_tc_pairs(int64_t n);
 // k_matvec_tc2.cu -- the same product with K v also on the tensor cores
 size_t mv_tc2_vsplit_elems(int64_t n);

@@ -105,6 +105,45 @@ template <typename T>
 cudaError_t pcg_tail(T* E, T* R, T* P, T* Z, const T* W, const T* Q, const T* QH, int64_t n,
                      int k, int mp, int G, int alpha_mode, double* scratch, ColState* cs,
                      GridBar* bar, int* err, cudaStream_t st);
+
+// arguments of the persistent step for one system
+template <typename T>
+struct TailArgs {
+  T* E;
+  T* R;
+  T* P;
+  T* Z;
+  const T* W;
+  const T* Q;
+  const T* QH;
+  int64_t n;
+  int k;
+  int rpc;            // rows per CTA of the system
+  int alpha_mode;     // 0: p^T w here; 1: the product kernel applied alpha to cs;
+                      // 2: the product kernel accumulated p^T w into this launch's set
+  double* acc;        // two sets of [pw 8 | rr 8 | rz 8 | t k x 8]
+  ColState* cs;
+  GridBar* bar;
+  int* err;
+};
+// Several systems' persistent steps in one cooperative launch of `grid`
+// CTAs: system s owns CTAs [cta0[s], cta0[s + 1]) (rpc of its TailArgs =
+// ceil(n / its CTA count)) and synchronises on its own GridBar; the header
+// and the table are read on the device when the launch runs.  kmax bounds
+// every system's k (shared memory), all systems have mp columns.
+constexpr int kTailGroupMax = 152;
+struct TailGroupHdr {
+  int nsys;
+  int kmax;
+  int cta0[kTailGroupMax + 1];
+};
+template <typename T>
+cudaError_t pcg_tail_group(const TailGroupHdr* hdr, const TailArgs<T>* tab, int kmax, int mp,
+                           int grid, cudaStream_t st);
+// the grouped float32 step's shared memory for k <= kmax fits the device
+bool pcg_tail_group_fits(int kmax, int mp);
+// its function attributes (call outside stream capture)
+bool pcg_tail_group_prepare(int mp);
 // power iterations of variant C in two persistent launches per iteration
 // (mode 0: U = (I - Pi) V | Q G Q^T V; mode 1: V = normalised (I - Pi) W | Pi W
 // with lam = the norms in cs); scratch: power_proj_scratch_doubles(k), zero

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "rr_common.cuh"
+#include "rr_group.cuh"
 
 namespace {
 
@@ -117,6 +118,27 @@ struct rr_server {
   size_t peak_bytes = 0;
   bool stop = false;
   std::vector<std::thread> workers;
+  // shared rounds (rr_server_create_rounds): built systems that qualify are
+  // handed to one executor thread, whose group advances all of their Krylov
+  // iterations together; the group's workspace sits at the front of the
+  // caller's arena, before `base`
+  struct Built {
+    uint64_t ticket;
+    rr_handle* h;
+    size_t off;
+    rr_request req;
+    double t_start, t_build;
+    rr_solve_info info[8];
+  };
+  bool rounds = false;
+  rr_rounds_opts ropts;
+  unsigned char* group_ws = nullptr;
+  size_t group_bytes = 0;
+  std::deque<Built*> built;
+  bool stop_exec = false;
+  std::condition_variable cv_exec;
+  std::thread exec;
+  int peak_running = 0;
 
   rr_server(unsigned char* b, size_t bytes, int dev) : base(b), arena(bytes), device(dev) {
     t0 = std::chrono::steady_clock::now();
@@ -141,6 +163,7 @@ struct rr_server {
         job = queue.front();
         queue.pop_front();
         ++running;
+        peak_running = std::max(peak_running, running);
         peak_bytes = std::max(peak_bytes, arena.in_use());
         rr_result& r = results[job.ticket];
         r.start_ms = now_ms(t0);
@@ -156,6 +179,24 @@ struct rr_server {
         const rr_request& q = job.req;
         s = randrand_build(&q.op, q.mu, q.k, q.sketch, q.seed, &q.opts, base + off, job.ws, st, &h);
         t_build = now_ms(t0);
+        if (s == RR_OK && rounds && rr::group_accepts(h, ropts.mp, ropts.kmax)) {
+          // the executor thread solves it in the shared rounds and completes the job
+          Built* bt = new (std::nothrow) Built();
+          if (bt) {
+            bt->ticket = job.ticket;
+            bt->h = h;
+            bt->off = off;
+            bt->req = q;
+            bt->t_start = t_start;
+            bt->t_build = t_build;
+            {
+              std::lock_guard<std::mutex> lk(m);
+              built.push_back(bt);
+            }
+            cv_exec.notify_all();
+            continue;
+          }
+        }
         if (s == RR_OK) {
           s = randrand_solve(h, q.b, q.nrhs, q.ldb, q.x, q.ldx, 0, q.rtol, q.maxit, out.info);
           randrand_free(h);   // waits for the handle's stream
@@ -177,6 +218,87 @@ struct rr_server {
       cv_done.notify_all();
     }
     if (have_stream) cudaStreamDestroy(st);
+  }
+
+  // a job of the shared rounds ends: handle freed, arena slice released
+  void complete(Built* bt, rr_status s, bool in_rounds) {
+    randrand_free(bt->h);
+    const double t_end = now_ms(t0);
+    {
+      std::lock_guard<std::mutex> lk(m);
+      arena.release(bt->off);
+      --running;
+      rr_result& r = results[bt->ticket];
+      memcpy(r.info, bt->info, sizeof(r.info));
+      r.build_ms = bt->t_build - bt->t_start;
+      r.solve_ms = t_end - bt->t_build;
+      r.end_ms = t_end;
+      r.rounds = in_rounds ? 1 : 0;
+      r.status = s;
+    }
+    delete bt;
+    cv_work.notify_all();
+    cv_done.notify_all();
+  }
+
+  void exec_main() {
+    cudaSetDevice(device);
+    cudaStream_t gst = nullptr;
+    rr_status gs = cudaStreamCreateWithFlags(&gst, cudaStreamNonBlocking) == cudaSuccess ? RR_OK : RR_ERR_CUDA;
+    rr::Group* g = nullptr;
+    if (gs == RR_OK)
+      g = rr::group_create(ropts.mp, ropts.kmax, ropts.max_systems, ropts.max_rows,
+                           rounds_part_bytes(ropts), group_ws, group_bytes, gst, &gs);
+    std::vector<Built*> pending;
+    std::vector<rr::GroupDone> done;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(m);
+        cv_exec.wait(lk, [&] {
+          return stop_exec || !built.empty() || !pending.empty() || (g && rr::group_size(g) > 0);
+        });
+        if (stop_exec && built.empty() && pending.empty() && !(g && rr::group_size(g) > 0)) break;
+        while (!built.empty()) {
+          pending.push_back(built.front());
+          built.pop_front();
+        }
+      }
+      done.clear();
+      std::vector<Built*> wait;
+      for (Built* bt : pending) {
+        rr::GroupReq r;
+        r.h = bt->h;
+        r.b = bt->req.b;
+        r.x = bt->req.x;
+        r.ldb = bt->req.ldb;
+        r.ldx = bt->req.ldx;
+        r.m = bt->req.nrhs;
+        r.rtol = bt->req.rtol;
+        r.maxit = bt->req.maxit;
+        r.info = bt->info;
+        r.user = bt;
+        rr_status s = g ? rr::group_add(g, r, &done) : gs;
+        if (s == RR_ERR_WORKSPACE && g && rr::group_size(g) > 0) {
+          wait.push_back(bt);        // joins once systems have left
+        } else if (s != RR_OK) {
+          // the group cannot take it (too large for its capacity, or no
+          // group): solved on its own
+          s = randrand_solve(bt->h, bt->req.b, bt->req.nrhs, bt->req.ldb, bt->req.x, bt->req.ldx, 0,
+                             bt->req.rtol, bt->req.maxit, bt->info);
+          complete(bt, s, false);
+        }
+      }
+      pending = wait;
+      if (g && rr::group_size(g) > 0) rr::group_step(g, &done);
+      for (const rr::GroupDone& d : done) complete((Built*)d.user, d.status, true);
+    }
+    rr::group_destroy(g);
+    if (gst) cudaStreamDestroy(gst);
+  }
+
+  static size_t rounds_part_bytes(const rr_rounds_opts& o) {
+    // 16 partial-sum slots per stacked row and column (see group_part_bound)
+    return (size_t)o.max_rows * o.mp * 4 * 16;
   }
 };
 
@@ -220,7 +342,9 @@ rr_status rr_arena_stats(const rr_arena* a, size_t* in_use, size_t* largest_free
 
 void rr_arena_destroy(rr_arena* a) { delete a; }
 
-rr_status rr_server_create(void* arena, size_t arena_bytes, int32_t workers, rr_server** out) {
+static rr_status server_create(void* arena, size_t arena_bytes, int32_t workers,
+                               const rr_rounds_opts* rounds, unsigned char* group_ws,
+                               size_t group_bytes, rr_server** out) {
   if (!out) return RR_ERR_INVALID_ARG;
   *out = nullptr;
   if (!arena || ((uintptr_t)arena & (kArenaAlign - 1)) || arena_bytes < kArenaAlign) return RR_ERR_INVALID_ARG;
@@ -229,7 +353,16 @@ rr_status rr_server_create(void* arena, size_t arena_bytes, int32_t workers, rr_
   RR_CUDA_TRY(cudaGetDevice(&dev));
   rr_server* s = new (std::nothrow) rr_server((unsigned char*)arena, arena_bytes, dev);
   if (!s) return RR_ERR_INVALID_ARG;
+  // the rounds settings are fixed before any thread starts
+  if (rounds) {
+    s->rounds = true;
+    s->ropts = *rounds;
+    s->ropts.max_rows = (rounds->max_rows + 255) / 256 * 256;
+    s->group_ws = group_ws;
+    s->group_bytes = group_bytes;
+  }
   try {
+    if (rounds) s->exec = std::thread(&rr_server::exec_main, s);
     for (int i = 0; i < workers; ++i) s->workers.emplace_back(&rr_server::worker_main, s);
   } catch (...) {
     rr_server_destroy(s);
@@ -237,6 +370,36 @@ rr_status rr_server_create(void* arena, size_t arena_bytes, int32_t workers, rr_
   }
   *out = s;
   return RR_OK;
+}
+
+rr_status rr_server_create(void* arena, size_t arena_bytes, int32_t workers, rr_server** out) {
+  return server_create(arena, arena_bytes, workers, nullptr, nullptr, 0, out);
+}
+
+rr_status rr_rounds_workspace_bytes(const rr_rounds_opts* o, size_t* bytes) {
+  if (!o || !bytes) return RR_ERR_INVALID_ARG;
+  if (o->mp < 2 || o->mp > 8 || (o->mp & (o->mp - 1)) || o->kmax < 1 || o->max_systems < 1 ||
+      o->max_systems > 152 || o->max_rows < 256)
+    return RR_ERR_INVALID_ARG;
+  const int64_t rows = (o->max_rows + 255) / 256 * 256;
+  rr_rounds_opts p = *o;
+  p.max_rows = rows;
+  *bytes = round_up(rr::group_bytes(o->mp, o->max_systems, rows, rr_server::rounds_part_bytes(p)),
+                    kArenaAlign);
+  return RR_OK;
+}
+
+rr_status rr_server_create_rounds(void* arena, size_t arena_bytes, int32_t workers,
+                                  const rr_rounds_opts* rounds, rr_server** out) {
+  if (!rounds) return rr_server_create(arena, arena_bytes, workers, out);
+  if (!out) return RR_ERR_INVALID_ARG;
+  *out = nullptr;
+  size_t gb = 0;
+  RR_TRY(rr_rounds_workspace_bytes(rounds, &gb));
+  if (!arena || ((uintptr_t)arena & (kArenaAlign - 1)) || arena_bytes < gb + kArenaAlign)
+    return RR_ERR_INVALID_ARG;
+  return server_create((unsigned char*)arena + gb, arena_bytes - gb, workers, rounds,
+                       (unsigned char*)arena, gb, out);
 }
 
 rr_status rr_server_submit(rr_server* s, const rr_request* req, uint64_t* ticket) {
@@ -292,6 +455,13 @@ rr_status rr_server_stats(rr_server* s, int32_t* queued, int32_t* running, size_
   return RR_OK;
 }
 
+rr_status rr_server_peak_running(rr_server* s, int32_t* peak) {
+  if (!s || !peak) return RR_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->m);
+  *peak = s->peak_running;
+  return RR_OK;
+}
+
 void rr_server_destroy(rr_server* s) {
   if (!s) return;
   rr_server_drain(s);
@@ -302,23 +472,37 @@ void rr_server_destroy(rr_server* s) {
   s->cv_work.notify_all();
   for (auto& t : s->workers)
     if (t.joinable()) t.join();
+  {
+    std::lock_guard<std::mutex> lk(s->m);
+    s->stop_exec = true;
+  }
+  s->cv_exec.notify_all();
+  if (s->exec.joinable()) s->exec.join();
   delete s;
 }
 
 rr_status randrand_solve_batch(const rr_request* reqs, int32_t nsys, void* arena,
                                size_t arena_bytes, int32_t workers, rr_result* results) {
+  return randrand_solve_batch_rounds(reqs, nsys, arena, arena_bytes, workers, nullptr, results);
+}
+
+rr_status randrand_solve_batch_rounds(const rr_request* reqs, int32_t nsys, void* arena,
+                                      size_t arena_bytes, int32_t workers,
+                                      const rr_rounds_opts* rounds, rr_result* results) {
   if (!reqs || !results || nsys < 1) return RR_ERR_INVALID_ARG;
+  size_t gb = 0;
+  if (rounds) RR_TRY(rr_rounds_workspace_bytes(rounds, &gb));
   std::vector<size_t> ws(nsys);
   for (int i = 0; i < nsys; ++i) {
     RR_TRY(check_request(&reqs[i]));
     RR_TRY(randrand_workspace_bytes(&reqs[i].op, reqs[i].k, &reqs[i].opts, &ws[i]));
-    if (round_up(ws[i], kArenaAlign) > arena_bytes) return RR_ERR_WORKSPACE;
+    if (round_up(ws[i], kArenaAlign) + gb > arena_bytes) return RR_ERR_WORKSPACE;
   }
   std::vector<int> order(nsys);
   for (int i = 0; i < nsys; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ws[a] > ws[b]; });
   rr_server* s = nullptr;
-  RR_TRY(rr_server_create(arena, arena_bytes, std::min(workers, nsys), &s));
+  RR_TRY(rr_server_create_rounds(arena, arena_bytes, std::min(workers, nsys), rounds, &s));
   std::vector<uint64_t> tickets(nsys, 0);
   rr_status st = RR_OK;
   for (int i : order) {

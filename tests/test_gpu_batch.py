@@ -147,7 +147,12 @@ def test_server_alone_vs_mix_and_admission(cuda_lib):
     srv = rr.Server(budget_bytes=sum(w + 256 for w in ws), workers=3)
     tickets = [srv.submit(q) for q in reqs]
     res = [srv.poll(t, wait=True) for t in tickets]
+    peak = srv.peak_running()
     srv.close()
+    # at least two requests were resident (admitted, not completed) at once
+    assert peak >= 2
+    spans = sorted((r["start_ms"], r["end_ms"]) for r in res)
+    assert any(s1 < e0 for (s0, e0), (s1, e1) in zip(spans, spans[1:]))
     for s, q, r in zip(systems, reqs, res):
         assert r["status"] == rr.RR_OK
         xa, sa, ia = alone(rr, s, rtol)
@@ -179,3 +184,56 @@ def test_server_rejects_request_larger_than_budget(cuda_lib):
         srv.submit(q)
     assert e.value.status == rr.RR_ERR_WORKSPACE
     srv.close()
+
+
+def _rounds_check(rr, systems, reqs, res, rtol):
+    for s, q, r in zip(systems, reqs, res):
+        assert r["status"] == rr.RR_OK
+        assert r["rounds"] == 1                     # iterated in the shared rounds
+        x = q.x.cpu().numpy()
+        assert np.all(O.true_rel_residual(s["oracle"], s["mu"], x, s["B"]) <= rtol)
+        xa, sa, ia = alone(rr, s, rtol)
+        assert sa == rr.RR_OK
+        # the grouped product and step sum in another order (float32
+        # rounding): iteration counts within a few steps, solutions within
+        # the forward error both solves have at this rtol
+        for a, b in zip([i["inner_iters"] for i in r["info"]], [i["inner_iters"] for i in ia]):
+            assert abs(a - b) <= max(3, 0.05 * b)
+        assert rel(x, xa) <= 1e-5
+
+
+def test_batch_in_shared_rounds_equals_systems_solved_alone(cuda_lib):
+    rr = cuda_lib
+    sizes = [600, 2000, 900, 1500, 1200, 777, 2600, 1000]
+    systems = [kernel_system(rr, 40 + i, n) for i, n in enumerate(sizes)]
+    rtol = 1e-6
+    reqs = [rr.Request(s["op"], s["mu"], s["k"], dev(s["B"]), rtol, seed=s["seed"]) for s in systems]
+    st, res = rr.solve_batch(reqs, workers=4, rounds=rr.batch_rounds_opts(reqs))
+    assert st == rr.RR_OK, res
+    _rounds_check(rr, systems, reqs, res, rtol)
+
+
+def test_server_shared_rounds_continuous_batching(cuda_lib):
+    """Requests that arrive while others iterate join the running rounds:
+    at least two are resident in the rounds at once, and each result is the
+    one the system has alone (within the stated tolerance)."""
+    import time
+    rr = cuda_lib
+    rtol = 1e-6
+    sizes = [1800, 700, 1300, 2200, 900, 1600]
+    systems = [kernel_system(rr, 60 + i, n) for i, n in enumerate(sizes)]
+    reqs = [rr.Request(s["op"], s["mu"], s["k"], dev(s["B"]), rtol, seed=s["seed"]) for s in systems]
+    ws = sum(q.workspace_bytes() + 256 for q in reqs)
+    srv = rr.Server(budget_bytes=ws, workers=3, rounds=rr.batch_rounds_opts(reqs))
+    tickets = []
+    for i, q in enumerate(reqs):
+        tickets.append(srv.submit(q))
+        if i == 2:
+            time.sleep(0.05)                        # later arrivals join running rounds
+    res = [srv.poll(t, wait=True) for t in tickets]
+    peak = srv.peak_running()
+    srv.close()
+    assert peak >= 2
+    spans = sorted((r["start_ms"], r["end_ms"]) for r in res)
+    assert any(s1 < e0 for (s0, e0), (s1, e1) in zip(spans, spans[1:]))
+    _rounds_check(rr, systems, reqs, res, rtol)
