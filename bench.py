@@ -724,12 +724,14 @@ def run_batched(args):
     # count: the best of a few on untimed passes, or as given
     cands = [(w, impl) for w in ([args.workers] if args.workers > 0 else [4, 8, 16])
              for impl in ("rounds", 0, 1)]
-    tune = {}
+    tune, rstats = {}, {}
     for w, impl in cands:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if impl == "rounds":
-            st, _ = rr.solve_batch(sets[0], workers=w, arena_bytes=arena, rounds=ropts)
+            rs = {}
+            st, _ = rr.solve_batch(sets[0], workers=w, arena_bytes=arena, rounds=ropts, stats=rs)
+            rstats[w] = rs
         else:
             st, _ = rr.solve_batch(sets[impl], workers=w, arena_bytes=arena)
         torch.cuda.synchronize()
@@ -778,6 +780,7 @@ def run_batched(args):
                                     "seconds": seq_s},
                  autotune_s={f"workers={k[0]},schedule={k[1]}": v for k, v in tune.items()},
                  in_rounds=sum(r.get("rounds", 0) for r in res),
+                 rounds_split_s={f"workers={w}": v for w, v in rstats.items()},
                  solve={"inner_iters_max": max(iters), "inner_iters_median": float(np.median(iters))},
                  roofline=None, clocks=clocks)
     if rank == 0:

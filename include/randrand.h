@@ -555,6 +555,17 @@ typedef struct {
   int64_t max_rows;
 } rr_rounds_opts;
 rr_status rr_rounds_workspace_bytes(const rr_rounds_opts* o, size_t* bytes);
+/* Host wall-clock split of the rounds' executor: replays of the round graph
+ * (launch to the read of every column state), restarts (bookkeeping and
+ * polling between replays) and joins; replays and rounds run; the rounds per
+ * replay the tuner settled on (0 while it is still trying candidates). */
+typedef struct {
+  double replay_s, restart_s, join_s;
+  int64_t replays, rounds;
+  int32_t rounds_per_replay;
+  int32_t pad_;
+} rr_rounds_stats;
+rr_status rr_server_rounds_stats(rr_server* s, rr_rounds_stats* out);
 rr_status rr_server_create_rounds(void* arena, size_t arena_bytes, int32_t workers,
                                   const rr_rounds_opts* rounds, rr_server** out);
 /* Most requests resident at once (admitted and not completed) so far. */
@@ -571,7 +582,8 @@ rr_status randrand_solve_batch(const rr_request* reqs, int32_t nsys, void* arena
 /* The same with shared rounds (rounds != NULL; see rr_rounds_opts). */
 rr_status randrand_solve_batch_rounds(const rr_request* reqs, int32_t nsys, void* arena,
                                       size_t arena_bytes, int32_t workers,
-                                      const rr_rounds_opts* rounds, rr_result* results);
+                                      const rr_rounds_opts* rounds, rr_result* results,
+                                      rr_rounds_stats* stats /* may be NULL */);
 
 #ifdef __cplusplus
 }

@@ -106,6 +106,15 @@ class rr_rounds_opts(ctypes.Structure):
                 ("pad_", ctypes.c_int32), ("max_rows", ctypes.c_int64)]
 
 
+class rr_rounds_stats(ctypes.Structure):
+    _fields_ = [("replay_s", ctypes.c_double), ("restart_s", ctypes.c_double),
+                ("join_s", ctypes.c_double), ("replays", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("rounds_per_replay", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad_"}
+
+
 class rr_result(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("ws_bytes", ctypes.c_size_t),
@@ -184,7 +193,8 @@ _SIGNATURES = [
     ("rr_server_peak_running", ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
     ("randrand_solve_batch_rounds", ctypes.c_int32,
      [ctypes.POINTER(rr_request), ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
-      ctypes.POINTER(rr_rounds_opts), ctypes.POINTER(rr_result)]),
+      ctypes.POINTER(rr_rounds_opts), ctypes.POINTER(rr_result), ctypes.POINTER(rr_rounds_stats)]),
+    ("rr_server_rounds_stats", ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rr_rounds_stats)]),
     ("rr_server_create", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
     ("rr_server_submit", ctypes.c_int32,
@@ -636,6 +646,11 @@ class Server:
             raise RandRandError(st, "rr_server_create")
         self._keep = {}
 
+    def rounds_stats(self) -> dict:
+        r = rr_rounds_stats()
+        _lib().rr_server_rounds_stats(self.s, ctypes.byref(r))
+        return r.as_dict()
+
     def peak_running(self) -> int:
         p = ctypes.c_int32(0)
         _lib().rr_server_peak_running(self.s, ctypes.byref(p))
@@ -715,9 +730,10 @@ def solve_group(handles: list, bs: list, rtol, maxit=20000, stream=None):
 
 
 def solve_batch(reqs: list, workers: int = 8, arena_bytes: int | None = None,
-                rounds: rr_rounds_opts | None = None):
+                rounds: rr_rounds_opts | None = None, stats: dict | None = None):
     """randrand_solve_batch (or, with ``rounds``, randrand_solve_batch_rounds)
-    over the requests; returns (status, [result dicts])."""
+    over the requests; returns (status, [result dicts]); ``stats`` (a dict)
+    receives the rounds' time split."""
     import torch
     n = len(reqs)
     arr = (rr_request * n)(*[r.c for r in reqs])
@@ -731,8 +747,12 @@ def solve_batch(reqs: list, workers: int = 8, arena_bytes: int | None = None,
         st = _lib().randrand_solve_batch(arr, n, ctypes.c_void_p(arena.data_ptr()), int(arena_bytes),
                                          int(workers), res)
     else:
+        rs = rr_rounds_stats()
         st = _lib().randrand_solve_batch_rounds(arr, n, ctypes.c_void_p(arena.data_ptr()),
-                                                int(arena_bytes), int(workers), ctypes.byref(rounds), res)
+                                                int(arena_bytes), int(workers), ctypes.byref(rounds), res,
+                                                ctypes.byref(rs))
+        if stats is not None:
+            stats.update(rs.as_dict())
     del arena
     return st, [res[i].as_dict() for i in range(n)]
 

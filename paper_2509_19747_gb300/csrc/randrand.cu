@@ -1895,6 +1895,11 @@ struct GroupSys {
   int64_t part_off = -1;         // 256-byte blocks of the group's partial-sum pool
   int64_t part_blocks = 0;
   void* user = nullptr;          // the serving loop's job
+  // restart outside the rounds, on a stream of the group's restart pool:
+  // 1 = residual in flight (ev), 2 = next inner init in flight (ev)
+  int phase = 0;
+  cudaEvent_t ev = nullptr;
+  cudaStream_t rst = nullptr;
 };
 
 // first-fit allocator of unit blocks (the stacked rows of a group)
@@ -1961,6 +1966,14 @@ struct GroupExec {
   std::vector<MvSys> mvtab;
   std::vector<TailArgs<float>> ttab;
   std::vector<GroupSys*> sys;   // systems whose inner solves run in the rounds
+  std::vector<GroupSys*> restarting;   // systems between two inner solves
+  static constexpr int kRestartStreams = 8;
+  cudaStream_t rst[kRestartStreams] = {nullptr};
+  int rst_next = 0;
+  cudaEvent_t ev_replay = nullptr;     // the last replay's end on the group stream
+  // time split of the loop (host wall clock, seconds)
+  double t_replay = 0.0, t_restart = 0.0, t_join = 0.0;
+  int64_t n_replays = 0, n_rounds = 0;
   rr_arena_lite rows;           // 256-row blocks of the stacked arrays
   rr_arena_lite parts;          // 256-byte blocks of the partial-sum pool
   int grid = 0;
@@ -2124,6 +2137,9 @@ rr_status group_init(GroupExec& g, int mp, int kmax, int maxsys, int64_t max_row
   g.rows.reset(max_rows / 256);
   g.parts.reset((int64_t)(part_bytes / 256));
   RR_CUDA_TRY(cudaMallocHost(&g.h_csg, (size_t)maxsys * 8 * sizeof(ColState) + 64));
+  for (int i = 0; i < GroupExec::kRestartStreams; ++i)
+    RR_CUDA_TRY(cudaStreamCreateWithFlags(&g.rst[i], cudaStreamNonBlocking));
+  RR_CUDA_TRY(cudaEventCreateWithFlags(&g.ev_replay, cudaEventDisableTiming));
   g.grid = (int)std::min<int64_t>(tc_persistent_ctas(INT64_MAX / 4), kGroupMaxSys);
   RR_CUDA_TRY(cudaMemsetAsync(g.d_err, 0, sizeof(int) * 4, st));
   // padding rows of the stacked arrays are never read for a live point, but
@@ -2137,6 +2153,14 @@ void group_destroy(GroupExec& g) {
   if (g.st) cudaStreamSynchronize(g.st);
   for (auto& p : g.graphs) cudaGraphExecDestroy(p.second);
   g.graphs.clear();
+  for (int i = 0; i < GroupExec::kRestartStreams; ++i)
+    if (g.rst[i]) {
+      cudaStreamSynchronize(g.rst[i]);
+      cudaStreamDestroy(g.rst[i]);
+      g.rst[i] = nullptr;
+    }
+  if (g.ev_replay) cudaEventDestroy(g.ev_replay);
+  g.ev_replay = nullptr;
   if (g.h_csg) cudaFreeHost(g.h_csg);
   g.h_csg = nullptr;
 }
@@ -2179,25 +2203,6 @@ bool group_decide(GroupSys* q, const double* rn2) {
   p_update<float>(vt<float>(h, kP), vt<float>(h, kZ), h->n, h->mp, h->cs, true, st);
   q->iters_seen = 0;
   return true;
-}
-
-// the restart step after an inner solve (or the first one): residual,
-// decision, inner init; false when the system is done
-rr_status group_restart(GroupSys* q, bool* running) {
-  rr_handle* h = q->h;
-  double rn2[8] = {0};
-  if (q->restart == 0) {
-    RR_CUDA_TRY(cudaMemcpyAsync(h->v64[kR64], h->v64[kB64], (size_t)h->n * h->mp * 8,
-                                cudaMemcpyDeviceToDevice, h->st));
-    for (int c = 0; c < h->mp; ++c) rn2[c] = q->bn2[c];
-  } else {
-    RR_TRY(residual<float>(h));
-    RR_TRY(read_doubles(h, h->norms, h->mp, rn2));
-    for (int c = 0; c < q->m; ++c)
-      if (!q->done[c]) q->mv[c] += 1;
-  }
-  *running = group_decide(q, rn2);
-  return cudaGetLastError() == cudaSuccess ? RR_OK : RR_ERR_CUDA;
 }
 
 // bookkeeping after an inner solve (its column states in cs), x += e
@@ -2249,6 +2254,8 @@ rr_status group_finish(GroupExec& g, GroupSys* q, int group_err) {
     if (s == RR_OK) s = worst;
   }
   h->st = q->st_saved;
+  if (q->ev) cudaEventDestroy(q->ev);
+  q->ev = nullptr;
   if (q->row_off >= 0) g.rows.release((int64_t)q->row_slot);
   if (q->part_off >= 0) g.parts.release(q->part_off);
   q->row_off = -1;
@@ -2265,7 +2272,7 @@ rr_status group_join_start(GroupExec& g, GroupSys* q);
 rr_status group_join(GroupExec& g, GroupSys* q) {
   rr_handle* h = q->h;
   if (!group_qualifies(h) || h->mp != g.mp || h->k > g.kmax) return RR_ERR_UNSUPPORTED;
-  if ((int)g.sys.size() >= g.maxsys) return RR_ERR_WORKSPACE;
+  if ((int)(g.sys.size() + g.restarting.size()) >= g.maxsys) return RR_ERR_WORKSPACE;
   int64_t off = 0;
   const int64_t npad = mv_tc_pad(h->n);
   if (!g.rows.alloc(npad / 256, &off)) return RR_ERR_WORKSPACE;
@@ -2285,28 +2292,31 @@ rr_status group_join(GroupExec& g, GroupSys* q) {
     return RR_ERR_CUDA;
   }
   q->st_saved = h->st;
-  h->st = g.st;
-  cudaStream_t st = g.st;
-  rr_status js = group_join_start(g, q);
+  q->rst = g.rst[g.rst_next++ % GroupExec::kRestartStreams];
+  h->st = q->rst;
+  if (cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    q->ev = nullptr;
+  }
+  // the start runs on the system's restart stream; it enters the rounds
+  // through the restart path (phase 3: |b|^2 in flight)
+  rr_status js = q->ev ? group_join_start(g, q) : RR_ERR_CUDA;
+  if (js == RR_OK && cudaEventRecord(q->ev, h->st) != cudaSuccess) js = RR_ERR_CUDA;
   if (js != RR_OK) {
+    cudaGetLastError();
     group_finish(g, q, 0);
     q->status = js;
     return js;
   }
-  bool running = false;
-  js = group_restart(q, &running);
-  if (js != RR_OK || !running) {
-    const rr_status f = group_finish(g, q, 0);
-    return js != RR_OK ? js : f;
-  }
-  g.sys.push_back(q);
+  q->phase = 3;
+  g.restarting.push_back(q);
   return RR_OK;
 }
 
 // the solve's start on the group stream: stacked points, b, x = 0, |b|
 rr_status group_join_start(GroupExec& g, GroupSys* q) {
   rr_handle* h = q->h;
-  cudaStream_t st = g.st;
+  cudaStream_t st = h->st;
   const int64_t npad = mv_tc_pad(h->n);
   RR_CUDA_TRY(cudaMemcpyAsync(g.A + q->row_off * kAugFloats, h->op.aug_a, (size_t)npad * kAugFloats * 4,
                               cudaMemcpyDeviceToDevice, st));
@@ -2320,7 +2330,18 @@ rr_status group_join_start(GroupExec& g, GroupSys* q) {
   RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
   dot_cols<double>(h->v64[kB64], h->v64[kB64], n, mp, kModeNone, h->rpart, h->cnt, nullptr, false,
                    h->norms, st);
-  RR_TRY(read_doubles(h, h->norms, mp, q->bn2));
+  RR_CUDA_TRY(cudaMemcpyAsync(h->norms_host, h->norms, (size_t)mp * sizeof(double),
+                              cudaMemcpyDeviceToHost, st));
+  return cudaGetLastError() == cudaSuccess ? RR_OK : RR_ERR_CUDA;
+}
+
+// |b|^2 has arrived (phase 3): zero right-hand sides, then the first
+// restart's decision with r = b; false when the system is already done
+bool group_join_decide(GroupSys* q) {
+  rr_handle* h = q->h;
+  const int64_t n = h->n;
+  const int mp = h->mp;
+  memcpy(q->bn2, h->norms_host, (size_t)mp * sizeof(double));
   for (int c = 0; c < 8; ++c) q->done[c] = c >= q->m;
   Coefs8 keep = coefs_all(1.0);
   bool any_zero = false;
@@ -2330,8 +2351,9 @@ rr_status group_join_start(GroupExec& g, GroupSys* q) {
       q->done[c] = true;
       any_zero = true;
     }
-  if (any_zero) axpby<double, double, double>(h->v64[kX64], keep, nullptr, coefs_all(0.0), h->v64[kX64], n, mp, st);
-  return cudaGetLastError() == cudaSuccess ? RR_OK : RR_ERR_CUDA;
+  if (any_zero) axpby<double, double, double>(h->v64[kX64], keep, nullptr, coefs_all(0.0), h->v64[kX64], n, mp, h->st);
+  cudaMemcpyAsync(h->v64[kR64], h->v64[kB64], (size_t)n * mp * 8, cudaMemcpyDeviceToDevice, h->st);
+  return group_decide(q, q->bn2);
 }
 
 rr_status group_graph(GroupExec& g, int R, cudaGraphExec_t* out) {
@@ -2394,61 +2416,154 @@ int group_pick_R(GroupExec& g) {
   return kTuneR[g.trials.size() % 4];
 }
 
-// one replay of R rounds, then the restarts of the systems whose inner
-// solves ended; returns the systems finished in this step
-rr_status group_step(GroupExec& g, std::vector<GroupSys*>* finished) {
-  if (g.sys.empty()) return RR_OK;
-  const int R = group_pick_R(g);
-  cudaGraphExec_t ex = nullptr;
-  RR_TRY(group_graph(g, R, &ex));
-  const auto t0 = std::chrono::steady_clock::now();
-  RR_CUDA_TRY(cudaGraphLaunch(ex, g.st));
-  const int ns = (int)g.sys.size();
-  k_group_gather_cs<<<ns, 32, 0, g.st>>>(g.d_mvtab, g.d_mvhdr, g.mp, g.d_csg);
-  RR_CUDA_TRY(cudaMemcpyAsync(g.h_csg, g.d_csg, (size_t)ns * 8 * sizeof(ColState), cudaMemcpyDeviceToHost, g.st));
-  // the grouped product's error flag, in the pinned block after the states
-  int* herr = (int*)(g.h_csg + (size_t)g.maxsys * 8);
-  RR_CUDA_TRY(cudaMemcpyAsync(herr, g.d_err, sizeof(int), cudaMemcpyDeviceToHost, g.st));
-  RR_CUDA_TRY(cudaStreamSynchronize(g.st));
-  const int gerr = *herr;
-  const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  double progress = 0.0;
-  for (int i = 0; i < ns; ++i) {
-    GroupSys* q = g.sys[i];
-    int it = 0;
-    for (int c = 0; c < q->m; ++c) it = std::max(it, g.h_csg[i * 8 + c].iters);
-    progress += (double)std::max(0, it - q->iters_seen) * (double)q->h->n * q->h->n;
-    q->iters_seen = it;
+// a system whose inner solve ended leaves the rounds: its restart runs on a
+// stream of the group's restart pool, after the replay that ended it
+// (ev_replay): bookkeeping and x += e, the float64-accurate residual and an
+// asynchronous read of |r|^2 (phase 1)
+void group_restart_begin(GroupExec& g, GroupSys* q, const ColState* cs) {
+  rr_handle* h = q->h;
+  h->st = q->rst;
+  cudaStreamWaitEvent(q->rst, g.ev_replay, 0);
+  group_inner_done(q, cs);
+  residual<float>(h);
+  cudaMemcpyAsync(h->norms_host, h->norms, (size_t)h->mp * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+  cudaEventRecord(q->ev, h->st);
+  q->phase = 1;
+}
+
+// advance a restarting system: 0 still waiting, 1 back in the rounds, 2 done
+int group_restart_poll(GroupExec& g, GroupSys* q) {
+  const cudaError_t e = cudaEventQuery(q->ev);
+  if (e == cudaErrorNotReady) return 0;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    group_finish(g, q, 0);
+    q->status = RR_ERR_CUDA;
+    return 2;
   }
-  if (g.R == 0 && progress > 0.0) g.trials.push_back({R, dt / progress});
+  rr_handle* h = q->h;
+  if (q->phase == 3) {
+    if (!group_join_decide(q)) {
+      group_finish(g, q, 0);
+      return 2;
+    }
+    cudaEventRecord(q->ev, h->st);       // the first inner solve's init
+    q->phase = 2;
+    return 0;
+  }
+  if (q->phase == 1) {
+    double rn2[8] = {0};
+    memcpy(rn2, h->norms_host, (size_t)h->mp * sizeof(double));
+    for (int c = 0; c < q->m; ++c)
+      if (!q->done[c]) q->mv[c] += 1;
+    if (!group_decide(q, rn2)) {
+      group_finish(g, q, 0);
+      return 2;
+    }
+    cudaEventRecord(q->ev, h->st);       // the next inner solve's init
+    q->phase = 2;
+    return 0;
+  }
+  // init done: the group stream waits for it before the system's next round
+  cudaStreamWaitEvent(g.st, q->ev, 0);
+  h->st = g.st;
+  q->phase = 0;
+  return 1;
+}
+
+// one replay of R rounds for the systems in the rounds, then the restarts
+// of those whose inner solves ended; the systems finished in this step are
+// appended to `finished`
+rr_status group_step(GroupExec& g, std::vector<GroupSys*>* finished) {
+  using clk = std::chrono::steady_clock;
   bool changed = false;
-  std::vector<GroupSys*> keep;
-  for (int i = 0; i < ns; ++i) {
-    GroupSys* q = g.sys[i];
-    bool act = false;
-    for (int c = 0; c < q->m; ++c) act |= g.h_csg[i * 8 + c].active != 0;
-    if (act && !gerr) {
-      keep.push_back(q);
-      continue;
+  if (!g.sys.empty()) {
+    const int R = group_pick_R(g);
+    cudaGraphExec_t ex = nullptr;
+    RR_TRY(group_graph(g, R, &ex));
+    const auto t0 = clk::now();
+    RR_CUDA_TRY(cudaGraphLaunch(ex, g.st));
+    const int ns = (int)g.sys.size();
+    k_group_gather_cs<<<ns, 32, 0, g.st>>>(g.d_mvtab, g.d_mvhdr, g.mp, g.d_csg);
+    RR_CUDA_TRY(cudaEventRecord(g.ev_replay, g.st));
+    RR_CUDA_TRY(cudaMemcpyAsync(g.h_csg, g.d_csg, (size_t)ns * 8 * sizeof(ColState), cudaMemcpyDeviceToHost, g.st));
+    // the grouped product's error flag, in the pinned block after the states
+    int* herr = (int*)(g.h_csg + (size_t)g.maxsys * 8);
+    RR_CUDA_TRY(cudaMemcpyAsync(herr, g.d_err, sizeof(int), cudaMemcpyDeviceToHost, g.st));
+    RR_CUDA_TRY(cudaStreamSynchronize(g.st));
+    const int gerr = *herr;
+    const double dt = std::chrono::duration<double>(clk::now() - t0).count();
+    g.t_replay += dt;
+    g.n_replays += 1;
+    g.n_rounds += R;
+    double progress = 0.0;
+    for (int i = 0; i < ns; ++i) {
+      GroupSys* q = g.sys[i];
+      int it = 0;
+      for (int c = 0; c < q->m; ++c) it = std::max(it, g.h_csg[i * 8 + c].iters);
+      progress += (double)std::max(0, it - q->iters_seen) * (double)q->h->n * q->h->n;
+      q->iters_seen = it;
     }
-    changed = true;
-    bool running = false;
-    if (!gerr) {
-      group_inner_done(q, g.h_csg + i * 8);
-      const rr_status s = group_restart(q, &running);
-      if (s != RR_OK) running = false;
+    if (g.R == 0 && progress > 0.0) g.trials.push_back({R, dt / progress});
+    const auto t1 = clk::now();
+    std::vector<GroupSys*> keep;
+    for (int i = 0; i < ns; ++i) {
+      GroupSys* q = g.sys[i];
+      bool act = false;
+      for (int c = 0; c < q->m; ++c) act |= g.h_csg[i * 8 + c].active != 0;
+      if (act && !gerr) {
+        keep.push_back(q);
+        continue;
+      }
+      changed = true;
+      if (gerr) {
+        group_finish(g, q, gerr);
+        finished->push_back(q);
+      } else {
+        group_restart_begin(g, q, g.h_csg + i * 8);
+        g.restarting.push_back(q);
+      }
     }
-    if (running) {
-      keep.push_back(q);
+    g.sys = keep;
+    g.t_restart += std::chrono::duration<double>(clk::now() - t1).count();
+  }
+  const auto t2 = clk::now();
+  std::vector<GroupSys*> still, entered;
+  for (GroupSys* q : g.restarting) {
+    const int r = group_restart_poll(g, q);
+    if (r == 0) {
+      still.push_back(q);
+    } else if (r == 1) {
+      g.sys.push_back(q);
+      entered.push_back(q);
+      changed = true;
     } else {
-      group_finish(g, q, gerr);
       finished->push_back(q);
     }
   }
+  g.restarting = still;
   if (changed) {
-    g.sys = keep;
-    RR_TRY(group_rebuild(g));
+    rr_status rb = group_rebuild(g);
+    // tables that cannot take the systems (a partial-sum region too small):
+    // the systems that entered in this step leave with that status, so that
+    // no handle is ever in the rounds twice
+    while (rb != RR_OK && !entered.empty()) {
+      GroupSys* q = entered.back();
+      entered.pop_back();
+      std::vector<GroupSys*> keep;
+      for (GroupSys* o : g.sys)
+        if (o != q) keep.push_back(o);
+      g.sys = keep;
+      group_finish(g, q, 0);
+      q->status = rb;
+      finished->push_back(q);
+      rb = group_rebuild(g);
+    }
+    RR_TRY(rb);
   }
+  // nothing to replay: wait for the oldest restart instead of polling
+  if (g.sys.empty() && !g.restarting.empty()) cudaEventSynchronize(g.restarting.front()->ev);
+  g.t_restart += std::chrono::duration<double>(clk::now() - t2).count();
   return RR_OK;
 }
 
@@ -2513,32 +2628,20 @@ rr_status group_add(Group* G, const GroupReq& r, std::vector<GroupDone>* done) {
   q->maxit = r.maxit;
   q->info = r.info;
   q->user = r.user;
-  if (G->g.sys.empty()) {
+  if (G->g.sys.empty() && G->g.restarting.empty()) {
     G->g.tune_key = group_tune_key(G->g.mp, (double)r.h->n, (double)r.h->k);
     G->g.R = 0;
     G->g.trials.clear();
   }
+  const auto tj = std::chrono::steady_clock::now();
   const rr_status s = group_join(G->g, q);
+  G->g.t_join += std::chrono::duration<double>(std::chrono::steady_clock::now() - tj).count();
   if (s != RR_OK && !q->finished) {
     // not joined and the handle untouched: the caller decides
     delete q;
     return s;
   }
   G->owned.push_back(q);
-  if (!q->finished) {
-    const rr_status rb = group_rebuild(G->g);
-    if (rb != RR_OK) {
-      // the tables do not take it: it leaves the rounds with that status
-      // (its handle is never joined twice)
-      std::vector<GroupSys*> keep;
-      for (GroupSys* o : G->g.sys)
-        if (o != q) keep.push_back(o);
-      G->g.sys = keep;
-      group_finish(G->g, q, 0);
-      q->status = rb;
-      group_rebuild(G->g);
-    }
-  }
   group_collect(G, done);
   return RR_OK;
 }
@@ -2548,18 +2651,31 @@ rr_status group_step(Group* G, std::vector<GroupDone>* done) {
   const rr_status s = group_step(G->g, &fin);
   if (s != RR_OK) {
     for (GroupSys* q : G->g.sys) group_finish(G->g, q, 1);
+    for (GroupSys* q : G->g.restarting) group_finish(G->g, q, 1);
     G->g.sys.clear();
+    G->g.restarting.clear();
   }
   group_collect(G, done);
   return s;
 }
 
-int group_size(const Group* G) { return (int)G->g.sys.size(); }
+int group_size(const Group* G) { return (int)(G->g.sys.size() + G->g.restarting.size()); }
+
+void group_stats(const Group* G, rr_rounds_stats* out) {
+  out->replay_s = G->g.t_replay;
+  out->restart_s = G->g.t_restart;
+  out->join_s = G->g.t_join;
+  out->replays = G->g.n_replays;
+  out->rounds = G->g.n_rounds;
+  out->rounds_per_replay = G->g.R;
+}
 
 void group_destroy(Group* G) {
   if (!G) return;
   for (GroupSys* q : G->g.sys) group_finish(G->g, q, 1);
+  for (GroupSys* q : G->g.restarting) group_finish(G->g, q, 1);
   G->g.sys.clear();
+  G->g.restarting.clear();
   for (GroupSys* q : G->owned) delete q;
   group_destroy(G->g);
   delete G;
@@ -2892,10 +3008,12 @@ rr_status randrand_solve_group(rr_handle* const* hs, int32_t nsys, const rr_grou
   }
   s = group_rebuild(g);
   std::vector<GroupSys*> fin;
-  while (s == RR_OK && !g.sys.empty()) s = group_step(g, &fin);
-  // a failure of the replay loop ends every system still in the rounds
+  while (s == RR_OK && (!g.sys.empty() || !g.restarting.empty())) s = group_step(g, &fin);
+  // a failure of the replay loop ends every system still in the group
   for (GroupSys* q : g.sys) group_finish(g, q, 1);
+  for (GroupSys* q : g.restarting) group_finish(g, q, 1);
   g.sys.clear();
+  g.restarting.clear();
   group_destroy(g);
   if (s != RR_OK) return s;
   rr_status worst = RR_OK;

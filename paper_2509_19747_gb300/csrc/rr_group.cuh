@@ -43,6 +43,8 @@ rr_status group_add(Group* g, const GroupReq& r, std::vector<GroupDone>* done);
 // appended to `done` (their handles are back on their own streams)
 rr_status group_step(Group* g, std::vector<GroupDone>* done);
 int group_size(const Group* g);
+// host wall-clock split of the replay loop so far (rr_rounds_stats)
+void group_stats(const Group* g, rr_rounds_stats* out);
 void group_destroy(Group* g);
 
 }  // namespace rr

@@ -139,6 +139,7 @@ struct rr_server {
   std::condition_variable cv_exec;
   std::thread exec;
   int peak_running = 0;
+  rr_rounds_stats gstats{};
 
   rr_server(unsigned char* b, size_t bytes, int dev) : base(b), arena(bytes), device(dev) {
     t0 = std::chrono::steady_clock::now();
@@ -290,6 +291,10 @@ struct rr_server {
       }
       pending = wait;
       if (g && rr::group_size(g) > 0) rr::group_step(g, &done);
+      if (g) {
+        std::lock_guard<std::mutex> lk(m);
+        rr::group_stats(g, &gstats);
+      }
       for (const rr::GroupDone& d : done) complete((Built*)d.user, d.status, true);
     }
     rr::group_destroy(g);
@@ -455,6 +460,13 @@ rr_status rr_server_stats(rr_server* s, int32_t* queued, int32_t* running, size_
   return RR_OK;
 }
 
+rr_status rr_server_rounds_stats(rr_server* s, rr_rounds_stats* out) {
+  if (!s || !out) return RR_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->m);
+  *out = s->gstats;
+  return RR_OK;
+}
+
 rr_status rr_server_peak_running(rr_server* s, int32_t* peak) {
   if (!s || !peak) return RR_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(s->m);
@@ -483,12 +495,14 @@ void rr_server_destroy(rr_server* s) {
 
 rr_status randrand_solve_batch(const rr_request* reqs, int32_t nsys, void* arena,
                                size_t arena_bytes, int32_t workers, rr_result* results) {
-  return randrand_solve_batch_rounds(reqs, nsys, arena, arena_bytes, workers, nullptr, results);
+  return randrand_solve_batch_rounds(reqs, nsys, arena, arena_bytes, workers, nullptr, results,
+                                     nullptr);
 }
 
 rr_status randrand_solve_batch_rounds(const rr_request* reqs, int32_t nsys, void* arena,
                                       size_t arena_bytes, int32_t workers,
-                                      const rr_rounds_opts* rounds, rr_result* results) {
+                                      const rr_rounds_opts* rounds, rr_result* results,
+                                      rr_rounds_stats* stats) {
   if (!reqs || !results || nsys < 1) return RR_ERR_INVALID_ARG;
   size_t gb = 0;
   if (rounds) RR_TRY(rr_rounds_workspace_bytes(rounds, &gb));
@@ -520,6 +534,7 @@ rr_status randrand_solve_batch_rounds(const rr_request* reqs, int32_t nsys, void
     rr_server_poll(s, tickets[i], 1, &results[i]);
     if (worst == RR_OK && results[i].status != RR_OK) worst = results[i].status;
   }
+  if (stats) rr_server_rounds_stats(s, stats);
   rr_server_destroy(s);
   return worst;
 }
