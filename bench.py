@@ -466,10 +466,13 @@ def roofline(name, stat, clocks):
                 "traffic": TRAFFIC["k_kernel_mv_tc"], "launches": cnt, "avg_us": avg_s * 1e6,
                 "peak_note": "derived: 152 SMs x 32 ex2 per clock x sampled max SM clock"}
     if name == "residual":
-        # double-float restart residual: ~190 float32-pipe ops per entry
-        ops = float(n) * n * 190
+        # double-float restart residual over the symmetric K: n (n + 1) / 2
+        # distinct entries, each ~142 float32-pipe ops to evaluate in
+        # double-float and 2 x 12 per right-hand side for its row and column
+        # products
+        ops = float(n) * (n + 1) / 2 * (142 + 24 * m)
         peak = 152 * 128 * f
-        return {"kernel": "k_kernel_mv_df2", "bound": "alu", "achieved": ops / avg_s / 1e9,
+        return {"kernel": "k_kernel_mv_df2s", "bound": "alu", "achieved": ops / avg_s / 1e9,
                 "peak": peak / 1e9, "unit": "G f32-op/s", "frac": ops / avg_s / peak,
                 "traffic": None, "launches": cnt, "avg_us": avg_s * 1e6}
     # sketch: 2 n^2 k flops on the tensor cores (bf16, dense)

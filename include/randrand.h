@@ -180,9 +180,16 @@ typedef struct {
                             Pi ~ Q T Q^T and Pi A_mu^-1 Pi ~ Q T G T Q^T with
                             the Neumann T = 2 I - Q^T Q of the stored basis,
                             so P = I + Q (tau T G T - T) Q^T; one k x k Gram
-                            at build, no cost per iteration.  Variants C and
-                            G with an explicit basis (else
-                            RR_ERR_UNSUPPORTED).  0 (default): plain Q Q^T */
+                            at build, no cost per iteration.  s = 2..8: the
+                            refinement recurrence of eq:accurate_proj_2 with
+                            s steps beyond the first (v_1 = Q^T u, v_{i+1} =
+                            v_i + Q^T (u - Q v_i)), whose result is the
+                            polynomial T = sum_{j <= s} (I - Q^T Q)^j applied
+                            to Q^T u: T is formed once at build (s - 1 more
+                            k x k products).  Variants C and G with an
+                            explicit basis (else RR_ERR_UNSUPPORTED); other
+                            values RR_ERR_INVALID_ARG.  0 (default): plain
+                            Q Q^T */
 } rr_build_opts;
 
 typedef struct {

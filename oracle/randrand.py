@@ -205,6 +205,7 @@ class Build:
     rho: float
     jitter: float = 0.0
     Tref: np.ndarray | None = None   # refined projector, eq:accurate_proj (refine=True)
+    refine_steps: int = 0            # eq:accurate_proj_2: refinement steps beyond the first
 
     # --- projector and preconditioner applications (Sec. 4.1 eq:projector)
     def Pi(self, V):
@@ -214,10 +215,32 @@ class Build:
         """A_mu^-1 Pi V = Omega R^-1 Q^T V (eq:projector with eq:invAPi)."""
         return self.Omega @ solve_upper(self.R, self.Q.T @ V)
 
+    def refined_coeffs(self, V):
+        """eq:accurate_proj_2: T(u, Q^T u) = v_s, v_1 = Q^T u,
+        v_{i+1} = v_i + Q^T (u - Q v_i), s = 1 + refine_steps."""
+        v = self.Q.T @ V
+        for _ in range(self.refine_steps):
+            v = v + self.Q.T @ (V - self.Q @ v)
+        return v
+
+    def refined_left(self, W):
+        """The same refinement for the outer projector of Pi A_mu^-1 Pi, whose
+        argument y = A_mu^-1 Pi u enters the recurrence only through
+        Q^T y = G c (a k-vector w): y_1 = w, y_{i+1} = y_i + w - Q^T (Q y_i)."""
+        y = W
+        for _ in range(self.refine_steps):
+            y = y + W - self.Q.T @ (self.Q @ y)
+        return y
+
     def apply_P(self, V):
         """C-RandRAND: P V = V - Q Q^T V + tau Q G Q^T V (eq:g_randrand_explicit).
         With the refined projector (eq:accurate_proj) Pi is replaced by
-        Q T Q^T and Pi A_mu^-1 Pi by Q T G T Q^T, T = 2 I - Q^T Q."""
+        Q T Q^T and Pi A_mu^-1 Pi by Q T G T Q^T, T = 2 I - Q^T Q; with
+        refine_steps >= 2 (eq:accurate_proj_2) the coefficients come from the
+        refinement recurrence on each vector."""
+        if self.refine_steps >= 2:
+            c = self.refined_coeffs(V)
+            return V - self.Q @ c + self.tau * (self.Q @ self.refined_left(self.G @ c))
         t = self.Q.T @ V
         if self.Tref is not None:
             Tt = self.Tref @ t
@@ -307,11 +330,12 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
           power_iters: int = 20, rho: float | None = None,
           tau: float | None = None, q: int = 0,
           a_omega: np.ndarray | None = None, ml_l1: int = 0, ml_gamma: int = 0,
-          refine: bool = False) -> Build:
+          refine: int = 0) -> Build:
     """a_omega: A Omega computed once for several shifts (Sec. 5.1): then
     omega must be the Omega it was computed from, and Y_mu = a_omega + mu
-    Omega replaces the product.  refine: the preconditioner applies the
-    Neumann-refined projector of eq:accurate_proj (variants C and G)."""
+    Omega replaces the product.  refine (variants C and G): 1 (or True) the
+    Neumann-refined projector of eq:accurate_proj; s >= 2 the refinement
+    recurrence of eq:accurate_proj_2 with s steps beyond the first."""
     n = op.n
     if not (1 <= k <= n):
         raise ValueError("need 1 <= k <= n")
@@ -412,7 +436,10 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
     else:
         raise ValueError(variant)
     if refine:
-        b.Tref = neumann_T(b.Q)
+        if int(refine) >= 2:
+            b.refine_steps = int(refine)        # eq:accurate_proj_2
+        else:
+            b.Tref = neumann_T(b.Q)             # eq:accurate_proj
     return b
 
 

@@ -410,7 +410,7 @@ class Handle:
                  gamma: int = 8, profile: bool = False, kernel_impl: int = 0, stream=None,
                  orth: str = "cholqr2", l_sk: int = 0, gamma_sk: int = 8, iter_impl: int = 0,
                  q: int = 0, keep_sketch: bool = False, ml_l1: int = 0, ml_gamma: int = 0,
-                 refine: bool = False):
+                 refine: int = 0):
         """sketch "multilevel": ml_l1 / ml_gamma give X1's rows and nonzeros per
         column; 0 takes rr_multilevel_defaults."""
         import torch
@@ -433,7 +433,7 @@ class Handle:
         o.iter_impl = iter_impl
         o.q = q
         o.keep_sketch = 1 if keep_sketch else 0
-        o.refine = 1 if refine else 0
+        o.refine = int(refine)
         set_multilevel(o, sketch, op.n, k, ml_l1, ml_gamma)
         self.opts = o
         self.ws_bytes = randrand_workspace_bytes(op.c, k, o)
@@ -575,7 +575,7 @@ class Request:
                  seed: int = 0, maxit: int = 20000, variant: str = "C", precision: str = "mixed",
                  orth: str = "cholqr2", power_iters: int = 20, gamma: int = 8, l_sk: int = 0,
                  gamma_sk: int = 8, kernel_impl: int = 0, iter_impl: int = 0, q: int = 0,
-                 ml_l1: int = 0, ml_gamma: int = 0, refine: bool = False):
+                 ml_l1: int = 0, ml_gamma: int = 0, refine: int = 0):
         import torch
         B = b.reshape(op.n, -1)
         m = B.shape[1]
@@ -594,7 +594,7 @@ class Request:
         o.kernel_impl = kernel_impl
         o.iter_impl = iter_impl
         o.q = q
-        o.refine = 1 if refine else 0
+        o.refine = int(refine)
         set_multilevel(o, sketch, op.n, k, ml_l1, ml_gamma)
         self.op = op
         self.c = rr_request(op=op.c, mu=float(mu), k=int(k), sketch=SKETCHES[sketch],

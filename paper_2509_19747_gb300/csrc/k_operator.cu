@@ -418,6 +418,95 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df(const float* __restri
   }
 }
 
+// Constants of the packed double-float entries below.
+struct Df2Const {
+  p2 ln2h, ln2l, sch2, scl2, m2, two, half, one, c3, c4, c5, s64, i64;
+};
+__device__ __forceinline__ Df2Const df2_const(float sch, float scl) {
+  Df2Const C;
+  C.ln2h = mk2(0.693147182464599609375f, 0.693147182464599609375f);
+  C.ln2l = mk2(-1.904654323148236e-09f, -1.904654323148236e-09f);
+  C.sch2 = mk2(sch, sch);
+  C.scl2 = mk2(scl, scl);
+  C.m2 = mk2(-2.f, -2.f);
+  C.two = mk2(2.f, 2.f);
+  C.half = mk2(0.5f, 0.5f);
+  C.one = mk2(1.f, 1.f);
+  C.c3 = mk2(0.16666667f, 0.16666667f);
+  C.c4 = mk2(0.041666668f, 0.041666668f);
+  C.c5 = mk2(0.0083333338f, 0.0083333338f);
+  C.s64 = mk2(64.f, 64.f);
+  C.i64 = mk2(0.015625f, 0.015625f);
+  return C;
+}
+
+// Two kernel entries K_ia, K_ib in double-float, one per lane of the packed
+// pair instructions: xj[d * xstride] = (x_a[d], x_b[d]) in shared memory,
+// pnj = (|x_a|^2 hi, |x_b|^2 hi, lo_a, lo_b); entries below 2^-100 (and lane
+// b when !pair) are zero.
+__device__ __forceinline__ df2 df2_entries(const p2* xi, const unsigned long long* xj, int xstride,
+                                           int dim, p2 pnih, p2 pnil, ulonglong2 pnj, bool pair,
+                                           const float2* tab, const Df2Const& C) {
+  // p_i . p_j in double-float
+  df2 c = two_prod2(xi[0], p2{xj[0]});
+#pragma unroll
+  for (int d = 1; d < kMaxDim; ++d) {
+    if (d < dim) {
+      const df2 t = two_prod2(xi[d], p2{xj[d * xstride]});
+      const df2 s2 = two_sum2(c.h, t.h);
+      c = {s2.h, add2(add2(c.l, t.l), s2.l)};
+    }
+  }
+  df2 a = two_sum2(pnih, p2{pnj.x});
+  a.l = add2(a.l, add2(pnil, p2{pnj.y}));
+  df2 b = two_sum2(a.h, mul2(C.m2, c.h));
+  b.l = add2(b.l, sub2(a.l, mul2(C.two, c.l)));
+  const df2 d2 = fast_two_sum2(b.h, b.l);
+  // t = -d2 * s  (s = log2(e) / (2 h^2) as sch + scl)
+  p2 th = neg2(mul2(d2.h, C.sch2));
+  p2 tl = neg2(fma2(d2.h, C.sch2, th));            // exact low part of -d2.h * sch
+  tl = fma2(neg2(d2.h), C.scl2, tl);
+  tl = fma2(neg2(d2.l), C.sch2, tl);
+  float2 thf = un2(th);
+  const bool va = thf.x > -100.f, vb = thf.y > -100.f && pair;
+  thf.x = va ? thf.x : -100.f;                     // keep the exponent in range
+  thf.y = vb ? thf.y : -100.f;
+  th = mk2(thf.x, thf.y);
+  const float kfa = rintf(thf.x), kfb = rintf(thf.y);
+  const p2 f = sub2(th, mk2(kfa, kfb));           // exact, |f| <= 1/2
+  const float2 f64 = un2(mul2(f, C.s64));
+  const float jfa = rintf(f64.x), jfb = rintf(f64.y);
+  const p2 r = sub2(f, mul2(mk2(jfa, jfb), C.i64));  // exact, |r| <= 1/128
+  const df2 rr = two_sum2(r, tl);
+  const df2 z = df_mul2(rr, df2{C.ln2h, C.ln2l});
+  const p2 zh = z.h;
+  const p2 p3 = mul2(mul2(mul2(zh, zh), zh), fma2(zh, fma2(zh, C.c5, C.c4), C.c3));
+  df2 q = two_prod2(zh, zh);
+  q.h = mul2(q.h, C.half);
+  q.l = fma2(zh, z.l, mul2(q.l, C.half));
+  const df2 ah = fast_two_sum2(C.one, zh);
+  const df2 bh = two_sum2(ah.h, q.h);
+  const p2 low = add2(add2(add2(ah.l, bh.l), add2(z.l, q.l)), p3);
+  const df2 E = fast_two_sum2(bh.h, low);
+  const float2 ta = tab[(int)jfa + 32], tb = tab[(int)jfb + 32];
+  df2 K = df_mul2(df2{mk2(ta.x, tb.x), mk2(ta.y, tb.y)}, E);
+  const float sca = va ? __int_as_float(((int)kfa + 127) << 23) : 0.f;   // 2^k or 0
+  const float scb = vb ? __int_as_float(((int)kfb + 127) << 23) : 0.f;
+  const p2 sc = mk2(sca, scb);
+  K.h = mul2(K.h, sc);
+  K.l = mul2(K.l, sc);
+  return K;
+}
+
+// acc += K * v in double-float (v = (hi, lo) pairs)
+__device__ __forceinline__ void df2_mac(df2& acc, const df2& K, p2 vh, p2 vl) {
+  df2 pr = two_prod2(K.h, vh);
+  pr.l = fma2(K.h, vl, pr.l);
+  pr.l = fma2(K.l, vh, pr.l);
+  const df2 s2 = two_sum2(acc.h, pr.h);
+  acc = {s2.h, add2(acc.l, add2(s2.l, pr.l))};
+}
+
 // The double-float product above with two columns j, j + 1 per step in the
 // lanes of packed float32 pair instructions (about half the instructions).
 // Every lane performs exactly the scalar kernel's operations; entries below
@@ -458,13 +547,7 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df2(const float* __restr
   df2 acc[MP];
 #pragma unroll
   for (int c = 0; c < MP; ++c) acc[c] = {mk2(0.f, 0.f), mk2(0.f, 0.f)};
-  const p2 ln2h = mk2(0.693147182464599609375f, 0.693147182464599609375f);
-  const p2 ln2l = mk2(-1.904654323148236e-09f, -1.904654323148236e-09f);
-  const p2 sch2 = mk2(sch, sch), scl2 = mk2(scl, scl);
-  const p2 m2 = mk2(-2.f, -2.f), two = mk2(2.f, 2.f), half = mk2(0.5f, 0.5f), one = mk2(1.f, 1.f);
-  const p2 c3 = mk2(0.16666667f, 0.16666667f), c4 = mk2(0.041666668f, 0.041666668f),
-           c5 = mk2(0.0083333338f, 0.0083333338f), s64 = mk2(64.f, 64.f),
-           i64 = mk2(0.015625f, 0.015625f);
+  const Df2Const C = df2_const(sch, scl);
   const int64_t j0 = (int64_t)blockIdx.y * cols_per_split;
   int64_t j1 = j0 + cols_per_split;
   if (j1 > n) j1 = n;
@@ -494,64 +577,12 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df2(const float* __restr
       const int jj = 2 * P;
       const bool pair = jj + 1 < cnt;
       const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(sx2 + P * kMaxDim);
-      // p_i . p_j in double-float
-      df2 c = two_prod2(xi[0], p2{xp[0]});
-#pragma unroll
-      for (int d = 1; d < kMaxDim; ++d) {
-        if (d < dim) {
-          const df2 t = two_prod2(xi[d], p2{xp[d]});
-          const df2 s2 = two_sum2(c.h, t.h);
-          c = {s2.h, add2(add2(c.l, t.l), s2.l)};
-        }
-      }
       const ulonglong2 pp = *reinterpret_cast<const ulonglong2*>(spn2 + P);
-      df2 a = two_sum2(pnih, p2{pp.x});
-      a.l = add2(a.l, add2(pnil, p2{pp.y}));
-      df2 b = two_sum2(a.h, mul2(m2, c.h));
-      b.l = add2(b.l, sub2(a.l, mul2(two, c.l)));
-      const df2 d2 = fast_two_sum2(b.h, b.l);
-      // t = -d2 * s  (s = log2(e) / (2 h^2) as sch + scl)
-      p2 th = neg2(mul2(d2.h, sch2));
-      p2 tl = neg2(fma2(d2.h, sch2, th));            // exact low part of -d2.h * sch
-      tl = fma2(neg2(d2.h), scl2, tl);
-      tl = fma2(neg2(d2.l), sch2, tl);
-      float2 thf = un2(th);
-      const bool va = thf.x > -100.f, vb = thf.y > -100.f && pair;
-      thf.x = va ? thf.x : -100.f;                     // keep the exponent in range
-      thf.y = vb ? thf.y : -100.f;
-      th = mk2(thf.x, thf.y);
-      const float kfa = rintf(thf.x), kfb = rintf(thf.y);
-      const p2 f = sub2(th, mk2(kfa, kfb));           // exact, |f| <= 1/2
-      const float2 f64 = un2(mul2(f, s64));
-      const float jfa = rintf(f64.x), jfb = rintf(f64.y);
-      const p2 r = sub2(f, mul2(mk2(jfa, jfb), i64));  // exact, |r| <= 1/128
-      const df2 rr = two_sum2(r, tl);
-      const df2 z = df_mul2(rr, df2{ln2h, ln2l});
-      const p2 zh = z.h;
-      const p2 p3 = mul2(mul2(mul2(zh, zh), zh), fma2(zh, fma2(zh, c5, c4), c3));
-      df2 q = two_prod2(zh, zh);
-      q.h = mul2(q.h, half);
-      q.l = fma2(zh, z.l, mul2(q.l, half));
-      const df2 ah = fast_two_sum2(one, zh);
-      const df2 bh = two_sum2(ah.h, q.h);
-      const p2 low = add2(add2(add2(ah.l, bh.l), add2(z.l, q.l)), p3);
-      const df2 E = fast_two_sum2(bh.h, low);
-      const float2 ta = tab[(int)jfa + 32], tb = tab[(int)jfb + 32];
-      df2 K = df_mul2(df2{mk2(ta.x, tb.x), mk2(ta.y, tb.y)}, E);
-      const float sca = va ? __int_as_float(((int)kfa + 127) << 23) : 0.f;   // 2^k or 0
-      const float scb = vb ? __int_as_float(((int)kfb + 127) << 23) : 0.f;
-      const p2 sc = mk2(sca, scb);
-      K.h = mul2(K.h, sc);
-      K.l = mul2(K.l, sc);
+      const df2 K = df2_entries(xi, xp, 1, dim, pnih, pnil, pp, pair, tab, C);
 #pragma unroll
       for (int cc = 0; cc < MP; ++cc) {
         const ulonglong2 vv = *reinterpret_cast<const ulonglong2*>(sv2 + P * MP + cc);
-        const p2 vh = p2{vv.x}, vl = p2{vv.y};
-        df2 pr = two_prod2(K.h, vh);
-        pr.l = fma2(K.h, vl, pr.l);
-        pr.l = fma2(K.l, vh, pr.l);
-        const df2 s2 = two_sum2(acc[cc].h, pr.h);
-        acc[cc] = {s2.h, add2(acc[cc].l, add2(s2.l, pr.l))};
+        df2_mac(acc[cc], K, p2{vv.x}, p2{vv.y});
       }
     }
   }
@@ -565,6 +596,147 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df2(const float* __restr
   }
 }
 
+
+// The same double-float product exploiting K_ij = K_ji: each 128 x 128 tile
+// (I, J) of the upper triangle (I <= J) is evaluated once (one CTA, one row of
+// block I per thread) and, off the diagonal, feeds both the row sums
+// w_I += K_IJ v_J and the column sums w_J += K_IJ^T v_I.  A warp's column sums
+// over its 32 rows rotate through the warp: at step s lane l evaluates its row
+// against column (l + s) mod 32 of a 32-column chunk (two chunks at once, one
+// per lane of the packed pair instructions) and adds K_ij v_i into the
+// accumulator of that column, then hands the accumulator to lane l - 1; after
+// 32 steps lane l holds column l's sum over the warp's rows, and the four
+// warps' sums are added in shared memory.  Each tile writes its two
+// contributions to the slot of the other block: part[J][rows of I] (row sums)
+// and part[I][rows of J] (column sums; the diagonal tile writes only its row
+// sums, to part[I][rows of I]), so every row receives exactly one value per
+// block, which k_sum_splits adds in block order.  Every entry is computed by
+// df2_entries, the arithmetic of k_kernel_mv_df2.  Grid: (blocks, blocks);
+// the CTAs below the diagonal return at once.
+template <int MP>
+__global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df2s(const float* __restrict__ x,
+                                                           const float2* __restrict__ pn,
+                                                           int64_t n, int dim, float sch, float scl,
+                                                           const double* __restrict__ V,
+                                                           double* __restrict__ part) {
+  const int J = blockIdx.x, I = blockIdx.y;
+  if (J < I) return;
+  const bool diag = I == J;
+  constexpr int kCh = 32;                        // columns per chunk (one warp rotation)
+  // pass p covers chunks 2p and 2p + 1; slot c of pass p holds the columns
+  // (64 p + c, 64 p + 32 + c) as the two lanes of a pair
+  __shared__ __align__(16) unsigned long long sx2[2][kMaxDim][kCh];
+  __shared__ __align__(16) float4 spn2[2][kCh];
+  __shared__ __align__(16) float4 sv2[2][kCh][MP];
+  __shared__ float2 tab[65];
+  __shared__ float2 scol[kKmvRows / 32][kKmvTile][MP];   // the warps' column sums (hi, lo)
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t < 65) {
+    const double tv = exp2((double)(t - 32) / 64.0);
+    const float h = (float)tv;
+    tab[t] = make_float2(h, (float)(tv - (double)h));
+  }
+  // this thread's row of block I, and its v_i as (hi, hi) / (lo, lo) pairs
+  const int64_t i = (int64_t)I * kKmvRows + t;
+  const bool live = i < n;
+  p2 xi[kMaxDim];
+#pragma unroll
+  for (int d = 0; d < kMaxDim; ++d) {
+    const float v = (live && d < dim) ? x[i * dim + d] : 0.f;
+    xi[d] = mk2(v, v);
+  }
+  const float2 pni = live ? pn[i] : make_float2(0.f, 0.f);
+  const p2 pnih = mk2(pni.x, pni.x), pnil = mk2(pni.y, pni.y);
+  p2 vih[MP], vil[MP];
+#pragma unroll
+  for (int cc = 0; cc < MP; ++cc) {
+    const df v = live ? df_from_double(V[i * MP + cc]) : df{0.f, 0.f};
+    vih[cc] = mk2(v.h, v.h);
+    vil[cc] = mk2(v.l, v.l);
+  }
+  // stage the columns of block J (thread t loads column t); columns past n
+  // get zero coordinates (finite entries) and zero coefficients
+  {
+    const int64_t j = (int64_t)J * kKmvTile + t;
+    const bool jl = j < n;
+    const int pp = t >> 6, hb = (t >> 5) & 1, c = t & 31;
+    float* xs = reinterpret_cast<float*>(&sx2[pp][0][c]) + hb;
+    for (int d = 0; d < kMaxDim; ++d) xs[d * kCh * 2] = (jl && d < dim) ? x[j * dim + d] : 0.f;
+    const float2 pj = jl ? pn[j] : make_float2(0.f, 0.f);
+    float* ps = reinterpret_cast<float*>(&spn2[pp][c]);
+    ps[hb] = pj.x;
+    ps[2 + hb] = pj.y;
+#pragma unroll
+    for (int cc = 0; cc < MP; ++cc) {
+      const df v = jl ? df_from_double(V[j * MP + cc]) : df{0.f, 0.f};
+      float* vs = reinterpret_cast<float*>(&sv2[pp][c][cc]);
+      vs[hb] = v.h;
+      vs[2 + hb] = v.l;
+    }
+  }
+  __syncthreads();
+  const Df2Const C = df2_const(sch, scl);
+  df2 acc[MP];
+#pragma unroll
+  for (int cc = 0; cc < MP; ++cc) acc[cc] = {mk2(0.f, 0.f), mk2(0.f, 0.f)};
+  for (int pp = 0; pp < 2; ++pp) {
+    df2 accc[MP];                                // column sums of the rotating columns
+#pragma unroll
+    for (int cc = 0; cc < MP; ++cc) accc[cc] = {mk2(0.f, 0.f), mk2(0.f, 0.f)};
+#pragma unroll 1
+    for (int step = 0; step < kCh; ++step) {
+      const int c = (lane + step) & (kCh - 1);
+      const ulonglong2 pj = *reinterpret_cast<const ulonglong2*>(&spn2[pp][c]);
+      const df2 K = df2_entries(xi, &sx2[pp][0][c], kCh, dim, pnih, pnil, pj, true, tab, C);
+#pragma unroll
+      for (int cc = 0; cc < MP; ++cc) {
+        const ulonglong2 vv = *reinterpret_cast<const ulonglong2*>(&sv2[pp][c][cc]);
+        df2_mac(acc[cc], K, p2{vv.x}, p2{vv.y});
+      }
+      if (!diag) {
+        const int src = (lane + 1) & 31;
+#pragma unroll
+        for (int cc = 0; cc < MP; ++cc) {
+          df2_mac(accc[cc], K, vih[cc], vil[cc]);
+          accc[cc].h.v = __shfl_sync(0xffffffffu, accc[cc].h.v, src);
+          accc[cc].l.v = __shfl_sync(0xffffffffu, accc[cc].l.v, src);
+        }
+      }
+    }
+    if (!diag) {
+      // lane l now holds the sums of columns 64 pp + l (lane a of the pair)
+      // and 64 pp + 32 + l (lane b) over this warp's rows
+#pragma unroll
+      for (int cc = 0; cc < MP; ++cc) {
+        const float2 h = un2(accc[cc].h), l = un2(accc[cc].l);
+        scol[warp][64 * pp + lane][cc] = make_float2(h.x, l.x);
+        scol[warp][64 * pp + 32 + lane][cc] = make_float2(h.y, l.y);
+      }
+    }
+  }
+  if (live) {
+    double* out = part + ((int64_t)J * n + i) * MP;
+#pragma unroll
+    for (int cc = 0; cc < MP; ++cc) {
+      const float2 h = un2(acc[cc].h), l = un2(acc[cc].l);
+      out[cc] = df_to_double(df_add(df{h.x, l.x}, df{h.y, l.y}));
+    }
+  }
+  if (!diag) {
+    __syncthreads();
+    const int64_t j = (int64_t)J * kKmvTile + t;
+    if (j < n) {
+      double* out = part + ((int64_t)I * n + j) * MP;
+#pragma unroll
+      for (int cc = 0; cc < MP; ++cc) {
+        df a = {scol[0][t][cc].x, scol[0][t][cc].y};
+#pragma unroll
+        for (int w = 1; w < kKmvRows / 32; ++w) a = df_add(a, df{scol[w][t][cc].x, scol[w][t][cc].y});
+        out[cc] = df_to_double(a);
+      }
+    }
+  }
+}
 
 __global__ void k_point_norms(const float* __restrict__ x, int64_t n, int dim,
                               float2* __restrict__ pn) {
@@ -619,6 +791,8 @@ static int kernel_nsplit(int64_t n) {
 size_t op_matvec_scratch_elems(const OpDev& op, int mp) {
   if (op.kind != RR_OP_GAUSS_KERNEL) return 0;
   int ns = kernel_nsplit(op.n);
+  // the symmetric double-float product keeps one slot per 128-row block
+  if (op.f64_df && op.dim <= kMaxDim && cdiv(op.n, kKmvRows) > ns) ns = (int)cdiv(op.n, kKmvRows);
   const int nt = mv_tc_nsplit(op.n), nt2 = mv_tc2_nsplit(op.n);
   if (nt > ns) ns = nt;
   if (nt2 > ns) ns = nt2;
@@ -684,6 +858,23 @@ void kernel_mv<double>(const OpDev& op, double mu, const double* V, double* W, i
   const double inv2h2 = 1.0 / (2.0 * op.bw * op.bw);
   dim3 grid((unsigned)cdiv(op.n, kKmvRows), (unsigned)ns);
   rec(ev, 0, st);
+  if (op.f64_df && op.df_sym) {
+    // K symmetric: each tile pair once (k_kernel_mv_df2s), one slot per block
+    const double s64 = 1.4426950408889634 * inv2h2;
+    const float sch = (float)s64;
+    const float scl = (float)(s64 - (double)sch);
+    const unsigned nb = (unsigned)cdiv(op.n, kKmvRows);
+    dim3 g2(nb, nb);
+    switch (mp) {
+      case 1: k_kernel_mv_df2s<1><<<g2, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, V, part); break;
+      case 2: k_kernel_mv_df2s<2><<<g2, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, V, part); break;
+      case 4: k_kernel_mv_df2s<4><<<g2, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, V, part); break;
+      default: k_kernel_mv_df2s<8><<<g2, kKmvRows, 0, st>>>(op.points, op.pn, op.n, op.dim, sch, scl, V, part); break;
+    }
+    rec(ev, 1, st);
+    k_sum_splits<double><<<(unsigned)cdiv(op.n * mp, 256), 256, 0, st>>>(part, (int)nb, op.n, mp, mu, V, W);
+    return;
+  }
   if (op.f64_df) {
     const double s64 = 1.4426950408889634 * inv2h2;
     const float sch = (float)s64;

@@ -78,6 +78,8 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   memset(&od, 0, sizeof(od));
   od.kind = A.kind;
   od.n = A.n;
+  od.dim = A.dim;
+  od.f64_df = (o.precision == RR_PREC_MIXED) ? 1 : 0;   // the restart residual's scratch
   const int gs_max = std::max(gram_nsplit(A.n, k, k), 1);
   L.size[R_OM] = n * kk * ts;
   L.size[R_OMB] = (o.precision == RR_PREC_MIXED) ? kk * (size_t)cdiv(A.n, 8) * 8 * 2 : 0;
@@ -182,7 +184,7 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
     return RR_ERR_UNSUPPORTED;
   if (o.q < 0 || o.q > 4) return RR_ERR_INVALID_ARG;
   if (!(o.restart_eta > 0.0 && o.restart_eta < 1.0)) return RR_ERR_INVALID_ARG;
-  if (o.refine != 0 && o.refine != 1) return RR_ERR_INVALID_ARG;
+  if (o.refine < 0 || o.refine > 8) return RR_ERR_INVALID_ARG;
   // the refined projector needs the stored basis (its Gram) and the H form
   if (o.refine && (o.variant == RR_VARIANT_R || basis_less(*A, o))) return RR_ERR_UNSUPPORTED;
   if (o.ml_gamma != 0 || o.ml_l1 != 0) {
@@ -372,6 +374,8 @@ void carve(rr_handle* h) {
   h->op.pn = (float2*)at(R_PN);
   // the refinement residual of the mixed path runs in double-float
   h->op.f64_df = (h->o.precision == RR_PREC_MIXED) ? 1 : 0;
+  h->op.df_sym = h->op.f64_df && h->op.kind == RR_OP_GAUSS_KERNEL &&
+                 h->L.size[R_MVS] >= (size_t)cdiv(h->n, 128) * h->n * h->mp * 8;
   h->mvs = at(R_MVS);
   const size_t ts = h->f64 ? 8 : 4;
   const size_t vec = (size_t)h->n * h->mp;
@@ -1338,9 +1342,23 @@ rr_status finish_build(rr_handle* h, const double* G1given) {
     // is the same expression)
     if (h->o.refine) {
       // Sec. 4.3 eq:accurate_proj: Pi ~ Q T Q^T, Pi A_mu^-1 Pi ~ Q T G T Q^T with
-      // T = 2 I - Q^T Q of the stored basis, so H = tau T G T - T
+      // T = 2 I - Q^T Q of the stored basis, so H = tau T G T - T.  With
+      // refine = s >= 2, eq:accurate_proj_2: the recurrence v_1 = Q^T u,
+      // v_{i+1} = v_i + Q^T (u - Q v_i) gives v_{s+1} = T Q^T u with the
+      // polynomial T = sum_{j <= s} (I - Q^T Q)^j (Horner: T <- I + E T,
+      // E = I - Q^T Q), folded into the k x k H once
       gram<T>(h, (const T*)h->Q, h->kk[kScA]);
-      kxk_scale_add_identity(h->kk[kScA], -1.0, 2.0, h->kk[kScB], k, st);
+      if (h->o.refine == 1) {
+        kxk_scale_add_identity(h->kk[kScA], -1.0, 2.0, h->kk[kScB], k, st);
+      } else {
+        kxk_scale_add_identity(h->kk[kScA], -1.0, 1.0, h->kk[kScA], k, st);     // E
+        kxk_scale_add_identity(h->kk[kScA], 1.0, 1.0, h->kk[kScB], k, st);      // I + E
+        for (int j = 2; j <= h->o.refine; ++j) {
+          gemm_nn<double>(k, k, k, 1.0, h->kk[kScA], k, h->kk[kScB], k, 0.0, nullptr, 0,
+                          h->kk[kTm], k, st);
+          kxk_scale_add_identity(h->kk[kTm], 1.0, 1.0, h->kk[kScB], k, st);    // I + E T
+        }
+      }
       gemm_nn<double>(k, k, k, 1.0, h->kk[kScB], k, h->kk[kG], k, 0.0, nullptr, 0, h->kk[kTm], k,
                       st);
       gemm_nn<double>(k, k, k, h->tau, h->kk[kTm], k, h->kk[kScB], k, 0.0, nullptr, 0,

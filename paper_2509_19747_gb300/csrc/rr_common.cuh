@@ -72,6 +72,9 @@ struct OpDev {
   // (float32 pipes) instead of native float64; pn = |p_i|^2 as hi + lo
   int f64_df;
   float2* pn;
+  // the double-float product takes each tile pair of the symmetric K once
+  // (its scratch holds one partial-sum slot per 128-row block)
+  int df_sym;
   // tensor-core float32 product (k_matvec_tc.cu): augmented TF32-split
   // point arrays, their tensor maps (host copies) and an error flag
   int use_tc;

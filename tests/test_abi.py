@@ -159,10 +159,13 @@ def test_refine_option_checks(lib):
     assert o.refine == 0
     o.refine = 1
     assert lib.randrand_workspace_bytes(dense, 10, o) > 0
-    o.refine = 2
-    with pytest.raises(lib.RandRandError) as e:
-        lib.randrand_workspace_bytes(dense, 10, o)
-    assert e.value.status == lib.RR_ERR_INVALID_ARG
+    o.refine = 8                     # eq:accurate_proj_2 with 8 refinement steps
+    assert lib.randrand_workspace_bytes(dense, 10, o) > 0
+    for bad in (9, -1):
+        o.refine = bad
+        with pytest.raises(lib.RandRandError) as e:
+            lib.randrand_workspace_bytes(dense, 10, o)
+        assert e.value.status == lib.RR_ERR_INVALID_ARG
     o.refine, o.variant = 1, lib.RR_VARIANT_R
     with pytest.raises(lib.RandRandError) as e:
         lib.randrand_workspace_bytes(dense, 10, o)

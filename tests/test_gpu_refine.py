@@ -1,7 +1,8 @@
-"""GPU parity of the refined projector (Sec. 4.3 eq:accurate_proj): P = I +
-Q (tau T G T - T) Q^T with T = 2 I - Q^T Q of the stored basis, against the
-oracle's refined build (float64), and its effect in the float32 paths, where
-the stored basis is orthonormal only to float32 rounding."""
+"""GPU parity of the refined projector (Sec. 4.3 eq:accurate_proj and
+eq:accurate_proj_2): P = I + Q (tau T G T - T) Q^T with T = 2 I - Q^T Q of
+the stored basis, or the polynomial T of the refinement recurrence, against
+the oracle's refined build (float64), and its effect in the float32 paths,
+where the stored basis is orthonormal only to float32 rounding."""
 import numpy as np
 import pytest
 
@@ -20,8 +21,13 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
+@pytest.mark.parametrize("refine", [1, 3])
 @pytest.mark.parametrize("variant", ["C", "G"])
-def test_refined_apply_and_iterates_fp64(cuda_lib, variant):
+def test_refined_apply_and_iterates_fp64(cuda_lib, variant, refine):
+    """refine = 1: the Neumann T of eq:accurate_proj; refine = 3: the
+    eq:accurate_proj_2 recurrence with three steps beyond the first (the
+    library folds it into a k x k polynomial at build, the oracle runs the
+    recurrence on every vector)."""
     rr = cuda_lib
     n, k = 600, 50
     P = W.dense_power_spectrum(n, seed=111, power=2.0)
@@ -32,9 +38,9 @@ def test_refined_apply_and_iterates_fp64(cuda_lib, variant):
         mu = 1e-4
     op = O.DenseOp(P.A)
     h = rr.Handle(rr.Operator.dense(dev(P.A)), mu, k, "gaussian", seed=111, variant=variant,
-                  q=1 if variant == "G" else 0, max_rhs=2, refine=True)
+                  q=1 if variant == "G" else 0, max_rhs=2, refine=refine)
     bd = O.build(op, mu, k, "gaussian", seed=111, variant=variant, q=1 if variant == "G" else 0,
-                 refine=True)
+                 refine=refine)
     r = np.random.default_rng(2).standard_normal((n, 2))
     cond = np.linalg.cond(bd.R)
     assert rel(h.apply(dev(r)).cpu().numpy(), bd.apply_P(r)) <= max(1e-12, 1e-15 * cond ** 2) * 100
@@ -79,6 +85,8 @@ def test_refine_options(cuda_lib):
     A = rr.Operator.dense(dev(P.A))
     with pytest.raises(rr.RandRandError):          # variant R keeps B's projector plain
         rr.Handle(A, 1e-3, 20, "gaussian", seed=113, variant="R", refine=True)
+    with pytest.raises(rr.RandRandError):          # at most 8 refinement steps
+        rr.Handle(A, 1e-3, 20, "gaussian", seed=113, refine=9)
     h = rr.Handle(A, 1e-3, 20, "gaussian", seed=113, refine=True, keep_sketch=True)
     h.set_mu(1e-2)                                 # the shift path rebuilds the refined H
     bd = O.build(O.DenseOp(P.A), 1e-2, 20, "gaussian", seed=113, refine=True)

@@ -826,3 +826,54 @@ def test_build_takes_the_jitter_ladder_for_an_indefinite_core():
     Rinv = np.linalg.inv(b.R)
     G_def = Rinv.T @ (M + b.jitter * np.eye(k)) @ Rinv
     assert np.allclose(b.G, G_def, rtol=0, atol=1e-10 * np.abs(G_def).max())
+
+
+def test_projector_refinement_recurrence_converges_to_pseudoinverse():
+    """eq:accurate_proj_2: v_1 = Q^T u, v_{i+1} = v_i + Q^T (u - Q v_i) is the
+    Neumann series of (Q^T Q)^-1 applied to Q^T u: for a nearly orthonormal Q
+    its error against the least-squares Q^+ u (library lstsq) falls like
+    |I - Q^T Q|^s, its first refinement equals the Neumann T = 2 I - Q^T Q of
+    eq:accurate_proj, and the refined P keeps the spectrum that exact
+    eigenvector deflation fixes."""
+    rng = np.random.default_rng(31)
+    n, k = 300, 25
+    Q0, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    Q = Q0 + 1e-3 * rng.standard_normal((n, k))            # |I - Q^T Q| ~ 1e-2
+    eps = np.linalg.norm(np.eye(k) - Q.T @ Q, 2)
+    u = rng.standard_normal((n, 2))
+    vstar = np.linalg.lstsq(Q, u, rcond=None)[0]
+    b = O.Build(op=None, mu=0.0, k=k, variant="C", Omega=None, Ymu=None, Q=Q, R=np.eye(k),
+                G=np.eye(k), normE=1.0, lam_max=1.0, tau=1.0, rho=1.0)
+    errs = []
+    for s in range(0, 5):
+        b.refine_steps = s
+        v = b.refined_coeffs(u)
+        errs.append(np.linalg.norm(v - vstar) / np.linalg.norm(vstar))
+        if s == 1:
+            assert np.allclose(v, O.neumann_T(Q) @ (Q.T @ u), rtol=0, atol=1e-13)
+    for s in range(1, 5):
+        assert errs[s] <= 3 * eps ** (s + 1)
+        assert errs[s] < errs[s - 1]
+    # the left refinement is the same polynomial in Q^T Q on a k-vector
+    w = rng.standard_normal((k, 2))
+    b.refine_steps = 3
+    E = np.eye(k) - Q.T @ Q
+    Tpoly = np.eye(k) + E + E @ E + E @ E @ E
+    assert np.allclose(b.refined_left(w), Tpoly @ w, rtol=0, atol=1e-12)
+    assert np.allclose(b.refined_coeffs(u), Tpoly @ (Q.T @ u), rtol=0, atol=1e-12)
+
+
+def test_refined_recurrence_build_solves_and_is_symmetric():
+    """A build with the eq:accurate_proj_2 refinement (3 steps beyond the
+    first) gives a symmetric P (checked on the dense matrix of the operator)
+    and solves to the dense Cholesky solution."""
+    P_, op = small_dense(n=200, seed=13)
+    mu, k = 1e-3, 30
+    bd = O.build(op, mu, k, "gaussian", seed=13, refine=3)
+    assert bd.refine_steps == 3
+    Pm = bd.apply_P(np.eye(200))
+    assert np.allclose(Pm, Pm.T, rtol=0, atol=1e-12 * np.abs(Pm).max())
+    B = W.gaussian_rhs(200, 2, 13)
+    X, infos = O.solve(bd, B, rtol=1e-12)
+    xs = np.linalg.solve(op.dense() + mu * np.eye(200), B)
+    assert np.linalg.norm(X - xs) / np.linalg.norm(xs) <= 1e-9
