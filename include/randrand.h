@@ -156,7 +156,14 @@ typedef struct {
                             other values: RR_ERR_INVALID_ARG */
   int32_t iter_impl;     /* variant C with a basis: 0 auto (one persistent
                             cooperative launch per iteration for everything
-                            after the operator product), 1 separate kernels */
+                            after the operator product), 1 separate kernels;
+                            basis-less CSR form: 0 one persistent launch per
+                            chunk of iterations, in its shared-memory window
+                            form (four grid barriers per iteration) when each
+                            CTA's rows and the rows they read fit, 1 separate
+                            kernels, 2 the persistent launch without windows
+                            (seven grid barriers); elsewhere 2 acts as 0;
+                            other values: RR_ERR_INVALID_ARG */
   int32_t q;             /* power of the test matrix Omega = A^q X^T
                             (eq:testmatrix), 0..4, default 0; q >= 1 costs q
                             more sketch products and is not available with the

@@ -33,7 +33,7 @@ constexpr int kMaxRestarts = 400;
 enum Region {
   R_OM, R_OMB, R_SSC, R_SSS, R_THC, R_THS, R_SK, R_Y, R_Q, R_Y0, R_KK, R_KKT, R_GPART, R_CHOLW,
   R_STATUS, R_XS, R_CN, R_PN, R_AUG, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT,
-  R_CS, R_NORMS, R_FUSED, R_ML, R_FWHT, R_PCNT, R_NREG
+  R_CS, R_NORMS, R_FUSED, R_ML, R_FWHT, R_PCNT, R_OMT, R_NREG
 };
 
 struct Layout {
@@ -118,6 +118,10 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_AUG] = (A.kind == RR_OP_GAUSS_KERNEL && A.dim == 8 && !uses_f64(o))
                       ? 2 * npad_tc * kAugFloats * 4 + mv_tc2_vsplit_elems(A.n) * 2 : 0;
   L.size[R_MVS] = op_matvec_scratch_elems(od, mp) * 8;
+  // Omega^T lists of the basis-less persistent step's window form
+  L.size[R_OMT] = (basis_less(A, o) && o.variant == RR_VARIANT_C && o.gamma >= 1 && o.gamma <= 8)
+                      ? align256(n * (size_t)o.gamma * 2) + (size_t)kFusedMaxCtas * (kk + 1) * 4
+                      : 0;
   // arrival counters of the tensor-core product's row pairs
   L.size[R_PCNT] = (A.kind == RR_OP_GAUSS_KERNEL && A.dim == 8 && !uses_f64(o))
                        ? (size_t)mv_tc_pairs(A.n) * 4 * 4 : 0;
@@ -176,7 +180,7 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
     }
   }
   if (o.power_iters < 1 || o.power_iters > 1000) return RR_ERR_INVALID_ARG;
-  if (o.iter_impl < 0 || o.iter_impl > 1) return RR_ERR_INVALID_ARG;
+  if (o.iter_impl < 0 || o.iter_impl > 2) return RR_ERR_INVALID_ARG;
   if (o.kernel_impl < 0 || o.kernel_impl > 3) return RR_ERR_INVALID_ARG;
   if (o.keep_sketch != 0 && o.keep_sketch != 1) return RR_ERR_INVALID_ARG;
   if (o.keep_sketch &&
@@ -285,6 +289,9 @@ struct rr_handle {
   int fusedG;         // CTAs of the persistent fused step (0: separate kernels)
   GridBar* bar;
   double* fscratch;
+  int imp_wmax;             // rows of the largest window of the basis-less step's window form
+  uint16_t* omt_ent;        // its Omega^T lists (n x gamma) and their offsets (G x (k + 1))
+  int32_t* omt_off;
   bool graph_failed;  // capture not possible: direct launches
   void* Y;
   void* Q;
@@ -410,6 +417,9 @@ void carve(rr_handle* h) {
   h->cnt = (unsigned*)at(R_CNT);
   h->cs = (ColState*)at(R_CS);
   h->norms = (double*)at(R_NORMS);
+  unsigned char* omt = (unsigned char*)at(R_OMT);
+  h->omt_ent = (uint16_t*)omt;
+  h->omt_off = omt ? (int32_t*)(omt + align256((size_t)h->n * h->o.gamma * 2)) : nullptr;
   unsigned char* fz = (unsigned char*)at(R_FUSED);
   h->bar = (GridBar*)fz;
   h->fscratch = fz ? (double*)(fz + sizeof(GridBar)) : nullptr;
@@ -835,7 +845,7 @@ rr_status power_iterations(rr_handle* h) {
   const Coefs8 a = coefs(1.0, 0.0);
   // the persistent step: the projections of an iteration in two persistent
   // launches around the product (variant R has no G and no column 1)
-  const int Gp = h->o.iter_impl == 0 ? pcg_tail_ctas<T>(n, h->k, mp) : 0;
+  const int Gp = h->o.iter_impl != 1 ? pcg_tail_ctas<T>(n, h->k, mp) : 0;
   const double* Gm = isC ? h->kk[kG] : nullptr;
   if (Gp > 0) {
     RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], h->st));
@@ -1333,10 +1343,24 @@ rr_status finish_build(rr_handle* h, const double* G1given) {
     // Hb = R^-1 (tau G - I) R^-T = tau Gb - Cinv
     axpby<double, double, double>(h->kk[kGb], coefs_all(h->tau), h->kk[kCinv], coefs_all(-1.0),
                                   h->kk[kHb], (int64_t)k * k, 1, st);
-    h->fusedG = (h->o.iter_impl == 0 && h->sketch == RR_SKETCH_SPARSE_SIGN &&
+    h->fusedG = (h->o.iter_impl != 1 && h->sketch == RR_SKETCH_SPARSE_SIGN &&
                  h->o.variant == RR_VARIANT_C)
                     ? pcg_implicit_ctas<T>(n, k, h->mp) : 0;
     if (h->fusedG > 0) RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
+    // the shared-memory window form when every CTA's window fits (the rows
+    // a banded operator's rows read stay near them)
+    h->imp_wmax = 0;
+    if (h->fusedG > 0 && h->o.iter_impl == 0 && h->omt_ent) {
+      int wmax = 0;
+      RR_CUDA_TRY(cudaMemsetAsync(h->dstatus + 5, 0, sizeof(int), st));
+      RR_CUDA_TRY(pcg_implicit_window(h->op, h->fusedG, h->dstatus + 5, st));
+      RR_TRY(read_int(h, h->dstatus + 5, &wmax));
+      if (pcg_implicit_window_fits<T>(wmax, k, h->mp, h->fusedG, n, h->o.gamma)) {
+        RR_CUDA_TRY(omega_t_lists(h->ss_cols, h->ss_sgn, n, h->fusedG, h->o.gamma, k, h->omt_ent,
+                                  h->omt_off, st));
+        h->imp_wmax = wmax;
+      }
+    }
   } else if (h->o.variant == RR_VARIANT_C || h->o.variant == RR_VARIANT_G) {
     // P = I + Q (tau G - I) Q^T = I + Q H Q^T (C; for G, (I - Pi) + tau Q G Q^T
     // is the same expression)
@@ -1368,7 +1392,7 @@ rr_status finish_build(rr_handle* h, const double* G1given) {
     } else {
       form_H(h->kk[kG], h->tau, h->kk[kH], k, st);
     }
-    h->fusedG = (h->o.iter_impl == 0 && h->o.variant == RR_VARIANT_C)
+    h->fusedG = (h->o.iter_impl != 1 && h->o.variant == RR_VARIANT_C)
                     ? pcg_tail_ctas<T>(n, k, h->mp) : 0;
     // keep QH = Q H so that z = r + QH (Q^T r)
     h->QH = h->Y;
@@ -1377,7 +1401,7 @@ rr_status finish_build(rr_handle* h, const double* G1given) {
       RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
   } else if (h->o.variant == RR_VARIANT_R) {
     // the projections of a CG step on B in two persistent launches
-    h->fusedG = h->o.iter_impl == 0 ? r_step_ctas<T>(n, k, h->mp) : 0;
+    h->fusedG = h->o.iter_impl != 1 ? r_step_ctas<T>(n, k, h->mp) : 0;
     if (h->fusedG > 0) RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
   }
   return sync_status(h);
@@ -1573,9 +1597,9 @@ rr_status run_chunk(rr_handle* h) {
     if (ev) RR_CUDA_TRY(cudaEventRecord(ev[0], h->st));
     RR_CUDA_TRY(pcg_implicit<T>(h->op, h->mu, h->ss_cols, h->ss_sgn, h->o.gamma, h->kk[kHb],
                                 vt<T>(h, kE), vt<T>(h, kR), vt<T>(h, kP), vt<T>(h, kW),
-                                vt<T>(h, kZ), vt<T>(h, kU), h->k, h->mp, h->fusedG, kImplicitChunk,
-                                h->fscratch,
-                                h->cs, h->bar, h->dstatus + 3, h->st));
+                                vt<T>(h, kZ), vt<T>(h, kU), vt<T>(h, kV), vt<T>(h, kS),
+                                h->imp_wmax, h->omt_ent, h->omt_off, h->k, h->mp, h->fusedG,
+                                kImplicitChunk, h->fscratch, h->cs, h->bar, h->dstatus + 3, h->st));
     if (ev) RR_CUDA_TRY(cudaEventRecord(ev[1], h->st));
     return RR_OK;
   }
@@ -2026,7 +2050,7 @@ size_t group_part_bound(int64_t n, int mp, int g) {
 
 bool group_qualifies(const rr_handle* h) {
   return h && !h->f64 && h->op.kind == RR_OP_GAUSS_KERNEL && h->op.use_tc && !h->op.tc2 &&
-         h->o.variant == RR_VARIANT_C && !h->implicit && h->fusedG > 0 && h->o.iter_impl == 0 &&
+         h->o.variant == RR_VARIANT_C && !h->implicit && h->fusedG > 0 && h->o.iter_impl != 1 &&
          h->Q && h->QH && h->op.pair_cnt && !h->prof;
 }
 

@@ -215,24 +215,63 @@ def test_sparse_operator_full_size(cuda_lib):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_persistent_basis_less_matches_separate_kernels(cuda_lib, precision):
-    """The persistent basis-less iteration (iter_impl 0) and the separate
-    kernels (iter_impl 1) agree: float64 iterates to 1e-10 at a fixed budget,
-    and both solve to rtol with the float64 residual as the judge."""
+    """The persistent basis-less iteration in its shared-memory window form
+    (iter_impl 0) and without windows (iter_impl 2), and the separate kernels
+    (iter_impl 1) agree: float64 iterates to 1e-10 at a fixed budget (an odd
+    one: the window form's r and p end in their second buffers), and all
+    solve to rtol with the float64 residual as the judge."""
     rr = cuda_lib
     C, op, vals = csr_problem(40, 46, fp64=(precision == "fp64"))
     mu, k = 1e-6, 32
     B = W.gaussian_rhs(C.n, 3, 46)
-    res = []
-    for impl in (0, 1):
-        h = csr_handle(rr, C, vals, mu, k, "sparse_sign", 46, precision=precision, max_rhs=3,
-                       iter_impl=impl)
+    _persistent_forms_agree(rr, C, op, vals, mu, k, B, 46, precision)
+
+
+def _persistent_forms_agree(rr, C, op, vals, mu, k, B, seed, precision):
+    res = {}
+    for impl in (0, 2, 1):
+        h = csr_handle(rr, C, vals, mu, k, "sparse_sign", seed, precision=precision,
+                       max_rhs=B.shape[1], iter_impl=impl)
         if precision == "fp64":
             x, status, infos = h.solve(dev(B), rtol=1e-14, maxit=25)
             assert status == rr.RR_ERR_MAXIT
-            res.append(x.cpu().numpy())
+            res[impl] = x.cpu().numpy()
         x, status, infos = h.solve(dev(B), rtol=1e-6, maxit=20000)
         assert status == rr.RR_OK
         assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), B) <= 1e-6)
         h.close()
     if precision == "fp64":
         assert rel(res[0], res[1]) <= 1e-10
+        assert rel(res[2], res[1]) <= 1e-10
+
+
+def random_graph_csr(n, deg, seed):
+    """SPD CSR without band structure: the weighted Laplacian of a random
+    graph (deg edges drawn per row, symmetrised) plus 1e-2 I, so that every
+    CTA's rows read columns across the whole range."""
+    sp = pytest.importorskip("scipy.sparse")
+    rng = np.random.default_rng(seed)
+    i = np.repeat(np.arange(n), deg)
+    j = rng.integers(0, n, n * deg)
+    w = rng.uniform(0.5, 2.0, n * deg)
+    keep = i != j
+    M = sp.coo_matrix((w[keep], (i[keep], j[keep])), shape=(n, n)).tocsr()
+    M = M + M.T
+    A = (sp.diags(np.asarray(M.sum(axis=1)).ravel()) - M + 1e-2 * sp.eye(n)).tocsr()
+    A.sort_indices()
+    return W.CsrMatrix(n=n, rowptr=A.indptr.astype(np.int32), colidx=A.indices.astype(np.int32),
+                       vals=A.data.astype(np.float64))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_persistent_forms_wide_and_banded_windows(cuda_lib, precision):
+    """Window form against the other two where the windows differ in kind: a
+    200 x 200 diffusion grid (each CTA's 264 rows read 200 rows on each side)
+    and a random graph Laplacian (every CTA reads nearly all 3000 rows)."""
+    rr = cuda_lib
+    C, op, vals = csr_problem(200, 47, fp64=(precision == "fp64"))
+    _persistent_forms_agree(rr, C, op, vals, 1e-5, 48, W.gaussian_rhs(C.n, 2, 47), 47, precision)
+    G = random_graph_csr(3000, 3, 48)
+    vals = dev(G.vals) if precision == "fp64" else dev(G.vals.astype(np.float32))
+    opg = O.CsrOp(G.rowptr, G.colidx, G.vals, G.n)
+    _persistent_forms_agree(rr, G, opg, vals, 1e-4, 40, W.gaussian_rhs(G.n, 3, 48), 48, precision)
