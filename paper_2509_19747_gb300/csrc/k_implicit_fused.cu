@@ -85,6 +85,8 @@ struct Dot<double> {
   __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
   __device__ __forceinline__ void shfl_add(int o) { s += __shfl_xor_sync(0xffffffffu, s, o); }
   __device__ __forceinline__ double get() const { return s; }
+  __device__ __forceinline__ void put(double* sh, int i) const { sh[i] = s; }
+  __device__ __forceinline__ void load(const double* sh, int i) { s = sh[i]; }
 };
 template <>
 struct Dot<float> {
@@ -96,14 +98,24 @@ struct Dot<float> {
     s = df_add(s, t);
   }
   __device__ __forceinline__ double get() const { return df_to_double(s); }
+  // a pair kept in one float64 slot of shared memory
+  __device__ __forceinline__ void put(double* sh, int i) const {
+    reinterpret_cast<float2*>(sh)[i] = make_float2(s.h, s.l);
+  }
+  __device__ __forceinline__ void load(const double* sh, int i) {
+    const float2 t = reinterpret_cast<const float2*>(sh)[i];
+    s = df{t.x, t.y};
+  }
 };
 
 // Block-wide sums of the threads' partials v[0..MP), added to dst[0..MP) with
-// float64 atomics when `add`.  Warp sums in the partials' own arithmetic, the
-// kIT / 32 warp sums in float64 by MP threads in fixed order.  Ends with the
-// block's threads synchronised after their earlier shared-memory writes.
+// float64 atomics when `add`: warp sums, then the kIT / 32 warp sums of
+// column c by warp c, all in the partials' own arithmetic, in fixed order.
+// Ends with the block's threads synchronised after their earlier
+// shared-memory writes.
 template <typename T, int MP>
 __device__ __forceinline__ void block_dot(Dot<T> (&v)[MP], double* sh, double* dst, bool add) {
+  static_assert(kIT / 32 == 16, "sixteen warp sums per column");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < MP; ++c)
@@ -111,14 +123,52 @@ __device__ __forceinline__ void block_dot(Dot<T> (&v)[MP], double* sh, double* d
     for (int o = 16; o > 0; o >>= 1) v[c].shfl_add(o);
   if (lane == 0)
 #pragma unroll
-    for (int c = 0; c < MP; ++c) sh[wid * 8 + c] = v[c].get();
+    for (int c = 0; c < MP; ++c) v[c].put(sh, wid * 8 + c);
   __syncthreads();
-  if (add && threadIdx.x < MP) {
-    double s = 0.0;
-    for (int w = 0; w < kIT / 32; ++w) s += sh[w * 8 + threadIdx.x];
-    atomicAdd(dst + threadIdx.x, s);
+  if (add && wid < MP) {
+    Dot<T> t;
+    t.zero();
+    if (lane < 16) t.load(sh, lane * 8 + wid);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) t.shfl_add(o);
+    if (lane == 0) atomicAdd(dst + wid, t.get());
   }
 }
+
+// One row's MP values (contiguous, aligned to their size) moved as 4-, 8- or
+// 16-byte pieces instead of MP scalar accesses.
+template <typename T, int MP>
+struct Vec {
+  static constexpr int kB = MP * (int)sizeof(T);
+  using W = typename std::conditional<(kB >= 16), uint4,
+                                      typename std::conditional<(kB == 8), uint2, unsigned>::type>::type;
+  static constexpr int kN = kB >= 16 ? kB / 16 : 1;
+  union U {
+    W w[kN];
+    T v[MP];
+  };
+  __device__ __forceinline__ static void ldcg(const T* p, T (&x)[MP]) {
+    U u;
+#pragma unroll
+    for (int i = 0; i < kN; ++i) u.w[i] = __ldcg(reinterpret_cast<const W*>(p) + i);
+#pragma unroll
+    for (int c = 0; c < MP; ++c) x[c] = u.v[c];
+  }
+  __device__ __forceinline__ static void ld(const T* p, T (&x)[MP]) {
+    U u;
+#pragma unroll
+    for (int i = 0; i < kN; ++i) u.w[i] = reinterpret_cast<const W*>(p)[i];
+#pragma unroll
+    for (int c = 0; c < MP; ++c) x[c] = u.v[c];
+  }
+  __device__ __forceinline__ static void st(T* p, const T (&x)[MP]) {
+    U u;
+#pragma unroll
+    for (int c = 0; c < MP; ++c) u.v[c] = x[c];
+#pragma unroll
+    for (int i = 0; i < kN; ++i) reinterpret_cast<W*>(p)[i] = u.w[i];
+  }
+};
 
 template <typename T>
 struct ImpArgs {
@@ -148,6 +198,7 @@ struct ImpArgs {
   int wmax;             // rows of the largest CTA window (window form), else 0
   const uint16_t* lst_ent;   // window form: Omega^T lists of each CTA's rows
   const int32_t* lst_off;    // [G][k + 1]
+  int ellw;                  // window form: ELL width of the rows in shared memory, 0: CSR
   ColState* cs;
   GridBar* bar;
   int* err;
@@ -244,13 +295,19 @@ __device__ int2 cta_window(const int32_t* __restrict__ rowptr, const int32_t* __
   return w;
 }
 
-// the largest window over the G CTAs of a launch with rpc rows each
+// the largest window over the G CTAs of a launch with rpc rows each (wmax[0])
+// and the longest row (wmax[1])
 __global__ void k_imp_window(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                              int64_t n, int rpc, int* __restrict__ wmax) {
   const int64_t r0 = (int64_t)blockIdx.x * rpc;
   const int cnt = (int)(r0 >= n ? 0 : (n - r0 < rpc ? n - r0 : rpc));
   const int2 w = cta_window(rowptr, colidx, r0, cnt);
   if (threadIdx.x == 0) atomicMax(wmax, w.y - w.x);
+  int len = 0;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) len = max(len, rowptr[r0 + i + 1] - rowptr[r0 + i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+  if ((threadIdx.x & 31) == 0 && len > 0) atomicMax(wmax + 1, len);
 }
 
 // Omega^T lists of the window form, per CTA range of rpc rows: for column c
@@ -337,6 +394,37 @@ __device__ __forceinline__ void csr_rows_sm(const ImpArgs<T>& a, const T* Xs, in
 #pragma unroll
           for (int c = 0; c < MP; ++c) out[m][c] = fma(av[m][q], Xs[j[m][q] * MP + c], out[m][c]);
   }
+}
+
+// csr_rows_sm on the CTA's rows held in shared memory as ELL: entry q of
+// local row i at ec/ev[q * rpc + i] (column relative to the window, padding
+// entries point at the row itself with value 0), in the CSR order
+template <typename T, int MP>
+__device__ __forceinline__ void ell_rows(const uint16_t* ec, const T* ev, int ellw, int rpc,
+                                         const T* Xs, int own0, int cnt, int i0, T mu,
+                                         T (&out)[kRPT][MP], bool (&live)[kRPT]) {
+#pragma unroll
+  for (int m = 0; m < kRPT; ++m) {
+    const int idx = i0 + m * kIT;
+    live[m] = idx < cnt;
+    T x[MP];
+    Vec<T, MP>::ld(Xs + (own0 + (live[m] ? idx : 0)) * MP, x);
+#pragma unroll
+    for (int c = 0; c < MP; ++c) out[m][c] = live[m] ? mu * x[c] : (T)0;
+  }
+#pragma unroll 6
+  for (int q = 0; q < ellw; ++q)
+#pragma unroll
+    for (int m = 0; m < kRPT; ++m)
+      if (live[m]) {
+        const int e = q * rpc + i0 + m * kIT;
+        const int j = ec[e];
+        const T v = ev[e];
+        T x[MP];
+        Vec<T, MP>::ld(Xs + j * MP, x);
+#pragma unroll
+        for (int c = 0; c < MP; ++c) out[m][c] = fma(v, x[c], out[m][c]);
+      }
 }
 
 template <typename T, int MP>
@@ -635,13 +723,15 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit(ImpArgs<T> a) {
 //   ps   wmax         and sign masks (bit t set: entry t negative)
 //   lo   k + 1        the CTA's Omega^T lists: column offsets
 //   le   rpc x gamma  entries: local row | 0x8000 when negative
+//   ec   ellw x rpc   the own rows as ELL (ellw > 0): columns in the window
+//   ev   ellw x rpc   and values
 struct WinSmem {
-  size_t acc, s, w0, w1, hb, pc, ps, lo, le, total;
+  size_t acc, s, w0, w1, hb, pc, ps, lo, le, ec, ev, total;
 };
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline int win_np(int k) { return k <= kIT ? kIT / k : 1; }
 __host__ __device__ inline WinSmem win_smem(int k, int mp, int ts, int wmax, int G, int rpc,
-                                            int gamma) {
+                                            int gamma, int ellw) {
   WinSmem L;
   size_t o = 0;
   L.acc = o; o += al16((size_t)win_np(k) * k * mp * ts);
@@ -653,6 +743,8 @@ __host__ __device__ inline WinSmem win_smem(int k, int mp, int ts, int wmax, int
   L.ps = o;  o += al16((size_t)wmax);
   L.lo = o;  o += al16((size_t)(k + 1) * 4);
   L.le = o;  o += al16((size_t)rpc * gamma * 2);
+  L.ec = o;  o += al16((size_t)ellw * rpc * 2);
+  L.ev = o;  o += al16((size_t)ellw * rpc * ts);
   L.total = o;
   return L;
 }
@@ -672,10 +764,10 @@ __host__ __device__ inline WinSmem win_smem(int k, int mp, int ts, int wmax, int
 //   3  convergence decision; s = Hb g (rows of Hb over the CTAs)     | barrier
 //   4  v = Omega s over the window; z = r + A_mu v; r^T z            | barrier
 //   5  beta
-template <typename T, int MP>
+template <typename T, int MP, int MA>
 __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit_win(ImpArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const WinSmem L = win_smem(a.k, MP, (int)sizeof(T), a.wmax, gridDim.x, a.rpc, a.gamma);
+  const WinSmem L = win_smem(a.k, MA, (int)sizeof(T), a.wmax, gridDim.x, a.rpc, a.gamma, a.ellw);
   T* acc_g = reinterpret_cast<T*>(smem_raw + L.acc);
   T* s_sh = reinterpret_cast<T*>(smem_raw + L.s);
   T* win0 = reinterpret_cast<T*>(smem_raw + L.w0);
@@ -686,6 +778,9 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit_win(ImpArgs<T> a) {
   unsigned char* ps_s = smem_raw + L.ps;
   int* lo_s = reinterpret_cast<int*>(smem_raw + L.lo);
   uint16_t* le_s = reinterpret_cast<uint16_t*>(smem_raw + L.le);
+  uint16_t* ec_s = reinterpret_cast<uint16_t*>(smem_raw + L.ec);
+  T* ev_s = reinterpret_cast<T*>(smem_raw + L.ev);
+  const int ellw = a.ellw;
   __shared__ ColState st[8];
   __shared__ double redd[kIT / 32 * 8];
   __shared__ double sh_alpha[8], sh_beta[8], sh_pw[8];
@@ -746,13 +841,22 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit_win(ImpArgs<T> a) {
   }
   for (int e = tid; e <= k; e += kIT) lo_s[e] = a.lst_off[(int64_t)cta * (k + 1) + e];
   for (int e = tid; e < cnt * gm; e += kIT) le_s[e] = a.lst_ent[r0 * gm + e];
+  for (int i = tid; ellw > 0 && i < cnt; i += kIT) {
+    const int32_t p0 = a.rowptr[r0 + i], p1 = a.rowptr[r0 + i + 1];
+    for (int q = 0; q < ellw; ++q) {
+      const int32_t p = p0 + q;
+      const bool ok = p < p1;
+      ec_s[q * a.rpc + i] = (uint16_t)(ok ? a.colidx[p] - lo : own0 + i);
+      ev_s[q * a.rpc + i] = ok ? aval(a, p) : (T)0;
+    }
+  }
   __syncthreads();
 
   int it = 0;
   for (; it < a.iters; ++it) {
     bool any = false;
 #pragma unroll
-    for (int c = 0; c < MP; ++c) any |= st[c].active != 0;
+    for (int c = 0; c < MA; ++c) any |= st[c].active != 0;
     if (!any) break;                               // identical in every CTA
     const int cur = it & 1;
 
@@ -762,25 +866,23 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit_win(ImpArgs<T> a) {
       // columns still active
       const T* Pold = it == 0 ? Pb[0] : Pb[cur ^ 1];
       T* Pnew = Pb[cur];
-      T be[MP];
-      bool act[MP];
+      T be[MA];
+      bool act[MA], anyact = false;
 #pragma unroll
-      for (int c = 0; c < MP; ++c) {
+      for (int c = 0; c < MA; ++c) {
         be[c] = (T)sh_beta[c];
         act[c] = it > 0 && st[c].active;
+        anyact |= act[c];
       }
-      constexpr int kB = MP * sizeof(T) >= 32 ? 2 : 4;   // window rows a thread loads together
+      constexpr int kB = MA * sizeof(T) >= 32 ? 2 : (MA * sizeof(T) >= 16 ? 4 : 6);  // rows loaded together
       for (int i0 = tid; i0 < wl; i0 += kIT * kB) {
-        T pp[kB][MP], zz[kB][MP];
+        T pp[kB][MA], zz[kB][MA];
 #pragma unroll
         for (int b = 0; b < kB; ++b) {
           const int i = i0 + b * kIT;
           const int64_t g0 = (int64_t)(lo + (i < wl ? i : 0)) * MP;
-#pragma unroll
-          for (int c = 0; c < MP; ++c) {
-            pp[b][c] = __ldcg(Pold + g0 + c);
-            zz[b][c] = act[c] ? __ldcg(a.Z + g0 + c) : (T)0;
-          }
+          Vec<T, MA>::ldcg(Pold + g0, pp[b]);
+          if (anyact) Vec<T, MA>::ldcg(a.Z + g0, zz[b]);
         }
 #pragma unroll
         for (int b = 0; b < kB; ++b) {
@@ -788,41 +890,43 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit_win(ImpArgs<T> a) {
           if (i >= wl) continue;
           const bool mine = it > 0 && i >= own0 && i < own0 + cnt;
           const int64_t g0 = (int64_t)(lo + i) * MP;
+          T p[MA];
 #pragma unroll
-          for (int c = 0; c < MP; ++c) {
-            const T p = act[c] ? fma(be[c], pp[b][c], zz[b][c]) : pp[b][c];
-            if (mine) Pnew[g0 + c] = p;
-            win0[i * MP + c] = p;
-          }
+          for (int c = 0; c < MA; ++c) p[c] = act[c] ? fma(be[c], pp[b][c], zz[b][c]) : pp[b][c];
+          if (mine) Vec<T, MA>::st(Pnew + g0, p);
+          Vec<T, MA>::st(win0 + i * MA, p);
         }
       }
     }
     __syncthreads();
-    Dot<T> v[MP];
+    Dot<T> v[MA];
 #pragma unroll
-    for (int c = 0; c < MP; ++c) v[c].zero();
+    for (int c = 0; c < MA; ++c) v[c].zero();
     for (int i0 = tid; i0 < cnt; i0 += kIT * kRPT) {
-      T w[kRPT][MP];
+      T w[kRPT][MA];
       bool live[kRPT];
-      csr_rows_sm<T, MP>(a, win0, lo, r0, cnt, i0, mu, w, live);
+      if (ellw > 0)
+        ell_rows<T, MA>(ec_s, ev_s, ellw, a.rpc, win0, own0, cnt, i0, mu, w, live);
+      else
+        csr_rows_sm<T, MA>(a, win0, lo, r0, cnt, i0, mu, w, live);
 #pragma unroll
       for (int m = 0; m < kRPT; ++m)
         if (live[m]) {
           const int li = own0 + i0 + m * kIT;
           const int64_t row = r0 + i0 + m * kIT;
+          Vec<T, MA>::st(a.W + row * MP, w[m]);
+          T pv[MA];
+          Vec<T, MA>::ld(win0 + li * MA, pv);
 #pragma unroll
-          for (int c = 0; c < MP; ++c) {
-            a.W[row * MP + c] = w[m][c];
-            v[c].add(win0[li * MP + c], w[m][c]);
-          }
+          for (int c = 0; c < MA; ++c) v[c].add(pv[c], w[m][c]);
         }
     }
-    block_dot<T, MP>(v, redd, acc_pw, cnt > 0);
+    block_dot<T, MA>(v, redd, acc_pw, cnt > 0);
     if (!barrier_all(a.bar, a.err)) return;
 
     // ---- 2: alpha; e (own rows), r over the window, |r|^2; u = A_mu r and
     // g += Omega^T u
-    if (tid < MP) {
+    if (tid < MA) {
       const int c = tid;
       const double pw = __ldcg(acc_pw + c);
       sh_pw[c] = pw;
@@ -838,27 +942,24 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit_win(ImpArgs<T> a) {
     if (cta == 0 && tid < 8) acc_rz[tid] = 0.0;
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < MP; ++c) v[c].zero();
+    for (int c = 0; c < MA; ++c) v[c].zero();
     {
       const T* Rold = Rb[cur];
       T* Rnew = Rb[cur ^ 1];
-      T al[MP];
+      T al[MA];
 #pragma unroll
-      for (int c = 0; c < MP; ++c) al[c] = (T)sh_alpha[c];
-      constexpr int kB = MP * sizeof(T) >= 32 ? 2 : 4;   // window rows a thread loads together
+      for (int c = 0; c < MA; ++c) al[c] = (T)sh_alpha[c];
+      constexpr int kB = MA * sizeof(T) >= 32 ? 2 : (MA * sizeof(T) >= 16 ? 4 : 6);  // rows loaded together
       for (int i0 = tid; i0 < wl; i0 += kIT * kB) {
-        T rr_[kB][MP], ww[kB][MP], ee[kB][MP];
+        T rr_[kB][MA], ww[kB][MA], ee[kB][MA];
 #pragma unroll
         for (int b = 0; b < kB; ++b) {
           const int i = i0 + b * kIT;
           const bool mine = i >= own0 && i < own0 + cnt;
           const int64_t g0 = (int64_t)(lo + (i < wl ? i : 0)) * MP;
-#pragma unroll
-          for (int c = 0; c < MP; ++c) {
-            rr_[b][c] = __ldcg(Rold + g0 + c);
-            ww[b][c] = __ldcg(a.W + g0 + c);
-            ee[b][c] = mine ? a.E[g0 + c] : (T)0;
-          }
+          Vec<T, MA>::ldcg(Rold + g0, rr_[b]);
+          Vec<T, MA>::ldcg(a.W + g0, ww[b]);
+          if (mine) Vec<T, MA>::ld(a.E + g0, ee[b]);
         }
 #pragma unroll
         for (int b = 0; b < kB; ++b) {
@@ -866,30 +967,36 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit_win(ImpArgs<T> a) {
           if (i >= wl) continue;
           const bool mine = i >= own0 && i < own0 + cnt;
           const int64_t g0 = (int64_t)(lo + i) * MP;
+          T r[MA];
 #pragma unroll
-          for (int c = 0; c < MP; ++c) {
-            const T r = fma(-al[c], ww[b][c], rr_[b][c]);
-            win1[i * MP + c] = r;
-            if (mine) {
-              Rnew[g0 + c] = r;
-              a.E[g0 + c] = fma(al[c], win0[i * MP + c], ee[b][c]);
-              v[c].add(r, r);
+          for (int c = 0; c < MA; ++c) r[c] = fma(-al[c], ww[b][c], rr_[b][c]);
+          Vec<T, MA>::st(win1 + i * MA, r);
+          if (mine) {
+            T pv[MA], e[MA];
+            Vec<T, MA>::ld(win0 + i * MA, pv);
+#pragma unroll
+            for (int c = 0; c < MA; ++c) {
+              e[c] = fma(al[c], pv[c], ee[b][c]);
+              v[c].add(r[c], r[c]);
             }
+            Vec<T, MA>::st(Rnew + g0, r);
+            Vec<T, MA>::st(a.E + g0, e);
           }
         }
       }
     }
-    block_dot<T, MP>(v, redd, acc_rr, cnt > 0);   // also orders win1 before its readers
+    block_dot<T, MA>(v, redd, acc_rr, cnt > 0);   // also orders win1 before its readers
     // u = A_mu r of the own rows into w0 (p is no longer read)
     for (int i0 = tid; i0 < cnt; i0 += kIT * kRPT) {
-      T u[kRPT][MP];
+      T u[kRPT][MA];
       bool live[kRPT];
-      csr_rows_sm<T, MP>(a, win1, lo, r0, cnt, i0, mu, u, live);
+      if (ellw > 0)
+        ell_rows<T, MA>(ec_s, ev_s, ellw, a.rpc, win1, own0, cnt, i0, mu, u, live);
+      else
+        csr_rows_sm<T, MA>(a, win1, lo, r0, cnt, i0, mu, u, live);
 #pragma unroll
       for (int m = 0; m < kRPT; ++m)
-        if (live[m])
-#pragma unroll
-          for (int c = 0; c < MP; ++c) win0[(own0 + i0 + m * kIT) * MP + c] = u[m][c];
+        if (live[m]) Vec<T, MA>::st(win0 + (own0 + i0 + m * kIT) * MA, u[m]);
     }
     __syncthreads();
     // g = Omega^T u over the own rows: np threads per column, each summing a
@@ -900,32 +1007,33 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit_win(ImpArgs<T> a) {
         const int c = e % k, h = e / k;
         const int b0 = lo_s[c], len = lo_s[c + 1] - b0;
         const int q0 = b0 + len * h / np, q1 = b0 + len * (h + 1) / np;
-        T acc[MP];
+        T acc[MA];
 #pragma unroll
-        for (int c2 = 0; c2 < MP; ++c2) acc[c2] = (T)0;
+        for (int c2 = 0; c2 < MA; ++c2) acc[c2] = (T)0;
         for (int q = q0; q < q1; ++q) {
           const unsigned ent = le_s[q];
-          const T* u = win0 + (own0 + (int)(ent & 0x7fffu)) * MP;
+          T u[MA];
+          Vec<T, MA>::ld(win0 + (own0 + (int)(ent & 0x7fffu)) * MA, u);
           const T sg = (ent & 0x8000u) ? -om : om;
 #pragma unroll
-          for (int c2 = 0; c2 < MP; ++c2) acc[c2] = fma(sg, u[c2], acc[c2]);
+          for (int c2 = 0; c2 < MA; ++c2) acc[c2] = fma(sg, u[c2], acc[c2]);
         }
 #pragma unroll
-        for (int c2 = 0; c2 < MP; ++c2) acc_g[((size_t)h * k + c) * MP + c2] = acc[c2];
+        for (int c2 = 0; c2 < MA; ++c2) acc_g[((size_t)h * k + c) * MA + c2] = acc[c2];
       }
       __syncthreads();
       if (cnt > 0)
-        for (int e = tid; e < k * MP; e += kIT) {
+        for (int e = tid; e < k * MA; e += kIT) {
           T x = acc_g[e];
-          for (int h = 1; h < np; ++h) x += acc_g[(size_t)h * k * MP + e];
-          if (x != (T)0) atomicAdd(gacc + (e / MP) * 8 + (e % MP), (double)x);
+          for (int h = 1; h < np; ++h) x += acc_g[(size_t)h * k * MA + e];
+          if (x != (T)0) atomicAdd(gacc + (e / MA) * 8 + (e % MA), (double)x);
         }
     }
     if (!barrier_all(a.bar, a.err)) return;
 
     // ---- 3: convergence decision; s = Hb g, the CTA's rows of Hb (j = cta,
     // cta + G, ...), g staged in shared memory
-    if (tid < MP) {
+    if (tid < MA) {
       const int c = tid;
       const double rr = __ldcg(acc_rr + c);
       ColState& s = st[c];
@@ -945,23 +1053,23 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit_win(ImpArgs<T> a) {
       }
     }
     if (cta == 0 && tid < 8) acc_pw[tid] = 0.0;
-    for (int e = tid; e < k * MP; e += kIT) s_sh[e] = (T)__ldcg(gacc + (e / MP) * 8 + (e % MP));
+    for (int e = tid; e < k * MA; e += kIT) s_sh[e] = (T)__ldcg(gacc + (e / MA) * 8 + (e % MA));
     __syncthreads();
     for (int w = wid; w < nr; w += kIT / 32) {
       const int j = cta + w * G;
       const HbT* hj = hb_s + (size_t)w * k;
-      double x[MP];
+      double x[MA];
       if constexpr (sizeof(T) == 8) {
-        double acc[MP];
+        double acc[MA];
 #pragma unroll
-        for (int c = 0; c < MP; ++c) acc[c] = 0.0;
+        for (int c = 0; c < MA; ++c) acc[c] = 0.0;
         for (int l = lane; l < k; l += 32) {
           const double h = hj[l];
 #pragma unroll
-          for (int c = 0; c < MP; ++c) acc[c] = fma(h, (double)s_sh[l * MP + c], acc[c]);
+          for (int c = 0; c < MA; ++c) acc[c] = fma(h, (double)s_sh[l * MA + c], acc[c]);
         }
 #pragma unroll
-        for (int c = 0; c < MP; ++c) {
+        for (int c = 0; c < MA; ++c) {
           double y = acc[c];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
@@ -969,21 +1077,21 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit_win(ImpArgs<T> a) {
         }
       } else {
         // double-float products of Hb's pairs with g, double-float sums
-        Dot<float> acc[MP];
+        Dot<float> acc[MA];
 #pragma unroll
-        for (int c = 0; c < MP; ++c) acc[c].zero();
+        for (int c = 0; c < MA; ++c) acc[c].zero();
         for (int l = lane; l < k; l += 32) {
           const float2 h = hj[l];
 #pragma unroll
-          for (int c = 0; c < MP; ++c) {
-            const float g = (float)s_sh[l * MP + c];
+          for (int c = 0; c < MA; ++c) {
+            const float g = (float)s_sh[l * MA + c];
             df p = two_prod(h.x, g);
             p.l = __fmaf_rn(h.y, g, p.l);
             acc[c].s = df_add(acc[c].s, p);
           }
         }
 #pragma unroll
-        for (int c = 0; c < MP; ++c) {
+        for (int c = 0; c < MA; ++c) {
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) acc[c].shfl_add(o);
           x[c] = acc[c].get();
@@ -991,61 +1099,82 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit_win(ImpArgs<T> a) {
       }
       if (lane == 0)
 #pragma unroll
-        for (int c = 0; c < MP; ++c) a.sglob[(int64_t)j * MP + c] = x[c];
+        for (int c = 0; c < MA; ++c) a.sglob[(int64_t)j * MA + c] = x[c];
     }
     if (!barrier_all(a.bar, a.err)) return;
 
     // ---- 4: v = Omega s over the window; z = r + A_mu v, r^T z
-    for (int e = tid; e < k * MP; e += kIT) s_sh[e] = (T)__ldcg(a.sglob + e);
+    for (int e = tid; e < k * MA; e += kIT) s_sh[e] = (T)__ldcg(a.sglob + e);
     if (cta == 0) {
       for (int e = tid; e < k * 8; e += kIT) gacc[e] = 0.0;
       if (tid < 8) acc_rr[tid] = 0.0;
     }
     __syncthreads();
-    for (int i = tid; i < wl; i += kIT) {
-      const uint4 cw = pc_s[i];
-      const unsigned sgn = ps_s[i];
-      const uint32_t ww[4] = {cw.x, cw.y, cw.z, cw.w};
-      T acc[MP];
+    for (int i0 = tid; i0 < wl; i0 += 2 * kIT) {
+      // two rows a thread: their pattern words and gathers in flight together
+      uint32_t ww[2][4];
+      unsigned sgn[2];
 #pragma unroll
-      for (int c = 0; c < MP; ++c) acc[c] = (T)0;
+      for (int b = 0; b < 2; ++b) {
+        const int i = i0 + b * kIT < wl ? i0 + b * kIT : i0;
+        const uint4 cw = pc_s[i];
+        ww[b][0] = cw.x;
+        ww[b][1] = cw.y;
+        ww[b][2] = cw.z;
+        ww[b][3] = cw.w;
+        sgn[b] = ps_s[i];
+      }
+      T acc[2][MA];
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int c = 0; c < MA; ++c) acc[b][c] = (T)0;
 #pragma unroll
       for (int t = 0; t < 8; ++t)
-        if (t < gm) {
-          const int col = (int)((ww[t >> 1] >> ((t & 1) * 16)) & 0xffffu);
-          const T sg = ((sgn >> t) & 1u) ? -om : om;
+        if (t < gm)
 #pragma unroll
-          for (int c = 0; c < MP; ++c) acc[c] = fma(sg, s_sh[col * MP + c], acc[c]);
-        }
+          for (int b = 0; b < 2; ++b) {
+            const int col = (int)((ww[b][t >> 1] >> ((t & 1) * 16)) & 0xffffu);
+            const T sg = ((sgn[b] >> t) & 1u) ? -om : om;
+            T sv[MA];
+            Vec<T, MA>::ld(s_sh + col * MA, sv);
 #pragma unroll
-      for (int c = 0; c < MP; ++c) win0[i * MP + c] = acc[c];
+            for (int c = 0; c < MA; ++c) acc[b][c] = fma(sg, sv[c], acc[b][c]);
+          }
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+        if (i0 + b * kIT < wl) Vec<T, MA>::st(win0 + (i0 + b * kIT) * MA, acc[b]);
     }
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < MP; ++c) v[c].zero();
+    for (int c = 0; c < MA; ++c) v[c].zero();
     for (int i0 = tid; i0 < cnt; i0 += kIT * kRPT) {
-      T zv[kRPT][MP];
+      T zv[kRPT][MA];
       bool live[kRPT];
-      csr_rows_sm<T, MP>(a, win0, lo, r0, cnt, i0, mu, zv, live);
+      if (ellw > 0)
+        ell_rows<T, MA>(ec_s, ev_s, ellw, a.rpc, win0, own0, cnt, i0, mu, zv, live);
+      else
+        csr_rows_sm<T, MA>(a, win0, lo, r0, cnt, i0, mu, zv, live);
 #pragma unroll
       for (int m = 0; m < kRPT; ++m)
         if (live[m]) {
           const int li = own0 + i0 + m * kIT;
           const int64_t row = r0 + i0 + m * kIT;
+          T r[MA], z[MA];
+          Vec<T, MA>::ld(win1 + li * MA, r);
 #pragma unroll
-          for (int c = 0; c < MP; ++c) {
-            const T r = win1[li * MP + c];
-            const T z = r + zv[m][c];
-            a.Z[row * MP + c] = z;
-            v[c].add(r, z);
+          for (int c = 0; c < MA; ++c) {
+            z[c] = r[c] + zv[m][c];
+            v[c].add(r[c], z[c]);
           }
+          Vec<T, MA>::st(a.Z + row * MP, z);
         }
     }
-    block_dot<T, MP>(v, redd, acc_rz, cnt > 0);
+    block_dot<T, MA>(v, redd, acc_rz, cnt > 0);
     if (!barrier_all(a.bar, a.err)) return;
 
     // ---- 5: beta (p is formed at the next iteration's start or below)
-    if (tid < MP) {
+    if (tid < MA) {
       const int c = tid;
       const double rz = __ldcg(acc_rz + c);
       ColState& s = st[c];
@@ -1071,7 +1200,7 @@ __global__ void __launch_bounds__(kIT, 1) k_pcg_implicit_win(ImpArgs<T> a) {
     for (int i = tid; i < cnt; i += kIT) {
       const int64_t g0 = (r0 + i) * MP;
 #pragma unroll
-      for (int c = 0; c < MP; ++c) {
+      for (int c = 0; c < MA; ++c) {
         T p = Pl[g0 + c];
         if (st[c].active) p = fma((T)sh_beta[c], p, a.Z[g0 + c]);
         a.P[g0 + c] = p;
@@ -1089,11 +1218,11 @@ size_t imp_smem(int k, int mp, int wmax) {
 
 // raise the kernel's dynamic shared-memory limit to the device maximum once
 // per device (outside any stream capture: called first from the build)
-template <typename T, int MP, bool WIN>
-bool imp_attr() {
-  static std::atomic<uint64_t> done{0};
-  return once_per_device(done, [] {
-    auto kern = WIN ? k_pcg_implicit_win<T, MP> : k_pcg_implicit<T, MP>;
+// raise a kernel's dynamic shared-memory limit to the device maximum once
+// per device (outside any stream capture: called first from the build)
+template <typename K>
+bool smem_attr(K kern, std::atomic<uint64_t>& done) {
+  return once_per_device(done, [kern] {
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
@@ -1114,12 +1243,19 @@ bool imp_attr() {
 }
 
 template <typename T, int MP>
-cudaError_t launch_imp(const ImpArgs<T>& a, int G, cudaStream_t st) {
-  const bool win = a.wmax > 0;
-  auto kern = win ? k_pcg_implicit_win<T, MP> : k_pcg_implicit<T, MP>;
-  const size_t smem =
-      win ? win_smem(a.k, MP, (int)sizeof(T), a.wmax, G, a.rpc, a.gamma).total : imp_smem<T>(a.k, MP, 0);
-  if (!(win ? imp_attr<T, MP, true>() : imp_attr<T, MP, false>())) return cudaErrorInvalidValue;
+bool imp_attr() {
+  static std::atomic<uint64_t> done{0};
+  return smem_attr(k_pcg_implicit<T, MP>, done);
+}
+
+template <typename T, int MP, int MA>
+bool imp_win_attr() {
+  static std::atomic<uint64_t> done{0};
+  return smem_attr(k_pcg_implicit_win<T, MP, MA>, done);
+}
+
+template <typename K, typename T>
+cudaError_t coop_launch(K kern, const ImpArgs<T>& a, int G, size_t smem, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
   cfg.blockDim = dim3(kIT);
@@ -1131,6 +1267,21 @@ cudaError_t launch_imp(const ImpArgs<T>& a, int G, cudaStream_t st) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <typename T, int MP>
+cudaError_t launch_imp(const ImpArgs<T>& a, int G, cudaStream_t st) {
+  if (!imp_attr<T, MP>()) return cudaErrorInvalidValue;
+  return coop_launch(k_pcg_implicit<T, MP>, a, G, imp_smem<T>(a.k, MP, 0), st);
+}
+
+// the window form computes the first MA of the MP columns (the others are
+// inactive in this solve)
+template <typename T, int MP, int MA>
+cudaError_t launch_imp_win(const ImpArgs<T>& a, int G, cudaStream_t st) {
+  if (!imp_win_attr<T, MP, MA>()) return cudaErrorInvalidValue;
+  const size_t smem = win_smem(a.k, MA, (int)sizeof(T), a.wmax, G, a.rpc, a.gamma, a.ellw).total;
+  return coop_launch(k_pcg_implicit_win<T, MP, MA>, a, G, smem, st);
 }
 
 }  // namespace
@@ -1150,10 +1301,10 @@ int pcg_implicit_ctas(int64_t n, int k, int mp) {
   if (imp_smem<T>(k, mp, 0) + 8192 > (size_t)optin) return 0;
   bool attr = false;
   switch (mp) {
-    case 1: attr = imp_attr<T, 1, false>(); break;
-    case 2: attr = imp_attr<T, 2, false>(); break;
-    case 4: attr = imp_attr<T, 4, false>(); break;
-    default: attr = imp_attr<T, 8, false>(); break;
+    case 1: attr = imp_attr<T, 1>(); break;
+    case 2: attr = imp_attr<T, 2>(); break;
+    case 4: attr = imp_attr<T, 4>(); break;
+    default: attr = imp_attr<T, 8>(); break;
   }
   if (!attr) return 0;
   int64_t g = sms;
@@ -1177,30 +1328,37 @@ cudaError_t omega_t_lists(const int32_t* cols, const int8_t* sgn, int64_t n, int
 }
 
 template <typename T>
-bool pcg_implicit_window_fits(int wmax, int k, int mp, int G, int64_t n, int gamma) {
+bool pcg_implicit_window_fits(int wmax, int maxrow, int k, int mp, int G, int64_t n, int gamma,
+                              int* ellw) {
   int dev = 0, optin = 0;
+  *ellw = 0;
   if (wmax < 1 || G < 1 || gamma < 1 || gamma > 8 || k > 65535 || (size_t)(k + 1) * 4 > 48 * 1024)
     return false;
   if (cdiv(n, G) > 32768) return false;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return false;
-  const WinSmem L = win_smem(k, mp, (int)sizeof(T), wmax, G, (int)cdiv(n, G), gamma);
+  const int rpc = (int)cdiv(n, G);
+  // the rows as ELL in shared memory when they fit, else read as CSR
+  if (wmax <= 65535 && maxrow >= 1 &&
+      win_smem(k, mp, (int)sizeof(T), wmax, G, rpc, gamma, maxrow).total + 8192 <= (size_t)optin)
+    *ellw = maxrow;
+  const WinSmem L = win_smem(k, mp, (int)sizeof(T), wmax, G, rpc, gamma, *ellw);
   if (L.total + 8192 > (size_t)optin) return false;
   switch (mp) {
-    case 1: return imp_attr<T, 1, true>();
-    case 2: return imp_attr<T, 2, true>();
-    case 4: return imp_attr<T, 4, true>();
-    default: return imp_attr<T, 8, true>();
+    case 1: return imp_win_attr<T, 1, 1>();
+    case 2: return imp_win_attr<T, 2, 1>() && imp_win_attr<T, 2, 2>();
+    case 4: return imp_win_attr<T, 4, 2>() && imp_win_attr<T, 4, 4>();
+    default: return imp_win_attr<T, 8, 4>() && imp_win_attr<T, 8, 8>();
   }
 }
 
 template <typename T>
 cudaError_t pcg_implicit(const OpDev& op, double mu, const int32_t* om_cols, const int8_t* om_sgn,
                          int gamma, const double* Hb, T* E, T* R, T* P, T* W, T* Z, T* U, T* R1,
-                         T* P1, int wmax, const uint16_t* lst_ent, const int32_t* lst_off, int k,
-                         int mp, int G, int iters, double* scratch, ColState* cs, GridBar* bar,
-                         int* err, cudaStream_t st) {
+                         T* P1, int wmax, int ellw, const uint16_t* lst_ent,
+                         const int32_t* lst_off, int k, int mp, int m, int G, int iters,
+                         double* scratch, ColState* cs, GridBar* bar, int* err, cudaStream_t st) {
   ImpArgs<T> a;
   a.rowptr = op.rowptr;
   a.colidx = op.colidx;
@@ -1217,6 +1375,7 @@ cudaError_t pcg_implicit(const OpDev& op, double mu, const int32_t* om_cols, con
   a.wmax = (R1 && P1 && lst_ent && lst_off) ? wmax : 0;
   a.lst_ent = lst_ent;
   a.lst_off = lst_off;
+  a.ellw = a.wmax > 0 ? ellw : 0;
   a.n = op.n;
   a.k = k;
   a.rpc = (int)cdiv(op.n, G);
@@ -1226,6 +1385,15 @@ cudaError_t pcg_implicit(const OpDev& op, double mu, const int32_t* om_cols, con
   a.cs = cs;
   a.bar = bar;
   a.err = err;
+  if (a.wmax > 0) {
+    // columns computed: the smallest instantiated count >= m
+    switch (mp) {
+      case 1: return launch_imp_win<T, 1, 1>(a, G, st);
+      case 2: return m <= 1 ? launch_imp_win<T, 2, 1>(a, G, st) : launch_imp_win<T, 2, 2>(a, G, st);
+      case 4: return m <= 2 ? launch_imp_win<T, 4, 2>(a, G, st) : launch_imp_win<T, 4, 4>(a, G, st);
+      default: return m <= 4 ? launch_imp_win<T, 8, 4>(a, G, st) : launch_imp_win<T, 8, 8>(a, G, st);
+    }
+  }
   switch (mp) {
     case 1: return launch_imp<T, 1>(a, G, st);
     case 2: return launch_imp<T, 2>(a, G, st);
@@ -1236,17 +1404,17 @@ cudaError_t pcg_implicit(const OpDev& op, double mu, const int32_t* om_cols, con
 
 template int pcg_implicit_ctas<float>(int64_t, int, int);
 template int pcg_implicit_ctas<double>(int64_t, int, int);
-template bool pcg_implicit_window_fits<float>(int, int, int, int, int64_t, int);
-template bool pcg_implicit_window_fits<double>(int, int, int, int, int64_t, int);
+template bool pcg_implicit_window_fits<float>(int, int, int, int, int, int64_t, int, int*);
+template bool pcg_implicit_window_fits<double>(int, int, int, int, int, int64_t, int, int*);
 template cudaError_t pcg_implicit<float>(const OpDev&, double, const int32_t*, const int8_t*, int,
                                          const double*, float*, float*, float*, float*, float*,
-                                         float*, float*, float*, int, const uint16_t*,
-                                         const int32_t*, int, int, int, int, double*, ColState*,
-                                         GridBar*, int*, cudaStream_t);
+                                         float*, float*, float*, int, int, const uint16_t*,
+                                         const int32_t*, int, int, int, int, int, double*,
+                                         ColState*, GridBar*, int*, cudaStream_t);
 template cudaError_t pcg_implicit<double>(const OpDev&, double, const int32_t*, const int8_t*, int,
                                           const double*, double*, double*, double*, double*,
-                                          double*, double*, double*, double*, int, const uint16_t*,
-                                          const int32_t*, int, int, int, int, double*, ColState*,
-                                          GridBar*, int*, cudaStream_t);
+                                          double*, double*, double*, double*, int, int,
+                                          const uint16_t*, const int32_t*, int, int, int, int, int,
+                                          double*, ColState*, GridBar*, int*, cudaStream_t);
 
 }  // namespace rr

@@ -290,6 +290,8 @@ struct rr_handle {
   GridBar* bar;
   double* fscratch;
   int imp_wmax;             // rows of the largest window of the basis-less step's window form
+  int imp_ellw;             // its ELL width (rows in shared memory), 0: CSR from global memory
+  int m_solve;              // right-hand sides of the running solve (the others stay inactive)
   uint16_t* omt_ent;        // its Omega^T lists (n x gamma) and their offsets (G x (k + 1))
   int32_t* omt_off;
   bool graph_failed;  // capture not possible: direct launches
@@ -1350,15 +1352,18 @@ rr_status finish_build(rr_handle* h, const double* G1given) {
     // the shared-memory window form when every CTA's window fits (the rows
     // a banded operator's rows read stay near them)
     h->imp_wmax = 0;
+    h->imp_ellw = 0;
     if (h->fusedG > 0 && h->o.iter_impl == 0 && h->omt_ent) {
-      int wmax = 0;
-      RR_CUDA_TRY(cudaMemsetAsync(h->dstatus + 5, 0, sizeof(int), st));
+      int wmax = 0, maxrow = 0, ellw = 0;
+      RR_CUDA_TRY(cudaMemsetAsync(h->dstatus + 5, 0, 2 * sizeof(int), st));
       RR_CUDA_TRY(pcg_implicit_window(h->op, h->fusedG, h->dstatus + 5, st));
       RR_TRY(read_int(h, h->dstatus + 5, &wmax));
-      if (pcg_implicit_window_fits<T>(wmax, k, h->mp, h->fusedG, n, h->o.gamma)) {
+      RR_TRY(read_int(h, h->dstatus + 6, &maxrow));
+      if (pcg_implicit_window_fits<T>(wmax, maxrow, k, h->mp, h->fusedG, n, h->o.gamma, &ellw)) {
         RR_CUDA_TRY(omega_t_lists(h->ss_cols, h->ss_sgn, n, h->fusedG, h->o.gamma, k, h->omt_ent,
                                   h->omt_off, st));
         h->imp_wmax = wmax;
+        h->imp_ellw = ellw;
       }
     }
   } else if (h->o.variant == RR_VARIANT_C || h->o.variant == RR_VARIANT_G) {
@@ -1598,7 +1603,8 @@ rr_status run_chunk(rr_handle* h) {
     RR_CUDA_TRY(pcg_implicit<T>(h->op, h->mu, h->ss_cols, h->ss_sgn, h->o.gamma, h->kk[kHb],
                                 vt<T>(h, kE), vt<T>(h, kR), vt<T>(h, kP), vt<T>(h, kW),
                                 vt<T>(h, kZ), vt<T>(h, kU), vt<T>(h, kV), vt<T>(h, kS),
-                                h->imp_wmax, h->omt_ent, h->omt_off, h->k, h->mp, h->fusedG,
+                                h->imp_wmax, h->imp_ellw, h->omt_ent, h->omt_off, h->k, h->mp,
+                                h->m_solve, h->fusedG,
                                 kImplicitChunk, h->fscratch, h->cs, h->bar, h->dstatus + 3, h->st));
     if (ev) RR_CUDA_TRY(cudaEventRecord(ev[1], h->st));
     return RR_OK;
@@ -1687,6 +1693,7 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
   double* B = h->v64[kB64];
   double* X = h->v64[kX64];
   double* R64 = h->v64[kR64];
+  h->m_solve = m;
   double bn2[8] = {0}, rn2[8] = {0};
   // the product's pair counters are zero between launches; a launch that gave
   // up on a wait (error flag) may have left some set
@@ -2827,6 +2834,7 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
   h->st = (cudaStream_t)stream;
   h->f64 = uses_f64(o);
   h->mp = pad_mp(o.max_rhs);
+  h->m_solve = h->mp;
   h->n = A->n;
   h->L = L;
   h->ws = (unsigned char*)workspace;

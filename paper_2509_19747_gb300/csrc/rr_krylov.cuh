@@ -170,24 +170,28 @@ size_t pcg_implicit_scratch_doubles(int k, int mp);
 template <typename T>
 int pcg_implicit_ctas(int64_t n, int k, int mp);
 // The largest row window over the G CTAs (own rows and the rows their CSR
-// rows read), atomically maxed into *wmax (cleared by the caller).
+// rows read) and the longest row, atomically maxed into wmax[0] and wmax[1]
+// (cleared by the caller).
 cudaError_t pcg_implicit_window(const OpDev& op, int G, int* wmax, cudaStream_t st);
 // Whether the window form applies (gamma <= 8, k <= 65535, at most 32768
-// rows per CTA) and its shared memory fits with windows of wmax rows.
+// rows per CTA) and its shared memory fits with windows of wmax rows; *ellw
+// = maxrow when the CTA's rows also fit there as ELL, else 0.
 template <typename T>
-bool pcg_implicit_window_fits(int wmax, int k, int mp, int G, int64_t n, int gamma);
+bool pcg_implicit_window_fits(int wmax, int maxrow, int k, int mp, int G, int64_t n, int gamma,
+                              int* ellw);
 // The window form's Omega^T lists of each CTA's rows (ent: n x gamma
 // entries, off: G x (k + 1)); deterministic.
 cudaError_t omega_t_lists(const int32_t* cols, const int8_t* sgn, int64_t n, int G, int gamma,
                           int k, uint16_t* ent, int32_t* off, cudaStream_t st);
 // wmax > 0 with R1, P1 (n x mp each, free during the launch) and the lists:
-// the window form (four grid barriers per iteration); wmax = 0: seven
+// the window form (four grid barriers per iteration), computing the first
+// m columns rounded up (columns >= m must be inactive); wmax = 0: seven
 // barriers, U as scratch.
 template <typename T>
 cudaError_t pcg_implicit(const OpDev& op, double mu, const int32_t* om_cols, const int8_t* om_sgn,
                          int gamma, const double* Hb, T* E, T* R, T* P, T* W, T* Z, T* U, T* R1,
-                         T* P1, int wmax, const uint16_t* lst_ent, const int32_t* lst_off, int k,
-                         int mp, int G, int iters, double* scratch, ColState* cs, GridBar* bar,
-                         int* err, cudaStream_t st);
+                         T* P1, int wmax, int ellw, const uint16_t* lst_ent,
+                         const int32_t* lst_off, int k, int mp, int m, int G, int iters,
+                         double* scratch, ColState* cs, GridBar* bar, int* err, cudaStream_t st);
 
 }  // namespace rr

@@ -275,3 +275,24 @@ def test_persistent_forms_wide_and_banded_windows(cuda_lib, precision):
     vals = dev(G.vals) if precision == "fp64" else dev(G.vals.astype(np.float32))
     opg = O.CsrOp(G.rowptr, G.colidx, G.vals, G.n)
     _persistent_forms_agree(rr, G, opg, vals, 1e-4, 40, W.gaussian_rhs(G.n, 3, 48), 48, precision)
+
+
+@pytest.mark.parametrize("max_rhs,m", [(4, 2), (8, 3), (2, 1)])
+def test_window_form_fewer_columns_than_handle(cuda_lib, max_rhs, m):
+    """The window form computes only the solve's columns (rounded up) of a
+    handle built for more: float64 iterates at a fixed budget equal the
+    separate kernels', and a second solve with all columns still agrees."""
+    rr = cuda_lib
+    C, op, vals = csr_problem(48, 49)
+    mu, k = 1e-5, 36
+    B = W.gaussian_rhs(C.n, max_rhs, 49)
+    out = {}
+    for impl in (0, 1):
+        h = csr_handle(rr, C, vals, mu, k, "sparse_sign", 49, max_rhs=max_rhs, iter_impl=impl)
+        x, status, _ = h.solve(dev(B[:, :m]), rtol=1e-14, maxit=31)
+        assert status == rr.RR_ERR_MAXIT
+        xa, status, _ = h.solve(dev(B), rtol=1e-14, maxit=17)
+        out[impl] = (x.cpu().numpy(), xa.cpu().numpy())
+        h.close()
+    assert rel(out[0][0], out[1][0]) <= 1e-10
+    assert rel(out[0][1], out[1][1]) <= 1e-10
