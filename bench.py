@@ -49,9 +49,9 @@ WORKLOAD = dict(workload="gaussian_kernel_ridge", n=20000, d=8, components=10, m
 METRIC = "RandRAND-PCG solves/s to rtol 1e-6 vs plain form on 1 GB300; p50/p99 latency"
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands (summaries in profiles/: k_kernel_mv_tc_kernel_ridge_n20000.md,
-# k_pcg_implicit_sparse_diffusion_512.md, the latter per iteration of a
+# k_pcg_implicit_win_sparse_diffusion_512.md, the latter per iteration of a
 # 256-iteration launch)
-TRAFFIC = {"k_kernel_mv_tc": 5.542656e6, "k_pcg_implicit": (28.929024e6 + 1.674240e6) / 256}
+TRAFFIC = {"k_kernel_mv_tc": 5.544704e6, "k_pcg_implicit_win": (41.677312e6 + 1.663744e6) / 256}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -624,18 +624,20 @@ def run_sparse(args):
     mv = [p["matvec"] for p, _ in prof]
     cnt, tot = sum(c for c, _ in mv), sum(t for _, t in mv)
     iters_total = sum(i["inner_iters"] for i in infos)
-    mp = 2    # one right-hand side, padded to two columns
+    mp = 1    # one right-hand side (stored padded to two columns; the step computes one)
     peaks = _peaks()
     if cnt < iters_total / 2:
         # persistent launches: the event pair spans whole runs of iterations.
         # Algorithmic bytes of one basis-less iteration: three products with
         # A_mu (values + indices, row pointers, one vector read, one written),
-        # Omega and Omega^T as patterns, ~10 vector streams.
+        # Omega and Omega^T as patterns, ~10 vector streams (the window form
+        # keeps the matrix and the patterns in shared memory across iterations,
+        # so this is what an unfused iteration would move, not its traffic).
         per_s = tot / 1000.0 / max(iters_total, 1)
         bytes_ = 3 * (8.0 * len(C.vals) + 4.0 * (C.n + 1) + 2 * 4.0 * C.n * mp) \
             + 2 * 5.0 * cfg["gamma"] * C.n + 10 * 4.0 * C.n * mp
-        kern, unit_note = "k_pcg_implicit (per iteration)", "iterations"
-        traffic = TRAFFIC["k_pcg_implicit"]
+        kern, unit_note = "k_pcg_implicit_win (per iteration)", "iterations"
+        traffic = TRAFFIC["k_pcg_implicit_win"]
     else:
         per_s = tot / 1000.0 / max(cnt, 1)
         bytes_ = 8.0 * len(C.vals) + 4.0 * (C.n + 1) + 2 * 4.0 * C.n * mp
