@@ -479,7 +479,7 @@ def roofline(name, stat, clocks):
     flops = 2.0 * n * n * WORKLOAD["k"]
     peak_tf = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
-    return {"kernel": "k_kernel_sketch_tc", "bound": "tensor", "achieved": flops / avg_s / 1e12,
+    return {"kernel": "k_kernel_sketch_sk", "bound": "tensor", "achieved": flops / avg_s / 1e12,
             "peak": peak_tf, "unit": "TFLOP/s", "frac": flops / avg_s / 1e12 / peak_tf,
             "traffic": None, "launches": cnt, "avg_us": avg_s * 1e6}
 

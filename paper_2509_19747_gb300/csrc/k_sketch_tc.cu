@@ -19,6 +19,7 @@
 // unwinds (RR_ERR_TIMEOUT on the host) instead of hanging.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "rr_common.cuh"
@@ -269,6 +270,342 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ------------------------------------------------------------------------
+// Persistent stream-K form: one CTA covers all sketch columns (k <= 512, two
+// 256-column accumulators = all 512 TMEM columns) of its row blocks, so each
+// 128 x 64 block of K is generated once.  The (row block, 64-point step) work
+// items, row block major, are cut into one contiguous range per CTA (grid =
+// min(SMs, row blocks), so a row block is shared by at most two CTAs).  A
+// segment (the part of a range in one row block) that covers the whole row
+// block writes Y = acc + mu Omega; of a shared row block, the first segment
+// writes its sum into Y and the second into `part` (same layout), and the
+// later of the two to finish (an arrival count per row block, cleared before
+// the launch) forms Y = Y + part + mu Omega.  Omega^T tiles (two 256-column
+// halves per step when k > 256) arrive by TMA through a 3-stage ring, the
+// generated K blocks through a 2-stage ring; the
+// generator warps read their step's 8 points once per warp (3 loads per lane)
+// and pass them between lanes by shuffles.
+constexpr int kSkStagesB = 3, kSkStagesA = 2;    // Omega^T tiles (NB halves each); generated K blocks
+constexpr int kSkHalf = kBN * kBK * 2;           // one 256-column half of an Omega^T tile (32 KB)
+
+struct __align__(16) SkSmem {
+  unsigned long long full_b[kSkStagesB], empty_b[kSkStagesB];
+  unsigned long long full_a[kSkStagesA], empty_a[kSkStagesA];
+  unsigned long long seg_done, tmem_free, written, decided;
+  uint32_t tmem_base;
+  int abort;
+  int last;
+};
+
+template <int NB>
+constexpr size_t sk_smem_bytes() {
+  return 1024 + (size_t)kSkStagesB * NB * kSkHalf + (size_t)kSkStagesA * kABytes + sizeof(SkSmem);
+}
+
+// the segments of CTA c's range, in order: row block, first step, steps
+struct SkRange {
+  int64_t x0, x1;
+};
+__device__ __forceinline__ SkRange sk_range(int64_t total, int64_t g, int64_t c) {
+  return SkRange{c * total / g, (c + 1) * total / g};
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_kernel_sketch_sk(const __grid_constant__ CUtensorMap omt_map, const float* __restrict__ xs,
+                       const float* __restrict__ cn, int64_t n, int k, double mu,
+                       const float* __restrict__ Om, float* __restrict__ Y,
+                       float* __restrict__ part, int* __restrict__ cnt, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sB = base;                                           // 3 x NB x 32 KB
+  unsigned char* sA = sB + (size_t)kSkStagesB * NB * kSkHalf;         // 2 x 16 KB
+  SkSmem* sm = (SkSmem*)(sA + (size_t)kSkStagesA * kABytes);
+  volatile int* abort = &sm->abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nsteps = (n + kBK - 1) / kBK;
+  const int64_t nrb = (n + kBM - 1) / kBM;
+  const int64_t total = nrb * nsteps;
+  const SkRange rg = sk_range(total, gridDim.x, blockIdx.x);
+  constexpr uint32_t idesc = make_idesc(kFmtBF16, kBM, kBN);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSkStagesB; ++s) {
+      mbar_init(&sm->full_b[s], 1);
+      mbar_init(&sm->empty_b[s], 1);
+    }
+    for (int s = 0; s < kSkStagesA; ++s) {
+      mbar_init(&sm->full_a[s], kGenWarps * 32);
+      mbar_init(&sm->empty_a[s], 1);
+    }
+    mbar_init(&sm->seg_done, 1);
+    mbar_init(&sm->tmem_free, kGenWarps);
+    mbar_init(&sm->written, kGenWarps);
+    mbar_init(&sm->decided, 1);
+    sm->abort = 0;
+    sm->last = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(&sm->tmem_base, 512);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = sm->tmem_base;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA
+    if (lane == 0) {
+      int64_t T = 0;
+      bool ok = true;
+      for (int64_t x = rg.x0; x < rg.x1 && ok; ++x, ++T) {
+        const int s = (int)(T % kSkStagesB);
+        const int64_t st = x % nsteps;
+        if (T >= kSkStagesB && !mbar_wait(&sm->empty_b[s], (uint32_t)((T / kSkStagesB) - 1) & 1u, err, abort)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_tx(&sm->full_b[s], (uint32_t)(NB * kSkHalf));
+        for (int h = 0; h < NB; ++h)
+          tma_load_2d(sB + ((size_t)s * NB + h) * kSkHalf, &omt_map, (int)(st * kBK), h * kBN,
+                      &sm->full_b[s]);
+      }
+      // never leave a copy in flight into shared memory that is about to be released
+      for (int64_t t = (T > kSkStagesB ? T - kSkStagesB : 0); t < T; ++t)
+        mbar_wait(&sm->full_b[t % kSkStagesB], (uint32_t)(t / kSkStagesB) & 1u, err, abort);
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA
+    if (lane == 0) {
+      bool ok = true;
+      int64_t T = 0;
+      int segi = 0;
+      for (int64_t x = rg.x0; x < rg.x1 && ok;) {
+        const int64_t rb = x / nsteps;
+        const int64_t xe = min(rg.x1, (rb + 1) * nsteps);
+        if (segi > 0 && !mbar_wait(&sm->tmem_free, (uint32_t)(segi - 1) & 1u, err, abort)) break;
+        fence_after();
+        for (int64_t t = x; t < xe && ok; ++t, ++T) {
+          const int sa = (int)(T % kSkStagesA), sb = (int)(T % kSkStagesB);
+          ok = mbar_wait(&sm->full_a[sa], (uint32_t)(T / kSkStagesA) & 1u, err, abort) &&
+               mbar_wait(&sm->full_b[sb], (uint32_t)(T / kSkStagesB) & 1u, err, abort);
+          if (!ok) break;
+          fence_after();
+          const uint32_t a0 = smem_u32(sA + (size_t)sa * kABytes);
+          uint32_t b0[NB];
+#pragma unroll
+          for (int h = 0; h < NB; ++h) b0[h] = smem_u32(sB + ((size_t)sb * NB + h) * kSkHalf);
+          // the two accumulators alternate, so consecutive MMAs do not wait on
+          // each other's accumulation
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk)
+#pragma unroll
+            for (int h = 0; h < NB; ++h)
+              mma_f16(tmem + (uint32_t)(h * kBN), umma_desc_sw128(a0 + kk * 32),
+                      umma_desc_sw128(b0[h] + kk * 32), idesc, (t > x || kk > 0) ? 1u : 0u);
+          mma_commit(&sm->empty_b[sb]);
+          mma_commit(&sm->empty_a[sa]);
+        }
+        if (!ok) break;
+        mma_commit(&sm->seg_done);
+        ++segi;
+        x = xe;
+      }
+    }
+  } else {
+    // ------------------------------------------------- generators / epilogue
+    // thread g owns rows rg + 32 rr (rr < 4) and the 8 points 8 cg .. 8 cg + 7
+    // of each step (one warp per cg); 4 x 8 register tile of K per step,
+    // stored as one 16-byte chunk per row into the 128-byte-swizzled K-major
+    // layout (row r, chunk c at c ^ (r & 7))
+    const int g = threadIdx.x - 64;        // 0 .. 255
+    const int rgl = g & 31;
+    const int cg = g >> 5;
+    const int quarter = warp & 3;                 // TMEM lanes this warp may read
+    const int colhalf = (warp - 2) >> 2;          // columns NB*128*colhalf ...
+    bool ok = true;
+    int64_t TA = 0;
+    int segi = 0, shi = 0;
+    const float muf = (float)mu;
+    for (int64_t x = rg.x0; x < rg.x1 && ok;) {
+      const int64_t rb = x / nsteps;
+      const int64_t xb = rb * nsteps, xe = min(rg.x1, (rb + 1) * nsteps);
+      const bool first = x == xb, lastseg = xe == (rb + 1) * nsteps;
+      const int64_t i0 = rb * kBM;
+      float xi[4][8], ci[4];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const int64_t gi = i0 + rgl + 32 * rr;
+        if (gi < n) {
+#pragma unroll
+          for (int d = 0; d < 8; ++d) xi[rr][d] = xs[gi * 8 + d];
+          ci[rr] = cn[gi];
+        } else {
+#pragma unroll
+          for (int d = 0; d < 8; ++d) xi[rr][d] = 0.f;
+          ci[rr] = -1e30f;
+        }
+      }
+      // this warp's points of the first step (xs, cn are padded to a multiple
+      // of 64 points)
+      float pa, pb, pc;
+      {
+        const int64_t j0 = (x - xb) * kBK + 8 * cg;
+        pa = xs[j0 * 8 + lane];
+        pb = xs[j0 * 8 + 32 + lane];
+        pc = lane < 8 ? cn[j0 + lane] : 0.f;
+      }
+      for (int64_t t = x; t < xe; ++t, ++TA) {
+        const int sa = (int)(TA % kSkStagesA);
+        const float ca = pa, cb2 = pb, cc = pc;
+        if (t + 1 < xe) {                           // the next step's points, in flight meanwhile
+          const int64_t j0 = (t + 1 - xb) * kBK + 8 * cg;
+          pa = xs[j0 * 8 + lane];
+          pb = xs[j0 * 8 + 32 + lane];
+          pc = lane < 8 ? cn[j0 + lane] : 0.f;
+        }
+        float xj[8][8], cj[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+#pragma unroll
+          for (int d = 0; d < 8; ++d) {
+            const int f = p * 8 + d;
+            xj[p][d] = __shfl_sync(0xffffffffu, f < 32 ? ca : cb2, f & 31);
+          }
+          cj[p] = __shfl_sync(0xffffffffu, cc, p);
+        }
+        if (TA >= kSkStagesA && !mbar_wait(&sm->empty_a[sa], (uint32_t)((TA / kSkStagesA) - 1) & 1u, err, abort)) {
+          ok = false;
+          break;
+        }
+        unsigned char* stage = sA + (size_t)sa * kABytes;
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          uint32_t packed[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float v2[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int p = 2 * q + u;
+              float a = ci[rr] + cj[p];
+#pragma unroll
+              for (int d = 0; d < 8; ++d) a = fmaf(xi[rr][d], xj[p][d], a);
+              v2[u] = ex2_approx(a);
+            }
+            packed[q] = pack_bf16x2(v2[0], v2[1]);
+          }
+          const int r = rgl + 32 * rr;
+          const int phys = cg ^ (r & 7);
+          uint4 v;
+          v.x = packed[0];
+          v.y = packed[1];
+          v.z = packed[2];
+          v.w = packed[3];
+          *reinterpret_cast<uint4*>(stage + (size_t)r * 128 + phys * 16) = v;
+        }
+        fence_proxy_async();
+        mbar_arrive(&sm->full_a[sa]);
+      }
+      // ------------------------------------------------------- epilogue
+      ok = __all_sync(0xffffffffu, ok);
+      if (ok) ok = mbar_wait(&sm->seg_done, (uint32_t)segi & 1u, err, abort);
+      ok = __all_sync(0xffffffffu, ok);            // tcgen05.ld is warp-collective
+      if (!ok) break;
+      fence_after();
+      const int row = quarter * 32 + lane;
+      const int64_t yi = i0 + row;
+      const bool whole = first && lastseg;
+      float* dst = (whole || first) ? Y : part;     // a shared block's second part goes to `part`
+      for (int chunk = 0; chunk < NB * 4; ++chunk) {
+        const int col0 = colhalf * (NB * 128) + chunk * 32;
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
+        if (yi < n) {
+#pragma unroll
+          for (int q4 = 0; q4 < 8; ++q4) {
+            const int c = col0 + 4 * q4;
+            if (c >= k) break;
+            if ((k & 3) == 0) {
+              float4 y;
+              y.x = __uint_as_float(v[4 * q4 + 0]);
+              y.y = __uint_as_float(v[4 * q4 + 1]);
+              y.z = __uint_as_float(v[4 * q4 + 2]);
+              y.w = __uint_as_float(v[4 * q4 + 3]);
+              if (whole) {
+                const float4 o = *reinterpret_cast<const float4*>(Om + yi * k + c);
+                y.x += muf * o.x;
+                y.y += muf * o.y;
+                y.z += muf * o.z;
+                y.w += muf * o.w;
+              }
+              *reinterpret_cast<float4*>(dst + yi * k + c) = y;
+            } else {
+              for (int e = 0; e < 4 && c + e < k; ++e) {
+                float yv = __uint_as_float(v[4 * q4 + e]);
+                if (whole) yv += muf * Om[yi * k + c + e];
+                dst[yi * k + c + e] = yv;
+              }
+            }
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm->tmem_free);   // the MMAs of the next segment may start
+      if (!whole) {
+        // the later of the two parts of this row block forms Y
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence();
+          mbar_arrive(&sm->written);
+        }
+        if (warp == 2 && lane == 0) {
+          bool w = mbar_wait(&sm->written, (uint32_t)shi & 1u, err, abort);
+          sm->last = (w && atomicAdd(cnt + rb, 1) == 1) ? 1 : 0;
+          __threadfence();
+          mbar_arrive(&sm->decided);
+        }
+        ok = mbar_wait(&sm->decided, (uint32_t)shi & 1u, err, abort);
+        ok = __all_sync(0xffffffffu, ok);
+        ++shi;
+        if (!ok) break;
+        if (*(volatile int*)&sm->last && yi < n) {
+          __threadfence();
+          const int cb = colhalf * (NB * 128), ce = min(k, cb + NB * 128);
+          if ((k & 3) == 0) {
+            for (int c = cb; c < ce; c += 4) {
+              const int64_t e = yi * k + c;
+              const float4 a = __ldcg(reinterpret_cast<const float4*>(Y + e));
+              const float4 b = __ldcg(reinterpret_cast<const float4*>(part + e));
+              const float4 o = *reinterpret_cast<const float4*>(Om + e);
+              float4 y;
+              y.x = a.x + b.x + muf * o.x;
+              y.y = a.y + b.y + muf * o.y;
+              y.z = a.z + b.z + muf * o.z;
+              y.w = a.w + b.w + muf * o.w;
+              *reinterpret_cast<float4*>(Y + e) = y;
+            }
+          } else {
+            for (int c = cb; c < ce; ++c) {
+              const int64_t e = yi * k + c;
+              Y[e] = __ldcg(Y + e) + __ldcg(part + e) + muf * Om[e];
+            }
+          }
+        }
+      }
+      ++segi;
+      x = xe;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -301,7 +638,8 @@ size_t sketch_tc_smem_bytes() { return kSmemBytes; }
 // if the tensor map cannot be encoded (the caller then uses the float32
 // sketch).
 rr_status sketch_kernel_tc(const OpDev& op, double mu, const __nv_bfloat16* omt, int64_t ldo,
-                           const float* Om, float* Y, int k, int* err, cudaStream_t st) {
+                           const float* Om, float* Y, int k, float* part, int* cnt, int* err,
+                           cudaStream_t st) {
   if (op.dim != 8 || (ldo % 8) != 0) return RR_ERR_UNSUPPORTED;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return RR_ERR_UNSUPPORTED;
@@ -314,6 +652,39 @@ rr_status sketch_kernel_tc(const OpDev& op, double mu, const __nv_bfloat16* omt,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return RR_ERR_UNSUPPORTED;
+  // stream-K form: every sketch column in one CTA (k <= 512), the second
+  // part of a shared row block in `part` (n x k), arrival counts in `cnt`
+  int dev = 0, sms = 0, optin = 0;
+  if (part && cnt && k <= 2 * kBN && cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess) {
+    const int64_t nrb = cdiv(op.n, kBM);
+    const int grid = (int)std::min<int64_t>(sms, nrb);
+    const bool two = k > kBN;
+    const size_t smem = two ? sk_smem_bytes<2>() : sk_smem_bytes<1>();
+    if (smem <= (size_t)optin) {
+      static std::atomic<uint64_t> attr1{0}, attr2{0};
+      const bool ok = two ? once_per_device(attr2, [] {
+                              return cudaFuncSetAttribute(k_kernel_sketch_sk<2>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)sk_smem_bytes<2>()) == cudaSuccess;
+                            })
+                          : once_per_device(attr1, [] {
+                              return cudaFuncSetAttribute(k_kernel_sketch_sk<1>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)sk_smem_bytes<1>()) == cudaSuccess;
+                            });
+      if (!ok) return RR_ERR_CUDA;
+      if (cudaMemsetAsync(cnt, 0, (size_t)nrb * sizeof(int), st) != cudaSuccess) return RR_ERR_CUDA;
+      if (two)
+        k_kernel_sketch_sk<2><<<grid, kThreads, smem, st>>>(map, op.xs, op.cn, op.n, k, mu, Om, Y,
+                                                             part, cnt, err);
+      else
+        k_kernel_sketch_sk<1><<<grid, kThreads, smem, st>>>(map, op.xs, op.cn, op.n, k, mu, Om, Y,
+                                                             part, cnt, err);
+      return cudaGetLastError() == cudaSuccess ? RR_OK : RR_ERR_CUDA;
+    }
+  }
   static std::atomic<uint64_t> attr{0};
   if (!once_per_device(attr, [] {
         return cudaFuncSetAttribute(k_kernel_sketch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,

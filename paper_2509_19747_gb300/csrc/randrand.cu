@@ -33,7 +33,7 @@ constexpr int kMaxRestarts = 400;
 enum Region {
   R_OM, R_OMB, R_SSC, R_SSS, R_THC, R_THS, R_SK, R_Y, R_Q, R_Y0, R_KK, R_KKT, R_GPART, R_CHOLW,
   R_STATUS, R_XS, R_CN, R_PN, R_AUG, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT,
-  R_CS, R_NORMS, R_FUSED, R_ML, R_FWHT, R_PCNT, R_OMT, R_NREG
+  R_CS, R_NORMS, R_FUSED, R_ML, R_FWHT, R_PCNT, R_OMT, R_SKP, R_NREG
 };
 
 struct Layout {
@@ -118,6 +118,11 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_AUG] = (A.kind == RR_OP_GAUSS_KERNEL && A.dim == 8 && !uses_f64(o))
                       ? 2 * npad_tc * kAugFloats * 4 + mv_tc2_vsplit_elems(A.n) * 2 : 0;
   L.size[R_MVS] = op_matvec_scratch_elems(od, mp) * 8;
+  // stream-K tensor-core sketch: second parts of shared row blocks (n x k)
+  // and arrival counts per 128-row block
+  L.size[R_SKP] = (A.kind == RR_OP_GAUSS_KERNEL && A.dim == 8 && !uses_f64(o) && kk <= 512)
+                      ? align256(n * kk * 4) + (size_t)cdiv(A.n, 128) * 4
+                      : 0;
   // Omega^T lists of the basis-less persistent step's window form
   L.size[R_OMT] = (basis_less(A, o) && o.variant == RR_VARIANT_C && o.gamma >= 1 && o.gamma <= 8)
                       ? align256(n * (size_t)o.gamma * 2) + (size_t)kFusedMaxCtas * (kk + 1) * 4
@@ -292,6 +297,8 @@ struct rr_handle {
   int imp_wmax;             // rows of the largest window of the basis-less step's window form
   int imp_ellw;             // its ELL width (rows in shared memory), 0: CSR from global memory
   int m_solve;              // right-hand sides of the running solve (the others stay inactive)
+  float* skp;               // stream-K sketch: second parts of shared row blocks (n x k)
+  int* skp_cnt;             // and their arrival counts
   uint16_t* omt_ent;        // its Omega^T lists (n x gamma) and their offsets (G x (k + 1))
   int32_t* omt_off;
   bool graph_failed;  // capture not possible: direct launches
@@ -419,6 +426,9 @@ void carve(rr_handle* h) {
   h->cnt = (unsigned*)at(R_CNT);
   h->cs = (ColState*)at(R_CS);
   h->norms = (double*)at(R_NORMS);
+  unsigned char* skp = (unsigned char*)at(R_SKP);
+  h->skp = (float*)skp;
+  h->skp_cnt = skp ? (int*)(skp + align256((size_t)h->n * h->k * 4)) : nullptr;
   unsigned char* omt = (unsigned char*)at(R_OMT);
   h->omt_ent = (uint16_t*)omt;
   h->omt_off = omt ? (int32_t*)(omt + align256((size_t)h->n * h->o.gamma * 2)) : nullptr;
@@ -1196,7 +1206,7 @@ rr_status sketch_product(rr_handle* h, double shift, bool tc, int64_t ldo) {
     const cudaEvent_t* ev = ev_take(h, RR_PROF_SKETCH);
     if (ev) cudaEventRecord(ev[0], st);
     const rr_status s = sketch_kernel_tc(h->op, shift, h->Omb, ldo, (const float*)h->Om,
-                                         (float*)h->Y, k, h->dstatus + 1, st);
+                                         (float*)h->Y, k, h->skp, h->skp_cnt, h->dstatus + 1, st);
     if (ev) cudaEventRecord(ev[1], st);
     if (s == RR_OK) {
       int err = 0;

@@ -308,8 +308,11 @@ bool kernel_mv_tc2(const void* amap, const void* bmap64, const void* vmap, int64
 
 // k_sketch_tc.cu -- tensor-core sketch of the Gaussian-kernel operator
 size_t sketch_tc_smem_bytes();
+// part (n x k) and cnt (ceil(n / 128) ints) enable the stream-K form (k <= 512);
+// nullptr: one CTA per (128 rows, 256 columns) tile
 rr_status sketch_kernel_tc(const OpDev& op, double mu, const __nv_bfloat16* omt, int64_t ldo,
-                           const float* Om, float* Y, int k, int* err, cudaStream_t st);
+                           const float* Om, float* Y, int k, float* part, int* cnt, int* err,
+                           cudaStream_t st);
 
 // k_sparse.cu -- sparse-sign Omega / Theta applications (basis-less Q)
 template <typename T>
