@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "df.cuh"
 #include "rr_common.cuh"
 #include "rr_krylov.cuh"
 
@@ -1199,6 +1200,42 @@ __device__ void tail_qtr(const T* __restrict__ Q, const T* __restrict__ R, int64
   }
 }
 
+// Column sums of the fused step's float32 dot products in double-float
+// (df.cuh: TwoProd, TwoSum), so that no per-element or per-thread float64
+// arithmetic runs (GB300 executes float64 at about 2 operations per clock per
+// SM).  tail_dot_add: acc += a b.  tail_cols_store: thread partials of column
+// (threadIdx.x % MP) reduced over the lanes of that column, the warp sums in
+// shared memory; tail_cols_add: the kFT / 32 warp sums of column c by warp c,
+// one float64 atomic add per column.
+__device__ __forceinline__ void tail_dot_add(df& acc, float a, float b) {
+  acc = df_add(acc, two_prod(a, b));
+}
+template <int MP>
+__device__ __forceinline__ void tail_cols_store(df v, float2* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o >= MP; o >>= 1) {
+    const df t{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+    v = df_add(v, t);
+  }
+  if (lane < MP) sh[wid * 8 + lane] = make_float2(v.h, v.l);
+}
+template <int MP>
+__device__ __forceinline__ void tail_cols_add(const float2* sh, double* dst) {
+  static_assert(kFT / 32 == 16, "sixteen warp sums per column");
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid < MP) {
+    const float2 w = lane < kFT / 32 ? sh[lane * 8 + wid] : make_float2(0.f, 0.f);
+    df t{w.x, w.y};
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      const df u{__shfl_xor_sync(0xffffffffu, t.h, o), __shfl_xor_sync(0xffffffffu, t.l, o)};
+      t = df_add(t, u);
+    }
+    if (lane == 0) atomicAdd(dst + wid, df_to_double(t));
+  }
+}
+
 // Alg. 7 steps 6-9 for the rows of CTA `cta` of the `ncta` CTAs that serve
 // this system (the whole grid, or the system's CTAs of a grouped launch)
 template <typename T, int MP>
@@ -1284,7 +1321,22 @@ __device__ __forceinline__ void pcg_tail_body(const TailArgs<T>& a, const int ct
   __syncthreads();
 
   // ---- B: e and r, |r|^2 and Q^T r
-  {
+  if constexpr (sizeof(T) == 4) {
+    // float32 iterations: |r|^2 in double-float partials (no float64 per element)
+    df vs{0.f, 0.f};
+    const T al = (T)sh_alpha[tid % MP];            // kFT is a multiple of MP: one column per thread
+    for (int e = tid; e < cnt * MP; e += kFT) {
+      const int64_t g = r0 * MP + e;
+      a.E[g] = fma(al, a.P[g], a.E[g]);
+      const T r = fma(-al, a.W[g], a.R[g]);
+      a.R[g] = r;
+      tail_dot_add(vs, r, r);
+    }
+    tail_cols_store<MP>(vs, reinterpret_cast<float2*>(redd));
+    __syncthreads();
+    if (cnt > 0) tail_cols_add<MP>(reinterpret_cast<const float2*>(redd), acc + 8);
+    __syncthreads();
+  } else {
     double vs = 0.0;
     for (int e = tid; e < cnt * MP; e += kFT) {
       const int64_t g = r0 * MP + e;
@@ -1296,11 +1348,11 @@ __device__ __forceinline__ void pcg_tail_body(const TailArgs<T>& a, const int ct
       vs += (double)r * (double)r;
     }
     place_col(v, vs, tid % MP);
+    block_sum_cols<kFT>(v, MP, redd);
+    if (tid == 0 && cnt > 0)
+      for (int c = 0; c < MP; ++c) atomicAdd(acc + 8 + c, v[c]);
+    __syncthreads();
   }
-  block_sum_cols<kFT>(v, MP, redd);
-  if (tid == 0 && cnt > 0)
-    for (int c = 0; c < MP; ++c) atomicAdd(acc + 8 + c, v[c]);
-  __syncthreads();
   tail_qtr<T, MP>(a.Q, a.R, r0, cnt, k, tacc, Rs, red);
   if (!grid_barrier(a.bar, a.err, (unsigned long long)ncta)) return;
 
@@ -1334,6 +1386,7 @@ __device__ __forceinline__ void pcg_tail_body(const TailArgs<T>& a, const int ct
   const int col = tr_col<MP>(lane);
   const bool writer = tr_writer<MP>(lane);
   double dacc = 0.0;
+  df dfacc{0.f, 0.f};                                // float32 iterations: r^T z in double-float
   if (sizeof(T) == 4 && (k % 4) == 0) {
     // two rows per warp step; each lane loads its quads of both rows before
     // any arithmetic (eight 16-byte loads in flight for k <= 512)
@@ -1386,13 +1439,13 @@ __device__ __forceinline__ void pcg_tail_body(const TailArgs<T>& a, const int ct
         const T r = a.R[i0];
         const T z = r + (T)sum0;
         a.Z[i0] = z;
-        dacc += (double)r * (double)z;
+        tail_dot_add(dfacc, (float)r, (float)z);
         if (two) {
           const int64_t i1 = row1 * MP + col;
           const T r1 = a.R[i1];
           const T z1 = r1 + (T)sum1;
           a.Z[i1] = z1;
-          dacc += (double)r1 * (double)z1;
+          tail_dot_add(dfacc, (float)r1, (float)z1);
         }
       }
     }
@@ -1418,11 +1471,19 @@ __device__ __forceinline__ void pcg_tail_body(const TailArgs<T>& a, const int ct
       }
     }
   }
+  if (sizeof(T) == 4 && (k % 4) == 0) {
+    // one writer lane per column and warp: the warp sums go to shared memory
+    // directly (the double-float partials of the fast path)
+    if (writer) reinterpret_cast<float2*>(redd)[wid * 8 + col] = make_float2(dfacc.h, dfacc.l);
+    __syncthreads();
+    if (cnt > 0) tail_cols_add<MP>(reinterpret_cast<const float2*>(redd), acc + 16);
+  } else {
 #pragma unroll
-  for (int c = 0; c < 8; ++c) v[c] = (c == col && writer) ? dacc : 0.0;
-  block_sum_cols<kFT>(v, MP, redd);
-  if (tid == 0 && cnt > 0)
-    for (int c = 0; c < MP; ++c) atomicAdd(acc + 16 + c, v[c]);
+    for (int c = 0; c < 8; ++c) v[c] = (c == col && writer) ? dacc : 0.0;
+    block_sum_cols<kFT>(v, MP, redd);
+    if (tid == 0 && cnt > 0)
+      for (int c = 0; c < MP; ++c) atomicAdd(acc + 16 + c, v[c]);
+  }
   if (!grid_barrier(a.bar, a.err, (unsigned long long)ncta)) return;
 
   // ---- F: beta, p = z + beta p
