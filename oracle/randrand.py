@@ -37,6 +37,11 @@ arXiv 2509.19747):
 * the refined projector of eq:accurate_proj: Pi ~ Q T Q^T with the Neumann
   T = 2 I - Q^T Q, and Pi A_mu^-1 Pi ~ Q T G T Q^T (the symmetric reading of
   the re-orthogonalized C-RandRAND, eq:c_randrand_reorth);
+* the factorization-free least-squares solve of Sec. 5.2
+  (eq:iterative_refinement): v <- v + D^-1 (A_mu Omega)^T (u - A_mu Omega v),
+  D = (Theta A_mu Omega)^T (Theta A_mu Omega), D^-1 by a library solve or by
+  CG on D (used to measure that form against the factored build; the library
+  factors R);
 * several shifts from one sketch (Sec. 5.1): A Omega computed once, Y_mu =
   A Omega + mu Omega per shift, and the Gram separation (A Omega + mu
   Omega)^T (A Omega + mu Omega) = Omega^T A^T A Omega + 2 mu Omega^T A Omega
@@ -635,6 +640,66 @@ def solve(b_: Build, B: np.ndarray, rtol: float, maxit: int = 20000,
                 break                              # no progress (breakdown) or too many restarts
         infos.append(info)
     return (X[:, 0] if one else X), infos
+
+
+# ==========================================================================
+# Factorization-free least squares (Sec. 5.2 eq:iterative_refinement)
+@dataclasses.dataclass
+class NewtonSketchInfo:
+    steps: int
+    rel_normal_residual: list       # |Y^T (u - Y v_t)| / |Y^T u| after each step
+    inner_iters: list               # CG iterations on D per step (0: exact solve)
+
+
+def cg_spd(matvec, rhs: np.ndarray, tol: float, maxit: int) -> tuple[np.ndarray, int]:
+    """Plain conjugate gradients for an SPD operator from x = 0, stopping at
+    |rhs - D x| <= tol |rhs| (textbook Hestenes-Stiefel recurrences)."""
+    x = np.zeros_like(rhs)
+    r = rhs.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    stop = (tol * np.linalg.norm(rhs)) ** 2
+    it = 0
+    while it < maxit and rr > stop:
+        Dp = matvec(p)
+        alpha = rr / float(p @ Dp)
+        x += alpha * p
+        r -= alpha * Dp
+        rr_new = float(r @ r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    return x, it
+
+
+def newton_sketch_lstsq(Y: np.ndarray, S: np.ndarray, u: np.ndarray, steps: int,
+                        inner_tol: float | None = None, inner_maxit: int = 100000):
+    """v = argmin |Y v - u| for Y = A_mu Omega (n x k) without factoring:
+    from v = 0, v <- v + D^-1 Y^T (u - Y v) with D = S^T S, S = Theta Y the
+    two-sided sketch (Sec. 5.2 eq:iterative_refinement, the Newton-sketch
+    iteration with the R factor taken as the identity).  D^-1 is applied by
+    a library solve of the k x k system (inner_tol None) or, as the paper
+    proposes, by CG on D (matvec S^T (S x)) to a relative residual inner_tol,
+    whose iteration counts are returned."""
+    Y = np.asarray(Y, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    D = S.T @ S
+    v = np.zeros(Y.shape[1])
+    g0 = np.linalg.norm(Y.T @ u)
+    info = NewtonSketchInfo(steps=0, rel_normal_residual=[], inner_iters=[])
+    for _ in range(steps):
+        g = Y.T @ (u - Y @ v)
+        if inner_tol is None:
+            dv = np.linalg.solve(D, g)
+            info.inner_iters.append(0)
+        else:
+            dv, it = cg_spd(lambda x: S.T @ (S @ x), g, inner_tol, inner_maxit)
+            info.inner_iters.append(it)
+        v = v + dv
+        info.steps += 1
+        info.rel_normal_residual.append(float(np.linalg.norm(Y.T @ (u - Y @ v)) / g0))
+    return v, info
 
 
 def exact_solve(op, mu: float, B: np.ndarray) -> np.ndarray:

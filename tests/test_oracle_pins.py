@@ -877,3 +877,72 @@ def test_refined_recurrence_build_solves_and_is_symmetric():
     X, infos = O.solve(bd, B, rtol=1e-12)
     xs = np.linalg.solve(op.dense() + mu * np.eye(200), B)
     assert np.linalg.norm(X - xs) / np.linalg.norm(xs) <= 1e-9
+
+
+# ------------------------------------------------- Sec. 5.2 Newton sketch
+def _newton_problem(n=600, k=20, seed=91):
+    rng = np.random.default_rng(seed)
+    # A_mu Omega with spread column scales (cond ~ 1e3), a generic right side
+    U, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    V, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    Y = U @ np.diag(np.logspace(0, -3, k)) @ V.T
+    u = rng.standard_normal(n)
+    return Y, u
+
+
+def test_newton_sketch_exact_sketch_solves_in_one_step():
+    """With Theta = I (S = Y) D is the normal matrix Y^T Y: the first step of
+    eq:iterative_refinement from v = 0 is the least-squares solution."""
+    Y, u = _newton_problem()
+    v, info = O.newton_sketch_lstsq(Y, Y, u, steps=1)
+    ref = np.linalg.lstsq(Y, u, rcond=None)[0]
+    assert np.linalg.norm(v - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert info.rel_normal_residual[0] <= 1e-9
+
+
+def test_newton_sketch_contracts_by_the_spectrum_of_d_inverse_normal_matrix():
+    """The error e_t = v_t - v* obeys e_{t+1} = (I - D^-1 Y^T Y) e_t, so its
+    Y^T Y-energy norm contracts each step by at most rho = max |1 - lambda|
+    over the eigenvalues of D^-1 Y^T Y; with a sparse-sign Theta of l_sk =
+    16 k rows (an epsilon-embedding) rho < 1 and the iteration reaches the
+    least-squares solution geometrically (O(log 1/u) steps)."""
+    Y, u = _newton_problem()
+    n, k = Y.shape
+    Th = philox.theta_dense(16 * k, n, 8, 92)
+    S = Th @ Y
+    lam = np.linalg.eigvals(np.linalg.solve(S.T @ S, Y.T @ Y)).real
+    rho = float(np.max(np.abs(1.0 - lam)))
+    assert rho < 1.0
+    ref = np.linalg.lstsq(Y, u, rcond=None)[0]
+    A = Y.T @ Y
+    enorm = lambda e: float(np.sqrt(e @ A @ e))
+    steps = int(math.ceil(math.log(1e-11) / math.log(rho)))   # O(log 1/u) steps
+    assert steps <= 80
+    v, info = O.newton_sketch_lstsq(Y, S, u, steps=steps)
+    for t in (1, 2, 5, steps // 2):
+        vt, _ = O.newton_sketch_lstsq(Y, S, u, steps=t)
+        assert enorm(vt - ref) <= rho ** t * enorm(ref) * (1 + 1e-6) + 1e-12 * enorm(ref)
+    assert enorm(v - ref) <= 1e-10 * enorm(ref)
+
+
+def test_newton_sketch_with_inner_cg_matches_exact_inner_solve():
+    """D^-1 by CG on D (matvec S^T S x) to 1e-13 gives the same iterates as a
+    direct solve, and its iteration count grows like sqrt(cond(D))."""
+    Y, u = _newton_problem()
+    n, k = Y.shape
+    S = philox.theta_dense(16 * k, n, 8, 93) @ Y
+    v1, _ = O.newton_sketch_lstsq(Y, S, u, steps=8)
+    v2, info = O.newton_sketch_lstsq(Y, S, u, steps=8, inner_tol=1e-13)
+    assert np.linalg.norm(v2 - v1) <= 1e-8 * np.linalg.norm(v1)
+    cond = np.linalg.cond(S.T @ S)
+    assert all(0 < it <= 4 * np.sqrt(cond) * math.log(2e13) for it in info.inner_iters)
+
+
+def test_cg_spd_is_exact_in_n_steps_on_small_systems():
+    rng = np.random.default_rng(94)
+    B = rng.standard_normal((12, 12))
+    D = B @ B.T + 12 * np.eye(12)
+    rhs = rng.standard_normal(12)
+    x, it = O.cg_spd(lambda z: D @ z, rhs, 1e-14, 100)
+    assert it <= 14
+    assert np.linalg.norm(D @ x - rhs) <= 1e-12 * np.linalg.norm(rhs)
