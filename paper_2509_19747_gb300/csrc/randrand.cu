@@ -622,7 +622,12 @@ rr_status orthogonalize(rr_handle* h, const double* G1given = nullptr) {
 // rounding; here CholeskyQR2, or shifted CholeskyQR3 (Fukaya et al. 2020: a
 // shifted first pass, then two plain passes) when the first Gram is
 // numerically singular, stable up to cond(S) ~ 1/u.  S is overwritten.
-rr_status sketch_qr_R(rr_handle* h, double* Rout) {
+// R_sk only preconditions W = Y_mu R_sk^-1 (R = R_chol R_sk satisfies
+// R^T R = Y_mu^T Y_mu whatever R_sk is), and one Cholesky QR pass leaves
+// S R_1^-1 orthonormal to about u cond(S)^2, so the second pass runs only when
+// the bound cond(S) <= |R_1|_F |R_1^-1|_F (|R_1|_F^2 = trace S^T S) exceeds
+// 1e6.  *inv_ready: kk[kRinvA] holds Rout^-1 (one pass taken).
+rr_status sketch_qr_R(rr_handle* h, double* Rout, bool* inv_ready) {
   const int k = h->k;
   const int64_t l = h->lsk;
   cudaStream_t st = h->st;
@@ -653,9 +658,24 @@ rr_status sketch_qr_R(rr_handle* h, double* Rout) {
     return s;
   }
   RR_CUDA_TRY(cudaMemcpyAsync(Rout, Rp, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, st));
+  *inv_ready = false;
+  bool have_inv = false;
+  if (passes == 2) {
+    trtri_upper_with(Rp, k, h->kk[kScB], Rip, st);
+    have_inv = true;
+    k_trace<<<1, 32, 0, st>>>(G1, k, h->norms);
+    kxk_frob_minus_identity(Rip, 0.0, k, h->norms + 1, st);
+    double nr[2] = {0.0, 0.0};
+    RR_TRY(read_doubles(h, h->norms, 2, nr));
+    const double bound = std::sqrt(std::max(nr[0], 0.0)) * nr[1];
+    if (std::isfinite(bound) && bound <= 1e6) {
+      passes = 1;
+      *inv_ready = true;
+    }
+  }
   for (int p = 1; p < passes; ++p) {
     // next pass on S R_p^-1
-    trtri_upper_with(Rp, k, h->kk[kScB], Rip, st);
+    if (!(p == 1 && have_inv)) trtri_upper_with(Rp, k, h->kk[kScB], Rip, st);
     gemm_nn<double>(l, k, k, 1.0, src, k, Rip, k, 0.0, nullptr, 0, dst, k, st);
     std::swap(src, dst);
     gram_S(src, Rp);
@@ -682,8 +702,9 @@ rr_status rand_qless_qr(rr_handle* h) {
   RR_CUDA_TRY(cudaMemsetAsync(h->S, 0, (size_t)h->lsk * k * 8, st));
   gen_sparse_sign(h->th_cols, h->th_sgn, n, h->lsk, h->o.gamma_sk, h->seed, 3u, st);
   theta_scatter<T>(Yb, n, k, h->th_cols, h->th_sgn, h->o.gamma_sk, h->S, st);
-  RR_TRY(sketch_qr_R(h, h->kk[kRsk]));
-  trtri_upper_with(h->kk[kRsk], k, h->kk[kScB], h->kk[kRinvA], st);
+  bool rsk_inv = false;
+  RR_TRY(sketch_qr_R(h, h->kk[kRsk], &rsk_inv));
+  if (!rsk_inv) trtri_upper_with(h->kk[kRsk], k, h->kk[kScB], h->kk[kRinvA], st);
   right_mult<T>(h, Yb, h->kk[kRinvA], Wb);                       // W = Y_mu R_sk^-1
   gram<T>(h, Wb, h->kk[kR2]);
   RR_TRY(chol(h, h->kk[kR2]));                                   // R_chol
