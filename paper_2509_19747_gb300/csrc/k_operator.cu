@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df(const float* __restri
 
 // Constants of the packed double-float entries below.
 struct Df2Const {
-  p2 ln2h, ln2l, sch2, scl2, m2, two, half, one, c3, c4, c5, s64, i64;
+  p2 ln2h, ln2l, sch2, scl2, m2, two, half, one, c3, c4, c5, s64, i64, rnd;
 };
 __device__ __forceinline__ Df2Const df2_const(float sch, float scl) {
   Df2Const C;
@@ -437,6 +437,7 @@ __device__ __forceinline__ Df2Const df2_const(float sch, float scl) {
   C.c5 = mk2(0.0083333338f, 0.0083333338f);
   C.s64 = mk2(64.f, 64.f);
   C.i64 = mk2(0.015625f, 0.015625f);
+  C.rnd = mk2(12582912.f, 12582912.f);     // 1.5 * 2^23
   return C;
 }
 
@@ -472,11 +473,13 @@ __device__ __forceinline__ df2 df2_entries(const p2* xi, const unsigned long lon
   thf.x = va ? thf.x : -100.f;                     // keep the exponent in range
   thf.y = vb ? thf.y : -100.f;
   th = mk2(thf.x, thf.y);
-  const float kfa = rintf(thf.x), kfb = rintf(thf.y);
-  const p2 f = sub2(th, mk2(kfa, kfb));           // exact, |f| <= 1/2
-  const float2 f64 = un2(mul2(f, C.s64));
-  const float jfa = rintf(f64.x), jfb = rintf(f64.y);
-  const p2 r = sub2(f, mul2(mk2(jfa, jfb), C.i64));  // exact, |r| <= 1/128
+  // round to the nearest integer (ties to even, as rintf) by adding and
+  // removing 1.5 * 2^23, exact for |x| < 2^22; the integer is then the low
+  // bits of the biased sum, so no float-to-int conversion is needed
+  const p2 kb = add2(th, C.rnd);
+  const p2 f = sub2(th, sub2(kb, C.rnd));         // exact, |f| <= 1/2
+  const p2 jb = fma2(f, C.s64, C.rnd);            // f * 64 is exact
+  const p2 r = sub2(f, mul2(sub2(jb, C.rnd), C.i64));  // exact, |r| <= 1/128
   const df2 rr = two_sum2(r, tl);
   const df2 z = df_mul2(rr, df2{C.ln2h, C.ln2l});
   const p2 zh = z.h;
@@ -488,10 +491,13 @@ __device__ __forceinline__ df2 df2_entries(const p2* xi, const unsigned long lon
   const df2 bh = two_sum2(ah.h, q.h);
   const p2 low = add2(add2(add2(ah.l, bh.l), add2(z.l, q.l)), p3);
   const df2 E = fast_two_sum2(bh.h, low);
-  const float2 ta = tab[(int)jfa + 32], tb = tab[(int)jfb + 32];
+  const float2 kbf = un2(kb), jbf = un2(jb);
+  constexpr int kRndBits = 0x4B400000;            // bits of 1.5 * 2^23
+  const float2 ta = tab[__float_as_int(jbf.x) - kRndBits + 32];
+  const float2 tb = tab[__float_as_int(jbf.y) - kRndBits + 32];
   df2 K = df_mul2(df2{mk2(ta.x, tb.x), mk2(ta.y, tb.y)}, E);
-  const float sca = va ? __int_as_float(((int)kfa + 127) << 23) : 0.f;   // 2^k or 0
-  const float scb = vb ? __int_as_float(((int)kfb + 127) << 23) : 0.f;
+  const float sca = va ? __int_as_float((__float_as_int(kbf.x) - kRndBits + 127) << 23) : 0.f;   // 2^k or 0
+  const float scb = vb ? __int_as_float((__float_as_int(kbf.y) - kRndBits + 127) << 23) : 0.f;
   const p2 sc = mk2(sca, scb);
   K.h = mul2(K.h, sc);
   K.l = mul2(K.l, sc);
