@@ -144,7 +144,7 @@ typedef struct {
   int32_t gamma;         /* nonzeros per row of a sparse-sign Omega, default 8  */
   int32_t l_sk;          /* rows of Theta for RAND_CHOLQR (0 -> 4k)             */
   int32_t gamma_sk;      /* nonzeros per column of Theta, default 8             */
-  int32_t power_iters;   /* power iterations per estimate, default 6            */
+  int32_t power_iters;   /* power iterations per estimate, default 20           */
   int32_t max_rhs;       /* right-hand sides a solve may pass (1..8), default 1 */
   int32_t profile;       /* 1: time the hot kernels with CUDA events (rr_profile) */
   int32_t kernel_impl;   /* Gaussian-kernel sketch (RR_PREC_MIXED) and float32

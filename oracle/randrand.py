@@ -52,8 +52,8 @@ optimal rho of eq:rho_g_rand_rand needs |A_mu^-1|), the norms as square
 roots of power-iteration estimates of the largest eigenvalues of A_mu (I -
 Pi) A_mu and A_mu Pi~^2 A_mu, and the MINRES inner stop as the same
 relative reduction of |r|_P = sqrt(r^T P r), the norm MINRES tracks.  Also:
-"a few" power iterations read as 6 by default, from seeded start vectors,
-estimate = |w_it| (norm of the last image of a unit vector); the
+20 power iterations from seeded start
+vectors, estimate = |w_20| (norm of the last image of a unit vector); the
 inner stop max(eta |r_0|, 0.5 rtol |b|); R = R_chol R_sk as the product
 order in Alg. 3 (the only order with R^T R = Y_mu^T Y_mu); l_sk = 4k and
 gamma_sk = 8 for Theta.
@@ -332,7 +332,7 @@ def build(op, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
           variant: str = VARIANT_C, omega: np.ndarray | None = None,
           omega_precision: str = "fp64", orth: str = "householder",
           gamma: int = 8, l_sk: int | None = None, gamma_sk: int = 8,
-          power_iters: int = 6, rho: float | None = None,
+          power_iters: int = 20, rho: float | None = None,
           tau: float | None = None, q: int = 0,
           a_omega: np.ndarray | None = None, ml_l1: int = 0, ml_gamma: int = 0,
           refine: int = 0) -> Build:

@@ -406,7 +406,7 @@ class Handle:
 
     def __init__(self, op: Operator, mu: float, k: int, sketch: str = "gaussian", seed: int = 0,
                  variant: str = "C", precision: str = "fp64", max_rhs: int = 1,
-                 power_iters: int = 6, rho: float = 0.0, restart_eta: float = 1e-2,
+                 power_iters: int = 20, rho: float = 0.0, restart_eta: float = 1e-2,
                  gamma: int = 8, profile: bool = False, kernel_impl: int = 0, stream=None,
                  orth: str = "cholqr2", l_sk: int = 0, gamma_sk: int = 8, iter_impl: int = 0,
                  q: int = 0, keep_sketch: bool = False, ml_l1: int = 0, ml_gamma: int = 0,
@@ -573,7 +573,7 @@ class Request:
 
     def __init__(self, op: Operator, mu: float, k: int, b, rtol: float, sketch: str = "gaussian",
                  seed: int = 0, maxit: int = 20000, variant: str = "C", precision: str = "mixed",
-                 orth: str = "cholqr2", power_iters: int = 6, gamma: int = 8, l_sk: int = 0,
+                 orth: str = "cholqr2", power_iters: int = 20, gamma: int = 8, l_sk: int = 0,
                  gamma_sk: int = 8, kernel_impl: int = 0, iter_impl: int = 0, q: int = 0,
                  ml_l1: int = 0, ml_gamma: int = 0, refine: int = 0):
         import torch

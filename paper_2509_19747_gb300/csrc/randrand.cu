@@ -2777,7 +2777,7 @@ void rr_build_opts_default(rr_build_opts* o) {
   o->gamma = 8;
   o->l_sk = 0;
   o->gamma_sk = 8;
-  o->power_iters = 6;
+  o->power_iters = 20;
   o->max_rhs = 1;
   o->rho = 0.0;
   o->restart_eta = 1e-2;

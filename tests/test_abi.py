@@ -73,7 +73,7 @@ def test_struct_layouts_match_header(lib):
 
 def test_defaults_and_status_strings(lib):
     o = lib.rr_build_opts_default()
-    assert (o.gamma, o.power_iters, o.max_rhs, o.restart_eta) == (8, 6, 1, 1e-2)
+    assert (o.gamma, o.power_iters, o.max_rhs, o.restart_eta) == (8, 20, 1, 1e-2)
     assert lib.randrand_status_str(lib.RR_OK) == "ok"
     assert "invalid" in lib.randrand_status_str(lib.RR_ERR_INVALID_ARG)
     assert lib.randrand_status_str(999) == "unknown status"

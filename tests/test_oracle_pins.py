@@ -222,7 +222,7 @@ def test_exact_eigenvector_deflation_spectrum(variant, q):
     # {lambda_i + mu, i > k}
     P, op = small_dense(n=120)
     k, mu = 10, 1e-3
-    bd = O.build(op, mu, k, omega=P.U[:, :k], variant=variant, q=q, power_iters=20)
+    bd = O.build(op, mu, k, omega=P.U[:, :k], variant=variant, q=q)
     I = np.eye(op.n)
     if variant == "C":
         M = bd.apply_P(I) @ (op.A + mu * I)
@@ -278,7 +278,7 @@ def test_c_randrand_eigenvalue_bracket():
     # rho = tau lambda_max(Pi A_mu Pi A_mu^-1 Pi) / |E|; all from dense algebra
     P, op = small_dense(n=150, power=1.5)
     mu = 1e-3
-    bd = O.build(op, mu, 12, "gaussian", seed=7, power_iters=20)
+    bd = O.build(op, mu, 12, "gaussian", seed=7)
     I = np.eye(op.n)
     Amu = op.A + mu * I
     Pi = bd.Pi(I)
