@@ -104,7 +104,7 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
   L.size[R_Q] = n * kk * ts;
   L.size[R_Y0] = o.keep_sketch ? n * kk * ts : 0;   // A Omega kept for other shifts
   L.size[R_KK] = (size_t)kKK * kk * kk * 8;
-  L.size[R_KKT] = kk * kk * ts;
+  L.size[R_KKT] = kk * kk * 8;   // M in the working type, or the split M^T hi | lo (float)
   L.size[R_GPART] = (size_t)gs_max * kk * kk * 8;
   L.size[R_CHOLW] = 32 * 32 * 8;
   L.size[R_STATUS] = 64;
@@ -524,7 +524,11 @@ void gram(rr_handle* h, const T* X, double* G) {
 
 template <typename T>
 void right_mult(rr_handle* h, const T* X, const double* Mkk, T* out) {
-  // out = X Mkk  (n x k times k x k), Mkk converted to the working type
+  // out = X Mkk  (n x k times k x k), Mkk converted to the working type;
+  // float32 on the tensor cores (3xTF32) where the tensor maps allow it
+  if (sizeof(T) == 4 && gemm_right_tf32x3((const float*)X, h->n, h->k, Mkk, (float*)h->kkT,
+                                          (float*)out, h->dstatus + 8, h->st))
+    return;
   const T* Mt;
   if (sizeof(T) == 8) {
     Mt = reinterpret_cast<const T*>(Mkk);
@@ -1440,7 +1444,10 @@ rr_status finish_build(rr_handle* h, const double* G1given) {
     h->fusedG = h->o.iter_impl != 1 ? r_step_ctas<T>(n, k, h->mp) : 0;
     if (h->fusedG > 0) RR_CUDA_TRY(cudaMemsetAsync(h->bar, 0, h->L.size[R_FUSED], st));
   }
-  return sync_status(h);
+  RR_TRY(sync_status(h));
+  int gerr = 0;
+  RR_TRY(read_int(h, h->dstatus + 8, &gerr));   // the tensor-core right multiplications
+  return gerr ? RR_ERR_TIMEOUT : RR_OK;
 }
 
 // Sec. 5.1 for the kept sketch: Y_mu = A Omega + mu Omega, the first Gram
