@@ -73,12 +73,16 @@ def test_sparse_sign_omega_bitwise(cuda_lib):
 
 # ------------------------------------------------------- build products
 @pytest.mark.parametrize("precision", ["mixed", "fp32"])
-def test_float32_basis_orthonormal_and_factorizes(cuda_lib, precision):
+@pytest.mark.parametrize("n,k", [(3001, 120), (2500, 260), (2000, 122)])
+def test_float32_basis_orthonormal_and_factorizes(cuda_lib, precision, n, k):
     """Float32 paths (the last Cholesky QR pass taken to first order in
     |I - Q1^T Q1|): the stored basis is orthonormal to float32 rounding and
-    Q R reproduces Y_mu = A_mu Omega of the oracle (same Omega)."""
+    Q R reproduces Y_mu = A_mu Omega of the oracle (same Omega).  The right
+    multiplications run on the tensor cores for k a multiple of 4 (k = 260:
+    two 256-column output tiles and a partial last K step) and on the float32
+    cores otherwise (k = 122)."""
     rr = cuda_lib
-    n, k, mu = 3001, 120, 1e-3
+    mu = 1e-3
     X = W.mixture_points(n, seed=121)
     op = O.GaussKernelOp(X)
     h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=121,
