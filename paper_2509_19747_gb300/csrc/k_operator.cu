@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df2s(const float* __rest
   // (64 p + c, 64 p + 32 + c) as the two lanes of a pair
   __shared__ __align__(16) unsigned long long sx2[2][kMaxDim][kCh];
   __shared__ __align__(16) float4 spn2[2][kCh];
-  __shared__ __align__(16) float4 sv2[2][kCh][MP];
+  __shared__ __align__(16) float4 sv2[2][MP][kCh];   // [pass][column of v][slot]: a warp's rotating slots are consecutive
   __shared__ float2 tab[65];
   __shared__ float2 scol[kKmvRows / 32][kKmvTile][MP];   // the warps' column sums (hi, lo)
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df2s(const float* __rest
 #pragma unroll
     for (int cc = 0; cc < MP; ++cc) {
       const df v = jl ? df_from_double(V[j * MP + cc]) : df{0.f, 0.f};
-      float* vs = reinterpret_cast<float*>(&sv2[pp][c][cc]);
+      float* vs = reinterpret_cast<float*>(&sv2[pp][cc][c]);
       vs[hb] = v.h;
       vs[2 + hb] = v.l;
     }
@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(kKmvRows) k_kernel_mv_df2s(const float* __rest
       const df2 K = df2_entries(xi, &sx2[pp][0][c], kCh, dim, pnih, pnil, pj, true, tab, C);
 #pragma unroll
       for (int cc = 0; cc < MP; ++cc) {
-        const ulonglong2 vv = *reinterpret_cast<const ulonglong2*>(&sv2[pp][c][cc]);
+        const ulonglong2 vv = *reinterpret_cast<const ulonglong2*>(&sv2[pp][cc][c]);
         df2_mac(acc[cc], K, p2{vv.x}, p2{vv.y});
       }
       if (!diag) {
