@@ -1000,6 +1000,10 @@ def run_serving(args):
                  completed=len(ok), failed=len(res) - len(ok), makespan_s=makespan,
                  offered_s=float(arrivals[-1]),
                  overloaded=bool(makespan > 1.5 * float(arrivals[-1])),
+                 # when the arrivals outrun the server it runs saturated, so the
+                 # completion rate is the mix's sustainable request rate
+                 capacity_req_per_s=(len(ok) / makespan
+                                     if makespan > 1.5 * float(arrivals[-1]) else None),
                  peak_arena_gb=stats["peak_bytes"] / 1e9,
                  in_rounds=sum(r.get("rounds", 0) for _, _, r in res), roofline=None, clocks=clocks)
     if rank == 0:
