@@ -45,7 +45,10 @@ arXiv 2509.19747):
 * several shifts from one sketch (Sec. 5.1): A Omega computed once, Y_mu =
   A Omega + mu Omega per shift, and the Gram separation (A Omega + mu
   Omega)^T (A Omega + mu Omega) = Omega^T A^T A Omega + 2 mu Omega^T A Omega
-  + mu^2 Omega^T Omega of the parameter-free projections.
+  + mu^2 Omega^T Omega of the parameter-free projections; and the joint basis
+  (Sec. 5.1): Q_joint from qr([Omega, A Omega]), C1 = Q_joint^T A Omega,
+  C2 = Q_joint^T Omega, then per shift qr(C1 + mu C2) = Q_red R and
+  Q = Q_joint Q_red.
 
 Readings where the paper is silent: for G-RandRAND rho = 0.5 a priori (the
 optimal rho of eq:rho_g_rand_rand needs |A_mu^-1|), the norms as square
@@ -484,6 +487,31 @@ def shifted_gram(sk: ShiftSketch, mu: float) -> np.ndarray:
     """(A Omega + mu Omega)^T (A Omega + mu Omega) from the parameter-free
     projections (the Gram separation of Sec. 5.1; A symmetric)."""
     return sk.P2 + 2.0 * mu * sk.M0 + mu * mu * sk.S0
+
+
+@dataclasses.dataclass
+class JointBasis:
+    """The joint basis of Sec. 5.1 for several shifts: Q_joint with
+    range(Q_joint) = range([Omega, A Omega]) and the 2k x k projections
+    C1 = Q_joint^T A Omega and C2 = Q_joint^T Omega."""
+    Qj: np.ndarray
+    C1: np.ndarray
+    C2: np.ndarray
+
+
+def joint_basis(sk: ShiftSketch) -> JointBasis:
+    """[Q_joint, ~] = qr([Omega, A Omega]) (Householder), then the two
+    projections."""
+    Qj, _ = householder_qr(np.hstack([sk.Omega, sk.AOmega]))
+    return JointBasis(Qj=Qj, C1=Qj.T @ sk.AOmega, C2=Qj.T @ sk.Omega)
+
+
+def joint_qr(jb: JointBasis, mu: float) -> tuple[np.ndarray, np.ndarray]:
+    """For one shift: [Q_red, R] = qr(C1 + mu C2) (2k x k, Householder,
+    diag(R) > 0) and Q = Q_joint Q_red, the QR factors of A Omega + mu Omega
+    (Sec. 5.1)."""
+    Qr, R = householder_qr(jb.C1 + mu * jb.C2)
+    return jb.Qj @ Qr, R
 
 
 # ==========================================================================

@@ -495,6 +495,32 @@ def test_recycled_sketch_build_equals_fresh_build():
         assert np.linalg.norm(x - O.exact_solve(op, mu, B)) <= 1e-8 * np.linalg.norm(x)
 
 
+def test_joint_basis_qr_matches_direct_qr():
+    """The joint basis of Sec. 5.1: Q_joint Q_red and R from qr(C1 + mu C2)
+    are the unique (positive-diagonal) QR factors of A Omega + mu Omega
+    computed directly, for several shifts including an ill-conditioned
+    basis; dropping the mu C2 term (a plausible slip) fails at mu > 0."""
+    P = W.dense_power_spectrum(300, seed=83, power=3.0)
+    op = O.DenseOp(P.A)
+    sk = O.shift_sketch(op, 24, "gaussian", seed=83)
+    jb = O.joint_basis(sk)
+    assert jb.Qj.shape == (300, 48) and jb.C1.shape == (48, 24) and jb.C2.shape == (48, 24)
+    assert np.linalg.norm(jb.Qj.T @ jb.Qj - np.eye(48), 2) <= 1e-13
+    for mu in (0.0, 1e-6, 1e-3, 0.4):
+        Ymu = P.A @ sk.Omega + mu * sk.Omega
+        Qh, Rh = O.householder_qr(Ymu)
+        Q, R = O.joint_qr(jb, mu)
+        scale = np.abs(Rh).max()
+        assert np.allclose(R, Rh, rtol=0, atol=1e-11 * scale)
+        # two backward-stable QRs: Q agrees to O(u cond(Y_mu))
+        assert np.linalg.norm(Q - Qh, 2) <= 1e3 * 2.2e-16 * np.linalg.cond(Ymu)
+        assert np.linalg.norm(Q @ R - Ymu) <= 1e-12 * np.linalg.norm(Ymu)
+    bad = O.JointBasis(Qj=jb.Qj, C1=jb.C1, C2=np.zeros_like(jb.C2))
+    _, Rb = O.joint_qr(bad, 0.4)
+    _, Rh = O.householder_qr(P.A @ sk.Omega + 0.4 * sk.Omega)
+    assert np.abs(Rb - Rh).max() > 1e-3 * np.abs(Rh).max()
+
+
 # ------------------------------------------------------------ SRHT (Sec. 2)
 def test_srht_subsampling_is_a_permutation():
     """The keyed Feistel permutation (with cycle-walking for odd log2 s) maps
