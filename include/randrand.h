@@ -174,9 +174,17 @@ typedef struct {
                             Omega^T A^T A Omega, Omega^T A Omega, Omega^T Omega
                             (Sec. 5.1) so that randrand_set_mu can rebuild the
                             preconditioner for another shift without a new
-                            sketch product; costs one more n x k array.  Variant
-                            C with an explicit basis (orth CHOLQR2) and q = 0
-                            only (else RR_ERR_UNSUPPORTED).  Default 0 */
+                            sketch product; costs one more n x k array.
+                            2: the joint basis instead (Sec. 5.1): Q_joint
+                            with range(Q_joint) = range([Omega, A Omega]), C1 =
+                            Q_joint^T A Omega and C2 = Q_joint^T Omega; a shift
+                            then takes R from a float64 Cholesky QR of the 2k x k
+                            C1 + mu C2 (never the Gram of an n-row matrix) and
+                            Q = Q_joint Q_red; costs 3 more n x k arrays and
+                            fails with RR_ERR_NOT_SPD when A Omega adds no
+                            direction to Omega.  Variant C with an explicit
+                            basis (orth CHOLQR2) and q = 0 only (else
+                            RR_ERR_UNSUPPORTED).  Default 0 */
   int32_t ml_l1;         /* RR_SKETCH_MULTILEVEL: rows l1 of X1, k <= l1 <= 2^24 */
   int32_t ml_gamma;      /* RR_SKETCH_MULTILEVEL: nonzeros per column of X1,
                             1..16, <= ml_l1.  0 (the default) reserves no
@@ -315,9 +323,11 @@ void randrand_free(rr_handle* h);
  * (A Omega + mu Omega)^T (A Omega + mu Omega) = Omega^T A^T A Omega +
  * 2 mu Omega^T A Omega + mu^2 Omega^T Omega, the second pass orthogonalizes
  * the result as in the build; then Omega^T A_mu Omega = Omega^T A Omega + mu
- * Omega^T Omega for G, the power iterations for tau, and Q H.  Later solves
- * use mu.  Synchronous on the handle stream.
- *   h   a handle built with opts.keep_sketch = 1.
+ * Omega^T Omega for G, the power iterations for tau, and Q H.  With
+ * keep_sketch = 2 the factors come from the joint basis instead: R = R(C1 +
+ * mu C2) and Q = Q_joint (C1 + mu C2) R^-1.  Later solves use mu.
+ * Synchronous on the handle stream.
+ *   h   a handle built with opts.keep_sketch = 1 or 2.
  *   mu  new shift, >= 0 and finite.
  * Errors: RR_ERR_INVALID_ARG (h NULL, mu < 0 or not finite),
  * RR_ERR_UNSUPPORTED (handle built without keep_sketch), RR_ERR_NOT_SPD,

@@ -409,7 +409,7 @@ class Handle:
                  power_iters: int = 20, rho: float = 0.0, restart_eta: float = 1e-2,
                  gamma: int = 8, profile: bool = False, kernel_impl: int = 0, stream=None,
                  orth: str = "cholqr2", l_sk: int = 0, gamma_sk: int = 8, iter_impl: int = 0,
-                 q: int = 0, keep_sketch: bool = False, ml_l1: int = 0, ml_gamma: int = 0,
+                 q: int = 0, keep_sketch: int = 0, ml_l1: int = 0, ml_gamma: int = 0,
                  refine: int = 0):
         """sketch "multilevel": ml_l1 / ml_gamma give X1's rows and nonzeros per
         column; 0 takes rr_multilevel_defaults."""
@@ -432,7 +432,7 @@ class Handle:
         o.kernel_impl = kernel_impl
         o.iter_impl = iter_impl
         o.q = q
-        o.keep_sketch = 1 if keep_sketch else 0
+        o.keep_sketch = int(keep_sketch)   # True / 1: Gram separation; 2: joint basis
         o.refine = int(refine)
         set_multilevel(o, sketch, op.n, k, ml_l1, ml_gamma)
         self.opts = o
@@ -477,7 +477,7 @@ class Handle:
         return randrand_core_jitter(self.h)
 
     def set_mu(self, mu: float):
-        """Rebuild for another shift from the kept sketch (keep_sketch=True)."""
+        """Rebuild for another shift from the kept sketch (keep_sketch 1 or 2)."""
         randrand_set_mu(self.h, mu)
 
     def profile(self) -> dict:

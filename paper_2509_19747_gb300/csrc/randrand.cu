@@ -33,7 +33,7 @@ constexpr int kMaxRestarts = 400;
 enum Region {
   R_OM, R_OMB, R_SSC, R_SSS, R_THC, R_THS, R_SK, R_Y, R_Q, R_Y0, R_KK, R_KKT, R_GPART, R_CHOLW,
   R_STATUS, R_XS, R_CN, R_PN, R_AUG, R_MVS, R_VT, R_V64, R_STAGE, R_TPART, R_TVEC, R_RPART, R_CNT,
-  R_CS, R_NORMS, R_FUSED, R_ML, R_FWHT, R_PCNT, R_OMT, R_SKP, R_NREG
+  R_CS, R_NORMS, R_FUSED, R_ML, R_FWHT, R_PCNT, R_OMT, R_SKP, R_QJ, R_CJ, R_NREG
 };
 
 struct Layout {
@@ -96,13 +96,17 @@ Layout make_layout(const rr_operator& A, int k, const rr_build_opts& o) {
     while (sp < A.n) sp <<= 1;
     L.size[R_FWHT] = basis_less(A, o) ? align256((size_t)sp * 4) + (size_t)sp * mp * ts : 0;
   }
-  const size_t lsk = uses_alg3(o) ? (size_t)sketch_rows(k, o) : 0;
+  // rows of the float64 matrix sketch_qr_R factors: Theta Y_mu (Alg. 3) or
+  // the 2k x k reduced matrix of the joint basis (Sec. 5.1)
+  const size_t lsk = uses_alg3(o) ? (size_t)sketch_rows(k, o) : (o.keep_sketch == 2 ? 2 * kk : 0);
   L.size[R_THC] = uses_alg3(o) ? n * (size_t)o.gamma_sk * 4 : 0;
   L.size[R_THS] = uses_alg3(o) ? n * (size_t)o.gamma_sk : 0;
   L.size[R_SK] = 2 * lsk * kk * 8;   // S = Theta Y_mu and one copy for CholeskyQR passes
   L.size[R_Y] = n * kk * ts;
   L.size[R_Q] = n * kk * ts;
   L.size[R_Y0] = o.keep_sketch ? n * kk * ts : 0;   // A Omega kept for other shifts
+  L.size[R_QJ] = o.keep_sketch == 2 ? n * 2 * kk * ts : 0;   // joint basis, rows [Q1_i | Q2_i]
+  L.size[R_CJ] = o.keep_sketch == 2 ? 2 * (2 * kk) * kk * 8 : 0;   // C1 and C2 (2k x k each)
   L.size[R_KK] = (size_t)kKK * kk * kk * 8;
   L.size[R_KKT] = kk * kk * 8;   // M in the working type, or the split M^T hi | lo (float)
   L.size[R_GPART] = (size_t)gs_max * kk * kk * 8;
@@ -187,7 +191,7 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
   if (o.power_iters < 1 || o.power_iters > 1000) return RR_ERR_INVALID_ARG;
   if (o.iter_impl < 0 || o.iter_impl > 2) return RR_ERR_INVALID_ARG;
   if (o.kernel_impl < 0 || o.kernel_impl > 3) return RR_ERR_INVALID_ARG;
-  if (o.keep_sketch != 0 && o.keep_sketch != 1) return RR_ERR_INVALID_ARG;
+  if (o.keep_sketch < 0 || o.keep_sketch > 2) return RR_ERR_INVALID_ARG;
   if (o.keep_sketch &&
       (o.variant != RR_VARIANT_C || uses_alg3(o) || o.q != 0 || basis_less(*A, o)))
     return RR_ERR_UNSUPPORTED;
@@ -306,6 +310,8 @@ struct rr_handle {
   void* Q;
   void* QH;
   void* Y0;           // A Omega (opts.keep_sketch)
+  void* Qj;           // joint basis n x 2k, rows [Q1_i | Q2_i] (opts.keep_sketch = 2)
+  double* Cj;         // C1 = Q_joint^T A Omega, then C2 = Q_joint^T Omega (2k x k each)
   double* kk[kKK];
   void* kkT;
   double* gpart;
@@ -379,6 +385,8 @@ void carve(rr_handle* h) {
   h->Q = at(R_Q);
   h->QH = nullptr;
   h->Y0 = h->L.size[R_Y0] ? at(R_Y0) : nullptr;
+  h->Qj = h->L.size[R_QJ] ? at(R_QJ) : nullptr;
+  h->Cj = h->L.size[R_CJ] ? (double*)at(R_CJ) : nullptr;
   double* kkbase = (double*)at(R_KK);
   for (int i = 0; i < kKK; ++i) h->kk[i] = kkbase + (size_t)i * h->k * h->k;
   h->kkT = at(R_KKT);
@@ -630,8 +638,9 @@ rr_status orthogonalize(rr_handle* h, const double* G1given = nullptr) {
 // R^T R = Y_mu^T Y_mu whatever R_sk is), and one Cholesky QR pass leaves
 // S R_1^-1 orthonormal to about u cond(S)^2, so the second pass runs only when
 // the bound cond(S) <= |R_1|_F |R_1^-1|_F (|R_1|_F^2 = trace S^T S) exceeds
-// 1e6.  *inv_ready: kk[kRinvA] holds Rout^-1 (one pass taken).
-rr_status sketch_qr_R(rr_handle* h, double* Rout, bool* inv_ready) {
+// 1e6 (always when one_pass_ok is false: there S R^-1 is itself a basis).
+// *inv_ready: kk[kRinvA] holds Rout^-1 (one pass taken).
+rr_status sketch_qr_R(rr_handle* h, double* Rout, bool* inv_ready, bool one_pass_ok = true) {
   const int k = h->k;
   const int64_t l = h->lsk;
   cudaStream_t st = h->st;
@@ -664,7 +673,7 @@ rr_status sketch_qr_R(rr_handle* h, double* Rout, bool* inv_ready) {
   RR_CUDA_TRY(cudaMemcpyAsync(Rout, Rp, (size_t)k * k * 8, cudaMemcpyDeviceToDevice, st));
   *inv_ready = false;
   bool have_inv = false;
-  if (passes == 2) {
+  if (passes == 2 && one_pass_ok) {
     trtri_upper_with(Rp, k, h->kk[kScB], Rip, st);
     have_inv = true;
     k_trace<<<1, 32, 0, st>>>(G1, k, h->norms);
@@ -1252,7 +1261,11 @@ rr_status sketch_product(rr_handle* h, double shift, bool tc, int64_t ldo) {
 }
 
 template <typename T>
-rr_status finish_build(rr_handle* h, const double* G1given);
+rr_status finish_build(rr_handle* h, const double* G1given, bool have_qr = false);
+template <typename T>
+rr_status joint_prepare(rr_handle* h);
+template <typename T>
+rr_status joint_finish(rr_handle* h);
 template <typename T>
 rr_status shift_finish(rr_handle* h);
 
@@ -1324,10 +1337,14 @@ rr_status build_impl(rr_handle* h) {
     // Sec. 5.1: A Omega once, then the shift-free projections
     RR_TRY(sketch_product<T>(h, 0.0, tc, ldo));
     RR_CUDA_TRY(cudaMemcpyAsync(h->Y0, h->Y, (size_t)n * k * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    gram<T>(h, (const T*)h->Y0, h->kk[kP2]);
+    if (h->o.keep_sketch == 1) gram<T>(h, (const T*)h->Y0, h->kk[kP2]);
     gram_partial<T>((const T*)h->Om, k, (const T*)h->Y0, k, n, k, k, false, h->gsplit, h->gpart, st);
     reduce_gram(h->gpart, h->gsplit, k, k, false, true, h->kk[kM0], st);
     gram<T>(h, (const T*)h->Om, h->kk[kS0]);
+    if (h->o.keep_sketch == 2) {
+      RR_TRY(joint_prepare<T>(h));
+      return joint_finish<T>(h);
+    }
     return shift_finish<T>(h);
   }
   RR_TRY(sketch_product<T>(h, h->mu, tc, ldo));
@@ -1343,13 +1360,18 @@ rr_status build_impl(rr_handle* h) {
 // given when the shift-free projections provide it), core matrix, power
 // iterations, tau, H and Q H
 template <typename T>
-rr_status finish_build(rr_handle* h, const double* G1given) {
+rr_status finish_build(rr_handle* h, const double* G1given, bool have_qr) {
   const int64_t n = h->n;
   const int k = h->k;
   cudaStream_t st = h->st;
   (void)n;
-  if (uses_alg3(h->o)) RR_TRY(rand_qless_qr<T>(h));
-  else RR_TRY(orthogonalize<T>(h, G1given));
+  if (have_qr) {
+    // Q, R and R^-1 are set (the joint basis of Sec. 5.1)
+  } else if (uses_alg3(h->o)) {
+    RR_TRY(rand_qless_qr<T>(h));
+  } else {
+    RR_TRY(orthogonalize<T>(h, G1given));
+  }
   if (h->o.variant == RR_VARIANT_C) RR_TRY(core_matrix(h));
   if (h->o.variant == RR_VARIANT_G) {
     // Sec. 3.3: G = (R^-T (Omega^T Omega) R^-1)^(1/2); core_matrix forms
@@ -1470,6 +1492,89 @@ rr_status shift_finish(rr_handle* h) {
   axpby<double, double, double>(h->kk[kM0], coefs_all(1.0), h->kk[kS0], coefs_all(mu), h->kk[kM],
                                 kk2, 1, st);
   return finish_build<T>(h, G1);
+}
+
+// The joint basis of Sec. 5.1 (opts.keep_sketch = 2), once per sketch:
+// Q1 R_Om = Omega (CholeskyQR2), Z = A Omega - Q1 T1 with T1 = Q1^T A Omega
+// (block Gram-Schmidt, twice), Q2 R_Z = Z, so that range([Q1 Q2]) =
+// range([Omega, A Omega]) and
+//   C1 = [Q1 Q2]^T A Omega = [T1; R_Z],   C2 = [Q1 Q2]^T Omega = [R_Om; 0].
+// Q_joint is stored with rows [Q1_i | Q2_i] (n x 2k).
+template <typename T>
+rr_status joint_prepare(rr_handle* h) {
+  const int64_t n = h->n;
+  const int k = h->k;
+  cudaStream_t st = h->st;
+  const int64_t kk2 = (int64_t)k * k;
+  const size_t row = (size_t)k * sizeof(T);
+  double* C1 = h->Cj;
+  double* C2 = h->Cj + 2 * kk2;
+  // Q1 R_Om = Omega
+  RR_CUDA_TRY(cudaMemcpyAsync(h->Y, h->Om, (size_t)n * row, cudaMemcpyDeviceToDevice, st));
+  RR_TRY(orthogonalize<T>(h));
+  RR_CUDA_TRY(cudaMemcpy2DAsync(h->Qj, 2 * row, h->Q, row, row, (size_t)n, cudaMemcpyDeviceToDevice, st));
+  RR_CUDA_TRY(cudaMemcpyAsync(C2, h->kk[kRfull], (size_t)kk2 * 8, cudaMemcpyDeviceToDevice, st));
+  RR_CUDA_TRY(cudaMemsetAsync(C2 + kk2, 0, (size_t)kk2 * 8, st));
+  // Z = A Omega - Q1 (Q1^T A Omega), the projection taken twice (the second
+  // removes what rounding left of range(Q1)); T1 accumulates both
+  const T* Q1 = (const T*)h->Q;
+  T* Z = (T*)h->Y;
+  RR_CUDA_TRY(cudaMemcpyAsync(Z, h->Y0, (size_t)n * row, cudaMemcpyDeviceToDevice, st));
+  RR_CUDA_TRY(cudaMemsetAsync(C1, 0, (size_t)kk2 * 8, st));
+  for (int pass = 0; pass < 2; ++pass) {
+    double* Tp = h->kk[kScA];
+    gram_partial<T>(Q1, k, Z, k, n, k, k, false, h->gsplit, h->gpart, st);
+    reduce_gram(h->gpart, h->gsplit, k, k, false, false, Tp, st);
+    axpby<double, double, double>(C1, coefs_all(1.0), Tp, coefs_all(1.0), C1, kk2, 1, st);
+    const T* Tt;
+    if (sizeof(T) == 8) {
+      Tt = reinterpret_cast<const T*>(Tp);
+    } else {
+      convert<double, float>(Tp, (float*)h->kkT, kk2, st);
+      Tt = reinterpret_cast<const T*>(h->kkT);
+    }
+    gemm_nn<T>(n, k, k, -1.0, Q1, k, Tt, k, 1.0, Z, k, Z, k, st);   // Z -= Q1 Tp
+  }
+  // Q2 R_Z = Z (orthogonalize reads h->Y = Z and leaves Q2 in h->Q)
+  RR_TRY(orthogonalize<T>(h));
+  RR_CUDA_TRY(cudaMemcpy2DAsync((unsigned char*)h->Qj + row, 2 * row, h->Q, row, row, (size_t)n,
+                                cudaMemcpyDeviceToDevice, st));
+  RR_CUDA_TRY(cudaMemcpyAsync(C1 + kk2, h->kk[kRfull], (size_t)kk2 * 8, cudaMemcpyDeviceToDevice, st));
+  return RR_OK;
+}
+
+// One shift from the joint basis (Sec. 5.1): F = C1 + mu C2 (2k x k),
+// R = R(F) by sketch_qr_R's float64 Cholesky QR, Q_red = F R^-1 and
+// Q = Q_joint Q_red; then the rest of the build with M = M0 + mu S0.
+template <typename T>
+rr_status joint_finish(rr_handle* h) {
+  const int64_t n = h->n;
+  const int k = h->k;
+  const double mu = h->mu;
+  cudaStream_t st = h->st;
+  const int64_t kk2 = (int64_t)k * k;
+  const double* C1 = h->Cj;
+  const double* C2 = h->Cj + 2 * kk2;
+  axpby<double, double, double>(C1, coefs_all(1.0), C2, coefs_all(mu), h->S, 2 * kk2, 1, st);
+  bool rinv = false;
+  RR_TRY(sketch_qr_R(h, h->kk[kRfull], &rinv, false));   // Q_red must be orthonormal
+  if (!rinv) trtri_upper_with(h->kk[kRfull], k, h->kk[kScB], h->kk[kRinvA], st);
+  RR_CUDA_TRY(cudaMemcpyAsync(h->kk[kRinv], h->kk[kRinvA], (size_t)kk2 * 8, cudaMemcpyDeviceToDevice, st));
+  // F again (sketch_qr_R overwrote S), Q_red = F R^-1 into S2
+  axpby<double, double, double>(C1, coefs_all(1.0), C2, coefs_all(mu), h->S, 2 * kk2, 1, st);
+  gemm_nn<double>(2 * k, k, k, 1.0, h->S, k, h->kk[kRinv], k, 0.0, nullptr, 0, h->S2, k, st);
+  const T* Qred;
+  if (sizeof(T) == 8) {
+    Qred = reinterpret_cast<const T*>(h->S2);
+  } else {
+    convert<double, float>(h->S2, (float*)h->kkT, 2 * kk2, st);   // kkT holds 2 k^2 floats
+    Qred = reinterpret_cast<const T*>(h->kkT);
+  }
+  // Q into the buffer that is not the free one (QH takes h->Y later)
+  gemm_nn<T>(n, k, 2 * k, 1.0, (const T*)h->Qj, 2 * k, Qred, k, 0.0, nullptr, 0, (T*)h->Q, k, st);
+  axpby<double, double, double>(h->kk[kM0], coefs_all(1.0), h->kk[kS0], coefs_all(mu), h->kk[kM],
+                                kk2, 1, st);
+  return finish_build<T>(h, nullptr, true);
 }
 
 // ------------------------------------------------------------------ solve
@@ -2877,7 +2982,7 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
   h->L = L;
   h->ws = (unsigned char*)workspace;
   h->gsplit = gram_nsplit(A->n, k, k);
-  h->lsk = uses_alg3(o) ? sketch_rows(k, o) : 0;
+  h->lsk = uses_alg3(o) ? sketch_rows(k, o) : (o.keep_sketch == 2 ? 2 * k : 0);
   h->fwht_B = 0;
   h->ml_l1 = ml_reserved(o) ? o.ml_l1 : 0;
   h->ml_g = ml_reserved(o) ? o.ml_gamma : 0;
@@ -2975,6 +3080,7 @@ rr_status randrand_set_mu(rr_handle* h, double mu) {
   RR_CUDA_TRY(cudaMemsetAsync(h->cnt, 0, h->L.size[R_CNT], h->st));
   RR_CUDA_TRY(cudaMemsetAsync(h->cs, 0, h->L.size[R_CS], h->st));
   RR_CUDA_TRY(cudaMemsetAsync(h->dstatus, 0, h->L.size[R_STATUS], h->st));
+  if (h->o.keep_sketch == 2) return h->f64 ? joint_finish<double>(h) : joint_finish<float>(h);
   return h->f64 ? shift_finish<double>(h) : shift_finish<float>(h);
 }
 

@@ -100,3 +100,69 @@ def test_keep_sketch_options(cuda_lib):
         h2.set_mu(-1.0)
     with pytest.raises(rr.RandRandError):
         h2.set_mu(float("nan"))
+
+
+# ------------------------------------------------ joint basis (Sec. 5.1)
+def test_joint_basis_matches_oracle_fp64(cuda_lib):
+    """keep_sketch = 2 (the joint basis): the factors at the build shift and
+    at two later shifts equal the oracle's joint QR and a fresh float64 build
+    (R unique with a positive diagonal), and the solves reach the exact
+    solution."""
+    rr = cuda_lib
+    n, k, seed = 700, 60, 93
+    P = W.dense_power_spectrum(n, seed=W.SEED_DENSE, power=2.0)
+    op = O.DenseOp(P.A)
+    B = W.gaussian_rhs(n, 2, seed)
+    mus = (1e-4, 1e-2, 0.5)
+    h = rr.Handle(rr.Operator.dense(dev(P.A)), mus[0], k, "gaussian", seed=seed, max_rhs=2,
+                  keep_sketch=2)
+    Om = h.export("omega").cpu().numpy()
+    jb = O.joint_basis(O.ShiftSketch(Omega=Om, AOmega=P.A @ Om, P2=None, M0=None, S0=None))
+    for i, mu in enumerate(mus):
+        if i > 0:
+            h.set_mu(mu)
+        _, Rj = O.joint_qr(jb, mu)
+        Rg = h.export("R").cpu().numpy()
+        assert rel(Rg, Rj) <= max(1e-12, 1e-15 * np.linalg.cond(Rj)) * 100
+        check_factors(h, O.build(op, mu, k, "gaussian", seed=seed))
+        Q = h.export("Q").cpu().numpy()
+        assert np.linalg.norm(Q.T @ Q - np.eye(k), 2) <= 1e-12
+        x, status, infos = h.solve(dev(B), rtol=1e-12)
+        assert status == rr.RR_OK
+        assert rel(x.cpu().numpy(), O.exact_solve(op, mu, B)) <= 1e-8
+
+
+def test_joint_basis_kernel_mixed(cuda_lib):
+    """Gaussian kernel with float32 iterations: along a shift path the joint
+    basis gives solves that meet rtol with the float64 residual as the judge,
+    and an orthonormal float32 basis whose Q R reproduces Y_mu = A Omega +
+    mu Omega of the oracle (same bf16-rounded Omega; the sketch products are
+    bf16 tensor-core products, hence 1e-2)."""
+    rr = cuda_lib
+    n, k, seed = 3001, 80, 94
+    X = W.mixture_points(n, seed=seed)
+    op = O.GaussKernelOp(X)
+    B = W.gaussian_rhs(n, 4, seed)
+    Xd = dev(X)
+    joint = rr.Handle(rr.Operator.gauss_kernel(Xd), 1e-3, k, "gaussian", seed=seed,
+                      precision="mixed", max_rhs=4, keep_sketch=2)
+    Om = joint.export("omega").cpu().numpy().astype(np.float64)
+    AOm = op.matmat(Om)
+    for i, mu in enumerate((1e-3, 1e-2, 1e-4)):
+        if i > 0:
+            joint.set_mu(mu)
+        Q = joint.export("Q").cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(Q.T @ Q - np.eye(k), 2) <= 2e-5
+        assert rel(Q @ joint.export("R").cpu().numpy(), AOm + mu * Om) <= 1e-2
+        x, status, infos = joint.solve(dev(B), rtol=1e-6)
+        assert status == rr.RR_OK
+        assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), B) <= 1e-6)
+
+
+def test_joint_basis_rejects_unsupported(cuda_lib):
+    """keep_sketch = 2 needs the C variant with an explicit basis."""
+    rr = cuda_lib
+    P = W.dense_power_spectrum(200, seed=W.SEED_DENSE, power=2.0)
+    with pytest.raises(rr.RandRandError):
+        rr.Handle(rr.Operator.dense(dev(P.A)), 1e-3, 20, "gaussian", seed=1, variant="R",
+                  keep_sketch=2)
