@@ -77,6 +77,8 @@ def parse():
                          "sparse sign for the sparse diffusion workload)")
     ap.add_argument("--variant", default="C", choices=["C", "R"],
                     help="kernel ridge and sparse diffusion: preconditioner variant")
+    ap.add_argument("--joint", action="store_true",
+                    help="shift_path: the joint basis of Sec. 5.1 (keep_sketch = 2)")
     ap.add_argument("--refine", action="store_true",
                     help="kernel ridge: refined projector (rr_build_opts.refine)")
     ap.add_argument("--kernel-impl", type=int, default=0,
@@ -864,7 +866,7 @@ def run_shift_path(args):
 
     def kept():
         h = rr.Handle(op, mus[0], cfg["k"], "gaussian", seed=seed, precision=cfg["precision"],
-                      max_rhs=cfg["nrhs"], keep_sketch=True)
+                      max_rhs=cfg["nrhs"], keep_sketch=2 if args.joint else 1)
         its = []
         for i, mu in enumerate(mus):
             if i > 0:
@@ -911,7 +913,8 @@ def run_shift_path(args):
     ms = max_over_ranks(sum(ms_kept), world) / args.steps
     line = _line(args, world, "RandRAND-PCG shifts solved/s along a regularization path (sketch kept)",
                  world * len(mus) * 1000.0 / ms, "solves/s", ms,
-                 {**cfg, "parallelism": f"replicas x{world}", "l2": "inputs of a path exceed L2"},
+                 {**cfg, "recycling": "joint basis" if args.joint else "Gram separation",
+                  "parallelism": f"replicas x{world}", "l2": "inputs of a path exceed L2"},
                  fresh_builds={"value": len(mus) * 1000.0 / (sum(ms_fresh) / len(ms_fresh)),
                                "unit": "solves/s", "ms_per_path": sum(ms_fresh) / len(ms_fresh)},
                  solve={"inner_iters_max_per_shift": its, "fresh_inner_iters_max_per_shift": its_fresh},
