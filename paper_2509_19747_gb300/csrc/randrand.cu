@@ -169,8 +169,9 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
   if (o.max_rhs < 1 || o.max_rhs > 8) return RR_ERR_INVALID_ARG;
   if (o.variant != RR_VARIANT_C && o.variant != RR_VARIANT_R && o.variant != RR_VARIANT_G)
     return RR_ERR_INVALID_ARG;
-  // G-RandRAND works with an explicit basis (its Pi~ needs Q)
-  if (o.variant == RR_VARIANT_G && uses_alg3(o)) return RR_ERR_UNSUPPORTED;
+  // G-RandRAND with Alg. 3: only in the basis-less CSR form (Q applied as
+  // A_mu Omega R^-1), not with an explicit basis
+  if (o.variant == RR_VARIANT_G && uses_alg3(o) && !basis_less(*A, o)) return RR_ERR_UNSUPPORTED;
   if (o.precision < RR_PREC_FP64 || o.precision > RR_PREC_MIXED) return RR_ERR_INVALID_ARG;
   if (o.orth != RR_ORTH_CHOLQR2 && o.orth != RR_ORTH_RAND_CHOLQR) return RR_ERR_INVALID_ARG;
   if (o.gamma < 1 || o.gamma > kMaxGammaHost) return RR_ERR_INVALID_ARG;
@@ -179,13 +180,15 @@ rr_status validate(const rr_operator* A, int32_t k, const rr_build_opts& o) {
     const int64_t l = o.l_sk > 0 ? o.l_sk : 4 * (int64_t)k;
     if (l < k || l > (int64_t)INT32_MAX / 2 || o.gamma_sk > l) return RR_ERR_INVALID_ARG;
     if (basis_less(*A, o)) {
-      // variants C and R: Q^T x = R^-T Omega^T A_mu x and Q s = A_mu Omega
-      // R^-1 s; G-RandRAND's estimates use the basis itself
-      if (o.variant == RR_VARIANT_G) return RR_ERR_UNSUPPORTED;
+      // Q^T x = R^-T Omega^T A_mu x and Q s = A_mu Omega R^-1 s for every
+      // variant (G-RandRAND's P = I + Q (tau G - I) Q^T has the C form)
       // the implicit Q applies Omega from its sparse pattern (q = 0 only)
       if (o.q != 0) return RR_ERR_UNSUPPORTED;
       // Omega^T v partials and Omega s stage k x m values in shared memory
       if ((size_t)k * pad_mp(o.max_rhs) * (uses_f64(o) ? 8 : 4) > 200 * 1024) return RR_ERR_UNSUPPORTED;
+      // G-RandRAND's MINRES keeps its preconditioner temporaries (2 n x m) in
+      // the unused n x k basis array
+      if (o.variant == RR_VARIANT_G && k < 2 * pad_mp(o.max_rhs)) return RR_ERR_UNSUPPORTED;
     }
   }
   if (o.power_iters < 1 || o.power_iters > 1000) return RR_ERR_INVALID_ARG;
@@ -1055,6 +1058,52 @@ rr_status power_iterations_implicit(rr_handle* h) {
   return RR_OK;
 }
 
+// The power iterations of power_iterations_G() with the basis-less Q:
+//   column 0: v -> A_mu (I - Pi) A_mu v          (|(I - Pi) A_mu|^2)
+//   column 1: v -> A_mu Q G^2 Q^T A_mu v         (|Pi~ A_mu|^2)
+// With u = A_mu v and g = Omega^T A_mu u: (I - Pi) u = u + A_mu Omega (-Cinv g)
+// and Q G^2 Q^T u = A_mu Omega G2b g, Cinv = R^-1 R^-T, G2b = (R^-1 G)(R^-1 G)^T.
+template <typename T>
+rr_status power_iterations_G_implicit(rr_handle* h) {
+  const int64_t n = h->n;
+  const int mp = h->mp, k = h->k;
+  cudaStream_t st = h->st;
+  T* Vv = vt<T>(h, kV);
+  T* Uv = vt<T>(h, kU);
+  T* Wv = vt<T>(h, kW);
+  T* Zv = vt<T>(h, kZ);
+  T* Av = vt<T>(h, kP);
+  T* Bv = vt<T>(h, kR);
+  double* G2b = h->kk[kH];   // H (explicit-basis form) is not used without a basis
+  gemm_nn<double>(k, k, k, 1.0, h->kk[kRinv], k, h->kk[kG], k, 0.0, nullptr, 0, h->kk[kTm], k, st);
+  transpose_kxk(h->kk[kTm], h->kk[kScA], k, st);
+  gemm_nn<double>(k, k, k, 1.0, h->kk[kTm], k, h->kk[kScA], k, 0.0, nullptr, 0, G2b, k, st);
+  RR_CUDA_TRY(cudaMemsetAsync(Vv, 0, (size_t)n * mp * sizeof(T), st));
+  gen_power_start<T>(Vv, n, mp, 0, 0, h->seed, st);
+  gen_power_start<T>(Vv, n, mp, 1, 1, h->seed, st);
+  dot_cols<T>(Vv, Vv, n, mp, kModeNorm, h->rpart, h->cnt, h->cs, false, nullptr, st);
+  scale_cols<T>(Vv, Vv, n, mp, h->cs, st);
+  const Coefs8 keep0 = coefs(1.0, 0.0);
+  for (int it = 0; it < h->o.power_iters; ++it) {
+    amul<T>(h, Vv, nullptr, nullptr, Wv, false, ev_take(h, RR_PROF_POWER));   // u = A_mu v
+    amul<T>(h, Wv, nullptr, nullptr, Av, false);
+    omega_t<T>(h, Av, h->t[0], false);                                          // g
+    kxk_apply(h->kk[kCinv], h->t[0], k, mp, coefs_all(0.0), coefs(-1.0, 0.0), h->t[1], st);
+    kxk_apply(G2b, h->t[0], k, mp, coefs_all(0.0), coefs(0.0, 1.0), h->t[2], st);
+    axpby<double, double, double>(h->t[1], coefs_all(1.0), h->t[2], coefs_all(1.0), h->t[1], k, mp,
+                                  st);
+    omega_mul<T>(h, h->t[1], Bv, false);
+    amul<T>(h, Bv, Wv, keep0.v, Uv, false);                     // (I - Pi) u | Q G^2 Q^T u
+    amul<T>(h, Uv, nullptr, nullptr, Zv, false, ev_take(h, RR_PROF_POWER));
+    dot_cols<T>(Zv, Zv, n, mp, kModeNorm, h->rpart, h->cnt, h->cs, false, nullptr, st);
+    scale_cols<T>(Zv, Vv, n, mp, h->cs, st);
+  }
+  RR_TRY(read_cs(h));
+  h->normE = std::sqrt(h->cs_host[0].lam);
+  h->lam_max = std::sqrt(h->cs_host[1].lam);
+  return RR_OK;
+}
+
 // Variant R without a basis (Sec. 4.2 with Alg. 4): with Q^T x = R^-T g_x,
 // g_x = Omega^T A_mu x, and Q s = A_mu Omega R^-1 s, Pi x = A_mu Omega Cinv g_x
 // (Cinv = R^-1 R^-T), so B x = (I - Pi) A_mu (I - Pi) x + tau Pi x =
@@ -1386,7 +1435,8 @@ rr_status finish_build(rr_handle* h, const double* G1given, bool have_qr) {
     if (h->o.variant == RR_VARIANT_R)
       RR_CUDA_TRY(cudaMemsetAsync(h->kk[kG], 0, (size_t)k * k * 8, st));
     implicit_core(h);
-    RR_TRY(power_iterations_implicit<T>(h));
+    if (h->o.variant == RR_VARIANT_G) RR_TRY(power_iterations_G_implicit<T>(h));
+    else RR_TRY(power_iterations_implicit<T>(h));
   } else if (h->o.variant == RR_VARIANT_G) {
     RR_TRY(power_iterations_G<T>(h));
   } else {
@@ -1668,6 +1718,32 @@ void iter_R_implicit(rr_handle* h, const cudaEvent_t* ev) {
 // - (gamma / gamma_prev) v_prev, z = P v_next and gamma_next = (v^T z)^(1/2)
 // with the rotation in the last block, then the direction and x updates and
 // zs = z / gamma_next.  All vectors keep their buffers (shifts are in place).
+// z = P r for MINRES with G-RandRAND, P = I + Q (tau G - I) Q^T, and the
+// reduction `mode` of r^T z.  Basis-less: Q (tau G - I) Q^T r = A_mu Omega
+// Hb Omega^T A_mu r with Hb = R^-1 (tau G - I) R^-T (the C variant's form);
+// its two n x m temporaries live in the basis region, unused without a
+// basis, since MINRES holds all eight iteration vectors.
+template <typename T>
+void precond_G(rr_handle* h, const T* Rv, T* Zv, int mode) {
+  if (!h->implicit) {
+    precond_C<T>(h, Rv, Zv, mode);
+    return;
+  }
+  const int64_t n = h->n;
+  const int mp = h->mp;
+  // the basis region (h->Q is null without a basis; the build's W, which it
+  // held, is not needed once R is formed); validate() ensures k >= 2 mp
+  T* U = reinterpret_cast<T*>(h->ws + h->L.off[R_Q]);
+  T* V = U + n * mp;
+  amul<T>(h, Rv, nullptr, nullptr, U, false, nullptr);
+  omega_t<T>(h, U, h->t[0], false);
+  kxk_apply(h->kk[kHb], h->t[0], h->k, mp, coefs_all(0.0), coefs_all(1.0), h->t[1], h->st);
+  omega_mul<T>(h, h->t[1], V, false);
+  const Coefs8 one = coefs_all(1.0);
+  amul<T>(h, V, Rv, one.v, Zv, false);
+  dot_cols<T>(Rv, Zv, n, mp, mode, h->rpart, h->cnt, h->cs, false, nullptr, h->st);
+}
+
 template <typename T>
 void iter_G(rr_handle* h, const cudaEvent_t* ev) {
   const int64_t n = h->n;
@@ -1684,7 +1760,7 @@ void iter_G(rr_handle* h, const cudaEvent_t* ev) {
   matvec<T>(h, Zs, Az, ev);
   dot_cols<T>(Az, Zs, n, mp, kModeMrDelta, h->rpart, h->cnt, h->cs, true, nullptr, st);
   minres_v<T>(Az, Vv, Vp, n, mp, h->cs, st);
-  precond_C<T>(h, Vv, Zv, kModeMrGamma);
+  precond_G<T>(h, Vv, Zv, kModeMrGamma);
   minres_w<T>(Zs, Zv, Wv, Wp, Ev, n, mp, h->cs, st);
 }
 
@@ -1694,6 +1770,7 @@ void iter_any(rr_handle* h, const cudaEvent_t* ev) {
   h->op.gate = h->cs;
   h->op.gate_mp = h->mp;
   if (h->implicit && h->o.variant == RR_VARIANT_R) iter_R_implicit<T>(h, ev);
+  else if (h->implicit && h->o.variant == RR_VARIANT_G) iter_G<T>(h, ev);
   else if (h->implicit) iter_C_implicit<T>(h, ev);
   else if (h->o.variant == RR_VARIANT_C) iter_C<T>(h, ev);
   else if (h->o.variant == RR_VARIANT_G) iter_G<T>(h, ev);
@@ -1916,7 +1993,7 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
       RR_CUDA_TRY(cudaMemsetAsync(vt<T>(h, kP), 0, vb, st));
       RR_CUDA_TRY(cudaMemsetAsync(vt<T>(h, kU), 0, vb, st));
       RR_CUDA_TRY(cudaMemsetAsync(vt<T>(h, kV), 0, vb, st));
-      precond_C<T>(h, Rv, vt<T>(h, kZ), kModeMrInit);
+      precond_G<T>(h, Rv, vt<T>(h, kZ), kModeMrInit);
       minres_zs<T>(vt<T>(h, kZ), vt<T>(h, kS), n, mp, h->cs, st);
     } else {
       p_update<T>(vt<T>(h, kP), Rv, n, mp, h->cs, true, st);

@@ -184,11 +184,50 @@ def test_basis_less_variant_R_mixed(cuda_lib):
     assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), b) <= 1e-6)
 
 
-def test_basis_less_variant_G_unsupported(cuda_lib):
+def csr_indefinite(side, seed, after=30):
+    """A CSR diffusion operator and a shift between its (after+1)-th and
+    (after+2)-th largest eigenvalues, so A_mu is indefinite."""
+    C, op, vals = csr_problem(side, seed)
+    ev = np.sort(np.linalg.eigvalsh(op.matmat(np.eye(C.n))))[::-1]
+    return C, op, vals, -0.5 * (ev[after] + ev[after + 1])
+
+
+@pytest.mark.parametrize("sketch", ["sparse_sign", "srht", "multilevel"])
+def test_basis_less_variant_G_fp64(cuda_lib, sketch):
+    """Basis-less G-RandRAND (Sec. 3.3 eq:g_randrand with the Q of Sec. 4.2:
+    P = I + A_mu Omega R^-1 (tau G - I) R^-T Omega^T A_mu) on an indefinite
+    CSR system: R, G, the two norm estimates and tau equal the oracle's Alg. 3
+    build with its explicit Q; restarted MINRES reaches the float64 residual
+    target."""
+    rr = cuda_lib
+    C, op, vals, mu = csr_indefinite(24, 47)
+    k = 40
+    h = csr_handle(rr, C, vals, mu, k, sketch, 47, variant="G", max_rhs=2)
+    bd = O.build(op, mu, k, sketch, seed=47, orth="qless", variant="G")
+    cond = np.linalg.cond(bd.R)
+    assert rel(h.export("R").cpu().numpy(), bd.R) <= max(1e-12, 1e-15 * cond) * 100
+    assert rel(h.export("G").cpu().numpy(), bd.G) <= 1e-9
+    tau, nE, lmax = h.scalars()
+    assert nE == pytest.approx(bd.normE, rel=1e-7)
+    assert lmax == pytest.approx(bd.lam_max, rel=1e-7)
+    assert tau == pytest.approx(bd.tau, rel=1e-7)
+    b = W.gaussian_rhs(C.n, 2, 47)
+    x, status, infos = h.solve(dev(b), rtol=1e-10)
+    assert status == rr.RR_OK
+    assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), b) <= 1e-10)
+    # the same number of MINRES steps as the oracle's restarted MINRES, to a few
+    _, oinfos = O.solve(bd, b, rtol=1e-10)
+    for gi, oi in zip(infos, oinfos):
+        assert abs(gi["inner_iters"] - oi.inner_iters) <= max(3, oi.inner_iters // 20)
+
+
+def test_basis_less_variant_G_needs_room(cuda_lib):
+    """The basis-less MINRES keeps two n x m temporaries in the n x k basis
+    array: k < 2 m is rejected."""
     rr = cuda_lib
     C, op, vals = csr_problem(16, 45)
     with pytest.raises(rr.RandRandError):
-        csr_handle(rr, C, vals, 1e-4, 8, "sparse_sign", 45, variant="G")
+        csr_handle(rr, C, vals, -1e-2, 8, "sparse_sign", 45, variant="G", max_rhs=8)
 
 
 def test_sparse_operator_full_size(cuda_lib):
