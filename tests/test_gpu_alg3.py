@@ -223,6 +223,21 @@ def test_basis_less_variant_G_fp64(cuda_lib, sketch):
         assert abs(gi["inner_iters"] - oi.inner_iters) <= max(3, oi.inner_iters // 5)
 
 
+def test_basis_less_variant_G_mixed(cuda_lib):
+    """Basis-less G-RandRAND with float32 iterations and float64 restart
+    residuals on an indefinite float32 CSR system: restarted MINRES meets
+    rtol 1e-6 with the float64 residual as the judge."""
+    rr = cuda_lib
+    C, op, _, mu = csr_indefinite(24, 48)
+    vals32 = dev(C.vals.astype(np.float32))
+    h = csr_handle(rr, C, vals32, mu, 40, "sparse_sign", 48, variant="G", precision="mixed",
+                   max_rhs=4)
+    b = W.gaussian_rhs(C.n, 4, 48)
+    x, status, infos = h.solve(dev(b), rtol=1e-6, maxit=20000)
+    assert status == rr.RR_OK
+    assert np.all(O.true_rel_residual(op, mu, x.cpu().numpy(), b) <= 1e-6)
+
+
 def test_basis_less_variant_G_needs_room(cuda_lib):
     """The basis-less MINRES keeps two n x m temporaries in the n x k basis
     array: k < 2 m is rejected."""
