@@ -1,13 +1,14 @@
-// Float32 right multiplication out = X M (X: n x k row-major, M: k x k) on
+// Float32 right multiplication out = X M (X: n x K row-major, M: K x N) on
 // the 5th-generation tensor cores, the n x k x k products of the basis
-// construction (Q1 = Y R1^-1, Q = Q1 R2^-1, W = Y R_sk^-1, QH = Q H).
+// construction (Q1 = Y R1^-1, Q = Q1 R2^-1, W = Y R_sk^-1, QH = Q H) and the
+// n x 2k x k product Q = Q_joint Q_red of the joint basis.
 //
 // Three-term TF32 split ("3xTF32"): every float32 x is written as
 // x = hi + lo with hi = RN_tf32(x) and lo = x - hi (exact), and
 //   X M = X_hi M_hi + X_hi M_lo + X_lo M_hi   (+ X_lo M_lo, below 2^-22),
 // so each product term has float32-level accuracy and the sums are float32
 // tensor-core accumulations, as in the float32 CUDA-core GEMM.  M is split
-// once per call into M^T hi and lo (k x k, K-major rows) in scratch; X tiles
+// once per call into M^T hi and lo (N x K, K-major rows) in scratch; X tiles
 // are split in shared memory as they arrive.
 //
 // One CTA per 128 x 256 output tile (MMA M = 128 rows in TMEM lanes,
@@ -52,13 +53,13 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float(r);
 }
 
-// Mt_hi[j][i] + Mt_lo[j][i] = (float)M[i][j]   (k x k, row-major)
-__global__ void k_split_mt(const double* __restrict__ M, int k, float* __restrict__ hi,
+// Mt_hi[j][i] + Mt_lo[j][i] = (float)M[i][j]   (M: K x N row-major, Mt: N x K)
+__global__ void k_split_mt(const double* __restrict__ M, int K, int N, float* __restrict__ hi,
                            float* __restrict__ lo) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)k * k) return;
-  const int j = (int)(e / k), i = (int)(e % k);
-  const float x = (float)M[(int64_t)i * k + j];
+  if (e >= (int64_t)K * N) return;
+  const int j = (int)(e / K), i = (int)(e % K);
+  const float x = (float)M[(int64_t)i * N + j];
   const float h = tf32_rn(x);
   hi[e] = h;
   lo[e] = x - h;
@@ -68,7 +69,7 @@ __global__ void k_split_mt(const double* __restrict__ M, int k, float* __restric
 // (rows beyond n or k and K beyond k read as zero)
 __global__ void __launch_bounds__(kGThreads, 1)
     k_gemm_tf32x3(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap hmap,
-                  const __grid_constant__ CUtensorMap lmap, int64_t n, int k,
+                  const __grid_constant__ CUtensorMap lmap, int64_t n, int K, int N,
                   float* __restrict__ out, int64_t ldo, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = (int64_t)blockIdx.y * kGM;
   const int n0 = blockIdx.x * kGN;
-  const int nk = (k + kGK - 1) / kGK;
+  const int nk = (K + kGK - 1) / kGK;
   constexpr uint32_t idesc = make_idesc(kFmtTF32, kGM, kGN);
 
   if (threadIdx.x == 0) {
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     if (ok) {
       fence_after();
       const int64_t gi = m0 + r;
-      const int ncols = (k - n0 < kGN) ? k - n0 : kGN;   // k % 4 == 0
+      const int ncols = (N - n0 < kGN) ? N - n0 : kGN;   // N % 4 == 0
 #pragma unroll 1
       for (int c0 = 0; c0 < kGN; c0 += 32) {
         uint32_t v[32];
@@ -203,11 +204,13 @@ __global__ void __launch_bounds__(kGThreads, 1)
 }  // namespace
 
 // out = X M on the tensor cores; false (nothing launched) when the shapes or
-// alignments do not fit the tensor maps (k a multiple of 4, 16-byte aligned
-// X and out rows, ldx = ldo = k).  scratch: 2 k^2 floats.
-bool gemm_right_tf32x3(const float* X, int64_t n, int k, const double* M, float* scratch,
+// alignments do not fit the tensor maps (K and N multiples of 4, 16-byte
+// aligned X and out, ldx = K, ldo = N, M row-major K x N).  scratch: 2 K N
+// floats.
+bool gemm_right_tf32x3(const float* X, int64_t n, int K, int N, const double* M, float* scratch,
                        float* out, int* err, cudaStream_t st) {
-  if (n < 1 || k < 4 || k % 4 != 0 || n > (int64_t)INT32_MAX - kGM) return false;
+  if (n < 1 || K < 4 || N < 4 || K % 4 != 0 || N % 4 != 0 || n > (int64_t)INT32_MAX - kGM)
+    return false;
   if (((uintptr_t)X % 16) || ((uintptr_t)out % 16) || ((uintptr_t)scratch % 16)) return false;
   static std::atomic<uint64_t> attr_done{0};
   if (!once_per_device(attr_done, [] {
@@ -216,15 +219,15 @@ bool gemm_right_tf32x3(const float* X, int64_t n, int k, const double* M, float*
       }))
     return false;
   float* hi = scratch;
-  float* lo = scratch + (int64_t)k * k;
+  float* lo = scratch + (int64_t)K * N;
   CUtensorMap xmap, hmap, lmap;
-  if (!tc_encode_2d(&xmap, false, X, (uint64_t)k, (uint64_t)n, kGK, kGM) ||
-      !tc_encode_2d(&hmap, false, hi, (uint64_t)k, (uint64_t)k, kGK, kGN) ||
-      !tc_encode_2d(&lmap, false, lo, (uint64_t)k, (uint64_t)k, kGK, kGN))
+  if (!tc_encode_2d(&xmap, false, X, (uint64_t)K, (uint64_t)n, kGK, kGM) ||
+      !tc_encode_2d(&hmap, false, hi, (uint64_t)K, (uint64_t)N, kGK, kGN) ||
+      !tc_encode_2d(&lmap, false, lo, (uint64_t)K, (uint64_t)N, kGK, kGN))
     return false;
-  k_split_mt<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(M, k, hi, lo);
-  dim3 grid((unsigned)cdiv(k, kGN), (unsigned)cdiv(n, kGM));
-  k_gemm_tf32x3<<<grid, kGThreads, gemm_smem_bytes(), st>>>(xmap, hmap, lmap, n, k, out, k, err);
+  k_split_mt<<<(unsigned)cdiv((int64_t)K * N, 256), 256, 0, st>>>(M, K, N, hi, lo);
+  dim3 grid((unsigned)cdiv(N, kGN), (unsigned)cdiv(n, kGM));
+  k_gemm_tf32x3<<<grid, kGThreads, gemm_smem_bytes(), st>>>(xmap, hmap, lmap, n, K, N, out, N, err);
   return cudaPeekAtLastError() == cudaSuccess;
 }
 

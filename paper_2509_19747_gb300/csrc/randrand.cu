@@ -537,7 +537,7 @@ template <typename T>
 void right_mult(rr_handle* h, const T* X, const double* Mkk, T* out) {
   // out = X Mkk  (n x k times k x k), Mkk converted to the working type;
   // float32 on the tensor cores (3xTF32) where the tensor maps allow it
-  if (sizeof(T) == 4 && gemm_right_tf32x3((const float*)X, h->n, h->k, Mkk, (float*)h->kkT,
+  if (sizeof(T) == 4 && gemm_right_tf32x3((const float*)X, h->n, h->k, h->k, Mkk, (float*)h->kkT,
                                           (float*)out, h->dstatus + 8, h->st))
     return;
   const T* Mt;
@@ -1613,15 +1613,20 @@ rr_status joint_finish(rr_handle* h) {
   // F again (sketch_qr_R overwrote S), Q_red = F R^-1 into S2
   axpby<double, double, double>(C1, coefs_all(1.0), C2, coefs_all(mu), h->S, 2 * kk2, 1, st);
   gemm_nn<double>(2 * k, k, k, 1.0, h->S, k, h->kk[kRinv], k, 0.0, nullptr, 0, h->S2, k, st);
-  const T* Qred;
-  if (sizeof(T) == 8) {
-    Qred = reinterpret_cast<const T*>(h->S2);
-  } else {
-    convert<double, float>(h->S2, (float*)h->kkT, 2 * kk2, st);   // kkT holds 2 k^2 floats
-    Qred = reinterpret_cast<const T*>(h->kkT);
+  // Q = Q_joint Q_red into the buffer that is not the free one (QH takes
+  // h->Y later): float32 on the tensor cores (scratch: S, 2 (2k) k floats)
+  if (!(sizeof(T) == 4 && gemm_right_tf32x3((const float*)h->Qj, n, 2 * k, k, h->S2,
+                                            reinterpret_cast<float*>(h->S), (float*)h->Q,
+                                            h->dstatus + 8, st))) {
+    const T* Qred;
+    if (sizeof(T) == 8) {
+      Qred = reinterpret_cast<const T*>(h->S2);
+    } else {
+      convert<double, float>(h->S2, (float*)h->kkT, 2 * kk2, st);   // kkT holds 2 k^2 floats
+      Qred = reinterpret_cast<const T*>(h->kkT);
+    }
+    gemm_nn<T>(n, k, 2 * k, 1.0, (const T*)h->Qj, 2 * k, Qred, k, 0.0, nullptr, 0, (T*)h->Q, k, st);
   }
-  // Q into the buffer that is not the free one (QH takes h->Y later)
-  gemm_nn<T>(n, k, 2 * k, 1.0, (const T*)h->Qj, 2 * k, Qred, k, 0.0, nullptr, 0, (T*)h->Q, k, st);
   axpby<double, double, double>(h->kk[kM0], coefs_all(1.0), h->kk[kS0], coefs_all(mu), h->kk[kM],
                                 kk2, 1, st);
   return finish_build<T>(h, nullptr, true);

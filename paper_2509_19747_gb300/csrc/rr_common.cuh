@@ -254,11 +254,11 @@ void prepare_mv_tc(const OpDev& op, float* Aaug, float* Baug, cudaStream_t st);
 bool encode_mv_tc(const float* Aaug, const float* Baug, int64_t n, void* amap, void* bmap);
 int mv_tc_nsplit(int64_t n);
 int64_t tc_persistent_ctas(int64_t total);
-// out = X M (n x k float32 times a k x k float64 matrix rounded to float32)
-// on the tensor cores with the 3xTF32 split; false (nothing launched) when k
-// is not a multiple of 4 or a pointer is not 16-byte aligned.  scratch: 2 k^2
-// floats; err: set on a wait that timed out
-bool gemm_right_tf32x3(const float* X, int64_t n, int k, const double* M, float* scratch,
+// out = X M (n x K float32 times a K x N float64 matrix rounded to float32;
+// ldx = K, ldo = N) on the tensor cores with the 3xTF32 split; false
+// (nothing launched) when K or N is not a multiple of 4 or a pointer is not
+// 16-byte aligned.  scratch: 2 K N floats; err: set on a wait that timed out
+bool gemm_right_tf32x3(const float* X, int64_t n, int K, int N, const double* M, float* scratch,
                        float* out, int* err, cudaStream_t st);
 bool tc_encode_2d(void* map, bool bf16, const void* base, uint64_t inner, uint64_t outer,
                   uint32_t box_inner, uint32_t box_outer);
