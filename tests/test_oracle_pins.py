@@ -400,6 +400,30 @@ def test_qless_R_matches_householder():
     assert np.linalg.cond(O.right_solve_upper(Ymu, Rsk)) < 10
 
 
+def test_qless_G_variant_matches_householder_on_indefinite_csr():
+    """G-RandRAND through Alg. 3 (the oracle route the basis-less GPU form is
+    compared with) equals the Householder route on an indefinite CSR system:
+    the same unique R, the same G = (R^-T Omega^T Omega R^-1)^(1/2), the two
+    norm estimates and tau; and P is symmetric positive definite."""
+    C = W.diffusion_csr(side=16, seed=11, corr_len=4.0)
+    op = O.CsrOp(C.rowptr, C.colidx, C.vals, C.n)
+    A = op.matmat(np.eye(C.n))
+    ev = np.sort(np.linalg.eigvalsh(A))[::-1]
+    mu = -0.5 * (ev[20] + ev[21])                       # A_mu indefinite
+    k = 30
+    hq = O.build(op, mu, k, "sparse_sign", seed=11, variant="G", orth="qless")
+    hh = O.build(op, mu, k, "sparse_sign", seed=11, variant="G", orth="householder")
+    c = np.linalg.cond(hh.R)
+    assert np.linalg.norm(hq.R - hh.R) <= 1e3 * c * 1e-16 * np.linalg.norm(hh.R)
+    assert np.allclose(hq.G, hh.G, rtol=0, atol=1e-9 * np.abs(hh.G).max())
+    assert hq.normE == pytest.approx(hh.normE, rel=1e-8)
+    assert hq.lam_max == pytest.approx(hh.lam_max, rel=1e-8)
+    assert hq.tau == pytest.approx(hh.tau, rel=1e-8)
+    Pm = hq.apply_P(np.eye(C.n))
+    assert np.allclose(Pm, Pm.T, atol=1e-10)
+    assert np.linalg.eigvalsh(0.5 * (Pm + Pm.T)).min() > 0
+
+
 # --------------------------------------------------------------------------
 # Lemma thm:apriori_gen00: expected projection error with l = 2k+2
 # --------------------------------------------------------------------------
