@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int64_t M, int64_t N, int64_t K
 // of 16 staged k-major in shared memory so that a step costs three 128-bit
 // shared loads per 32 FMAs, the next step's global loads held in registers
 // while the current one is computed.  Used when the leading dimensions and
-// the widths are multiples of 4 (16-byte vectors).
+// the widths are multiples of 4 (16-byte vectors) or, with two 8-byte loads
+// per vector (VW = 2), multiples of 2.
 // ======================================================================
 constexpr int kSgM = 64, kSgN = 128, kSgK = 16;
 constexpr int kSgFold = 256;   // rows summed in float32 before a fold
@@ -109,11 +110,23 @@ __device__ __forceinline__ void sg_step(const float (*As)[kSgM], const float (*B
   }
 }
 
-__device__ __forceinline__ float4 ld4_or_zero(const float* p, bool ok) {
-  return ok ? *reinterpret_cast<const float4*>(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+// four consecutive floats at column `col` of a row of width `width` (zero
+// where outside): one 16-byte load (VW = 4, width a multiple of 4) or two
+// 8-byte loads (VW = 2, width a multiple of 2)
+template <int VW>
+__device__ __forceinline__ float4 ld4v(const float* p, bool row_ok, int64_t col, int64_t width) {
+  if (VW == 4)
+    return (row_ok && col < width) ? *reinterpret_cast<const float4*>(p)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float2 lo = (row_ok && col < width) ? *reinterpret_cast<const float2*>(p)
+                                            : make_float2(0.f, 0.f);
+  const float2 hi = (row_ok && col + 2 < width) ? *reinterpret_cast<const float2*>(p + 2)
+                                                : make_float2(0.f, 0.f);
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
 // C = alpha A B + beta D (A: M x K, B: K x N, row-major)
+template <int VW>
 __global__ void __launch_bounds__(256) k_sgemm_nn(int64_t M, int64_t N, int64_t K, float alpha,
                                                   const float* __restrict__ A, int64_t lda,
                                                   const float* __restrict__ B, int64_t ldb,
@@ -129,9 +142,9 @@ __global__ void __launch_bounds__(256) k_sgemm_nn(int64_t M, int64_t N, int64_t 
   const int br = tid / 32, bc = (tid % 32) * 4;
   float4 ra, rb0, rb1;
   auto load = [&](int64_t k0) {
-    ra = ld4_or_zero(A + (m0 + ar) * lda + k0 + ac, m0 + ar < M && k0 + ac < K);
-    rb0 = ld4_or_zero(B + (k0 + br) * ldb + n0 + bc, k0 + br < K && n0 + bc < N);
-    rb1 = ld4_or_zero(B + (k0 + 8 + br) * ldb + n0 + bc, k0 + 8 + br < K && n0 + bc < N);
+    ra = ld4v<VW>(A + (m0 + ar) * lda + k0 + ac, m0 + ar < M, k0 + ac, K);
+    rb0 = ld4v<VW>(B + (k0 + br) * ldb + n0 + bc, k0 + br < K, n0 + bc, N);
+    rb1 = ld4v<VW>(B + (k0 + 8 + br) * ldb + n0 + bc, k0 + 8 + br < K, n0 + bc, N);
   };
   auto store = [&](int buf) {
     As[buf][ac + 0][ar] = ra.x;
@@ -169,13 +182,18 @@ __global__ void __launch_bounds__(256) k_sgemm_nn(int64_t M, int64_t N, int64_t 
       float4 v = make_float4(alpha * acc[x][4 * h], alpha * acc[x][4 * h + 1],
                              alpha * acc[x][4 * h + 2], alpha * acc[x][4 * h + 3]);
       if (D) {
-        const float4 d = *reinterpret_cast<const float4*>(D + gi * ldd + gj);
+        const float4 d = ld4v<VW>(D + gi * ldd + gj, true, gj, N);
         v.x = fmaf(beta, d.x, v.x);
         v.y = fmaf(beta, d.y, v.y);
         v.z = fmaf(beta, d.z, v.z);
         v.w = fmaf(beta, d.w, v.w);
       }
-      *reinterpret_cast<float4*>(C + gi * ldc + gj) = v;
+      if (VW == 4) {
+        *reinterpret_cast<float4*>(C + gi * ldc + gj) = v;
+      } else {
+        *reinterpret_cast<float2*>(C + gi * ldc + gj) = make_float2(v.x, v.y);
+        if (gj + 2 < N) *reinterpret_cast<float2*>(C + gi * ldc + gj + 2) = make_float2(v.z, v.w);
+      }
     }
   }
 }
@@ -184,6 +202,7 @@ __global__ void __launch_bounds__(256) k_sgemm_nn(int64_t M, int64_t N, int64_t 
 // products summed in float32 over blocks of 256 rows, each block folded into
 // double-float accumulators (float32 two-sums; float64 adds run at a small
 // fraction of the float32 rate here), written as float64
+template <int VW>
 __global__ void __launch_bounds__(256) k_sgram(const float* __restrict__ A, int64_t lda,
                                                const float* __restrict__ B, int64_t ldb,
                                                int64_t nrows, int k1, int k2, int symmetric,
@@ -201,9 +220,9 @@ __global__ void __launch_bounds__(256) k_sgram(const float* __restrict__ A, int6
   const int br = tid / 32, bc = (tid % 32) * 4;
   float4 ra, rb0, rb1;
   auto load = [&](int64_t r) {
-    ra = ld4_or_zero(A + (r + ar) * lda + i0 + ac, r + ar < r1 && i0 + ac < k1);
-    rb0 = ld4_or_zero(B + (r + br) * ldb + j0 + bc, r + br < r1 && j0 + bc < k2);
-    rb1 = ld4_or_zero(B + (r + 8 + br) * ldb + j0 + bc, r + 8 + br < r1 && j0 + bc < k2);
+    ra = ld4v<VW>(A + (r + ar) * lda + i0 + ac, r + ar < r1, i0 + ac, k1);
+    rb0 = ld4v<VW>(B + (r + br) * ldb + j0 + bc, r + br < r1, j0 + bc, k2);
+    rb1 = ld4v<VW>(B + (r + 8 + br) * ldb + j0 + bc, r + 8 + br < r1, j0 + bc, k2);
   };
   auto store = [&](int buf) {
     *reinterpret_cast<float4*>(&As[buf][ar][ac]) = ra;
@@ -262,8 +281,10 @@ __global__ void __launch_bounds__(256) k_sgram(const float* __restrict__ A, int6
   }
 }
 
-static bool sg_aligned(const void* p, int64_t ld, int64_t width) {
-  return ((uintptr_t)p % 16) == 0 && ld % 4 == 0 && width % 4 == 0;
+// rows of `width` floats at stride `ld` that the VW-float vector loads of the
+// float32 tiles can read (VW = 4: 16-byte vectors; VW = 2: 8-byte halves)
+static bool sg_aligned(const void* p, int64_t ld, int64_t width, int vw = 4) {
+  return ((uintptr_t)p % (4 * vw)) == 0 && ld % vw == 0 && width % vw == 0;
 }
 
 template <typename T>
@@ -286,11 +307,19 @@ template <typename T>
 void gemm_nn(int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t lda,
              const T* B, int64_t ldb, double beta, const T* D, int64_t ldd, T* C,
              int64_t ldc, cudaStream_t st) {
-  if (sizeof(T) == 4 && sg_aligned(A, lda, K) && sg_aligned(B, ldb, N) && sg_aligned(C, ldc, N) &&
-      (!D || sg_aligned(D, ldd, N))) {
+  for (int vw = 4; vw >= 2 && sizeof(T) == 4; vw -= 2) {
+    if (!(sg_aligned(A, lda, K, vw) && sg_aligned(B, ldb, N, vw) && sg_aligned(C, ldc, N, vw) &&
+          (!D || sg_aligned(D, ldd, N, vw))))
+      continue;
     dim3 grid((unsigned)cdiv(N, kSgN), (unsigned)cdiv(M, kSgM));
-    k_sgemm_nn<<<grid, 256, 0, st>>>(M, N, K, (float)alpha, (const float*)A, lda, (const float*)B,
-                                     ldb, (float)beta, (const float*)D, ldd, (float*)C, ldc);
+    if (vw == 4)
+      k_sgemm_nn<4><<<grid, 256, 0, st>>>(M, N, K, (float)alpha, (const float*)A, lda,
+                                          (const float*)B, ldb, (float)beta, (const float*)D, ldd,
+                                          (float*)C, ldc);
+    else
+      k_sgemm_nn<2><<<grid, 256, 0, st>>>(M, N, K, (float)alpha, (const float*)A, lda,
+                                          (const float*)B, ldb, (float)beta, (const float*)D, ldd,
+                                          (float*)C, ldc);
     return;
   }
   gemm_launch<T>(M, N, K, alpha, A, lda, B, ldb, beta, D, ldd, C, ldc, 0, 0, st);
@@ -421,11 +450,16 @@ static void gram_launch(const T* A, int64_t lda, const T* B, int64_t ldb, int64_
 template <typename T>
 void gram_partial(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t nrows, int k1,
                   int k2, bool symmetric, int nsplit, double* part, cudaStream_t st) {
-  if (sizeof(T) == 4 && sg_aligned(A, lda, k1) && sg_aligned(B, ldb, k2)) {
+  for (int vw = 4; vw >= 2 && sizeof(T) == 4; vw -= 2) {
+    if (!(sg_aligned(A, lda, k1, vw) && sg_aligned(B, ldb, k2, vw))) continue;
     const int64_t rps = cdiv(cdiv(nrows, nsplit), kSgK) * kSgK;
     dim3 grid((unsigned)cdiv(k2, kSgN), (unsigned)cdiv(k1, kSgM), (unsigned)nsplit);
-    k_sgram<<<grid, 256, 0, st>>>((const float*)A, lda, (const float*)B, ldb, nrows, k1, k2,
-                                  symmetric ? 1 : 0, rps, part);
+    if (vw == 4)
+      k_sgram<4><<<grid, 256, 0, st>>>((const float*)A, lda, (const float*)B, ldb, nrows, k1, k2,
+                                       symmetric ? 1 : 0, rps, part);
+    else
+      k_sgram<2><<<grid, 256, 0, st>>>((const float*)A, lda, (const float*)B, ldb, nrows, k1, k2,
+                                       symmetric ? 1 : 0, rps, part);
     return;
   }
   gram_launch<T>(A, lda, B, ldb, nrows, k1, k2, symmetric, nsplit, 0, part, st);
