@@ -5,7 +5,7 @@ oracle built with orth="qless" (same Theta pattern from the same seed).
 Tolerances: float64 factors and iterates 1e-10 relative (the R factor is unique
 once its diagonal is positive; the GPU takes it from a Cholesky QR of the
 sketch S, the oracle from Householder QR, so they agree to u * cond(S));
-low-precision solves are judged by their float64 residual (oracle product).
+low-precision solves are checked by their float64 residual (oracle product).
 """
 import numpy as np
 import pytest
@@ -119,7 +119,7 @@ def test_basis_less_iteration_level_fp64(cuda_lib, sketch, m):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "fp32"])
 def test_basis_less_solve(cuda_lib, precision):
-    """Solves to rtol 1e-6 with the float64 residual as the judge; the float64
+    """Solves to rtol 1e-6 with the float64 residual as the criterion; the float64
     path also reaches the dense Cholesky solution."""
     rr = cuda_lib
     C, op, vals = csr_problem(40, 44, fp64=(precision == "fp64"))
@@ -226,7 +226,7 @@ def test_basis_less_variant_G_fp64(cuda_lib, sketch):
 def test_basis_less_variant_G_mixed(cuda_lib):
     """Basis-less G-RandRAND with float32 iterations and float64 restart
     residuals on an indefinite float32 CSR system: restarted MINRES meets
-    rtol 1e-6 with the float64 residual as the judge."""
+    rtol 1e-6 with the float64 residual as the criterion."""
     rr = cuda_lib
     C, op, _, mu = csr_indefinite(24, 48)
     vals32 = dev(C.vals.astype(np.float32))
@@ -252,7 +252,7 @@ def test_sparse_operator_full_size(cuda_lib):
     float32, log-normal coefficients sigma = 1, correlation length 16),
     mu = 1e-6, k = 256, sparse-sign Omega with 8 nonzeros per row, Alg. 3 with
     l_sk = 1024, basis-less C-RandRAND PCG with float32 iterations and float64
-    refinement to rtol 1e-6.  Judge: the float64 residual of the oracle's
+    refinement to rtol 1e-6.  Criterion: the float64 residual of the oracle's
     product, per column."""
     rr = cuda_lib
     C = W.diffusion_csr(side=512, seed=W.SEED_CSR)
@@ -275,7 +275,7 @@ def test_persistent_basis_less_matches_separate_kernels(cuda_lib, precision):
     (iter_impl 0) and without windows (iter_impl 2), and the separate kernels
     (iter_impl 1) agree: float64 iterates to 1e-10 at a fixed budget (an odd
     one: the window form's r and p end in their second buffers), and all
-    solve to rtol with the float64 residual as the judge."""
+    solve to rtol with the float64 residual as the criterion."""
     rr = cuda_lib
     C, op, vals = csr_problem(40, 46, fp64=(precision == "fp64"))
     mu, k = 1e-6, 32

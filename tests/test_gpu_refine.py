@@ -58,7 +58,7 @@ def test_refined_apply_and_iterates_fp64(cuda_lib, variant, refine):
 def test_refined_kernel_mixed_solve(cuda_lib):
     """bf16 sketch, float32 basis: T differs from I at float32 rounding, the
     refined P from the plain one at about that level; both solves meet rtol
-    with the float64 residual as the judge, in about the same iterations."""
+    with the float64 residual as the criterion, in about the same iterations."""
     rr = cuda_lib
     n, k, mu = 3001, 80, 1e-3
     X = W.mixture_points(n, seed=112)

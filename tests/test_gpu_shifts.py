@@ -58,7 +58,7 @@ def test_set_mu_matches_fresh_builds_fp64(cuda_lib):
 
 def test_set_mu_kernel_mixed(cuda_lib):
     """Gaussian kernel, bf16 tensor-core sketch and float32 iterations: along a
-    shift path each solve meets rtol with the float64 residual as the judge,
+    shift path each solve meets rtol with the float64 residual as the criterion,
     in about the iterations of a fresh build at that shift."""
     rr = cuda_lib
     n, k, seed = 3001, 80, 92
@@ -134,7 +134,7 @@ def test_joint_basis_matches_oracle_fp64(cuda_lib):
 
 def test_joint_basis_kernel_mixed(cuda_lib):
     """Gaussian kernel with float32 iterations: along a shift path the joint
-    basis gives solves that meet rtol with the float64 residual as the judge,
+    basis gives solves that meet rtol with the float64 residual as the criterion,
     and an orthonormal float32 basis whose Q R reproduces Y_mu = A Omega +
     mu Omega of the oracle (same bf16-rounded Omega; the sketch products are
     bf16 tensor-core products, hence 1e-2)."""
