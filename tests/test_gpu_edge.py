@@ -1,7 +1,7 @@
 """Degenerate sizes through every path: one-point and few-point systems,
 k = n, one right-hand side and the maximum of eight, each operator kind,
 variant and test matrix.  The float64 residual of the oracle's product is the
-judge (these systems are too small for iteration counts to mean much)."""
+criterion (these systems are too small for iteration counts to mean much)."""
 import numpy as np
 import pytest
 

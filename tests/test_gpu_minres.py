@@ -1,7 +1,7 @@
 """GPU parity of G-RandRAND MINRES (Sec. 3.3 eq:g_randrand, Sec. 6.3) on
 indefinite shifted systems: factors and estimates against the float64 oracle
 build (same Omega), iterates at fixed budgets against the oracle's restarted
-MINRES, and solves against the exact solution (float64) or judged by the
+MINRES, and solves against the exact solution (float64) or checked by the
 float64 residual (mixed precision, Gaussian kernel)."""
 import numpy as np
 import pytest

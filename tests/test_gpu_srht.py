@@ -1,7 +1,7 @@
 """GPU parity of the SRHT test matrix (Sec. 2, fast randomized transforms):
 Omega bit for bit against the oracle's draw (same Philox streams, same keyed
 Feistel subsampling), float64 factors against the oracle build, a mixed
-precision kernel solve judged by the float64 residual, and the basis-less CSR
+precision kernel solve checked by the float64 residual, and the basis-less CSR
 form, which applies Omega and Omega^T by fast Walsh-Hadamard transforms (one
 shared-memory pass, or two when s exceeds the block)."""
 import numpy as np
