@@ -484,7 +484,7 @@ def roofline(name, stat, clocks):
         # tensor-core float32 kernel product: the exponent arguments come from
         # the tensor cores, so each of the n^2 entries needs exactly one ex2 on
         # the special-function units (MUFU): peak 152 SMs x 32 ex2/clk x clock
-        # (a throughput probe measured 30.2 ex2 per SM per clock on this part)
+        # (a throughput probe measured 31.6 ex2 per SM per clock on this part)
         ops = float(n) * n
         peak = 152 * 32 * f
         return {"kernel": "k_kernel_mv_tc", "bound": "alu", "achieved": ops / avg_s / 1e9,
