@@ -660,6 +660,43 @@ def run_sparse(args):
         torch.cuda.synchronize()
     ms = max_over_ranks(sum(step_ms), world) / args.steps
     infos = [i for _, inf in runs for i in inf]
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the C ABI: every step copies the CSR arrays from
+        # pinned host memory into the operator's device arrays, builds, and
+        # solves with host b and x (randrand_solve_host)
+        hrp, hci, hva = (torch.from_numpy(a).pin_memory() for a in (C.rowptr, C.colidx, C.vals))
+        bh = torch.from_numpy(np.ascontiguousarray(b[:, 0])).pin_memory()
+        xh = torch.zeros_like(bh).pin_memory()
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                rp.copy_(hrp, non_blocking=True)
+                ci.copy_(hci, non_blocking=True)
+                va.copy_(hva, non_blocking=True)
+                h = rr.randrand_build(op.c, cfg["mu"], cfg["k"], rr.SKETCHES[sketch], seed, o,
+                                      ws.data_ptr(), ws_bytes, stream.cuda_stream)
+                st, _ = rr.randrand_solve_host(h, bh.data_ptr(), 1, C.n, xh.data_ptr(), C.n,
+                                               cfg["rtol"], 100000)
+                rr.randrand_free(h)
+                if st != rr.RR_OK:
+                    raise RuntimeError(f"sparse e2e solve failed: {rr.randrand_status_str(st)}")
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        e2e = {"value": world * args.steps / max_over_ranks(sum(ts), world), "unit": "solves/s",
+               "h2d_bytes_per_step": int(C.rowptr.nbytes + C.colidx.nbytes + C.vals.nbytes +
+                                         bh.numel() * bh.element_size()),
+               "d2h_bytes_per_step": int(xh.numel() * xh.element_size())}
     mv = [p["matvec"] for p, _ in prof]
     cnt, tot = sum(c for c, _ in mv), sum(t for _, t in mv)
     # iterations of the profiled pass, whose event times the roofline divides
@@ -703,7 +740,7 @@ def run_sparse(args):
                         "ms_per_iteration": ms / max(i["inner_iters"] for i in infos)},
                  kernels_ms_per_step={kk: sum(p[kk][1] for p, _ in prof) / args.steps
                                       for kk in prof[0][0]},
-                 roofline=roof, clocks=clocks)
+                 roofline=roof, clocks=clocks, e2e=e2e)
     if rank == 0 and not args.no_cpu_baseline:
         # bounded sample: the oracle's build of this system (sparse-sign Omega,
         # basis by Householder QR: its Alg. 3 forms Theta as a dense l_sk x n
