@@ -210,6 +210,35 @@ def test_core_matrix_G_equals_QT_Ainv_Q():
     assert np.linalg.eigvalsh(bd.G).min() > 0
 
 
+def test_nystrom_preconditioner_is_c_randrand_at_mu_zero():
+    # Sec. 1.3: for mu = 0 the Nystrom approximation
+    # A_hat = A Omega (Omega^T A Omega)^-1 Omega^T A equals (Pi A^-1 Pi)^+, so
+    # the Nystrom preconditioner lambda_hat_min A_hat^+ + (I - U U^T), with
+    # (U, Lambda_hat) the nonzero eigenpairs of A_hat, is C-RandRAND with
+    # tau = |Pi A^-1 Pi|^-1.  The Nystrom side here is the textbook route (an
+    # eigendecomposition of A_hat), tau comes from a dense inverse, and
+    # neither uses the oracle's R, G or power iterations.
+    P, op = small_dense(n=140)
+    n, k = op.n, 12
+    A = op.A
+    Om = np.random.default_rng(3).standard_normal((n, k))
+    Y = A @ Om
+    Ahat = Y @ np.linalg.solve(Om.T @ Y, Y.T)
+    w, V = np.linalg.eigh(0.5 * (Ahat + Ahat.T))
+    U, lam = V[:, -k:], w[-k:]
+    assert lam.min() > 1e6 * abs(w[:-k]).max()          # rank k, well separated
+    I = np.eye(n)
+    P_nys = lam.min() * (U / lam) @ U.T + (I - U @ U.T)
+    Qy = np.linalg.qr(Y)[0]
+    Pi = Qy @ Qy.T
+    tau = 1.0 / np.linalg.norm(Pi @ np.linalg.inv(A) @ Pi, 2)
+    bd = O.build(op, 0.0, k, omega=Om, tau=tau)
+    P_c = bd.apply_P(I)
+    assert np.linalg.norm(P_c - P_nys, 2) <= 1e-8 * np.linalg.norm(P_nys, 2)
+    # the same tau through the oracle's own factors: 1 / lambda_max(G)
+    assert tau == pytest.approx(1.0 / np.linalg.eigvalsh(bd.G).max(), rel=1e-8)
+
+
 # --------------------------------------------------------------------------
 # Special cases with closed-form spectra
 # --------------------------------------------------------------------------
