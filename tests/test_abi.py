@@ -172,6 +172,48 @@ def test_refine_option_checks(lib):
     assert e.value.status == lib.RR_ERR_UNSUPPORTED
 
 
+def test_shift_and_variant_G_option_checks(lib):
+    """keep_sketch (Sec. 5.1: 1 = Gram separation, 2 = joint basis) and the
+    basis-less G-RandRAND form are checked on the host, before any launch."""
+    n, k = 100, 10
+    dense = lib.rr_operator(kind=lib.RR_OP_DENSE, dtype=0, n=n, dense=0x1000, ld=n)
+    o = lib.rr_build_opts_default()
+    ws = {}
+    for ks in (0, 1, 2):
+        o.keep_sketch = ks
+        ws[ks] = lib.randrand_workspace_bytes(dense, k, o)
+    # the joint basis keeps Q_joint (n x 2k) beyond what the Gram separation keeps
+    assert ws[2] >= ws[1] + n * 2 * k * 8 and ws[1] > ws[0]
+    for bad in (-1, 3):
+        o.keep_sketch = bad
+        with pytest.raises(lib.RandRandError) as e:
+            lib.randrand_workspace_bytes(dense, k, o)
+        assert e.value.status == lib.RR_ERR_INVALID_ARG
+    for ks in (1, 2):
+        for field, value in (("variant", lib.RR_VARIANT_R), ("orth", lib.RR_ORTH_RAND_CHOLQR),
+                             ("q", 1)):
+            o = lib.rr_build_opts_default()
+            o.keep_sketch = ks
+            setattr(o, field, value)
+            with pytest.raises(lib.RandRandError) as e:
+                lib.randrand_workspace_bytes(dense, k, o)
+            assert e.value.status == lib.RR_ERR_UNSUPPORTED, (ks, field)
+    # G-RandRAND with Alg. 3: only basis-less (CSR), with room for its
+    # MINRES temporaries (2 x padded columns) in the unused basis array
+    g = lib.rr_build_opts_default()
+    g.variant, g.orth = lib.RR_VARIANT_G, lib.RR_ORTH_RAND_CHOLQR
+    with pytest.raises(lib.RandRandError) as e:
+        lib.randrand_workspace_bytes(dense, k, g)
+    assert e.value.status == lib.RR_ERR_UNSUPPORTED
+    csr = lib.rr_operator(kind=lib.RR_OP_CSR, dtype=0, n=n, rowptr=0x1000, colidx=0x2000,
+                          vals=0x3000, nnz=3 * n)
+    g.max_rhs = 4                                   # 4 columns: k >= 8 needed
+    assert lib.randrand_workspace_bytes(csr, 8, g) > 0
+    with pytest.raises(lib.RandRandError) as e:
+        lib.randrand_workspace_bytes(csr, 7, g)
+    assert e.value.status == lib.RR_ERR_UNSUPPORTED
+
+
 def test_oracle_not_imported_by_product():
     # the product path never imports the oracle
     for dirpath, _, files in os.walk(os.path.join(ROOT, "paper_2509_19747_gb300")):
