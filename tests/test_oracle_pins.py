@@ -340,6 +340,22 @@ def test_c_randrand_eigenvalue_bracket():
     assert ev.min() >= lo * (1 - 1e-9) and ev.max() <= hi * (1 + 1e-9)
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_power_estimate_of_E_within_five_percent_from_below(seed):
+    # |E| = |(I - Pi) A_mu (I - Pi)| by 20 power iterations (Alg. 7 step 2,
+    # the count fixed at 20): on the lambda_i = i^-2 spectrum the norm-ratio
+    # estimate of a symmetric PSD matrix never exceeds the 2-norm and is
+    # within 5% of the dense value
+    n, k, mu = 400, 30, 1e-4
+    P = W.dense_power_spectrum(n, seed=W.SEED_DENSE, power=2.0)
+    op = O.DenseOp(P.A)
+    bd = O.build(op, mu, k, "gaussian", seed=seed)
+    I = np.eye(n)
+    Pi = bd.Pi(I)
+    nE = np.linalg.norm((I - Pi) @ (P.A + mu * I) @ (I - Pi), 2)
+    assert 0.95 * nE <= bd.normE <= nE * (1 + 1e-12)
+
+
 def test_r_randrand_condition_bound():
     # Prop. thm:cnd_bound eq:cnd_bound: for lambda_min <= tau <= |E| the
     # spectrum of B lies in [lambda_min(A_mu), |E|] (rho = 1)
