@@ -295,6 +295,9 @@ rr_status randrand_build(const rr_operator* A, double mu, int32_t k, int32_t ske
  *   rtol    stop when |b - A_mu x| <= rtol |b| for every column.
  *   maxit   budget of Krylov iterations per column (summed over restarts).
  *   info    host array of nrhs entries (may be NULL).
+ * A zero column of b gets x = 0 (RR_OK); a column of b holding a NaN or an
+ * Inf ends at once with RR_ERR_BREAKDOWN (0 iterations) while the other
+ * columns solve.
  * Synchronises the stream.  Returns RR_OK when every column met rtol,
  * otherwise the worst per-column status.  Errors: RR_ERR_INVALID_ARG,
  * RR_ERR_CUDA.

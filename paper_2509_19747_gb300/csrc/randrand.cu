@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <chrono>
+#include <limits>
 #include <map>
 #include <mutex>
 #include <new>
@@ -54,6 +55,15 @@ bool uses_f64(const rr_build_opts& o) { return o.precision == RR_PREC_FP64; }
 
 // Alg. 3 (randomized Q-less QR) replaces CholeskyQR2 when asked for
 bool uses_alg3(const rr_build_opts& o) { return o.orth == RR_ORTH_RAND_CHOLQR; }
+// |r| / |b| of one column from the squared norms.  A zero b gives 0 (its
+// solution x = 0 is exact); a non-finite |b| (NaN or Inf in b) gives NaN,
+// which ends the column with RR_ERR_BREAKDOWN rather than reading as
+// converged
+double rel_residual(double rn2, double bn2) {
+  const double bn = std::sqrt(bn2);
+  if (!std::isfinite(bn)) return std::numeric_limits<double>::quiet_NaN();
+  return bn > 0.0 ? std::sqrt(rn2) / bn : 0.0;
+}
 // basis-less representation (Sec. 4.2): no n x k basis is kept, Q is applied
 // through A_mu, Omega and R^-1 (sparse operators only)
 bool basis_less(const rr_operator& A, const rr_build_opts& o) {
@@ -1964,7 +1974,7 @@ rr_status solve_impl(rr_handle* h, int m, double rtol, int maxit, bool x_guess,
     for (int c = 0; c < mp; ++c) {
       if (c >= m) continue;
       const double bn = std::sqrt(bn2[c]);
-      rel[c] = bn > 0.0 ? std::sqrt(rn2[c]) / bn : 0.0;
+      rel[c] = rel_residual(rn2[c], bn2[c]);
       if (done[c]) continue;
       if (!std::isfinite(rel[c])) { done[c] = true; stat[c] = RR_ERR_BREAKDOWN; continue; }
       if (rel[c] <= rtol) { done[c] = true; stat[c] = RR_OK; continue; }
@@ -2450,7 +2460,7 @@ bool group_decide(GroupSys* q, const double* rn2) {
     q->active[c] = false;
     if (c >= q->m) continue;
     const double bn = std::sqrt(q->bn2[c]);
-    q->rel[c] = bn > 0.0 ? std::sqrt(rn2[c]) / bn : 0.0;
+    q->rel[c] = rel_residual(rn2[c], q->bn2[c]);
     if (q->done[c]) continue;
     if (!std::isfinite(q->rel[c])) { q->done[c] = true; q->stat[c] = RR_ERR_BREAKDOWN; continue; }
     if (q->rel[c] <= q->rtol) { q->done[c] = true; q->stat[c] = RR_OK; continue; }

@@ -79,3 +79,27 @@ def test_eight_rhs_kernel_mixed(cuda_lib):
     x5, status, infos = h.solve(dev(B[:, :5]), rtol=1e-6)
     assert status == rr.RR_OK and len(infos) == 5
     assert np.all(O.true_rel_residual(op, mu, x5.cpu().numpy(), B[:, :5]) <= 1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_non_finite_right_hand_side_column_breaks_down_alone(cuda_lib, precision):
+    """A NaN or an Inf in one column of b ends that column at once with
+    RR_ERR_BREAKDOWN (its |b| is not finite: it must not read as converged),
+    and the other column still solves to the tolerance."""
+    rr = cuda_lib
+    n, k, mu = 1501, 40, 1e-3
+    X = W.mixture_points(n, seed=160)
+    op = O.GaussKernelOp(X)
+    B = W.gaussian_rhs(n, 2, 160)
+    tol = 1e-8 if precision == "fp64" else 1e-6
+    h = rr.Handle(rr.Operator.gauss_kernel(dev(X)), mu, k, "gaussian", seed=160,
+                  precision=precision, max_rhs=2)
+    for bad in (np.nan, np.inf):
+        Bb = B.copy()
+        Bb[7, 0] = bad
+        x, status, infos = h.solve(dev(Bb), rtol=tol)
+        assert status == rr.RR_ERR_BREAKDOWN
+        assert infos[0]["status"] == rr.RR_ERR_BREAKDOWN and infos[0]["inner_iters"] == 0
+        assert infos[1]["status"] == rr.RR_OK
+        assert O.true_rel_residual(op, mu, x[:, 1:].cpu().numpy(), B[:, 1:])[0] <= tol
+    h.close()
