@@ -587,6 +587,16 @@ def run_other(args):
      "shift_path": run_shift_path, "indefinite": run_indefinite}[args.workload](args)
 
 
+def sparse_iteration_bytes(nnz, n, gamma, mp=1):
+    """Algorithmic bytes of one basis-less CSR iteration: three products with
+    A_mu (float32 values and int32 column indices, int32 row pointers, one
+    float32 vector read and one written per column), Omega^T and Omega as
+    sparse-sign patterns (gamma entries of a 4-byte index and a 1-byte sign
+    per row, each read once), and ~10 float32 vector streams per column."""
+    return (3 * (8.0 * nnz + 4.0 * (n + 1) + 2 * 4.0 * n * mp) + 2 * 5.0 * gamma * n
+            + 10 * 4.0 * n * mp)
+
+
 def run_sparse(args):
     import torch
     rank, world, local = dist_init(args)
@@ -705,14 +715,11 @@ def run_sparse(args):
     peaks = _peaks()
     if cnt < iters_total / 2:
         # persistent launches: the event pair spans whole runs of iterations.
-        # Algorithmic bytes of one basis-less iteration: three products with
-        # A_mu (values + indices, row pointers, one vector read, one written),
-        # Omega and Omega^T as patterns, ~10 vector streams (the window form
-        # keeps the matrix and the patterns in shared memory across iterations,
-        # so this is what an unfused iteration would move, not its traffic).
+        # The window form keeps the matrix and the patterns in shared memory
+        # across iterations, so these bytes are what an unfused iteration
+        # would move, not its traffic.
         per_s = tot / 1000.0 / max(iters_total, 1)
-        bytes_ = 3 * (8.0 * len(C.vals) + 4.0 * (C.n + 1) + 2 * 4.0 * C.n * mp) \
-            + 2 * 5.0 * cfg["gamma"] * C.n + 10 * 4.0 * C.n * mp
+        bytes_ = sparse_iteration_bytes(len(C.vals), C.n, cfg["gamma"], mp)
         kern, unit_note = "k_pcg_implicit_win (per iteration)", "iterations"
         traffic = TRAFFIC["k_pcg_implicit_win"]
     else:

@@ -77,3 +77,21 @@ def test_json_line_carries_the_contract_keys():
         assert key in line
     assert line["higher_is_better"] is True and line["vs_baseline"] is None
     assert line["roofline"] == {"frac": 0.41}
+
+
+def test_sparse_iteration_bytes_of_the_diffusion_stencil():
+    # 512 x 512 five-point stencil: n = 262144 rows, 5 n - 4 * 512 nonzeros
+    # (the boundary rows miss one neighbour per edge they touch); gamma = 8
+    side = 512
+    n = side * side
+    nnz = 5 * n - 4 * side
+    product = 8 * nnz + 4 * (n + 1) + 2 * 4 * n        # values+indices, rowptr, v in, w out
+    patterns = 2 * 5 * 8 * n                            # Omega^T and Omega: 8 x (4 + 1) B per row
+    vectors = 10 * 4 * n
+    expect = 3 * product + patterns + vectors
+    assert expect == 72302604
+    assert bench.sparse_iteration_bytes(nnz, n, 8, 1) == pytest.approx(expect, rel=0, abs=0)
+    # the generator's matrix has that many nonzeros
+    from workloads import generators as W
+    C = W.diffusion_csr(side=64, seed=0x52523)
+    assert len(C.vals) == 5 * 64 * 64 - 4 * 64
